@@ -1,0 +1,195 @@
+/*
+ * FP64 oracle for the coupled Dean--Kawasaki MLMC hot path (see dk_oracle.h).
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by tests/, __graft_entry__.smoke() and the
+ * CPU legs of bench.py; never by the product path.  Plain, slow, obviously
+ * correct: every array is double, every step is written out as the paper
+ * states it, nothing is fused or reordered.
+ */
+#include "dk_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------ Philox */
+/* Philox4x32-10 as published by Salmon, Moraes, Dror and Shaw, "Parallel
+ * random numbers: as easy as 1, 2, 3" (SC'11): ten rounds, each multiplying
+ * words 0 and 2 by the two round multipliers, xoring the high halves with the
+ * other two words and the round key, and swapping; the key is advanced by the
+ * two Weyl constants between rounds. */
+#define PHILOX_M0 0xD2511F53u
+#define PHILOX_M1 0xCD9E8D57u
+#define PHILOX_W0 0x9E3779B9u
+#define PHILOX_W1 0xBB67AE85u
+
+void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += PHILOX_W0;
+            k1 += PHILOX_W1;
+        }
+        uint64_t prod0 = (uint64_t)PHILOX_M0 * (uint64_t)c0;
+        uint64_t prod1 = (uint64_t)PHILOX_M1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(prod0 >> 32), lo0 = (uint32_t)prod0;
+        uint32_t hi1 = (uint32_t)(prod1 >> 32), lo1 = (uint32_t)prod1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* ----------------------------------------------------------------- normals */
+static void box_muller(uint32_t a, uint32_t b, double* z1, double* z2)
+{
+    const double two32 = 4294967296.0;
+    double u = ((double)a + 1.0) / two32;            /* in (0, 1] */
+    double theta = 2.0 * M_PI * ((double)b + 0.5) / two32;
+    double radius = sqrt(-2.0 * log(u));
+    *z1 = radius * cos(theta);
+    *z2 = radius * sin(theta);
+}
+
+void oracle_normals(uint64_t seed, int level, int stream, uint64_t sample, int64_t m,
+                    int n, double* Z)
+{
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    uint32_t tag = ((uint32_t)(level + 1) & 0xffu) | (((uint32_t)stream & 0xffu) << 8) |
+                   ((uint32_t)((sample >> 32) & 0xffffu) << 16);
+    int64_t cells = (int64_t)n * n;
+    for (int64_t p = 0; p < cells / 2; ++p) {
+        uint32_t ctr[4] = {(uint32_t)p, (uint32_t)m, (uint32_t)(sample & 0xffffffffu), tag};
+        uint32_t x[4];
+        oracle_philox4x32_10(ctr, key, x);
+        box_muller(x[0], x[1], &Z[(2 * p) * 2 + 0], &Z[(2 * p) * 2 + 1]);
+        box_muller(x[2], x[3], &Z[(2 * p + 1) * 2 + 0], &Z[(2 * p + 1) * 2 + 1]);
+    }
+}
+
+/* -------------------------------------------------------------------- step */
+static inline int wrap(int i, int n) { return (i % n + n) % n; }
+
+void oracle_dk_step(int n, double h, double tau, double inv_sqrt_N,
+                    const double* rho, const double* dbeta, double* out)
+{
+    const int d = 2;
+    const double h_pow = pow(h, -0.5 * d);   /* h^{-d/2}: grid white-noise basis scale */
+    /* Flux field F_r(y) = h^{-d/2} sqrt([rho(y)]^+) dbeta_(y,r). */
+    double* F = NULL;
+    if (inv_sqrt_N != 0.0) {
+        F = (double*)malloc(sizeof(double) * (size_t)n * n * 2);
+        for (int y = 0; y < n * n; ++y) {
+            double pos = rho[y] > 0.0 ? rho[y] : 0.0;
+            F[2 * y + 0] = h_pow * sqrt(pos) * dbeta[2 * y + 0];
+            F[2 * y + 1] = h_pow * sqrt(pos) * dbeta[2 * y + 1];
+        }
+    }
+    for (int i1 = 0; i1 < n; ++i1) {
+        for (int i2 = 0; i2 < n; ++i2) {
+            int x = i1 * n + i2;
+            int up = wrap(i1 - 1, n) * n + i2, down = wrap(i1 + 1, n) * n + i2;
+            int left = i1 * n + wrap(i2 - 1, n), right = i1 * n + wrap(i2 + 1, n);
+            /* Delta_h a(x) = (-4 a(x) + sum_{y~x} a(y)) / h^2 */
+            double lap = (-4.0 * rho[x] + rho[up] + rho[down] + rho[left] + rho[right]) / (h * h);
+            double value = rho[x] + tau * 0.5 * lap;
+            if (F) {
+                /* nabla_h . b(x) = sum_r ([b]_r(x + h f_r) - [b]_r(x - h f_r)) / (2h) */
+                double div = (F[2 * down + 0] - F[2 * up + 0]) / (2.0 * h) +
+                             (F[2 * right + 1] - F[2 * left + 1]) / (2.0 * h);
+                value += inv_sqrt_N * div;
+            }
+            out[x] = value;
+        }
+    }
+    free(F);
+}
+
+void oracle_mean_field(int n, double h, double tau, int64_t M, const double* rho0, double* out)
+{
+    double* a = (double*)malloc(sizeof(double) * (size_t)n * n);
+    double* b = (double*)malloc(sizeof(double) * (size_t)n * n);
+    memcpy(a, rho0, sizeof(double) * (size_t)n * n);
+    for (int64_t m = 0; m < M; ++m) {
+        oracle_dk_step(n, h, tau, 0.0, a, NULL, b);
+        double* t = a; a = b; b = t;
+    }
+    memcpy(out, a, sizeof(double) * (size_t)n * n);
+    free(a);
+    free(b);
+}
+
+/* ------------------------------------------------------------------ sample */
+static double inner_h(int n, double h, const double* f, const double* g)
+{
+    /* (f, g)_h = h^d sum_x f(x) g(x) */
+    double s = 0.0;
+    for (int x = 0; x < n * n; ++x) s += f[x] * g[x];
+    return h * h * s;
+}
+
+int oracle_sample(const oracle_level* lv, uint64_t seed, int stream, uint64_t sample,
+                  int coupled, double* Y_f, double* Y_c, double* mass_f, double* mass_c,
+                  double* rho_f_out, double* rho_c_out)
+{
+    const int n = lv->n, nc = n / 2;
+    if (n < 2 || (n & 1)) return -1;
+    if (coupled && (lv->M % 4) != 0) return -2;
+    const size_t cf = (size_t)n * n, cc = (size_t)nc * nc;
+    double* rho_f = (double*)malloc(sizeof(double) * cf);
+    double* tmp_f = (double*)malloc(sizeof(double) * cf);
+    double* Z = (double*)malloc(sizeof(double) * cf * 2);
+    double* dbeta_f = (double*)malloc(sizeof(double) * cf * 2);
+    double* rho_c = NULL, *tmp_c = NULL, *dbeta_c = NULL;
+    memcpy(rho_f, lv->rho0_f, sizeof(double) * cf);
+    if (coupled) {
+        rho_c = (double*)malloc(sizeof(double) * cc);
+        tmp_c = (double*)malloc(sizeof(double) * cc);
+        dbeta_c = (double*)calloc(cc * 2, sizeof(double));
+        memcpy(rho_c, lv->rho0_c, sizeof(double) * cc);
+    }
+    const double sqrt_tau = sqrt(lv->tau);
+    const double block_weight = pow(2.0, -0.5 * 2);   /* 2^{-d/2} of the NN coupling */
+    for (int64_t m = 0; m < lv->M; ++m) {
+        oracle_normals(seed, lv->level, stream, sample, m, n, Z);
+        for (size_t i = 0; i < cf * 2; ++i) dbeta_f[i] = sqrt_tau * Z[i];
+        if (coupled) {
+            /* beta-tilde_(y,r) = 2^{-d/2} sum_{z in B->(y)} beta_(z,r), B->(y) = {y + h v}:
+             * fine cells (2 I1 + v1, 2 I2 + v2).  The coarse increment over one coarse
+             * step is the sum of the kappa_t = 4 fine increments inside it. */
+            for (int i1 = 0; i1 < n; ++i1)
+                for (int i2 = 0; i2 < n; ++i2) {
+                    int z = i1 * n + i2, y = (i1 / 2) * nc + (i2 / 2);
+                    dbeta_c[2 * y + 0] += block_weight * dbeta_f[2 * z + 0];
+                    dbeta_c[2 * y + 1] += block_weight * dbeta_f[2 * z + 1];
+                }
+        }
+        oracle_dk_step(n, lv->h, lv->tau, lv->inv_sqrt_N, rho_f, dbeta_f, tmp_f);
+        double* t = rho_f; rho_f = tmp_f; tmp_f = t;
+        if (coupled && (m % 4) == 3) {
+            oracle_dk_step(nc, 2.0 * lv->h, 4.0 * lv->tau, lv->inv_sqrt_N, rho_c, dbeta_c, tmp_c);
+            double* tc = rho_c; rho_c = tmp_c; tmp_c = tc;
+            memset(dbeta_c, 0, sizeof(double) * cc * 2);
+        }
+    }
+    double* ones = (double*)malloc(sizeof(double) * cf);
+    for (size_t i = 0; i < cf; ++i) ones[i] = 1.0;
+    for (int k = 0; k < lv->n_obs; ++k) Y_f[k] = inner_h(n, lv->h, rho_f, lv->phi_f + (size_t)k * cf);
+    if (mass_f) *mass_f = inner_h(n, lv->h, rho_f, ones);
+    if (rho_f_out) memcpy(rho_f_out, rho_f, sizeof(double) * cf);
+    if (coupled) {
+        for (int k = 0; k < lv->n_obs; ++k)
+            Y_c[k] = inner_h(nc, 2.0 * lv->h, rho_c, lv->phi_c + (size_t)k * cc);
+        if (mass_c) *mass_c = inner_h(nc, 2.0 * lv->h, rho_c, ones);
+        if (rho_c_out) memcpy(rho_c_out, rho_c, sizeof(double) * cc);
+    }
+    free(ones);
+    free(rho_f); free(tmp_f); free(Z); free(dbeta_f);
+    free(rho_c); free(tmp_c); free(dbeta_c);
+    return 0;
+}

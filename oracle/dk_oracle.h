@@ -1,0 +1,82 @@
+/*
+ * FP64 oracle for the coupled Dean--Kawasaki MLMC hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference legs of bench.py may load this library.  It shares
+ * no code with the CUDA path (paper_2311_08872_gb300/csrc) and never calls it.
+ *
+ * Plain, single-threaded, double precision, written to be read against the
+ * paper (Cornalba & Fischer, "Multilevel Monte Carlo methods for the
+ * Dean--Kawasaki equation from Fluctuating Hydrodynamics"):
+ *   - Definition 2.1, Eq. (FullyDiscreteDK) with b0 = 0, b1 = 1 (Section 7.2),
+ *   - the operators Delta_h and nabla_h. of Section 7.2,
+ *   - the Right-Most Nearest-Neighbour coupling of Section 3.2,
+ *   - the observable P_l of Eq. (eqn_MLMCLevels) with psi(x) = x^2.
+ *
+ * Conventions (readings where the paper is silent; same reading as the CUDA
+ * path, written separately):
+ *   grid point (i1,i2) at (i1*h, i2*h), flat index i1*n+i2, periodic;
+ *   component r = 1 is the i1 axis, r = 2 the i2 axis;
+ *   Brownian increments dbeta = sqrt(tau) * Z with Z from Philox4x32-10 +
+ *   Box--Muller (see oracle_normals).
+ */
+#ifndef DK_ORACLE_H
+#define DK_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Philox4x32 with 10 rounds (Salmon et al., SC'11). */
+void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* Standard normals Z[(i1*n+i2)*2 + (r-1)] for fine step m of sample `sample`
+ * at level `level` (tag level+1) in stream `stream` (0 coupled MLMC, 1 plain
+ * MC), for an n x n grid (n even).  Cell pair p = (i1*n+i2)/2 uses
+ *   ctr = (p, m, sample & 0xffffffff,
+ *          (level+1)&0xff | (stream&0xff)<<8 | ((sample>>32)&0xffff)<<16),
+ *   key = (seed & 0xffffffff, seed >> 32);
+ * words (x0,x1) give cell 2p, (x2,x3) cell 2p+1 via Box--Muller with
+ *   u = (x0+1) 2^-32, theta = 2 pi (x1 + 1/2) 2^-32,
+ *   Z_1 = sqrt(-2 ln u) cos theta, Z_2 = sqrt(-2 ln u) sin theta. */
+void oracle_normals(uint64_t seed, int level, int stream, uint64_t sample, int64_t m,
+                    int n, double* Z);
+
+/* One step of Eq. (FullyDiscreteDK), b0 = 0, b1 = 1:
+ *   out = rho + tau/2 Delta_h rho + inv_sqrt_N * div_h( F ),
+ *   F_r(y) = h^{-d/2} sqrt([rho(y)]^+) dbeta[(y, r)],  d = 2.
+ * dbeta has layout [n*n][2]; inv_sqrt_N = 0 switches the noise off. */
+void oracle_dk_step(int n, double h, double tau, double inv_sqrt_N,
+                    const double* rho, const double* dbeta, double* out);
+
+typedef struct {
+    int n;               /* fine cells per axis (even) */
+    double h;            /* fine mesh size */
+    double tau;          /* fine time step */
+    int64_t M;           /* fine steps (multiple of 4 when coupled) */
+    int level;           /* level index l (tag l+1) */
+    double inv_sqrt_N;   /* N^{-1/2}; 0 = noise off */
+    const double* rho0_f;/* I_h rho0 on the fine grid, n*n */
+    const double* rho0_c;/* I_{2h} rho0 on the coarse grid, (n/2)^2 (coupled only) */
+    int n_obs;
+    const double* phi_f; /* [n_obs][n*n] */
+    const double* phi_c; /* [n_obs][(n/2)^2] */
+} oracle_level;
+
+/* One sample of level `lv`: fine path, and if `coupled` the NN-coupled coarse
+ * path (mesh 2h, step 4 tau, increments summed over 2x2 cells and 4 steps).
+ * Outputs Y_f[k] = (rho_f^M, phi_f[k])_h, Y_c[k] likewise on the coarse grid,
+ * masses (rho, 1)_h, and optionally the final fields.  Returns 0 on success. */
+int oracle_sample(const oracle_level* lv, uint64_t seed, int stream, uint64_t sample,
+                  int coupled, double* Y_f, double* Y_c, double* mass_f, double* mass_c,
+                  double* rho_f_out, double* rho_c_out);
+
+/* Noise-free scheme (the discrete mean field rho-bar of Eq. (eqn_MLMCLevels))
+ * iterated M times from rho0. */
+void oracle_mean_field(int n, double h, double tau, int64_t M, const double* rho0, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
