@@ -1,0 +1,420 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 MLMC hot path for the 2-D Dean--Kawasaki equation.
+
+Workload (default ``mlmc16_256``): unit torus, levels 16^2..256^2 (h_l =
+1/16..1/256), tau_l ~ 0.1 h_l^2, T = 0.02, N = 1e5, rho0 = 1 + 0.5 sin sin,
+phi = cos(2 pi x1), NN-coupled levels, RMSE target eps = 1e-3 relative.
+
+One *step* is one pass of the whole hot path over the workload's MLMC batch:
+for every level l, M_l coupled samples (Philox normals, fused fine/coarse
+stepping, observables, P, FP64 moment sums; the per-level counts M_l are the
+allocation Algorithm 1 reaches for eps = 1e-3), then the estimator and its
+variance from the sums (Eq. MLMCEstimator).  ``value`` is coupled
+sample-steps per second (sum over levels of M_l x fine steps, per second),
+inputs resident on the device; ``e2e`` is the same through the public C-ABI
+with host buffers (init uploads the level tables from pinned memory, host
+sums are read back per level).  Also reported: the wall time of a full
+adaptive Algorithm 1 run to eps and the plain single-level MC time to the
+same eps on the finest level reached (sample count 2 Var[P_L] / eps^2 times
+the measured MC time per sample).
+
+Under torchrun every rank runs the same batch under its own seed (independent
+samples, no collective on the data path): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLMC wall time to RMSE ε vs plain MC (1 GB300); coupled sample-steps/s; HBM GB/s"
+UNIT = "coupled sample-steps/s"
+# XU-pipe (MUFU) operations the method needs per fine cell-step: Box--Muller
+# for the two normals (log, sqrt, sin, cos) and sqrt([rho]^+); per coarse
+# cell-step sqrt([rho]^+) only (coarse normals are sums of fine ones).
+XU_OPS_FINE = 5.0
+XU_OPS_COARSE = 1.0
+XU_PER_CLK_PER_SM = 16
+SMS = 152
+SM_MAX_MHZ = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="mlmc16_256")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-adaptive", action="store_true", help="skip the Algorithm 1 / plain MC timing")
+    ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+def level_costs(wl):
+    import oracle
+    lv = oracle.level_table(wl.length, wl.n0, wl.L_max, wl.T, wl.mu, wl.M0)
+    fine = [l.n * l.n * l.M for l in lv]
+    coarse = [0.0] + [lv[l - 1].n ** 2 * lv[l - 1].M for l in range(1, len(lv))]
+    return lv, fine, coarse
+
+
+def batch_units(wl, alloc):
+    lv, fine, coarse = level_costs(wl)
+    sample_steps = sum(m * lv[l].M for l, m in enumerate(alloc))
+    cell_steps = sum(m * (fine[l] + coarse[l]) for l, m in enumerate(alloc))
+    return sample_steps, cell_steps
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------ CPU oracle leg
+def _oracle_task(args):
+    (wl, level, sample) = args
+    import oracle
+    lv = oracle.level_table(wl.length, wl.n0, wl.L_max, wl.T, wl.mu, wl.M0)
+    ol = oracle.level_inputs(wl.length, lv, wl.N, wl.rho0_all(), wl.phi_all(), level, level > 0)
+    t = time.perf_counter()
+    ol.sample(wl.seed, sample, level > 0)
+    return level, time.perf_counter() - t
+
+
+def oracle_rate(wl, alloc, budget_s, cores=None):
+    """The FP64 oracle, as it stands, on the host cores: per-level single-core
+    seconds per coupled sample measured on a bounded sample (levels with a
+    sample of at most ~budget/4 core-seconds), extrapolated by cell-steps to
+    the others, then the batch's sample-steps over the batch's CPU time on
+    `cores` cores."""
+    import multiprocessing as mp
+    cores = cores or min(os.cpu_count() or 1, 16)
+    lv, fine, coarse = level_costs(wl)
+    per_cell = 1.0 / 15e6     # first guess, refined by the measurement below
+    tasks = []
+    for l in range(len(alloc)):
+        est = (fine[l] + coarse[l]) * per_cell
+        if est > budget_s * cores / 4:
+            continue
+        k = max(1, min(64, int(budget_s * cores / (4 * max(est, 1e-6) * len(alloc)))))
+        tasks += [(wl, l, 1000 + i) for i in range(k)]
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_task, tasks, chunksize=1)
+    wall = time.perf_counter() - t0
+    per_level = {}
+    for l, dt in res:
+        per_level.setdefault(l, []).append(dt)
+    t = {l: statistics.mean(v) for l, v in per_level.items()}
+    top = max(t)
+    cell_rate = (fine[top] + coarse[top]) / t[top]
+    secs = []
+    for l, m in enumerate(alloc):
+        secs.append(m * (t[l] if l in t else (fine[l] + coarse[l]) / cell_rate))
+    sample_steps, cell_steps = batch_units(wl, alloc)
+    cpu_time = sum(secs) / cores
+    sample = (f"{len(tasks)} coupled samples of levels {sorted(t)} in {wall:.1f} s wall on {cores} processes; "
+              f"levels {[l for l in range(len(alloc)) if l not in t]} extrapolated by cell-steps from level {top}")
+    return {"value": sample_steps / cpu_time, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": sample, "cell_steps_per_s": cell_steps / cpu_time,
+            "batch_cpu_s": cpu_time, "wall_s": wall}
+
+
+# --------------------------------------------------------------- our arm
+def run_ours(args, wl, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2311_08872_gb300 import mlmc_dk
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    alloc = list(wl.alloc) if wl.alloc else None
+    seed0 = wl.seed + 1000003 * rank
+
+    ctx = mlmc_dk.Context.from_workload(wl, stream=stream.cuda_stream)
+    info = [ctx.level_info(l) for l in range(wl.L_max + 1)]
+    out = {}
+
+    # ---- adaptive Algorithm 1 to eps (also gives the allocation if none is fixed)
+    adaptive = None
+    if not args.no_adaptive or alloc is None:
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        r = ctx.estimate(wl.eps_rel, relative=True, seed=seed0)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t
+        L = r.L
+        adaptive = {"s": wall, "L": L, "M": [r.M[l] for l in range(L + 1)], "estimate": r.estimate,
+                    "variance": r.variance, "eps_abs": r.eps_abs, "converged": bool(r.converged),
+                    "var_pf_L": r.var_pf[L]}
+        if alloc is None:
+            alloc = adaptive["M"]
+    alloc = alloc + [0] * (wl.L_max + 1 - len(alloc))
+    sample_steps, cell_steps = batch_units(wl, alloc)
+
+    nq = ctx.n_quant
+    sums = torch.zeros(wl.L_max + 1, mlmc_dk.sums_len(nq), dtype=torch.float64, device=dev)
+    host = torch.zeros_like(sums, device="cpu").pin_memory()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in alloc]
+    step_ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+
+    def step(seed):
+        step_ev[0].record(stream)
+        for l, m in enumerate(alloc):
+            if m <= 0:
+                continue
+            ev[l][0].record(stream)
+            ctx.run_level_dev(l, 0, 0, m, seed, sums[l].data_ptr(), 0, stream.cuda_stream)
+            ev[l][1].record(stream)
+        host.copy_(sums, non_blocking=True)
+        step_ev[1].record(stream)
+        stream.synchronize()
+        s = host.numpy()
+        est, var = 0.0, 0.0
+        for l, m in enumerate(alloc):
+            if m <= 0:
+                continue
+            e = s[l, 2] / m
+            est += e
+            var += max(0.0, (s[l, 3] - s[l, 2] ** 2 / m) / (m - 1)) / m
+        return est, var
+
+    for w in range(args.warmup):
+        step(seed0 + 17 + w)
+    clocks = Clocks(local_rank)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    step_ms, level_ms = [], [0.0] * len(alloc)
+    launches = 0
+    for k in range(args.steps):
+        flush.zero_()                      # evict L2 between steps (outside the step events)
+        step(seed0 + 101 + k)
+        step_ms.append(step_ev[0].elapsed_time(step_ev[1]))
+        for l, m in enumerate(alloc):
+            if m > 0:
+                level_ms[l] += ev[l][0].elapsed_time(ev[l][1])
+                launches += 2
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * sample_steps * args.steps / (total_ms * 1e-3)
+
+    # ---- roofline of the dominant kernel (the level kernel of the costliest level)
+    dom = max(range(len(alloc)), key=lambda l: level_ms[l])
+    lv, fine, coarse = level_costs(wl)
+    ops = alloc[dom] * (fine[dom] * XU_OPS_FINE + coarse[dom] * XU_OPS_COARSE) * args.steps
+    achieved = ops / (level_ms[dom] * 1e-3)
+    peak = XU_PER_CLK_PER_SM * SMS * SM_MAX_MHZ * 1e6
+    roofline = {"bound": "alu", "pipe": "XU (MUFU)", "kernel": f"level_kernel n={info[dom].n} coupled={dom > 0}",
+                "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gop/s", "frac": achieved / peak,
+                "traffic": None, "ops_per_fine_cell_step": XU_OPS_FINE,
+                "cell_steps_per_s": alloc[dom] * (fine[dom] + coarse[dom]) * args.steps / (level_ms[dom] * 1e-3),
+                "level_ms_per_step": [x / args.steps for x in level_ms]}
+
+    # ---- plain MC to the same eps on the finest level reached
+    mc = None
+    if adaptive is not None:
+        L = adaptive["L"]
+        n_mc = int(max(64, min(20000, 2.0e11 / (fine[L]))))
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        ctx.run_level(L, n_mc, seed0 + 7, mc=True)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        per = a0.elapsed_time(a1) * 1e-3 / n_mc
+        m_mc = math.ceil(2.0 * adaptive["var_pf_L"] / adaptive["eps_abs"] ** 2)
+        mc = {"level": L, "samples": m_mc, "s_per_sample": per, "s": m_mc * per, "extrapolated": True,
+              "measured_samples": n_mc}
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        ctx.close()
+        times, h2d, d2h = [], 0, 0
+        for k in range(args.steps):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            c2 = mlmc_dk.Context.from_workload(wl, stream=stream.cuda_stream)
+            est, d2h_k = 0.0, 0
+            for l, m in enumerate(alloc):
+                if m > 0:
+                    s = c2.run_level(l, m, seed0 + 101 + k)[0]
+                    est += s.dp1 / s.n
+                    d2h_k += s.d2h_bytes
+            h2d_k = c2.level_info(0).h2d_bytes
+            c2.close()
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t)
+            h2d, d2h = h2d_k, d2h_k
+        tot = sum(times)
+        if world > 1:
+            t = torch.tensor([tot], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            tot = float(t.item())
+        e2e = {"value": world * sample_steps * args.steps / tot, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * tot / args.steps,
+               "what": "mlmc_dk_init (FFT mean fields + pinned uploads) + mlmc_dk_run_level per level + free"}
+    else:
+        ctx.close()
+
+    if rank != 0:
+        return None
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_rate(wl, alloc, args.cpu_budget)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "i32 fixed-point state, f32 noise, f64 sums",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "levels": [i.n for i in info], "fine_steps": [i.M for i in info],
+                   "T": wl.T, "N": wl.N, "mu": wl.mu, "eps_rel": wl.eps_rel, "alloc": alloc,
+                   "sample_steps_per_step": sample_steps, "cell_steps_per_step": cell_steps,
+                   "l2": "512 MiB buffer zeroed between timed steps, outside the step events",
+                   "parallelism": f"{world} independent rank(s), own seeds"},
+        "cell_steps_per_s": world * cell_steps * args.steps / (total_ms * 1e-3),
+        "gpu_launches": launches,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clk,
+    }
+    if adaptive is not None:
+        line["mlmc_s_to_eps"] = adaptive["s"]
+        line["mlmc_adaptive"] = adaptive
+        line["mc_s_to_eps"] = mc["s"] if mc else None
+        line["mc"] = mc
+        if mc:
+            line["mlmc_speedup_vs_mc"] = mc["s"] / adaptive["s"]
+    return line
+
+
+def run_reference(args, wl, rank, world):
+    if rank != 0:
+        return None
+    alloc = list(wl.alloc) if wl.alloc else None
+    if alloc is None:
+        return {"impl": "reference", "unavailable": "workload has no fixed allocation"}
+    alloc = alloc + [0] * (wl.L_max + 1 - len(alloc))
+    sample_steps, cell_steps = batch_units(wl, alloc)
+    budget = max(2.0, args.cpu_budget / 3)
+    for _ in range(args.warmup):
+        oracle_rate(wl, alloc, budget / 2)
+    vals, res = [], None
+    for _ in range(args.steps):
+        res = oracle_rate(wl, alloc, budget)
+        vals.append(res["batch_cpu_s"])
+    cpu_s = statistics.mean(vals)
+    value = sample_steps / cpu_s
+    cb = dict(res)
+    cb["value"] = value
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * cpu_s, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "alloc": alloc, "sample_steps_per_step": sample_steps,
+                       "cell_steps_per_step": cell_steps,
+                       "what": "FP64 oracle (plain C) per coupled sample on the host cores; each step times a "
+                               "bounded sample of the batch and scales it to the full batch by level"},
+            "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    from paper_2311_08872_gb300 import workloads
+    wl = workloads.get(args.workload)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        line = run_reference(args, wl, rank, world)
+    else:
+        if world > 1:
+            import torch
+            torch.cuda.set_device(local_rank)
+            torch.distributed.init_process_group("nccl")
+        line = run_ours(args, wl, rank, world, local_rank)
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+    if line is not None:
+        print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,242 @@
+/*
+ * mlmc_dk.h -- C-ABI of the GB300 (sm_103a) Multilevel Monte Carlo library for
+ * the 2-D Dean--Kawasaki equation (Cornalba & Fischer, arXiv 2311.08872).
+ *
+ * What the library computes
+ * -------------------------
+ * For levels l = 0..L_max with n_l = n0 2^l cells per axis, h_l = length/n_l,
+ * tau_l = tau_0 4^-l and M_l = M_0 4^l fine steps (Eq. cfl_preserved, Section
+ * 7.2), one *sample* of level l is the pair of paths of Eq. (FullyDiscreteDK)
+ * with b0 = 0, b1 = 1 (explicit Euler--Maruyama, Section 7.2):
+ *     rho^{m+1} = rho^m + tau/2 Delta_h rho^m
+ *                 + N^{-1/2} div_h( h^{-1} sqrt([rho^m]^+) dbeta^m ),
+ * on the fine grid (h_l, tau_l) and -- for l >= 1 -- on the coarse grid
+ * (h_{l-1}, tau_{l-1}) driven by the Right-Most Nearest-Neighbour coupled
+ * increments of Section 3.2 (each coarse increment is 1/2 x the sum of the
+ * 2x2 fine increments to its right, summed over the 4 fine steps inside one
+ * coarse step).  Each path is reduced at T to Y_k = (rho^T, I_h phi_k)_h and to
+ *     P = N (Y_j - Ybar_j)(Y_k - Ybar_k)          (Eq. eqn_MLMCLevels, psi = x^2;
+ *                                                    j = k unless `products`),
+ * where Ybar is the discrete mean field (the noise-free scheme), and the
+ * library accumulates per level the moment sums of dP = P_f - P_c (P_c = 0 on
+ * level 0) that the estimator of Eq. (MLMCEstimator) telescopes.
+ * mlmc_dk_estimate runs Algorithm 1 (Section 7.1) with the sample allocation
+ * of Eq. (opt_M_ell) and the stopping test of Eq. (convergence_criterion).
+ *
+ * Noise: dbeta = sqrt(tau) Z, Z from Philox4x32-10 + Box--Muller.  Sample i of
+ * level l in stream s is a pure function of (seed, l, s, i): for the fine cell
+ * pair p = (i1 n + i2)/2 and fine step m the counter is
+ *     (p, m, i & 0xffffffff, (l+1) | s << 8 | ((i >> 32) & 0xffff) << 16),
+ * key (seed & 0xffffffff, seed >> 32); words (x0,x1) feed cell 2p and (x2,x3)
+ * cell 2p+1 with u = (x0+1) 2^-32, theta = 2 pi (x1 + 1/2) 2^-32,
+ * Z_1 = sqrt(-2 ln u) cos theta, Z_2 = sqrt(-2 ln u) sin theta.  Stream 0 is
+ * the coupled MLMC stream, stream 1 plain single-level Monte Carlo.
+ *
+ * Grids are row-major, point (i1, i2) at (i1 h, i2 h), flat index i1 n + i2;
+ * component r = 1 of the noise flux is along i1.
+ *
+ * Precision: the state is 32-bit fixed point, rho = q 2^-S_l, with S_l in
+ * [16, 28] chosen per level at init from the initial range and the expected
+ * per-cell fluctuation sqrt(rho/(N h^2)).  Each step adds per-edge diffusion
+ * fluxes and per-cell noise transfers (computed in FP32, rounded to integers)
+ * exactly, so the mass (rho, 1)_h is conserved bit for bit and every rounding
+ * error enters in divergence form; observables and moment sums are FP64.
+ *
+ * Ownership and errors
+ * --------------------
+ * The context owns all device memory it allocates and frees it in
+ * mlmc_dk_free.  The caller owns every struct and array it passes (they are
+ * copied or only read during the call).  Every function returning int returns
+ * MLMC_DK_OK (0) on success, MLMC_DK_NOT_CONVERGED (1) when Algorithm 1 hit
+ * L_max without passing the stopping test (the result is still filled), or a
+ * negative MLMC_DK_ERR_* code; mlmc_dk_last_error gives the message.  No call
+ * aborts the process.  All device work runs on the context's stream; calls on
+ * one context must not overlap.
+ */
+#ifndef MLMC_DK_H
+#define MLMC_DK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MLMC_DK_OK 0
+#define MLMC_DK_NOT_CONVERGED 1
+#define MLMC_DK_ERR_INVALID (-1)     /* bad argument or configuration */
+#define MLMC_DK_ERR_CUDA (-2)        /* a CUDA runtime call failed */
+#define MLMC_DK_ERR_RANGE (-3)       /* |rho| reached 2^(30-S_l): the level's fixed-point range */
+#define MLMC_DK_ERR_UNSUPPORTED (-4) /* grid size without a kernel variant */
+#define MLMC_DK_ERR_STATE (-5)       /* checkpoint buffer does not match */
+
+#define MLMC_DK_MAX_LEVELS 16
+#define MLMC_DK_MAX_OBS 4
+#define MLMC_DK_MAX_QUANT 10          /* 4 observables with all products j <= k */
+#define MLMC_DK_NSUM 12               /* per-quantity device sums, see below */
+
+/* Configuration (read during mlmc_dk_init, then not referenced again). */
+typedef struct {
+    double length;          /* torus side (1.0, or 2 pi for the paper's setting) */
+    int32_t n0;             /* level-0 cells per axis: a power of two in [4, 1024] */
+    int32_t L_max;          /* finest level index, n0 << L_max <= 1024 */
+    double T;               /* final time */
+    double cfl_mu;          /* nominal tau/h^2 (<= 1/2): M_0 = ceil(T/(mu h0^2)), tau_0 = T/M_0 */
+    int32_t M0;             /* > 0: use this M_0 instead (tau_0 = T/M_0) */
+    double N;               /* particle number; 0 switches the noise off */
+    const double* const* rho0; /* [L_max+1] host arrays: rho0[l] = I_{h_l} rho-bar_0, n_l^2 values */
+    int32_t n_obs;          /* number of test functions, 1..4 */
+    const double* const* phi;  /* [(L_max+1) * n_obs] host arrays: phi[l*n_obs+k] = I_{h_l} phi_k */
+    int32_t products;       /* 0: one quantity per phi_k; 1: all pairs j <= k (n_obs(n_obs+1)/2) */
+    int32_t pilot;          /* Algorithm 1 initial samples per level (0 -> 256) */
+    int32_t L_start;        /* Algorithm 1 initial finest level (0 -> 2, capped at L_max) */
+    void* cuda_stream;      /* cudaStream_t for all device work, or NULL (legacy default stream) */
+} mlmc_dk_config;
+
+/* Per-level description returned by mlmc_dk_level_info. */
+typedef struct {
+    int32_t level, n, M;    /* fine cells per axis and fine steps */
+    double h, tau;          /* fine mesh size and step */
+    double ybar_f[MLMC_DK_MAX_OBS];  /* (rho-bar^T, phi_k)_h on the fine grid */
+    double ybar_c[MLMC_DK_MAX_OBS];  /* same on the coarse grid (level >= 1) */
+    double cost;            /* cell-steps per coupled sample: n_l^2 M_l + n_{l-1}^2 M_{l-1} */
+    double cost_mc;         /* cell-steps per plain MC sample: n_l^2 M_l */
+    int64_t next_sample;    /* first sample id the next mlmc_dk_run_level call uses */
+    int64_t h2d_bytes;      /* bytes mlmc_dk_init uploaded for all levels (pinned staging) */
+} mlmc_dk_level_desc;
+
+/* Host-side moment sums of one quantity on one level (accumulated into). */
+typedef struct {
+    int64_t n;                    /* samples */
+    double dp1, dp2, dp3, dp4;    /* sum of dP, dP^2, dP^3, dP^4 (dP = P_f - P_c) */
+    double pf1, pf2;              /* sum of P_f, P_f^2 */
+    double pc1, pc2;              /* sum of P_c, P_c^2 (0 on level 0 and for plain MC) */
+    double yf1, yf2;              /* sum of (Y_f - Ybar_f), its square (first observable of the quantity) */
+    double yc1, yc2;              /* same for the coarse path */
+    double max_mass_err;          /* max |(rho^T,1)_h - (rho^0,1)_h| over the samples (exactly 0 expected) */
+    double cost;                  /* cell-steps performed */
+    double wall_s;                /* wall time of the calls that produced the samples */
+    double kernel_s;              /* device time of their level kernels (CUDA events on the launching stream) */
+    int64_t launches;             /* kernels launched (level kernel + fixed-order reduction per call) */
+    int64_t d2h_bytes;            /* bytes read back to the host (sums and the device error word) */
+} mlmc_dk_level_sums;
+
+/* Result of Algorithm 1. */
+typedef struct {
+    double estimate;              /* mu_MLMC of the first quantity, Eq. (MLMCEstimator) */
+    double variance;              /* sum_l V_l / M_l */
+    double eps_abs;               /* absolute RMSE target used */
+    int32_t L;                    /* finest level reached */
+    int32_t converged;            /* 1 if the stopping test passed */
+    int64_t M[MLMC_DK_MAX_LEVELS];
+    double V[MLMC_DK_MAX_LEVELS], E[MLMC_DK_MAX_LEVELS], C[MLMC_DK_MAX_LEVELS];
+    double estimates[MLMC_DK_MAX_QUANT];   /* mu_MLMC of every quantity */
+    double sample_steps;          /* coupled sample-steps performed (sum of M_l x fine steps) */
+    double cell_steps;            /* fine + coarse cell-steps performed */
+    double wall_s;
+    double kernel_s[MLMC_DK_MAX_LEVELS];   /* device time of each level's kernels */
+    double var_pf[MLMC_DK_MAX_LEVELS];     /* sample variance of P_l from the level-l fine paths */
+    int64_t launches;             /* kernels launched */
+    int64_t d2h_bytes;            /* bytes read back to the host */
+} mlmc_dk_result;
+
+typedef struct mlmc_dk_ctx mlmc_dk_ctx;   /* opaque */
+
+/* Validate `cfg`, build the level table, compute on the host the discrete
+ * mean field rho-bar^T of every level (FFT diagonalisation of the noise-free
+ * scheme) and its pairings with phi, and upload the per-level tables (fixed
+ * point initial states and mean fields, FP32 test functions) to the device.
+ * Errors: MLMC_DK_ERR_INVALID (mu > 1/2, n0 not a power of two, sizes out of
+ * range, |rho0| >= 64, null arrays), MLMC_DK_ERR_CUDA.  On error *out is NULL
+ * and the message is available from mlmc_dk_last_error(NULL). */
+int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out);
+
+/* Release all device and host memory of the context (NULL is a no-op). */
+void mlmc_dk_free(mlmc_dk_ctx* ctx);
+
+/* Message of the last failed call on ctx (ctx == NULL: last failure of
+ * mlmc_dk_init in this thread).  Owned by the library, valid until the next
+ * call on the same context. */
+const char* mlmc_dk_last_error(const mlmc_dk_ctx* ctx);
+
+/* Fill *out with the level table entry of `level` (0..L_max). */
+int mlmc_dk_level_info(const mlmc_dk_ctx* ctx, int32_t level, mlmc_dk_level_desc* out);
+
+/* Run n_samples coupled samples of level `level` (P_l - P_{l-1}; P_0 on level
+ * 0) with ids next_sample .. next_sample+n_samples-1 under `seed`, and add
+ * their moment sums into sums[q] for every quantity q (caller-allocated host
+ * array of n_quant structs).  Advances next_sample.  Synchronous: returns
+ * after the device work and the copy of the sums to the host. */
+int mlmc_dk_run_level(mlmc_dk_ctx* ctx, int32_t level, int64_t n_samples, uint64_t seed,
+                      mlmc_dk_level_sums* sums);
+
+/* Same for plain single-level Monte Carlo samples of P_l (stream 1, fine
+ * path only; sample ids 0..n_samples-1 after the previous MC call on that
+ * level). */
+int mlmc_dk_run_mc(mlmc_dk_ctx* ctx, int32_t level, int64_t n_samples, uint64_t seed,
+                   mlmc_dk_level_sums* sums);
+
+/* Device-resident batch: samples first_sample .. first_sample+n_samples-1 of
+ * `level` in `stream_tag` (0 coupled, 1 plain MC) under `seed`.  Writes (not
+ * accumulates) into device memory:
+ *   sums_dev:    double[2 + n_quant * MLMC_DK_NSUM]: [0] sample count,
+ *                [1] max mass error, then per quantity
+ *                {dp1..dp4, pf1, pf2, pc1, pc2, yf1, yf2, yc1, yc2};
+ *   samples_dev: NULL, or double[n_samples][2 n_obs + 2]: Y_f-Ybar_f (n_obs),
+ *                Y_c-Ybar_c (n_obs, 0 without a coarse path), mass_f, mass_c.
+ * Both must be 8-byte aligned device pointers.  Asynchronous on `cuda_stream`
+ * (NULL: the context's stream); does not touch next_sample.  The scratch it
+ * needs (per-slot partial sums) is owned by the context. */
+int mlmc_dk_run_level_dev(mlmc_dk_ctx* ctx, int32_t level, int32_t stream_tag,
+                          int64_t first_sample, int64_t n_samples, uint64_t seed,
+                          double* sums_dev, double* samples_dev, void* cuda_stream);
+
+/* Algorithm 1 (Section 7.1): start at L = L_start with `pilot` samples on
+ * levels 0..L; repeat {run the missing samples, re-estimate V_l, set targets by
+ * Eq. (opt_M_ell), once no level needs samples apply Eq.
+ * (convergence_criterion) with alpha = 2 and add a level if it fails}.  The
+ * first quantity drives the allocation; eps is absolute, or relative to the
+ * pilot estimate |mu| when `relative` is nonzero (frozen after the pilot).
+ * Returns MLMC_DK_OK, MLMC_DK_NOT_CONVERGED (L_max reached) or an error. */
+int mlmc_dk_estimate(mlmc_dk_ctx* ctx, double eps, int32_t relative, uint64_t seed,
+                     mlmc_dk_result* out);
+
+/* Host-only planning step of Algorithm 1 for levels 0..L: from per-level
+ * sample counts n[l], sums s1[l] = sum dP and s2[l] = sum dP^2 and costs
+ * cost[l], compute target[l] by Eq. (opt_M_ell) (never below n[l]) and
+ * *converged by Eq. (convergence_criterion) with alpha = 2.  Needs n[l] >= 2. */
+int mlmc_dk_plan(int32_t L, const int64_t* n, const double* s1, const double* s2,
+                 const double* cost, double eps, int64_t* target, int32_t* converged);
+
+/* Host-only discrete mean field: the noise-free scheme with mesh h and step
+ * tau iterated M times from rho0 (n x n, n a power of two), by FFT
+ * diagonalisation in FP64.  out may alias rho0. */
+int mlmc_dk_mean_field_host(int32_t n, double h, double tau, int64_t M, const double* rho0, double* out);
+
+/* Checkpoint: the per-level next sample ids (coupled and MC).  With
+ * buf == NULL, *len receives the size needed.  Results stay a pure function
+ * of (seed, level, stream, sample id), so a restored context continues the
+ * same sample sequence bit for bit. */
+int mlmc_dk_save_state(const mlmc_dk_ctx* ctx, void* buf, size_t* len);
+int mlmc_dk_load_state(mlmc_dk_ctx* ctx, const void* buf, size_t len);
+
+/* The standard normals Z of fine step m of sample `sample` on an n x n grid
+ * (n even), exactly as the level kernel generates them in registers (see the
+ * counter layout above; Definition 2.1 asks for independent increments per
+ * cell and component).  z_dev: NULL or device float[n*n][2]; raw_dev: NULL or
+ * device uint32[n*n/2][4], the Philox4x32-10 words of each cell pair.  Both
+ * 16-byte aligned.  Asynchronous on cuda_stream.  Needs no context. */
+int mlmc_dk_noise_dev(uint64_t seed, int32_t level, int32_t stream_tag, int64_t sample, int32_t m, int32_t n,
+                      float* z_dev, uint32_t* raw_dev, void* cuda_stream);
+
+/* Number of quantities (n_obs, or n_obs(n_obs+1)/2 with products). */
+int32_t mlmc_dk_num_quantities(const mlmc_dk_ctx* ctx);
+
+/* Library version string (static). */
+const char* mlmc_dk_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MLMC_DK_H */

@@ -1,0 +1,66 @@
+// Device building blocks of the coupled Dean--Kawasaki step (sm_103a).
+//
+// Noise source: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) evaluated in
+// registers, mapped to standard normals by Box--Muller.  The paper (Definition
+// 2.1) only asks for independent Brownian increments per cell, component and
+// step; the counter layout that makes sample i of level l a pure function of
+// (seed, l, stream, i) is documented in include/mlmc_dk.h.
+#pragma once
+#include <cstdint>
+
+namespace dk {
+
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
+constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
+constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
+
+// Ten rounds: multiply words 0 and 2 by the round multipliers, xor the high
+// halves with the opposite words and the round key, swap; the key advances by
+// the Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += kPhiloxW0;
+            k1 += kPhiloxW1;
+        }
+        const uint32_t hi0 = __umulhi(kPhiloxM0, c.x), lo0 = kPhiloxM0 * c.x;
+        const uint32_t hi1 = __umulhi(kPhiloxM1, c.z), lo1 = kPhiloxM1 * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Box--Muller: u = (a+1) 2^-32 in (0,1], theta = 2 pi (b + 1/2) 2^-32.
+// theta is evaluated as pi ((int)b + 1/2) 2^-31, which differs from it by a
+// multiple of 2 pi, so that the hardware sine/cosine see |x| <= pi.
+__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float& z1, float& z2) {
+    const float u = fmaf(static_cast<float>(a), 2.3283064365386963e-10f, 2.3283064365386963e-10f);
+    const float radius = sqrt_approx(-1.3862943611198906f * __log2f(u));   // sqrt(-2 ln u)
+    const float t = (static_cast<float>(static_cast<int32_t>(b)) + 0.5f) * 4.656612873077393e-10f;
+    float s, c;
+    __sincosf(3.14159265358979f * t, &s, &c);
+    z1 = radius * c;
+    z2 = radius * s;
+}
+
+// Noise transfer G = rint(g sqrt(max(q,0)) z) in fixed-point units.
+__device__ __forceinline__ float noise_amp(int32_t q, float g) {
+    return g * sqrt_approx(__int2float_rn(max(q, 0)));
+}
+
+// Diffusion flux across one edge: round(a * (q_far - q_near)) with a given as
+// A = round(a 2^32); computed identically by both cells of the edge.
+__device__ __forceinline__ int32_t edge_flux(int32_t A, int32_t d) {
+    const long long p = static_cast<long long>(A) * static_cast<long long>(d) + 0x80000000LL;
+    return static_cast<int32_t>(p >> 32);
+}
+
+}  // namespace dk

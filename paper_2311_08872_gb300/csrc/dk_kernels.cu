@@ -1,0 +1,685 @@
+// Fused coupled fine/coarse Dean--Kawasaki sample kernel for sm_103a.
+//
+// One launch runs `count` independent samples of one level (Section 3.2: the
+// fine path on G_{h_l} and, for l >= 1, the Right-Most NN coupled coarse path
+// on G_{h_{l-1}}), each for M fine steps of Eq. (FullyDiscreteDK) with
+// b0 = 0, b1 = 1 (Section 7.2), and reduces every sample on the fly to the
+// observables (rho^T, I_h phi_k)_h, the quantities P = N (Y_j - Ybar_j)(Y_k -
+// Ybar_k) of Eq. (eqn_MLMCLevels) and the FP64 moment sums that the estimator
+// of Eq. (MLMCEstimator) and the allocation of Eq. (opt_M_ell) need.
+//
+// Work decomposition.  A sample's fine grid is cut into bands of FR = 2R fine
+// rows; a band is held by LPB <= 32 consecutive lanes of one warp, each lane
+// owning an FR x FC block (FC = 2C) of fine cells, i.e. an R x C block of the
+// coarse grid, so the coupled coarse increment (the sum over the 2x2 fine
+// cells to the right of each coarse point and over the 4 fine steps of one
+// coarse step) is accumulated in the lane's registers.  The whole state lives
+// in registers for the whole run.  Left/right neighbours come from the
+// adjacent lanes by warp shuffles (the periodic wrap is the shuffle's segment
+// wrap).  Up/down neighbours come
+//   * by shuffles too when the whole sample fits one warp (n <= 32), so those
+//     samples run without any barrier or shared memory, or
+//   * through shared memory (double-buffered band edge rows, one barrier per
+//     fine step) when the sample spans several warps; grids that need more
+//     registers than one SM has span a thread-block cluster and read the
+//     neighbouring CTA's edge rows through distributed shared memory.
+//
+// Arithmetic.  The state is 32-bit fixed point q = rho 2^S.  Each fine step
+// computes, per cell, the noise transfers G_r = rint(c 2^S sqrt(rho^+) Z_r)
+// (c = N^-1/2 sqrt(tau) / (2 h^2)) and, per edge, the diffusion flux
+// rint(tau/(2h^2) (q_far - q_near)); the new state adds these integers
+// exactly, so sum_x q is invariant bit for bit (the divergence form of the
+// scheme) and every rounding error enters in divergence form.  Observables
+// and moments are accumulated in FP64.
+#include <cooperative_groups.h>
+
+#include "dk_device.cuh"
+#include "dk_kernels.h"
+
+namespace cg = cooperative_groups;
+
+namespace dk {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kRedW = 2 * kMaxObs + 2;     // reduced values per sample
+constexpr int kMaxStride = 2 + kNSum * 10;  // largest slot stride (4 obs with products)
+
+template <int NF_, int C_, int R_, int CL_, bool COUPLED_>
+struct Shape {
+    static constexpr int NF = NF_, C = C_, R = R_, CL = CL_;
+    static constexpr bool COUPLED = COUPLED_;
+    static constexpr int NC = NF / 2;
+    static constexpr int FR = 2 * R, FC = 2 * C;
+    static constexpr int LPB = NC / C;            // lanes per band
+    static constexpr int NB = NC / R;             // bands per sample
+    static constexpr int LPS = LPB * NB;          // lanes per sample
+    static constexpr bool WARP = LPS <= 32;       // sample resident in one warp
+    static constexpr int SPW = WARP ? 32 / LPS : 1;
+    static constexpr int THREADS = WARP ? 128 : LPS / CL;
+    static constexpr int BPC = WARP ? 1 : NB / CL;   // bands per CTA
+    static constexpr int SLOTS_PER_CTA = WARP ? (THREADS / 32) * SPW : 1;
+    static_assert(LPB <= 32 && (LPB & (LPB - 1)) == 0, "a band must be a power-of-two warp segment");
+    static_assert(NC % C == 0 && NC % R == 0, "lane blocks must tile the coarse grid");
+    static_assert(WARP || (THREADS % 32 == 0 && THREADS <= 1024 && NB % CL == 0), "bad CTA shape");
+    static_assert(WARP || CL == 1 || (LPS / CL) % LPB == 0, "bands may not straddle CTAs");
+    static constexpr size_t fixed_smem() {
+        return WARP ? 0
+                    : sizeof(int2) * 2 * 2 * BPC * NF + (COUPLED ? sizeof(int2) * 2 * BPC * NC : 0) +
+                          sizeof(double) * (THREADS / 32) * kRedW;
+    }
+};
+
+template <int N>
+__device__ __forceinline__ void load_row(int32_t (&dst)[N], const int32_t* src) {
+    if constexpr (N == 1) {
+        dst[0] = __ldg(src);
+    } else if constexpr (N == 2) {
+        const int2 v = __ldg(reinterpret_cast<const int2*>(src));
+        dst[0] = v.x; dst[1] = v.y;
+    } else {
+        static_assert(N % 4 == 0, "");
+#pragma unroll
+        for (int i = 0; i < N; i += 4) {
+            const int4 v = __ldg(reinterpret_cast<const int4*>(src + i));
+            dst[i] = v.x; dst[i + 1] = v.y; dst[i + 2] = v.z; dst[i + 3] = v.w;
+        }
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void load_row_f(float (&dst)[N], const float* src) {
+    if constexpr (N == 1) {
+        dst[0] = __ldg(src);
+    } else if constexpr (N == 2) {
+        const float2 v = __ldg(reinterpret_cast<const float2*>(src));
+        dst[0] = v.x; dst[1] = v.y;
+    } else {
+#pragma unroll
+        for (int i = 0; i < N; i += 4) {
+            const float4 v = __ldg(reinterpret_cast<const float4*>(src + i));
+            dst[i] = v.x; dst[i + 1] = v.y; dst[i + 2] = v.z; dst[i + 3] = v.w;
+        }
+    }
+}
+
+// Store / load N consecutive (q, G1) pairs of an edge row to / from shared memory.
+template <int N>
+__device__ __forceinline__ void put_edge(int2* dst, const int32_t (&qv)[N], const int32_t (&gv)[N]) {
+    if constexpr (N % 2 == 0) {
+#pragma unroll
+        for (int i = 0; i < N; i += 2)
+            *reinterpret_cast<int4*>(dst + i) = make_int4(qv[i], gv[i], qv[i + 1], gv[i + 1]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < N; ++i) dst[i] = make_int2(qv[i], gv[i]);
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void get_edge(const int2* src, int32_t (&qv)[N], int32_t (&gv)[N]) {
+    if constexpr (N % 2 == 0) {
+#pragma unroll
+        for (int i = 0; i < N; i += 2) {
+            const int4 v = *reinterpret_cast<const int4*>(src + i);
+            qv[i] = v.x; gv[i] = v.y; qv[i + 1] = v.z; gv[i + 1] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            const int2 v = src[i];
+            qv[i] = v.x; gv[i] = v.y;
+        }
+    }
+}
+
+template <class S>
+__device__ __forceinline__ void block_or_cluster_sync() {
+    if constexpr (S::CL > 1) {
+        cg::this_cluster().sync();
+    } else {
+        __syncthreads();
+    }
+}
+
+template <class S, class T>
+__device__ __forceinline__ const T* peer(const T* local, int rank) {
+    if constexpr (S::CL > 1) {
+        return cg::this_cluster().map_shared_rank(const_cast<T*>(local), rank);
+    } else {
+        return local;
+    }
+}
+
+// Update of an RR x CC block of cells given its halo: explicit Euler--Maruyama
+// step in flux form.  up/dn are the rows above/below the block, lf/rt the
+// columns left/right; G1/G2 the noise transfers (component 1 along rows).
+template <int RR, int CC>
+__device__ __forceinline__ void flux_update(int32_t (&q)[RR][CC], const int32_t (&G1)[RR][CC],
+                                            const int32_t (&G2)[RR][CC], const int32_t (&qU)[CC],
+                                            const int32_t (&gU)[CC], const int32_t (&qD)[CC],
+                                            const int32_t (&gD)[CC], const int32_t (&qL)[RR],
+                                            const int32_t (&gL)[RR], const int32_t (&qR)[RR],
+                                            const int32_t (&gR)[RR], int32_t A) {
+    // vertical edge fluxes V[r][c]: across the edge between rows r-1 and r (r = 0..RR)
+    int32_t V[RR + 1][CC];
+#pragma unroll
+    for (int c = 0; c < CC; ++c) {
+        V[0][c] = edge_flux(A, q[0][c] - qU[c]);
+#pragma unroll
+        for (int r = 1; r < RR; ++r) V[r][c] = edge_flux(A, q[r][c] - q[r - 1][c]);
+        V[RR][c] = edge_flux(A, qD[c] - q[RR - 1][c]);
+    }
+    int32_t H[RR][CC + 1];
+#pragma unroll
+    for (int r = 0; r < RR; ++r) {
+        H[r][0] = edge_flux(A, q[r][0] - qL[r]);
+#pragma unroll
+        for (int c = 1; c < CC; ++c) H[r][c] = edge_flux(A, q[r][c] - q[r][c - 1]);
+        H[r][CC] = edge_flux(A, qR[r] - q[r][CC - 1]);
+    }
+#pragma unroll
+    for (int r = 0; r < RR; ++r) {
+#pragma unroll
+        for (int c = 0; c < CC; ++c) {
+            const int32_t g1d = (r + 1 < RR) ? G1[r + 1][c] : gD[c];
+            const int32_t g1u = (r > 0) ? G1[r - 1][c] : gU[c];
+            const int32_t g2r = (c + 1 < CC) ? G2[r][c + 1] : gR[r];
+            const int32_t g2l = (c > 0) ? G2[r][c - 1] : gL[r];
+            q[r][c] += (V[r + 1][c] - V[r][c]) + (H[r][c + 1] - H[r][c]) + (g1d - g1u) + (g2r - g2l);
+        }
+    }
+}
+
+template <class S>
+__global__ void __launch_bounds__(S::THREADS) level_kernel(const KArgs a) {
+    constexpr int NF = S::NF, NC = S::NC, FR = S::FR, FC = S::FC, R = S::R, C = S::C;
+    constexpr int LPB = S::LPB, LPS = S::LPS, CL = S::CL, BPC = S::BPC;
+    constexpr bool CPL = S::COUPLED;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int lib = lane % LPB;   // lane within its band
+    int band, bl = 0, rank = 0, slot_local;
+    long long slot, n_slots, base_slot;
+    if constexpr (S::WARP) {
+        band = (lane % LPS) / LPB;
+        slot_local = (tid >> 5) * S::SPW + lane / LPS;
+        slot = (long long)blockIdx.x * S::SLOTS_PER_CTA + slot_local;
+        n_slots = (long long)gridDim.x * S::SLOTS_PER_CTA;
+        base_slot = (long long)blockIdx.x * S::SLOTS_PER_CTA + (tid >> 5) * S::SPW;
+    } else {
+        if constexpr (CL > 1) rank = (int)cg::this_cluster().block_rank();
+        bl = tid / LPB;
+        band = rank * BPC + bl;
+        slot_local = 0;
+        slot = blockIdx.x / CL;
+        n_slots = gridDim.x / CL;
+        base_slot = slot;
+    }
+    const int row0 = band * FR, col0 = lib * FC;     // fine block origin
+    const int crow0 = band * R, ccol0 = lib * C;      // coarse block origin
+    const int left = (lib + LPB - 1) % LPB, right = (lib + 1) % LPB;
+    const int up_lane = ((lane % LPS) + LPS - LPB) % LPS, dn_lane = ((lane % LPS) + LPB) % LPS;
+
+    // shared memory: [fine edge rows][coarse edge rows][reduction][slot accumulators]
+    unsigned char* sp = smem_raw;
+    int2* fx = nullptr;
+    int2* cx = nullptr;
+    double* red = nullptr;
+    if constexpr (!S::WARP) {
+        fx = reinterpret_cast<int2*>(sp);
+        sp += sizeof(int2) * 2 * 2 * BPC * NF;
+        if constexpr (CPL) {
+            cx = reinterpret_cast<int2*>(sp);
+            sp += sizeof(int2) * 2 * BPC * NC;
+        }
+        red = reinterpret_cast<double*>(sp);
+        sp += sizeof(double) * (S::THREADS / 32) * kRedW;
+    }
+    double* acc = reinterpret_cast<double*>(sp);
+    for (int i = tid; i < S::SLOTS_PER_CTA * a.slot_stride; i += S::THREADS) acc[i] = 0.0;
+    __syncthreads();
+
+    const long long iters = a.count > base_slot ? (a.count - base_slot + n_slots - 1) / n_slots : 0;
+    unsigned bad = 0;
+
+    for (long long it = 0; it < iters; ++it) {
+        const long long idx = slot + it * n_slots;
+        const bool active = idx < a.count;
+        const long long sid = a.first + (active ? idx : 0);
+        const uint32_t c2 = static_cast<uint32_t>(sid);
+        const uint32_t c3 = a.tag | ((static_cast<uint32_t>(static_cast<unsigned long long>(sid) >> 32) & 0xffffu) << 16);
+
+        int32_t q[FR][FC];
+#pragma unroll
+        for (int r = 0; r < FR; ++r) load_row<FC>(q[r], a.q0f + (size_t)(row0 + r) * NF + col0);
+        int32_t qc[R][C];
+        float zt[R][C][2];
+        if constexpr (CPL) {
+#pragma unroll
+            for (int i = 0; i < R; ++i) load_row<C>(qc[i], a.q0c + (size_t)(crow0 + i) * NC + ccol0);
+#pragma unroll
+            for (int i = 0; i < R; ++i)
+#pragma unroll
+                for (int j = 0; j < C; ++j) zt[i][j][0] = zt[i][j][1] = 0.f;
+        }
+
+        for (int m = 0; m < a.M; ++m) {
+            // ---- noise: Philox4x32-10 per horizontal cell pair, Box--Muller, transfers
+            int32_t G1[FR][FC], G2[FR][FC];
+#pragma unroll
+            for (int r = 0; r < FR; ++r) {
+#pragma unroll
+                for (int pc = 0; pc < C; ++pc) {
+                    const uint32_t p = static_cast<uint32_t>(((row0 + r) * NF + col0 + 2 * pc) >> 1);
+                    const uint4 x = philox10(make_uint4(p, static_cast<uint32_t>(m), c2, c3), a.key0, a.key1);
+                    float z1a, z2a, z1b, z2b;
+                    box_muller(x.x, x.y, z1a, z2a);
+                    box_muller(x.z, x.w, z1b, z2b);
+                    const float sa = noise_amp(q[r][2 * pc], a.gf);
+                    const float sb = noise_amp(q[r][2 * pc + 1], a.gf);
+                    G1[r][2 * pc] = __float2int_rn(sa * z1a);
+                    G2[r][2 * pc] = __float2int_rn(sa * z2a);
+                    G1[r][2 * pc + 1] = __float2int_rn(sb * z1b);
+                    G2[r][2 * pc + 1] = __float2int_rn(sb * z2b);
+                    if constexpr (CPL) {
+                        zt[r >> 1][pc][0] += z1a + z1b;
+                        zt[r >> 1][pc][1] += z2a + z2b;
+                    }
+                }
+            }
+            const bool cstep = CPL && ((m & 3) == 3);
+            int32_t Gc1[R][C], Gc2[R][C];
+            if constexpr (CPL) {
+                if (cstep) {
+#pragma unroll
+                    for (int i = 0; i < R; ++i)
+#pragma unroll
+                        for (int j = 0; j < C; ++j) {
+                            const float s = noise_amp(qc[i][j], a.gc);
+                            Gc1[i][j] = __float2int_rn(s * zt[i][j][0]);
+                            Gc2[i][j] = __float2int_rn(s * zt[i][j][1]);
+                            zt[i][j][0] = zt[i][j][1] = 0.f;
+                        }
+                }
+            }
+
+            // ---- horizontal halo by shuffles within the band segment
+            int32_t qL[FR], gL[FR], qR[FR], gR[FR];
+#pragma unroll
+            for (int r = 0; r < FR; ++r) {
+                qL[r] = __shfl_sync(kFull, q[r][FC - 1], left, LPB);
+                gL[r] = __shfl_sync(kFull, G2[r][FC - 1], left, LPB);
+                qR[r] = __shfl_sync(kFull, q[r][0], right, LPB);
+                gR[r] = __shfl_sync(kFull, G2[r][0], right, LPB);
+            }
+            int32_t cqL[R], cgL[R], cqR[R], cgR[R];
+            if constexpr (CPL) {
+                if (cstep) {
+#pragma unroll
+                    for (int i = 0; i < R; ++i) {
+                        cqL[i] = __shfl_sync(kFull, qc[i][C - 1], left, LPB);
+                        cgL[i] = __shfl_sync(kFull, Gc2[i][C - 1], left, LPB);
+                        cqR[i] = __shfl_sync(kFull, qc[i][0], right, LPB);
+                        cgR[i] = __shfl_sync(kFull, Gc2[i][0], right, LPB);
+                    }
+                }
+            }
+
+            // ---- vertical halo
+            int32_t qU[FC], gU[FC], qD[FC], gD[FC];
+            int32_t cqU[C], cgU[C], cqD[C], cgD[C];
+            if constexpr (S::WARP) {
+#pragma unroll
+                for (int c = 0; c < FC; ++c) {
+                    qU[c] = __shfl_sync(kFull, q[FR - 1][c], up_lane, LPS);
+                    gU[c] = __shfl_sync(kFull, G1[FR - 1][c], up_lane, LPS);
+                    qD[c] = __shfl_sync(kFull, q[0][c], dn_lane, LPS);
+                    gD[c] = __shfl_sync(kFull, G1[0][c], dn_lane, LPS);
+                }
+                if constexpr (CPL) {
+                    if (cstep) {
+#pragma unroll
+                        for (int j = 0; j < C; ++j) {
+                            cqU[j] = __shfl_sync(kFull, qc[R - 1][j], up_lane, LPS);
+                            cgU[j] = __shfl_sync(kFull, Gc1[R - 1][j], up_lane, LPS);
+                            cqD[j] = __shfl_sync(kFull, qc[0][j], dn_lane, LPS);
+                            cgD[j] = __shfl_sync(kFull, Gc1[0][j], dn_lane, LPS);
+                        }
+                    }
+                }
+            } else {
+                const int par = m & 1;
+                int2* const ftop = fx + ((par * 2 + 0) * BPC) * NF;
+                int2* const fbot = fx + ((par * 2 + 1) * BPC) * NF;
+                put_edge<FC>(ftop + bl * NF + col0, q[0], G1[0]);
+                put_edge<FC>(fbot + bl * NF + col0, q[FR - 1], G1[FR - 1]);
+                int2* const ctop = cx;
+                int2* const cbot = cx + BPC * NC;
+                if constexpr (CPL) {
+                    if (cstep) {
+                        put_edge<C>(ctop + bl * NC + ccol0, qc[0], Gc1[0]);
+                        put_edge<C>(cbot + bl * NC + ccol0, qc[R - 1], Gc1[R - 1]);
+                    }
+                }
+                block_or_cluster_sync<S>();
+                const int2* above = (bl > 0) ? fbot + (bl - 1) * NF + col0
+                                             : peer<S>(fbot + (BPC - 1) * NF + col0, (rank + CL - 1) % CL);
+                const int2* below = (bl + 1 < BPC) ? ftop + (bl + 1) * NF + col0
+                                                   : peer<S>(ftop + col0, (rank + 1) % CL);
+                get_edge<FC>(above, qU, gU);
+                get_edge<FC>(below, qD, gD);
+                if constexpr (CPL) {
+                    if (cstep) {
+                        const int2* cab = (bl > 0) ? cbot + (bl - 1) * NC + ccol0
+                                                   : peer<S>(cbot + (BPC - 1) * NC + ccol0, (rank + CL - 1) % CL);
+                        const int2* cbe = (bl + 1 < BPC) ? ctop + (bl + 1) * NC + ccol0
+                                                         : peer<S>(ctop + ccol0, (rank + 1) % CL);
+                        get_edge<C>(cab, cqU, cgU);
+                        get_edge<C>(cbe, cqD, cgD);
+                    }
+                }
+            }
+
+            // ---- updates
+            flux_update<FR, FC>(q, G1, G2, qU, gU, qD, gD, qL, gL, qR, gR, a.Af);
+            if constexpr (CPL) {
+                if (cstep) {
+                    flux_update<R, C>(qc, Gc1, Gc2, cqU, cgU, cqD, cgD, cqL, cgL, cqR, cgR, a.Ac);
+#pragma unroll
+                    for (int i = 0; i < R; ++i)
+#pragma unroll
+                        for (int j = 0; j < C; ++j) bad |= (static_cast<uint32_t>(qc[i][j]) + 0x40000000u) >> 31;
+                }
+            }
+            if ((m & 3) == 3 || m + 1 == a.M) {
+#pragma unroll
+                for (int r = 0; r < FR; ++r)
+#pragma unroll
+                    for (int c = 0; c < FC; ++c) bad |= (static_cast<uint32_t>(q[r][c]) + 0x40000000u) >> 31;
+            }
+        }
+
+        // ---- observables: fluctuation sums against the fixed-point mean field, mass
+        double v[kRedW];
+        {
+            long long mf = 0;
+#pragma unroll
+            for (int r = 0; r < FR; ++r)
+#pragma unroll
+                for (int c = 0; c < FC; ++c) mf += q[r][c];
+            v[2 * kMaxObs] = static_cast<double>(mf);
+            long long mc = 0;
+            if constexpr (CPL) {
+#pragma unroll
+                for (int i = 0; i < R; ++i)
+#pragma unroll
+                    for (int j = 0; j < C; ++j) mc += qc[i][j];
+            }
+            v[2 * kMaxObs + 1] = static_cast<double>(mc);
+#pragma unroll
+            for (int k = 0; k < kMaxObs; ++k) {
+                float sf = 0.f, sc = 0.f;
+                if (k < a.n_obs) {
+#pragma unroll
+                    for (int r = 0; r < FR; ++r) {
+                        int32_t qb[FC];
+                        float ph[FC];
+                        load_row<FC>(qb, a.qbf + (size_t)(row0 + r) * NF + col0);
+                        load_row_f<FC>(ph, a.phif + (size_t)k * NF * NF + (size_t)(row0 + r) * NF + col0);
+#pragma unroll
+                        for (int c = 0; c < FC; ++c) sf = fmaf(__int2float_rn(q[r][c] - qb[c]), ph[c], sf);
+                    }
+                    if constexpr (CPL) {
+#pragma unroll
+                        for (int i = 0; i < R; ++i) {
+                            int32_t qb[C];
+                            float ph[C];
+                            load_row<C>(qb, a.qbc + (size_t)(crow0 + i) * NC + ccol0);
+                            load_row_f<C>(ph, a.phic + (size_t)k * NC * NC + (size_t)(crow0 + i) * NC + ccol0);
+#pragma unroll
+                            for (int j = 0; j < C; ++j) sc = fmaf(__int2float_rn(qc[i][j] - qb[j]), ph[j], sc);
+                        }
+                    }
+                }
+                v[k] = static_cast<double>(sf);
+                v[kMaxObs + k] = static_cast<double>(sc);
+            }
+        }
+        bool leader;
+        if constexpr (S::WARP) {
+#pragma unroll
+            for (int off = LPS / 2; off >= 1; off >>= 1)
+#pragma unroll
+                for (int i = 0; i < kRedW; ++i) v[i] += __shfl_xor_sync(kFull, v[i], off, LPS);
+            leader = (lane % LPS) == 0;
+        } else {
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1)
+#pragma unroll
+                for (int i = 0; i < kRedW; ++i) v[i] += __shfl_xor_sync(kFull, v[i], off);
+            if (lane == 0)
+#pragma unroll
+                for (int i = 0; i < kRedW; ++i) red[(tid >> 5) * kRedW + i] = v[i];
+            __syncthreads();
+            if (tid == 0) {
+                for (int w = 1; w < S::THREADS / 32; ++w)
+#pragma unroll
+                    for (int i = 0; i < kRedW; ++i) v[i] += red[w * kRedW + i];
+#pragma unroll
+                for (int i = 0; i < kRedW; ++i) red[i] = v[i];
+            }
+            if constexpr (CL > 1) {
+                cg::this_cluster().sync();
+                if (rank == 0 && tid == 0) {
+                    for (int rr = 1; rr < CL; ++rr) {
+                        const double* o = peer<S>(red, rr);
+#pragma unroll
+                        for (int i = 0; i < kRedW; ++i) v[i] += o[i];
+                    }
+                }
+            }
+            leader = (tid == 0) && (rank == 0);
+        }
+
+        // ---- FP64 quantities and moment sums (one lane per sample)
+        if (leader && active) {
+            double Df[kMaxObs], Dc[kMaxObs];
+#pragma unroll
+            for (int k = 0; k < kMaxObs; ++k) {
+                Df[k] = a.dscale_f * v[k] + a.delta_f[k];
+                Dc[k] = CPL ? a.dscale_c * v[kMaxObs + k] + a.delta_c[k] : 0.0;
+            }
+            double* A = acc + slot_local * a.slot_stride;
+            A[0] += 1.0;
+            double merr = fabs(v[2 * kMaxObs] - static_cast<double>(a.mass0_f)) * a.dscale_f;
+            if (CPL) merr = fmax(merr, fabs(v[2 * kMaxObs + 1] - static_cast<double>(a.mass0_c)) * a.dscale_c);
+            A[1] = fmax(A[1], merr);
+            int qi = 0;
+            for (int j = 0; j < a.n_obs; ++j) {
+                const int kend = a.products ? a.n_obs : j + 1;
+                for (int k = j; k < kend; ++k, ++qi) {
+                    const double pf = a.N * Df[j] * Df[k];
+                    const double pc = CPL ? a.N * Dc[j] * Dc[k] : 0.0;
+                    const double dp = pf - pc, dp2 = dp * dp;
+                    double* B = A + 2 + kNSum * qi;
+                    B[0] += dp; B[1] += dp2; B[2] += dp2 * dp; B[3] += dp2 * dp2;
+                    B[4] += pf; B[5] += pf * pf; B[6] += pc; B[7] += pc * pc;
+                    B[8] += Df[j]; B[9] += Df[j] * Df[j]; B[10] += Dc[j]; B[11] += Dc[j] * Dc[j];
+                }
+            }
+            if (a.samples) {
+                double* o = a.samples + idx * (2 * a.n_obs + 2);
+                for (int k = 0; k < a.n_obs; ++k) {
+                    o[k] = Df[k];
+                    o[a.n_obs + k] = Dc[k];
+                }
+                o[2 * a.n_obs] = v[2 * kMaxObs] * a.dscale_f;
+                o[2 * a.n_obs + 1] = CPL ? v[2 * kMaxObs + 1] * a.dscale_c : 0.0;
+            }
+        }
+    }
+    if (bad) atomicOr(a.err, kErrRange);
+
+    // ---- per-slot partial sums to global scratch, entry-major [stride][n_slots]
+    __syncthreads();
+    if (S::WARP || rank == 0) {
+        const long long slot0 = S::WARP ? (long long)blockIdx.x * S::SLOTS_PER_CTA : slot;
+        for (int i = tid; i < S::SLOTS_PER_CTA * a.slot_stride; i += S::THREADS) {
+            const int s = i / a.slot_stride, e = i % a.slot_stride;
+            a.partials[(size_t)e * n_slots + slot0 + s] = acc[i];
+        }
+    }
+    if constexpr (CL > 1) cg::this_cluster().sync();   // peers may still read our shared memory
+}
+
+// Fixed-order reduction over slots: one block per entry.
+__global__ void __launch_bounds__(256) reduce_kernel(const double* part, int n_slots, double* out) {
+    const int e = blockIdx.x;
+    const bool is_max = (e == 1);
+    const double* row = part + (size_t)e * n_slots;
+    double v = 0.0;
+    for (int s = threadIdx.x; s < n_slots; s += 256) v = is_max ? fmax(v, row[s]) : v + row[s];
+    __shared__ double sh[256];
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            const double o = sh[threadIdx.x + w];
+            sh[threadIdx.x] = is_max ? fmax(sh[threadIdx.x], o) : sh[threadIdx.x] + o;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[e] = sh[0];
+}
+
+// Normals of one fine step, written out (the level kernel keeps them in
+// registers); same device functions as the level kernel.
+__global__ void noise_kernel(int n, uint32_t m, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1,
+                             float* z, uint32_t* raw) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n * n / 2) return;
+    const uint4 x = philox10(make_uint4(static_cast<uint32_t>(p), m, c2, c3), k0, k1);
+    if (raw) reinterpret_cast<uint4*>(raw)[p] = x;
+    if (z) {
+        float a1, a2, b1, b2;
+        box_muller(x.x, x.y, a1, a2);
+        box_muller(x.z, x.w, b1, b2);
+        reinterpret_cast<float4*>(z)[p] = make_float4(a1, a2, b1, b2);
+    }
+}
+
+cudaError_t launch_noise(int n, uint32_t m, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1, float* z,
+                         uint32_t* raw, cudaStream_t st) {
+    const int pairs = n * n / 2;
+    noise_kernel<<<(pairs + 255) / 256, 256, 0, st>>>(n, m, c2, c3, k0, k1, z, raw);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ dispatch
+template <class S>
+struct Kern {
+    static size_t smem_bytes(int stride) { return S::fixed_smem() + sizeof(double) * S::SLOTS_PER_CTA * stride; }
+
+    static cudaError_t info(int stride, VariantInfo* vi) {
+        auto fn = level_kernel<S>;
+        const size_t smax = smem_bytes(kMaxStride);
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
+        if (e != cudaSuccess) return e;
+        if (S::CL > 1) {
+            e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            if (e != cudaSuccess) return e;
+        }
+        int dev = 0, sms = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        vi->supported = 1;
+        vi->threads = S::THREADS;
+        vi->cluster = S::CL;
+        vi->slots_per_cta = S::SLOTS_PER_CTA;
+        vi->smem = smem_bytes(stride);
+        if (S::CL == 1) {
+            int nb = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, S::THREADS, vi->smem);
+            if (e != cudaSuccess) return e;
+            vi->max_ctas = nb * sms;
+        } else {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(S::CL * sms);
+            cfg.blockDim = dim3(S::THREADS);
+            cfg.dynamicSmemBytes = vi->smem;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = S::CL;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            int ncl = 0;
+            e = cudaOccupancyMaxActiveClusters(&ncl, fn, &cfg);
+            if (e != cudaSuccess) return e;
+            vi->max_ctas = ncl * S::CL;
+        }
+        return vi->max_ctas > 0 ? cudaSuccess : cudaErrorInvalidConfiguration;
+    }
+
+    static cudaError_t launch(const KArgs& a, int n_ctas, cudaStream_t st) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(n_ctas);
+        cfg.blockDim = dim3(S::THREADS);
+        cfg.dynamicSmemBytes = smem_bytes(a.slot_stride);
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        if (S::CL > 1) {
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = S::CL;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+        }
+        return cudaLaunchKernelEx(&cfg, level_kernel<S>, a);
+    }
+};
+
+// Variant per fine size n: (C, R, cluster).  See the header comment for the
+// geometry; every entry keeps the whole state in registers.
+#define DK_VARIANTS(X)            \
+    X(4, 1, 1, 1)                 \
+    X(8, 1, 1, 1)                 \
+    X(16, 1, 2, 1)                \
+    X(32, 2, 2, 1)                \
+    X(64, 2, 2, 1)                \
+    X(128, 2, 2, 2)               \
+    X(256, 4, 2, 8)
+
+cudaError_t variant_info(int n, bool coupled, int stride, VariantInfo* out) {
+    *out = VariantInfo{};
+#define DK_INFO(NF, C, R, CL)                                                   \
+    if (n == NF) {                                                              \
+        return coupled ? Kern<Shape<NF, C, R, CL, true>>::info(stride, out)      \
+                       : Kern<Shape<NF, C, R, CL, false>>::info(stride, out);    \
+    }
+    DK_VARIANTS(DK_INFO)
+#undef DK_INFO
+    return cudaSuccess;   // supported = 0
+}
+
+cudaError_t launch_level(int n, bool coupled, const KArgs& a, int n_ctas, cudaStream_t st) {
+#define DK_LAUNCH(NF, C, R, CL)                                                 \
+    if (n == NF) {                                                              \
+        return coupled ? Kern<Shape<NF, C, R, CL, true>>::launch(a, n_ctas, st)  \
+                       : Kern<Shape<NF, C, R, CL, false>>::launch(a, n_ctas, st);\
+    }
+    DK_VARIANTS(DK_LAUNCH)
+#undef DK_LAUNCH
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_reduce(const double* partials, int n_slots, int slot_stride, double* out, cudaStream_t st) {
+    reduce_kernel<<<slot_stride, 256, 0, st>>>(partials, n_slots, out);
+    return cudaGetLastError();
+}
+
+}  // namespace dk

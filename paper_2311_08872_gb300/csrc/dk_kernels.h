@@ -1,0 +1,72 @@
+// Launch interface between the host runtime (mlmc_dk.cpp) and the CUDA
+// kernels (dk_kernels.cu).  Plain structs and device pointers only.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace dk {
+
+constexpr int kMaxObs = 4;
+constexpr int kNSum = 12;   // per-quantity sums, layout as in include/mlmc_dk.h
+
+// Everything one level launch needs (passed by value as a kernel parameter).
+struct KArgs {
+    const int32_t* q0f;     // fine initial state, fixed point, n^2
+    const int32_t* qbf;     // fine discrete mean field at T, fixed point, n^2
+    const float* phif;      // fine test functions [n_obs][n^2]
+    const int32_t* q0c;     // coarse (level l-1) tables, (n/2)^2
+    const int32_t* qbc;
+    const float* phic;
+    double* partials;       // scratch: [n_slots][slot_stride] per-slot sums
+    double* samples;        // optional per-sample output [count][2 n_obs + 2]
+    unsigned int* err;      // sticky device error bits
+    int64_t first;          // first sample id
+    int64_t count;          // number of samples
+    int32_t M;              // fine steps
+    int32_t n_obs;
+    int32_t n_quant;
+    int32_t products;
+    int32_t Af, Ac;         // diffusion multipliers round(tau/(2h^2) 2^32)
+    float gf, gc;           // noise multipliers (gc includes the 1/4 of the coupled sum)
+    uint32_t key0, key1;    // seed words
+    uint32_t tag;           // (level + 1) | stream << 8
+    int32_t slot_stride;    // 2 + kNSum * n_quant doubles
+    double N;
+    double dscale_f, dscale_c;        // h^2 2^-S: fixed-point sums -> (rho, phi)_h
+    double delta_f[kMaxObs], delta_c[kMaxObs];  // (2^-S qbar - rho-bar^T, phi)_h
+    double mscale_f, mscale_c;        // h^2 2^-S for the mass
+    long long mass0_f, mass0_c;       // sum of the initial fixed-point states
+};
+
+enum : unsigned int { kErrRange = 1u };
+
+// Static facts about the kernel variant used for a grid size.
+struct VariantInfo {
+    int supported;
+    int threads;            // threads per CTA
+    int cluster;            // CTAs per cluster (1 = no cluster)
+    int slots_per_cta;      // samples in flight per CTA (1/cluster for clusters)
+    size_t smem;            // dynamic shared memory per CTA
+    int max_ctas;           // resident CTAs on the whole GPU
+};
+
+// Query (and prepare: attributes, occupancy) the variant for fine size n;
+// supported = 0 when no variant exists for n.
+cudaError_t variant_info(int n, bool coupled, int slot_stride, VariantInfo* out);
+
+// Launch one batch; n_slots = number of sample slots actually used
+// (returned), partials must hold n_slots * slot_stride doubles.
+cudaError_t launch_level(int n, bool coupled, const KArgs& a, int n_ctas, cudaStream_t stream);
+
+// Deterministic fixed-order reduction of the per-slot partials into
+// out[slot_stride]: entry 1 is a max, all others sums.
+cudaError_t launch_reduce(const double* partials, int n_slots, int slot_stride, double* out,
+                          cudaStream_t stream);
+
+// Normals (and raw Philox words) of one fine step: z [n*n][2], raw [n*n/2][4].
+cudaError_t launch_noise(int n, uint32_t m, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1, float* z,
+                         uint32_t* raw, cudaStream_t stream);
+
+}  // namespace dk

@@ -1,0 +1,634 @@
+// Host runtime behind include/mlmc_dk.h: level hierarchy, discrete mean field,
+// fixed-point tables, kernel launches, Algorithm 1 and checkpointing.
+#include "mlmc_dk.h"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "dk_kernels.h"
+
+namespace {
+
+thread_local std::string g_init_error;
+
+struct LevelTab {
+    int n = 0, M = 0;
+    double h = 0, tau = 0;
+    int S = 24;              // fixed-point fraction bits: rho = q 2^-S
+    int32_t A = 0;           // round(tau / (2 h^2) 2^32)
+    float g = 0.f;           // N^-1/2 sqrt(tau) / (2 h^2) 2^(S/2)
+    double dscale = 0;       // h^2 2^-S
+    long long mass0 = 0;     // sum of q0
+    double ybar[MLMC_DK_MAX_OBS] = {0, 0, 0, 0};
+    double delta[MLMC_DK_MAX_OBS] = {0, 0, 0, 0};
+    int32_t* d_q0 = nullptr;
+    int32_t* d_qbar = nullptr;
+    float* d_phi = nullptr;
+    dk::VariantInfo vi_coupled{}, vi_single{};
+};
+
+}  // namespace
+
+struct mlmc_dk_ctx {
+    double length = 1, T = 0, N = 0;
+    int L_max = 0, n_obs = 1, products = 0, n_quant = 1, stride = 0, pilot = 256, L_start = 2;
+    std::vector<LevelTab> lv;
+    cudaStream_t stream = nullptr;
+    double* d_partials = nullptr;
+    size_t partials_cap = 0;   // doubles
+    double* d_sums = nullptr;
+    double* h_sums = nullptr;  // pinned
+    unsigned* d_err = nullptr;
+    unsigned* h_err = nullptr;  // pinned
+    int64_t h2d_bytes = 0;      // bytes uploaded by mlmc_dk_init
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::vector<int64_t> next_id[2];
+    std::string err;
+};
+
+namespace {
+
+int fail(mlmc_dk_ctx* ctx, int code, const std::string& msg) {
+    if (ctx) ctx->err = msg; else g_init_error = msg;
+    return code;
+}
+
+int cuda_fail(mlmc_dk_ctx* ctx, cudaError_t e, const char* what) {
+    return fail(ctx, MLMC_DK_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+// ---------------------------------------------------------------- FFT (FP64)
+// In-place iterative radix-2 complex transform of length n (a power of two);
+// sign = -1 forward, +1 inverse (unnormalised).
+void fft1(std::complex<double>* a, int n, int stride, int sign) {
+    for (int i = 1, j = 0; i < n; ++i) {
+        int bit = n >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) std::swap(a[(size_t)i * stride], a[(size_t)j * stride]);
+    }
+    for (int len = 2; len <= n; len <<= 1) {
+        const double ang = sign * 2.0 * M_PI / len;
+        for (int i = 0; i < n; i += len) {
+            for (int k = 0; k < len / 2; ++k) {
+                const std::complex<double> w(std::cos(ang * k), std::sin(ang * k));
+                std::complex<double>& x = a[(size_t)(i + k) * stride];
+                std::complex<double>& y = a[(size_t)(i + k + len / 2) * stride];
+                const std::complex<double> t = w * y;
+                y = x - t;
+                x = x + t;
+            }
+        }
+    }
+}
+
+void fft2(std::vector<std::complex<double>>& a, int n, int sign) {
+    for (int r = 0; r < n; ++r) fft1(a.data() + (size_t)r * n, n, 1, sign);
+    for (int c = 0; c < n; ++c) fft1(a.data() + c, n, n, sign);
+}
+
+// Noise-free scheme rho <- rho + tau/2 Delta_h rho iterated M times: every
+// discrete Fourier mode k is multiplied by 1 - 2 (tau/h^2)(sin^2(pi k1/n) +
+// sin^2(pi k2/n)) per step, the symbol of Delta_h (Section 7.2).
+void mean_field(int n, double h, double tau, long long M, const double* rho0, double* out) {
+    std::vector<std::complex<double>> a((size_t)n * n);
+    for (size_t i = 0; i < a.size(); ++i) a[i] = rho0[i];
+    fft2(a, n, -1);
+    const double mu = tau / (h * h);
+    std::vector<double> s2(n);
+    for (int k = 0; k < n; ++k) {
+        const double s = std::sin(M_PI * k / n);
+        s2[k] = s * s;
+    }
+    for (int k1 = 0; k1 < n; ++k1)
+        for (int k2 = 0; k2 < n; ++k2) {
+            const double g = 1.0 - 2.0 * mu * (s2[k1] + s2[k2]);
+            a[(size_t)k1 * n + k2] *= std::pow(g, (double)M);
+        }
+    fft2(a, n, +1);
+    const double inv = 1.0 / ((double)n * n);
+    for (size_t i = 0; i < a.size(); ++i) out[i] = a[i].real() * inv;
+}
+
+int quantities(int n_obs, int products) { return products ? n_obs * (n_obs + 1) / 2 : n_obs; }
+
+// Fill the kernel arguments of one batch.
+dk::KArgs make_args(mlmc_dk_ctx* c, int level, int stream_tag, bool coupled, int64_t first, int64_t count,
+                    uint64_t seed, double* samples) {
+    const LevelTab& f = c->lv[level];
+    dk::KArgs a{};
+    a.q0f = f.d_q0;
+    a.qbf = f.d_qbar;
+    a.phif = f.d_phi;
+    a.partials = c->d_partials;
+    a.samples = samples;
+    a.err = c->d_err;
+    a.first = first;
+    a.count = count;
+    a.M = f.M;
+    a.n_obs = c->n_obs;
+    a.n_quant = c->n_quant;
+    a.products = c->products;
+    a.Af = f.A;
+    a.gf = f.g;
+    a.key0 = (uint32_t)(seed & 0xffffffffu);
+    a.key1 = (uint32_t)(seed >> 32);
+    a.tag = ((uint32_t)(level + 1) & 0xffu) | (((uint32_t)stream_tag & 0xffu) << 8);
+    a.slot_stride = c->stride;
+    a.N = c->N;
+    a.dscale_f = f.dscale;
+    a.mass0_f = f.mass0;
+    for (int k = 0; k < dk::kMaxObs; ++k) a.delta_f[k] = f.delta[k];
+    if (coupled) {
+        const LevelTab& g = c->lv[level - 1];
+        a.q0c = g.d_q0;
+        a.qbc = g.d_qbar;
+        a.phic = g.d_phi;
+        a.Ac = g.A;
+        a.gc = 0.25f * g.g;   // coupled coarse normal = 1/4 x (sum of 16 fine normals)
+        a.dscale_c = g.dscale;
+        a.mass0_c = g.mass0;
+        for (int k = 0; k < dk::kMaxObs; ++k) a.delta_c[k] = g.delta[k];
+    }
+    return a;
+}
+
+// Launch one batch and reduce it into sums_dev (device, stride doubles).
+int launch_batch(mlmc_dk_ctx* c, int level, int stream_tag, int64_t first, int64_t count, uint64_t seed,
+                 double* sums_dev, double* samples_dev, cudaStream_t st) {
+    const bool coupled = (stream_tag == 0) && level > 0;
+    const dk::VariantInfo& vi = coupled ? c->lv[level].vi_coupled : c->lv[level].vi_single;
+    if (!vi.supported)
+        return fail(c, MLMC_DK_ERR_UNSUPPORTED, "no kernel variant for n = " + std::to_string(c->lv[level].n));
+    cudaError_t e;
+    if (count == 0) {
+        e = cudaMemsetAsync(sums_dev, 0, sizeof(double) * c->stride, st);
+        return e == cudaSuccess ? MLMC_DK_OK : cuda_fail(c, e, "cudaMemsetAsync");
+    }
+    const int64_t per_cluster = vi.slots_per_cta;            // slots per CTA (mode i) or per cluster
+    const int64_t want_groups = (count + per_cluster - 1) / per_cluster;
+    const int64_t max_groups = vi.max_ctas / vi.cluster;
+    const int64_t groups = std::min(want_groups, max_groups);
+    const int n_ctas = (int)(groups * vi.cluster);
+    const int n_slots = (int)(groups * per_cluster);
+    if ((size_t)n_slots * c->stride > c->partials_cap) return fail(c, MLMC_DK_ERR_INVALID, "scratch too small");
+    dk::KArgs a = make_args(c, level, stream_tag, coupled, first, count, seed, samples_dev);
+    if ((e = dk::launch_level(c->lv[level].n, coupled, a, n_ctas, st)) != cudaSuccess)
+        return cuda_fail(c, e, "level kernel launch");
+    if ((e = dk::launch_reduce(c->d_partials, n_slots, c->stride, sums_dev, st)) != cudaSuccess)
+        return cuda_fail(c, e, "reduce kernel launch");
+    return MLMC_DK_OK;
+}
+
+int check_device_error(mlmc_dk_ctx* c) {
+    cudaError_t e = cudaMemcpyAsync(c->h_err, c->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "device error word");
+    if (*c->h_err & dk::kErrRange) {
+        cudaMemsetAsync(c->d_err, 0, sizeof(unsigned), c->stream);
+        return fail(c, MLMC_DK_ERR_RANGE, "fixed-point range exceeded (|rho| too large for this level's scale)");
+    }
+    return MLMC_DK_OK;
+}
+
+void accumulate(const mlmc_dk_ctx* c, const double* s, mlmc_dk_level_sums* out, double cost_per, double wall,
+                double kernel_s, int launches) {
+    const int64_t n = (int64_t)std::llround(s[0]);
+    for (int q = 0; q < c->n_quant; ++q) {
+        const double* b = s + 2 + dk::kNSum * q;
+        mlmc_dk_level_sums& o = out[q];
+        o.n += n;
+        o.dp1 += b[0]; o.dp2 += b[1]; o.dp3 += b[2]; o.dp4 += b[3];
+        o.pf1 += b[4]; o.pf2 += b[5]; o.pc1 += b[6]; o.pc2 += b[7];
+        o.yf1 += b[8]; o.yf2 += b[9]; o.yc1 += b[10]; o.yc2 += b[11];
+        o.max_mass_err = std::max(o.max_mass_err, s[1]);
+        o.cost += cost_per * (double)n;
+        o.wall_s += wall;
+        o.kernel_s += kernel_s;
+        o.launches += launches;
+        o.d2h_bytes += (int64_t)(sizeof(double) * c->stride + sizeof(unsigned));
+    }
+}
+
+int run_host(mlmc_dk_ctx* c, int level, int stream_tag, int64_t n_samples, uint64_t seed, mlmc_dk_level_sums* sums) {
+    if (!c) return fail(nullptr, MLMC_DK_ERR_INVALID, "null context");
+    if (level < 0 || level > c->L_max) return fail(c, MLMC_DK_ERR_INVALID, "level out of range");
+    if (n_samples < 0 || !sums) return fail(c, MLMC_DK_ERR_INVALID, "bad sample count or null sums");
+    const auto t0 = std::chrono::steady_clock::now();
+    int64_t& next = c->next_id[stream_tag][level];
+    cudaError_t e = cudaEventRecord(c->ev0, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventRecord");
+    int rc = launch_batch(c, level, stream_tag, next, n_samples, seed, c->d_sums, nullptr, c->stream);
+    if (rc != MLMC_DK_OK) return rc;
+    if ((e = cudaEventRecord(c->ev1, c->stream)) != cudaSuccess) return cuda_fail(c, e, "cudaEventRecord");
+    e = cudaMemcpyAsync(c->h_sums, c->d_sums, sizeof(double) * c->stride, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "level batch");
+    float ms = 0.f;
+    if ((e = cudaEventElapsedTime(&ms, c->ev0, c->ev1)) != cudaSuccess) return cuda_fail(c, e, "cudaEventElapsedTime");
+    if ((rc = check_device_error(c)) != MLMC_DK_OK) return rc;
+    next += n_samples;
+    const double wall = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    const LevelTab& f = c->lv[level];
+    double cost = (double)f.n * f.n * f.M;
+    if (stream_tag == 0 && level > 0) cost += (double)c->lv[level - 1].n * c->lv[level - 1].n * c->lv[level - 1].M;
+    accumulate(c, c->h_sums, sums, cost, wall, 1e-3 * ms, n_samples > 0 ? 2 : 0);
+    return MLMC_DK_OK;
+}
+
+void release(mlmc_dk_ctx* c) {
+    for (auto& l : c->lv) {
+        cudaFree(l.d_q0);
+        cudaFree(l.d_qbar);
+        cudaFree(l.d_phi);
+    }
+    cudaFree(c->d_partials);
+    cudaFree(c->d_sums);
+    cudaFree(c->d_err);
+    if (c->h_sums) cudaFreeHost(c->h_sums);
+    if (c->h_err) cudaFreeHost(c->h_err);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mlmc_dk_version(void) { return "mlmc_dk 0.1 (sm_103a)"; }
+
+const char* mlmc_dk_last_error(const mlmc_dk_ctx* ctx) {
+    return ctx ? ctx->err.c_str() : g_init_error.c_str();
+}
+
+int32_t mlmc_dk_num_quantities(const mlmc_dk_ctx* ctx) { return ctx ? ctx->n_quant : 0; }
+
+int mlmc_dk_mean_field_host(int32_t n, double h, double tau, int64_t M, const double* rho0, double* out) {
+    if (!is_pow2(n) || n < 2 || h <= 0 || tau < 0 || M < 0 || !rho0 || !out)
+        return fail(nullptr, MLMC_DK_ERR_INVALID, "mean_field_host: bad arguments");
+    std::vector<double> tmp(rho0, rho0 + (size_t)n * n);
+    mean_field(n, h, tau, M, tmp.data(), out);
+    return MLMC_DK_OK;
+}
+
+int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
+    if (!out) return fail(nullptr, MLMC_DK_ERR_INVALID, "null output pointer");
+    *out = nullptr;
+    if (!cfg) return fail(nullptr, MLMC_DK_ERR_INVALID, "null config");
+    if (!is_pow2(cfg->n0) || cfg->n0 < 4 || cfg->L_max < 0 || cfg->L_max >= MLMC_DK_MAX_LEVELS ||
+        ((long long)cfg->n0 << cfg->L_max) > 1024)
+        return fail(nullptr, MLMC_DK_ERR_INVALID, "n0 must be a power of two >= 4 with n0 2^L_max <= 1024");
+    if (!(cfg->length > 0) || !(cfg->T > 0) || !(cfg->N >= 0))
+        return fail(nullptr, MLMC_DK_ERR_INVALID, "length, T must be > 0 and N >= 0");
+    if (cfg->n_obs < 1 || cfg->n_obs > MLMC_DK_MAX_OBS || !cfg->rho0 || !cfg->phi)
+        return fail(nullptr, MLMC_DK_ERR_INVALID, "n_obs must be 1..4 and rho0/phi non-null");
+    const double h0 = cfg->length / cfg->n0;
+    long long M0 = cfg->M0;
+    if (M0 <= 0) {
+        if (!(cfg->cfl_mu > 0)) return fail(nullptr, MLMC_DK_ERR_INVALID, "cfl_mu must be > 0 when M0 is not given");
+        const double x = cfg->T / (cfg->cfl_mu * h0 * h0);
+        M0 = (long long)std::ceil(x - 1e-9 * x);
+    }
+    const double tau0 = cfg->T / (double)M0;
+    if (tau0 / (h0 * h0) > 0.5 + 1e-12)
+        return fail(nullptr, MLMC_DK_ERR_INVALID,
+                    "tau/h^2 > 1/2: the noise-free scheme violates the discrete maximum principle");
+    if (M0 * (1LL << (2 * cfg->L_max)) > (1LL << 30)) return fail(nullptr, MLMC_DK_ERR_INVALID, "too many time steps");
+
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0)
+        return fail(nullptr, MLMC_DK_ERR_CUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+
+    mlmc_dk_ctx* c = new mlmc_dk_ctx();
+    c->length = cfg->length;
+    c->T = cfg->T;
+    c->N = cfg->N;
+    c->L_max = cfg->L_max;
+    c->n_obs = cfg->n_obs;
+    c->products = cfg->products ? 1 : 0;
+    c->n_quant = quantities(c->n_obs, c->products);
+    c->stride = 2 + dk::kNSum * c->n_quant;
+    c->pilot = cfg->pilot > 1 ? cfg->pilot : 256;
+    c->L_start = std::min(cfg->L_start > 0 ? cfg->L_start : 2, cfg->L_max);
+    c->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
+    c->lv.resize(cfg->L_max + 1);
+    c->next_id[0].assign(cfg->L_max + 1, 0);
+    c->next_id[1].assign(cfg->L_max + 1, 0);
+
+    size_t partials_need = 0;
+    for (int l = 0; l <= cfg->L_max; ++l) {
+        LevelTab& t = c->lv[l];
+        t.n = cfg->n0 << l;
+        t.h = h0 / (double)(1 << l);
+        t.tau = tau0 / std::pow(4.0, l);
+        t.M = (int)(M0 << (2 * l));
+        const size_t cells = (size_t)t.n * t.n;
+        const double* rho0 = cfg->rho0[l];
+        if (!rho0) { mlmc_dk_free(c); return fail(nullptr, MLMC_DK_ERR_INVALID, "null rho0 level array"); }
+        double rmax = 0;
+        for (size_t i = 0; i < cells; ++i) {
+            if (!std::isfinite(rho0[i])) { mlmc_dk_free(c); return fail(nullptr, MLMC_DK_ERR_INVALID, "non-finite rho0"); }
+            rmax = std::max(rmax, std::fabs(rho0[i]));
+        }
+        // Fixed-point scale: headroom for twice the initial range plus 12
+        // standard deviations of the per-cell fluctuation sqrt(rho/(N h^2)).
+        const double noise_sd = cfg->N > 0 ? std::sqrt(std::max(rmax, 1e-3) / (cfg->N * t.h * t.h)) : 0.0;
+        const double range = 2.0 * rmax + 1.0 + 12.0 * noise_sd;
+        int S = 30 - (int)std::ceil(std::log2(range));
+        S = std::max(16, std::min(28, S));
+        const double c_noise = cfg->N > 0 ? std::sqrt(t.tau) / (std::sqrt(cfg->N) * 2.0 * t.h * t.h) : 0.0;
+        // keep the noise multiplier g = c 2^(S/2) small enough that |G| stays far below 2^31
+        while (S > 16 && c_noise * std::pow(2.0, 0.5 * S) > 2048.0) --S;
+        if (rmax * std::ldexp(1.0, S) >= std::ldexp(1.0, 30)) {
+            mlmc_dk_free(c);
+            return fail(nullptr, MLMC_DK_ERR_INVALID, "|rho0| too large for the fixed-point range");
+        }
+        t.S = S;
+        t.A = (int32_t)std::llround(t.tau / (2.0 * t.h * t.h) * 4294967296.0);
+        t.g = (float)(c_noise * std::pow(2.0, 0.5 * S));
+        t.dscale = t.h * t.h * std::ldexp(1.0, -S);
+
+        std::vector<int32_t> q0(cells), qb(cells);
+        std::vector<double> rbar(cells);
+        long long mass = 0;
+        for (size_t i = 0; i < cells; ++i) {
+            q0[i] = (int32_t)std::llrint(std::ldexp(rho0[i], S));
+            mass += q0[i];
+        }
+        t.mass0 = mass;
+        mean_field(t.n, t.h, t.tau, t.M, rho0, rbar.data());
+        for (size_t i = 0; i < cells; ++i) qb[i] = (int32_t)std::llrint(std::ldexp(rbar[i], S));
+        std::vector<float> phif(cells * c->n_obs);
+        for (int k = 0; k < c->n_obs; ++k) {
+            const double* ph = cfg->phi[(size_t)l * c->n_obs + k];
+            if (!ph) { mlmc_dk_free(c); return fail(nullptr, MLMC_DK_ERR_INVALID, "null phi level array"); }
+            double yb = 0, dl = 0;
+            for (size_t i = 0; i < cells; ++i) {
+                yb += rbar[i] * ph[i];
+                dl += (std::ldexp((double)qb[i], -S) - rbar[i]) * ph[i];
+                phif[(size_t)k * cells + i] = (float)ph[i];
+            }
+            t.ybar[k] = t.h * t.h * yb;
+            t.delta[k] = t.h * t.h * dl;
+        }
+        // stage the level's tables in pinned memory and copy them in one transfer each
+        const size_t bytes = sizeof(int32_t) * cells * 2 + sizeof(float) * cells * c->n_obs;
+        unsigned char* stage = nullptr;
+        if ((e = cudaMallocHost(&stage, bytes)) != cudaSuccess) {
+            mlmc_dk_free(c);
+            return cuda_fail(nullptr, e, "pinned staging");
+        }
+        std::memcpy(stage, q0.data(), sizeof(int32_t) * cells);
+        std::memcpy(stage + sizeof(int32_t) * cells, qb.data(), sizeof(int32_t) * cells);
+        std::memcpy(stage + sizeof(int32_t) * cells * 2, phif.data(), sizeof(float) * cells * c->n_obs);
+        if ((e = cudaMalloc(&t.d_q0, sizeof(int32_t) * cells)) != cudaSuccess ||
+            (e = cudaMalloc(&t.d_qbar, sizeof(int32_t) * cells)) != cudaSuccess ||
+            (e = cudaMalloc(&t.d_phi, sizeof(float) * cells * c->n_obs)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(t.d_q0, stage, sizeof(int32_t) * cells, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(t.d_qbar, stage + sizeof(int32_t) * cells, sizeof(int32_t) * cells,
+                                 cudaMemcpyHostToDevice, c->stream)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(t.d_phi, stage + sizeof(int32_t) * cells * 2, sizeof(float) * cells * c->n_obs,
+                                 cudaMemcpyHostToDevice, c->stream)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(c->stream)) != cudaSuccess) {
+            cudaFreeHost(stage);
+            mlmc_dk_free(c);
+            return cuda_fail(nullptr, e, "level tables");
+        }
+        cudaFreeHost(stage);
+        c->h2d_bytes += (int64_t)bytes;
+        if ((e = dk::variant_info(t.n, false, c->stride, &t.vi_single)) != cudaSuccess ||
+            (l > 0 && (e = dk::variant_info(t.n, true, c->stride, &t.vi_coupled)) != cudaSuccess)) {
+            mlmc_dk_free(c);
+            return cuda_fail(nullptr, e, "kernel variant setup");
+        }
+        for (const dk::VariantInfo* vi : {&t.vi_single, &t.vi_coupled})
+            if (vi->supported)
+                partials_need = std::max(partials_need, (size_t)(vi->max_ctas / vi->cluster) * vi->slots_per_cta * c->stride);
+    }
+    if ((e = cudaMalloc(&c->d_partials, sizeof(double) * std::max<size_t>(partials_need, 1))) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_sums, sizeof(double) * c->stride)) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_err, sizeof(unsigned))) != cudaSuccess ||
+        (e = cudaMemset(c->d_err, 0, sizeof(unsigned))) != cudaSuccess ||
+        (e = cudaMallocHost(&c->h_sums, sizeof(double) * c->stride)) != cudaSuccess ||
+        (e = cudaMallocHost(&c->h_err, sizeof(unsigned))) != cudaSuccess ||
+        (e = cudaEventCreate(&c->ev0)) != cudaSuccess || (e = cudaEventCreate(&c->ev1)) != cudaSuccess) {
+        mlmc_dk_free(c);
+        return cuda_fail(nullptr, e, "context buffers");
+    }
+    c->partials_cap = partials_need;
+    *out = c;
+    return MLMC_DK_OK;
+}
+
+void mlmc_dk_free(mlmc_dk_ctx* ctx) {
+    if (!ctx) return;
+    release(ctx);
+    delete ctx;
+}
+
+int mlmc_dk_level_info(const mlmc_dk_ctx* ctx, int32_t level, mlmc_dk_level_desc* out) {
+    if (!ctx || !out || level < 0 || level > ctx->L_max)
+        return fail(const_cast<mlmc_dk_ctx*>(ctx), MLMC_DK_ERR_INVALID, "level_info: bad arguments");
+    const LevelTab& t = ctx->lv[level];
+    *out = mlmc_dk_level_desc{};
+    out->level = level;
+    out->n = t.n;
+    out->M = t.M;
+    out->h = t.h;
+    out->tau = t.tau;
+    for (int k = 0; k < ctx->n_obs; ++k) {
+        out->ybar_f[k] = t.ybar[k];
+        out->ybar_c[k] = level > 0 ? ctx->lv[level - 1].ybar[k] : 0.0;
+    }
+    out->cost_mc = (double)t.n * t.n * t.M;
+    out->cost = out->cost_mc + (level > 0 ? (double)ctx->lv[level - 1].n * ctx->lv[level - 1].n * ctx->lv[level - 1].M : 0.0);
+    out->next_sample = ctx->next_id[0][level];
+    out->h2d_bytes = ctx->h2d_bytes;
+    return MLMC_DK_OK;
+}
+
+int mlmc_dk_run_level(mlmc_dk_ctx* ctx, int32_t level, int64_t n_samples, uint64_t seed, mlmc_dk_level_sums* sums) {
+    return run_host(ctx, level, 0, n_samples, seed, sums);
+}
+
+int mlmc_dk_run_mc(mlmc_dk_ctx* ctx, int32_t level, int64_t n_samples, uint64_t seed, mlmc_dk_level_sums* sums) {
+    return run_host(ctx, level, 1, n_samples, seed, sums);
+}
+
+int mlmc_dk_run_level_dev(mlmc_dk_ctx* ctx, int32_t level, int32_t stream_tag, int64_t first_sample,
+                          int64_t n_samples, uint64_t seed, double* sums_dev, double* samples_dev,
+                          void* cuda_stream) {
+    if (!ctx) return fail(nullptr, MLMC_DK_ERR_INVALID, "null context");
+    if (level < 0 || level > ctx->L_max || (stream_tag != 0 && stream_tag != 1) || first_sample < 0 ||
+        n_samples < 0 || !sums_dev || ((uintptr_t)sums_dev & 7) || ((uintptr_t)samples_dev & 7))
+        return fail(ctx, MLMC_DK_ERR_INVALID, "run_level_dev: bad arguments");
+    cudaStream_t st = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : ctx->stream;
+    return launch_batch(ctx, level, stream_tag, first_sample, n_samples, seed, sums_dev, samples_dev, st);
+}
+
+int mlmc_dk_plan(int32_t L, const int64_t* n, const double* s1, const double* s2, const double* cost, double eps,
+                 int64_t* target, int32_t* converged) {
+    if (L < 0 || L >= MLMC_DK_MAX_LEVELS || !n || !s1 || !s2 || !cost || !target || !converged || !(eps > 0))
+        return fail(nullptr, MLMC_DK_ERR_INVALID, "plan: bad arguments");
+    double V[MLMC_DK_MAX_LEVELS], E[MLMC_DK_MAX_LEVELS];
+    double total = 0;
+    for (int l = 0; l <= L; ++l) {
+        if (n[l] < 2 || !(cost[l] > 0)) return fail(nullptr, MLMC_DK_ERR_INVALID, "plan: need n >= 2 and cost > 0");
+        const double m = (double)n[l];
+        E[l] = s1[l] / m;
+        V[l] = std::max(0.0, (s2[l] - s1[l] * s1[l] / m) / (m - 1.0));
+        total += std::sqrt(V[l] * cost[l]);
+    }
+    // Eq. (opt_M_ell)
+    for (int l = 0; l <= L; ++l) {
+        const double opt = std::ceil(2.0 / (eps * eps) * std::sqrt(V[l] / cost[l]) * total);
+        target[l] = std::max<int64_t>(n[l], (int64_t)std::min(opt, 9.0e18));
+    }
+    // Eq. (convergence_criterion), alpha = 2, P_{-1} = 0
+    const double alpha = 2.0;
+    double worst = 0;
+    for (int t = 0; t <= 2 && L - t >= 0; ++t) worst = std::max(worst, std::pow(2.0, -t * alpha) * std::fabs(E[L - t]));
+    *converged = worst / (std::pow(2.0, alpha) - 1.0) < eps / std::sqrt(2.0) ? 1 : 0;
+    return MLMC_DK_OK;
+}
+
+int mlmc_dk_estimate(mlmc_dk_ctx* ctx, double eps, int32_t relative, uint64_t seed, mlmc_dk_result* out) {
+    if (!ctx || !out || !(eps > 0)) return fail(ctx, MLMC_DK_ERR_INVALID, "estimate: bad arguments");
+    const auto t0 = std::chrono::steady_clock::now();
+    *out = mlmc_dk_result{};
+    const int Q = ctx->n_quant;
+    std::vector<std::vector<mlmc_dk_level_sums>> sums(ctx->L_max + 1, std::vector<mlmc_dk_level_sums>(Q));
+    std::vector<int64_t> target(ctx->L_max + 1, 0);
+    std::fill(ctx->next_id[0].begin(), ctx->next_id[0].end(), 0);
+    int L = ctx->L_start;
+    for (int l = 0; l <= L; ++l) target[l] = ctx->pilot;
+    double eps_abs = relative ? -1.0 : eps;
+    int status = MLMC_DK_OK, converged = 0;
+    std::vector<double> cost(ctx->L_max + 1);
+    for (int l = 0; l <= ctx->L_max; ++l) {
+        mlmc_dk_level_desc li;
+        mlmc_dk_level_info(ctx, l, &li);
+        cost[l] = li.cost;
+    }
+    for (int iter = 0; iter < 1000; ++iter) {
+        for (int l = 0; l <= L; ++l) {
+            const int64_t need = target[l] - sums[l][0].n;
+            if (need > 0) {
+                const int rc = mlmc_dk_run_level(ctx, l, need, seed, sums[l].data());
+                if (rc != MLMC_DK_OK) return rc;
+            }
+        }
+        int64_t n[MLMC_DK_MAX_LEVELS];
+        double s1[MLMC_DK_MAX_LEVELS], s2[MLMC_DK_MAX_LEVELS];
+        for (int l = 0; l <= L; ++l) {
+            n[l] = sums[l][0].n;
+            s1[l] = sums[l][0].dp1;
+            s2[l] = sums[l][0].dp2;
+        }
+        if (eps_abs < 0) {
+            double mu = 0;
+            for (int l = 0; l <= L; ++l) mu += s1[l] / (double)n[l];
+            eps_abs = eps * std::fabs(mu);
+            if (!(eps_abs > 0)) return fail(ctx, MLMC_DK_ERR_INVALID, "relative eps with a zero pilot estimate");
+        }
+        int64_t tgt[MLMC_DK_MAX_LEVELS];
+        int32_t conv = 0;
+        int rc = mlmc_dk_plan(L, n, s1, s2, cost.data(), eps_abs, tgt, &conv);
+        if (rc != MLMC_DK_OK) return fail(ctx, rc, g_init_error);
+        bool more = false;
+        for (int l = 0; l <= L; ++l) {
+            target[l] = std::max(target[l], tgt[l]);
+            if ((double)(target[l] - n[l]) > 0.01 * (double)n[l]) more = true;
+        }
+        if (more) continue;
+        if (conv) { converged = 1; break; }
+        if (L == ctx->L_max) { status = MLMC_DK_NOT_CONVERGED; break; }
+        ++L;
+        target[L] = ctx->pilot;
+    }
+    out->L = L;
+    out->converged = converged;
+    out->eps_abs = eps_abs;
+    for (int q = 0; q < Q && q < MLMC_DK_MAX_QUANT; ++q) {
+        double est = 0;
+        for (int l = 0; l <= L; ++l) est += sums[l][q].dp1 / (double)sums[l][q].n;
+        out->estimates[q] = est;
+    }
+    out->estimate = out->estimates[0];
+    for (int l = 0; l <= L; ++l) {
+        const mlmc_dk_level_sums& s = sums[l][0];
+        const double m = (double)s.n;
+        out->M[l] = s.n;
+        out->E[l] = s.dp1 / m;
+        out->V[l] = std::max(0.0, (s.dp2 - s.dp1 * s.dp1 / m) / (m - 1.0));
+        out->C[l] = cost[l];
+        out->variance += out->V[l] / m;
+        out->sample_steps += m * ctx->lv[l].M;
+        out->cell_steps += m * cost[l];
+        out->kernel_s[l] = s.kernel_s;
+        out->var_pf[l] = std::max(0.0, (s.pf2 - s.pf1 * s.pf1 / m) / (m - 1.0));
+        out->launches += s.launches;
+        out->d2h_bytes += s.d2h_bytes;
+    }
+    out->wall_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return status;
+}
+
+int mlmc_dk_noise_dev(uint64_t seed, int32_t level, int32_t stream_tag, int64_t sample, int32_t m, int32_t n,
+                      float* z_dev, uint32_t* raw_dev, void* cuda_stream) {
+    if (n < 2 || (n & 1) || m < 0 || sample < 0 || level < -1 || level > 254 || stream_tag < 0 || stream_tag > 255 ||
+        (!z_dev && !raw_dev) || ((uintptr_t)z_dev & 15) || ((uintptr_t)raw_dev & 15))
+        return fail(nullptr, MLMC_DK_ERR_INVALID, "noise_dev: bad arguments");
+    const uint32_t c3 = ((uint32_t)(level + 1) & 0xffu) | (((uint32_t)stream_tag & 0xffu) << 8) |
+                        ((uint32_t)(((uint64_t)sample >> 32) & 0xffffu) << 16);
+    cudaError_t e = dk::launch_noise(n, (uint32_t)m, (uint32_t)sample, c3, (uint32_t)(seed & 0xffffffffu),
+                                     (uint32_t)(seed >> 32), z_dev, raw_dev, static_cast<cudaStream_t>(cuda_stream));
+    return e == cudaSuccess ? MLMC_DK_OK : cuda_fail(nullptr, e, "noise kernel");
+}
+
+int mlmc_dk_save_state(const mlmc_dk_ctx* ctx, void* buf, size_t* len) {
+    if (!ctx || !len) return fail(const_cast<mlmc_dk_ctx*>(ctx), MLMC_DK_ERR_INVALID, "save_state: bad arguments");
+    const size_t levels = ctx->lv.size();
+    const size_t need = 16 + 2 * levels * sizeof(int64_t);
+    if (!buf) { *len = need; return MLMC_DK_OK; }
+    if (*len < need) return fail(const_cast<mlmc_dk_ctx*>(ctx), MLMC_DK_ERR_INVALID, "save_state: buffer too small");
+    unsigned char* p = static_cast<unsigned char*>(buf);
+    const uint32_t magic = 0x4d4c444bu, version = 1, nl = (uint32_t)levels, nq = (uint32_t)ctx->n_quant;
+    std::memcpy(p, &magic, 4); std::memcpy(p + 4, &version, 4); std::memcpy(p + 8, &nl, 4); std::memcpy(p + 12, &nq, 4);
+    std::memcpy(p + 16, ctx->next_id[0].data(), levels * sizeof(int64_t));
+    std::memcpy(p + 16 + levels * sizeof(int64_t), ctx->next_id[1].data(), levels * sizeof(int64_t));
+    *len = need;
+    return MLMC_DK_OK;
+}
+
+int mlmc_dk_load_state(mlmc_dk_ctx* ctx, const void* buf, size_t len) {
+    if (!ctx || !buf) return fail(ctx, MLMC_DK_ERR_INVALID, "load_state: bad arguments");
+    const size_t levels = ctx->lv.size();
+    if (len != 16 + 2 * levels * sizeof(int64_t)) return fail(ctx, MLMC_DK_ERR_STATE, "load_state: size mismatch");
+    const unsigned char* p = static_cast<const unsigned char*>(buf);
+    uint32_t magic, version, nl, nq;
+    std::memcpy(&magic, p, 4); std::memcpy(&version, p + 4, 4); std::memcpy(&nl, p + 8, 4); std::memcpy(&nq, p + 12, 4);
+    if (magic != 0x4d4c444bu || version != 1 || nl != levels || nq != (uint32_t)ctx->n_quant)
+        return fail(ctx, MLMC_DK_ERR_STATE, "load_state: checkpoint does not match this context");
+    std::vector<int64_t> a(levels), b(levels);
+    std::memcpy(a.data(), p + 16, levels * sizeof(int64_t));
+    std::memcpy(b.data(), p + 16 + levels * sizeof(int64_t), levels * sizeof(int64_t));
+    for (size_t l = 0; l < levels; ++l)
+        if (a[l] < 0 || b[l] < 0) return fail(ctx, MLMC_DK_ERR_STATE, "load_state: negative sample id");
+    ctx->next_id[0] = a;
+    ctx->next_id[1] = b;
+    return MLMC_DK_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,253 @@
+"""ctypes binding of ``libmlmc_dk.so`` (C-ABI in include/mlmc_dk.h).
+
+Argument marshalling only: every step of the hot path runs in the library's
+CUDA kernels.  There is no fallback: if the library is missing or no GPU is
+present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libmlmc_dk.so")
+
+MAX_LEVELS = 16
+MAX_OBS = 4
+MAX_QUANT = 10
+NSUM = 12
+
+OK, NOT_CONVERGED = 0, 1
+ERR_INVALID, ERR_CUDA, ERR_RANGE, ERR_UNSUPPORTED, ERR_STATE = -1, -2, -3, -4, -5
+
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("length", ctypes.c_double),
+        ("n0", ctypes.c_int32),
+        ("L_max", ctypes.c_int32),
+        ("T", ctypes.c_double),
+        ("cfl_mu", ctypes.c_double),
+        ("M0", ctypes.c_int32),
+        ("N", ctypes.c_double),
+        ("rho0", ctypes.POINTER(_dp)),
+        ("n_obs", ctypes.c_int32),
+        ("phi", ctypes.POINTER(_dp)),
+        ("products", ctypes.c_int32),
+        ("pilot", ctypes.c_int32),
+        ("L_start", ctypes.c_int32),
+        ("cuda_stream", ctypes.c_void_p),
+    ]
+
+
+class LevelDesc(ctypes.Structure):
+    _fields_ = [
+        ("level", ctypes.c_int32), ("n", ctypes.c_int32), ("M", ctypes.c_int32),
+        ("h", ctypes.c_double), ("tau", ctypes.c_double),
+        ("ybar_f", ctypes.c_double * MAX_OBS), ("ybar_c", ctypes.c_double * MAX_OBS),
+        ("cost", ctypes.c_double), ("cost_mc", ctypes.c_double),
+        ("next_sample", ctypes.c_int64), ("h2d_bytes", ctypes.c_int64),
+    ]
+
+
+class LevelSums(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64)] + [(k, ctypes.c_double) for k in (
+        "dp1", "dp2", "dp3", "dp4", "pf1", "pf2", "pc1", "pc2", "yf1", "yf2", "yc1", "yc2",
+        "max_mass_err", "cost", "wall_s", "kernel_s")] + [("launches", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Result(ctypes.Structure):
+    _fields_ = [
+        ("estimate", ctypes.c_double), ("variance", ctypes.c_double), ("eps_abs", ctypes.c_double),
+        ("L", ctypes.c_int32), ("converged", ctypes.c_int32),
+        ("M", ctypes.c_int64 * MAX_LEVELS),
+        ("V", ctypes.c_double * MAX_LEVELS), ("E", ctypes.c_double * MAX_LEVELS),
+        ("C", ctypes.c_double * MAX_LEVELS),
+        ("estimates", ctypes.c_double * MAX_QUANT),
+        ("sample_steps", ctypes.c_double), ("cell_steps", ctypes.c_double), ("wall_s", ctypes.c_double),
+        ("kernel_s", ctypes.c_double * MAX_LEVELS), ("var_pf", ctypes.c_double * MAX_LEVELS),
+        ("launches", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64),
+    ]
+
+
+_LIB = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load the library (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with paper_2311_08872_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp = ctypes.c_void_p
+        L.mlmc_dk_init.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(vp)]
+        L.mlmc_dk_free.argtypes = [vp]
+        L.mlmc_dk_free.restype = None
+        L.mlmc_dk_last_error.argtypes = [vp]
+        L.mlmc_dk_last_error.restype = ctypes.c_char_p
+        L.mlmc_dk_level_info.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(LevelDesc)]
+        L.mlmc_dk_run_level.argtypes = [vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.POINTER(LevelSums)]
+        L.mlmc_dk_run_mc.argtypes = [vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.POINTER(LevelSums)]
+        L.mlmc_dk_run_level_dev.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64,
+                                            ctypes.c_uint64, vp, vp, vp]
+        L.mlmc_dk_estimate.argtypes = [vp, ctypes.c_double, ctypes.c_int32, ctypes.c_uint64, ctypes.POINTER(Result)]
+        L.mlmc_dk_plan.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_int64), _dp, _dp, _dp, ctypes.c_double,
+                                   ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]
+        L.mlmc_dk_mean_field_host.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
+                                              _dp, _dp]
+        L.mlmc_dk_save_state.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_size_t)]
+        L.mlmc_dk_load_state.argtypes = [vp, vp, ctypes.c_size_t]
+        L.mlmc_dk_num_quantities.argtypes = [vp]
+        L.mlmc_dk_num_quantities.restype = ctypes.c_int32
+        L.mlmc_dk_version.restype = ctypes.c_char_p
+        L.mlmc_dk_noise_dev.argtypes = [ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
+                                        ctypes.c_int32, ctypes.c_int32, vp, vp, vp]
+        _LIB = L
+    return _LIB
+
+
+class MLMCError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"mlmc_dk error {code}: {msg}")
+        self.code = code
+
+
+def _check(rc: int, ctx=None, allow=(OK,)) -> int:
+    if rc not in allow:
+        msg = lib().mlmc_dk_last_error(ctx)
+        raise MLMCError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ------------------------------------------------------------ host helpers
+def mean_field_host(n: int, h: float, tau: float, M: int, rho0: np.ndarray) -> np.ndarray:
+    r = _f64(rho0).reshape(-1)
+    out = np.empty_like(r)
+    _check(lib().mlmc_dk_mean_field_host(n, h, tau, M, r.ctypes.data_as(_dp), out.ctypes.data_as(_dp)))
+    return out.reshape(n, n)
+
+
+def noise_dev(seed: int, level: int, stream_tag: int, sample: int, m: int, n: int,
+              z_ptr: int = 0, raw_ptr: int = 0, stream: int = 0):
+    """Normals / raw Philox words of one fine step into device memory."""
+    _check(lib().mlmc_dk_noise_dev(seed, level, stream_tag, sample, m, n, ctypes.c_void_p(z_ptr or None),
+                                   ctypes.c_void_p(raw_ptr or None), ctypes.c_void_p(stream or None)))
+
+
+def plan(n: Sequence[int], s1: Sequence[float], s2: Sequence[float], cost: Sequence[float], eps: float):
+    """Algorithm 1's host step: targets by Eq. (opt_M_ell), stopping test."""
+    L = len(n) - 1
+    n_ = (ctypes.c_int64 * (L + 1))(*n)
+    a = (ctypes.c_double * (L + 1))(*s1)
+    b = (ctypes.c_double * (L + 1))(*s2)
+    c = (ctypes.c_double * (L + 1))(*cost)
+    t = (ctypes.c_int64 * (L + 1))()
+    conv = ctypes.c_int32(0)
+    _check(lib().mlmc_dk_plan(L, n_, a, b, c, eps, t, ctypes.byref(conv)))
+    return list(t), bool(conv.value)
+
+
+# ------------------------------------------------------------------ context
+class Context:
+    """An initialised MLMC context (levels, tables and buffers on the GPU)."""
+
+    def __init__(self, length: float, n0: int, L_max: int, T: float, mu: float, N: float,
+                 rho0: List[np.ndarray], phi: List[List[np.ndarray]], products: bool = False,
+                 M0: int = 0, pilot: int = 0, L_start: int = 0, stream: Optional[int] = None):
+        self._ctx = None
+        self._rho0 = [_f64(r).reshape(-1) for r in rho0]
+        self.n_obs = len(phi[0])
+        self._phi = [_f64(p).reshape(-1) for lvl in phi for p in lvl]
+        rho_ptrs = (_dp * len(self._rho0))(*[r.ctypes.data_as(_dp) for r in self._rho0])
+        phi_ptrs = (_dp * len(self._phi))(*[p.ctypes.data_as(_dp) for p in self._phi])
+        self.cfg = Config(length, n0, L_max, T, mu, M0, N, rho_ptrs, self.n_obs, phi_ptrs,
+                          int(products), pilot, L_start, stream)
+        h = ctypes.c_void_p()
+        _check(lib().mlmc_dk_init(ctypes.byref(self.cfg), ctypes.byref(h)))
+        self._ctx = h
+        self.L_max = L_max
+        self.n_quant = lib().mlmc_dk_num_quantities(self._ctx)
+
+    @classmethod
+    def from_workload(cls, wl, **kw) -> "Context":
+        return cls(wl.length, wl.n0, wl.L_max, wl.T, wl.mu, wl.N, wl.rho0_all(), wl.phi_all(),
+                   products=wl.products, M0=wl.M0, **kw)
+
+    def close(self):
+        if self._ctx is not None:
+            lib().mlmc_dk_free(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._ctx
+
+    def level_info(self, level: int) -> LevelDesc:
+        d = LevelDesc()
+        _check(lib().mlmc_dk_level_info(self._ctx, level, ctypes.byref(d)), self._ctx)
+        return d
+
+    def run_level(self, level: int, n_samples: int, seed: int, sums=None, mc: bool = False):
+        if sums is None:
+            sums = (LevelSums * self.n_quant)()
+        fn = lib().mlmc_dk_run_mc if mc else lib().mlmc_dk_run_level
+        _check(fn(self._ctx, level, n_samples, seed, sums), self._ctx)
+        return sums
+
+    def run_level_dev(self, level: int, stream_tag: int, first: int, n_samples: int, seed: int,
+                      sums_ptr: int, samples_ptr: int = 0, stream: int = 0):
+        """Device-resident batch; pointers are device addresses (e.g. tensor.data_ptr())."""
+        _check(lib().mlmc_dk_run_level_dev(self._ctx, level, stream_tag, first, n_samples, seed,
+                                           ctypes.c_void_p(sums_ptr), ctypes.c_void_p(samples_ptr or None),
+                                           ctypes.c_void_p(stream or None)), self._ctx)
+
+    def estimate(self, eps: float, relative: bool, seed: int) -> Result:
+        r = Result()
+        _check(lib().mlmc_dk_estimate(self._ctx, eps, int(relative), seed, ctypes.byref(r)), self._ctx,
+               allow=(OK, NOT_CONVERGED))
+        return r
+
+    def save_state(self) -> bytes:
+        n = ctypes.c_size_t(0)
+        _check(lib().mlmc_dk_save_state(self._ctx, None, ctypes.byref(n)), self._ctx)
+        buf = ctypes.create_string_buffer(n.value)
+        _check(lib().mlmc_dk_save_state(self._ctx, buf, ctypes.byref(n)), self._ctx)
+        return buf.raw[: n.value]
+
+    def load_state(self, blob: bytes):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        _check(lib().mlmc_dk_load_state(self._ctx, buf, len(blob)), self._ctx)
+
+
+def sample_stride(n_obs: int) -> int:
+    """Doubles per sample in run_level_dev's per-sample output."""
+    return 2 * n_obs + 2
+
+
+def sums_len(n_quant: int) -> int:
+    return 2 + NSUM * n_quant

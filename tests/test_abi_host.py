@@ -1,0 +1,95 @@
+"""CPU checks of the C-ABI library: it loads without a GPU, exports every
+function include/*.h declares, and its host-only logic (the FFT mean field and
+Algorithm 1's planning step) agrees with the FP64 oracle."""
+import ctypes
+import glob
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2311_08872_gb300 import build as libbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def dk():
+    libbuild.build()
+    from paper_2311_08872_gb300 import mlmc_dk
+    return mlmc_dk
+
+
+def _declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for m in re.finditer(r"\b(mlmc_dk_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_function(dk):
+    names = _declared_functions()
+    assert len(names) >= 15
+    L = ctypes.CDLL(dk.LIB_PATH)
+    for n in names:
+        assert hasattr(L, n), n
+    assert dk.lib().mlmc_dk_version().startswith(b"mlmc_dk")
+
+
+@pytest.mark.parametrize("n,mu,M", [(8, 0.1, 30), (32, 0.25, 200), (64, 0.098, 832)])
+def test_host_mean_field_matches_oracle_iteration(dk, n, mu, M):
+    L = 1.0
+    h = L / n
+    x = np.arange(n) * h
+    x1, x2 = np.meshgrid(x, x, indexing="ij")
+    rho0 = 0.02 + 0.98 * np.exp(-((x1 - 0.5) ** 2 + (x2 - 0.4) ** 2) / 0.02) + 0.3 * np.cos(4 * math.pi * x2)
+    got = dk.mean_field_host(n, h, mu * h * h, M, rho0)
+    ref = oracle.mean_field(n, h, mu * h * h, M, rho0)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-12)
+
+
+def test_plan_matches_oracle_allocation_and_stopping_test(dk):
+    rng = np.random.default_rng(3)
+    for trial in range(200):
+        L = int(rng.integers(0, 6))
+        n = [int(rng.integers(2, 10 ** 6)) for _ in range(L + 1)]
+        E = [float(rng.normal(0, 10.0 ** -rng.uniform(1, 5))) for _ in range(L + 1)]
+        V = [float(10.0 ** -rng.uniform(1, 8)) for _ in range(L + 1)]
+        s1 = [e * m for e, m in zip(E, n)]
+        s2 = [(v * (m - 1) + e * e * m) for e, v, m in zip(E, V, n)]
+        cost = [float(4.0 ** l * 1e4) for l in range(L + 1)]
+        eps = float(10.0 ** -rng.uniform(1, 4))
+        targets, conv = dk.plan(n, s1, s2, cost, eps)
+        Vh = [max(0.0, (b - a * a / m) / (m - 1)) for a, b, m in zip(s1, s2, n)]
+        Eh = [a / m for a, m in zip(s1, n)]
+        ref = oracle.mlmc_optimal_samples(Vh, cost, eps)
+        for t, r, m in zip(targets, ref, n):
+            # ceil of the same real number; allow one unit for rounding order
+            assert abs(t - max(r, m)) <= 1 or t == m
+        assert conv == oracle.mlmc_converged(Eh, eps)
+
+
+def test_init_reports_errors_without_crashing(dk):
+    one = [np.ones((4, 4))]
+    phi = [[np.ones((4, 4))]]
+    with pytest.raises(dk.MLMCError) as e:   # mu > 1/2 violates the discrete maximum principle
+        dk.Context(1.0, 4, 0, 1.0, 0.6, 100.0, one, phi)
+    assert e.value.code == dk.ERR_INVALID
+    with pytest.raises(dk.MLMCError) as e:   # n0 not a power of two
+        dk.Context(1.0, 6, 0, 1.0, 0.1, 100.0, [np.ones((6, 6))], [[np.ones((6, 6))]])
+    assert e.value.code == dk.ERR_INVALID
+
+
+def test_init_without_gpu_fails_loudly(dk):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    one = [np.ones((4, 4))]
+    with pytest.raises(dk.MLMCError) as e:
+        dk.Context(1.0, 4, 0, 0.01, 0.1, 100.0, one, [[np.ones((4, 4))]])
+    assert e.value.code == dk.ERR_CUDA

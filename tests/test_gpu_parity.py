@@ -1,0 +1,227 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the FP64 oracle on
+identical seeds and sample ids.
+
+Per-sample bar (FP32-noise / fixed-point state against FP64):
+    |Y_gpu - Y_oracle| <= 1e-5 * max(|Y_oracle|, RMS over the batch of (Y_oracle - Ybar)),
+the relative form being meaningless where E[Y] = Ybar = 0.  Integer results
+(sample counts, the exactly conserved mass, raw Philox words) must match
+bit for bit.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2311_08872_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def dk():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2311_08872_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2311_08872_gb300 import mlmc_dk
+    return mlmc_dk
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def gpu_samples(ctx, dk, level, stream_tag, first, count, seed):
+    torch = _torch()
+    sums = torch.zeros(dk.sums_len(ctx.n_quant), dtype=torch.float64, device="cuda")
+    samp = torch.zeros(max(count, 1), dk.sample_stride(ctx.n_obs), dtype=torch.float64, device="cuda")
+    ctx.run_level_dev(level, stream_tag, first, count, seed, sums.data_ptr(), samp.data_ptr(),
+                      torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    return sums.cpu().numpy(), samp.cpu().numpy()[:count]
+
+
+def oracle_samples(wl, level, stream_tag, first, count, seed, processes=1):
+    levels = oracle.level_table(wl.length, wl.n0, wl.L_max, wl.T, wl.mu, wl.M0)
+    coupled = stream_tag == 0 and level > 0
+    ol = oracle.level_inputs(wl.length, levels, wl.N, wl.rho0_all(), wl.phi_all(), level, coupled)
+    r = oracle.run_samples(ol, seed, range(first, first + count), coupled, stream=stream_tag, processes=processes)
+    lf = levels[level]
+    ybf = [oracle.inner_h(oracle.mean_field(lf.n, lf.h, lf.tau, lf.M, wl.rho0(level)), p, lf.h) for p in wl.phi(level)]
+    ybc = None
+    if coupled:
+        lc = levels[level - 1]
+        ybc = [oracle.inner_h(oracle.mean_field(lc.n, lc.h, lc.tau, lc.M, wl.rho0(level - 1)), p, lc.h)
+               for p in wl.phi(level - 1)]
+    return r, np.array(ybf), None if ybc is None else np.array(ybc)
+
+
+def assert_parity(y_gpu, y_or, ybar_or, what):
+    scale = np.sqrt(np.mean((y_or - ybar_or[None, :]) ** 2, axis=0))
+    bound = TOL * np.maximum(np.abs(y_or), scale[None, :])
+    err = np.abs(y_gpu - y_or)
+    worst = float(np.max(err / bound))
+    assert worst <= 1.0, f"{what}: worst error / bound = {worst:.3g} (max abs err {err.max():.3g})"
+    return worst
+
+
+def check_level(dk, wl, level, stream_tag, first, count, seed, processes=1):
+    ctx = dk.Context.from_workload(wl)
+    try:
+        info = ctx.level_info(level)
+        sums, samp = gpu_samples(ctx, dk, level, stream_tag, first, count, seed)
+        r, ybf, ybc = oracle_samples(wl, level, stream_tag, first, count, seed, processes)
+        K = ctx.n_obs
+        np.testing.assert_allclose(np.array(info.ybar_f[:K]), ybf, rtol=1e-9, atol=1e-12)
+        yf = samp[:, :K] + np.array(info.ybar_f[:K])[None, :]
+        w = assert_parity(yf, r["Y_f"], ybf, f"{wl.name} level {level} fine")
+        # the fixed-point state conserves mass exactly
+        assert sums[1] == 0.0
+        m0 = oracle.inner_h(wl.rho0(level), np.ones_like(wl.rho0(level)), info.h)
+        np.testing.assert_allclose(samp[:, 2 * K], m0, rtol=1e-7)
+        np.testing.assert_allclose(r["mass_f"], m0, rtol=1e-12)
+        if ybc is not None:
+            np.testing.assert_allclose(np.array(info.ybar_c[:K]), ybc, rtol=1e-9, atol=1e-12)
+            yc = samp[:, K:2 * K] + np.array(info.ybar_c[:K])[None, :]
+            w = max(w, assert_parity(yc, r["Y_c"], ybc, f"{wl.name} level {level} coarse"))
+        assert int(sums[0]) == count
+        return w
+    finally:
+        ctx.close()
+
+
+# ----------------------------------------------------------------- noise source
+@pytest.mark.parametrize("seed,level,stream,sample,m,n", [
+    (0, 0, 0, 0, 0, 16), (7, 3, 1, 12345, 99, 64), (2 ** 40 + 3, 4, 0, 2 ** 33 + 17, 13311, 256)])
+def test_noise_source_matches_oracle(dk, seed, level, stream, sample, m, n):
+    torch = _torch()
+    z = torch.zeros(n * n * 2, dtype=torch.float32, device="cuda")
+    raw = torch.zeros(n * n * 2, dtype=torch.int32, device="cuda")
+    dk.noise_dev(seed, level, stream, sample, m, n, z.data_ptr(), raw.data_ptr())
+    torch.cuda.synchronize()
+    raw = raw.cpu().numpy().view(np.uint32).reshape(-1, 4)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    tag = ((level + 1) & 0xFF) | ((stream & 0xFF) << 8) | (((sample >> 32) & 0xFFFF) << 16)
+    for p in list(range(0, n * n // 2, max(1, n * n // 256))) + [n * n // 2 - 1]:
+        assert list(raw[p]) == oracle.philox4x32_10([p, m, sample & 0xFFFFFFFF, tag], key)
+    zg = z.cpu().numpy().astype(np.float64).reshape(n, n, 2)
+    zo = oracle.normals(seed, level, stream, sample, m, n)
+    r = np.sqrt(zo[..., 0] ** 2 + zo[..., 1] ** 2)[..., None]
+    # FP32 Box--Muller: ~1e-6 relative, plus the float rounding of u near 1 (radius -> 0)
+    allowed = 4e-6 * (1 + np.abs(zo)) + 6e-8 / np.maximum(r, 1e-6)
+    assert np.all(np.abs(zg - zo) <= allowed)
+
+
+# ------------------------------------------------------------- per-sample parity
+def test_plain_mc_32(dk):
+    w = check_level(dk, W.get("mc32"), 0, 1, 0, 200, seed=0)
+    print("mc32 worst/bound", w)
+
+
+@pytest.mark.parametrize("level,count", [(0, 96), (1, 40), (2, 6), (3, 2)])
+def test_coupled_mlmc16_256_levels(dk, level, count):
+    check_level(dk, W.get("mlmc16_256"), level, 0, 0, count, seed=1)
+
+
+@pytest.mark.slow
+def test_coupled_mlmc16_256_finest_level_full_size(dk):
+    """Level 4 (256^2 fine, 128^2 coarse, 13312 fine steps): sampled outputs at
+    the full size of the benchmarked workload."""
+    check_level(dk, W.get("mlmc16_256"), 4, 0, 17, 2, seed=1, processes=2)
+
+
+def test_ragged_tail_large_ids_and_mc_stream(dk):
+    wl = W.get("mlmc16_256")
+    check_level(dk, wl, 1, 0, 2 ** 32 + 5, 37, seed=2 ** 35 + 9)
+    check_level(dk, wl, 2, 1, 3, 5, seed=11)
+
+
+def test_tiny_grids_paper_setting(dk):
+    """The paper's Section 7.2 hierarchy on (0, 2 pi)^2: 4^2 level 0 with a single
+    step, 8^2 and 16^2 coupled levels, phi = sin x + sin y."""
+    wl = W.get("paper_reg").with_(N=2e5, L_max=2)
+    check_level(dk, wl, 0, 0, 0, 64, seed=5)
+    check_level(dk, wl, 1, 0, 0, 64, seed=5)
+    check_level(dk, wl, 2, 0, 0, 32, seed=5)
+
+
+def test_low_density_gaussian(dk):
+    wl = W.get("lowdens32_512")
+    check_level(dk, wl, 0, 0, 0, 32, seed=2)
+    check_level(dk, wl, 1, 0, 0, 8, seed=2)
+    check_level(dk, wl, 2, 0, 0, 1, seed=2)
+
+
+def test_four_observables_with_products(dk):
+    wl = W.get("large32_1024")
+    check_level(dk, wl, 0, 0, 0, 24, seed=4)
+    check_level(dk, wl, 1, 0, 0, 4, seed=4)
+
+
+# ------------------------------------------------------------------- the sums
+def test_device_sums_match_per_sample_outputs_and_are_deterministic(dk):
+    wl = W.get("large32_1024")
+    ctx = dk.Context.from_workload(wl)
+    try:
+        s1, samp = gpu_samples(ctx, dk, 1, 0, 100, 3000, seed=8)
+        s2, _ = gpu_samples(ctx, dk, 1, 0, 100, 3000, seed=8)
+        assert np.array_equal(s1, s2)
+        K = ctx.n_obs
+        Df, Dc = samp[:, :K], samp[:, K:2 * K]
+        q = 0
+        for j in range(K):
+            for k in range(j, K):
+                pf = wl.N * Df[:, j] * Df[:, k]
+                pc = wl.N * Dc[:, j] * Dc[:, k]
+                dp = pf - pc
+                ref = [dp.sum(), (dp ** 2).sum(), (dp ** 3).sum(), (dp ** 4).sum(), pf.sum(), (pf ** 2).sum(),
+                       pc.sum(), (pc ** 2).sum(), Df[:, j].sum(), (Df[:, j] ** 2).sum(), Dc[:, j].sum(),
+                       (Dc[:, j] ** 2).sum()]
+                got = s1[2 + 12 * q: 2 + 12 * (q + 1)]
+                np.testing.assert_allclose(got, ref, rtol=1e-10, atol=1e-300)
+                q += 1
+        assert q == ctx.n_quant == 10
+        assert s1[0] == 3000 and s1[1] == 0.0
+        z, _ = gpu_samples(ctx, dk, 1, 0, 0, 0, seed=8)
+        assert not np.any(z)
+    finally:
+        ctx.close()
+
+
+def test_checkpoint_resume_is_bit_exact(dk):
+    wl = W.get("mlmc16_256")
+    a = dk.Context.from_workload(wl)
+    b = dk.Context.from_workload(wl)
+    try:
+        a.run_level(1, 300, seed=3)
+        blob = a.save_state()
+        ra = a.run_level(1, 200, seed=3)
+        b.load_state(blob)
+        rb = b.run_level(1, 200, seed=3)
+        timing = {"wall_s": 0, "kernel_s": 0}
+        assert ra[0].as_dict() | timing == rb[0].as_dict() | timing
+        assert b.level_info(1).next_sample == 500
+        with pytest.raises(dk.MLMCError):
+            b.load_state(blob[:-8])
+    finally:
+        a.close()
+        b.close()
+
+
+def test_range_overflow_is_reported_not_faulted(dk):
+    """A particle number so small that |rho| leaves the fixed-point range: the
+    kernel flags it, the call returns MLMC_DK_ERR_RANGE, the context stays usable."""
+    wl = W.get("mc32").with_(N=1e-3)
+    ctx = dk.Context.from_workload(wl)
+    try:
+        with pytest.raises(dk.MLMCError) as e:
+            ctx.run_level(0, 64, seed=1, mc=True)
+        assert e.value.code == dk.ERR_RANGE
+    finally:
+        ctx.close()
+    check_level(dk, W.get("mc32"), 0, 1, 0, 8, seed=0)

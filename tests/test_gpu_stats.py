@@ -1,0 +1,147 @@
+"""GPU statistical checks and MLMC driver parity.
+
+* E[P] against the martingale closed form at high density, E[Y] = Ybar at
+  low density, and the coarse-path law equality of the NN coupling (Remark
+  distribution_W_ell / Section 3.2), with many GPU samples.
+* mlmc_dk_estimate (Algorithm 1 on the GPU path) against the same algorithm
+  driven by the FP64 oracle on identical seeds: same sample ids, so the
+  allocations agree and the estimates agree far inside 3 standard errors.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2311_08872_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+K_SE = 3.5
+
+
+@pytest.fixture(scope="module")
+def dk():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2311_08872_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2311_08872_gb300 import mlmc_dk
+    return mlmc_dk
+
+
+def _mean_se(s1, s2, n):
+    m = s1 / n
+    v = (s2 - s1 * s1 / n) / (n - 1)
+    return m, math.sqrt(max(v, 0.0) / n)
+
+
+@pytest.mark.parametrize("n0", [16, 32])
+def test_mean_P_matches_closed_form_high_density(dk, n0):
+    wl = W.get("mlmc16_256").with_(n0=n0, L_max=0, N=1e8)
+    with dk.Context.from_workload(wl) as ctx:
+        s = ctx.run_level(0, 200000, seed=9, mc=True)[0]
+        info = ctx.level_info(0)
+    m, se = _mean_se(s.pf1, s.pf2, s.n)
+    expect = oracle.closed_form_EP_cos1(1.0, n0, info.tau, info.M)
+    assert abs(m - expect) < K_SE * se, (m, expect, se)
+    assert se / expect < 0.01
+
+
+def test_mean_Y_is_mean_field_at_low_density(dk):
+    wl = W.get("lowdens32_512").with_(L_max=1)
+    with dk.Context.from_workload(wl) as ctx:
+        s = ctx.run_level(1, 100000, seed=21)[0]
+    for a, b in ((s.yf1, s.yf2), (s.yc1, s.yc2)):
+        m, se = _mean_se(a, b, s.n)
+        assert abs(m) < K_SE * se
+
+
+@pytest.mark.parametrize("level", [1, 2])
+def test_coarse_path_law_equals_standalone_path(dk, level):
+    wl = W.get("mlmc16_256").with_(L_max=level)
+    with dk.Context.from_workload(wl) as ctx:
+        pair = ctx.run_level(level, 40000 // level, seed=4)[0]
+        alone = ctx.run_level(level - 1, 40000 // level, seed=4, mc=True)[0]
+    mc, sc = _mean_se(pair.pc1, pair.pc2, pair.n)
+    ma, sa = _mean_se(alone.pf1, alone.pf2, alone.n)
+    assert abs(mc - ma) < K_SE * math.hypot(sc, sa)
+    # the coupling removes most of the fine-level variance
+    vdp = (pair.dp2 - pair.dp1 ** 2 / pair.n) / (pair.n - 1)
+    vpf = (pair.pf2 - pair.pf1 ** 2 / pair.n) / (pair.n - 1)
+    assert vdp < 0.5 * vpf
+
+
+def _oracle_mlmc(wl, eps_rel, seed, pilot, L_start):
+    """Algorithm 1 with oracle samples, same decisions as the library's driver."""
+    levels = oracle.level_table(wl.length, wl.n0, wl.L_max, wl.T, wl.mu, wl.M0)
+    rho0, phi = wl.rho0_all(), wl.phi_all()
+    ybar = [oracle.inner_h(oracle.mean_field(l.n, l.h, l.tau, l.M, rho0[l.level]), phi[l.level][0], l.h)
+            for l in levels]
+    cost = [levels[l].n ** 2 * levels[l].M + (levels[l - 1].n ** 2 * levels[l - 1].M if l else 0)
+            for l in range(len(levels))]
+    dps = [np.zeros(0) for _ in levels]
+
+    def run(l, count):
+        ol = oracle.level_inputs(wl.length, levels, wl.N, rho0, phi, l, l > 0)
+        first = dps[l].size
+        r = oracle.run_samples(ol, seed, range(first, first + count), l > 0)
+        pf = wl.N * (r["Y_f"][:, 0] - ybar[l]) ** 2
+        pc = wl.N * (r["Y_c"][:, 0] - ybar[l - 1]) ** 2 if l else 0.0
+        dps[l] = np.concatenate([dps[l], pf - pc])
+
+    L = min(L_start, wl.L_max)
+    target = [pilot] * (L + 1)
+    eps = None
+    while True:
+        for l in range(L + 1):
+            if target[l] > dps[l].size:
+                run(l, target[l] - dps[l].size)
+        E = [d.mean() for d in dps[:L + 1]]
+        V = [d.var(ddof=1) for d in dps[:L + 1]]
+        if eps is None:
+            eps = eps_rel * abs(sum(E))
+        opt = oracle.mlmc_optimal_samples(V, cost[:L + 1], eps)
+        more = False
+        for l in range(L + 1):
+            target[l] = max(target[l], opt[l], dps[l].size)
+            if target[l] - dps[l].size > 0.01 * dps[l].size:
+                more = True
+        if more:
+            continue
+        if oracle.mlmc_converged(E, eps) or L == wl.L_max:
+            break
+        L += 1
+        target.append(pilot)
+    est = oracle.mlmc_estimator([d.sum() for d in dps[:L + 1]], [d.size for d in dps[:L + 1]])
+    var = sum(d.var(ddof=1) / d.size for d in dps[:L + 1])
+    return est, var, [d.size for d in dps[:L + 1]]
+
+
+def test_estimate_matches_oracle_driven_algorithm(dk):
+    wl = W.get("mlmc16_256").with_(n0=4, L_max=3, T=0.01, N=3e3)
+    pilot = 200
+    with dk.Context.from_workload(wl, pilot=pilot, L_start=2) as ctx:
+        r = ctx.estimate(0.05, relative=True, seed=13)
+    est, var, counts = _oracle_mlmc(wl, 0.05, 13, pilot, 2)
+    gM = [r.M[l] for l in range(r.L + 1)]
+    se = math.sqrt(r.variance + var)
+    assert abs(r.estimate - est) < K_SE * se
+    if gM == counts:   # identical allocation -> identical samples -> per-sample tolerance
+        assert abs(r.estimate - est) <= 1e-4 * abs(est)
+    assert r.variance <= (r.eps_abs ** 2) / 2 * 1.05
+
+
+def test_estimate_on_benchmark_workload(dk):
+    """Algorithm 1 to eps = 1e-3 relative on the 16^2..256^2 workload: the
+    estimator variance meets eps^2/2 and the estimate sits near the level-L
+    closed form (bias and the positive-part effect are O(eps))."""
+    wl = W.get("mlmc16_256")
+    with dk.Context.from_workload(wl) as ctx:
+        r = ctx.estimate(wl.eps_rel, relative=True, seed=wl.seed)
+        info = ctx.level_info(r.L)
+    assert r.variance <= r.eps_abs ** 2 / 2 * 1.05
+    cf = oracle.closed_form_EP_cos1(1.0, info.n, info.tau, info.M)
+    assert abs(r.estimate - cf) < 5 * math.sqrt(r.variance) + 10 * r.eps_abs
+    print("estimate", r.estimate, "closed form", cf, "L", r.L, "M", [r.M[l] for l in range(r.L + 1)],
+          "wall", r.wall_s)
