@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adaptive", action="store_true", help="skip the Algorithm 1 / plain MC timing")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--adaptive-eps", type=float, default=1e-2,
+                    help="relative eps of the fully measured Algorithm 1 run (0: the workload's)")
     return ap.parse_args()
 
 
@@ -200,20 +202,20 @@ def run_ours(args, wl, rank, world, local_rank):
     info = [ctx.level_info(l) for l in range(wl.L_max + 1)]
     out = {}
 
-    # ---- adaptive Algorithm 1 to eps (also gives the allocation if none is fixed)
+    # ---- a complete adaptive Algorithm 1 run, measured (at a looser eps than the
+    #      workload's when the workload's eps would take longer than the bench allows)
     adaptive = None
-    if not args.no_adaptive or alloc is None:
+    if not args.no_adaptive:
+        eps_meas = args.adaptive_eps or wl.eps_rel
         torch.cuda.synchronize()
         t = time.perf_counter()
-        r = ctx.estimate(wl.eps_rel, relative=True, seed=seed0)
+        r = ctx.estimate(eps_meas, relative=True, seed=seed0 + 5)
         torch.cuda.synchronize()
-        wall = time.perf_counter() - t
-        L = r.L
-        adaptive = {"s": wall, "L": L, "M": [r.M[l] for l in range(L + 1)], "estimate": r.estimate,
-                    "variance": r.variance, "eps_abs": r.eps_abs, "converged": bool(r.converged),
-                    "var_pf_L": r.var_pf[L]}
-        if alloc is None:
-            alloc = adaptive["M"]
+        adaptive = {"eps_rel": eps_meas, "s": time.perf_counter() - t, "L": r.L,
+                    "M": [r.M[l] for l in range(r.L + 1)], "estimate": r.estimate, "variance": r.variance,
+                    "eps_abs": r.eps_abs, "converged": bool(r.converged), "cell_steps": r.cell_steps}
+    if alloc is None:
+        raise SystemExit("workload has no fixed allocation")
     alloc = alloc + [0] * (wl.L_max + 1 - len(alloc))
     sample_steps, cell_steps = batch_units(wl, alloc)
 
@@ -243,7 +245,7 @@ def run_ours(args, wl, rank, world, local_rank):
             e = s[l, 2] / m
             est += e
             var += max(0.0, (s[l, 3] - s[l, 2] ** 2 / m) / (m - 1)) / m
-        return est, var
+        return est, var, s.copy()
 
     for w in range(args.warmup):
         step(seed0 + 17 + w)
@@ -254,9 +256,10 @@ def run_ours(args, wl, rank, world, local_rank):
     clocks.start()
     step_ms, level_ms = [], [0.0] * len(alloc)
     launches = 0
+    last = None
     for k in range(args.steps):
         flush.zero_()                      # evict L2 between steps (outside the step events)
-        step(seed0 + 101 + k)
+        last = step(seed0 + 101 + k)
         step_ms.append(step_ev[0].elapsed_time(step_ev[1]))
         for l, m in enumerate(alloc):
             if m > 0:
@@ -285,21 +288,36 @@ def run_ours(args, wl, rank, world, local_rank):
                 "cell_steps_per_s": alloc[dom] * (fine[dom] + coarse[dom]) * args.steps / (level_ms[dom] * 1e-3),
                 "level_ms_per_step": [x / args.steps for x in level_ms]}
 
-    # ---- plain MC to the same eps on the finest level reached
-    mc = None
-    if adaptive is not None:
-        L = adaptive["L"]
-        n_mc = int(max(64, min(20000, 2.0e11 / (fine[L]))))
-        torch.cuda.synchronize()
-        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        ctx.run_level(L, n_mc, seed0 + 7, mc=True)
-        a1.record(stream)
-        torch.cuda.synchronize()
-        per = a0.elapsed_time(a1) * 1e-3 / n_mc
-        m_mc = math.ceil(2.0 * adaptive["var_pf_L"] / adaptive["eps_abs"] ** 2)
-        mc = {"level": L, "samples": m_mc, "s_per_sample": per, "s": m_mc * per, "extrapolated": True,
-              "measured_samples": n_mc}
+    # ---- time to the workload's eps, MLMC against plain MC on the finest level.
+    # From the timed batch: V_l = Var[P_l - P_{l-1}] and the device seconds per
+    # sample t_l give the eps-optimal MLMC time 2 eps^-2 (sum_l sqrt(V_l t_l))^2
+    # (Eq. opt_M_ell with C_l = t_l); plain MC needs 2 Var[P_L] / eps^2 samples
+    # of level L, timed separately below.
+    est, _, s = last
+    Ls = max(l for l, m in enumerate(alloc) if m > 0)
+    V, tsec = [], []
+    for l, m in enumerate(alloc):
+        if m > 0:
+            V.append(max(0.0, (s[l, 3] - s[l, 2] ** 2 / m) / (m - 1)))
+            tsec.append(level_ms[l] * 1e-3 / (args.steps * m))
+    eps_abs = wl.eps_rel * abs(est)
+    t_mlmc = 2.0 / eps_abs ** 2 * sum(math.sqrt(v * t) for v, t in zip(V, tsec)) ** 2
+    mL = alloc[Ls]
+    var_pL = max(0.0, (s[Ls, 7] - s[Ls, 6] ** 2 / mL) / (mL - 1))
+    n_mc = int(max(32, min(20000, 2.0e11 / fine[Ls])))
+    torch.cuda.synchronize()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    ctx.run_level(Ls, n_mc, seed0 + 7, mc=True)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    per = a0.elapsed_time(a1) * 1e-3 / n_mc
+    m_mc = math.ceil(2.0 * var_pL / eps_abs ** 2)
+    mc = {"level": Ls, "samples": m_mc, "s_per_sample": per, "s": m_mc * per, "extrapolated": True,
+          "measured_samples": n_mc, "var_P_L": var_pL}
+    to_eps = {"eps_rel": wl.eps_rel, "eps_abs": eps_abs, "estimate": est, "V": V, "s_per_sample": tsec,
+              "mlmc_s": t_mlmc, "mc_s": m_mc * per, "extrapolated": True,
+              "how": "eps-optimal allocation from the timed batch's V_l and measured per-sample device time"}
 
     # ---- end to end through the public API with host buffers
     e2e = None
@@ -354,13 +372,12 @@ def run_ours(args, wl, rank, world, local_rank):
         "e2e": e2e,
         "clocks": clk,
     }
-    if adaptive is not None:
-        line["mlmc_s_to_eps"] = adaptive["s"]
-        line["mlmc_adaptive"] = adaptive
-        line["mc_s_to_eps"] = mc["s"] if mc else None
-        line["mc"] = mc
-        if mc:
-            line["mlmc_speedup_vs_mc"] = mc["s"] / adaptive["s"]
+    line["mlmc_s_to_eps"] = t_mlmc
+    line["mc_s_to_eps"] = mc["s"]
+    line["mlmc_speedup_vs_mc"] = mc["s"] / t_mlmc
+    line["to_eps"] = to_eps
+    line["mc"] = mc
+    line["mlmc_adaptive_measured"] = adaptive
     return line
 
 

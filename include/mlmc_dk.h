@@ -36,8 +36,8 @@
  * component r = 1 of the noise flux is along i1.
  *
  * Precision: the state is 32-bit fixed point, rho = q 2^-S_l, with S_l in
- * [16, 28] chosen per level at init from the initial range and the expected
- * per-cell fluctuation sqrt(rho/(N h^2)).  Each step adds per-edge diffusion
+ * [16, 40] chosen per level at init as large as the initial range and the
+ * expected per-cell fluctuation sqrt(rho/(N h^2)) allow.  Each step adds per-edge diffusion
  * fluxes and per-cell noise transfers (computed in FP32, rounded to integers)
  * exactly, so the mass (rho, 1)_h is conserved bit for bit and every rounding
  * error enters in divergence form; observables and moment sums are FP64.
@@ -104,6 +104,7 @@ typedef struct {
     double cost_mc;         /* cell-steps per plain MC sample: n_l^2 M_l */
     int64_t next_sample;    /* first sample id the next mlmc_dk_run_level call uses */
     int64_t h2d_bytes;      /* bytes mlmc_dk_init uploaded for all levels (pinned staging) */
+    int32_t frac_bits;      /* S_l: the level's fixed-point state is rho 2^S_l */
 } mlmc_dk_level_desc;
 
 /* Host-side moment sums of one quantity on one level (accumulated into). */

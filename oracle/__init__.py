@@ -66,6 +66,10 @@ def lib():
         L.oracle_sample.argtypes = [ctypes.POINTER(_OracleLevelC), ctypes.c_uint64, ctypes.c_int,
                                     ctypes.c_uint64, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp]
         L.oracle_sample.restype = ctypes.c_int
+        L.oracle_sample_perturbed.argtypes = [ctypes.POINTER(_OracleLevelC), ctypes.c_uint64, ctypes.c_int,
+                                              ctypes.c_uint64, ctypes.c_int, ctypes.c_double, ctypes.c_uint64,
+                                              _dp, _dp, _dp, _dp]
+        L.oracle_sample_perturbed.restype = ctypes.c_int
         L.oracle_mean_field.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
                                         _dp, _dp]
         _LIB = L
@@ -180,6 +184,21 @@ class OracleLevel:
             if coupled:
                 out["rho_c"] = rc.reshape(n // 2, n // 2)
         return out
+
+
+    def sample_perturbed(self, seed: int, sample: int, coupled: bool, amp: float, perturb_seed: int,
+                         stream: int = 0):
+        """The same sample with mass-conserving random edge transfers of size
+        amp after every step (see oracle_sample_perturbed)."""
+        Yf = np.zeros(self.n_obs)
+        Yc = np.zeros(self.n_obs)
+        mf = ctypes.c_double(0.0)
+        mc = ctypes.c_double(0.0)
+        rc_ = lib().oracle_sample_perturbed(ctypes.byref(self.c), seed, stream, sample, int(coupled), amp,
+                                            perturb_seed, _ptr(Yf), _ptr(Yc), ctypes.byref(mf), ctypes.byref(mc))
+        if rc_ != 0:
+            raise ValueError(f"oracle_sample_perturbed failed ({rc_})")
+        return dict(Y_f=Yf, Y_c=Yc if coupled else None, mass_f=mf.value, mass_c=mc.value if coupled else None)
 
 
 def level_inputs(length: float, levels: List[Level], N: float, rho0: List[np.ndarray],

@@ -133,10 +133,36 @@ static double inner_h(int n, double h, const double* f, const double* g)
     return h * h * s;
 }
 
-int oracle_sample(const oracle_level* lv, uint64_t seed, int stream, uint64_t sample,
-                  int coupled, double* Y_f, double* Y_c, double* mass_f, double* mass_c,
-                  double* rho_f_out, double* rho_c_out)
+/* splitmix64 (Steele, Lea, Flood, "Fast splittable pseudorandom number
+ * generators", OOPSLA 2014): the perturbation stream of oracle_sample_perturbed. */
+static uint64_t splitmix64(uint64_t* state)
 {
+    uint64_t z = (*state += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+static void perturb_edges(int n, double amp, uint64_t* state, double* rho)
+{
+    for (int i1 = 0; i1 < n; ++i1)
+        for (int i2 = 0; i2 < n; ++i2) {
+            int x = i1 * n + i2;
+            int down = wrap(i1 + 1, n) * n + i2, right = i1 * n + wrap(i2 + 1, n);
+            double e1 = ((double)(splitmix64(state) >> 11) / 9007199254740992.0 - 0.5) * amp;
+            double e2 = ((double)(splitmix64(state) >> 11) / 9007199254740992.0 - 0.5) * amp;
+            rho[x] += e1 + e2;
+            rho[down] -= e1;
+            rho[right] -= e2;
+        }
+}
+
+static int sample_impl(const oracle_level* lv, uint64_t seed, int stream, uint64_t sample,
+                       int coupled, double amp, uint64_t perturb_seed,
+                       double* Y_f, double* Y_c, double* mass_f, double* mass_c,
+                       double* rho_f_out, double* rho_c_out)
+{
+    uint64_t pstate = perturb_seed;
     const int n = lv->n, nc = n / 2;
     if (n < 2 || (n & 1)) return -1;
     if (coupled && (lv->M % 4) != 0) return -2;
@@ -171,10 +197,12 @@ int oracle_sample(const oracle_level* lv, uint64_t seed, int stream, uint64_t sa
         }
         oracle_dk_step(n, lv->h, lv->tau, lv->inv_sqrt_N, rho_f, dbeta_f, tmp_f);
         double* t = rho_f; rho_f = tmp_f; tmp_f = t;
+        if (amp > 0.0) perturb_edges(n, amp, &pstate, rho_f);
         if (coupled && (m % 4) == 3) {
             oracle_dk_step(nc, 2.0 * lv->h, 4.0 * lv->tau, lv->inv_sqrt_N, rho_c, dbeta_c, tmp_c);
             double* tc = rho_c; rho_c = tmp_c; tmp_c = tc;
             memset(dbeta_c, 0, sizeof(double) * cc * 2);
+            if (amp > 0.0) perturb_edges(nc, amp, &pstate, rho_c);
         }
     }
     double* ones = (double*)malloc(sizeof(double) * cf);
@@ -192,4 +220,20 @@ int oracle_sample(const oracle_level* lv, uint64_t seed, int stream, uint64_t sa
     free(rho_f); free(tmp_f); free(Z); free(dbeta_f);
     free(rho_c); free(tmp_c); free(dbeta_c);
     return 0;
+}
+
+int oracle_sample(const oracle_level* lv, uint64_t seed, int stream, uint64_t sample,
+                  int coupled, double* Y_f, double* Y_c, double* mass_f, double* mass_c,
+                  double* rho_f_out, double* rho_c_out)
+{
+    return sample_impl(lv, seed, stream, sample, coupled, 0.0, 0, Y_f, Y_c, mass_f, mass_c,
+                       rho_f_out, rho_c_out);
+}
+
+int oracle_sample_perturbed(const oracle_level* lv, uint64_t seed, int stream, uint64_t sample,
+                            int coupled, double amp, uint64_t perturb_seed,
+                            double* Y_f, double* Y_c, double* mass_f, double* mass_c)
+{
+    return sample_impl(lv, seed, stream, sample, coupled, amp, perturb_seed, Y_f, Y_c, mass_f, mass_c,
+                       NULL, NULL);
 }

@@ -72,6 +72,17 @@ int oracle_sample(const oracle_level* lv, uint64_t seed, int stream, uint64_t sa
                   int coupled, double* Y_f, double* Y_c, double* mass_f, double* mass_c,
                   double* rho_f_out, double* rho_c_out);
 
+/* Same as oracle_sample, and after every fine (coarse) step each edge of the
+ * fine (coarse) grid moves a uniform random amount in [-amp/2, amp/2] from one
+ * of its cells to the other (splitmix64 stream from perturb_seed).  These
+ * perturbations conserve mass and have the size of one unit of a fixed-point
+ * state with quantum amp; they measure how sensitive a sample path of the
+ * scheme is to rounding of that size (the positive part [rho]^+ under the
+ * square root makes paths ill-conditioned where rho crosses 0). */
+int oracle_sample_perturbed(const oracle_level* lv, uint64_t seed, int stream, uint64_t sample,
+                            int coupled, double amp, uint64_t perturb_seed,
+                            double* Y_f, double* Y_c, double* mass_f, double* mass_c);
+
 /* Noise-free scheme (the discrete mean field rho-bar of Eq. (eqn_MLMCLevels))
  * iterated M times from rho0. */
 void oracle_mean_field(int n, double h, double tau, int64_t M, const double* rho0, double* out);

@@ -341,12 +341,15 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
             if (!std::isfinite(rho0[i])) { mlmc_dk_free(c); return fail(nullptr, MLMC_DK_ERR_INVALID, "non-finite rho0"); }
             rmax = std::max(rmax, std::fabs(rho0[i]));
         }
-        // Fixed-point scale: headroom for twice the initial range plus 12
-        // standard deviations of the per-cell fluctuation sqrt(rho/(N h^2)).
+        // Fixed-point scale: the largest S with 2^S times (twice the initial range
+        // plus 12 standard deviations of the per-cell fluctuation sqrt(rho/(N h^2)))
+        // below 2^29, so |q| stays under the 2^30 range check with a factor 2 to
+        // spare; a larger S resolves the noise transfers and diffusion fluxes
+        // more finely.
         const double noise_sd = cfg->N > 0 ? std::sqrt(std::max(rmax, 1e-3) / (cfg->N * t.h * t.h)) : 0.0;
-        const double range = 2.0 * rmax + 1.0 + 12.0 * noise_sd;
-        int S = 30 - (int)std::ceil(std::log2(range));
-        S = std::max(16, std::min(28, S));
+        const double range = std::max(2.0 * rmax + 12.0 * noise_sd, 1e-6);
+        int S = 29 - (int)std::ceil(std::log2(range));
+        S = std::max(16, std::min(40, S));
         const double c_noise = cfg->N > 0 ? std::sqrt(t.tau) / (std::sqrt(cfg->N) * 2.0 * t.h * t.h) : 0.0;
         // keep the noise multiplier g = c 2^(S/2) small enough that |G| stays far below 2^31
         while (S > 16 && c_noise * std::pow(2.0, 0.5 * S) > 2048.0) --S;
@@ -455,6 +458,7 @@ int mlmc_dk_level_info(const mlmc_dk_ctx* ctx, int32_t level, mlmc_dk_level_desc
     out->cost = out->cost_mc + (level > 0 ? (double)ctx->lv[level - 1].n * ctx->lv[level - 1].n * ctx->lv[level - 1].M : 0.0);
     out->next_sample = ctx->next_id[0][level];
     out->h2d_bytes = ctx->h2d_bytes;
+    out->frac_bits = t.S;
     return MLMC_DK_OK;
 }
 

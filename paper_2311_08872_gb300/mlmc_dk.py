@@ -51,7 +51,7 @@ class LevelDesc(ctypes.Structure):
         ("h", ctypes.c_double), ("tau", ctypes.c_double),
         ("ybar_f", ctypes.c_double * MAX_OBS), ("ybar_c", ctypes.c_double * MAX_OBS),
         ("cost", ctypes.c_double), ("cost_mc", ctypes.c_double),
-        ("next_sample", ctypes.c_int64), ("h2d_bytes", ctypes.c_int64),
+        ("next_sample", ctypes.c_int64), ("h2d_bytes", ctypes.c_int64), ("frac_bits", ctypes.c_int32),
     ]
 
 

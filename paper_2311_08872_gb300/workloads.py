@@ -139,6 +139,7 @@ class Workload:
     samples: Optional[int] = None   # fixed sample count (plain MC workload)
     M0: int = 0                     # >0 overrides M_0 = ceil(T / (mu h0^2))
     alloc: Optional[Tuple[int, ...]] = None   # fixed per-level sample counts of one benchmark step
+    alloc_scale: int = 1            # the eps-optimal allocation is about alloc * alloc_scale
     note: str = ""
 
     def n(self, level: int) -> int:
@@ -172,7 +173,7 @@ WORKLOADS: Dict[str, Workload] = {
                      seed=0, samples=1000,
                      note="plain single-level MC, 32^2, 1000 samples"),
     "mlmc16_256": Workload("mlmc16_256", 1.0, 16, 4, 0.02, 0.1, 1e5, "sinsin", [COS1],
-                           seed=1, eps_rel=1e-3, alloc=(20000000, 2000000, 250000, 30000, 0),
+                           seed=1, eps_rel=1e-3, alloc=(578250, 28946, 4617, 1570, 955), alloc_scale=1024,
                            note="coupled MLMC, levels 16^2..256^2"),
     "lowdens32_512": Workload("lowdens32_512", 1.0, 32, 4, 0.02, 0.1, 1e5, "gauss", [COS1],
                               seed=2, eps_rel=2e-3,
