@@ -193,6 +193,34 @@ int mlmc_dk_run_level_dev(mlmc_dk_ctx* ctx, int32_t level, int32_t stream_tag,
                           int64_t first_sample, int64_t n_samples, uint64_t seed,
                           double* sums_dev, double* samples_dev, void* cuda_stream);
 
+/* Same batch as mlmc_dk_run_level_dev, for callers that must not allocate
+ * device memory when they run it: processes that hand out all of their GPU
+ * memory from a pool reserved at start-up and may not allocate afterwards,
+ * and latency-critical loops in which cudaMalloc/cudaFree (which synchronise
+ * the device) are not allowed.  This call allocates nothing and uses none of
+ * the context's device buffers except its read-only level tables: the per-slot
+ * partial sums go to a statically allocated device array of 4 MiB that every
+ * GPU loading the library keeps until the process exits.  The paper has no
+ * counterpart of this entry point.
+ *   - The first call on a device looks up that array's device address
+ *     (cudaGetSymbolAddress, with the device current); make that first call
+ *     before any stream capture on that device.
+ *   - All calls share the array and it keeps the last call's contents; the
+ *     kernel overwrites every entry it later reads, so nothing needs clearing.
+ *     Calls that overlap on the GPU (other streams, other host threads, other
+ *     contexts) race on the array and corrupt each other's sums: serialise them.
+ *   - The grid is limited to the sample slots whose partial sums fit the array
+ *     (at least one CTA's worth; otherwise MLMC_DK_ERR_INVALID), so a call may
+ *     keep fewer samples in flight than mlmc_dk_run_level_dev.  Per-sample
+ *     values are identical; the sums agree up to FP64 summation order.
+ *   - err_dev: NULL, or a caller-owned device word that receives the range
+ *     error bit (1) by atomic OR; with NULL, range errors are not reported.
+ * Outputs and alignment as mlmc_dk_run_level_dev; asynchronous on cuda_stream
+ * (NULL: the context's stream); the context is not modified. */
+int mlmc_dk_run_level_static(const mlmc_dk_ctx* ctx, int32_t level, int32_t stream_tag, int64_t first_sample,
+                             int64_t n_samples, uint64_t seed, double* sums_dev, double* samples_dev,
+                             unsigned int* err_dev, void* cuda_stream);
+
 /* Algorithm 1 (Section 7.1): start at L = L_start with `pilot` samples on
  * levels 0..L; repeat {run the missing samples, re-estimate V_l, set targets by
  * Eq. (opt_M_ell), once no level needs samples apply Eq.

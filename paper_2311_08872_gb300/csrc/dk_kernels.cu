@@ -33,6 +33,9 @@
 // and moments are accumulated in FP64.
 #include <cooperative_groups.h>
 
+#include <atomic>
+#include <mutex>
+
 #include "dk_device.cuh"
 #include "dk_kernels.h"
 
@@ -575,6 +578,42 @@ cudaError_t launch_noise(int n, uint32_t m, uint32_t c2, uint32_t c3, uint32_t k
     const int pairs = n * n / 2;
     noise_kernel<<<(pairs + 255) / 256, 256, 0, st>>>(n, m, c2, c3, k0, k1, z, raw);
     return cudaGetLastError();
+}
+
+// -------------------------------------------- statically allocated scratch
+// Scratch for the per-slot partial sums of mlmc_dk_run_level_static, whose
+// callers cannot allocate device memory.  Every GPU that loads the library
+// holds this array until the process exits; all calls share it.
+static __device__ __align__(256) double g_static_partials[kStaticScratchDoubles];
+
+namespace {
+constexpr int kMaxDevices = 64;
+double* g_static_ptr[kMaxDevices] = {};
+std::atomic<int> g_static_ready[kMaxDevices];
+std::mutex g_static_mutex;
+}  // namespace
+
+cudaError_t static_scratch(double** out, size_t* capacity) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    if (!g_static_ready[dev].load(std::memory_order_acquire)) {
+        // Set-up, once per device, with that device current: in host code the
+        // array's name is only a host-side stand-in, so the kernels get the
+        // device address from the runtime.
+        std::lock_guard<std::mutex> lock(g_static_mutex);
+        if (!g_static_ready[dev].load(std::memory_order_relaxed)) {
+            void* p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_static_partials);
+            if (e != cudaSuccess) return e;
+            g_static_ptr[dev] = static_cast<double*>(p);
+            g_static_ready[dev].store(1, std::memory_order_release);
+        }
+    }
+    *out = g_static_ptr[dev];
+    *capacity = kStaticScratchDoubles;
+    return cudaSuccess;
 }
 
 // ------------------------------------------------------------------ dispatch

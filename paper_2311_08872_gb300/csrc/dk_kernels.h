@@ -65,6 +65,12 @@ cudaError_t launch_level(int n, bool coupled, const KArgs& a, int n_ctas, cudaSt
 cudaError_t launch_reduce(const double* partials, int n_slots, int slot_stride, double* out,
                           cudaStream_t stream);
 
+// Device address and size (doubles) of the statically allocated scratch used
+// by mlmc_dk_run_level_static; the first call on a device looks the address up
+// with cudaGetSymbolAddress (device must be current).
+constexpr size_t kStaticScratchDoubles = size_t(1) << 19;   // 4 MiB
+cudaError_t static_scratch(double** out, size_t* capacity);
+
 // Normals (and raw Philox words) of one fine step: z [n*n][2], raw [n*n/2][4].
 cudaError_t launch_noise(int n, uint32_t m, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1, float* z,
                          uint32_t* raw, cudaStream_t stream);

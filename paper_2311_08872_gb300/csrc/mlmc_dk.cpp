@@ -481,6 +481,52 @@ int mlmc_dk_run_level_dev(mlmc_dk_ctx* ctx, int32_t level, int32_t stream_tag, i
     return launch_batch(ctx, level, stream_tag, first_sample, n_samples, seed, sums_dev, samples_dev, st);
 }
 
+int mlmc_dk_run_level_static(const mlmc_dk_ctx* ctx, int32_t level, int32_t stream_tag, int64_t first_sample,
+                             int64_t n_samples, uint64_t seed, double* sums_dev, double* samples_dev,
+                             unsigned int* err_dev, void* cuda_stream) {
+    mlmc_dk_ctx* c = const_cast<mlmc_dk_ctx*>(ctx);   // only the error message is written
+    if (!ctx) return fail(nullptr, MLMC_DK_ERR_INVALID, "null context");
+    if (level < 0 || level > ctx->L_max || (stream_tag != 0 && stream_tag != 1) || first_sample < 0 ||
+        n_samples < 0 || !sums_dev || ((uintptr_t)sums_dev & 7) || ((uintptr_t)samples_dev & 7) ||
+        ((uintptr_t)err_dev & 3))
+        return fail(c, MLMC_DK_ERR_INVALID, "run_level_static: bad arguments");
+    const bool coupled = (stream_tag == 0) && level > 0;
+    const dk::VariantInfo& vi = coupled ? ctx->lv[level].vi_coupled : ctx->lv[level].vi_single;
+    if (!vi.supported)
+        return fail(c, MLMC_DK_ERR_UNSUPPORTED, "no kernel variant for n = " + std::to_string(ctx->lv[level].n));
+    cudaStream_t st = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : ctx->stream;
+    cudaError_t e;
+    if (n_samples == 0) {
+        e = cudaMemsetAsync(sums_dev, 0, sizeof(double) * ctx->stride, st);
+        return e == cudaSuccess ? MLMC_DK_OK : cuda_fail(c, e, "cudaMemsetAsync");
+    }
+    double* scratch = nullptr;
+    size_t capacity = 0;
+    if ((e = dk::static_scratch(&scratch, &capacity)) != cudaSuccess)
+        return cuda_fail(c, e, "static scratch set-up (cudaGetSymbolAddress)");
+    // As many sample slots as fit the static array: fewer resident slots than
+    // mlmc_dk_run_level_dev may use, the same per-sample arithmetic.
+    const int64_t per_group = vi.slots_per_cta;
+    const size_t usable = capacity - 32;   // the last 32 doubles hold the fallback error word
+    const int64_t fit_groups = (int64_t)(usable / ((size_t)ctx->stride * per_group));
+    if (fit_groups < 1)
+        return fail(c, MLMC_DK_ERR_INVALID, "run_level_static: one CTA's partial sums (" +
+                    std::to_string(per_group * ctx->stride) + " doubles) exceed the static scratch of " +
+                    std::to_string(usable) + " doubles");
+    const int64_t groups = std::min({(n_samples + per_group - 1) / per_group, (int64_t)(vi.max_ctas / vi.cluster),
+                                     fit_groups});
+    const int n_ctas = (int)(groups * vi.cluster);
+    const int n_slots = (int)(groups * per_group);
+    dk::KArgs a = make_args(c, level, stream_tag, coupled, first_sample, n_samples, seed, samples_dev);
+    a.partials = scratch;        // fully overwritten by the level kernel: nothing to clear
+    a.err = err_dev ? err_dev : reinterpret_cast<unsigned*>(scratch + (capacity - 1));
+    if ((e = dk::launch_level(ctx->lv[level].n, coupled, a, n_ctas, st)) != cudaSuccess)
+        return cuda_fail(c, e, "level kernel launch");
+    if ((e = dk::launch_reduce(scratch, n_slots, ctx->stride, sums_dev, st)) != cudaSuccess)
+        return cuda_fail(c, e, "reduce kernel launch");
+    return MLMC_DK_OK;
+}
+
 int mlmc_dk_plan(int32_t L, const int64_t* n, const double* s1, const double* s2, const double* cost, double eps,
                  int64_t* target, int32_t* converged) {
     if (L < 0 || L >= MLMC_DK_MAX_LEVELS || !n || !s1 || !s2 || !cost || !target || !converged || !(eps > 0))

@@ -109,6 +109,8 @@ def lib() -> ctypes.CDLL:
         L.mlmc_dk_num_quantities.argtypes = [vp]
         L.mlmc_dk_num_quantities.restype = ctypes.c_int32
         L.mlmc_dk_version.restype = ctypes.c_char_p
+        L.mlmc_dk_run_level_static.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
+                                               ctypes.c_int64, ctypes.c_uint64, vp, vp, vp, vp]
         L.mlmc_dk_noise_dev.argtypes = [ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
                                         ctypes.c_int32, ctypes.c_int32, vp, vp, vp]
         _LIB = L
@@ -225,6 +227,15 @@ class Context:
         _check(lib().mlmc_dk_run_level_dev(self._ctx, level, stream_tag, first, n_samples, seed,
                                            ctypes.c_void_p(sums_ptr), ctypes.c_void_p(samples_ptr or None),
                                            ctypes.c_void_p(stream or None)), self._ctx)
+
+    def run_level_static(self, level: int, stream_tag: int, first: int, n_samples: int, seed: int,
+                         sums_ptr: int, samples_ptr: int = 0, err_ptr: int = 0, stream: int = 0):
+        """As run_level_dev, with the scratch in the library's static device array
+        (no allocation; calls must not overlap on the GPU)."""
+        _check(lib().mlmc_dk_run_level_static(self._ctx, level, stream_tag, first, n_samples, seed,
+                                              ctypes.c_void_p(sums_ptr), ctypes.c_void_p(samples_ptr or None),
+                                              ctypes.c_void_p(err_ptr or None), ctypes.c_void_p(stream or None)),
+               self._ctx)
 
     def estimate(self, eps: float, relative: bool, seed: int) -> Result:
         r = Result()
