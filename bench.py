@@ -199,8 +199,9 @@ def run_ours(args, wl, rank, world, local_rank):
     seed0 = wl.seed + 1000003 * rank
 
     ctx = mlmc_dk.Context.from_workload(wl, stream=stream.cuda_stream)
+    tune_s = ctx.tune(repeats=1)          # autotuner: fastest kernel variant per level (outside timing)
+    choice = ctx.variants()
     info = [ctx.level_info(l) for l in range(wl.L_max + 1)]
-    out = {}
 
     # ---- a complete adaptive Algorithm 1 run, measured (at a looser eps than the
     #      workload's when the workload's eps would take longer than the bench allows)
@@ -282,7 +283,9 @@ def run_ours(args, wl, rank, world, local_rank):
     ops = alloc[dom] * (fine[dom] * XU_OPS_FINE + coarse[dom] * XU_OPS_COARSE) * args.steps
     achieved = ops / (level_ms[dom] * 1e-3)
     peak = XU_PER_CLK_PER_SM * SMS * SM_MAX_MHZ * 1e6
-    roofline = {"bound": "alu", "pipe": "XU (MUFU)", "kernel": f"level_kernel n={info[dom].n} coupled={dom > 0}",
+    roofline = {"bound": "alu", "pipe": "XU (MUFU)",
+                "kernel": f"level_kernel n={info[dom].n} C={info[dom].lane_cols} R={info[dom].lane_rows} "
+                          f"cluster={info[dom].cluster} coupled={dom > 0}",
                 "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gop/s", "frac": achieved / peak,
                 "traffic": None, "ops_per_fine_cell_step": XU_OPS_FINE,
                 "cell_steps_per_s": alloc[dom] * (fine[dom] + coarse[dom]) * args.steps / (level_ms[dom] * 1e-3),
@@ -328,6 +331,10 @@ def run_ours(args, wl, rank, world, local_rank):
             torch.cuda.synchronize()
             t = time.perf_counter()
             c2 = mlmc_dk.Context.from_workload(wl, stream=stream.cuda_stream)
+            for l, (vs, vc) in enumerate(choice):   # the tuned variants, as a user would reuse them
+                c2.set_variant(l, False, vs)
+                if l > 0:
+                    c2.set_variant(l, True, vc)
             est, d2h_k = 0.0, 0
             for l, m in enumerate(alloc):
                 if m > 0:
@@ -364,7 +371,10 @@ def run_ours(args, wl, rank, world, local_rank):
                    "T": wl.T, "N": wl.N, "mu": wl.mu, "eps_rel": wl.eps_rel, "alloc": alloc,
                    "sample_steps_per_step": sample_steps, "cell_steps_per_step": cell_steps,
                    "l2": "512 MiB buffer zeroed between timed steps, outside the step events",
-                   "parallelism": f"{world} independent rank(s), own seeds"},
+                   "parallelism": f"{world} independent rank(s), own seeds",
+                   "kernel_variants": [{"n": i.n, "C": i.lane_cols, "R": i.lane_rows, "cluster": i.cluster}
+                                       for i in info],
+                   "tune_s": tune_s},
         "cell_steps_per_s": world * cell_steps * args.steps / (total_ms * 1e-3),
         "gpu_launches": launches,
         "roofline": roofline,

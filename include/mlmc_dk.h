@@ -105,6 +105,9 @@ typedef struct {
     int64_t next_sample;    /* first sample id the next mlmc_dk_run_level call uses */
     int64_t h2d_bytes;      /* bytes mlmc_dk_init uploaded for all levels (pinned staging) */
     int32_t frac_bits;      /* S_l: the level's fixed-point state is rho 2^S_l */
+    int32_t n_variants;     /* kernel variants (lane-block shapes, cluster sizes) for this grid size */
+    int32_t variant_single, variant_coupled;  /* variants in use for the fine-only and the coupled kernel */
+    int32_t lane_cols, lane_rows, cluster;    /* the level's main kernel: C x R coarse cells per lane, cluster */
 } mlmc_dk_level_desc;
 
 /* Host-side moment sums of one quantity on one level (accumulated into). */
@@ -230,6 +233,20 @@ int mlmc_dk_run_level_static(const mlmc_dk_ctx* ctx, int32_t level, int32_t stre
  * Returns MLMC_DK_OK, MLMC_DK_NOT_CONVERGED (L_max reached) or an error. */
 int mlmc_dk_estimate(mlmc_dk_ctx* ctx, double eps, int32_t relative, uint64_t seed,
                      mlmc_dk_result* out);
+
+/* Choose kernel variant `variant` (0 .. n_variants-1, see mlmc_dk_level_info)
+ * for level `level`'s coupled (coupled = 1, level >= 1) or fine-only kernel.
+ * All variants compute the same fixed-point paths bit for bit (hence equal
+ * masses); the observables differ only by the order of their FP32 partial
+ * sums.  Variants differ in how many cells a lane owns and how many SMs share
+ * a sample. */
+int mlmc_dk_set_variant(mlmc_dk_ctx* ctx, int32_t level, int32_t coupled, int32_t variant);
+
+/* Autotuner: for every level and kernel with more than one variant, time each
+ * variant (CUDA events, `repeats` timed launches of two full waves of sample
+ * slots after a warm-up launch; sample ids from 0, results discarded) and keep
+ * the fastest per sample.  *seconds (optional) receives the tuning time. */
+int mlmc_dk_tune(mlmc_dk_ctx* ctx, int32_t repeats, double* seconds);
 
 /* Host-only planning step of Algorithm 1 for levels 0..L: from per-level
  * sample counts n[l], sums s1[l] = sum dP and s2[l] = sum dP^2 and costs

@@ -105,33 +105,35 @@ __device__ __forceinline__ void load_row_f(float (&dst)[N], const float* src) {
     }
 }
 
-// Store / load N consecutive (q, G1) pairs of an edge row to / from shared memory.
-template <int N>
-__device__ __forceinline__ void put_edge(int2* dst, const int32_t (&qv)[N], const int32_t (&gv)[N]) {
+// Store / load the N (q, G1) pairs of one lane's part of a band edge row.
+// Lane-interleaved layout: pair chunk k (columns 2k, 2k+1 of the lane) of lane
+// `lib` is int4 number k*LPB + lib of the row, so a warp's store or load of one
+// chunk is LPB consecutive 16-byte words (no bank conflicts).  N = 1 uses one
+// int2 per lane.
+template <int N, int LPB>
+__device__ __forceinline__ void put_edge(int2* row, int lib, const int32_t (&qv)[N], const int32_t (&gv)[N]) {
     if constexpr (N % 2 == 0) {
+        int4* r4 = reinterpret_cast<int4*>(row);
 #pragma unroll
-        for (int i = 0; i < N; i += 2)
-            *reinterpret_cast<int4*>(dst + i) = make_int4(qv[i], gv[i], qv[i + 1], gv[i + 1]);
+        for (int k = 0; k < N / 2; ++k) r4[k * LPB + lib] = make_int4(qv[2 * k], gv[2 * k], qv[2 * k + 1], gv[2 * k + 1]);
     } else {
-#pragma unroll
-        for (int i = 0; i < N; ++i) dst[i] = make_int2(qv[i], gv[i]);
+        static_assert(N == 1, "odd edge chunks other than 1 are not used");
+        row[lib] = make_int2(qv[0], gv[0]);
     }
 }
 
-template <int N>
-__device__ __forceinline__ void get_edge(const int2* src, int32_t (&qv)[N], int32_t (&gv)[N]) {
+template <int N, int LPB>
+__device__ __forceinline__ void get_edge(const int2* row, int lib, int32_t (&qv)[N], int32_t (&gv)[N]) {
     if constexpr (N % 2 == 0) {
+        const int4* r4 = reinterpret_cast<const int4*>(row);
 #pragma unroll
-        for (int i = 0; i < N; i += 2) {
-            const int4 v = *reinterpret_cast<const int4*>(src + i);
-            qv[i] = v.x; gv[i] = v.y; qv[i + 1] = v.z; gv[i + 1] = v.w;
+        for (int k = 0; k < N / 2; ++k) {
+            const int4 v = r4[k * LPB + lib];
+            qv[2 * k] = v.x; gv[2 * k] = v.y; qv[2 * k + 1] = v.z; gv[2 * k + 1] = v.w;
         }
     } else {
-#pragma unroll
-        for (int i = 0; i < N; ++i) {
-            const int2 v = src[i];
-            qv[i] = v.x; gv[i] = v.y;
-        }
+        const int2 v = row[lib];
+        qv[0] = v.x; gv[0] = v.y;
     }
 }
 
@@ -356,31 +358,29 @@ __global__ void __launch_bounds__(S::THREADS) level_kernel(const KArgs a) {
                 const int par = m & 1;
                 int2* const ftop = fx + ((par * 2 + 0) * BPC) * NF;
                 int2* const fbot = fx + ((par * 2 + 1) * BPC) * NF;
-                put_edge<FC>(ftop + bl * NF + col0, q[0], G1[0]);
-                put_edge<FC>(fbot + bl * NF + col0, q[FR - 1], G1[FR - 1]);
+                put_edge<FC, LPB>(ftop + bl * NF, lib, q[0], G1[0]);
+                put_edge<FC, LPB>(fbot + bl * NF, lib, q[FR - 1], G1[FR - 1]);
                 int2* const ctop = cx;
                 int2* const cbot = cx + BPC * NC;
                 if constexpr (CPL) {
                     if (cstep) {
-                        put_edge<C>(ctop + bl * NC + ccol0, qc[0], Gc1[0]);
-                        put_edge<C>(cbot + bl * NC + ccol0, qc[R - 1], Gc1[R - 1]);
+                        put_edge<C, LPB>(ctop + bl * NC, lib, qc[0], Gc1[0]);
+                        put_edge<C, LPB>(cbot + bl * NC, lib, qc[R - 1], Gc1[R - 1]);
                     }
                 }
                 block_or_cluster_sync<S>();
-                const int2* above = (bl > 0) ? fbot + (bl - 1) * NF + col0
-                                             : peer<S>(fbot + (BPC - 1) * NF + col0, (rank + CL - 1) % CL);
-                const int2* below = (bl + 1 < BPC) ? ftop + (bl + 1) * NF + col0
-                                                   : peer<S>(ftop + col0, (rank + 1) % CL);
-                get_edge<FC>(above, qU, gU);
-                get_edge<FC>(below, qD, gD);
+                const int2* above = (bl > 0) ? fbot + (bl - 1) * NF
+                                             : peer<S>(fbot + (BPC - 1) * NF, (rank + CL - 1) % CL);
+                const int2* below = (bl + 1 < BPC) ? ftop + (bl + 1) * NF : peer<S>(ftop, (rank + 1) % CL);
+                get_edge<FC, LPB>(above, lib, qU, gU);
+                get_edge<FC, LPB>(below, lib, qD, gD);
                 if constexpr (CPL) {
                     if (cstep) {
-                        const int2* cab = (bl > 0) ? cbot + (bl - 1) * NC + ccol0
-                                                   : peer<S>(cbot + (BPC - 1) * NC + ccol0, (rank + CL - 1) % CL);
-                        const int2* cbe = (bl + 1 < BPC) ? ctop + (bl + 1) * NC + ccol0
-                                                         : peer<S>(ctop + ccol0, (rank + 1) % CL);
-                        get_edge<C>(cab, cqU, cgU);
-                        get_edge<C>(cbe, cqD, cgD);
+                        const int2* cab = (bl > 0) ? cbot + (bl - 1) * NC
+                                                   : peer<S>(cbot + (BPC - 1) * NC, (rank + CL - 1) % CL);
+                        const int2* cbe = (bl + 1 < BPC) ? ctop + (bl + 1) * NC : peer<S>(ctop, (rank + 1) % CL);
+                        get_edge<C, LPB>(cab, lib, cqU, cgU);
+                        get_edge<C, LPB>(cbe, lib, cqD, cgD);
                     }
                 }
             }
@@ -682,38 +682,80 @@ struct Kern {
     }
 };
 
-// Variant per fine size n: (C, R, cluster).  See the header comment for the
-// geometry; every entry keeps the whole state in registers.
-#define DK_VARIANTS(X)            \
-    X(4, 1, 1, 1)                 \
-    X(8, 1, 1, 1)                 \
-    X(16, 1, 2, 1)                \
-    X(32, 2, 2, 1)                \
-    X(64, 2, 2, 1)                \
-    X(128, 2, 2, 2)               \
-    X(256, 4, 2, 8)
+// Kernel variants: fine size n, lane block C x R coarse cells (2R x 2C fine),
+// cluster size.  Every entry keeps the whole state in registers; the first
+// entry for each n is the default, the others are candidates for the tuner.
+#define DK_VARIANTS(X) \
+    X(4, 1, 1, 1)      \
+    X(8, 1, 1, 1)      \
+    X(16, 1, 2, 1)     \
+    X(16, 2, 2, 1)     \
+    X(16, 1, 1, 1)     \
+    X(32, 2, 2, 1)     \
+    X(32, 1, 2, 1)     \
+    X(32, 2, 1, 1)     \
+    X(64, 2, 2, 1)     \
+    X(64, 4, 2, 1)     \
+    X(64, 2, 1, 1)     \
+    X(64, 4, 1, 1)     \
+    X(128, 2, 2, 2)    \
+    X(128, 4, 1, 2)    \
+    X(128, 2, 1, 4)    \
+    X(256, 4, 2, 8)    \
+    X(256, 4, 1, 8)
 
-cudaError_t variant_info(int n, bool coupled, int stride, VariantInfo* out) {
-    *out = VariantInfo{};
-#define DK_INFO(NF, C, R, CL)                                                   \
-    if (n == NF) {                                                              \
-        return coupled ? Kern<Shape<NF, C, R, CL, true>>::info(stride, out)      \
-                       : Kern<Shape<NF, C, R, CL, false>>::info(stride, out);    \
-    }
-    DK_VARIANTS(DK_INFO)
-#undef DK_INFO
-    return cudaSuccess;   // supported = 0
+namespace {
+struct VariantEntry {
+    int n, C, R, CL;
+    cudaError_t (*info)(bool coupled, int stride, VariantInfo* vi);
+    cudaError_t (*launch)(bool coupled, const KArgs& a, int n_ctas, cudaStream_t st);
+};
+
+template <int NF, int C, int R, int CL>
+cudaError_t variant_info_fn(bool coupled, int stride, VariantInfo* vi) {
+    return coupled ? Kern<Shape<NF, C, R, CL, true>>::info(stride, vi)
+                   : Kern<Shape<NF, C, R, CL, false>>::info(stride, vi);
 }
 
-cudaError_t launch_level(int n, bool coupled, const KArgs& a, int n_ctas, cudaStream_t st) {
-#define DK_LAUNCH(NF, C, R, CL)                                                 \
-    if (n == NF) {                                                              \
-        return coupled ? Kern<Shape<NF, C, R, CL, true>>::launch(a, n_ctas, st)  \
-                       : Kern<Shape<NF, C, R, CL, false>>::launch(a, n_ctas, st);\
-    }
-    DK_VARIANTS(DK_LAUNCH)
-#undef DK_LAUNCH
-    return cudaErrorInvalidValue;
+template <int NF, int C, int R, int CL>
+cudaError_t variant_launch_fn(bool coupled, const KArgs& a, int n_ctas, cudaStream_t st) {
+    return coupled ? Kern<Shape<NF, C, R, CL, true>>::launch(a, n_ctas, st)
+                   : Kern<Shape<NF, C, R, CL, false>>::launch(a, n_ctas, st);
+}
+
+#define DK_ENTRY(NF, C, R, CL) {NF, C, R, CL, variant_info_fn<NF, C, R, CL>, variant_launch_fn<NF, C, R, CL>},
+const VariantEntry kVariants[] = {DK_VARIANTS(DK_ENTRY)};
+#undef DK_ENTRY
+constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+
+const VariantEntry* find_variant(int n, int idx) {
+    int k = 0;
+    for (int i = 0; i < kNumVariants; ++i)
+        if (kVariants[i].n == n && k++ == idx) return &kVariants[i];
+    return nullptr;
+}
+}  // namespace
+
+int variant_count(int n) {
+    int k = 0;
+    for (int i = 0; i < kNumVariants; ++i) k += kVariants[i].n == n;
+    return k;
+}
+
+cudaError_t variant_info(int n, bool coupled, int stride, int idx, VariantInfo* out) {
+    *out = VariantInfo{};
+    const VariantEntry* v = find_variant(n, idx);
+    if (!v) return cudaSuccess;   // supported = 0
+    cudaError_t e = v->info(coupled, stride, out);
+    out->C = v->C;
+    out->R = v->R;
+    return e;
+}
+
+cudaError_t launch_level(int n, bool coupled, int idx, const KArgs& a, int n_ctas, cudaStream_t st) {
+    const VariantEntry* v = find_variant(n, idx);
+    if (!v) return cudaErrorInvalidValue;
+    return v->launch(coupled, a, n_ctas, st);
 }
 
 cudaError_t launch_reduce(const double* partials, int n_slots, int slot_stride, double* out, cudaStream_t st) {

@@ -50,15 +50,19 @@ struct VariantInfo {
     int slots_per_cta;      // samples in flight per CTA (1/cluster for clusters)
     size_t smem;            // dynamic shared memory per CTA
     int max_ctas;           // resident CTAs on the whole GPU
+    int C, R;               // lane block: C x R coarse cells (2R x 2C fine)
 };
 
-// Query (and prepare: attributes, occupancy) the variant for fine size n;
-// supported = 0 when no variant exists for n.
-cudaError_t variant_info(int n, bool coupled, int slot_stride, VariantInfo* out);
+// Number of kernel variants (lane-block shapes / cluster sizes) for fine size n.
+int variant_count(int n);
 
-// Launch one batch; n_slots = number of sample slots actually used
-// (returned), partials must hold n_slots * slot_stride doubles.
-cudaError_t launch_level(int n, bool coupled, const KArgs& a, int n_ctas, cudaStream_t stream);
+// Query (and prepare: attributes, occupancy) variant `idx` for fine size n;
+// supported = 0 when it does not exist.
+cudaError_t variant_info(int n, bool coupled, int slot_stride, int idx, VariantInfo* out);
+
+// Launch one batch with variant `idx` on n_ctas CTAs; partials must hold
+// (n_ctas / cluster) * slots_per_cta * slot_stride doubles.
+cudaError_t launch_level(int n, bool coupled, int idx, const KArgs& a, int n_ctas, cudaStream_t stream);
 
 // Deterministic fixed-order reduction of the per-slot partials into
 // out[slot_stride]: entry 1 is a max, all others sums.

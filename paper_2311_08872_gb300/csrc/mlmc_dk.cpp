@@ -32,7 +32,13 @@ struct LevelTab {
     int32_t* d_q0 = nullptr;
     int32_t* d_qbar = nullptr;
     float* d_phi = nullptr;
-    dk::VariantInfo vi_coupled{}, vi_single{};
+    std::vector<dk::VariantInfo> vis[2];   // kernel variants: [0] fine path only, [1] coupled pair
+    int sel[2] = {0, 0};                   // variant in use for each mode
+    const dk::VariantInfo& vi(bool coupled) const {
+        static const dk::VariantInfo none{};
+        const auto& v = vis[coupled ? 1 : 0];
+        return v.empty() ? none : v[sel[coupled ? 1 : 0]];
+    }
 };
 
 }  // namespace
@@ -167,7 +173,7 @@ dk::KArgs make_args(mlmc_dk_ctx* c, int level, int stream_tag, bool coupled, int
 int launch_batch(mlmc_dk_ctx* c, int level, int stream_tag, int64_t first, int64_t count, uint64_t seed,
                  double* sums_dev, double* samples_dev, cudaStream_t st) {
     const bool coupled = (stream_tag == 0) && level > 0;
-    const dk::VariantInfo& vi = coupled ? c->lv[level].vi_coupled : c->lv[level].vi_single;
+    const dk::VariantInfo& vi = c->lv[level].vi(coupled);
     if (!vi.supported)
         return fail(c, MLMC_DK_ERR_UNSUPPORTED, "no kernel variant for n = " + std::to_string(c->lv[level].n));
     cudaError_t e;
@@ -183,7 +189,8 @@ int launch_batch(mlmc_dk_ctx* c, int level, int stream_tag, int64_t first, int64
     const int n_slots = (int)(groups * per_cluster);
     if ((size_t)n_slots * c->stride > c->partials_cap) return fail(c, MLMC_DK_ERR_INVALID, "scratch too small");
     dk::KArgs a = make_args(c, level, stream_tag, coupled, first, count, seed, samples_dev);
-    if ((e = dk::launch_level(c->lv[level].n, coupled, a, n_ctas, st)) != cudaSuccess)
+    if ((e = dk::launch_level(c->lv[level].n, coupled, c->lv[level].sel[coupled ? 1 : 0], a, n_ctas, st)) !=
+        cudaSuccess)
         return cuda_fail(c, e, "level kernel launch");
     if ((e = dk::launch_reduce(c->d_partials, n_slots, c->stride, sums_dev, st)) != cudaSuccess)
         return cuda_fail(c, e, "reduce kernel launch");
@@ -410,14 +417,20 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
         }
         cudaFreeHost(stage);
         c->h2d_bytes += (int64_t)bytes;
-        if ((e = dk::variant_info(t.n, false, c->stride, &t.vi_single)) != cudaSuccess ||
-            (l > 0 && (e = dk::variant_info(t.n, true, c->stride, &t.vi_coupled)) != cudaSuccess)) {
-            mlmc_dk_free(c);
-            return cuda_fail(nullptr, e, "kernel variant setup");
+        const int nv = dk::variant_count(t.n);
+        for (int mode = 0; mode < 2; ++mode) {
+            if (mode == 1 && l == 0) continue;
+            for (int v = 0; v < nv; ++v) {
+                dk::VariantInfo vi{};
+                if ((e = dk::variant_info(t.n, mode == 1, c->stride, v, &vi)) != cudaSuccess) {
+                    mlmc_dk_free(c);
+                    return cuda_fail(nullptr, e, "kernel variant setup");
+                }
+                t.vis[mode].push_back(vi);
+                if (vi.supported)
+                    partials_need = std::max(partials_need, (size_t)(vi.max_ctas / vi.cluster) * vi.slots_per_cta * c->stride);
+            }
         }
-        for (const dk::VariantInfo* vi : {&t.vi_single, &t.vi_coupled})
-            if (vi->supported)
-                partials_need = std::max(partials_need, (size_t)(vi->max_ctas / vi->cluster) * vi->slots_per_cta * c->stride);
     }
     if ((e = cudaMalloc(&c->d_partials, sizeof(double) * std::max<size_t>(partials_need, 1))) != cudaSuccess ||
         (e = cudaMalloc(&c->d_sums, sizeof(double) * c->stride)) != cudaSuccess ||
@@ -459,6 +472,13 @@ int mlmc_dk_level_info(const mlmc_dk_ctx* ctx, int32_t level, mlmc_dk_level_desc
     out->next_sample = ctx->next_id[0][level];
     out->h2d_bytes = ctx->h2d_bytes;
     out->frac_bits = t.S;
+    out->n_variants = (int32_t)t.vis[0].size();
+    out->variant_single = t.sel[0];
+    out->variant_coupled = t.sel[1];
+    const dk::VariantInfo& vs = t.vi(level > 0);
+    out->lane_cols = vs.C;
+    out->lane_rows = vs.R;
+    out->cluster = vs.cluster;
     return MLMC_DK_OK;
 }
 
@@ -491,7 +511,7 @@ int mlmc_dk_run_level_static(const mlmc_dk_ctx* ctx, int32_t level, int32_t stre
         ((uintptr_t)err_dev & 3))
         return fail(c, MLMC_DK_ERR_INVALID, "run_level_static: bad arguments");
     const bool coupled = (stream_tag == 0) && level > 0;
-    const dk::VariantInfo& vi = coupled ? ctx->lv[level].vi_coupled : ctx->lv[level].vi_single;
+    const dk::VariantInfo& vi = ctx->lv[level].vi(coupled);
     if (!vi.supported)
         return fail(c, MLMC_DK_ERR_UNSUPPORTED, "no kernel variant for n = " + std::to_string(ctx->lv[level].n));
     cudaStream_t st = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : ctx->stream;
@@ -520,10 +540,66 @@ int mlmc_dk_run_level_static(const mlmc_dk_ctx* ctx, int32_t level, int32_t stre
     dk::KArgs a = make_args(c, level, stream_tag, coupled, first_sample, n_samples, seed, samples_dev);
     a.partials = scratch;        // fully overwritten by the level kernel: nothing to clear
     a.err = err_dev ? err_dev : reinterpret_cast<unsigned*>(scratch + (capacity - 1));
-    if ((e = dk::launch_level(ctx->lv[level].n, coupled, a, n_ctas, st)) != cudaSuccess)
+    if ((e = dk::launch_level(ctx->lv[level].n, coupled, ctx->lv[level].sel[coupled ? 1 : 0], a, n_ctas, st)) !=
+        cudaSuccess)
         return cuda_fail(c, e, "level kernel launch");
     if ((e = dk::launch_reduce(scratch, n_slots, ctx->stride, sums_dev, st)) != cudaSuccess)
         return cuda_fail(c, e, "reduce kernel launch");
+    return MLMC_DK_OK;
+}
+
+int mlmc_dk_set_variant(mlmc_dk_ctx* ctx, int32_t level, int32_t coupled, int32_t variant) {
+    if (!ctx || level < 0 || level > ctx->L_max || (coupled && level == 0))
+        return fail(ctx, MLMC_DK_ERR_INVALID, "set_variant: bad level");
+    LevelTab& t = ctx->lv[level];
+    const int mode = coupled ? 1 : 0;
+    if (variant < 0 || variant >= (int)t.vis[mode].size() || !t.vis[mode][variant].supported)
+        return fail(ctx, MLMC_DK_ERR_INVALID, "set_variant: no such variant");
+    t.sel[mode] = variant;
+    return MLMC_DK_OK;
+}
+
+int mlmc_dk_tune(mlmc_dk_ctx* ctx, int32_t repeats, double* seconds) {
+    if (!ctx) return fail(nullptr, MLMC_DK_ERR_INVALID, "null context");
+    const auto t0 = std::chrono::steady_clock::now();
+    repeats = std::max(1, repeats);
+    cudaError_t e;
+    for (int l = 0; l <= ctx->L_max; ++l) {
+        LevelTab& t = ctx->lv[l];
+        for (int mode = 0; mode < 2; ++mode) {
+            if (t.vis[mode].size() < 2) continue;
+            double best = 1e300;
+            int best_v = t.sel[mode];
+            for (int v = 0; v < (int)t.vis[mode].size(); ++v) {
+                const dk::VariantInfo& vi = t.vis[mode][v];
+                if (!vi.supported) continue;
+                t.sel[mode] = v;
+                // two full waves of resident sample slots
+                const int64_t count = 2LL * (vi.max_ctas / vi.cluster) * vi.slots_per_cta;
+                double ms_min = 1e300;
+                for (int r = 0; r < repeats + 1; ++r) {
+                    if ((e = cudaEventRecord(ctx->ev0, ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "tune");
+                    int rc = launch_batch(ctx, l, mode == 1 ? 0 : 1, 0, count, 0x7475, ctx->d_sums, nullptr, ctx->stream);
+                    if (rc != MLMC_DK_OK) return rc;
+                    if ((e = cudaEventRecord(ctx->ev1, ctx->stream)) != cudaSuccess ||
+                        (e = cudaEventSynchronize(ctx->ev1)) != cudaSuccess)
+                        return cuda_fail(ctx, e, "tune");
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+                    if (r > 0) ms_min = std::min(ms_min, (double)ms);   // the first run warms up
+                }
+                const double per_sample = ms_min / (double)count;
+                if (per_sample < best) {
+                    best = per_sample;
+                    best_v = v;
+                }
+            }
+            t.sel[mode] = best_v;
+        }
+    }
+    int rc = check_device_error(ctx);
+    if (rc != MLMC_DK_OK) return rc;
+    if (seconds) *seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return MLMC_DK_OK;
 }
 

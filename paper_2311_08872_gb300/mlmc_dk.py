@@ -52,6 +52,8 @@ class LevelDesc(ctypes.Structure):
         ("ybar_f", ctypes.c_double * MAX_OBS), ("ybar_c", ctypes.c_double * MAX_OBS),
         ("cost", ctypes.c_double), ("cost_mc", ctypes.c_double),
         ("next_sample", ctypes.c_int64), ("h2d_bytes", ctypes.c_int64), ("frac_bits", ctypes.c_int32),
+        ("n_variants", ctypes.c_int32), ("variant_single", ctypes.c_int32), ("variant_coupled", ctypes.c_int32),
+        ("lane_cols", ctypes.c_int32), ("lane_rows", ctypes.c_int32), ("cluster", ctypes.c_int32),
     ]
 
 
@@ -111,6 +113,8 @@ def lib() -> ctypes.CDLL:
         L.mlmc_dk_version.restype = ctypes.c_char_p
         L.mlmc_dk_run_level_static.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
                                                ctypes.c_int64, ctypes.c_uint64, vp, vp, vp, vp]
+        L.mlmc_dk_set_variant.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+        L.mlmc_dk_tune.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]
         L.mlmc_dk_noise_dev.argtypes = [ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
                                         ctypes.c_int32, ctypes.c_int32, vp, vp, vp]
         _LIB = L
@@ -236,6 +240,19 @@ class Context:
                                               ctypes.c_void_p(sums_ptr), ctypes.c_void_p(samples_ptr or None),
                                               ctypes.c_void_p(err_ptr or None), ctypes.c_void_p(stream or None)),
                self._ctx)
+
+    def set_variant(self, level: int, coupled: bool, variant: int):
+        _check(lib().mlmc_dk_set_variant(self._ctx, level, int(coupled), variant), self._ctx)
+
+    def tune(self, repeats: int = 1) -> float:
+        """Time every kernel variant per level and keep the fastest; returns seconds spent."""
+        t = ctypes.c_double(0.0)
+        _check(lib().mlmc_dk_tune(self._ctx, repeats, ctypes.byref(t)), self._ctx)
+        return t.value
+
+    def variants(self):
+        """[(variant_single, variant_coupled)] per level."""
+        return [(d.variant_single, d.variant_coupled) for d in (self.level_info(l) for l in range(self.L_max + 1))]
 
     def estimate(self, eps: float, relative: bool, seed: int) -> Result:
         r = Result()

@@ -263,3 +263,43 @@ def test_range_overflow_is_reported_not_faulted(dk):
     finally:
         ctx.close()
     check_level(dk, W.get("mc32"), 0, 1, 0, 8, seed=0)
+
+
+# ------------------------------------------------------------- kernel variants
+@pytest.mark.parametrize("name,level", [("mlmc16_256", 0), ("mlmc16_256", 1), ("mlmc16_256", 2),
+                                        ("mlmc16_256", 3), ("mlmc16_256", 4)])
+def test_kernel_variants_agree(dk, name, level):
+    """Every lane-block shape / cluster size computes the same fixed-point paths:
+    identical masses, observables equal up to FP32 partial-sum order."""
+    wl = W.get(name)
+    ctx = dk.Context.from_workload(wl)
+    try:
+        info = ctx.level_info(level)
+        count = {0: 300, 1: 200, 2: 40, 3: 8, 4: 3}[level]
+        base = None
+        for mode in ((0, 1) if level > 0 else (0,)):
+            coupled = mode == 0 and level > 0
+            for v in range(info.n_variants):
+                ctx.set_variant(level, coupled, v)
+                _, samp = gpu_samples(ctx, dk, level, mode, 5, count, seed=3)
+                if v == 0:
+                    base = samp
+                    continue
+                K = ctx.n_obs
+                assert np.array_equal(samp[:, 2 * K:], base[:, 2 * K:])          # masses
+                scale = np.sqrt(np.mean(base[:, :2 * K] ** 2, axis=0)) + 1e-300
+                assert np.all(np.abs(samp[:, :2 * K] - base[:, :2 * K]) <= 1e-6 * scale), (mode, v)
+    finally:
+        ctx.close()
+
+
+def test_tuner_picks_supported_variants(dk):
+    wl = W.get("mlmc16_256").with_(L_max=3)
+    with dk.Context.from_workload(wl) as ctx:
+        secs = ctx.tune(repeats=1)
+        assert secs > 0
+        for l, (vs, vc) in enumerate(ctx.variants()):
+            n = ctx.level_info(l).n_variants
+            assert 0 <= vs < n and 0 <= vc < n
+        check = ctx.run_level(2, 64, seed=1)[0]
+        assert check.n == 64 and check.max_mass_err == 0.0
