@@ -224,17 +224,12 @@ def run_ours(args, wl, rank, world, local_rank):
     sums = torch.zeros(wl.L_max + 1, mlmc_dk.sums_len(nq), dtype=torch.float64, device=dev)
     host = torch.zeros_like(sums, device="cpu").pin_memory()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in alloc]
     step_ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
 
     def step(seed):
+        # all levels concurrently: one CUDA-graph launch of the multi-level batch
         step_ev[0].record(stream)
-        for l, m in enumerate(alloc):
-            if m <= 0:
-                continue
-            ev[l][0].record(stream)
-            ctx.run_level_dev(l, 0, 0, m, seed, sums[l].data_ptr(), 0, stream.cuda_stream)
-            ev[l][1].record(stream)
+        ctx.run_batch_dev(alloc, 0, seed, sums.data_ptr(), stream.cuda_stream)
         host.copy_(sums, non_blocking=True)
         step_ev[1].record(stream)
         stream.synchronize()
@@ -262,9 +257,9 @@ def run_ours(args, wl, rank, world, local_rank):
         flush.zero_()                      # evict L2 between steps (outside the step events)
         last = step(seed0 + 101 + k)
         step_ms.append(step_ev[0].elapsed_time(step_ev[1]))
-        for l, m in enumerate(alloc):
-            if m > 0:
-                level_ms[l] += ev[l][0].elapsed_time(ev[l][1])
+        for l, t in enumerate(ctx.batch_level_ms()):   # CUDA events on each level's stream in the graph
+            level_ms[l] += t
+            if alloc[l] > 0:
                 launches += 2
     torch.cuda.synchronize()
     if world > 1:
@@ -279,6 +274,8 @@ def run_ours(args, wl, rank, world, local_rank):
 
     # ---- roofline of the dominant kernel (the level kernel of the costliest level)
     dom = max(range(len(alloc)), key=lambda l: level_ms[l])
+    if level_ms[dom] <= 0:
+        raise SystemExit("no per-level kernel times from the batch")
     lv, fine, coarse = level_costs(wl)
     ops = alloc[dom] * (fine[dom] * XU_OPS_FINE + coarse[dom] * XU_OPS_COARSE) * args.steps
     achieved = ops / (level_ms[dom] * 1e-3)
@@ -289,22 +286,26 @@ def run_ours(args, wl, rank, world, local_rank):
                 "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gop/s", "frac": achieved / peak,
                 "traffic": None, "ops_per_fine_cell_step": XU_OPS_FINE,
                 "cell_steps_per_s": alloc[dom] * (fine[dom] + coarse[dom]) * args.steps / (level_ms[dom] * 1e-3),
-                "level_ms_per_step": [x / args.steps for x in level_ms]}
+                "level_ms_per_step": [x / args.steps for x in level_ms],
+                "note": "levels run concurrently in one CUDA graph; each level's time is its own stream's span"}
 
     # ---- time to the workload's eps, MLMC against plain MC on the finest level.
-    # From the timed batch: V_l = Var[P_l - P_{l-1}] and the device seconds per
-    # sample t_l give the eps-optimal MLMC time 2 eps^-2 (sum_l sqrt(V_l t_l))^2
-    # (Eq. opt_M_ell with C_l = t_l); plain MC needs 2 Var[P_L] / eps^2 samples
-    # of level L, timed separately below.
+    # From the timed batch: V_l = Var[P_l - P_{l-1}]; the eps-optimal cost in
+    # cell-steps is 2 eps^-2 (sum_l sqrt(V_l C_l))^2 (Eq. opt_M_ell with C_l the
+    # cell-steps of one coupled sample, as Algorithm 1 uses), timed at the
+    # batch's measured cell-step rate; plain MC needs 2 Var[P_L] / eps^2
+    # samples of level L, timed separately below.
     est, _, s = last
     Ls = max(l for l, m in enumerate(alloc) if m > 0)
-    V, tsec = [], []
+    V, C = [], []
     for l, m in enumerate(alloc):
         if m > 0:
             V.append(max(0.0, (s[l, 3] - s[l, 2] ** 2 / m) / (m - 1)))
-            tsec.append(level_ms[l] * 1e-3 / (args.steps * m))
+            C.append(fine[l] + coarse[l])
     eps_abs = wl.eps_rel * abs(est)
-    t_mlmc = 2.0 / eps_abs ** 2 * sum(math.sqrt(v * t) for v, t in zip(V, tsec)) ** 2
+    cost_opt = 2.0 / eps_abs ** 2 * sum(math.sqrt(v * c) for v, c in zip(V, C)) ** 2
+    rate = cell_steps * args.steps / (sum(step_ms) * 1e-3)
+    t_mlmc = cost_opt / rate
     mL = alloc[Ls]
     var_pL = max(0.0, (s[Ls, 7] - s[Ls, 6] ** 2 / mL) / (mL - 1))
     n_mc = int(max(32, min(20000, 2.0e11 / fine[Ls])))
@@ -318,9 +319,10 @@ def run_ours(args, wl, rank, world, local_rank):
     m_mc = math.ceil(2.0 * var_pL / eps_abs ** 2)
     mc = {"level": Ls, "samples": m_mc, "s_per_sample": per, "s": m_mc * per, "extrapolated": True,
           "measured_samples": n_mc, "var_P_L": var_pL}
-    to_eps = {"eps_rel": wl.eps_rel, "eps_abs": eps_abs, "estimate": est, "V": V, "s_per_sample": tsec,
-              "mlmc_s": t_mlmc, "mc_s": m_mc * per, "extrapolated": True,
-              "how": "eps-optimal allocation from the timed batch's V_l and measured per-sample device time"}
+    to_eps = {"eps_rel": wl.eps_rel, "eps_abs": eps_abs, "estimate": est, "V": V, "cost_cell_steps": cost_opt,
+              "batch_cell_steps_per_s": rate, "mlmc_s": t_mlmc, "mc_s": m_mc * per, "extrapolated": True,
+              "how": "eps-optimal cost from the timed batch's V_l at its measured cell-step rate; "
+                     "plain MC from 2 Var[P_L]/eps^2 samples at the measured MC time per sample"}
 
     # ---- end to end through the public API with host buffers
     e2e = None
@@ -335,12 +337,9 @@ def run_ours(args, wl, rank, world, local_rank):
                 c2.set_variant(l, False, vs)
                 if l > 0:
                     c2.set_variant(l, True, vc)
-            est, d2h_k = 0.0, 0
-            for l, m in enumerate(alloc):
-                if m > 0:
-                    s = c2.run_level(l, m, seed0 + 101 + k)[0]
-                    est += s.dp1 / s.n
-                    d2h_k += s.d2h_bytes
+            res = c2.run_batch(alloc, seed0 + 101 + k)      # host sums of every level
+            est = sum(res[l][0].dp1 / res[l][0].n for l, m in enumerate(alloc) if m > 0)
+            d2h_k = 8 * mlmc_dk.sums_len(nq) * len(alloc) + 4
             h2d_k = c2.level_info(0).h2d_bytes
             c2.close()
             torch.cuda.synchronize()
@@ -353,7 +352,7 @@ def run_ours(args, wl, rank, world, local_rank):
             tot = float(t.item())
         e2e = {"value": world * sample_steps * args.steps / tot, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * tot / args.steps,
-               "what": "mlmc_dk_init (FFT mean fields + pinned uploads) + mlmc_dk_run_level per level + free"}
+               "what": "mlmc_dk_init (FFT mean fields + pinned uploads) + mlmc_dk_run_batch (host sums) + free"}
     else:
         ctx.close()
 

@@ -196,6 +196,30 @@ int mlmc_dk_run_level_dev(mlmc_dk_ctx* ctx, int32_t level, int32_t stream_tag,
                           int64_t first_sample, int64_t n_samples, uint64_t seed,
                           double* sums_dev, double* samples_dev, void* cuda_stream);
 
+/* Multi-level batch: counts[l] coupled samples of every level l = 0..L_max
+ * (0 skips the level), sample ids first_sample.. on every level, under
+ * `seed`.  The levels run concurrently, each on its own stream and scratch,
+ * finest level first with the most urgent launch priority so that its
+ * thread-block clusters are placed before the coarser levels fill the SMs the
+ * clusters leave free; the whole fork/join is captured into a CUDA graph and
+ * replayed (re-instantiated only when the batch's shape changes).  Writes
+ * sums_dev[l * (2 + n_quant*MLMC_DK_NSUM) ...] for every level in the layout of
+ * mlmc_dk_run_level_dev (zeros for skipped levels).  Asynchronous on
+ * cuda_stream (NULL: the context's stream); does not touch next_sample; must
+ * not be called while cuda_stream is being captured. */
+int mlmc_dk_run_batch_dev(mlmc_dk_ctx* ctx, const int64_t* counts, int64_t first_sample, uint64_t seed,
+                          double* sums_dev, void* cuda_stream);
+
+/* Device time (ms) of each level's kernels in the last completed multi-level
+ * batch, from CUDA events recorded on that level's stream inside the graph
+ * (ms[0..L_max]; 0 for levels the batch skipped or never ran). */
+int mlmc_dk_batch_level_ms(mlmc_dk_ctx* ctx, double* ms);
+
+/* Host form of the multi-level batch: ids start at the largest next_sample
+ * over the levels (then next_sample = that + counts[l] on every level run);
+ * sums[l * n_quant + q] receives level l, quantity q.  Synchronous. */
+int mlmc_dk_run_batch(mlmc_dk_ctx* ctx, const int64_t* counts, uint64_t seed, mlmc_dk_level_sums* sums);
+
 /* Same batch as mlmc_dk_run_level_dev, for callers that must not allocate
  * device memory when they run it: processes that hand out all of their GPU
  * memory from a pool reserved at start-up and may not allocate afterwards,

@@ -663,21 +663,28 @@ struct Kern {
         return vi->max_ctas > 0 ? cudaSuccess : cudaErrorInvalidConfiguration;
     }
 
-    static cudaError_t launch(const KArgs& a, int n_ctas, cudaStream_t st) {
+    static cudaError_t launch(const KArgs& a, int n_ctas, cudaStream_t st, int priority) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(n_ctas);
         cfg.blockDim = dim3(S::THREADS);
         cfg.dynamicSmemBytes = smem_bytes(a.slot_stride);
         cfg.stream = st;
-        cudaLaunchAttribute at[1];
+        cudaLaunchAttribute at[2];
+        int na = 0;
         if (S::CL > 1) {
-            at[0].id = cudaLaunchAttributeClusterDimension;
-            at[0].val.clusterDim.x = S::CL;
-            at[0].val.clusterDim.y = 1;
-            at[0].val.clusterDim.z = 1;
-            cfg.attrs = at;
-            cfg.numAttrs = 1;
+            at[na].id = cudaLaunchAttributeClusterDimension;
+            at[na].val.clusterDim.x = S::CL;
+            at[na].val.clusterDim.y = 1;
+            at[na].val.clusterDim.z = 1;
+            ++na;
         }
+        if (priority != 0) {
+            at[na].id = cudaLaunchAttributePriority;
+            at[na].val.priority = priority;
+            ++na;
+        }
+        cfg.attrs = na ? at : nullptr;
+        cfg.numAttrs = na;
         return cudaLaunchKernelEx(&cfg, level_kernel<S>, a);
     }
 };
@@ -708,7 +715,7 @@ namespace {
 struct VariantEntry {
     int n, C, R, CL;
     cudaError_t (*info)(bool coupled, int stride, VariantInfo* vi);
-    cudaError_t (*launch)(bool coupled, const KArgs& a, int n_ctas, cudaStream_t st);
+    cudaError_t (*launch)(bool coupled, const KArgs& a, int n_ctas, cudaStream_t st, int priority);
 };
 
 template <int NF, int C, int R, int CL>
@@ -718,9 +725,9 @@ cudaError_t variant_info_fn(bool coupled, int stride, VariantInfo* vi) {
 }
 
 template <int NF, int C, int R, int CL>
-cudaError_t variant_launch_fn(bool coupled, const KArgs& a, int n_ctas, cudaStream_t st) {
-    return coupled ? Kern<Shape<NF, C, R, CL, true>>::launch(a, n_ctas, st)
-                   : Kern<Shape<NF, C, R, CL, false>>::launch(a, n_ctas, st);
+cudaError_t variant_launch_fn(bool coupled, const KArgs& a, int n_ctas, cudaStream_t st, int priority) {
+    return coupled ? Kern<Shape<NF, C, R, CL, true>>::launch(a, n_ctas, st, priority)
+                   : Kern<Shape<NF, C, R, CL, false>>::launch(a, n_ctas, st, priority);
 }
 
 #define DK_ENTRY(NF, C, R, CL) {NF, C, R, CL, variant_info_fn<NF, C, R, CL>, variant_launch_fn<NF, C, R, CL>},
@@ -752,10 +759,10 @@ cudaError_t variant_info(int n, bool coupled, int stride, int idx, VariantInfo* 
     return e;
 }
 
-cudaError_t launch_level(int n, bool coupled, int idx, const KArgs& a, int n_ctas, cudaStream_t st) {
+cudaError_t launch_level(int n, bool coupled, int idx, const KArgs& a, int n_ctas, cudaStream_t st, int priority) {
     const VariantEntry* v = find_variant(n, idx);
     if (!v) return cudaErrorInvalidValue;
-    return v->launch(coupled, a, n_ctas, st);
+    return v->launch(coupled, a, n_ctas, st, priority);
 }
 
 cudaError_t launch_reduce(const double* partials, int n_slots, int slot_stride, double* out, cudaStream_t st) {

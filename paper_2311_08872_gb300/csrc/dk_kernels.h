@@ -62,7 +62,10 @@ cudaError_t variant_info(int n, bool coupled, int slot_stride, int idx, VariantI
 
 // Launch one batch with variant `idx` on n_ctas CTAs; partials must hold
 // (n_ctas / cluster) * slots_per_cta * slot_stride doubles.
-cudaError_t launch_level(int n, bool coupled, int idx, const KArgs& a, int n_ctas, cudaStream_t stream);
+// `priority` (0: none) is passed as the launch's scheduling priority (lower
+// numbers are more urgent, as for streams).
+cudaError_t launch_level(int n, bool coupled, int idx, const KArgs& a, int n_ctas, cudaStream_t stream,
+                         int priority = 0);
 
 // Deterministic fixed-order reduction of the per-slot partials into
 // out[slot_stride]: entry 1 is a max, all others sums.

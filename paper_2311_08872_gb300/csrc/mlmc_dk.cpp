@@ -58,6 +58,19 @@ struct mlmc_dk_ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<int64_t> next_id[2];
     std::string err;
+    // multi-level batch: one stream and one scratch buffer per level, the
+    // captured CUDA graph of the last batch shape
+    std::vector<cudaStream_t> lstream;
+    std::vector<double*> d_lpart;
+    std::vector<size_t> lpart_cap;
+    std::vector<int> lprio;
+    cudaStream_t cap_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr;
+    std::vector<cudaEvent_t> ev_join;
+    std::vector<cudaEvent_t> ev_lb, ev_le;   // timing of each level inside the batch
+    cudaGraphExec_t gexec = nullptr;
+    double* d_bsums = nullptr;        // device sums of mlmc_dk_run_batch
+    double* h_bsums = nullptr;        // pinned host copy
 };
 
 namespace {
@@ -169,9 +182,21 @@ dk::KArgs make_args(mlmc_dk_ctx* c, int level, int stream_tag, bool coupled, int
     return a;
 }
 
+// Launch one batch with the given scratch and reduce it into sums_dev.
+int launch_batch_into(mlmc_dk_ctx* c, int level, int stream_tag, int64_t first, int64_t count, uint64_t seed,
+                      double* sums_dev, double* samples_dev, cudaStream_t st, double* partials, size_t cap,
+                      int priority);
+
 // Launch one batch and reduce it into sums_dev (device, stride doubles).
 int launch_batch(mlmc_dk_ctx* c, int level, int stream_tag, int64_t first, int64_t count, uint64_t seed,
                  double* sums_dev, double* samples_dev, cudaStream_t st) {
+    return launch_batch_into(c, level, stream_tag, first, count, seed, sums_dev, samples_dev, st, c->d_partials,
+                             c->partials_cap, 0);
+}
+
+int launch_batch_into(mlmc_dk_ctx* c, int level, int stream_tag, int64_t first, int64_t count, uint64_t seed,
+                      double* sums_dev, double* samples_dev, cudaStream_t st, double* partials, size_t cap,
+                      int priority) {
     const bool coupled = (stream_tag == 0) && level > 0;
     const dk::VariantInfo& vi = c->lv[level].vi(coupled);
     if (!vi.supported)
@@ -187,12 +212,13 @@ int launch_batch(mlmc_dk_ctx* c, int level, int stream_tag, int64_t first, int64
     const int64_t groups = std::min(want_groups, max_groups);
     const int n_ctas = (int)(groups * vi.cluster);
     const int n_slots = (int)(groups * per_cluster);
-    if ((size_t)n_slots * c->stride > c->partials_cap) return fail(c, MLMC_DK_ERR_INVALID, "scratch too small");
+    if ((size_t)n_slots * c->stride > cap) return fail(c, MLMC_DK_ERR_INVALID, "scratch too small");
     dk::KArgs a = make_args(c, level, stream_tag, coupled, first, count, seed, samples_dev);
-    if ((e = dk::launch_level(c->lv[level].n, coupled, c->lv[level].sel[coupled ? 1 : 0], a, n_ctas, st)) !=
-        cudaSuccess)
+    a.partials = partials;
+    if ((e = dk::launch_level(c->lv[level].n, coupled, c->lv[level].sel[coupled ? 1 : 0], a, n_ctas, st,
+                              priority)) != cudaSuccess)
         return cuda_fail(c, e, "level kernel launch");
-    if ((e = dk::launch_reduce(c->d_partials, n_slots, c->stride, sums_dev, st)) != cudaSuccess)
+    if ((e = dk::launch_reduce(partials, n_slots, c->stride, sums_dev, st)) != cudaSuccess)
         return cuda_fail(c, e, "reduce kernel launch");
     return MLMC_DK_OK;
 }
@@ -266,6 +292,16 @@ void release(mlmc_dk_ctx* c) {
     if (c->h_err) cudaFreeHost(c->h_err);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    for (auto p : c->d_lpart) cudaFree(p);
+    for (auto s : c->lstream) if (s) cudaStreamDestroy(s);
+    for (auto ev : c->ev_join) if (ev) cudaEventDestroy(ev);
+    for (auto ev : c->ev_lb) if (ev) cudaEventDestroy(ev);
+    for (auto ev : c->ev_le) if (ev) cudaEventDestroy(ev);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    cudaFree(c->d_bsums);
+    if (c->h_bsums) cudaFreeHost(c->h_bsums);
 }
 
 }  // namespace
@@ -443,6 +479,41 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
         return cuda_fail(nullptr, e, "context buffers");
     }
     c->partials_cap = partials_need;
+    // per-level streams (finest level most urgent), scratch and events of the multi-level batch
+    int prio_lo = 0, prio_hi = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    const int nl = cfg->L_max + 1;
+    c->lstream.assign(nl, nullptr);
+    c->d_lpart.assign(nl, nullptr);
+    c->lpart_cap.assign(nl, 0);
+    c->lprio.assign(nl, 0);
+    c->ev_join.assign(nl, nullptr);
+    c->ev_lb.assign(nl, nullptr);
+    c->ev_le.assign(nl, nullptr);
+    for (int l = 0; l < nl; ++l) {
+        const LevelTab& t = c->lv[l];
+        size_t need = 0;
+        for (int mode = 0; mode < 2; ++mode)
+            for (const auto& vi : t.vis[mode])
+                if (vi.supported) need = std::max(need, (size_t)(vi.max_ctas / vi.cluster) * vi.slots_per_cta * c->stride);
+        c->lpart_cap[l] = need;
+        // the finest level gets the most urgent priority, coarser levels fill in
+        c->lprio[l] = std::max(prio_hi, prio_lo - (l * (prio_lo - prio_hi)) / std::max(1, nl - 1));
+        if ((e = cudaMalloc(&c->d_lpart[l], sizeof(double) * std::max<size_t>(need, 1))) != cudaSuccess ||
+            (e = cudaStreamCreateWithPriority(&c->lstream[l], cudaStreamNonBlocking, c->lprio[l])) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&c->ev_join[l], cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreate(&c->ev_lb[l])) != cudaSuccess || (e = cudaEventCreate(&c->ev_le[l])) != cudaSuccess) {
+            mlmc_dk_free(c);
+            return cuda_fail(nullptr, e, "batch streams");
+        }
+    }
+    if ((e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_bsums, sizeof(double) * c->stride * nl)) != cudaSuccess ||
+        (e = cudaMallocHost(&c->h_bsums, sizeof(double) * c->stride * nl)) != cudaSuccess) {
+        mlmc_dk_free(c);
+        return cuda_fail(nullptr, e, "batch graph resources");
+    }
     *out = c;
     return MLMC_DK_OK;
 }
@@ -545,6 +616,115 @@ int mlmc_dk_run_level_static(const mlmc_dk_ctx* ctx, int32_t level, int32_t stre
         return cuda_fail(c, e, "level kernel launch");
     if ((e = dk::launch_reduce(scratch, n_slots, ctx->stride, sums_dev, st)) != cudaSuccess)
         return cuda_fail(c, e, "reduce kernel launch");
+    return MLMC_DK_OK;
+}
+
+int mlmc_dk_run_batch_dev(mlmc_dk_ctx* ctx, const int64_t* counts, int64_t first_sample, uint64_t seed,
+                          double* sums_dev, void* cuda_stream) {
+    if (!ctx) return fail(nullptr, MLMC_DK_ERR_INVALID, "null context");
+    if (!counts || !sums_dev || ((uintptr_t)sums_dev & 7) || first_sample < 0)
+        return fail(ctx, MLMC_DK_ERR_INVALID, "run_batch_dev: bad arguments");
+    const int nl = ctx->L_max + 1;
+    for (int l = 0; l < nl; ++l)
+        if (counts[l] < 0) return fail(ctx, MLMC_DK_ERR_INVALID, "run_batch_dev: negative count");
+    cudaStream_t st = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : ctx->stream;
+    cudaError_t e;
+    if ((e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return cuda_fail(ctx, e, "cudaStreamBeginCapture");
+    int rc = MLMC_DK_OK;
+    e = cudaEventRecord(ctx->ev_fork, ctx->cap_stream);
+    // finest level first: its clusters are placed before the coarser levels fill the remaining SMs
+    for (int l = nl - 1; l >= 0 && e == cudaSuccess && rc == MLMC_DK_OK; --l) {
+        double* out = sums_dev + (size_t)l * ctx->stride;
+        if ((e = cudaStreamWaitEvent(ctx->lstream[l], ctx->ev_fork, 0)) != cudaSuccess) break;
+        // external records become event-record nodes of the graph (timing)
+        if ((e = cudaEventRecordWithFlags(ctx->ev_lb[l], ctx->lstream[l], cudaEventRecordExternal)) != cudaSuccess)
+            break;
+        rc = launch_batch_into(ctx, l, 0, first_sample, counts[l], seed, out, nullptr, ctx->lstream[l],
+                               ctx->d_lpart[l], ctx->lpart_cap[l], ctx->lprio[l]);
+        if (rc != MLMC_DK_OK) break;
+        if ((e = cudaEventRecordWithFlags(ctx->ev_le[l], ctx->lstream[l], cudaEventRecordExternal)) != cudaSuccess)
+            break;
+        if ((e = cudaEventRecord(ctx->ev_join[l], ctx->lstream[l])) != cudaSuccess) break;
+        e = cudaStreamWaitEvent(ctx->cap_stream, ctx->ev_join[l], 0);
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(ctx->cap_stream, &graph);
+    if (rc != MLMC_DK_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess || ec != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(ctx, e != cudaSuccess ? e : ec, "batch capture");
+    }
+    // reuse the instantiated graph when only parameters changed
+    bool updated = false;
+    if (ctx->gexec) {
+        cudaGraphExecUpdateResultInfo info;
+        updated = cudaGraphExecUpdate(ctx->gexec, graph, &info) == cudaSuccess;
+        if (!updated) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(ctx->gexec);
+            ctx->gexec = nullptr;
+        }
+    }
+    if (!updated && (e = cudaGraphInstantiate(&ctx->gexec, graph, 0)) != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        ctx->gexec = nullptr;
+        return cuda_fail(ctx, e, "cudaGraphInstantiate");
+    }
+    cudaGraphDestroy(graph);
+    if ((e = cudaGraphLaunch(ctx->gexec, st)) != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphLaunch");
+    return MLMC_DK_OK;
+}
+
+int mlmc_dk_batch_level_ms(mlmc_dk_ctx* ctx, double* ms) {
+    if (!ctx || !ms) return fail(ctx, MLMC_DK_ERR_INVALID, "batch_level_ms: bad arguments");
+    for (int l = 0; l <= ctx->L_max; ++l) {
+        float t = 0.f;
+        const cudaError_t e = cudaEventElapsedTime(&t, ctx->ev_lb[l], ctx->ev_le[l]);
+        if (e == cudaErrorNotReady) return cuda_fail(ctx, e, "batch still running");
+        ms[l] = e == cudaSuccess ? (double)t : 0.0;
+        if (e != cudaSuccess) cudaGetLastError();
+    }
+    return MLMC_DK_OK;
+}
+
+int mlmc_dk_run_batch(mlmc_dk_ctx* ctx, const int64_t* counts, uint64_t seed, mlmc_dk_level_sums* sums) {
+    if (!ctx) return fail(nullptr, MLMC_DK_ERR_INVALID, "null context");
+    if (!counts || !sums) return fail(ctx, MLMC_DK_ERR_INVALID, "run_batch: bad arguments");
+    const int nl = ctx->L_max + 1;
+    for (int l = 0; l < nl; ++l)
+        if (counts[l] < 0) return fail(ctx, MLMC_DK_ERR_INVALID, "run_batch: negative count");
+    // one id range for all levels: the batch starts after the furthest level
+    int64_t first = 0;
+    for (int l = 0; l < nl; ++l) first = std::max(first, ctx->next_id[0][l]);
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaError_t e = cudaEventRecord(ctx->ev0, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaEventRecord");
+    int rc = mlmc_dk_run_batch_dev(ctx, counts, first, seed, ctx->d_bsums, ctx->stream);
+    if (rc != MLMC_DK_OK) return rc;
+    if ((e = cudaEventRecord(ctx->ev1, ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "cudaEventRecord");
+    e = cudaMemcpyAsync(ctx->h_bsums, ctx->d_bsums, sizeof(double) * ctx->stride * nl, cudaMemcpyDeviceToHost,
+                        ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "batch");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    if ((rc = check_device_error(ctx)) != MLMC_DK_OK) return rc;
+    const double wall = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    int active = 0;
+    for (int l = 0; l < nl; ++l) active += counts[l] > 0;
+    for (int l = 0; l < nl; ++l) {
+        if (counts[l] == 0) continue;
+        ctx->next_id[0][l] = first + counts[l];
+        const LevelTab& f = ctx->lv[l];
+        double cost = (double)f.n * f.n * f.M;
+        if (l > 0) cost += (double)ctx->lv[l - 1].n * ctx->lv[l - 1].n * ctx->lv[l - 1].M;
+        accumulate(ctx, ctx->h_bsums + (size_t)l * ctx->stride, sums + (size_t)l * ctx->n_quant, cost,
+                   wall / active, 1e-3 * ms / active, 2);
+    }
     return MLMC_DK_OK;
 }
 

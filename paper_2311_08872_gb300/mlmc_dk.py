@@ -113,6 +113,10 @@ def lib() -> ctypes.CDLL:
         L.mlmc_dk_version.restype = ctypes.c_char_p
         L.mlmc_dk_run_level_static.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
                                                ctypes.c_int64, ctypes.c_uint64, vp, vp, vp, vp]
+        L.mlmc_dk_run_batch_dev.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.c_int64, ctypes.c_uint64,
+                                            vp, vp]
+        L.mlmc_dk_run_batch.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.c_uint64, ctypes.POINTER(LevelSums)]
+        L.mlmc_dk_batch_level_ms.argtypes = [vp, _dp]
         L.mlmc_dk_set_variant.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
         L.mlmc_dk_tune.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]
         L.mlmc_dk_noise_dev.argtypes = [ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
@@ -240,6 +244,24 @@ class Context:
                                               ctypes.c_void_p(sums_ptr), ctypes.c_void_p(samples_ptr or None),
                                               ctypes.c_void_p(err_ptr or None), ctypes.c_void_p(stream or None)),
                self._ctx)
+
+    def run_batch_dev(self, counts, first: int, seed: int, sums_ptr: int, stream: int = 0):
+        """All levels concurrently (CUDA graph); sums_ptr: device double[L_max+1][sums_len]."""
+        c = (ctypes.c_int64 * (self.L_max + 1))(*[int(x) for x in counts])
+        _check(lib().mlmc_dk_run_batch_dev(self._ctx, c, first, seed, ctypes.c_void_p(sums_ptr),
+                                           ctypes.c_void_p(stream or None)), self._ctx)
+
+    def batch_level_ms(self):
+        ms = (ctypes.c_double * (self.L_max + 1))()
+        _check(lib().mlmc_dk_batch_level_ms(self._ctx, ms), self._ctx)
+        return list(ms)
+
+    def run_batch(self, counts, seed: int):
+        """Host form: returns sums[level][quantity]."""
+        c = (ctypes.c_int64 * (self.L_max + 1))(*[int(x) for x in counts])
+        sums = (LevelSums * ((self.L_max + 1) * self.n_quant))()
+        _check(lib().mlmc_dk_run_batch(self._ctx, c, seed, sums), self._ctx)
+        return [[sums[l * self.n_quant + q] for q in range(self.n_quant)] for l in range(self.L_max + 1)]
 
     def set_variant(self, level: int, coupled: bool, variant: int):
         _check(lib().mlmc_dk_set_variant(self._ctx, level, int(coupled), variant), self._ctx)
