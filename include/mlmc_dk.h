@@ -32,6 +32,10 @@
  * Z_1 = sqrt(-2 ln u) cos theta, Z_2 = sqrt(-2 ln u) sin theta.  Stream 0 is
  * the coupled MLMC stream, stream 1 plain single-level Monte Carlo.
  *
+ * Grids up to 256^2 keep each sample's state in registers for the whole run;
+ * larger grids (512^2, 1024^2) stream the state of a wave of samples through
+ * global memory with one launch per fine step (same arithmetic, same results).
+ *
  * Grids are row-major, point (i1, i2) at (i1 h, i2 h), flat index i1 n + i2;
  * component r = 1 of the noise flux is along i1.
  *
@@ -92,6 +96,8 @@ typedef struct {
     int32_t pilot;          /* Algorithm 1 initial samples per level (0 -> 256) */
     int32_t L_start;        /* Algorithm 1 initial finest level (0 -> 2, capped at L_max) */
     void* cuda_stream;      /* cudaStream_t for all device work, or NULL (legacy default stream) */
+    int32_t stream_from_n;  /* 0: stream the state only where no register kernel exists (n >= 512);
+                               k > 0: also for every level with n >= k (n a multiple of 64) */
 } mlmc_dk_config;
 
 /* Per-level description returned by mlmc_dk_level_info. */
@@ -108,6 +114,8 @@ typedef struct {
     int32_t n_variants;     /* kernel variants (lane-block shapes, cluster sizes) for this grid size */
     int32_t variant_single, variant_coupled;  /* variants in use for the fine-only and the coupled kernel */
     int32_t lane_cols, lane_rows, cluster;    /* the level's main kernel: C x R coarse cells per lane, cluster */
+    int32_t streamed;       /* 1: grid too large for registers; state streamed through global memory */
+    int32_t in_flight;      /* streamed path: samples advanced together (their state fits L2) */
 } mlmc_dk_level_desc;
 
 /* Host-side moment sums of one quantity on one level (accumulated into). */

@@ -72,6 +72,34 @@ cudaError_t launch_level(int n, bool coupled, int idx, const KArgs& a, int n_cta
 cudaError_t launch_reduce(const double* partials, int n_slots, int slot_stride, double* out,
                           cudaStream_t stream);
 
+// ---- streamed-state path (grids without a register-resident variant)
+struct SArgs {
+    int n, nc, M, coupled, n_obs;
+    int count;                   // samples in this wave (<= samples in flight)
+    long long sid0;              // sample id of the wave's first sample
+    int32_t* q[2];               // [S][n][n] fine state, double buffered
+    int2* G[2];                  // [S][n][n] (G1, G2) noise transfers, double buffered
+    int32_t* qc[2];              // [S][n/2][n/2] coarse state, double buffered
+    int2* Gc;                    // [S][n/2][n/2] coarse transfers
+    float2* zt;                  // [S][n/2][n/2] coupled normal sums
+    double* tile_part;           // [S][tiles][2 kMaxObs + 2] per-tile observables
+    const int32_t* q0f; const int32_t* qbf; const float* phif;
+    const int32_t* q0c; const int32_t* qbc; const float* phic;
+    int32_t Af, Ac;
+    float gf, gc;
+    uint32_t key0, key1, tag;
+    unsigned int* err;
+};
+
+// Device bytes for `S` samples in flight on an n x n grid, and their layout.
+size_t stream_bytes(int n, int S);
+void stream_carve(SArgs* a, void* buf, int n, int S);
+
+// Run k.count samples (ids k.first..) in waves of S: per-slot moment sums go
+// to k.partials ([k.slot_stride][S], zeroed here), per-sample outputs to
+// k.samples; the caller reduces the S slots.
+cudaError_t stream_run(const KArgs& k, SArgs a, int S, cudaStream_t stream);
+
 // Device address and size (doubles) of the statically allocated scratch used
 // by mlmc_dk_run_level_static; the first call on a device looks the address up
 // with cudaGetSymbolAddress (device must be current).

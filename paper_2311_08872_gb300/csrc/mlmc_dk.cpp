@@ -33,9 +33,15 @@ struct LevelTab {
     int32_t* d_qbar = nullptr;
     float* d_phi = nullptr;
     std::vector<dk::VariantInfo> vis[2];   // kernel variants: [0] fine path only, [1] coupled pair
+    int streamed = 0;                      // no register variant: state streamed through global memory
+    int inflight = 0;                      // samples in flight on the streamed path
+    void* d_stream = nullptr;              // their state
+    double* d_spart = nullptr;             // their per-slot partial sums [stride][S]
     int sel[2] = {0, 0};                   // variant in use for each mode
     const dk::VariantInfo& vi(bool coupled) const {
         static const dk::VariantInfo none{};
+        static const dk::VariantInfo streamed_info{1, 256, 1, 0, 0, 0, 0, 0};
+        if (streamed) return streamed_info;
         const auto& v = vis[coupled ? 1 : 0];
         return v.empty() ? none : v[sel[coupled ? 1 : 0]];
     }
@@ -194,9 +200,40 @@ int launch_batch(mlmc_dk_ctx* c, int level, int stream_tag, int64_t first, int64
                              c->partials_cap, 0);
 }
 
+int launch_streamed(mlmc_dk_ctx* c, int level, int stream_tag, int64_t first, int64_t count, uint64_t seed,
+                    double* sums_dev, double* samples_dev, cudaStream_t st) {
+    const bool coupled = (stream_tag == 0) && level > 0;
+    LevelTab& t = c->lv[level];
+    cudaError_t e;
+    if (count == 0) {
+        e = cudaMemsetAsync(sums_dev, 0, sizeof(double) * c->stride, st);
+        return e == cudaSuccess ? MLMC_DK_OK : cuda_fail(c, e, "cudaMemsetAsync");
+    }
+    dk::KArgs k = make_args(c, level, stream_tag, coupled, first, count, seed, samples_dev);
+    k.partials = t.d_spart;
+    dk::SArgs a{};
+    dk::stream_carve(&a, t.d_stream, t.n, t.inflight);
+    a.n = t.n;
+    a.nc = t.n / 2;
+    a.M = t.M;
+    a.coupled = coupled ? 1 : 0;
+    a.n_obs = c->n_obs;
+    a.q0f = k.q0f; a.qbf = k.qbf; a.phif = k.phif;
+    a.q0c = k.q0c; a.qbc = k.qbc; a.phic = k.phic;
+    a.Af = k.Af; a.Ac = k.Ac; a.gf = k.gf; a.gc = k.gc;
+    a.key0 = k.key0; a.key1 = k.key1; a.tag = k.tag;
+    a.err = c->d_err;
+    if ((e = dk::stream_run(k, a, t.inflight, st)) != cudaSuccess) return cuda_fail(c, e, "streamed level");
+    if ((e = dk::launch_reduce(t.d_spart, t.inflight, c->stride, sums_dev, st)) != cudaSuccess)
+        return cuda_fail(c, e, "reduce kernel launch");
+    return MLMC_DK_OK;
+}
+
 int launch_batch_into(mlmc_dk_ctx* c, int level, int stream_tag, int64_t first, int64_t count, uint64_t seed,
                       double* sums_dev, double* samples_dev, cudaStream_t st, double* partials, size_t cap,
                       int priority) {
+    if (c->lv[level].streamed)
+        return launch_streamed(c, level, stream_tag, first, count, seed, sums_dev, samples_dev, st);
     const bool coupled = (stream_tag == 0) && level > 0;
     const dk::VariantInfo& vi = c->lv[level].vi(coupled);
     if (!vi.supported)
@@ -284,6 +321,8 @@ void release(mlmc_dk_ctx* c) {
         cudaFree(l.d_q0);
         cudaFree(l.d_qbar);
         cudaFree(l.d_phi);
+        cudaFree(l.d_stream);
+        cudaFree(l.d_spart);
     }
     cudaFree(c->d_partials);
     cudaFree(c->d_sums);
@@ -453,7 +492,23 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
         }
         cudaFreeHost(stage);
         c->h2d_bytes += (int64_t)bytes;
-        const int nv = dk::variant_count(t.n);
+        const bool force_stream = cfg->stream_from_n > 0 && t.n >= cfg->stream_from_n && t.n % 64 == 0;
+        const int nv = force_stream ? 0 : dk::variant_count(t.n);
+        if (nv == 0) {
+            // no register-resident variant: stream the state through global memory,
+            // as many samples in flight as fit a 64 MB working set (L2-resident)
+            if (t.n % 64 != 0) {
+                mlmc_dk_free(c);
+                return fail(nullptr, MLMC_DK_ERR_UNSUPPORTED, "grid size without a kernel");
+            }
+            t.streamed = 1;
+            t.inflight = (int)std::max<size_t>(1, (size_t)(64u << 20) / dk::stream_bytes(t.n, 1));
+            if ((e = cudaMalloc(&t.d_stream, dk::stream_bytes(t.n, t.inflight))) != cudaSuccess ||
+                (e = cudaMalloc(&t.d_spart, sizeof(double) * c->stride * t.inflight)) != cudaSuccess) {
+                mlmc_dk_free(c);
+                return cuda_fail(nullptr, e, "streamed level buffers");
+            }
+        }
         for (int mode = 0; mode < 2; ++mode) {
             if (mode == 1 && l == 0) continue;
             for (int v = 0; v < nv; ++v) {
@@ -550,6 +605,8 @@ int mlmc_dk_level_info(const mlmc_dk_ctx* ctx, int32_t level, mlmc_dk_level_desc
     out->lane_cols = vs.C;
     out->lane_rows = vs.R;
     out->cluster = vs.cluster;
+    out->streamed = t.streamed;
+    out->in_flight = t.inflight;
     return MLMC_DK_OK;
 }
 
@@ -583,8 +640,8 @@ int mlmc_dk_run_level_static(const mlmc_dk_ctx* ctx, int32_t level, int32_t stre
         return fail(c, MLMC_DK_ERR_INVALID, "run_level_static: bad arguments");
     const bool coupled = (stream_tag == 0) && level > 0;
     const dk::VariantInfo& vi = ctx->lv[level].vi(coupled);
-    if (!vi.supported)
-        return fail(c, MLMC_DK_ERR_UNSUPPORTED, "no kernel variant for n = " + std::to_string(ctx->lv[level].n));
+    if (!vi.supported || ctx->lv[level].streamed)
+        return fail(c, MLMC_DK_ERR_UNSUPPORTED, "no register-resident kernel for n = " + std::to_string(ctx->lv[level].n));
     cudaStream_t st = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : ctx->stream;
     cudaError_t e;
     if (n_samples == 0) {
@@ -635,6 +692,7 @@ int mlmc_dk_run_batch_dev(mlmc_dk_ctx* ctx, const int64_t* counts, int64_t first
     e = cudaEventRecord(ctx->ev_fork, ctx->cap_stream);
     // finest level first: its clusters are placed before the coarser levels fill the remaining SMs
     for (int l = nl - 1; l >= 0 && e == cudaSuccess && rc == MLMC_DK_OK; --l) {
+        if (ctx->lv[l].streamed) continue;   // thousands of launches: run after the graph
         double* out = sums_dev + (size_t)l * ctx->stride;
         if ((e = cudaStreamWaitEvent(ctx->lstream[l], ctx->ev_fork, 0)) != cudaSuccess) break;
         // external records become event-record nodes of the graph (timing)
@@ -676,6 +734,13 @@ int mlmc_dk_run_batch_dev(mlmc_dk_ctx* ctx, const int64_t* counts, int64_t first
     }
     cudaGraphDestroy(graph);
     if ((e = cudaGraphLaunch(ctx->gexec, st)) != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphLaunch");
+    for (int l = nl - 1; l >= 0; --l) {
+        if (!ctx->lv[l].streamed) continue;
+        if ((e = cudaEventRecord(ctx->ev_lb[l], st)) != cudaSuccess) return cuda_fail(ctx, e, "cudaEventRecord");
+        rc = launch_streamed(ctx, l, 0, first_sample, counts[l], seed, sums_dev + (size_t)l * ctx->stride, nullptr, st);
+        if (rc != MLMC_DK_OK) return rc;
+        if ((e = cudaEventRecord(ctx->ev_le[l], st)) != cudaSuccess) return cuda_fail(ctx, e, "cudaEventRecord");
+    }
     return MLMC_DK_OK;
 }
 

@@ -42,6 +42,7 @@ class Config(ctypes.Structure):
         ("pilot", ctypes.c_int32),
         ("L_start", ctypes.c_int32),
         ("cuda_stream", ctypes.c_void_p),
+        ("stream_from_n", ctypes.c_int32),
     ]
 
 
@@ -54,6 +55,7 @@ class LevelDesc(ctypes.Structure):
         ("next_sample", ctypes.c_int64), ("h2d_bytes", ctypes.c_int64), ("frac_bits", ctypes.c_int32),
         ("n_variants", ctypes.c_int32), ("variant_single", ctypes.c_int32), ("variant_coupled", ctypes.c_int32),
         ("lane_cols", ctypes.c_int32), ("lane_rows", ctypes.c_int32), ("cluster", ctypes.c_int32),
+        ("streamed", ctypes.c_int32), ("in_flight", ctypes.c_int32),
     ]
 
 
@@ -176,7 +178,8 @@ class Context:
 
     def __init__(self, length: float, n0: int, L_max: int, T: float, mu: float, N: float,
                  rho0: List[np.ndarray], phi: List[List[np.ndarray]], products: bool = False,
-                 M0: int = 0, pilot: int = 0, L_start: int = 0, stream: Optional[int] = None):
+                 M0: int = 0, pilot: int = 0, L_start: int = 0, stream: Optional[int] = None,
+                 stream_from_n: int = 0):
         self._ctx = None
         self._rho0 = [_f64(r).reshape(-1) for r in rho0]
         self.n_obs = len(phi[0])
@@ -184,7 +187,7 @@ class Context:
         rho_ptrs = (_dp * len(self._rho0))(*[r.ctypes.data_as(_dp) for r in self._rho0])
         phi_ptrs = (_dp * len(self._phi))(*[p.ctypes.data_as(_dp) for p in self._phi])
         self.cfg = Config(length, n0, L_max, T, mu, M0, N, rho_ptrs, self.n_obs, phi_ptrs,
-                          int(products), pilot, L_start, stream)
+                          int(products), pilot, L_start, stream, stream_from_n)
         h = ctypes.c_void_p()
         _check(lib().mlmc_dk_init(ctypes.byref(self.cfg), ctypes.byref(h)))
         self._ctx = h

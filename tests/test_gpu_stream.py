@@ -1,0 +1,97 @@
+"""Streamed-state kernels (grids too large for registers: 512^2, 1024^2).
+
+* Forced onto 128^2 and 256^2 levels they must reproduce the register kernels:
+  identical fixed-point paths (equal masses), observables equal up to the
+  order of FP32 partial sums.
+* At 512^2 (short horizon, so the oracle is affordable) they match the FP64
+  oracle sample by sample.
+* At the full 512^2 and 1024^2 levels of the low-density and large workloads:
+  exact mass conservation, and with the noise off the observables equal the
+  discrete mean field (a property that holds at any size).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2311_08872_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dk():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2311_08872_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2311_08872_gb300 import mlmc_dk
+    return mlmc_dk
+
+
+def _samples(ctx, dk, level, tag, first, count, seed):
+    import torch
+    sums = torch.zeros(dk.sums_len(ctx.n_quant), dtype=torch.float64, device="cuda")
+    samp = torch.zeros(count, dk.sample_stride(ctx.n_obs), dtype=torch.float64, device="cuda")
+    ctx.run_level_dev(level, tag, first, count, seed, sums.data_ptr(), samp.data_ptr(),
+                      torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    return sums.cpu().numpy(), samp.cpu().numpy()
+
+
+@pytest.mark.parametrize("level,count", [(3, 12), (4, 10)])
+def test_streamed_equals_register_kernels(dk, level, count):
+    wl = W.get("mlmc16_256").with_(L_max=level)
+    with dk.Context.from_workload(wl) as reg, dk.Context.from_workload(wl, stream_from_n=128) as stm:
+        assert stm.level_info(level).streamed == 1 and reg.level_info(level).streamed == 0
+        for tag in (0, 1):
+            s_r, a = _samples(reg, dk, level, tag, 3, count, 11)
+            s_s, b = _samples(stm, dk, level, tag, 3, count, 11)
+            K = reg.n_obs
+            assert np.array_equal(a[:, 2 * K:], b[:, 2 * K:])
+            scale = np.sqrt(np.mean(a[:, :2 * K] ** 2, axis=0)) + 1e-300
+            assert np.all(np.abs(a[:, :2 * K] - b[:, :2 * K]) <= 1e-6 * scale)
+            assert s_s[0] == count and s_s[1] == 0.0
+            np.testing.assert_allclose(s_s[2:], s_r[2:], rtol=1e-5, atol=1e-12)
+
+
+def test_streamed_512_matches_oracle(dk):
+    # 256^2 / 512^2 levels over a short horizon: 2 and 8 fine steps
+    wl = W.get("lowdens32_512").with_(n0=256, L_max=1, T=2.0e-6)
+    with dk.Context.from_workload(wl) as ctx:
+        info = ctx.level_info(1)
+        assert info.n == 512 and info.streamed == 1 and info.M == 8
+        _, samp = _samples(ctx, dk, 1, 0, 0, 3, 21)
+    lv = oracle.level_table(wl.length, wl.n0, wl.L_max, wl.T, wl.mu)
+    ol = oracle.level_inputs(wl.length, lv, wl.N, wl.rho0_all(), wl.phi_all(), 1, True)
+    ref = oracle.run_samples(ol, 21, range(3), True)
+    for col, key, yb in ((0, "Y_f", info.ybar_f[0]), (1, "Y_c", info.ybar_c[0])):
+        y = samp[:, col] + yb
+        yo = ref[key][:, 0]
+        rms = np.sqrt(np.mean((yo - yb) ** 2))
+        assert np.all(np.abs(y - yo) <= 1e-5 * np.maximum(np.abs(yo), rms)), (key, y - yo, rms)
+
+
+@pytest.mark.parametrize("name,level,count", [("lowdens32_512", 4, 9), ("large32_1024", 5, 2)])
+def test_full_size_streamed_levels_conserve_mass(dk, name, level, count):
+    wl = W.get(name)
+    with dk.Context.from_workload(wl) as ctx:
+        info = ctx.level_info(level)
+        assert info.streamed == 1
+        sums, samp = _samples(ctx, dk, level, 0, 0, count, 5)
+    assert sums[0] == count and sums[1] == 0.0
+    assert np.all(np.isfinite(samp))
+
+
+def test_full_size_1024_noise_off_is_mean_field(dk):
+    wl = W.get("large32_1024").with_(N=0.0)
+    with dk.Context.from_workload(wl) as ctx:
+        sums, samp = _samples(ctx, dk, 5, 0, 0, 1, 5)
+    K = 4
+    # Y - Ybar: fixed-point rounding of a deterministic run only.  Each step rounds
+    # every edge flux to within half a unit (2^-S); even fully coherent rounding
+    # reaches (rho, phi)_h through grad phi only: <= 0.5 2^-S h^3 (2 n^2) 2 pi k per step,
+    # about 5e-5 over the 524288 steps of 1024^2 (S = 26).
+    assert np.all(np.abs(samp[:, :2 * K]) < 1e-4)
+    print("max |Y - Ybar| with the noise off:", np.abs(samp[:, :2 * K]).max())
+    assert sums[1] == 0.0
