@@ -1,0 +1,127 @@
+"""FP64 oracle for the learned level below level 0 (not in the paper).
+
+TEST INFRASTRUCTURE ONLY (same rules as the rest of ``oracle/``).
+
+* ``modes(n, count)``: the lowest real orthonormal Fourier modes of an n x n
+  grid (orthonormal for the plain sum over grid points), excluding the
+  constant: wave vectors k with k1 > 0, or k1 = 0 and k2 > 0, ordered by
+  |k|^2 then (k1, k2); each contributes a cosine and a sine mode.
+* ``features(Z, g)``: heat-weighted projections F_(j, r) = sum_m g_j^(M-1-m)
+  <Z^m_(., r), e_j> of the level-0 normals on the modes e_j (component r of
+  the noise), with g_j the per-step factor of the noise-free scheme on mode j
+  (the discrete heat symbol of Section 7.2's operators).  With i.i.d. N(0,1)
+  normals and orthonormal modes they are independent N(0, sum_i g_j^(2i)).
+* ``mlp_*``: a plain FP64 4-layer ReLU perceptron 64-256-256-256-1 (forward,
+  backward, mean-squared-error loss) for checking the GPU kernels.
+"""
+from __future__ import annotations
+
+import math
+from typing import List, Tuple
+
+import numpy as np
+
+
+def mode_vectors(n: int, count: int) -> List[Tuple[int, int]]:
+    ks = []
+    half = n // 2
+    for k1 in range(0, half + 1):
+        for k2 in range(-half + 1, half + 1):
+            if k1 == 0 and k2 <= 0:
+                continue
+            if 2 * k1 == n or 2 * abs(k2) == n:
+                continue   # Nyquist lines: no sine partner
+            ks.append((k1, k2))
+    ks.sort(key=lambda k: (k[0] * k[0] + k[1] * k[1], k[0], k[1]))
+    return ks[: (count + 1) // 2]
+
+
+def modes(n: int, count: int = 32) -> np.ndarray:
+    """E of shape (count, n, n): cos/sin pairs, orthonormal for the plain sum."""
+    i1, i2 = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    out = []
+    for k1, k2 in mode_vectors(n, count):
+        ang = 2 * math.pi * (k1 * i1 + k2 * i2) / n
+        out.append(math.sqrt(2.0 / (n * n)) * np.cos(ang))
+        out.append(math.sqrt(2.0 / (n * n)) * np.sin(ang))
+    return np.array(out[:count])
+
+
+def heat_factors(n: int, mu: float, count: int = 32) -> np.ndarray:
+    g = []
+    for k1, k2 in mode_vectors(n, count):
+        gk = 1.0 - 2.0 * mu * (math.sin(math.pi * k1 / n) ** 2 + math.sin(math.pi * k2 / n) ** 2)
+        g += [gk, gk]
+    return np.array(g[:count])
+
+
+def feature_sigma(g: np.ndarray, M: int) -> np.ndarray:
+    """Standard deviation of each feature: sqrt(sum_{i<M} g^(2i)), per (mode, component)."""
+    s = np.sqrt(np.array([np.sum(gk ** (2 * np.arange(M))) for gk in g]))
+    return np.repeat(s, 2)
+
+
+def features(Zs: List[np.ndarray], E: np.ndarray, g: np.ndarray) -> np.ndarray:
+    """Zs: the M arrays of normals (n, n, 2) of one sample, in step order.
+    Returns the 2*count features ordered (mode j, component r) -> 2 j + r."""
+    M = len(Zs)
+    F = np.zeros((E.shape[0], 2))
+    for m, Z in enumerate(Zs):
+        w = g ** (M - 1 - m)
+        for r in range(2):
+            F[:, r] += w * np.tensordot(E, Z[..., r], axes=([1, 2], [0, 1]))
+    return F.reshape(-1)
+
+
+# ------------------------------------------------------------------- MLP
+LAYERS = (64, 256, 256, 256, 1)
+
+
+def mlp_param_count() -> int:
+    return sum(LAYERS[i] * LAYERS[i + 1] + LAYERS[i + 1] for i in range(len(LAYERS) - 1))
+
+
+def mlp_unpack(theta: np.ndarray):
+    """Flat parameter vector -> [(W [out, in], b [out])], layer by layer (W then b)."""
+    out, off = [], 0
+    for i in range(len(LAYERS) - 1):
+        a, b = LAYERS[i], LAYERS[i + 1]
+        W = theta[off: off + a * b].reshape(b, a)
+        off += a * b
+        bias = theta[off: off + b]
+        off += b
+        out.append((W, bias))
+    return out
+
+
+def mlp_forward(theta: np.ndarray, X: np.ndarray):
+    acts = [X]
+    h = X
+    layers = mlp_unpack(theta)
+    for i, (W, b) in enumerate(layers):
+        z = h @ W.T + b
+        h = np.maximum(z, 0.0) if i < len(layers) - 1 else z
+        acts.append(h)
+    return h[:, 0], acts
+
+
+def mlp_loss_grad(theta: np.ndarray, X: np.ndarray, T: np.ndarray):
+    """Mean squared error and its gradient (flat, same layout as theta)."""
+    y, acts = mlp_forward(theta, X)
+    B = X.shape[0]
+    loss = float(np.mean((y - T) ** 2))
+    d = (2.0 / B) * (y - T)[:, None]
+    layers = mlp_unpack(theta)
+    grads = []
+    for i in range(len(layers) - 1, -1, -1):
+        W, b = layers[i]
+        h_in = acts[i]
+        gW = d.T @ h_in
+        gb = d.sum(axis=0)
+        grads.append((gW, gb))
+        if i > 0:
+            d = (d @ W) * (acts[i] > 0)
+    flat = []
+    for gW, gb in reversed(grads):
+        flat += [gW.reshape(-1), gb]
+    return loss, np.concatenate(flat)

@@ -4,6 +4,7 @@
 #include <cstddef>
 #include <cstdint>
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 namespace dk {
@@ -99,6 +100,49 @@ void stream_carve(SArgs* a, void* buf, int n, int S);
 // to k.partials ([k.slot_stride][S], zeroed here), per-sample outputs to
 // k.samples; the caller reduces the S slots.
 cudaError_t stream_run(const KArgs& k, SArgs a, int S, cudaStream_t stream);
+
+// ---- learned level below level 0
+constexpr int kModes = 32;     // real orthonormal modes
+constexpr int kFeat = 64;      // features = modes x 2 noise components
+constexpr int kHidden = 256;
+
+struct FeatArgs {
+    const float* E;            // [32][n*n] mode table (plain-sum orthonormal)
+    const float* g;            // [32] per-step factor of the noise-free scheme on each mode
+    const float* inv_sigma;    // [64] 1 / standard deviation of each feature
+    int n, M;
+    uint32_t key0, key1, tag;
+    long long first, count;
+    __nv_bfloat16* X;          // [count][64] standardised features
+    float* Xf;                 // optional FP32 copy
+};
+
+struct GemmArgs {
+    int M, N, K;
+    const __nv_bfloat16* A; long long sam, sak;   // A[m][k] = A[m*sam + k*sak]
+    const __nv_bfloat16* B; long long sbk, sbn;   // B[k][n] = B[k*sbk + n*sbn]
+    float* C; long long ldc;                       // optional FP32 output
+    __nv_bfloat16* Cb; long long ldcb;             // optional BF16 output
+    const float* bias;                             // optional bias[n]
+    int relu;
+    const __nv_bfloat16* mask; long long ldm;      // optional: zero where mask <= 0
+};
+
+cudaError_t launch_features(const FeatArgs& a, int max_ctas, cudaStream_t st);
+cudaError_t launch_direct_features(const FeatArgs& a, cudaStream_t st);
+cudaError_t launch_gemm(const GemmArgs& g, cudaStream_t st);
+cudaError_t launch_out_forward(const __nv_bfloat16* H, const float* w, const float* b, int B, int K, float* y,
+                               cudaStream_t st);
+cudaError_t launch_out_backward(const float* y, const float* t, const __nv_bfloat16* H, const float* w, int B, int K,
+                                float* dy, __nv_bfloat16* dH, float* dw, float* db, cudaStream_t st);
+cudaError_t launch_colsum(const __nv_bfloat16* Xb, const float* Xf, int B, int N, float* out, cudaStream_t st);
+cudaError_t launch_adam(float* theta, const float* grad, float* m1, float* m2, int P, float lr, float b1, float b2,
+                        float eps, float c1, float c2, const int* bf_index, __nv_bfloat16* theta_bf, cudaStream_t st);
+cudaError_t launch_gather(const __nv_bfloat16* X, const float* T, const int* idx, int B, __nv_bfloat16* Xb, float* Tb,
+                          cudaStream_t st);
+cudaError_t launch_mse(const float* y, const float* t, int B, double* out, cudaStream_t st);
+cudaError_t launch_surrogate_moments(const float* that, const double* d0, int d0_stride, int part, double N,
+                                     long long count, int stride, int blocks, double* partials, cudaStream_t st);
 
 // Device address and size (doubles) of the statically allocated scratch used
 // by mlmc_dk_run_level_static; the first call on a device looks the address up

@@ -1,0 +1,398 @@
+// Learned level below level 0 (not in the paper): feature projection of the
+// level-0 noise, a direct sampler of the features' exact law, and the
+// kernels that train and run a 64-256-256-256-1 ReLU perceptron on BF16
+// tensor cores with FP32 accumulation and FP32 master weights.
+//
+// Features.  With e_j the 32 lowest real orthonormal grid modes (cosine and
+// sine per wave vector k, ordered by |k|^2) and g_j the per-step factor of the
+// noise-free scheme on e_j, a level-0 sample's features are
+//     F_(j,r) = sum_m g_j^(M-1-m) <Z^m_(.,r), e_j>,   r = 1, 2,
+// i.e. the noise that the heat semigroup carries to time T on each low mode.
+// For i.i.d. standard normals they are independent N(0, sum_i g_j^(2i)); the
+// network sees F / sigma, so the level below 0 draws its inputs as plain
+// standard normals, the exact law of the features of the coupled correction
+// level, which keeps the telescoping sum unbiased whatever the network.
+#include <cuda_bf16.h>
+
+#include <cstdint>
+
+#include "dk_device.cuh"
+#include "dk_kernels.h"
+
+namespace dk {
+
+namespace {
+constexpr unsigned kFullMask = 0xffffffffu;
+}
+
+// ------------------------------------------------------------------ features
+// One CTA of 128 threads per sample (grid-stride over samples); thread t
+// handles the cell pairs t, t + 128, ...; shared memory holds the mode table.
+__global__ void __launch_bounds__(128) feature_kernel(const FeatArgs a) {
+    extern __shared__ float fsm[];
+    const int cells = a.n * a.n;
+    float* E = fsm;                         // [32][cells]
+    float* red = fsm + kModes * cells;      // [4][64]
+    for (int i = threadIdx.x; i < kModes * cells; i += 128) E[i] = a.E[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (long long s = blockIdx.x; s < a.count; s += gridDim.x) {
+        const long long sid = a.first + s;
+        const uint32_t c2 = static_cast<uint32_t>(sid);
+        const uint32_t c3 = a.tag | ((static_cast<uint32_t>(static_cast<unsigned long long>(sid) >> 32) & 0xffffu) << 16);
+        float acc[kModes][2];
+#pragma unroll
+        for (int k = 0; k < kModes; ++k) acc[k][0] = acc[k][1] = 0.f;
+        for (int m = 0; m < a.M; ++m) {
+#pragma unroll
+            for (int k = 0; k < kModes; ++k) {
+                acc[k][0] *= a.g[k];
+                acc[k][1] *= a.g[k];
+            }
+            for (int p = threadIdx.x; p < cells / 2; p += 128) {
+                const uint4 x = philox10(make_uint4(static_cast<uint32_t>(p), static_cast<uint32_t>(m), c2, c3),
+                                         a.key0, a.key1);
+                float z1a, z2a, z1b, z2b;
+                box_muller(x.x, x.y, z1a, z2a);
+                box_muller(x.z, x.w, z1b, z2b);
+#pragma unroll
+                for (int k = 0; k < kModes; ++k) {
+                    const float2 e = *reinterpret_cast<const float2*>(E + k * cells + 2 * p);
+                    acc[k][0] = fmaf(e.x, z1a, fmaf(e.y, z1b, acc[k][0]));
+                    acc[k][1] = fmaf(e.x, z2a, fmaf(e.y, z2b, acc[k][1]));
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kModes; ++k)
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                float v = acc[k][r];
+#pragma unroll
+                for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(kFullMask, v, off);
+                if (lane == 0) red[warp * kFeat + 2 * k + r] = v;
+            }
+        __syncthreads();
+        if (threadIdx.x < kFeat) {
+            const int j = threadIdx.x;
+            const float f = (red[j] + red[kFeat + j] + red[2 * kFeat + j] + red[3 * kFeat + j]) * a.inv_sigma[j];
+            a.X[s * kFeat + j] = __float2bfloat16_rn(f);
+            if (a.Xf) a.Xf[s * kFeat + j] = f;
+        }
+        __syncthreads();
+    }
+}
+
+// Direct draw of the standardised features: 64 normals per sample from
+// Philox counters (j, 0, id, tag), j = 0..15 giving 4 normals each.
+__global__ void direct_feature_kernel(const FeatArgs a) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= a.count * (kFeat / 4)) return;
+    const long long s = t / (kFeat / 4);
+    const int j = static_cast<int>(t % (kFeat / 4));
+    const long long sid = a.first + s;
+    const uint32_t c3 = a.tag | ((static_cast<uint32_t>(static_cast<unsigned long long>(sid) >> 32) & 0xffffu) << 16);
+    const uint4 x = philox10(make_uint4(static_cast<uint32_t>(j), 0u, static_cast<uint32_t>(sid), c3), a.key0, a.key1);
+    float z0, z1, z2, z3;
+    box_muller(x.x, x.y, z0, z1);
+    box_muller(x.z, x.w, z2, z3);
+    __nv_bfloat16* o = a.X + s * kFeat + 4 * j;
+    o[0] = __float2bfloat16_rn(z0);
+    o[1] = __float2bfloat16_rn(z1);
+    o[2] = __float2bfloat16_rn(z2);
+    o[3] = __float2bfloat16_rn(z3);
+    if (a.Xf) {
+        float* of = a.Xf + s * kFeat + 4 * j;
+        of[0] = z0; of[1] = z1; of[2] = z2; of[3] = z3;
+    }
+}
+
+// ------------------------------------------------------------- BF16 GEMM
+// C[M x N] = A[M x K] B[K x N] with arbitrary element strides, on tensor cores
+// (mma.sync m16n8k16, BF16 inputs, FP32 accumulation).  CTA tile 64 x 64 x 32,
+// 4 warps of 32 x 32.  Tiles are staged in shared memory as A[m][k] and B[n][k]
+// (k contiguous, padded rows).  Epilogue: + bias[n], ReLU, * (mask[m][n] > 0),
+// FP32 and/or BF16 output.
+namespace {
+constexpr int BM = 64, BN = 64, BK = 32, PAD = 8;
+
+__device__ __forceinline__ uint32_t ld_pair(const __nv_bfloat16* p) {
+    return *reinterpret_cast<const uint32_t*>(p);
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+}  // namespace
+
+__global__ void __launch_bounds__(128) gemm_bf16_kernel(const GemmArgs g) {
+    __shared__ __align__(16) __nv_bfloat16 sA[BM][BK + PAD];
+    __shared__ __align__(16) __nv_bfloat16 sB[BN][BK + PAD];
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    const int gid = lane >> 2, tig = lane & 3;
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
+    const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
+    for (int k0 = 0; k0 < g.K; k0 += BK) {
+        for (int i = tid; i < BM * BK; i += 128) {
+            const int r = i / BK, c = i % BK;
+            const int m = m0 + r, k = k0 + c;
+            sA[r][c] = (m < g.M && k < g.K) ? g.A[m * g.sam + k * g.sak] : zero;
+        }
+        for (int i = tid; i < BN * BK; i += 128) {
+            const int r = i / BK, c = i % BK;
+            const int n = n0 + r, k = k0 + c;
+            sB[r][c] = (n < g.N && k < g.K) ? g.B[k * g.sbk + n * g.sbn] : zero;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; kk += 16) {
+            uint32_t af[2][4], bf[4][2];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int r = wm + 16 * i + gid;
+                af[i][0] = ld_pair(&sA[r][kk + 2 * tig]);
+                af[i][1] = ld_pair(&sA[r + 8][kk + 2 * tig]);
+                af[i][2] = ld_pair(&sA[r][kk + 8 + 2 * tig]);
+                af[i][3] = ld_pair(&sA[r + 8][kk + 8 + 2 * tig]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int c = wn + 8 * j + gid;
+                bf[j][0] = ld_pair(&sB[c][kk + 2 * tig]);
+                bf[j][1] = ld_pair(&sB[c][kk + 8 + 2 * tig]);
+            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bf[j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int m = m0 + wm + 16 * i + gid + (r >= 2 ? 8 : 0);
+                const int n = n0 + wn + 8 * j + 2 * tig + (r & 1);
+                if (m >= g.M || n >= g.N) continue;
+                float v = acc[i][j][r];
+                if (g.bias) v += g.bias[n];
+                if (g.relu) v = fmaxf(v, 0.f);
+                if (g.mask && !(__bfloat162float(g.mask[m * g.ldm + n]) > 0.f)) v = 0.f;
+                if (g.C) g.C[m * g.ldc + n] = v;
+                if (g.Cb) g.Cb[m * g.ldcb + n] = __float2bfloat16_rn(v);
+            }
+}
+
+// -------------------------------------------------------- small MLP kernels
+// Output layer forward: y[b] = H3[b] . w4 + b4 (one warp per row).
+__global__ void out_forward_kernel(const __nv_bfloat16* H, const float* w, const float* b, int B, int K, float* y) {
+    const int row = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= B) return;
+    float s = 0.f;
+    for (int k = lane; k < K; k += 32) s = fmaf(__bfloat162float(H[(size_t)row * K + k]), w[k], s);
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) s += __shfl_xor_sync(kFullMask, s, off);
+    if (lane == 0) y[row] = s + b[0];
+}
+
+// dy = 2 (y - t) / B; dH[b][k] = dy[b] w4[k] (H[b][k] > 0) as BF16.
+__global__ void out_backward_kernel(const float* y, const float* t, const __nv_bfloat16* H, const float* w, int B,
+                                    int K, float* dy, __nv_bfloat16* dH) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)B * K) return;
+    const int b = static_cast<int>(i / K), k = static_cast<int>(i % K);
+    const float d = 2.f * (y[b] - t[b]) / static_cast<float>(B);
+    if (k == 0) dy[b] = d;
+    const float v = __bfloat162float(H[i]) > 0.f ? d * w[k] : 0.f;
+    dH[i] = __float2bfloat16_rn(v);
+}
+
+// Column sums: out[n] = sum_b X[b][n] (X BF16 or FP32), fixed order per column.
+__global__ void colsum_kernel(const __nv_bfloat16* Xb, const float* Xf, int B, int N, float* out) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    float s = 0.f;
+    for (int b = 0; b < B; ++b) s += Xb ? __bfloat162float(Xb[(size_t)b * N + n]) : Xf[(size_t)b * N + n];
+    out[n] = s;
+}
+
+// dW4[k] = sum_b dy[b] H3[b][k]; db4 = sum_b dy[b].
+__global__ void out_weight_grad_kernel(const float* dy, const __nv_bfloat16* H, int B, int K, float* dw, float* db) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < K) {
+        float s = 0.f;
+        for (int b = 0; b < B; ++b) s = fmaf(dy[b], __bfloat162float(H[(size_t)b * K + k]), s);
+        dw[k] = s;
+    }
+    if (k == K) {
+        float s = 0.f;
+        for (int b = 0; b < B; ++b) s += dy[b];
+        db[0] = s;
+    }
+}
+
+// Adam (Kingma & Ba, 2015) with bias correction; refreshes the BF16 weights.
+__global__ void adam_kernel(float* theta, const float* grad, float* m1, float* m2, int P, float lr, float b1, float b2,
+                            float eps, float c1, float c2, const int* bf_index, __nv_bfloat16* theta_bf) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P) return;
+    const float gi = grad[i];
+    const float a = b1 * m1[i] + (1.f - b1) * gi;
+    const float v = b2 * m2[i] + (1.f - b2) * gi * gi;
+    m1[i] = a;
+    m2[i] = v;
+    const float upd = lr * (a / c1) / (sqrtf(v / c2) + eps);
+    const float w = theta[i] - upd;
+    theta[i] = w;
+    const int j = bf_index[i];
+    if (j >= 0) theta_bf[j] = __float2bfloat16_rn(w);
+}
+
+__global__ void gather_kernel(const __nv_bfloat16* X, const float* T, const int* idx, int B, __nv_bfloat16* Xb,
+                              float* Tb) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)B * kFeat) return;
+    const int b = static_cast<int>(i / kFeat), j = static_cast<int>(i % kFeat);
+    const int src = idx[b];
+    Xb[i] = X[(size_t)src * kFeat + j];
+    if (j == 0) Tb[b] = T[src];
+}
+
+// Mean squared error of a batch, FP64 accumulation, one block.
+__global__ void mse_kernel(const float* y, const float* t, int B, double* out) {
+    __shared__ double sh[256];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < B; i += 256) {
+        const double d = static_cast<double>(y[i]) - t[i];
+        s += d * d;
+    }
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0] / B;
+}
+
+// Per-sample quantities of a surrogate batch into per-block FP64 partials
+// (entry-major [stride][blocks]) in the moment layout of the level kernels.
+// part = -1: dP = S = That^2 (level below 0); part = 0: dP = P_0 - S with
+// P_0 = N D0^2 (correction level).  That = network output (sqrt(N)(Y - Ybar)).
+__global__ void __launch_bounds__(256) surrogate_moments_kernel(const float* that, const double* d0, int d0_stride,
+                                                                int part, double N, long long count, int stride,
+                                                                double* partials) {
+    double v[14];
+#pragma unroll
+    for (int i = 0; i < 14; ++i) v[i] = 0.0;
+    for (long long i = blockIdx.x * 256LL + threadIdx.x; i < count; i += 256LL * gridDim.x) {
+        const double S = static_cast<double>(that[i]) * that[i];
+        const double dd = part == 0 ? d0[i * d0_stride] : 0.0;
+        const double pf = part == 0 ? N * dd * dd : S;
+        const double pc = part == 0 ? S : 0.0;
+        const double dp = pf - pc, dp2 = dp * dp;
+        v[0] += 1.0;
+        v[2] += dp; v[3] += dp2; v[4] += dp2 * dp; v[5] += dp2 * dp2;
+        v[6] += pf; v[7] += pf * pf; v[8] += pc; v[9] += pc * pc;
+        const double yf = part == 0 ? dd : that[i] / sqrt(N);
+        const double yc = part == 0 ? that[i] / sqrt(N) : 0.0;
+        v[10] += yf; v[11] += yf * yf; v[12] += yc; v[13] += yc * yc;
+    }
+    __shared__ double sh[8][14];
+#pragma unroll
+    for (int i = 0; i < 14; ++i)
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) v[i] += __shfl_xor_sync(kFullMask, v[i], off);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < 14; ++i) sh[w][i] = v[i];
+    __syncthreads();
+    if (threadIdx.x < 14 && threadIdx.x < stride) {
+        double t = 0.0;
+        for (int ww = 0; ww < 8; ++ww) t += sh[ww][threadIdx.x];
+        partials[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = t;
+    }
+}
+
+// ------------------------------------------------------------------ launch
+cudaError_t launch_features(const FeatArgs& a, int max_ctas, cudaStream_t st) {
+    const size_t smem = sizeof(float) * (kModes * a.n * a.n + 4 * kFeat);
+    cudaError_t e = cudaFuncSetAttribute(feature_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int grid = (int)std::min<long long>(a.count, max_ctas);
+    feature_kernel<<<grid, 128, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_direct_features(const FeatArgs& a, cudaStream_t st) {
+    const long long threads = a.count * (kFeat / 4);
+    direct_feature_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gemm(const GemmArgs& g, cudaStream_t st) {
+    const dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM);
+    gemm_bf16_kernel<<<grid, 128, 0, st>>>(g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_out_forward(const __nv_bfloat16* H, const float* w, const float* b, int B, int K, float* y,
+                               cudaStream_t st) {
+    out_forward_kernel<<<(B + 7) / 8, 256, 0, st>>>(H, w, b, B, K, y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_out_backward(const float* y, const float* t, const __nv_bfloat16* H, const float* w, int B, int K,
+                                float* dy, __nv_bfloat16* dH, float* dw, float* db, cudaStream_t st) {
+    out_backward_kernel<<<(unsigned)(((long long)B * K + 255) / 256), 256, 0, st>>>(y, t, H, w, B, K, dy, dH);
+    out_weight_grad_kernel<<<(K + 1 + 127) / 128, 128, 0, st>>>(dy, H, B, K, dw, db);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_colsum(const __nv_bfloat16* Xb, const float* Xf, int B, int N, float* out, cudaStream_t st) {
+    colsum_kernel<<<(N + 127) / 128, 128, 0, st>>>(Xb, Xf, B, N, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float* theta, const float* grad, float* m1, float* m2, int P, float lr, float b1, float b2,
+                        float eps, float c1, float c2, const int* bf_index, __nv_bfloat16* theta_bf,
+                        cudaStream_t st) {
+    adam_kernel<<<(P + 255) / 256, 256, 0, st>>>(theta, grad, m1, m2, P, lr, b1, b2, eps, c1, c2, bf_index, theta_bf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const __nv_bfloat16* X, const float* T, const int* idx, int B, __nv_bfloat16* Xb, float* Tb,
+                          cudaStream_t st) {
+    gather_kernel<<<(unsigned)(((long long)B * kFeat + 255) / 256), 256, 0, st>>>(X, T, idx, B, Xb, Tb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mse(const float* y, const float* t, int B, double* out, cudaStream_t st) {
+    mse_kernel<<<1, 256, 0, st>>>(y, t, B, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_surrogate_moments(const float* that, const double* d0, int d0_stride, int part, double N,
+                                     long long count, int stride, int blocks, double* partials, cudaStream_t st) {
+    surrogate_moments_kernel<<<blocks, 256, 0, st>>>(that, d0, d0_stride, part, N, count, stride, partials);
+    return cudaGetLastError();
+}
+
+}  // namespace dk

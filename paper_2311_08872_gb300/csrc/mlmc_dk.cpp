@@ -7,10 +7,13 @@
 #include <cmath>
 #include <complex>
 #include <cstdio>
+#include <numeric>
+#include <random>
 #include <cstring>
 #include <string>
 #include <vector>
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "dk_kernels.h"
@@ -77,9 +80,37 @@ struct mlmc_dk_ctx {
     cudaGraphExec_t gexec = nullptr;
     double* d_bsums = nullptr;        // device sums of mlmc_dk_run_batch
     double* h_bsums = nullptr;        // pinned host copy
+    struct Surrogate* sur = nullptr;  // learned level below level 0 (mlmc_dk_surrogate_init)
+};
+
+// Learned level below level 0: mode tables, network parameters (FP32 master,
+// BF16 copies of the weight matrices, Adam moments) and chunk buffers.
+struct Surrogate {
+    int n = 0, M = 0;
+    int chunk = 65536;                 // samples per inference chunk
+    int batch_cap = 0;                 // largest training batch
+    float *d_E = nullptr, *d_g = nullptr, *d_inv_sigma = nullptr;
+    float *d_theta = nullptr, *d_grad = nullptr, *d_m1 = nullptr, *d_m2 = nullptr;
+    __nv_bfloat16* d_wbf = nullptr;    // BF16 W1 | W2 | W3 | W4
+    int* d_bfidx = nullptr;            // parameter -> BF16 index (-1 for biases)
+    __nv_bfloat16 *d_X = nullptr, *d_H1 = nullptr, *d_H2 = nullptr, *d_H3 = nullptr;
+    __nv_bfloat16 *d_dH1 = nullptr, *d_dH2 = nullptr, *d_dH3 = nullptr;
+    float *d_y = nullptr, *d_dy = nullptr, *d_T = nullptr, *d_Xf = nullptr;
+    double* d_samp = nullptr;          // level-0 per-sample outputs of a chunk
+    double* d_D0 = nullptr;
+    double* d_part = nullptr;          // moment partials [stride][blocks]
+    double* d_loss = nullptr;
+    __nv_bfloat16* d_trainX = nullptr; // training pairs
+    float* d_trainT = nullptr;
+    int* d_idx = nullptr;
+    int64_t n_train = 0;
+    int64_t adam_t = 0;
+    int64_t next_id[2] = {0, 0};       // [0] level below 0, [1] correction level
+    double kernel_s[2] = {0, 0};
 };
 
 namespace {
+void free_surrogate(Surrogate* s);
 
 int fail(mlmc_dk_ctx* ctx, int code, const std::string& msg) {
     if (ctx) ctx->err = msg; else g_init_error = msg;
@@ -341,6 +372,8 @@ void release(mlmc_dk_ctx* c) {
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     cudaFree(c->d_bsums);
     if (c->h_bsums) cudaFreeHost(c->h_bsums);
+    free_surrogate(c->sur);
+    c->sur = nullptr;
 }
 
 }  // namespace
@@ -1000,6 +1033,523 @@ int mlmc_dk_load_state(mlmc_dk_ctx* ctx, const void* buf, size_t len) {
     ctx->next_id[0] = a;
     ctx->next_id[1] = b;
     return MLMC_DK_OK;
+}
+
+}  // extern "C"
+
+// ===================================================== learned level below 0
+namespace {
+
+constexpr int kP = 148481;   // 64*256+256 + 2*(256*256+256) + 256+1
+constexpr int kOffW1 = 0, kOffB1 = 16384, kOffW2 = 16640, kOffB2 = 82176, kOffW3 = 82432, kOffB3 = 147968,
+              kOffW4 = 148224, kOffB4 = 148480;
+constexpr int kBfW1 = 0, kBfW2 = 16384, kBfW3 = 81920, kBfW4 = 147456, kBfTotal = 147712;
+constexpr int kMomentBlocks = 128;
+
+void free_surrogate(Surrogate* s) {
+    if (!s) return;
+    for (void* p : {(void*)s->d_E, (void*)s->d_g, (void*)s->d_inv_sigma, (void*)s->d_theta, (void*)s->d_grad,
+                    (void*)s->d_m1, (void*)s->d_m2, (void*)s->d_wbf, (void*)s->d_bfidx, (void*)s->d_X,
+                    (void*)s->d_H1, (void*)s->d_H2, (void*)s->d_H3, (void*)s->d_dH1, (void*)s->d_dH2,
+                    (void*)s->d_dH3, (void*)s->d_y, (void*)s->d_dy, (void*)s->d_T, (void*)s->d_Xf,
+                    (void*)s->d_samp, (void*)s->d_D0, (void*)s->d_part, (void*)s->d_loss, (void*)s->d_trainX,
+                    (void*)s->d_trainT, (void*)s->d_idx})
+        cudaFree(p);
+    delete s;
+}
+
+// The 32 lowest real orthonormal modes of the n x n grid: wave vectors with
+// k1 > 0, or k1 = 0 and k2 > 0 (Nyquist lines excluded), ordered by |k|^2
+// then (k1, k2); a cosine and a sine mode each, scaled to unit plain-sum norm.
+void build_modes(int n, double mu, int M, std::vector<float>& E, std::vector<float>& g, std::vector<float>& isig) {
+    std::vector<std::pair<int, int>> ks;
+    for (int k1 = 0; k1 <= n / 2; ++k1)
+        for (int k2 = -n / 2 + 1; k2 <= n / 2; ++k2) {
+            if ((k1 == 0 && k2 <= 0) || 2 * k1 == n || 2 * std::abs(k2) == n) continue;
+            ks.push_back({k1, k2});
+        }
+    std::sort(ks.begin(), ks.end(), [](const std::pair<int, int>& a, const std::pair<int, int>& b) {
+        const int na = a.first * a.first + a.second * a.second, nb = b.first * b.first + b.second * b.second;
+        return na != nb ? na < nb : a < b;  // (k1, k2) lexicographic among equal |k|^2
+    });
+    E.assign((size_t)dk::kModes * n * n, 0.f);
+    g.assign(dk::kModes, 0.f);
+    isig.assign(dk::kFeat, 0.f);
+    const double scale = std::sqrt(2.0 / ((double)n * n));
+    for (int j = 0; j < dk::kModes / 2; ++j) {
+        const int k1 = ks[j].first, k2 = ks[j].second;
+        const double gk = 1.0 - 2.0 * mu * (std::pow(std::sin(M_PI * k1 / n), 2) + std::pow(std::sin(M_PI * k2 / n), 2));
+        double var = 0.0, p = 1.0;
+        for (int i = 0; i < M; ++i, p *= gk * gk) var += p;
+        for (int cs = 0; cs < 2; ++cs) {
+            const int mode = 2 * j + cs;
+            g[mode] = (float)gk;
+            for (int i1 = 0; i1 < n; ++i1)
+                for (int i2 = 0; i2 < n; ++i2) {
+                    const double ang = 2.0 * M_PI * (double)(k1 * i1 + k2 * i2) / n;
+                    E[(size_t)mode * n * n + i1 * n + i2] = (float)(scale * (cs == 0 ? std::cos(ang) : std::sin(ang)));
+                }
+            isig[2 * mode] = isig[2 * mode + 1] = (float)(1.0 / std::sqrt(var));
+        }
+    }
+}
+
+dk::GemmArgs gemm(int M, int N, int K, const __nv_bfloat16* A, long long sam, long long sak, const __nv_bfloat16* B,
+                  long long sbk, long long sbn) {
+    dk::GemmArgs g{};
+    g.M = M; g.N = N; g.K = K;
+    g.A = A; g.sam = sam; g.sak = sak;
+    g.B = B; g.sbk = sbk; g.sbn = sbn;
+    return g;
+}
+
+// Network forward on n standardised feature rows X (n <= chunk): y = That.
+cudaError_t mlp_forward(Surrogate* s, const __nv_bfloat16* X, int n, float* y, cudaStream_t st) {
+    cudaError_t e;
+    dk::GemmArgs g = gemm(n, dk::kHidden, dk::kFeat, X, dk::kFeat, 1, s->d_wbf + kBfW1, 1, dk::kFeat);
+    g.Cb = s->d_H1; g.ldcb = dk::kHidden; g.bias = s->d_theta + kOffB1; g.relu = 1;
+    if ((e = dk::launch_gemm(g, st)) != cudaSuccess) return e;
+    g = gemm(n, dk::kHidden, dk::kHidden, s->d_H1, dk::kHidden, 1, s->d_wbf + kBfW2, 1, dk::kHidden);
+    g.Cb = s->d_H2; g.ldcb = dk::kHidden; g.bias = s->d_theta + kOffB2; g.relu = 1;
+    if ((e = dk::launch_gemm(g, st)) != cudaSuccess) return e;
+    g = gemm(n, dk::kHidden, dk::kHidden, s->d_H2, dk::kHidden, 1, s->d_wbf + kBfW3, 1, dk::kHidden);
+    g.Cb = s->d_H3; g.ldcb = dk::kHidden; g.bias = s->d_theta + kOffB3; g.relu = 1;
+    if ((e = dk::launch_gemm(g, st)) != cudaSuccess) return e;
+    return dk::launch_out_forward(s->d_H3, s->d_theta + kOffW4, s->d_theta + kOffB4, n, dk::kHidden, y, st);
+}
+
+// Mean-squared-error gradient of a batch (after mlp_forward on it) into d_grad.
+cudaError_t mlp_backward(Surrogate* s, const __nv_bfloat16* X, const float* T, int B, cudaStream_t st) {
+    cudaError_t e;
+    float* G = s->d_grad;
+    if ((e = dk::launch_out_backward(s->d_y, T, s->d_H3, s->d_theta + kOffW4, B, dk::kHidden, s->d_dy, s->d_dH3,
+                                     G + kOffW4, G + kOffB4, st)) != cudaSuccess)
+        return e;
+    struct Layer { const __nv_bfloat16* dH; const __nv_bfloat16* Hin; int K; float* gW; float* gb;
+                   const __nv_bfloat16* W; __nv_bfloat16* dHin; };
+    const Layer layers[3] = {
+        {s->d_dH3, s->d_H2, dk::kHidden, G + kOffW3, G + kOffB3, s->d_wbf + kBfW3, s->d_dH2},
+        {s->d_dH2, s->d_H1, dk::kHidden, G + kOffW2, G + kOffB2, s->d_wbf + kBfW2, s->d_dH1},
+        {s->d_dH1, X, dk::kFeat, G + kOffW1, G + kOffB1, nullptr, nullptr}};
+    for (const Layer& L : layers) {
+        // dW = dH^T Hin  (256 x K, summed over the batch)
+        dk::GemmArgs g = gemm(dk::kHidden, L.K, B, L.dH, 1, dk::kHidden, L.Hin, L.K, 1);
+        g.C = L.gW; g.ldc = L.K;
+        if ((e = dk::launch_gemm(g, st)) != cudaSuccess) return e;
+        if ((e = dk::launch_colsum(L.dH, nullptr, B, dk::kHidden, L.gb, st)) != cudaSuccess) return e;
+        if (L.W) {
+            // dHin = (dH W) * (Hin > 0)
+            g = gemm(B, dk::kHidden, dk::kHidden, L.dH, dk::kHidden, 1, L.W, dk::kHidden, 1);
+            g.Cb = L.dHin; g.ldcb = dk::kHidden; g.mask = L.Hin; g.ldm = dk::kHidden;
+            if ((e = dk::launch_gemm(g, st)) != cudaSuccess) return e;
+        }
+    }
+    return cudaSuccess;
+}
+
+cudaError_t upload_params(Surrogate* s, const float* theta_host, cudaStream_t st) {
+    cudaError_t e = cudaMemcpyAsync(s->d_theta, theta_host, sizeof(float) * kP, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    std::vector<__nv_bfloat16> wb(kBfTotal);
+    std::vector<int> idx(kP, -1);
+    for (int i = 0; i < kP; ++i) {
+        int j = -1;
+        if (i < kOffB1) j = kBfW1 + i;
+        else if (i >= kOffW2 && i < kOffB2) j = kBfW2 + (i - kOffW2);
+        else if (i >= kOffW3 && i < kOffB3) j = kBfW3 + (i - kOffW3);
+        else if (i >= kOffW4 && i < kOffB4) j = kBfW4 + (i - kOffW4);
+        idx[i] = j;
+        if (j >= 0) wb[j] = __float2bfloat16_rn(theta_host[i]);
+    }
+    if ((e = cudaMemcpyAsync(s->d_wbf, wb.data(), sizeof(__nv_bfloat16) * kBfTotal, cudaMemcpyHostToDevice, st)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaMemcpyAsync(s->d_bfidx, idx.data(), sizeof(int) * kP, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return e;
+    return cudaStreamSynchronize(st);
+}
+
+dk::FeatArgs feat_args(mlmc_dk_ctx* c, int level_tag, int stream_tag, int64_t first, int64_t n, uint64_t seed,
+                       __nv_bfloat16* X, float* Xf) {
+    Surrogate* s = c->sur;
+    dk::FeatArgs a{};
+    a.E = s->d_E; a.g = s->d_g; a.inv_sigma = s->d_inv_sigma;
+    a.n = s->n; a.M = s->M;
+    a.key0 = (uint32_t)(seed & 0xffffffffu);
+    a.key1 = (uint32_t)(seed >> 32);
+    a.tag = ((uint32_t)level_tag & 0xffu) | (((uint32_t)stream_tag & 0xffu) << 8);
+    a.first = first; a.count = n;
+    a.X = X; a.Xf = Xf;
+    return a;
+}
+
+int sur_fail(mlmc_dk_ctx* c, cudaError_t e, const char* what) { return cuda_fail(c, e, what); }
+
+}  // namespace
+
+extern "C" {
+
+int mlmc_dk_surrogate_init(mlmc_dk_ctx* ctx, uint64_t seed) {
+    if (!ctx) return fail(nullptr, MLMC_DK_ERR_INVALID, "null context");
+    if (ctx->n_obs != 1 || ctx->products)
+        return fail(ctx, MLMC_DK_ERR_INVALID, "surrogate: one observable, no products");
+    const LevelTab& l0 = ctx->lv[0];
+    if (l0.n < 8 || l0.n > 32 || l0.streamed)
+        return fail(ctx, MLMC_DK_ERR_UNSUPPORTED, "surrogate: level-0 grid must be 8^2..32^2");
+    free_surrogate(ctx->sur);
+    Surrogate* s = ctx->sur = new Surrogate();
+    s->n = l0.n;
+    s->M = l0.M;
+    s->batch_cap = 4096;
+    std::vector<float> E, g, isig;
+    build_modes(l0.n, l0.tau / (l0.h * l0.h), l0.M, E, g, isig);
+    const size_t ch = (size_t)s->chunk;
+    cudaError_t e;
+    auto alloc = [&](void** p, size_t bytes) { return e == cudaSuccess ? (e = cudaMalloc(p, bytes)) : e; };
+    e = cudaSuccess;
+    alloc((void**)&s->d_E, sizeof(float) * E.size());
+    alloc((void**)&s->d_g, sizeof(float) * g.size());
+    alloc((void**)&s->d_inv_sigma, sizeof(float) * isig.size());
+    alloc((void**)&s->d_theta, sizeof(float) * kP);
+    alloc((void**)&s->d_grad, sizeof(float) * kP);
+    alloc((void**)&s->d_m1, sizeof(float) * kP);
+    alloc((void**)&s->d_m2, sizeof(float) * kP);
+    alloc((void**)&s->d_wbf, sizeof(__nv_bfloat16) * kBfTotal);
+    alloc((void**)&s->d_bfidx, sizeof(int) * kP);
+    alloc((void**)&s->d_X, sizeof(__nv_bfloat16) * ch * dk::kFeat);
+    alloc((void**)&s->d_Xf, sizeof(float) * ch * dk::kFeat);
+    alloc((void**)&s->d_H1, sizeof(__nv_bfloat16) * ch * dk::kHidden);
+    alloc((void**)&s->d_H2, sizeof(__nv_bfloat16) * ch * dk::kHidden);
+    alloc((void**)&s->d_H3, sizeof(__nv_bfloat16) * ch * dk::kHidden);
+    alloc((void**)&s->d_dH1, sizeof(__nv_bfloat16) * s->batch_cap * dk::kHidden);
+    alloc((void**)&s->d_dH2, sizeof(__nv_bfloat16) * s->batch_cap * dk::kHidden);
+    alloc((void**)&s->d_dH3, sizeof(__nv_bfloat16) * s->batch_cap * dk::kHidden);
+    alloc((void**)&s->d_y, sizeof(float) * ch);
+    alloc((void**)&s->d_dy, sizeof(float) * s->batch_cap);
+    alloc((void**)&s->d_T, sizeof(float) * ch);
+    alloc((void**)&s->d_samp, sizeof(double) * ch * 4);
+    alloc((void**)&s->d_part, sizeof(double) * ctx->stride * kMomentBlocks);
+    alloc((void**)&s->d_loss, sizeof(double));
+    if (e == cudaSuccess) e = cudaMemcpy(s->d_E, E.data(), sizeof(float) * E.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(s->d_g, g.data(), sizeof(float) * g.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(s->d_inv_sigma, isig.data(), sizeof(float) * isig.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        free_surrogate(s);
+        ctx->sur = nullptr;
+        return sur_fail(ctx, e, "surrogate buffers");
+    }
+    // He-uniform weights, zero biases, from a splitmix64 stream of `seed`
+    std::vector<float> theta(kP, 0.f);
+    uint64_t st = seed ^ 0x5deece66dull;
+    auto uni = [&]() {
+        uint64_t z = (st += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        return (double)(z >> 11) / 9007199254740992.0;
+    };
+    const int fan[4] = {dk::kFeat, dk::kHidden, dk::kHidden, dk::kHidden};
+    const int offW[4] = {kOffW1, kOffW2, kOffW3, kOffW4};
+    const int cnt[4] = {dk::kFeat * dk::kHidden, dk::kHidden * dk::kHidden, dk::kHidden * dk::kHidden, dk::kHidden};
+    for (int l = 0; l < 4; ++l) {
+        const double lim = std::sqrt(6.0 / fan[l]);
+        for (int i = 0; i < cnt[l]; ++i) theta[offW[l] + i] = (float)((2.0 * uni() - 1.0) * lim * (l == 3 ? 0.1 : 1.0));
+    }
+    if ((e = upload_params(s, theta.data(), ctx->stream)) != cudaSuccess) return sur_fail(ctx, e, "surrogate params");
+    return MLMC_DK_OK;
+}
+
+int mlmc_dk_surrogate_params(mlmc_dk_ctx* ctx, float* theta_out, const float* theta_in) {
+    if (!ctx || !ctx->sur) return fail(ctx, MLMC_DK_ERR_INVALID, "surrogate not initialised");
+    cudaError_t e;
+    if (theta_in) {
+        if ((e = upload_params(ctx->sur, theta_in, ctx->stream)) != cudaSuccess) return sur_fail(ctx, e, "set params");
+        ctx->sur->adam_t = 0;
+    }
+    if (theta_out &&
+        (e = cudaMemcpy(theta_out, ctx->sur->d_theta, sizeof(float) * kP, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return sur_fail(ctx, e, "get params");
+    return MLMC_DK_OK;
+}
+
+int mlmc_dk_surrogate_features(mlmc_dk_ctx* ctx, int32_t direct, int32_t stream_tag, int64_t first, int64_t n,
+                               uint64_t seed, float* X_host) {
+    if (!ctx || !ctx->sur || n < 0 || n > ctx->sur->chunk || !X_host)
+        return fail(ctx, MLMC_DK_ERR_INVALID, "surrogate_features: bad arguments");
+    Surrogate* s = ctx->sur;
+    dk::FeatArgs a = feat_args(ctx, direct ? 0 : 1, stream_tag, first, n, seed, s->d_X, s->d_Xf);
+    cudaError_t e = direct ? dk::launch_direct_features(a, ctx->stream)
+                           : dk::launch_features(a, 152 * 8, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(X_host, s->d_Xf, sizeof(float) * n * dk::kFeat, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    return e == cudaSuccess ? MLMC_DK_OK : sur_fail(ctx, e, "surrogate features");
+}
+
+int mlmc_dk_surrogate_forward(mlmc_dk_ctx* ctx, const float* X_host, int64_t n, float* y_host) {
+    if (!ctx || !ctx->sur || n < 1 || n > ctx->sur->chunk || !X_host || !y_host)
+        return fail(ctx, MLMC_DK_ERR_INVALID, "surrogate_forward: bad arguments");
+    Surrogate* s = ctx->sur;
+    std::vector<__nv_bfloat16> xb((size_t)n * dk::kFeat);
+    for (size_t i = 0; i < xb.size(); ++i) xb[i] = __float2bfloat16_rn(X_host[i]);
+    cudaError_t e = cudaMemcpy(s->d_X, xb.data(), sizeof(__nv_bfloat16) * xb.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = mlp_forward(s, s->d_X, (int)n, s->d_y, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(y_host, s->d_y, sizeof(float) * n, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    return e == cudaSuccess ? MLMC_DK_OK : sur_fail(ctx, e, "surrogate forward");
+}
+
+int mlmc_dk_surrogate_loss_grad(mlmc_dk_ctx* ctx, const float* X_host, const float* T_host, int32_t B, double* loss,
+                                float* grad_host) {
+    if (!ctx || !ctx->sur || B < 1 || B > ctx->sur->batch_cap || !X_host || !T_host)
+        return fail(ctx, MLMC_DK_ERR_INVALID, "surrogate_loss_grad: bad arguments");
+    Surrogate* s = ctx->sur;
+    std::vector<__nv_bfloat16> xb((size_t)B * dk::kFeat);
+    for (size_t i = 0; i < xb.size(); ++i) xb[i] = __float2bfloat16_rn(X_host[i]);
+    cudaError_t e = cudaMemcpy(s->d_X, xb.data(), sizeof(__nv_bfloat16) * xb.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(s->d_T, T_host, sizeof(float) * B, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = mlp_forward(s, s->d_X, B, s->d_y, ctx->stream);
+    if (e == cudaSuccess) e = dk::launch_mse(s->d_y, s->d_T, B, s->d_loss, ctx->stream);
+    if (e == cudaSuccess) e = mlp_backward(s, s->d_X, s->d_T, B, ctx->stream);
+    if (e == cudaSuccess && loss) e = cudaMemcpyAsync(loss, s->d_loss, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess && grad_host)
+        e = cudaMemcpyAsync(grad_host, s->d_grad, sizeof(float) * kP, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    return e == cudaSuccess ? MLMC_DK_OK : sur_fail(ctx, e, "surrogate loss/grad");
+}
+
+int mlmc_dk_surrogate_train(mlmc_dk_ctx* ctx, int64_t n_pairs, int32_t epochs, int32_t batch, double lr, uint64_t seed,
+                            double* train_mse, double* val_mse, double* seconds) {
+    if (!ctx || !ctx->sur || n_pairs < 2 * batch || epochs < 1 || batch < 64 || batch > ctx->sur->batch_cap ||
+        batch % 64 || !(lr > 0))
+        return fail(ctx, MLMC_DK_ERR_INVALID, "surrogate_train: bad arguments");
+    const auto t0 = std::chrono::steady_clock::now();
+    Surrogate* s = ctx->sur;
+    cudaStream_t st = ctx->stream;
+    cudaError_t e = cudaSuccess;
+    if (s->n_train != n_pairs) {
+        cudaFree(s->d_trainX);
+        cudaFree(s->d_trainT);
+        cudaFree(s->d_idx);
+        s->d_trainX = nullptr; s->d_trainT = nullptr; s->d_idx = nullptr;
+        if ((e = cudaMalloc(&s->d_trainX, sizeof(__nv_bfloat16) * n_pairs * dk::kFeat)) != cudaSuccess ||
+            (e = cudaMalloc(&s->d_trainT, sizeof(float) * n_pairs)) != cudaSuccess ||
+            (e = cudaMalloc(&s->d_idx, sizeof(int) * n_pairs)) != cudaSuccess)
+            return sur_fail(ctx, e, "training buffers");
+        s->n_train = n_pairs;
+    }
+    // training pairs: level-0 paths of the training stream (3) and their features
+    std::vector<double> hs;
+    std::vector<float> ht;
+    const double sqrtN = std::sqrt(ctx->N);
+    for (int64_t done = 0; done < n_pairs; done += s->chunk) {
+        const int64_t n = std::min<int64_t>(s->chunk, n_pairs - done);
+        int rc = launch_batch(ctx, 0, 3, done, n, seed, ctx->d_sums, s->d_samp, st);
+        if (rc != MLMC_DK_OK) return rc;
+        dk::FeatArgs a = feat_args(ctx, 1, 3, done, n, seed, s->d_trainX + done * dk::kFeat, nullptr);
+        if ((e = dk::launch_features(a, 152 * 8, st)) != cudaSuccess) return sur_fail(ctx, e, "features");
+        hs.resize((size_t)n * 4);
+        if ((e = cudaMemcpyAsync(hs.data(), s->d_samp, sizeof(double) * n * 4, cudaMemcpyDeviceToHost, st)) !=
+                cudaSuccess ||
+            (e = cudaStreamSynchronize(st)) != cudaSuccess)
+            return sur_fail(ctx, e, "training targets");
+        ht.resize(n);
+        for (int64_t i = 0; i < n; ++i) ht[i] = (float)(sqrtN * hs[(size_t)i * 4]);   // sqrt(N) (Y_0 - Ybar_0)
+        if ((e = cudaMemcpy(s->d_trainT + done, ht.data(), sizeof(float) * n, cudaMemcpyHostToDevice)) != cudaSuccess)
+            return sur_fail(ctx, e, "training targets");
+    }
+    // last 1/16 held out for validation
+    const int64_t n_val = std::max<int64_t>(batch, n_pairs / 16);
+    const int64_t n_fit = (n_pairs - n_val) / batch * batch;
+    std::vector<int> idx(n_fit);
+    std::iota(idx.begin(), idx.end(), 0);
+    std::mt19937_64 rng(seed ^ 0x7261696eull);
+    if ((e = cudaMemsetAsync(s->d_m1, 0, sizeof(float) * kP, st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(s->d_m2, 0, sizeof(float) * kP, st)) != cudaSuccess)
+        return sur_fail(ctx, e, "adam state");
+    s->adam_t = 0;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    double last_loss = 0.0;
+    for (int ep = 0; ep < epochs; ++ep) {
+        std::shuffle(idx.begin(), idx.end(), rng);
+        if ((e = cudaMemcpyAsync(s->d_idx, idx.data(), sizeof(int) * n_fit, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(st)) != cudaSuccess)
+            return sur_fail(ctx, e, "shuffle");
+        // cosine-decayed step size over the epochs
+        const double lr_ep = lr * 0.5 * (1.0 + std::cos(M_PI * ep / (double)epochs));
+        for (int64_t b0 = 0; b0 < n_fit; b0 += batch) {
+            if ((e = dk::launch_gather(s->d_trainX, s->d_trainT, s->d_idx + b0, batch, s->d_X, s->d_T, st)) != cudaSuccess ||
+                (e = mlp_forward(s, s->d_X, batch, s->d_y, st)) != cudaSuccess ||
+                (e = mlp_backward(s, s->d_X, s->d_T, batch, st)) != cudaSuccess)
+                return sur_fail(ctx, e, "training step");
+            ++s->adam_t;
+            const float c1 = 1.f - std::pow(b1, (float)s->adam_t), c2 = 1.f - std::pow(b2, (float)s->adam_t);
+            if ((e = dk::launch_adam(s->d_theta, s->d_grad, s->d_m1, s->d_m2, kP, (float)lr_ep, b1, b2, eps, c1, c2,
+                                     s->d_bfidx, s->d_wbf, st)) != cudaSuccess)
+                return sur_fail(ctx, e, "adam");
+        }
+        if (ep == epochs - 1 && train_mse) {
+            // mean-squared error of the last batch's predictions (before its update)
+            if ((e = dk::launch_mse(s->d_y, s->d_T, batch, s->d_loss, st)) != cudaSuccess ||
+                (e = cudaMemcpyAsync(&last_loss, s->d_loss, sizeof(double), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+                (e = cudaStreamSynchronize(st)) != cudaSuccess)
+                return sur_fail(ctx, e, "train loss");
+        }
+    }
+    if (train_mse) *train_mse = last_loss;
+    if (val_mse) {
+        double acc = 0.0;
+        int64_t cnt = 0;
+        for (int64_t v0 = n_pairs - n_val; v0 < n_pairs; v0 += s->chunk) {
+            const int64_t n = std::min<int64_t>(s->chunk, n_pairs - v0);
+            double l = 0.0;
+            if ((e = mlp_forward(s, s->d_trainX + v0 * dk::kFeat, (int)n, s->d_y, st)) != cudaSuccess ||
+                (e = dk::launch_mse(s->d_y, s->d_trainT + v0, (int)n, s->d_loss, st)) != cudaSuccess ||
+                (e = cudaMemcpyAsync(&l, s->d_loss, sizeof(double), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+                (e = cudaStreamSynchronize(st)) != cudaSuccess)
+                return sur_fail(ctx, e, "validation");
+            acc += l * n;
+            cnt += n;
+        }
+        *val_mse = acc / cnt;
+    }
+    if (seconds) *seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return check_device_error(ctx);
+}
+
+int mlmc_dk_run_surrogate(mlmc_dk_ctx* ctx, int32_t part, int64_t n_samples, uint64_t seed, mlmc_dk_level_sums* sums) {
+    if (!ctx || !ctx->sur || (part != -1 && part != 0) || n_samples < 0 || !sums)
+        return fail(ctx, MLMC_DK_ERR_INVALID, "run_surrogate: bad arguments");
+    Surrogate* s = ctx->sur;
+    cudaStream_t st = ctx->stream;
+    cudaError_t e;
+    int64_t& next = s->next_id[part == -1 ? 0 : 1];
+    const auto t0 = std::chrono::steady_clock::now();
+    for (int64_t done = 0; done < n_samples; done += s->chunk) {
+        const int64_t n = std::min<int64_t>(s->chunk, n_samples - done);
+        const int64_t first = next + done;
+        if ((e = cudaEventRecord(ctx->ev0, st)) != cudaSuccess) return sur_fail(ctx, e, "event");
+        if (part == -1) {
+            // level below 0: standardised features drawn from their exact law (stream 2, level tag 0)
+            dk::FeatArgs a = feat_args(ctx, 0, 2, first, n, seed, s->d_X, nullptr);
+            if ((e = dk::launch_direct_features(a, st)) != cudaSuccess) return sur_fail(ctx, e, "direct features");
+        } else {
+            // correction level: the level-0 paths of the coupled stream and their own features
+            int rc = launch_batch(ctx, 0, 0, first, n, seed, ctx->d_sums, s->d_samp, st);
+            if (rc != MLMC_DK_OK) return rc;
+            dk::FeatArgs a = feat_args(ctx, 1, 0, first, n, seed, s->d_X, nullptr);
+            if ((e = dk::launch_features(a, 152 * 8, st)) != cudaSuccess) return sur_fail(ctx, e, "features");
+        }
+        if ((e = mlp_forward(s, s->d_X, (int)n, s->d_y, st)) != cudaSuccess ||
+            (e = dk::launch_surrogate_moments(s->d_y, s->d_samp, 4, part, ctx->N, n, ctx->stride, kMomentBlocks,
+                                              s->d_part, st)) != cudaSuccess ||
+            (e = dk::launch_reduce(s->d_part, kMomentBlocks, ctx->stride, ctx->d_sums, st)) != cudaSuccess ||
+            (e = cudaEventRecord(ctx->ev1, st)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(ctx->h_sums, ctx->d_sums, sizeof(double) * ctx->stride, cudaMemcpyDeviceToHost, st)) !=
+                cudaSuccess ||
+            (e = cudaStreamSynchronize(st)) != cudaSuccess)
+            return sur_fail(ctx, e, "surrogate level");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+        const double cost = part == -1 ? 0.0 : (double)ctx->lv[0].n * ctx->lv[0].n * ctx->lv[0].M;
+        accumulate(ctx, ctx->h_sums, sums, cost, 0.0, 1e-3 * ms, part == -1 ? 6 : 8);
+    }
+    next += n_samples;
+    const double wall = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    sums[0].wall_s += wall;
+    return check_device_error(ctx);
+}
+
+int mlmc_dk_estimate_surrogate(mlmc_dk_ctx* ctx, double eps, int32_t relative, uint64_t seed, mlmc_dk_result* out,
+                               mlmc_dk_level_sums* sur_out) {
+    if (!ctx || !ctx->sur || !out || !(eps > 0)) return fail(ctx, MLMC_DK_ERR_INVALID, "estimate_surrogate: bad arguments");
+    const auto t0 = std::chrono::steady_clock::now();
+    *out = mlmc_dk_result{};
+    // virtual levels: 0 = level below 0 (S), 1 = correction (P_0 - S), 1 + l = level l >= 1
+    const int VL = ctx->L_max + 2;
+    std::vector<mlmc_dk_level_sums> sums(VL);
+    std::vector<int64_t> target(VL, 0);
+    std::fill(ctx->next_id[0].begin(), ctx->next_id[0].end(), 0);
+    ctx->sur->next_id[0] = ctx->sur->next_id[1] = 0;
+    int L = ctx->L_start;
+    for (int v = 0; v <= L + 1; ++v) target[v] = ctx->pilot;
+    double eps_abs = relative ? -1.0 : eps;
+    int status = MLMC_DK_OK, converged = 0;
+    auto run = [&](int v, int64_t n) -> int {
+        if (v <= 1) return mlmc_dk_run_surrogate(ctx, v == 0 ? -1 : 0, n, seed, &sums[v]);
+        return mlmc_dk_run_level(ctx, v - 1, n, seed, &sums[v]);
+    };
+    for (int iter = 0; iter < 1000; ++iter) {
+        for (int v = 0; v <= L + 1; ++v) {
+            const int64_t need = target[v] - sums[v].n;
+            if (need > 0) {
+                const int rc = run(v, need);
+                if (rc != MLMC_DK_OK) return rc;
+            }
+        }
+        std::vector<double> E(L + 2), V(L + 2), C(L + 2);
+        for (int v = 0; v <= L + 1; ++v) {
+            const double m = (double)sums[v].n;
+            E[v] = sums[v].dp1 / m;
+            V[v] = std::max(0.0, (sums[v].dp2 - sums[v].dp1 * sums[v].dp1 / m) / (m - 1.0));
+            C[v] = std::max(sums[v].kernel_s / m, 1e-12);   // measured device seconds per sample
+        }
+        if (eps_abs < 0) {
+            double mu = 0;
+            for (double x : E) mu += x;
+            eps_abs = eps * std::fabs(mu);
+            if (!(eps_abs > 0)) return fail(ctx, MLMC_DK_ERR_INVALID, "relative eps with a zero pilot estimate");
+        }
+        double total = 0;
+        for (int v = 0; v <= L + 1; ++v) total += std::sqrt(V[v] * C[v]);
+        bool more = false;
+        for (int v = 0; v <= L + 1; ++v) {
+            const double opt = std::ceil(2.0 / (eps_abs * eps_abs) * std::sqrt(V[v] / C[v]) * total);
+            target[v] = std::max(target[v], (int64_t)std::min(opt, 9.0e18));
+            if ((double)(target[v] - sums[v].n) > 0.01 * (double)sums[v].n) more = true;
+        }
+        if (more) continue;
+        // stopping test on the level differences of the plain hierarchy (level 0 = S + (P_0 - S))
+        double worst = 0;
+        for (int t = 0; t <= 2 && L - t >= 0; ++t) {
+            const int l = L - t;
+            const double el = l == 0 ? E[0] + E[1] : E[l + 1];
+            worst = std::max(worst, std::pow(4.0, -t) * std::fabs(el));
+        }
+        if (worst / 3.0 < eps_abs / std::sqrt(2.0)) { converged = 1; break; }
+        if (L == ctx->L_max) { status = MLMC_DK_NOT_CONVERGED; break; }
+        ++L;
+        target[L + 1] = ctx->pilot;
+    }
+    out->L = L;
+    out->converged = converged;
+    out->eps_abs = eps_abs;
+    double est = 0.0;
+    for (int v = 0; v <= L + 1; ++v) {
+        const mlmc_dk_level_sums& q = sums[v];
+        const double m = (double)q.n;
+        const double Vv = std::max(0.0, (q.dp2 - q.dp1 * q.dp1 / m) / (m - 1.0));
+        est += q.dp1 / m;
+        out->variance += Vv / m;
+        out->cell_steps += q.cost;
+        if (v >= 1) {
+            const int l = v - 1;
+            out->M[l] = q.n;
+            out->E[l] = q.dp1 / m;
+            out->V[l] = Vv;
+            out->C[l] = q.kernel_s / m;
+            out->kernel_s[l] = q.kernel_s;
+            out->sample_steps += m * ctx->lv[l].M;
+            out->var_pf[l] = std::max(0.0, (q.pf2 - q.pf1 * q.pf1 / m) / (m - 1.0));
+        }
+        out->launches += q.launches;
+        out->d2h_bytes += q.d2h_bytes;
+    }
+    out->estimate = est;
+    out->estimates[0] = est;
+    if (sur_out) *sur_out = sums[0];
+    out->wall_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return status;
 }
 
 }  // extern "C"

@@ -119,6 +119,19 @@ def lib() -> ctypes.CDLL:
                                             vp, vp]
         L.mlmc_dk_run_batch.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.c_uint64, ctypes.POINTER(LevelSums)]
         L.mlmc_dk_batch_level_ms.argtypes = [vp, _dp]
+        fp = ctypes.POINTER(ctypes.c_float)
+        L.mlmc_dk_surrogate_init.argtypes = [vp, ctypes.c_uint64]
+        L.mlmc_dk_surrogate_params.argtypes = [vp, fp, fp]
+        L.mlmc_dk_surrogate_features.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64,
+                                                 ctypes.c_uint64, fp]
+        L.mlmc_dk_surrogate_forward.argtypes = [vp, fp, ctypes.c_int64, fp]
+        L.mlmc_dk_surrogate_loss_grad.argtypes = [vp, fp, fp, ctypes.c_int32, _dp, fp]
+        L.mlmc_dk_surrogate_train.argtypes = [vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                              ctypes.c_uint64, _dp, _dp, _dp]
+        L.mlmc_dk_run_surrogate.argtypes = [vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64,
+                                            ctypes.POINTER(LevelSums)]
+        L.mlmc_dk_estimate_surrogate.argtypes = [vp, ctypes.c_double, ctypes.c_int32, ctypes.c_uint64,
+                                                 ctypes.POINTER(Result), ctypes.POINTER(LevelSums)]
         L.mlmc_dk_set_variant.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
         L.mlmc_dk_tune.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]
         L.mlmc_dk_noise_dev.argtypes = [ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
@@ -265,6 +278,63 @@ class Context:
         sums = (LevelSums * ((self.L_max + 1) * self.n_quant))()
         _check(lib().mlmc_dk_run_batch(self._ctx, c, seed, sums), self._ctx)
         return [[sums[l * self.n_quant + q] for q in range(self.n_quant)] for l in range(self.L_max + 1)]
+
+    # ---- learned level below level 0
+    N_PARAMS = 148481
+
+    def surrogate_init(self, seed: int = 0):
+        _check(lib().mlmc_dk_surrogate_init(self._ctx, seed), self._ctx)
+
+    def surrogate_params(self, theta=None) -> np.ndarray:
+        fp = ctypes.POINTER(ctypes.c_float)
+        out = np.empty(self.N_PARAMS, dtype=np.float32)
+        tin = None if theta is None else np.ascontiguousarray(theta, dtype=np.float32)
+        _check(lib().mlmc_dk_surrogate_params(self._ctx, out.ctypes.data_as(fp),
+                                              None if tin is None else tin.ctypes.data_as(fp)), self._ctx)
+        return out
+
+    def surrogate_features(self, first: int, n: int, seed: int, stream_tag: int = 0, direct: bool = False):
+        fp = ctypes.POINTER(ctypes.c_float)
+        X = np.empty((n, 64), dtype=np.float32)
+        _check(lib().mlmc_dk_surrogate_features(self._ctx, int(direct), stream_tag, first, n, seed,
+                                                X.ctypes.data_as(fp)), self._ctx)
+        return X
+
+    def surrogate_forward(self, X) -> np.ndarray:
+        fp = ctypes.POINTER(ctypes.c_float)
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        y = np.empty(X.shape[0], dtype=np.float32)
+        _check(lib().mlmc_dk_surrogate_forward(self._ctx, X.ctypes.data_as(fp), X.shape[0], y.ctypes.data_as(fp)),
+               self._ctx)
+        return y
+
+    def surrogate_loss_grad(self, X, T):
+        fp = ctypes.POINTER(ctypes.c_float)
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        T = np.ascontiguousarray(T, dtype=np.float32)
+        g = np.empty(self.N_PARAMS, dtype=np.float32)
+        loss = ctypes.c_double(0.0)
+        _check(lib().mlmc_dk_surrogate_loss_grad(self._ctx, X.ctypes.data_as(fp), T.ctypes.data_as(fp), X.shape[0],
+                                                 ctypes.byref(loss), g.ctypes.data_as(fp)), self._ctx)
+        return loss.value, g
+
+    def surrogate_train(self, n_pairs: int, epochs: int, batch: int, lr: float, seed: int):
+        a, b, c = ctypes.c_double(0.0), ctypes.c_double(0.0), ctypes.c_double(0.0)
+        _check(lib().mlmc_dk_surrogate_train(self._ctx, n_pairs, epochs, batch, lr, seed, ctypes.byref(a),
+                                             ctypes.byref(b), ctypes.byref(c)), self._ctx)
+        return {"train_mse": a.value, "val_mse": b.value, "seconds": c.value}
+
+    def run_surrogate(self, part: int, n: int, seed: int, sums=None):
+        if sums is None:
+            sums = LevelSums()
+        _check(lib().mlmc_dk_run_surrogate(self._ctx, part, n, seed, ctypes.byref(sums)), self._ctx)
+        return sums
+
+    def estimate_surrogate(self, eps: float, relative: bool, seed: int):
+        r, s = Result(), LevelSums()
+        _check(lib().mlmc_dk_estimate_surrogate(self._ctx, eps, int(relative), seed, ctypes.byref(r), ctypes.byref(s)),
+               self._ctx, allow=(OK, NOT_CONVERGED))
+        return r, s
 
     def set_variant(self, level: int, coupled: bool, variant: int):
         _check(lib().mlmc_dk_set_variant(self._ctx, level, int(coupled), variant), self._ctx)
