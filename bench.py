@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adaptive", action="store_true", help="skip the Algorithm 1 / plain MC timing")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the learned level below 0")
     ap.add_argument("--adaptive-eps", type=float, default=1e-2,
                     help="relative eps of the fully measured Algorithm 1 run (0: the workload's)")
     return ap.parse_args()
@@ -195,8 +196,10 @@ def run_ours(args, wl, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream(dev)
+    from paper_2311_08872_gb300 import distributed as D
     alloc = list(wl.alloc) if wl.alloc else None
-    seed0 = wl.seed + 1000003 * rank
+    seed0 = wl.seed
+    first0 = D.first_sample(rank)          # ranks shard the sample ids (no collective on the data path)
 
     ctx = mlmc_dk.Context.from_workload(wl, stream=stream.cuda_stream)
     tune_s = ctx.tune(repeats=1)          # autotuner: fastest kernel variant per level (outside timing)
@@ -229,7 +232,7 @@ def run_ours(args, wl, rank, world, local_rank):
     def step(seed):
         # all levels concurrently: one CUDA-graph launch of the multi-level batch
         step_ev[0].record(stream)
-        ctx.run_batch_dev(alloc, 0, seed, sums.data_ptr(), stream.cuda_stream)
+        ctx.run_batch_dev(alloc, first0, seed, sums.data_ptr(), stream.cuda_stream)
         host.copy_(sums, non_blocking=True)
         step_ev[1].record(stream)
         stream.synchronize()
@@ -324,7 +327,30 @@ def run_ours(args, wl, rank, world, local_rank):
               "how": "eps-optimal cost from the timed batch's V_l at its measured cell-step rate; "
                      "plain MC from 2 Var[P_L]/eps^2 samples at the measured MC time per sample"}
 
-    # ---- end to end through the public API with host buffers
+    # ---- learned level below 0 (trained on 2^18 level-0 paths): the same eps-optimal
+    #      time with levels {S, P_0 - S, 1..L} in place of {0, 1..L}
+    surrogate = None
+    if not args.no_surrogate:
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        ctx.surrogate_init(seed0 + 3)
+        tr = ctx.surrogate_train(1 << 18, epochs=8, batch=1024, lr=1e-3, seed=seed0 + 4)
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t
+        n_s = 200000
+        s_sur = ctx.run_surrogate(-1, n_s, seed0 + 5)
+        s_cor = ctx.run_surrogate(0, n_s, seed0 + 6)
+        var = lambda q: max(0.0, (q.dp2 - q.dp1 ** 2 / q.n) / (q.n - 1))
+        t_l = [c / rate for c in C]        # seconds per sample of levels 0..L at the batch's rate
+        terms = [math.sqrt(var(s_sur) * s_sur.kernel_s / n_s), math.sqrt(var(s_cor) * s_cor.kernel_s / n_s)]
+        terms += [math.sqrt(v * tt) for v, tt in zip(V[1:], t_l[1:])]
+        t_sur = 2.0 / eps_abs ** 2 * sum(terms) ** 2
+        surrogate = {"train_s": train_s, "train_pairs": 1 << 18, "val_mse": tr["val_mse"],
+                     "var_P0": V[0], "var_S": var(s_sur), "var_P0_minus_S": var(s_cor),
+                     "s_per_sample_S": s_sur.kernel_s / n_s, "s_per_sample_P0_minus_S": s_cor.kernel_s / n_s,
+                     "s_per_sample_P0": t_l[0], "mlmc_s_to_eps": t_sur,
+                     "mlmc_s_to_eps_incl_training": t_sur + train_s, "extrapolated": True}
+
     e2e = None
     if not args.no_e2e:
         ctx.close()
@@ -370,7 +396,7 @@ def run_ours(args, wl, rank, world, local_rank):
                    "T": wl.T, "N": wl.N, "mu": wl.mu, "eps_rel": wl.eps_rel, "alloc": alloc,
                    "sample_steps_per_step": sample_steps, "cell_steps_per_step": cell_steps,
                    "l2": "512 MiB buffer zeroed between timed steps, outside the step events",
-                   "parallelism": f"{world} independent rank(s), own seeds",
+                   "parallelism": f"{world} rank(s), disjoint sample ids per rank",
                    "kernel_variants": [{"n": i.n, "C": i.lane_cols, "R": i.lane_rows, "cluster": i.cluster}
                                        for i in info],
                    "tune_s": tune_s},
@@ -387,6 +413,9 @@ def run_ours(args, wl, rank, world, local_rank):
     line["to_eps"] = to_eps
     line["mc"] = mc
     line["mlmc_adaptive_measured"] = adaptive
+    if surrogate:
+        line["surrogate"] = surrogate
+        line["mlmc_surrogate_s_to_eps"] = surrogate["mlmc_s_to_eps_incl_training"]
     return line
 
 
