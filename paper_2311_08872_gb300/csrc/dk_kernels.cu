@@ -195,11 +195,88 @@ __device__ __forceinline__ void flux_update(int32_t (&q)[RR][CC], const int32_t 
     }
 }
 
+// The same update in two phases around a split barrier: phase 1 updates the
+// interior rows (1 .. RR-2), which need no vertical halo, and keeps the old
+// values of rows 1 and RR-2 that the boundary rows' fluxes need; phase 2
+// (after the halo arrives) updates rows 0 and RR-1.
+template <int RR, int CC>
+__device__ __forceinline__ void flux_update_interior(int32_t (&q)[RR][CC], const int32_t (&G1)[RR][CC],
+                                                     const int32_t (&G2)[RR][CC], const int32_t (&qL)[RR],
+                                                     const int32_t (&gL)[RR], const int32_t (&qR)[RR],
+                                                     const int32_t (&gR)[RR], int32_t A, int32_t (&keep1)[CC],
+                                                     int32_t (&keep2)[CC]) {
+#pragma unroll
+    for (int c = 0; c < CC; ++c) {
+        keep1[c] = q[1][c];
+        keep2[c] = q[RR - 2][c];
+    }
+    if constexpr (RR >= 3) {
+        int32_t V[RR + 1][CC];
+#pragma unroll
+        for (int c = 0; c < CC; ++c)
+#pragma unroll
+            for (int r = 1; r < RR; ++r) V[r][c] = edge_flux(A, q[r][c] - q[r - 1][c]);
+#pragma unroll
+        for (int r = 1; r + 1 < RR; ++r) {
+            int32_t H[CC + 1];
+            H[0] = edge_flux(A, q[r][0] - qL[r]);
+#pragma unroll
+            for (int c = 1; c < CC; ++c) H[c] = edge_flux(A, q[r][c] - q[r][c - 1]);
+            H[CC] = edge_flux(A, qR[r] - q[r][CC - 1]);
+#pragma unroll
+            for (int c = 0; c < CC; ++c) {
+                const int32_t g2r = (c + 1 < CC) ? G2[r][c + 1] : gR[r];
+                const int32_t g2l = (c > 0) ? G2[r][c - 1] : gL[r];
+                q[r][c] += (V[r + 1][c] - V[r][c]) + (H[c + 1] - H[c]) + (G1[r + 1][c] - G1[r - 1][c]) + (g2r - g2l);
+            }
+        }
+    }
+}
+
+template <int RR, int CC>
+__device__ __forceinline__ void flux_update_boundary(int32_t (&q)[RR][CC], const int32_t (&G1)[RR][CC],
+                                                     const int32_t (&G2)[RR][CC], const int32_t (&qU)[CC],
+                                                     const int32_t (&gU)[CC], const int32_t (&qD)[CC],
+                                                     const int32_t (&gD)[CC], const int32_t (&qL)[RR],
+                                                     const int32_t (&gL)[RR], const int32_t (&qR)[RR],
+                                                     const int32_t (&gR)[RR], int32_t A, const int32_t (&keep1)[CC],
+                                                     const int32_t (&keep2)[CC]) {
+    // row 0 (its lower neighbour is the old row 1) and row RR-1 (upper neighbour the old row RR-2)
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        const int r = side == 0 ? 0 : RR - 1;
+        if (side == 1 && RR == 1) break;
+        int32_t H[CC + 1];
+        H[0] = edge_flux(A, q[r][0] - qL[r]);
+#pragma unroll
+        for (int c = 1; c < CC; ++c) H[c] = edge_flux(A, q[r][c] - q[r][c - 1]);
+        H[CC] = edge_flux(A, qR[r] - q[r][CC - 1]);
+#pragma unroll
+        for (int c = 0; c < CC; ++c) {
+            const int32_t up = (r == 0) ? qU[c] : keep2[c];
+            const int32_t dn = (r == RR - 1) ? qD[c] : keep1[c];
+            const int32_t g1u = (r == 0) ? gU[c] : G1[r - 1][c];
+            const int32_t g1d = (r == RR - 1) ? gD[c] : G1[r + 1][c];
+            const int32_t x = q[r][c];
+            const int32_t v = edge_flux(A, dn - x) - edge_flux(A, x - up);
+            const int32_t g2r = (c + 1 < CC) ? G2[r][c + 1] : gR[r];
+            const int32_t g2l = (c > 0) ? G2[r][c - 1] : gL[r];
+            q[r][c] = x + v + (H[c + 1] - H[c]) + (g1d - g1u) + (g2r - g2l);
+        }
+    }
+}
+
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory"); }
+
 template <class S>
 __global__ void __launch_bounds__(S::THREADS) level_kernel(const KArgs a) {
     constexpr int NF = S::NF, NC = S::NC, FR = S::FR, FC = S::FC, R = S::R, C = S::C;
     constexpr int LPB = S::LPB, LPS = S::LPS, CL = S::CL, BPC = S::BPC;
     constexpr bool CPL = S::COUPLED;
+    // clusters split the per-step barrier: arrive after publishing the edge
+    // rows, update the interior rows, then wait for the neighbours' rows
+    constexpr bool SPLIT = !S::WARP && (CL > 1);
     extern __shared__ __align__(16) unsigned char smem_raw[];
 
     const int tid = threadIdx.x;
@@ -310,6 +387,19 @@ __global__ void __launch_bounds__(S::THREADS) level_kernel(const KArgs a) {
                 }
             }
 
+            if constexpr (SPLIT) {
+                const int par = m & 1;
+                put_edge<FC, LPB>(fx + ((par * 2 + 0) * BPC + bl) * NF, lib, q[0], G1[0]);
+                put_edge<FC, LPB>(fx + ((par * 2 + 1) * BPC + bl) * NF, lib, q[FR - 1], G1[FR - 1]);
+                if constexpr (CPL) {
+                    if (cstep) {
+                        put_edge<C, LPB>(cx + bl * NC, lib, qc[0], Gc1[0]);
+                        put_edge<C, LPB>(cx + (BPC + bl) * NC, lib, qc[R - 1], Gc1[R - 1]);
+                    }
+                }
+                cluster_arrive();
+            }
+
             // ---- horizontal halo by shuffles within the band segment
             int32_t qL[FR], gL[FR], qR[FR], gR[FR];
 #pragma unroll
@@ -334,6 +424,7 @@ __global__ void __launch_bounds__(S::THREADS) level_kernel(const KArgs a) {
 
             // ---- vertical halo
             int32_t qU[FC], gU[FC], qD[FC], gD[FC];
+            int32_t keep1[FC], keep2[FC];   // old rows 1 and FR-2 (split barrier only)
             int32_t cqU[C], cgU[C], cqD[C], cgD[C];
             if constexpr (S::WARP) {
 #pragma unroll
@@ -358,17 +449,22 @@ __global__ void __launch_bounds__(S::THREADS) level_kernel(const KArgs a) {
                 const int par = m & 1;
                 int2* const ftop = fx + ((par * 2 + 0) * BPC) * NF;
                 int2* const fbot = fx + ((par * 2 + 1) * BPC) * NF;
-                put_edge<FC, LPB>(ftop + bl * NF, lib, q[0], G1[0]);
-                put_edge<FC, LPB>(fbot + bl * NF, lib, q[FR - 1], G1[FR - 1]);
                 int2* const ctop = cx;
                 int2* const cbot = cx + BPC * NC;
-                if constexpr (CPL) {
-                    if (cstep) {
-                        put_edge<C, LPB>(ctop + bl * NC, lib, qc[0], Gc1[0]);
-                        put_edge<C, LPB>(cbot + bl * NC, lib, qc[R - 1], Gc1[R - 1]);
+                if constexpr (SPLIT) {
+                    flux_update_interior<FR, FC>(q, G1, G2, qL, gL, qR, gR, a.Af, keep1, keep2);
+                    cluster_wait();
+                } else {
+                    put_edge<FC, LPB>(ftop + bl * NF, lib, q[0], G1[0]);
+                    put_edge<FC, LPB>(fbot + bl * NF, lib, q[FR - 1], G1[FR - 1]);
+                    if constexpr (CPL) {
+                        if (cstep) {
+                            put_edge<C, LPB>(ctop + bl * NC, lib, qc[0], Gc1[0]);
+                            put_edge<C, LPB>(cbot + bl * NC, lib, qc[R - 1], Gc1[R - 1]);
+                        }
                     }
+                    block_or_cluster_sync<S>();
                 }
-                block_or_cluster_sync<S>();
                 const int2* above = (bl > 0) ? fbot + (bl - 1) * NF
                                              : peer<S>(fbot + (BPC - 1) * NF, (rank + CL - 1) % CL);
                 const int2* below = (bl + 1 < BPC) ? ftop + (bl + 1) * NF : peer<S>(ftop, (rank + 1) % CL);
@@ -386,7 +482,11 @@ __global__ void __launch_bounds__(S::THREADS) level_kernel(const KArgs a) {
             }
 
             // ---- updates
-            flux_update<FR, FC>(q, G1, G2, qU, gU, qD, gD, qL, gL, qR, gR, a.Af);
+            if constexpr (SPLIT) {
+                flux_update_boundary<FR, FC>(q, G1, G2, qU, gU, qD, gD, qL, gL, qR, gR, a.Af, keep1, keep2);
+            } else {
+                flux_update<FR, FC>(q, G1, G2, qU, gU, qD, gD, qL, gL, qR, gR, a.Af);
+            }
             if constexpr (CPL) {
                 if (cstep) {
                     flux_update<R, C>(qc, Gc1, Gc2, cqU, cgU, cqD, cgD, cqL, cgL, cqR, cgR, a.Ac);
