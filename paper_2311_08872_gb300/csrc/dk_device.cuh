@@ -40,17 +40,24 @@ __device__ __forceinline__ float sqrt_approx(float x) {
     return y;
 }
 
-// Box--Muller: u = (a+1) 2^-32 in (0,1], theta = 2 pi (b + 1/2) 2^-32.
-// theta is evaluated as pi ((int)b + 1/2) 2^-31, which differs from it by a
+// Box--Muller in polar form: u = (a+1) 2^-32 in (0,1], theta = 2 pi (b + 1/2)
+// 2^-32; returns the radius sqrt(-2 ln u) and (cos theta, sin theta), so that
+// the normals are (r cos theta, r sin theta).  theta is evaluated as
+// pi ((int)b + 1/2) 2^-31 (one fused multiply-add), which differs from it by a
 // multiple of 2 pi, so that the hardware sine/cosine see |x| <= pi.
-__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float& z1, float& z2) {
+__device__ __forceinline__ void box_muller_polar(uint32_t a, uint32_t b, float& r, float& c, float& s) {
     const float u = fmaf(static_cast<float>(a), 2.3283064365386963e-10f, 2.3283064365386963e-10f);
-    const float radius = sqrt_approx(-1.3862943611198906f * __log2f(u));   // sqrt(-2 ln u)
-    const float t = (static_cast<float>(static_cast<int32_t>(b)) + 0.5f) * 4.656612873077393e-10f;
-    float s, c;
-    __sincosf(3.14159265358979f * t, &s, &c);
-    z1 = radius * c;
-    z2 = radius * s;
+    r = sqrt_approx(-1.3862943611198906f * __log2f(u));   // sqrt(-2 ln u)
+    const float th = fmaf(static_cast<float>(static_cast<int32_t>(b)), 1.4629180792671596e-09f,
+                          7.314590396335798e-10f);
+    __sincosf(th, &s, &c);
+}
+
+__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float& z1, float& z2) {
+    float r, c, s;
+    box_muller_polar(a, b, r, c, s);
+    z1 = r * c;
+    z2 = r * s;
 }
 
 // Noise transfer G = rint(g sqrt(max(q,0)) z) in fixed-point units.

@@ -356,18 +356,19 @@ __global__ void __launch_bounds__(S::THREADS) level_kernel(const KArgs a) {
                 for (int pc = 0; pc < C; ++pc) {
                     const uint32_t p = static_cast<uint32_t>(((row0 + r) * NF + col0 + 2 * pc) >> 1);
                     const uint4 x = philox10(make_uint4(p, static_cast<uint32_t>(m), c2, c3), a.key0, a.key1);
-                    float z1a, z2a, z1b, z2b;
-                    box_muller(x.x, x.y, z1a, z2a);
-                    box_muller(x.z, x.w, z1b, z2b);
-                    const float sa = noise_amp(q[r][2 * pc], a.gf);
-                    const float sb = noise_amp(q[r][2 * pc + 1], a.gf);
-                    G1[r][2 * pc] = __float2int_rn(sa * z1a);
-                    G2[r][2 * pc] = __float2int_rn(sa * z2a);
-                    G1[r][2 * pc + 1] = __float2int_rn(sb * z1b);
-                    G2[r][2 * pc + 1] = __float2int_rn(sb * z2b);
+                    // normals (ra ca, ra sa) and (rb cb, rb sb); the amplitude scales the radius
+                    float ra, ca, sa, rb, cb, sb;
+                    box_muller_polar(x.x, x.y, ra, ca, sa);
+                    box_muller_polar(x.z, x.w, rb, cb, sb);
+                    const float ta = noise_amp(q[r][2 * pc], a.gf) * ra;
+                    const float tb = noise_amp(q[r][2 * pc + 1], a.gf) * rb;
+                    G1[r][2 * pc] = __float2int_rn(ta * ca);
+                    G2[r][2 * pc] = __float2int_rn(ta * sa);
+                    G1[r][2 * pc + 1] = __float2int_rn(tb * cb);
+                    G2[r][2 * pc + 1] = __float2int_rn(tb * sb);
                     if constexpr (CPL) {
-                        zt[r >> 1][pc][0] += z1a + z1b;
-                        zt[r >> 1][pc][1] += z2a + z2b;
+                        zt[r >> 1][pc][0] = fmaf(rb, cb, fmaf(ra, ca, zt[r >> 1][pc][0]));
+                        zt[r >> 1][pc][1] = fmaf(rb, sb, fmaf(ra, sa, zt[r >> 1][pc][1]));
                     }
                 }
             }

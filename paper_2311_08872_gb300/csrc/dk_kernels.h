@@ -79,10 +79,8 @@ struct SArgs {
     int count;                   // samples in this wave (<= samples in flight)
     long long sid0;              // sample id of the wave's first sample
     int32_t* q[2];               // [S][n][n] fine state, double buffered
-    int2* G[2];                  // [S][n][n] (G1, G2) noise transfers, double buffered
     int32_t* qc[2];              // [S][n/2][n/2] coarse state, double buffered
-    int2* Gc;                    // [S][n/2][n/2] coarse transfers
-    float2* zt;                  // [S][n/2][n/2] coupled normal sums
+    float2* zt;                  // [S][n/2][n/2] coupled normal sums of the current coarse step
     double* tile_part;           // [S][tiles][2 kMaxObs + 2] per-tile observables
     const int32_t* q0f; const int32_t* qbf; const float* phif;
     const int32_t* q0c; const int32_t* qbc; const float* phic;
@@ -94,6 +92,9 @@ struct SArgs {
 
 // Device bytes for `S` samples in flight on an n x n grid, and their layout.
 size_t stream_bytes(int n, int S);
+// Samples in flight for an n x n level within `budget` bytes of working set,
+// chosen so that the fine-step CTAs fill whole waves of the GPU.
+int stream_inflight(int n, size_t budget);
 void stream_carve(SArgs* a, void* buf, int n, int S);
 
 // Run k.count samples (ids k.first..) in waves of S: per-slot moment sums go

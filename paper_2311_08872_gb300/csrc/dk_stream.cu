@@ -2,22 +2,24 @@
 // (n >= 512: the finest levels of the low-density and large workloads).
 //
 // The state of `S` samples in flight lives in global memory (sized to stay in
-// L2): fine fixed-point state q and noise transfers G = (G1, G2), both double
-// buffered, the coarse state qc (double buffered) with its transfers Gc, and
-// the coupled coarse normal sums zt.  The scheme is the same as the register
-// kernels' (Eq. FullyDiscreteDK with b0 = 0, b1 = 1; NN coupling of Section
-// 3.2), in the same integer flux form, so results agree with them bit for bit
-// in the state.
+// L2): the fine fixed-point state q and the coarse state qc (both double
+// buffered) and the coupled coarse normal sums zt.  The scheme is the same as
+// the register kernels' (Eq. FullyDiscreteDK with b0 = 0, b1 = 1; NN coupling
+// of Section 3.2), in the same integer flux form and with the same FP32
+// expressions for the transfers and the coupled sums, so the fine and coarse
+// states agree with theirs bit for bit.
 //
-// One launch per fine step m reads q^m and G^m (own cells and the 1-cell
-// halo), writes q^{m+1}, then draws the normals of step m+1 for its own cells
-// and writes G^{m+1} (and the coarse sums zt).  The launch that draws the last
-// fine normals of a coarse step also writes that coarse step's transfers Gc; a
-// coarse launch then updates qc.  Kernel boundaries order all reads and
-// writes: no kernel waits on another.
+// One launch per fine step m: a CTA loads q^m on its tile and a one-cell halo,
+// draws the normals of step m for the tile and for the halo cells (one extra
+// Philox call per halo cell pair, so the transfers G^m never go to memory),
+// and writes q^{m+1} and, for coupled samples, the running coarse sums zt.
+// After the fourth fine step of a coarse step, a coarse launch forms the
+// coarse transfers from qc and zt (tile and halo) and updates qc.  Kernel
+// boundaries order all reads and writes: no kernel waits on another.
 //
-// CTA: 16 x 16 threads on a 32 x 32 tile of fine cells; thread (tx, ty) owns
-// the 2x2 fine block = 1 coarse cell at (16 T1 + ty, 16 T2 + tx).
+// Fine-step CTAs: 16 x 16 threads on a 32 x 64 tile, each thread a 2 x 4 block
+// of fine cells (two coarse cells).  The coarse step and the observables use
+// 32 x 32 tiles.
 #include <cstdint>
 
 #include "dk_device.cuh"
@@ -30,37 +32,44 @@ namespace {
 constexpr int kTile = 32;            // fine cells per tile side
 constexpr int kTc = kTile / 2;       // coarse cells per tile side (= threads per side)
 constexpr int kThreads = kTc * kTc;  // 256
+// fine-step tiles: kFR x kFC fine cells with a one-cell halo in shared memory,
+// row lr = r - R0 + 1 (0 .. kFR+1), column lc = c - C0 + 4 (3 .. kFC+4), so
+// that each thread's own four cells sit on a 16-byte boundary
+constexpr int kFR = 32, kFC = 64;
+constexpr int kFW = kFC + 8;
+constexpr int kHaloPairs = 128;      // 2 x 32 pairs in the halo rows + 2 x 32 in the halo columns
 
 __device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
-// Noise of fine step m for the 2x2 block at fine (r0, c0): transfers into G,
-// coupled sums into zt (overwrite when m % 4 == 0).
-__device__ __forceinline__ void block_noise(const SArgs& a, int s, int m, int r0, int c0, const int32_t (&q)[2][2],
-                                            int2 (&G)[2][2], float2& zt) {
+// Transfers of the horizontal cell pair p (cells 2p, 2p+1 of the row-major
+// grid) at fine step m, from the pair's state qa, qb; the normals of the pair
+// are also added to the running coarse sums (z1, z2) in the register kernels'
+// order (cell 2p first).
+struct PairNoise {
+    int32_t g1a, g2a, g1b, g2b;
+};
+
+__device__ __forceinline__ PairNoise pair_noise(const SArgs& a, uint32_t p, int m, uint32_t c2, uint32_t c3,
+                                                int32_t qa, int32_t qb, float& z1, float& z2) {
+    const uint4 x = philox10(make_uint4(p, static_cast<uint32_t>(m), c2, c3), a.key0, a.key1);
+    float ra, ca, sa, rb, cb, sb;
+    box_muller_polar(x.x, x.y, ra, ca, sa);
+    box_muller_polar(x.z, x.w, rb, cb, sb);
+    const float ta = noise_amp(qa, a.gf) * ra, tb = noise_amp(qb, a.gf) * rb;
+    z1 = fmaf(rb, cb, fmaf(ra, ca, z1));
+    z2 = fmaf(rb, sb, fmaf(ra, sa, z2));
+    return {__float2int_rn(ta * ca), __float2int_rn(ta * sa), __float2int_rn(tb * cb), __float2int_rn(tb * sb)};
+}
+
+__device__ __forceinline__ void sample_counter(const SArgs& a, int s, uint32_t& c2, uint32_t& c3) {
     const long long sid = a.sid0 + s;
-    const uint32_t c2 = static_cast<uint32_t>(sid);
-    const uint32_t c3 = a.tag | ((static_cast<uint32_t>(static_cast<unsigned long long>(sid) >> 32) & 0xffffu) << 16);
-    float s1 = 0.f, s2 = 0.f;
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const uint32_t p = static_cast<uint32_t>(((r0 + i) * a.n + c0) >> 1);
-        const uint4 x = philox10(make_uint4(p, static_cast<uint32_t>(m), c2, c3), a.key0, a.key1);
-        float z1a, z2a, z1b, z2b;
-        box_muller(x.x, x.y, z1a, z2a);
-        box_muller(x.z, x.w, z1b, z2b);
-        const float sa = noise_amp(q[i][0], a.gf), sb = noise_amp(q[i][1], a.gf);
-        G[i][0] = make_int2(__float2int_rn(sa * z1a), __float2int_rn(sa * z2a));
-        G[i][1] = make_int2(__float2int_rn(sb * z1b), __float2int_rn(sb * z2b));
-        s1 += z1a + z1b;
-        s2 += z2a + z2b;
-    }
-    if ((m & 3) == 0) zt = make_float2(s1, s2);
-    else zt = make_float2(zt.x + s1, zt.y + s2);
+    c2 = static_cast<uint32_t>(sid);
+    c3 = a.tag | ((static_cast<uint32_t>(static_cast<unsigned long long>(sid) >> 32) & 0xffffu) << 16);
 }
 
 }  // namespace
 
-// Initial state and the noise of step 0.
+// Initial state.
 __global__ void __launch_bounds__(kThreads) stream_init_kernel(const SArgs a) {
     const int s = blockIdx.y;
     if (s >= a.count) return;
@@ -70,97 +79,129 @@ __global__ void __launch_bounds__(kThreads) stream_init_kernel(const SArgs a) {
     const int I = T1 * kTc + ty, J = T2 * kTc + tx;            // coarse cell
     const int r0 = 2 * I, c0 = 2 * J;
     const size_t base = (size_t)s * a.n * a.n;
-    int32_t q[2][2];
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const int2 v = *reinterpret_cast<const int2*>(a.q0f + (size_t)(r0 + i) * a.n + c0);
-        q[i][0] = v.x; q[i][1] = v.y;
-        *reinterpret_cast<int2*>(a.q[0] + base + (size_t)(r0 + i) * a.n + c0) = v;
-    }
-    int2 G[2][2];
-    float2 zt = make_float2(0.f, 0.f);
-    block_noise(a, s, 0, r0, c0, q, G, zt);
 #pragma unroll
     for (int i = 0; i < 2; ++i)
-        *reinterpret_cast<int4*>(a.G[0] + base + (size_t)(r0 + i) * a.n + c0) =
-            make_int4(G[i][0].x, G[i][0].y, G[i][1].x, G[i][1].y);
-    if (a.coupled) {
-        const size_t cb = (size_t)s * a.nc * a.nc + (size_t)I * a.nc + J;
-        a.qc[0][cb] = a.q0c[(size_t)I * a.nc + J];
-        a.zt[cb] = zt;
-    }
+        *reinterpret_cast<int2*>(a.q[0] + base + (size_t)(r0 + i) * a.n + c0) =
+            *reinterpret_cast<const int2*>(a.q0f + (size_t)(r0 + i) * a.n + c0);
+    if (a.coupled) a.qc[0][(size_t)s * a.nc * a.nc + (size_t)I * a.nc + J] = a.q0c[(size_t)I * a.nc + J];
 }
 
-// Fine step m: q^{m+1} from q^m, G^m; then the noise of step m+1.
+// Fine step m: noise of step m on the tile and its halo, then q^{m+1}.
+// CTA: 16 x 16 threads on a 32 x 64 tile (kFR x kFC); thread (tx, ty) owns the
+// 2 x 4 fine block at (R0 + 2 ty, C0 + 4 tx) = 2 coarse cells.
 __global__ void __launch_bounds__(kThreads) stream_fine_kernel(const SArgs a, int m) {
-    const int s = blockIdx.y;
+    const int s = blockIdx.z;
     if (s >= a.count) return;
     const int n = a.n;
-    const int tpr = n / kTile;
-    const int T1 = blockIdx.x / tpr, T2 = blockIdx.x % tpr;
-    const int tx = threadIdx.x % kTc, ty = threadIdx.x / kTc;
-    const int I = T1 * kTc + ty, J = T2 * kTc + tx;
-    const int r0 = 2 * I, c0 = 2 * J;
+    const int t = threadIdx.x;
+    const int tx = t % 16, ty = t / 16;
+    const int R0 = blockIdx.y * kFR, C0 = blockIdx.x * kFC;
+    const int r0 = R0 + 2 * ty, c0 = C0 + 4 * tx;
     const size_t base = (size_t)s * n * n;
     const int32_t* qin = a.q[m & 1] + base;
     int32_t* qout = a.q[(m + 1) & 1] + base;
-    const int2* Gin = a.G[m & 1] + base;
-    int2* Gout = a.G[(m + 1) & 1] + base;
+    uint32_t c2, c3;
+    sample_counter(a, s, c2, c3);
 
-    // tile + 1-cell halo in shared memory: q and (G1, G2)
-    __shared__ int32_t sq[kTile + 2][kTile + 2];
-    __shared__ int2 sg[kTile + 2][kTile + 2];
-    const int R0 = T1 * kTile, C0 = T2 * kTile;
-    for (int k = threadIdx.x; k < (kTile + 2) * (kTile + 2); k += kThreads) {
-        const int lr = k / (kTile + 2), lc = k % (kTile + 2);
-        const int gr = wrapi(R0 + lr - 1, n), gc = wrapi(C0 + lc - 1, n);
-        sq[lr][lc] = qin[(size_t)gr * n + gc];
-        sg[lr][lc] = Gin[(size_t)gr * n + gc];
+    __shared__ __align__(16) int32_t sq[kFR + 2][kFW];
+    __shared__ __align__(16) int32_t s1[kFR + 2][kFW];
+    __shared__ __align__(16) int32_t s2[kFR + 2][kFW];
+
+    // own 2x4 block: state, normals of step m, transfers; coupled sums of its
+    // two coarse cells in the register kernels' order
+    const int lr0 = 2 * ty + 1, lc0 = 4 * tx + 4;
+    int32_t q[2][4], G1[2][4], G2[2][4];
+    float4* const zp = reinterpret_cast<float4*>(a.zt + (size_t)s * a.nc * a.nc + (size_t)(r0 >> 1) * a.nc + (c0 >> 1));
+    float z[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+    if (a.coupled && (m & 3) != 0) {
+        const float4 v = *zp;
+        z[0][0] = v.x; z[0][1] = v.y; z[1][0] = v.z; z[1][1] = v.w;
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int4 v = *reinterpret_cast<const int4*>(qin + (size_t)(r0 + i) * n + c0);
+        q[i][0] = v.x; q[i][1] = v.y; q[i][2] = v.z; q[i][3] = v.w;
+        const uint32_t p = static_cast<uint32_t>(((r0 + i) * n + c0) >> 1);
+        const PairNoise g = pair_noise(a, p, m, c2, c3, v.x, v.y, z[0][0], z[0][1]);
+        const PairNoise h = pair_noise(a, p + 1, m, c2, c3, v.z, v.w, z[1][0], z[1][1]);
+        G1[i][0] = g.g1a; G2[i][0] = g.g2a; G1[i][1] = g.g1b; G2[i][1] = g.g2b;
+        G1[i][2] = h.g1a; G2[i][2] = h.g2a; G1[i][3] = h.g1b; G2[i][3] = h.g2b;
+        *reinterpret_cast<int4*>(&sq[lr0 + i][lc0]) = v;
+        *reinterpret_cast<int4*>(&s1[lr0 + i][lc0]) = make_int4(g.g1a, g.g1b, h.g1a, h.g1b);
+        *reinterpret_cast<int4*>(&s2[lr0 + i][lc0]) = make_int4(g.g2a, g.g2b, h.g2a, h.g2b);
+    }
+    // halo: rows R0-1 and R0+kFR (32 pairs each: state and G1), columns C0-1
+    // and C0+kFC (one pair per row: state and G2 of the cell next to the tile)
+    if (t < kHaloPairs) {
+        float d1 = 0.f, d2 = 0.f;   // halo normals do not enter this tile's coarse sums
+        if (t < 64) {
+            const int side = t >> 5, k = t & 31;
+            const int r = wrapi(side ? R0 + kFR : R0 - 1, n), c = C0 + 2 * k;
+            const int2 v = *reinterpret_cast<const int2*>(qin + (size_t)r * n + c);
+            const PairNoise g = pair_noise(a, static_cast<uint32_t>((r * n + c) >> 1), m, c2, c3, v.x, v.y, d1, d2);
+            const int lr = side ? kFR + 1 : 0;
+            *reinterpret_cast<int2*>(&sq[lr][4 + 2 * k]) = v;
+            *reinterpret_cast<int2*>(&s1[lr][4 + 2 * k]) = make_int2(g.g1a, g.g1b);
+        } else {
+            const int u = t - 64, side = u >> 5, rr = u & 31;
+            const int r = R0 + rr, c = wrapi(side ? C0 + kFC : C0 - 2, n);
+            const int2 v = *reinterpret_cast<const int2*>(qin + (size_t)r * n + c);
+            const PairNoise g = pair_noise(a, static_cast<uint32_t>((r * n + c) >> 1), m, c2, c3, v.x, v.y, d1, d2);
+            if (side) {
+                sq[rr + 1][kFC + 4] = v.x;
+                s2[rr + 1][kFC + 4] = g.g2a;
+            } else {
+                sq[rr + 1][3] = v.y;
+                s2[rr + 1][3] = g.g2b;
+            }
+        }
     }
     __syncthreads();
-    int32_t q[2][2];
-    const int lr0 = 2 * ty + 1, lc0 = 2 * tx + 1;
+
     unsigned bad = 0;
+    int32_t up[4], dn[4], gu[4], gd[4];
+    {
+        const int4 a0 = *reinterpret_cast<const int4*>(&sq[lr0 - 1][lc0]);
+        const int4 a1 = *reinterpret_cast<const int4*>(&sq[lr0 + 2][lc0]);
+        const int4 b0 = *reinterpret_cast<const int4*>(&s1[lr0 - 1][lc0]);
+        const int4 b1 = *reinterpret_cast<const int4*>(&s1[lr0 + 2][lc0]);
+        up[0] = a0.x; up[1] = a0.y; up[2] = a0.z; up[3] = a0.w;
+        dn[0] = a1.x; dn[1] = a1.y; dn[2] = a1.z; dn[3] = a1.w;
+        gu[0] = b0.x; gu[1] = b0.y; gu[2] = b0.z; gu[3] = b0.w;
+        gd[0] = b1.x; gd[1] = b1.y; gd[2] = b1.z; gd[3] = b1.w;
+    }
+    int32_t out[2][4];
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 2; ++i) {
+        const int32_t ql = sq[lr0 + i][lc0 - 1], qr = sq[lr0 + i][lc0 + 4];
+        const int32_t gl = s2[lr0 + i][lc0 - 1], gr = s2[lr0 + i][lc0 + 4];
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const int lr = lr0 + i, lc = lc0 + j;
-            const int32_t x = sq[lr][lc];
-            const int32_t d = edge_flux(a.Af, sq[lr + 1][lc] - x) - edge_flux(a.Af, x - sq[lr - 1][lc]) +
-                              edge_flux(a.Af, sq[lr][lc + 1] - x) - edge_flux(a.Af, x - sq[lr][lc - 1]);
-            const int32_t v = x + d + (sg[lr + 1][lc].x - sg[lr - 1][lc].x) + (sg[lr][lc + 1].y - sg[lr][lc - 1].y);
-            q[i][j] = v;
+        for (int j = 0; j < 4; ++j) {
+            const int32_t x = q[i][j];
+            const int32_t u = i == 0 ? up[j] : q[0][j];
+            const int32_t d = i == 1 ? dn[j] : q[1][j];
+            const int32_t l = j == 0 ? ql : q[i][j - 1];
+            const int32_t r = j == 3 ? qr : q[i][j + 1];
+            const int32_t g1u = i == 0 ? gu[j] : G1[0][j];
+            const int32_t g1d = i == 1 ? gd[j] : G1[1][j];
+            const int32_t g2l = j == 0 ? gl : G2[i][j - 1];
+            const int32_t g2r = j == 3 ? gr : G2[i][j + 1];
+            const int32_t f = edge_flux(a.Af, d - x) - edge_flux(a.Af, x - u) + edge_flux(a.Af, r - x) -
+                              edge_flux(a.Af, x - l);
+            const int32_t v = x + f + (g1d - g1u) + (g2r - g2l);
+            out[i][j] = v;
             bad |= (static_cast<uint32_t>(v) + 0x40000000u) >> 31;
         }
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-        *reinterpret_cast<int2*>(qout + (size_t)(r0 + i) * n + c0) = make_int2(q[i][0], q[i][1]);
-    if (bad) atomicOr(a.err, kErrRange);
-    if (m + 1 >= a.M) return;
-    int2 G[2][2];
-    const size_t cb = (size_t)s * a.nc * a.nc + (size_t)I * a.nc + J;
-    float2 zt = make_float2(0.f, 0.f);
-    if (a.coupled && ((m + 1) & 3) != 0) zt = a.zt[cb];
-    block_noise(a, s, m + 1, r0, c0, q, G, zt);
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-        *reinterpret_cast<int4*>(Gout + (size_t)(r0 + i) * n + c0) =
-            make_int4(G[i][0].x, G[i][0].y, G[i][1].x, G[i][1].y);
-    if (a.coupled) {
-        if (((m + 1) & 3) == 3) {
-            // the coupled normals of coarse step (m+1)/4 are complete: its transfers
-            const int cn = (m + 1) >> 2;
-            const int32_t qcv = a.qc[cn & 1][cb];
-            const float amp = noise_amp(qcv, a.gc);
-            a.Gc[cb] = make_int2(__float2int_rn(amp * zt.x), __float2int_rn(amp * zt.y));
-        } else {
-            a.zt[cb] = zt;
-        }
     }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+        *reinterpret_cast<int4*>(qout + (size_t)(r0 + i) * n + c0) = make_int4(out[i][0], out[i][1], out[i][2], out[i][3]);
+    if (a.coupled) *zp = make_float4(z[0][0], z[0][1], z[1][0], z[1][1]);
+    if (bad) atomicOr(a.err, kErrRange);
 }
 
-// Coarse step cn: qc^{cn+1} from qc^cn and Gc.
+// Coarse step cn (after fine step 4 cn + 3): transfers from qc^cn and the
+// coupled sums on the tile and its halo, then qc^{cn+1}.
 __global__ void __launch_bounds__(kThreads) stream_coarse_kernel(const SArgs a, int cn) {
     const int s = blockIdx.y;
     if (s >= a.count) return;
@@ -170,15 +211,18 @@ __global__ void __launch_bounds__(kThreads) stream_coarse_kernel(const SArgs a, 
     const size_t base = (size_t)s * nc * nc;
     const int32_t* qin = a.qc[cn & 1] + base;
     int32_t* qout = a.qc[(cn + 1) & 1] + base;
-    const int2* Gc = a.Gc + base;
+    const float2* zt = a.zt + base;
     __shared__ int32_t sq[kTile + 2][kTile + 2];
     __shared__ int2 sg[kTile + 2][kTile + 2];
     const int R0 = T1 * kTile, C0 = T2 * kTile;
     for (int k = threadIdx.x; k < (kTile + 2) * (kTile + 2); k += kThreads) {
         const int lr = k / (kTile + 2), lc = k % (kTile + 2);
         const int gr = wrapi(R0 + lr - 1, nc), gcol = wrapi(C0 + lc - 1, nc);
-        sq[lr][lc] = qin[(size_t)gr * nc + gcol];
-        sg[lr][lc] = Gc[(size_t)gr * nc + gcol];
+        const int32_t qv = qin[(size_t)gr * nc + gcol];
+        const float2 z = zt[(size_t)gr * nc + gcol];
+        const float amp = noise_amp(qv, a.gc);
+        sq[lr][lc] = qv;
+        sg[lr][lc] = make_int2(__float2int_rn(amp * z.x), __float2int_rn(amp * z.y));
     }
     __syncthreads();
     unsigned bad = 0;
@@ -304,32 +348,49 @@ __global__ void zero_kernel(double* p, size_t count) {
 
 size_t stream_bytes(int n, int S) {
     const size_t nc = n / 2, tiles = (size_t)(n / kTile) * (n / kTile);
-    return (size_t)S * ((size_t)n * n * (2 * sizeof(int32_t) + 2 * sizeof(int2)) +
-                        nc * nc * (2 * sizeof(int32_t) + sizeof(int2) + sizeof(float2)) +
+    return (size_t)S * ((size_t)n * n * 2 * sizeof(int32_t) + nc * nc * (2 * sizeof(int32_t) + sizeof(float2)) +
                         tiles * (2 * kMaxObs + 2) * sizeof(double));
+}
+
+int stream_inflight(int n, size_t budget) {
+    // the largest count that fits the budget, lowered while a smaller count
+    // fills the last wave of fine-step CTAs clearly better
+    const int s_max = (int)std::max<size_t>(1, budget / stream_bytes(n, 1));
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stream_fine_kernel, kThreads, 0) != cudaSuccess ||
+        sms * per_sm == 0)
+        return s_max;
+    const long long resident = (long long)sms * per_sm, ctas = (long long)(n / kFC) * (n / kFR);
+    int best = s_max;
+    double best_eff = 0.0;
+    for (int S = s_max; S >= std::max(1, s_max / 2); --S) {
+        const long long c = S * ctas, waves = (c + resident - 1) / resident;
+        const double eff = (double)c / (double)(waves * resident);
+        if (eff > best_eff + 0.01) {
+            best = S;
+            best_eff = eff;
+        }
+    }
+    return best;
 }
 
 void stream_carve(SArgs* a, void* buf, int n, int S) {
     unsigned char* p = static_cast<unsigned char*>(buf);
     const size_t cf = (size_t)S * n * n, cc = (size_t)S * (n / 2) * (n / 2);
-    const size_t tiles = (size_t)(n / kTile) * (n / kTile);
     a->q[0] = reinterpret_cast<int32_t*>(p); p += cf * sizeof(int32_t);
     a->q[1] = reinterpret_cast<int32_t*>(p); p += cf * sizeof(int32_t);
-    a->G[0] = reinterpret_cast<int2*>(p); p += cf * sizeof(int2);
-    a->G[1] = reinterpret_cast<int2*>(p); p += cf * sizeof(int2);
     a->qc[0] = reinterpret_cast<int32_t*>(p); p += cc * sizeof(int32_t);
     a->qc[1] = reinterpret_cast<int32_t*>(p); p += cc * sizeof(int32_t);
-    a->Gc = reinterpret_cast<int2*>(p); p += cc * sizeof(int2);
     a->zt = reinterpret_cast<float2*>(p); p += cc * sizeof(float2);
     a->tile_part = reinterpret_cast<double*>(p);
-    (void)tiles;
 }
 
 cudaError_t stream_run(const KArgs& k, SArgs a, int S, cudaStream_t st) {
     // k.partials holds S slots (entry-major, [stride][S]); zero them, run the
     // waves of S samples, accumulate per slot, then the caller reduces.
     const int n = a.n;
-    if (n % kTile != 0 || (a.coupled && (a.nc % kTile != 0 || a.M % 4 != 0))) return cudaErrorInvalidValue;
+    if (n % kFC != 0 || (a.coupled && (a.nc % kTile != 0 || a.M % 4 != 0))) return cudaErrorInvalidValue;
     const int tiles = (n / kTile) * (n / kTile);
     const int ctiles = a.coupled ? (a.nc / kTile) * (a.nc / kTile) : 0;
     zero_kernel<<<64, 256, 0, st>>>(k.partials, (size_t)k.slot_stride * S);
@@ -338,11 +399,11 @@ cudaError_t stream_run(const KArgs& k, SArgs a, int S, cudaStream_t st) {
     for (long long done = 0; done < k.count; done += S) {
         a.sid0 = k.first + done;
         a.count = (int)std::min<long long>(S, k.count - done);
-        const dim3 grid(tiles, a.count), cgrid(ctiles, a.count);
+        const dim3 grid(tiles, a.count), cgrid(ctiles, a.count), fgrid(n / kFC, n / kFR, a.count);
         stream_init_kernel<<<grid, kThreads, 0, st>>>(a);
         for (int m = 0; m < a.M; ++m) {
-            stream_fine_kernel<<<grid, kThreads, 0, st>>>(a, m);
-            if (a.coupled && (m & 3) == 2) stream_coarse_kernel<<<cgrid, kThreads, 0, st>>>(a, m >> 2);
+            stream_fine_kernel<<<fgrid, kThreads, 0, st>>>(a, m);
+            if (a.coupled && (m & 3) == 3) stream_coarse_kernel<<<cgrid, kThreads, 0, st>>>(a, m >> 2);
         }
         stream_observe_kernel<<<grid, kThreads, 0, st>>>(a);
         stream_finish_kernel<<<(a.count + 63) / 64, 64, 0, st>>>(a, k, tiles, S);

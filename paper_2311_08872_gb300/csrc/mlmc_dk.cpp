@@ -529,13 +529,13 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
         const int nv = force_stream ? 0 : dk::variant_count(t.n);
         if (nv == 0) {
             // no register-resident variant: stream the state through global memory,
-            // as many samples in flight as fit a 64 MB working set (L2-resident)
+            // samples in flight within a 96 MB working set (L2-resident)
             if (t.n % 64 != 0) {
                 mlmc_dk_free(c);
                 return fail(nullptr, MLMC_DK_ERR_UNSUPPORTED, "grid size without a kernel");
             }
             t.streamed = 1;
-            t.inflight = (int)std::max<size_t>(1, (size_t)(64u << 20) / dk::stream_bytes(t.n, 1));
+            t.inflight = dk::stream_inflight(t.n, (size_t)96 << 20);
             if ((e = cudaMalloc(&t.d_stream, dk::stream_bytes(t.n, t.inflight))) != cudaSuccess ||
                 (e = cudaMalloc(&t.d_spart, sizeof(double) * c->stride * t.inflight)) != cudaSuccess) {
                 mlmc_dk_free(c);

@@ -24,6 +24,7 @@ def main() -> None:
     ap.add_argument("--samples", type=int, default=19)
     ap.add_argument("--mc", action="store_true", help="plain MC stream (fine path only)")
     ap.add_argument("--repeat", type=int, default=2, help="timed launches after one warm-up launch")
+    ap.add_argument("--T", type=float, default=None, help="override the final time (fewer steps per sample)")
     args = ap.parse_args()
 
     import torch
@@ -32,6 +33,8 @@ def main() -> None:
 
     build.build()
     wl = workloads.get(args.workload)
+    if args.T is not None:
+        wl = wl.with_(T=args.T)
     st = torch.cuda.current_stream()
     with mlmc_dk.Context.from_workload(wl, stream=st.cuda_stream) as ctx:
         info = ctx.level_info(args.level)
@@ -48,7 +51,8 @@ def main() -> None:
             torch.cuda.synchronize()
             ms.append(e0.elapsed_time(e1))
     avg = sum(ms) / len(ms)
-    print(json.dumps({"workload": wl.name, "level": args.level, "n": info.n, "coupled": tag == 0 and args.level > 0,
+    print(json.dumps({"workload": wl.name, "level": args.level, "n": info.n, "fine_steps": info.M,
+                      "streamed": bool(info.streamed), "coupled": tag == 0 and args.level > 0,
                       "samples": args.samples, "ms_per_launch": avg,
                       "cell_steps_per_s": args.samples * cost / (avg * 1e-3)}))
 
