@@ -46,6 +46,24 @@ XU_OPS_COARSE = 1.0
 XU_PER_CLK_PER_SM = 16
 SMS = 152
 SM_MAX_MHZ = 2070.0
+# DRAM bytes of one full-size launch of the dominant kernel (read + write; the
+# state never leaves registers, so this is the initial-state, mean-field and
+# observable tables), from the ncu launch list of
+#   python bench.py --steps 2 --warmup 3 --no-cpu-baseline --no-surrogate
+# (mean of its 7 launches of 955 samples).  Reported only while the kernel
+# sources hash to the value recorded with the capture.
+LEVEL_KERNEL_TRAFFIC = {"kernel": "level_kernel n=256 C=4 R=2 cluster=8 coupled=True",
+                        "bytes_per_launch": 2.126e6, "sources_sha256_16": "2b6964eac8425ad6"}
+KERNEL_SOURCES = ("dk_kernels.cu", "dk_device.cuh", "dk_kernels.h")
+
+
+def kernel_sources_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2311_08872_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def parse():
@@ -283,11 +301,16 @@ def run_ours(args, wl, rank, world, local_rank):
     ops = alloc[dom] * (fine[dom] * XU_OPS_FINE + coarse[dom] * XU_OPS_COARSE) * args.steps
     achieved = ops / (level_ms[dom] * 1e-3)
     peak = XU_PER_CLK_PER_SM * SMS * SM_MAX_MHZ * 1e6
+    kname = (f"level_kernel n={info[dom].n} C={info[dom].lane_cols} R={info[dom].lane_rows} "
+             f"cluster={info[dom].cluster} coupled={dom > 0}")
+    traffic = None
+    if kname == LEVEL_KERNEL_TRAFFIC["kernel"] and kernel_sources_hash() == LEVEL_KERNEL_TRAFFIC["sources_sha256_16"]:
+        traffic = LEVEL_KERNEL_TRAFFIC["bytes_per_launch"]
     roofline = {"bound": "alu", "pipe": "XU (MUFU)",
-                "kernel": f"level_kernel n={info[dom].n} C={info[dom].lane_cols} R={info[dom].lane_rows} "
-                          f"cluster={info[dom].cluster} coupled={dom > 0}",
+                "kernel": kname,
                 "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gop/s", "frac": achieved / peak,
-                "traffic": None, "ops_per_fine_cell_step": XU_OPS_FINE,
+                "traffic": traffic, "traffic_unit": "DRAM bytes per launch (ncu, one launch per step)",
+                "ops_per_fine_cell_step": XU_OPS_FINE,
                 "cell_steps_per_s": alloc[dom] * (fine[dom] + coarse[dom]) * args.steps / (level_ms[dom] * 1e-3),
                 "level_ms_per_step": [x / args.steps for x in level_ms],
                 "note": "levels run concurrently in one CUDA graph; each level's time is its own stream's span"}

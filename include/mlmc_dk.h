@@ -116,6 +116,8 @@ typedef struct {
     int32_t lane_cols, lane_rows, cluster;    /* the level's main kernel: C x R coarse cells per lane, cluster */
     int32_t streamed;       /* 1: grid too large for registers; state streamed through global memory */
     int32_t in_flight;      /* streamed path: samples advanced together (their state fits L2) */
+    int32_t tile_rows;      /* streamed path: fine rows per CTA tile of the variant in use (tiles are
+                               tile_rows x 64 fine cells); 0 for the register kernels */
 } mlmc_dk_level_desc;
 
 /* Host-side moment sums of one quantity on one level (accumulated into). */
@@ -271,12 +273,13 @@ int mlmc_dk_estimate(mlmc_dk_ctx* ctx, double eps, int32_t relative, uint64_t se
  * All variants compute the same fixed-point paths bit for bit (hence equal
  * masses); the observables differ only by the order of their FP32 partial
  * sums.  Variants differ in how many cells a lane owns and how many SMs share
- * a sample. */
+ * a sample; on streamed levels, in the fine-step tile (tile_rows x 64 cells). */
 int mlmc_dk_set_variant(mlmc_dk_ctx* ctx, int32_t level, int32_t coupled, int32_t variant);
 
 /* Autotuner: for every level and kernel with more than one variant, time each
  * variant (CUDA events, `repeats` timed launches of two full waves of sample
- * slots after a warm-up launch; sample ids from 0, results discarded) and keep
+ * slots after a warm-up launch -- on streamed levels one wave of samples in
+ * flight over 64 fine steps; sample ids from 0, results discarded) and keep
  * the fastest per sample.  *seconds (optional) receives the tuning time. */
 int mlmc_dk_tune(mlmc_dk_ctx* ctx, int32_t repeats, double* seconds);
 

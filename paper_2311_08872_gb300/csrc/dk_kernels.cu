@@ -155,46 +155,6 @@ __device__ __forceinline__ const T* peer(const T* local, int rank) {
     }
 }
 
-// Update of an RR x CC block of cells given its halo: explicit Euler--Maruyama
-// step in flux form.  up/dn are the rows above/below the block, lf/rt the
-// columns left/right; G1/G2 the noise transfers (component 1 along rows).
-template <int RR, int CC>
-__device__ __forceinline__ void flux_update(int32_t (&q)[RR][CC], const int32_t (&G1)[RR][CC],
-                                            const int32_t (&G2)[RR][CC], const int32_t (&qU)[CC],
-                                            const int32_t (&gU)[CC], const int32_t (&qD)[CC],
-                                            const int32_t (&gD)[CC], const int32_t (&qL)[RR],
-                                            const int32_t (&gL)[RR], const int32_t (&qR)[RR],
-                                            const int32_t (&gR)[RR], int32_t A) {
-    // vertical edge fluxes V[r][c]: across the edge between rows r-1 and r (r = 0..RR)
-    int32_t V[RR + 1][CC];
-#pragma unroll
-    for (int c = 0; c < CC; ++c) {
-        V[0][c] = edge_flux(A, q[0][c] - qU[c]);
-#pragma unroll
-        for (int r = 1; r < RR; ++r) V[r][c] = edge_flux(A, q[r][c] - q[r - 1][c]);
-        V[RR][c] = edge_flux(A, qD[c] - q[RR - 1][c]);
-    }
-    int32_t H[RR][CC + 1];
-#pragma unroll
-    for (int r = 0; r < RR; ++r) {
-        H[r][0] = edge_flux(A, q[r][0] - qL[r]);
-#pragma unroll
-        for (int c = 1; c < CC; ++c) H[r][c] = edge_flux(A, q[r][c] - q[r][c - 1]);
-        H[r][CC] = edge_flux(A, qR[r] - q[r][CC - 1]);
-    }
-#pragma unroll
-    for (int r = 0; r < RR; ++r) {
-#pragma unroll
-        for (int c = 0; c < CC; ++c) {
-            const int32_t g1d = (r + 1 < RR) ? G1[r + 1][c] : gD[c];
-            const int32_t g1u = (r > 0) ? G1[r - 1][c] : gU[c];
-            const int32_t g2r = (c + 1 < CC) ? G2[r][c + 1] : gR[r];
-            const int32_t g2l = (c > 0) ? G2[r][c - 1] : gL[r];
-            q[r][c] += (V[r + 1][c] - V[r][c]) + (H[r][c + 1] - H[r][c]) + (g1d - g1u) + (g2r - g2l);
-        }
-    }
-}
-
 // The same update in two phases around a split barrier: phase 1 updates the
 // interior rows (1 .. RR-2), which need no vertical halo, and keeps the old
 // values of rows 1 and RR-2 that the boundary rows' fluxes need; phase 2

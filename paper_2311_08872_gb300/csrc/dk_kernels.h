@@ -52,6 +52,7 @@ struct VariantInfo {
     size_t smem;            // dynamic shared memory per CTA
     int max_ctas;           // resident CTAs on the whole GPU
     int C, R;               // lane block: C x R coarse cells (2R x 2C fine)
+    int tile_rows;          // streamed kernels: fine rows per CTA tile (0 for the register kernels)
 };
 
 // Number of kernel variants (lane-block shapes / cluster sizes) for fine size n.
@@ -92,15 +93,19 @@ struct SArgs {
 
 // Device bytes for `S` samples in flight on an n x n grid, and their layout.
 size_t stream_bytes(int n, int S);
-// Samples in flight for an n x n level within `budget` bytes of working set,
-// chosen so that the fine-step CTAs fill whole waves of the GPU.
-int stream_inflight(int n, size_t budget);
+// Fine-step tile variants of the streamed kernels (FR x 64 fine cells per CTA,
+// FR = tile_rows), their launch shape on this device, and the samples in
+// flight for an n x n level within `budget` bytes of working set, chosen so
+// that the fine-step CTAs of `variant` fill whole waves of the GPU.
+int stream_variant_count();
+cudaError_t stream_variant_info(int n, int variant, VariantInfo* out);
+int stream_inflight(int n, size_t budget, int variant);
 void stream_carve(SArgs* a, void* buf, int n, int S);
 
 // Run k.count samples (ids k.first..) in waves of S: per-slot moment sums go
 // to k.partials ([k.slot_stride][S], zeroed here), per-sample outputs to
 // k.samples; the caller reduces the S slots.
-cudaError_t stream_run(const KArgs& k, SArgs a, int S, cudaStream_t stream);
+cudaError_t stream_run(const KArgs& k, SArgs a, int S, int variant, cudaStream_t stream);
 
 // ---- learned level below level 0
 constexpr int kModes = 32;     // real orthonormal modes

@@ -17,9 +17,9 @@
 // coarse transfers from qc and zt (tile and halo) and updates qc.  Kernel
 // boundaries order all reads and writes: no kernel waits on another.
 //
-// Fine-step CTAs: 16 x 16 threads on a 32 x 64 tile, each thread a 2 x 4 block
-// of fine cells (two coarse cells).  The coarse step and the observables use
-// 32 x 32 tiles.
+// Fine-step CTAs: 16 x FR/2 threads on an FR x 64 tile (FR = 32 or 64, picked
+// by the autotuner), each thread a 2 x 4 block of fine cells (two coarse
+// cells).  The coarse step and the observables use 32 x 32 tiles.
 #include <cstdint>
 
 #include "dk_device.cuh"
@@ -32,12 +32,16 @@ namespace {
 constexpr int kTile = 32;            // fine cells per tile side
 constexpr int kTc = kTile / 2;       // coarse cells per tile side (= threads per side)
 constexpr int kThreads = kTc * kTc;  // 256
-// fine-step tiles: kFR x kFC fine cells with a one-cell halo in shared memory,
-// row lr = r - R0 + 1 (0 .. kFR+1), column lc = c - C0 + 4 (3 .. kFC+4), so
-// that each thread's own four cells sit on a 16-byte boundary
-constexpr int kFR = 32, kFC = 64;
+// fine-step tiles: FR x kFC fine cells (FR = 32 or 64, the two tile variants)
+// with a one-cell halo in shared memory, row lr = r - R0 + 1 (0 .. FR+1),
+// column lc = c - C0 + 4 (3 .. kFC+4), so that each thread's own four cells
+// sit on a 16-byte boundary
+constexpr int kFC = 64;
 constexpr int kFW = kFC + 8;
-constexpr int kHaloPairs = 128;      // 2 x 32 pairs in the halo rows + 2 x 32 in the halo columns
+constexpr int kStreamVariants = 2;
+__host__ __device__ constexpr int fine_rows(int variant) { return variant == 0 ? 32 : 64; }
+__host__ __device__ constexpr int fine_threads(int fr) { return 8 * fr; }
+__host__ __device__ constexpr int fine_smem(int fr) { return 3 * (fr + 2) * kFW * (int)sizeof(int32_t); }
 
 __device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
@@ -87,15 +91,17 @@ __global__ void __launch_bounds__(kThreads) stream_init_kernel(const SArgs a) {
 }
 
 // Fine step m: noise of step m on the tile and its halo, then q^{m+1}.
-// CTA: 16 x 16 threads on a 32 x 64 tile (kFR x kFC); thread (tx, ty) owns the
-// 2 x 4 fine block at (R0 + 2 ty, C0 + 4 tx) = 2 coarse cells.
-__global__ void __launch_bounds__(kThreads) stream_fine_kernel(const SArgs a, int m) {
+// CTA: 16 x FR/2 threads on an FR x 64 tile; thread (tx, ty) owns the 2 x 4
+// fine block at (R0 + 2 ty, C0 + 4 tx) = 2 coarse cells.
+template <int FR>
+__global__ void __launch_bounds__(fine_threads(FR)) stream_fine_kernel(const SArgs a, int m) {
+    constexpr int kHaloPairs = 64 + 2 * FR;   // 2 x 32 pairs in the halo rows, one per row in the halo columns
     const int s = blockIdx.z;
     if (s >= a.count) return;
     const int n = a.n;
     const int t = threadIdx.x;
     const int tx = t % 16, ty = t / 16;
-    const int R0 = blockIdx.y * kFR, C0 = blockIdx.x * kFC;
+    const int R0 = blockIdx.y * FR, C0 = blockIdx.x * kFC;
     const int r0 = R0 + 2 * ty, c0 = C0 + 4 * tx;
     const size_t base = (size_t)s * n * n;
     const int32_t* qin = a.q[m & 1] + base;
@@ -103,9 +109,10 @@ __global__ void __launch_bounds__(kThreads) stream_fine_kernel(const SArgs a, in
     uint32_t c2, c3;
     sample_counter(a, s, c2, c3);
 
-    __shared__ __align__(16) int32_t sq[kFR + 2][kFW];
-    __shared__ __align__(16) int32_t s1[kFR + 2][kFW];
-    __shared__ __align__(16) int32_t s2[kFR + 2][kFW];
+    extern __shared__ __align__(16) int32_t smem_fine[];
+    int32_t (*sq)[kFW] = reinterpret_cast<int32_t (*)[kFW]>(smem_fine);
+    int32_t (*s1)[kFW] = reinterpret_cast<int32_t (*)[kFW]>(smem_fine + (FR + 2) * kFW);
+    int32_t (*s2)[kFW] = reinterpret_cast<int32_t (*)[kFW]>(smem_fine + 2 * (FR + 2) * kFW);
 
     // own 2x4 block: state, normals of step m, transfers; coupled sums of its
     // two coarse cells in the register kernels' order
@@ -130,20 +137,20 @@ __global__ void __launch_bounds__(kThreads) stream_fine_kernel(const SArgs a, in
         *reinterpret_cast<int4*>(&s1[lr0 + i][lc0]) = make_int4(g.g1a, g.g1b, h.g1a, h.g1b);
         *reinterpret_cast<int4*>(&s2[lr0 + i][lc0]) = make_int4(g.g2a, g.g2b, h.g2a, h.g2b);
     }
-    // halo: rows R0-1 and R0+kFR (32 pairs each: state and G1), columns C0-1
+    // halo: rows R0-1 and R0+FR (32 pairs each: state and G1), columns C0-1
     // and C0+kFC (one pair per row: state and G2 of the cell next to the tile)
     if (t < kHaloPairs) {
         float d1 = 0.f, d2 = 0.f;   // halo normals do not enter this tile's coarse sums
         if (t < 64) {
             const int side = t >> 5, k = t & 31;
-            const int r = wrapi(side ? R0 + kFR : R0 - 1, n), c = C0 + 2 * k;
+            const int r = wrapi(side ? R0 + FR : R0 - 1, n), c = C0 + 2 * k;
             const int2 v = *reinterpret_cast<const int2*>(qin + (size_t)r * n + c);
             const PairNoise g = pair_noise(a, static_cast<uint32_t>((r * n + c) >> 1), m, c2, c3, v.x, v.y, d1, d2);
-            const int lr = side ? kFR + 1 : 0;
+            const int lr = side ? FR + 1 : 0;
             *reinterpret_cast<int2*>(&sq[lr][4 + 2 * k]) = v;
             *reinterpret_cast<int2*>(&s1[lr][4 + 2 * k]) = make_int2(g.g1a, g.g1b);
         } else {
-            const int u = t - 64, side = u >> 5, rr = u & 31;
+            const int u = t - 64, side = u / FR, rr = u % FR;
             const int r = R0 + rr, c = wrapi(side ? C0 + kFC : C0 - 2, n);
             const int2 v = *reinterpret_cast<const int2*>(qin + (size_t)r * n + c);
             const PairNoise g = pair_noise(a, static_cast<uint32_t>((r * n + c) >> 1), m, c2, c3, v.x, v.y, d1, d2);
@@ -170,32 +177,22 @@ __global__ void __launch_bounds__(kThreads) stream_fine_kernel(const SArgs a, in
         gu[0] = b0.x; gu[1] = b0.y; gu[2] = b0.z; gu[3] = b0.w;
         gd[0] = b1.x; gd[1] = b1.y; gd[2] = b1.z; gd[3] = b1.w;
     }
-    int32_t out[2][4];
+    int32_t ql[2], qr[2], gl[2], gr[2];
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
-        const int32_t ql = sq[lr0 + i][lc0 - 1], qr = sq[lr0 + i][lc0 + 4];
-        const int32_t gl = s2[lr0 + i][lc0 - 1], gr = s2[lr0 + i][lc0 + 4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int32_t x = q[i][j];
-            const int32_t u = i == 0 ? up[j] : q[0][j];
-            const int32_t d = i == 1 ? dn[j] : q[1][j];
-            const int32_t l = j == 0 ? ql : q[i][j - 1];
-            const int32_t r = j == 3 ? qr : q[i][j + 1];
-            const int32_t g1u = i == 0 ? gu[j] : G1[0][j];
-            const int32_t g1d = i == 1 ? gd[j] : G1[1][j];
-            const int32_t g2l = j == 0 ? gl : G2[i][j - 1];
-            const int32_t g2r = j == 3 ? gr : G2[i][j + 1];
-            const int32_t f = edge_flux(a.Af, d - x) - edge_flux(a.Af, x - u) + edge_flux(a.Af, r - x) -
-                              edge_flux(a.Af, x - l);
-            const int32_t v = x + f + (g1d - g1u) + (g2r - g2l);
-            out[i][j] = v;
-            bad |= (static_cast<uint32_t>(v) + 0x40000000u) >> 31;
-        }
+        ql[i] = sq[lr0 + i][lc0 - 1];
+        qr[i] = sq[lr0 + i][lc0 + 4];
+        gl[i] = s2[lr0 + i][lc0 - 1];
+        gr[i] = s2[lr0 + i][lc0 + 4];
     }
+    // each edge flux once per block, as in the register kernels
+    flux_update<2, 4>(q, G1, G2, up, gu, dn, gd, ql, gl, qr, gr, a.Af);
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
-        *reinterpret_cast<int4*>(qout + (size_t)(r0 + i) * n + c0) = make_int4(out[i][0], out[i][1], out[i][2], out[i][3]);
+    for (int i = 0; i < 2; ++i) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) bad |= (static_cast<uint32_t>(q[i][j]) + 0x40000000u) >> 31;
+        *reinterpret_cast<int4*>(qout + (size_t)(r0 + i) * n + c0) = make_int4(q[i][0], q[i][1], q[i][2], q[i][3]);
+    }
     if (a.coupled) *zp = make_float4(z[0][0], z[0][1], z[1][0], z[1][1]);
     if (bad) atomicOr(a.err, kErrRange);
 }
@@ -352,16 +349,47 @@ size_t stream_bytes(int n, int S) {
                         tiles * (2 * kMaxObs + 2) * sizeof(double));
 }
 
-int stream_inflight(int n, size_t budget) {
+int stream_variant_count() { return kStreamVariants; }
+
+template <int FR>
+static cudaError_t fine_attr() {
+    return cudaFuncSetAttribute(stream_fine_kernel<FR>, cudaFuncAttributeMaxDynamicSharedMemorySize, fine_smem(FR));
+}
+
+cudaError_t stream_variant_info(int n, int variant, VariantInfo* out) {
+    if (variant < 0 || variant >= kStreamVariants) return cudaErrorInvalidValue;
+    const int fr = fine_rows(variant);
+    cudaError_t e = variant == 0 ? fine_attr<32>() : fine_attr<64>();
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return e;
+    e = variant == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stream_fine_kernel<32>, fine_threads(32),
+                                                                     fine_smem(32))
+                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stream_fine_kernel<64>, fine_threads(64),
+                                                                     fine_smem(64));
+    if (e != cudaSuccess) return e;
+    *out = VariantInfo{};
+    out->supported = (n % kFC == 0 && n % fr == 0 && per_sm > 0) ? 1 : 0;
+    out->threads = fine_threads(fr);
+    out->cluster = 1;
+    out->slots_per_cta = 0;
+    out->smem = fine_smem(fr);
+    out->max_ctas = sms * per_sm;
+    out->C = 2;        // coarse cells per thread along a row
+    out->R = 1;
+    out->tile_rows = fr;
+    return cudaSuccess;
+}
+
+int stream_inflight(int n, size_t budget, int variant) {
     // the largest count that fits the budget, lowered while a smaller count
     // fills the last wave of fine-step CTAs clearly better
     const int s_max = (int)std::max<size_t>(1, budget / stream_bytes(n, 1));
-    int dev = 0, sms = 0, per_sm = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stream_fine_kernel, kThreads, 0) != cudaSuccess ||
-        sms * per_sm == 0)
-        return s_max;
-    const long long resident = (long long)sms * per_sm, ctas = (long long)(n / kFC) * (n / kFR);
+    VariantInfo vi{};
+    if (stream_variant_info(n, variant, &vi) != cudaSuccess || !vi.supported) return s_max;
+    const long long resident = vi.max_ctas, ctas = (long long)(n / kFC) * (n / vi.tile_rows);
     int best = s_max;
     double best_eff = 0.0;
     for (int S = s_max; S >= std::max(1, s_max / 2); --S) {
@@ -386,23 +414,29 @@ void stream_carve(SArgs* a, void* buf, int n, int S) {
     a->tile_part = reinterpret_cast<double*>(p);
 }
 
-cudaError_t stream_run(const KArgs& k, SArgs a, int S, cudaStream_t st) {
+cudaError_t stream_run(const KArgs& k, SArgs a, int S, int variant, cudaStream_t st) {
     // k.partials holds S slots (entry-major, [stride][S]); zero them, run the
     // waves of S samples, accumulate per slot, then the caller reduces.
     const int n = a.n;
-    if (n % kFC != 0 || (a.coupled && (a.nc % kTile != 0 || a.M % 4 != 0))) return cudaErrorInvalidValue;
+    if (variant < 0 || variant >= kStreamVariants) return cudaErrorInvalidValue;
+    const int fr = fine_rows(variant);
+    if (n % kFC != 0 || n % fr != 0 || (a.coupled && (a.nc % kTile != 0 || a.M % 4 != 0))) return cudaErrorInvalidValue;
     const int tiles = (n / kTile) * (n / kTile);
     const int ctiles = a.coupled ? (a.nc / kTile) * (a.nc / kTile) : 0;
-    zero_kernel<<<64, 256, 0, st>>>(k.partials, (size_t)k.slot_stride * S);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = variant == 0 ? fine_attr<32>() : fine_attr<64>();
     if (e != cudaSuccess) return e;
+    zero_kernel<<<64, 256, 0, st>>>(k.partials, (size_t)k.slot_stride * S);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     for (long long done = 0; done < k.count; done += S) {
         a.sid0 = k.first + done;
         a.count = (int)std::min<long long>(S, k.count - done);
-        const dim3 grid(tiles, a.count), cgrid(ctiles, a.count), fgrid(n / kFC, n / kFR, a.count);
+        const dim3 grid(tiles, a.count), cgrid(ctiles, a.count), fgrid(n / kFC, n / fr, a.count);
         stream_init_kernel<<<grid, kThreads, 0, st>>>(a);
         for (int m = 0; m < a.M; ++m) {
-            stream_fine_kernel<<<fgrid, kThreads, 0, st>>>(a, m);
+            if (variant == 0)
+                stream_fine_kernel<32><<<fgrid, fine_threads(32), fine_smem(32), st>>>(a, m);
+            else
+                stream_fine_kernel<64><<<fgrid, fine_threads(64), fine_smem(64), st>>>(a, m);
             if (a.coupled && (m & 3) == 3) stream_coarse_kernel<<<cgrid, kThreads, 0, st>>>(a, m >> 2);
         }
         stream_observe_kernel<<<grid, kThreads, 0, st>>>(a);

@@ -37,14 +37,13 @@ struct LevelTab {
     float* d_phi = nullptr;
     std::vector<dk::VariantInfo> vis[2];   // kernel variants: [0] fine path only, [1] coupled pair
     int streamed = 0;                      // no register variant: state streamed through global memory
-    int inflight = 0;                      // samples in flight on the streamed path
+    int inflight = 0;                      // samples in flight on the streamed path (buffers sized for this)
+    int inflight_v[8] = {0};               // ... per streamed tile variant
     void* d_stream = nullptr;              // their state
     double* d_spart = nullptr;             // their per-slot partial sums [stride][S]
     int sel[2] = {0, 0};                   // variant in use for each mode
     const dk::VariantInfo& vi(bool coupled) const {
         static const dk::VariantInfo none{};
-        static const dk::VariantInfo streamed_info{1, 256, 1, 0, 0, 0, 0, 0};
-        if (streamed) return streamed_info;
         const auto& v = vis[coupled ? 1 : 0];
         return v.empty() ? none : v[sel[coupled ? 1 : 0]];
     }
@@ -231,10 +230,13 @@ int launch_batch(mlmc_dk_ctx* c, int level, int stream_tag, int64_t first, int64
                              c->partials_cap, 0);
 }
 
+// Streamed level (state in global memory); `steps` > 0 truncates every sample
+// to that many fine steps (used only to time the tile variants).
 int launch_streamed(mlmc_dk_ctx* c, int level, int stream_tag, int64_t first, int64_t count, uint64_t seed,
-                    double* sums_dev, double* samples_dev, cudaStream_t st) {
+                    double* sums_dev, double* samples_dev, cudaStream_t st, int steps = 0) {
     const bool coupled = (stream_tag == 0) && level > 0;
     LevelTab& t = c->lv[level];
+    const int variant = t.sel[coupled ? 1 : 0];
     cudaError_t e;
     if (count == 0) {
         e = cudaMemsetAsync(sums_dev, 0, sizeof(double) * c->stride, st);
@@ -246,7 +248,7 @@ int launch_streamed(mlmc_dk_ctx* c, int level, int stream_tag, int64_t first, in
     dk::stream_carve(&a, t.d_stream, t.n, t.inflight);
     a.n = t.n;
     a.nc = t.n / 2;
-    a.M = t.M;
+    a.M = steps > 0 ? steps : t.M;
     a.coupled = coupled ? 1 : 0;
     a.n_obs = c->n_obs;
     a.q0f = k.q0f; a.qbf = k.qbf; a.phif = k.phif;
@@ -254,8 +256,9 @@ int launch_streamed(mlmc_dk_ctx* c, int level, int stream_tag, int64_t first, in
     a.Af = k.Af; a.Ac = k.Ac; a.gf = k.gf; a.gc = k.gc;
     a.key0 = k.key0; a.key1 = k.key1; a.tag = k.tag;
     a.err = c->d_err;
-    if ((e = dk::stream_run(k, a, t.inflight, st)) != cudaSuccess) return cuda_fail(c, e, "streamed level");
-    if ((e = dk::launch_reduce(t.d_spart, t.inflight, c->stride, sums_dev, st)) != cudaSuccess)
+    const int S = t.inflight_v[variant];
+    if ((e = dk::stream_run(k, a, S, variant, st)) != cudaSuccess) return cuda_fail(c, e, "streamed level");
+    if ((e = dk::launch_reduce(t.d_spart, S, c->stride, sums_dev, st)) != cudaSuccess)
         return cuda_fail(c, e, "reduce kernel launch");
     return MLMC_DK_OK;
 }
@@ -535,7 +538,21 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
                 return fail(nullptr, MLMC_DK_ERR_UNSUPPORTED, "grid size without a kernel");
             }
             t.streamed = 1;
-            t.inflight = dk::stream_inflight(t.n, (size_t)96 << 20);
+            for (int v = 0; v < dk::stream_variant_count(); ++v) {
+                t.inflight_v[v] = dk::stream_inflight(t.n, (size_t)96 << 20, v);
+                t.inflight = std::max(t.inflight, t.inflight_v[v]);
+            }
+            for (int mode = 0; mode < 2; ++mode) {
+                if (mode == 1 && l == 0) continue;
+                for (int v = 0; v < dk::stream_variant_count(); ++v) {
+                    dk::VariantInfo vi{};
+                    if ((e = dk::stream_variant_info(t.n, v, &vi)) != cudaSuccess) {
+                        mlmc_dk_free(c);
+                        return cuda_fail(nullptr, e, "streamed kernel variant setup");
+                    }
+                    t.vis[mode].push_back(vi);
+                }
+            }
             if ((e = cudaMalloc(&t.d_stream, dk::stream_bytes(t.n, t.inflight))) != cudaSuccess ||
                 (e = cudaMalloc(&t.d_spart, sizeof(double) * c->stride * t.inflight)) != cudaSuccess) {
                 mlmc_dk_free(c);
@@ -639,7 +656,8 @@ int mlmc_dk_level_info(const mlmc_dk_ctx* ctx, int32_t level, mlmc_dk_level_desc
     out->lane_rows = vs.R;
     out->cluster = vs.cluster;
     out->streamed = t.streamed;
-    out->in_flight = t.inflight;
+    out->in_flight = t.streamed ? t.inflight_v[t.sel[level > 0 ? 1 : 0]] : 0;
+    out->tile_rows = vs.tile_rows;
     return MLMC_DK_OK;
 }
 
@@ -852,12 +870,16 @@ int mlmc_dk_tune(mlmc_dk_ctx* ctx, int32_t repeats, double* seconds) {
                 const dk::VariantInfo& vi = t.vis[mode][v];
                 if (!vi.supported) continue;
                 t.sel[mode] = v;
-                // two full waves of resident sample slots
-                const int64_t count = 2LL * (vi.max_ctas / vi.cluster) * vi.slots_per_cta;
+                // two full waves of resident sample slots; streamed levels: one wave
+                // of samples in flight over a short horizon
+                const int64_t count = t.streamed ? t.inflight_v[v] : 2LL * (vi.max_ctas / vi.cluster) * vi.slots_per_cta;
                 double ms_min = 1e300;
                 for (int r = 0; r < repeats + 1; ++r) {
                     if ((e = cudaEventRecord(ctx->ev0, ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "tune");
-                    int rc = launch_batch(ctx, l, mode == 1 ? 0 : 1, 0, count, 0x7475, ctx->d_sums, nullptr, ctx->stream);
+                    const int tag = mode == 1 ? 0 : 1;
+                    int rc = t.streamed ? launch_streamed(ctx, l, tag, 0, count, 0x7475, ctx->d_sums, nullptr, ctx->stream,
+                                                          std::min(t.M, 64))
+                                        : launch_batch(ctx, l, tag, 0, count, 0x7475, ctx->d_sums, nullptr, ctx->stream);
                     if (rc != MLMC_DK_OK) return rc;
                     if ((e = cudaEventRecord(ctx->ev1, ctx->stream)) != cudaSuccess ||
                         (e = cudaEventSynchronize(ctx->ev1)) != cudaSuccess)

@@ -55,7 +55,7 @@ class LevelDesc(ctypes.Structure):
         ("next_sample", ctypes.c_int64), ("h2d_bytes", ctypes.c_int64), ("frac_bits", ctypes.c_int32),
         ("n_variants", ctypes.c_int32), ("variant_single", ctypes.c_int32), ("variant_coupled", ctypes.c_int32),
         ("lane_cols", ctypes.c_int32), ("lane_rows", ctypes.c_int32), ("cluster", ctypes.c_int32),
-        ("streamed", ctypes.c_int32), ("in_flight", ctypes.c_int32),
+        ("streamed", ctypes.c_int32), ("in_flight", ctypes.c_int32), ("tile_rows", ctypes.c_int32),
     ]
 
 
