@@ -37,7 +37,11 @@
  * global memory with one launch per fine step (same arithmetic, same results).
  *
  * Grids are row-major, point (i1, i2) at (i1 h, i2 h), flat index i1 n + i2;
- * component r = 1 of the noise flux is along i1.
+ * component r = 1 of the noise flux is along i1.  The library only sees the
+ * caller's samples of rho-bar_0 and phi_k: sampled at (i1 + 1/2, i2 + 1/2) h
+ * instead (cell-centred grids), each coarse point is the centre of its coupled
+ * 2x2 block and the same kernels run the symmetric variant of the coupling
+ * (Remark avoid_right_bias).
  *
  * Precision: the state is 32-bit fixed point, rho = q 2^-S_l, with S_l in
  * [16, 40] chosen per level at init as large as the initial range and the

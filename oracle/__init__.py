@@ -70,6 +70,9 @@ def lib():
                                               ctypes.c_uint64, ctypes.c_int, ctypes.c_double, ctypes.c_uint64,
                                               _dp, _dp, _dp, _dp]
         L.oracle_sample_perturbed.restype = ctypes.c_int
+        L.oracle_sample_given.argtypes = [ctypes.POINTER(_OracleLevelC), _dp, ctypes.c_int,
+                                          _dp, _dp, _dp, _dp, _dp, _dp]
+        L.oracle_sample_given.restype = ctypes.c_int
         L.oracle_mean_field.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
                                         _dp, _dp]
         _LIB = L
@@ -185,6 +188,30 @@ class OracleLevel:
                 out["rho_c"] = rc.reshape(n // 2, n // 2)
         return out
 
+
+    def sample_given(self, Z: np.ndarray, coupled: bool, fields: bool = False):
+        """The sample driven by the caller's fine normals Z of shape (M, n, n, 2)
+        (see oracle_sample_given)."""
+        n, M = self.lv.n, self.lv.M
+        Z = np.ascontiguousarray(Z, dtype=np.float64)
+        if Z.shape != (M, n, n, 2):
+            raise ValueError(f"normals must have shape {(M, n, n, 2)}")
+        Yf = np.zeros(self.n_obs)
+        Yc = np.zeros(self.n_obs)
+        mf = ctypes.c_double(0.0)
+        mc = ctypes.c_double(0.0)
+        rf = np.empty(n * n) if fields else None
+        rc = np.empty((n // 2) ** 2) if (fields and coupled) else None
+        rc_ = lib().oracle_sample_given(ctypes.byref(self.c), _ptr(Z), int(coupled), _ptr(Yf), _ptr(Yc),
+                                        ctypes.byref(mf), ctypes.byref(mc), _ptr(rf), _ptr(rc))
+        if rc_ != 0:
+            raise ValueError(f"oracle_sample_given failed ({rc_})")
+        out = dict(Y_f=Yf, Y_c=Yc if coupled else None, mass_f=mf.value, mass_c=mc.value if coupled else None)
+        if fields:
+            out["rho_f"] = rf.reshape(n, n)
+            if coupled:
+                out["rho_c"] = rc.reshape(n // 2, n // 2)
+        return out
 
     def sample_perturbed(self, seed: int, sample: int, coupled: bool, amp: float, perturb_seed: int,
                          stream: int = 0):

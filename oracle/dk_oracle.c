@@ -158,7 +158,7 @@ static void perturb_edges(int n, double amp, uint64_t* state, double* rho)
 }
 
 static int sample_impl(const oracle_level* lv, uint64_t seed, int stream, uint64_t sample,
-                       int coupled, double amp, uint64_t perturb_seed,
+                       int coupled, double amp, uint64_t perturb_seed, const double* given,
                        double* Y_f, double* Y_c, double* mass_f, double* mass_c,
                        double* rho_f_out, double* rho_c_out)
 {
@@ -182,7 +182,10 @@ static int sample_impl(const oracle_level* lv, uint64_t seed, int stream, uint64
     const double sqrt_tau = sqrt(lv->tau);
     const double block_weight = pow(2.0, -0.5 * 2);   /* 2^{-d/2} of the NN coupling */
     for (int64_t m = 0; m < lv->M; ++m) {
-        oracle_normals(seed, lv->level, stream, sample, m, n, Z);
+        if (given)
+            memcpy(Z, given + (size_t)m * cf * 2, sizeof(double) * cf * 2);
+        else
+            oracle_normals(seed, lv->level, stream, sample, m, n, Z);
         for (size_t i = 0; i < cf * 2; ++i) dbeta_f[i] = sqrt_tau * Z[i];
         if (coupled) {
             /* beta-tilde_(y,r) = 2^{-d/2} sum_{z in B->(y)} beta_(z,r), B->(y) = {y + h v}:
@@ -226,14 +229,21 @@ int oracle_sample(const oracle_level* lv, uint64_t seed, int stream, uint64_t sa
                   int coupled, double* Y_f, double* Y_c, double* mass_f, double* mass_c,
                   double* rho_f_out, double* rho_c_out)
 {
-    return sample_impl(lv, seed, stream, sample, coupled, 0.0, 0, Y_f, Y_c, mass_f, mass_c,
+    return sample_impl(lv, seed, stream, sample, coupled, 0.0, 0, NULL, Y_f, Y_c, mass_f, mass_c,
                        rho_f_out, rho_c_out);
+}
+
+int oracle_sample_given(const oracle_level* lv, const double* Z_all, int coupled,
+                        double* Y_f, double* Y_c, double* mass_f, double* mass_c,
+                        double* rho_f_out, double* rho_c_out)
+{
+    return sample_impl(lv, 0, 0, 0, coupled, 0.0, 0, Z_all, Y_f, Y_c, mass_f, mass_c, rho_f_out, rho_c_out);
 }
 
 int oracle_sample_perturbed(const oracle_level* lv, uint64_t seed, int stream, uint64_t sample,
                             int coupled, double amp, uint64_t perturb_seed,
                             double* Y_f, double* Y_c, double* mass_f, double* mass_c)
 {
-    return sample_impl(lv, seed, stream, sample, coupled, amp, perturb_seed, Y_f, Y_c, mass_f, mass_c,
+    return sample_impl(lv, seed, stream, sample, coupled, amp, perturb_seed, NULL, Y_f, Y_c, mass_f, mass_c,
                        NULL, NULL);
 }

@@ -72,6 +72,16 @@ int oracle_sample(const oracle_level* lv, uint64_t seed, int stream, uint64_t sa
                   int coupled, double* Y_f, double* Y_c, double* mass_f, double* mass_c,
                   double* rho_f_out, double* rho_c_out);
 
+/* Same as oracle_sample with the fine normals supplied by the caller instead
+ * of drawn: Z_all holds M arrays of n*n*2 standard normals in step order, cell
+ * x = i1*n + i2, component r at 2x + r.  The coarse increments are formed from
+ * them exactly as in oracle_sample (used to check properties of the coupling
+ * that need chosen noise, such as its behaviour under a reflection of the
+ * torus; Remark avoid_right_bias). */
+int oracle_sample_given(const oracle_level* lv, const double* Z_all, int coupled,
+                        double* Y_f, double* Y_c, double* mass_f, double* mass_c,
+                        double* rho_f_out, double* rho_c_out);
+
 /* Same as oracle_sample, and after every fine (coarse) step each edge of the
  * fine (coarse) grid moves a uniform random amount in [-amp/2, amp/2] from one
  * of its cells to the other (splitmix64 stream from perturb_seed).  These

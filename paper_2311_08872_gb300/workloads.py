@@ -7,13 +7,19 @@ sampled at grid points, and seeds.  It holds none of the scheme's arithmetic
 (no stepping, no noise, no observables, no level coupling), so that the CUDA
 path and the FP64 oracle can both be fed from it without sharing method code.
 
-Grid convention: point (i1, i2) of an n x n grid sits at (i1*h, i2*h) with
-h = L/n; arrays are row-major with flat index i1*n + i2.  The paper's grid
-{-pi, ..., pi-h}^2 is the same point set when n is even (Section 2).
+Grid convention: point (i1, i2) of an n x n grid sits at ((i1+o)*h, (i2+o)*h)
+with h = L/n and the workload's offset o; arrays are row-major with flat index
+i1*n + i2.  With o = 0 the coarse point I of a level pair is the fine point 2I
+and its coupled noise block {2I, 2I+1}^2 lies to its right (the Right-Most
+coupling of Section 3.2; the paper's grid {-pi, ..., pi-h}^2 is this point set
+when n is even).  With o = 1/2 (cell-centred points, the shifted grid of
+Remark avoid_right_bias) the coarse point (I+1/2)*2h is the centre of the same
+block: the symmetric variant of the coupling, with no change to the kernels.
 
 Workloads:
   * ``mc32``         -- plain MC on 32^2, unit torus, T=0.01, N=1e4.
   * ``mlmc16_256``   -- coupled MLMC, levels 16^2..256^2, T=0.02, N=1e5.
+  * ``mlmc16_256_sym`` -- the same on cell-centred grids (symmetric coupling).
   * ``lowdens32_512``-- low-density periodised Gaussian, levels 32^2..512^2.
   * ``large32_1024`` -- levels 32^2..1024^2, T=0.05, N=1e6, four cosine modes
                         plus all pairwise products.
@@ -32,10 +38,11 @@ import numpy as np
 TWO_PI = 2.0 * math.pi
 
 
-def grid_coords(n: int, length: float) -> Tuple[np.ndarray, np.ndarray]:
-    """(x1, x2) coordinate arrays of shape (n, n) for the n x n torus grid."""
+def grid_coords(n: int, length: float, offset: float = 0.0) -> Tuple[np.ndarray, np.ndarray]:
+    """(x1, x2) coordinate arrays of shape (n, n) for the n x n torus grid,
+    points at (i + offset) h."""
     h = length / n
-    i = np.arange(n, dtype=np.float64) * h
+    i = (np.arange(n, dtype=np.float64) + offset) * h
     return np.meshgrid(i, i, indexing="ij")
 
 
@@ -113,8 +120,8 @@ class Observable:
     kind: str                    # "cos" or "sin+sin"
     k: Tuple[int, int] = (1, 0)  # wave vector for "cos"
 
-    def grid(self, n: int, length: float) -> np.ndarray:
-        x1, x2 = grid_coords(n, length)
+    def grid(self, n: int, length: float, offset: float = 0.0) -> np.ndarray:
+        x1, x2 = grid_coords(n, length, offset)
         if self.kind == "cos":
             return phi_cos(x1, x2, length, self.k)
         if self.kind == "sin+sin":
@@ -140,6 +147,7 @@ class Workload:
     M0: int = 0                     # >0 overrides M_0 = ceil(T / (mu h0^2))
     alloc: Optional[Tuple[int, ...]] = None   # fixed per-level sample counts of one benchmark step
     alloc_scale: int = 1            # the eps-optimal allocation is about alloc * alloc_scale
+    offset: float = 0.0             # grid points at (i + offset) h: 0 right-most, 1/2 symmetric coupling
     note: str = ""
 
     def n(self, level: int) -> int:
@@ -147,12 +155,13 @@ class Workload:
 
     def rho0(self, level: int) -> np.ndarray:
         n = self.n(level)
-        x1, x2 = grid_coords(n, self.length)
+        x1, x2 = grid_coords(n, self.length, self.offset)
         return np.ascontiguousarray(RHO0_KINDS[self.rho0_kind](x1, x2, self.length), dtype=np.float64)
 
     def phi(self, level: int) -> List[np.ndarray]:
         n = self.n(level)
-        return [np.ascontiguousarray(o.grid(n, self.length), dtype=np.float64) for o in self.observables]
+        return [np.ascontiguousarray(o.grid(n, self.length, self.offset), dtype=np.float64)
+                for o in self.observables]
 
     def rho0_all(self) -> List[np.ndarray]:
         return [self.rho0(l) for l in range(self.L_max + 1)]
@@ -175,6 +184,10 @@ WORKLOADS: Dict[str, Workload] = {
     "mlmc16_256": Workload("mlmc16_256", 1.0, 16, 4, 0.02, 0.1, 1e5, "sinsin", [COS1],
                            seed=1, eps_rel=1e-3, alloc=(578250, 28946, 4617, 1570, 955), alloc_scale=1024,
                            note="coupled MLMC, levels 16^2..256^2"),
+    "mlmc16_256_sym": Workload("mlmc16_256_sym", 1.0, 16, 4, 0.02, 0.1, 1e5, "sinsin", [COS1],
+                               seed=1, eps_rel=1e-3, alloc=(578250, 28946, 4617, 1570, 955), alloc_scale=1024,
+                               offset=0.5,
+                               note="mlmc16_256 on cell-centred grids: symmetric NN coupling"),
     "lowdens32_512": Workload("lowdens32_512", 1.0, 32, 4, 0.02, 0.1, 1e5, "gauss", [COS1],
                               seed=2, eps_rel=2e-3,
                               note="low-density periodised Gaussian, levels 32^2..512^2"),

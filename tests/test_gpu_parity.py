@@ -165,6 +165,13 @@ def test_coupled_mlmc16_256_finest_level_full_size(dk):
     check_level(dk, W.get("mlmc16_256"), 4, 0, 17, 2, seed=1, processes=2)
 
 
+@pytest.mark.parametrize("level,count", [(1, 40), (2, 6)])
+def test_symmetric_coupling_levels(dk, level, count):
+    """Cell-centred grids (the symmetric coupling of Remark avoid_right_bias):
+    the same kernels fed with inputs sampled at the shifted points."""
+    check_level(dk, W.get("mlmc16_256_sym"), level, 0, 0, count, seed=1)
+
+
 def test_ragged_tail_large_ids_and_mc_stream(dk):
     wl = W.get("mlmc16_256")
     check_level(dk, wl, 1, 0, 2 ** 32 + 5, 37, seed=2 ** 35 + 9)

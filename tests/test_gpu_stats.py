@@ -72,6 +72,28 @@ def test_coarse_path_law_equals_standalone_path(dk, level):
     assert vdp < 0.5 * vpf
 
 
+def test_symmetric_and_right_most_couplings_are_unbiased(dk):
+    """At high density E[P_l - P_(l-1)] equals the difference of the closed
+    forms (which do not depend on the grid offset) for the Right-Most coupling
+    on vertex grids and the symmetric one on cell-centred grids; the level
+    variances of both are printed for comparison."""
+    out = {}
+    for name in ("mlmc16_256", "mlmc16_256_sym"):
+        wl = W.get(name).with_(L_max=3, N=1e7)
+        V = []
+        with dk.Context.from_workload(wl) as ctx:
+            for level in (1, 2, 3):
+                s = ctx.run_level(level, {1: 60000, 2: 12000, 3: 3000}[level], seed=31)[0]
+                f, c = ctx.level_info(level), ctx.level_info(level - 1)
+                m, se = _mean_se(s.dp1, s.dp2, s.n)
+                expect = (oracle.closed_form_EP_cos1(1.0, f.n, f.tau, f.M) -
+                          oracle.closed_form_EP_cos1(1.0, c.n, c.tau, c.M))
+                assert abs(m - expect) < K_SE * se, (name, level, m, expect, se)
+                V.append((s.dp2 - s.dp1 ** 2 / s.n) / (s.n - 1))
+        out[name] = V
+    print("V_l (levels 1..3), right-most:", out["mlmc16_256"], "symmetric:", out["mlmc16_256_sym"])
+
+
 def _oracle_mlmc(wl, eps_rel, seed, pilot, L_start):
     """Algorithm 1 with oracle samples, same decisions as the library's driver."""
     levels = oracle.level_table(wl.length, wl.n0, wl.L_max, wl.T, wl.mu, wl.M0)
