@@ -66,6 +66,61 @@ def kernel_sources_hash() -> str:
     return h.hexdigest()[:16]
 
 
+# Streamed-state stencil: algorithmic bytes per coupled fine cell-step (4 B read
+# + 4 B write of the fine state; the coarse state's 8 B every 4th step on a
+# quarter of the cells = 0.5 B); the normals are generated in registers.
+STREAM_BYTES_PER_FINE_CELL_STEP = 8.5
+
+
+def measured_peaks():
+    """(HBM GB/s, source) from the measured peaks, else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def closed_form_EP_cos1(n, tau, M):
+    """Martingale-lemma value of E[P] for phi = cos(2 pi x1) on the unit torus
+    when rho stays positive (a lower bound otherwise): (tau/2) (sin(2 pi h)/h)^2
+    (1 - g^2M) / (1 - g^2), g = 1 - 2 (tau/h^2) sin^2(pi h)."""
+    h = 1.0 / n
+    g = 1.0 - 2.0 * (tau / (h * h)) * math.sin(math.pi * h) ** 2
+    return 0.5 * tau * (math.sin(2 * math.pi * h) / h) ** 2 * (1.0 - g ** (2 * M)) / (1.0 - g * g)
+
+
+def streamed_stencil(stream):
+    """One wave of samples in flight of the 512^2 level of the low-density
+    workload on the streamed-state kernels (CUDA events on the launching
+    stream; tile variant picked by the autotuner)."""
+    import torch
+    from paper_2311_08872_gb300 import mlmc_dk, workloads
+    wl = workloads.get("lowdens32_512")
+    level = wl.L_max
+    with mlmc_dk.Context.from_workload(wl, stream=stream.cuda_stream) as c:
+        c.tune(1)
+        info = c.level_info(level)
+        S = info.in_flight
+        sums = torch.zeros(mlmc_dk.sums_len(c.n_quant), dtype=torch.float64, device="cuda")
+        c.run_level_dev(level, 0, 0, 1, 9, sums.data_ptr(), 0, stream.cuda_stream)      # warm-up
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        c.run_level_dev(level, 0, 1, S, 9, sums.data_ptr(), 0, stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) * 1e-3
+    fine = S * info.n ** 2 * info.M
+    peak, src = measured_peaks()
+    gbs = fine * STREAM_BYTES_PER_FINE_CELL_STEP / sec / 1e9
+    return {"workload": wl.name, "level": level, "n": info.n, "fine_steps": info.M, "samples": S,
+            "tile_rows": info.tile_rows, "s": sec, "cell_steps_per_s": S * info.cost / sec,
+            "fine_cell_steps_per_s": fine / sec, "algorithmic_bytes_per_fine_cell_step": STREAM_BYTES_PER_FINE_CELL_STEP,
+            "achieved_GBps": gbs, "hbm_peak_GBps": peak, "peak_source": src, "frac_of_hbm": gbs / peak,
+            "bound": "alu (instruction issue): the working set stays in L2, DRAM traffic is the cold start only"}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -75,6 +130,7 @@ def parse():
     ap.add_argument("--workload", default="mlmc16_256")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-streamed", action="store_true", help="skip the streamed-state stencil timing")
     ap.add_argument("--no-adaptive", action="store_true", help="skip the Algorithm 1 / plain MC timing")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned level below 0")
@@ -374,6 +430,10 @@ def run_ours(args, wl, rank, world, local_rank):
                      "s_per_sample_P0": t_l[0], "mlmc_s_to_eps": t_sur,
                      "mlmc_s_to_eps_incl_training": t_sur + train_s, "extrapolated": True}
 
+    streamed = None
+    if not args.no_streamed:
+        streamed = streamed_stencil(stream)
+
     e2e = None
     if not args.no_e2e:
         ctx.close()
@@ -436,6 +496,13 @@ def run_ours(args, wl, rank, world, local_rank):
     line["to_eps"] = to_eps
     line["mc"] = mc
     line["mlmc_adaptive_measured"] = adaptive
+    fin = info[Ls]
+    cf = closed_form_EP_cos1(fin.n, fin.tau, fin.M) if wl.rho0_kind == "sinsin" and wl.length == 1.0 else None
+    line["closed_form_EP_finest"] = {"value": cf, "estimate": to_eps["estimate"],
+                                     "note": "martingale-lemma E[P_L] if rho stayed positive; at the finest "
+                                             "level N h^2 = %.2g particles per cell, so it is a lower bound and "
+                                             "the gap is the positive-part effect" % (wl.N * (wl.length / fin.n) ** 2)}
+    line["streamed_stencil"] = streamed
     if surrogate:
         line["surrogate"] = surrogate
         line["mlmc_surrogate_s_to_eps"] = surrogate["mlmc_s_to_eps_incl_training"]
