@@ -296,6 +296,10 @@ def run_ours(args, wl, rank, world, local_rank):
         raise SystemExit("workload has no fixed allocation")
     alloc = alloc + [0] * (wl.L_max + 1 - len(alloc))
     sample_steps, cell_steps = batch_units(wl, alloc)
+    # batch split: share of the 256^2 level's samples on the streamed kernels, on the
+    # SMs its 8-SM clusters leave free (tuned on the batch at a quarter of its size)
+    split_frac, split_s = ctx.tune_batch([(a + 3) // 4 for a in alloc], 1)
+    split_level = max((l for l in range(len(alloc)) if ctx.level_info(l).split_capable), default=None)
 
     nq = ctx.n_quant
     sums = torch.zeros(wl.L_max + 1, mlmc_dk.sums_len(nq), dtype=torch.float64, device=dev)
@@ -338,6 +342,10 @@ def run_ours(args, wl, rank, world, local_rank):
             level_ms[l] += t
             if alloc[l] > 0:
                 launches += 2
+            d = ctx.level_info(l)
+            if d.batch_streamed > 0:      # zero + per wave (init, fine steps, coarse steps, observe, finish) + reduce + merge
+                waves = -(-d.batch_streamed // d.in_flight)
+                launches += 1 + waves * (3 + d.M + d.M // 4) + 2
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -349,12 +357,15 @@ def run_ours(args, wl, rank, world, local_rank):
         total_ms = float(t.item())
     value = world * sample_steps * args.steps / (total_ms * 1e-3)
 
+    split_samples = ctx.level_info(split_level).batch_streamed if split_level is not None else 0
+
     # ---- roofline of the dominant kernel (the level kernel of the costliest level)
     dom = max(range(len(alloc)), key=lambda l: level_ms[l])
     if level_ms[dom] <= 0:
         raise SystemExit("no per-level kernel times from the batch")
     lv, fine, coarse = level_costs(wl)
-    ops = alloc[dom] * (fine[dom] * XU_OPS_FINE + coarse[dom] * XU_OPS_COARSE) * args.steps
+    reg_dom = alloc[dom] - ctx.level_info(dom).batch_streamed    # samples the register kernel ran
+    ops = reg_dom * (fine[dom] * XU_OPS_FINE + coarse[dom] * XU_OPS_COARSE) * args.steps
     achieved = ops / (level_ms[dom] * 1e-3)
     peak = XU_PER_CLK_PER_SM * SMS * SM_MAX_MHZ * 1e6
     kname = (f"level_kernel n={info[dom].n} C={info[dom].lane_cols} R={info[dom].lane_rows} "
@@ -367,7 +378,8 @@ def run_ours(args, wl, rank, world, local_rank):
                 "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gop/s", "frac": achieved / peak,
                 "traffic": traffic, "traffic_unit": "DRAM bytes per launch (ncu, one launch per step)",
                 "ops_per_fine_cell_step": XU_OPS_FINE,
-                "cell_steps_per_s": alloc[dom] * (fine[dom] + coarse[dom]) * args.steps / (level_ms[dom] * 1e-3),
+                "samples_per_launch": reg_dom,
+                "cell_steps_per_s": reg_dom * (fine[dom] + coarse[dom]) * args.steps / (level_ms[dom] * 1e-3),
                 "level_ms_per_step": [x / args.steps for x in level_ms],
                 "note": "levels run concurrently in one CUDA graph; each level's time is its own stream's span"}
 
@@ -446,6 +458,8 @@ def run_ours(args, wl, rank, world, local_rank):
                 c2.set_variant(l, False, vs)
                 if l > 0:
                     c2.set_variant(l, True, vc)
+            if split_level is not None:
+                c2.set_batch_split(split_level, split_frac)
             res = c2.run_batch(alloc, seed0 + 101 + k)      # host sums of every level
             est = sum(res[l][0].dp1 / res[l][0].n for l, m in enumerate(alloc) if m > 0)
             d2h_k = 8 * mlmc_dk.sums_len(nq) * len(alloc) + 4
@@ -482,7 +496,9 @@ def run_ours(args, wl, rank, world, local_rank):
                    "parallelism": f"{world} rank(s), disjoint sample ids per rank",
                    "kernel_variants": [{"n": i.n, "C": i.lane_cols, "R": i.lane_rows, "cluster": i.cluster}
                                        for i in info],
-                   "tune_s": tune_s},
+                   "tune_s": tune_s,
+                   "batch_split": {"level": split_level, "fraction": split_frac,
+                                   "streamed_samples": split_samples, "tune_s": split_s}},
         "cell_steps_per_s": world * cell_steps * args.steps / (total_ms * 1e-3),
         "gpu_launches": launches,
         "roofline": roofline,

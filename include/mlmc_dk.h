@@ -122,6 +122,10 @@ typedef struct {
     int32_t in_flight;      /* streamed path: samples advanced together (their state fits L2) */
     int32_t tile_rows;      /* streamed path: fine rows per CTA tile of the variant in use (tiles are
                                tile_rows x 64 fine cells); 0 for the register kernels */
+    int32_t split_capable;  /* 1: a register level (n >= 256, 8-SM clusters) whose batch samples can be
+                               shared with the streamed kernels (mlmc_dk_set_batch_split) */
+    double split_fraction;  /* share of this level's batch samples run on the streamed kernels */
+    int64_t batch_streamed; /* samples of the last multi-level batch that ran on the streamed kernels */
 } mlmc_dk_level_desc;
 
 /* Host-side moment sums of one quantity on one level (accumulated into). */
@@ -226,8 +230,28 @@ int mlmc_dk_run_batch_dev(mlmc_dk_ctx* ctx, const int64_t* counts, int64_t first
 
 /* Device time (ms) of each level's kernels in the last completed multi-level
  * batch, from CUDA events recorded on that level's stream inside the graph
- * (ms[0..L_max]; 0 for levels the batch skipped or never ran). */
+ * (ms[0..L_max]; 0 for levels the batch skipped or never ran).  On a split
+ * level this is the register kernels' share only. */
 int mlmc_dk_batch_level_ms(mlmc_dk_ctx* ctx, double* ms);
+
+/* Batch split.  The 8-SM thread-block clusters of the 256^2 (and larger
+ * register) levels cannot use every SM (152 SMs hold 15 such clusters), and
+ * once the coarser levels of a batch are done those SMs idle.  With
+ * `fraction` > 0 the multi-level batch runs the last floor(fraction *
+ * counts[level]) sample ids of `level` on the streamed-state kernels (same
+ * samples, same fixed-point paths) on the least urgent stream beside the
+ * graph, and adds their sums to the level's (entry 1 by max).  level in
+ * 1..L_max, fraction in [0, 1/2]; MLMC_DK_ERR_UNSUPPORTED unless
+ * level_info.split_capable (fraction 0 is always accepted). */
+int mlmc_dk_set_batch_split(mlmc_dk_ctx* ctx, int32_t level, double fraction);
+
+/* Autotuner of the batch split: on the finest split-capable level with
+ * counts[l] > 1, times the whole batch `counts` (sample ids from 0, results
+ * discarded; CUDA events on the context's stream, `repeats` timed runs after a
+ * warm-up per candidate) for fractions 0, 0.04, 0.08, 0.12, 0.16 and keeps the
+ * fastest (a larger share only when it is at least 1% faster).  *fraction and
+ * *seconds (optional) receive the choice and the tuning time. */
+int mlmc_dk_tune_batch(mlmc_dk_ctx* ctx, const int64_t* counts, int32_t repeats, double* fraction, double* seconds);
 
 /* Host form of the multi-level batch: ids start at the largest next_sample
  * over the levels (then next_sample = that + counts[l] on every level run);

@@ -618,6 +618,12 @@ __global__ void __launch_bounds__(256) reduce_kernel(const double* part, int n_s
     if (threadIdx.x == 0) out[e] = sh[0];
 }
 
+// out[e] += in[e] (entry 1, the max mass error: max): merges the sums of two
+// disjoint sample ranges of one level.
+__global__ void add_sums_kernel(double* out, const double* in, int stride) {
+    for (int e = threadIdx.x; e < stride; e += blockDim.x) out[e] = e == 1 ? fmax(out[e], in[e]) : out[e] + in[e];
+}
+
 // Normals of one fine step, written out (the level kernel keeps them in
 // registers); same device functions as the level kernel.
 __global__ void noise_kernel(int n, uint32_t m, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1,
@@ -828,6 +834,11 @@ cudaError_t launch_level(int n, bool coupled, int idx, const KArgs& a, int n_cta
 
 cudaError_t launch_reduce(const double* partials, int n_slots, int slot_stride, double* out, cudaStream_t st) {
     reduce_kernel<<<slot_stride, 256, 0, st>>>(partials, n_slots, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_add_sums(double* out, const double* in, int slot_stride, cudaStream_t st) {
+    add_sums_kernel<<<1, 256, 0, st>>>(out, in, slot_stride);
     return cudaGetLastError();
 }
 

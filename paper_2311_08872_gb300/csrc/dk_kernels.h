@@ -73,6 +73,8 @@ cudaError_t launch_level(int n, bool coupled, int idx, const KArgs& a, int n_cta
 // out[slot_stride]: entry 1 is a max, all others sums.
 cudaError_t launch_reduce(const double* partials, int n_slots, int slot_stride, double* out,
                           cudaStream_t stream);
+// out[e] += in[e] for the slot_stride entries of one level's sums (entry 1: max).
+cudaError_t launch_add_sums(double* out, const double* in, int slot_stride, cudaStream_t stream);
 
 // ---- streamed-state path (grids without a register-resident variant)
 struct SArgs {

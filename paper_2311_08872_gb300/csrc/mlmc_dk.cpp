@@ -39,6 +39,9 @@ struct LevelTab {
     int streamed = 0;                      // no register variant: state streamed through global memory
     int inflight = 0;                      // samples in flight on the streamed path (buffers sized for this)
     int inflight_v[8] = {0};               // ... per streamed tile variant
+    int split_ok = 0;                      // register level that can also run samples streamed (batch split)
+    double split_frac = 0.0;               // share of a batch's samples run on the streamed kernels
+    int64_t batch_streamed = 0;            // samples of the last batch run on the streamed kernels
     void* d_stream = nullptr;              // their state
     double* d_spart = nullptr;             // their per-slot partial sums [stride][S]
     int sel[2] = {0, 0};                   // variant in use for each mode
@@ -77,6 +80,11 @@ struct mlmc_dk_ctx {
     std::vector<cudaEvent_t> ev_join;
     std::vector<cudaEvent_t> ev_lb, ev_le;   // timing of each level inside the batch
     cudaGraphExec_t gexec = nullptr;
+    // batch split: samples of a cluster level run on the streamed kernels
+    // beside the graph, on the least urgent stream, on the SMs clusters leave
+    cudaStream_t sstream = nullptr;
+    cudaEvent_t ev_sfork = nullptr, ev_sjoin = nullptr;
+    double* d_ssums = nullptr;        // [L_max+1][stride] sums of the streamed share
     double* d_bsums = nullptr;        // device sums of mlmc_dk_run_batch
     double* h_bsums = nullptr;        // pinned host copy
     struct Surrogate* sur = nullptr;  // learned level below level 0 (mlmc_dk_surrogate_init)
@@ -232,11 +240,13 @@ int launch_batch(mlmc_dk_ctx* c, int level, int stream_tag, int64_t first, int64
 
 // Streamed level (state in global memory); `steps` > 0 truncates every sample
 // to that many fine steps (used only to time the tile variants).
+// `variant` >= 0 picks the fine-step tile (levels that normally run the
+// register kernels); otherwise the level's tuned streamed variant.
 int launch_streamed(mlmc_dk_ctx* c, int level, int stream_tag, int64_t first, int64_t count, uint64_t seed,
-                    double* sums_dev, double* samples_dev, cudaStream_t st, int steps = 0) {
+                    double* sums_dev, double* samples_dev, cudaStream_t st, int steps = 0, int variant = -1) {
     const bool coupled = (stream_tag == 0) && level > 0;
     LevelTab& t = c->lv[level];
-    const int variant = t.sel[coupled ? 1 : 0];
+    if (variant < 0) variant = t.sel[coupled ? 1 : 0];
     cudaError_t e;
     if (count == 0) {
         e = cudaMemsetAsync(sums_dev, 0, sizeof(double) * c->stride, st);
@@ -373,6 +383,10 @@ void release(mlmc_dk_ctx* c) {
     for (auto ev : c->ev_le) if (ev) cudaEventDestroy(ev);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->ev_sfork) cudaEventDestroy(c->ev_sfork);
+    if (c->ev_sjoin) cudaEventDestroy(c->ev_sjoin);
+    if (c->sstream) cudaStreamDestroy(c->sstream);
+    cudaFree(c->d_ssums);
     cudaFree(c->d_bsums);
     if (c->h_bsums) cudaFreeHost(c->h_bsums);
     free_surrogate(c->sur);
@@ -572,6 +586,17 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
                     partials_need = std::max(partials_need, (size_t)(vi.max_ctas / vi.cluster) * vi.slots_per_cta * c->stride);
             }
         }
+        if (!t.streamed && t.n >= 256 && t.n % 64 == 0) {
+            // register level with 8-SM clusters: streamed buffers for a batch split
+            t.inflight_v[0] = dk::stream_inflight(t.n, (size_t)96 << 20, 0);
+            t.inflight = t.inflight_v[0];
+            if ((e = cudaMalloc(&t.d_stream, dk::stream_bytes(t.n, t.inflight))) != cudaSuccess ||
+                (e = cudaMalloc(&t.d_spart, sizeof(double) * c->stride * t.inflight)) != cudaSuccess) {
+                mlmc_dk_free(c);
+                return cuda_fail(nullptr, e, "batch split buffers");
+            }
+            t.split_ok = 1;
+        }
     }
     if ((e = cudaMalloc(&c->d_partials, sizeof(double) * std::max<size_t>(partials_need, 1))) != cudaSuccess ||
         (e = cudaMalloc(&c->d_sums, sizeof(double) * c->stride)) != cudaSuccess ||
@@ -614,6 +639,10 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
     }
     if ((e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaStreamCreateWithPriority(&c->sstream, cudaStreamNonBlocking, prio_lo)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&c->ev_sfork, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&c->ev_sjoin, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_ssums, sizeof(double) * c->stride * nl)) != cudaSuccess ||
         (e = cudaMalloc(&c->d_bsums, sizeof(double) * c->stride * nl)) != cudaSuccess ||
         (e = cudaMallocHost(&c->h_bsums, sizeof(double) * c->stride * nl)) != cudaSuccess) {
         mlmc_dk_free(c);
@@ -658,6 +687,9 @@ int mlmc_dk_level_info(const mlmc_dk_ctx* ctx, int32_t level, mlmc_dk_level_desc
     out->streamed = t.streamed;
     out->in_flight = t.streamed ? t.inflight_v[t.sel[level > 0 ? 1 : 0]] : 0;
     out->tile_rows = vs.tile_rows;
+    out->split_capable = t.split_ok;
+    out->split_fraction = t.split_frac;
+    out->batch_streamed = t.batch_streamed;
     return MLMC_DK_OK;
 }
 
@@ -737,6 +769,19 @@ int mlmc_dk_run_batch_dev(mlmc_dk_ctx* ctx, const int64_t* counts, int64_t first
         if (counts[l] < 0) return fail(ctx, MLMC_DK_ERR_INVALID, "run_batch_dev: negative count");
     cudaStream_t st = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : ctx->stream;
     cudaError_t e;
+    // split: the last n_split[l] ids of a split level run streamed beside the graph
+    std::vector<int64_t> n_split(nl, 0), n_reg(counts, counts + nl);
+    bool any_split = false;
+    for (int l = 0; l < nl; ++l) {
+        LevelTab& t = ctx->lv[l];
+        t.batch_streamed = 0;
+        if (t.split_ok && t.split_frac > 0 && l > 0 && counts[l] > 1) {
+            n_split[l] = std::min<int64_t>(counts[l] - 1, (int64_t)std::floor(t.split_frac * (double)counts[l]));
+            n_reg[l] = counts[l] - n_split[l];
+            t.batch_streamed = n_split[l];
+            any_split = any_split || n_split[l] > 0;
+        }
+    }
     if ((e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
         return cuda_fail(ctx, e, "cudaStreamBeginCapture");
     int rc = MLMC_DK_OK;
@@ -749,7 +794,7 @@ int mlmc_dk_run_batch_dev(mlmc_dk_ctx* ctx, const int64_t* counts, int64_t first
         // external records become event-record nodes of the graph (timing)
         if ((e = cudaEventRecordWithFlags(ctx->ev_lb[l], ctx->lstream[l], cudaEventRecordExternal)) != cudaSuccess)
             break;
-        rc = launch_batch_into(ctx, l, 0, first_sample, counts[l], seed, out, nullptr, ctx->lstream[l],
+        rc = launch_batch_into(ctx, l, 0, first_sample, n_reg[l], seed, out, nullptr, ctx->lstream[l],
                                ctx->d_lpart[l], ctx->lpart_cap[l], ctx->lprio[l]);
         if (rc != MLMC_DK_OK) break;
         if ((e = cudaEventRecordWithFlags(ctx->ev_le[l], ctx->lstream[l], cudaEventRecordExternal)) != cudaSuccess)
@@ -784,7 +829,28 @@ int mlmc_dk_run_batch_dev(mlmc_dk_ctx* ctx, const int64_t* counts, int64_t first
         return cuda_fail(ctx, e, "cudaGraphInstantiate");
     }
     cudaGraphDestroy(graph);
+    if (any_split) {
+        if ((e = cudaEventRecord(ctx->ev_sfork, st)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(ctx->sstream, ctx->ev_sfork, 0)) != cudaSuccess)
+            return cuda_fail(ctx, e, "batch split fork");
+    }
     if ((e = cudaGraphLaunch(ctx->gexec, st)) != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphLaunch");
+    if (any_split) {
+        for (int l = nl - 1; l >= 0; --l) {
+            if (n_split[l] == 0) continue;
+            rc = launch_streamed(ctx, l, 0, first_sample + n_reg[l], n_split[l], seed,
+                                 ctx->d_ssums + (size_t)l * ctx->stride, nullptr, ctx->sstream, 0, 0);
+            if (rc != MLMC_DK_OK) return rc;
+        }
+        if ((e = cudaEventRecord(ctx->ev_sjoin, ctx->sstream)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(st, ctx->ev_sjoin, 0)) != cudaSuccess)
+            return cuda_fail(ctx, e, "batch split join");
+        for (int l = 0; l < nl; ++l)
+            if (n_split[l] > 0 && (e = dk::launch_add_sums(sums_dev + (size_t)l * ctx->stride,
+                                                             ctx->d_ssums + (size_t)l * ctx->stride, ctx->stride,
+                                                             st)) != cudaSuccess)
+                return cuda_fail(ctx, e, "batch split merge");
+    }
     for (int l = nl - 1; l >= 0; --l) {
         if (!ctx->lv[l].streamed) continue;
         if ((e = cudaEventRecord(ctx->ev_lb[l], st)) != cudaSuccess) return cuda_fail(ctx, e, "cudaEventRecord");
@@ -792,6 +858,56 @@ int mlmc_dk_run_batch_dev(mlmc_dk_ctx* ctx, const int64_t* counts, int64_t first
         if (rc != MLMC_DK_OK) return rc;
         if ((e = cudaEventRecord(ctx->ev_le[l], st)) != cudaSuccess) return cuda_fail(ctx, e, "cudaEventRecord");
     }
+    return MLMC_DK_OK;
+}
+
+int mlmc_dk_set_batch_split(mlmc_dk_ctx* ctx, int32_t level, double fraction) {
+    if (!ctx || level < 1 || level > ctx->L_max || !(fraction >= 0.0 && fraction <= 0.5))
+        return fail(ctx, MLMC_DK_ERR_INVALID, "set_batch_split: level 1..L_max, fraction in [0, 1/2]");
+    LevelTab& t = ctx->lv[level];
+    if (fraction > 0 && !t.split_ok)
+        return fail(ctx, MLMC_DK_ERR_UNSUPPORTED, "set_batch_split: the level has no streamed share");
+    t.split_frac = fraction;
+    return MLMC_DK_OK;
+}
+
+int mlmc_dk_tune_batch(mlmc_dk_ctx* ctx, const int64_t* counts, int32_t repeats, double* fraction, double* seconds) {
+    if (!ctx || !counts) return fail(ctx, MLMC_DK_ERR_INVALID, "tune_batch: bad arguments");
+    const auto t0 = std::chrono::steady_clock::now();
+    repeats = std::max(1, repeats);
+    int lvl = -1;
+    for (int l = ctx->L_max; l >= 1 && lvl < 0; --l)
+        if (ctx->lv[l].split_ok && counts[l] > 1) lvl = l;
+    double best_f = 0.0;
+    if (lvl >= 0) {
+        static const double kFractions[] = {0.0, 0.04, 0.08, 0.12, 0.16};
+        double best_ms = 1e300;
+        cudaError_t e;
+        for (double f : kFractions) {
+            ctx->lv[lvl].split_frac = f;
+            double ms_min = 1e300;
+            for (int r = 0; r < repeats + 1; ++r) {
+                if ((e = cudaEventRecord(ctx->ev0, ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "tune_batch");
+                int rc = mlmc_dk_run_batch_dev(ctx, counts, 0, 0x7475, ctx->d_bsums, ctx->stream);
+                if (rc != MLMC_DK_OK) return rc;
+                if ((e = cudaEventRecord(ctx->ev1, ctx->stream)) != cudaSuccess ||
+                    (e = cudaEventSynchronize(ctx->ev1)) != cudaSuccess)
+                    return cuda_fail(ctx, e, "tune_batch");
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+                if (r > 0 || repeats == 0) ms_min = std::min(ms_min, (double)ms);   // the first run warms up
+            }
+            if (ms_min < 0.99 * best_ms) {   // a larger share only if clearly faster
+                best_ms = ms_min;
+                best_f = f;
+            }
+        }
+        ctx->lv[lvl].split_frac = best_f;
+    }
+    int rc = check_device_error(ctx);
+    if (rc != MLMC_DK_OK) return rc;
+    if (fraction) *fraction = best_f;
+    if (seconds) *seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return MLMC_DK_OK;
 }
 

@@ -56,6 +56,7 @@ class LevelDesc(ctypes.Structure):
         ("n_variants", ctypes.c_int32), ("variant_single", ctypes.c_int32), ("variant_coupled", ctypes.c_int32),
         ("lane_cols", ctypes.c_int32), ("lane_rows", ctypes.c_int32), ("cluster", ctypes.c_int32),
         ("streamed", ctypes.c_int32), ("in_flight", ctypes.c_int32), ("tile_rows", ctypes.c_int32),
+        ("split_capable", ctypes.c_int32), ("split_fraction", ctypes.c_double), ("batch_streamed", ctypes.c_int64),
     ]
 
 
@@ -271,6 +272,18 @@ class Context:
         ms = (ctypes.c_double * (self.L_max + 1))()
         _check(lib().mlmc_dk_batch_level_ms(self._ctx, ms), self._ctx)
         return list(ms)
+
+    def set_batch_split(self, level: int, fraction: float):
+        """Share of `level`'s batch samples run on the streamed kernels beside the graph."""
+        _check(lib().mlmc_dk_set_batch_split(self._ctx, level, ctypes.c_double(fraction)), self._ctx)
+
+    def tune_batch(self, counts, repeats: int = 1):
+        """Time the batch `counts` for a few split fractions and keep the fastest;
+        returns (fraction, seconds spent)."""
+        c = (ctypes.c_int64 * (self.L_max + 1))(*[int(x) for x in counts])
+        f, t = ctypes.c_double(0.0), ctypes.c_double(0.0)
+        _check(lib().mlmc_dk_tune_batch(self._ctx, c, repeats, ctypes.byref(f), ctypes.byref(t)), self._ctx)
+        return f.value, t.value
 
     def run_batch(self, counts, seed: int):
         """Host form: returns sums[level][quantity]."""
