@@ -119,7 +119,8 @@ typedef struct {
     int32_t variant_single, variant_coupled;  /* variants in use for the fine-only and the coupled kernel */
     int32_t lane_cols, lane_rows, cluster;    /* the level's main kernel: C x R coarse cells per lane, cluster */
     int32_t streamed;       /* 1: grid too large for registers; state streamed through global memory */
-    int32_t in_flight;      /* streamed path: samples advanced together (their state fits L2) */
+    int32_t in_flight;      /* streamed path: samples advanced together (their state fits L2); on a
+                               split-capable level, those of its streamed share */
     int32_t tile_rows;      /* streamed path: fine rows per CTA tile of the variant in use (tiles are
                                tile_rows x 64 fine cells); 0 for the register kernels */
     int32_t split_capable;  /* 1: a register level (n >= 256, 8-SM clusters) whose batch samples can be

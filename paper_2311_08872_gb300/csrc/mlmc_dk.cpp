@@ -685,7 +685,7 @@ int mlmc_dk_level_info(const mlmc_dk_ctx* ctx, int32_t level, mlmc_dk_level_desc
     out->lane_rows = vs.R;
     out->cluster = vs.cluster;
     out->streamed = t.streamed;
-    out->in_flight = t.streamed ? t.inflight_v[t.sel[level > 0 ? 1 : 0]] : 0;
+    out->in_flight = t.streamed ? t.inflight_v[t.sel[level > 0 ? 1 : 0]] : (t.split_ok ? t.inflight_v[0] : 0);
     out->tile_rows = vs.tile_rows;
     out->split_capable = t.split_ok;
     out->split_fraction = t.split_frac;
