@@ -131,6 +131,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-streamed", action="store_true", help="skip the streamed-state stencil timing")
+    ap.add_argument("--split-fraction", type=float, default=None,
+                    help="fixed batch split of the finest cluster level (default: autotuned)")
     ap.add_argument("--no-adaptive", action="store_true", help="skip the Algorithm 1 / plain MC timing")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned level below 0")
@@ -298,8 +300,13 @@ def run_ours(args, wl, rank, world, local_rank):
     sample_steps, cell_steps = batch_units(wl, alloc)
     # batch split: share of the 256^2 level's samples on the streamed kernels, on the
     # SMs its 8-SM clusters leave free (tuned on the batch at a quarter of its size)
-    split_frac, split_s = ctx.tune_batch([(a + 3) // 4 for a in alloc], 1)
     split_level = max((l for l in range(len(alloc)) if ctx.level_info(l).split_capable), default=None)
+    if args.split_fraction is None:
+        split_frac, split_s = ctx.tune_batch([(a + 3) // 4 for a in alloc], 1)
+    else:
+        split_frac, split_s = args.split_fraction, 0.0
+        if split_level is not None:
+            ctx.set_batch_split(split_level, split_frac)
 
     nq = ctx.n_quant
     sums = torch.zeros(wl.L_max + 1, mlmc_dk.sums_len(nq), dtype=torch.float64, device=dev)
