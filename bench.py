@@ -48,12 +48,13 @@ SMS = 152
 SM_MAX_MHZ = 2070.0
 # DRAM bytes of one full-size launch of the dominant kernel (read + write; the
 # state never leaves registers, so this is the initial-state, mean-field and
-# observable tables), from the ncu launch list of
-#   python bench.py --steps 2 --warmup 3 --no-cpu-baseline --no-surrogate
-# (mean of its 7 launches of 955 samples).  Reported only while the kernel
+# observable tables), from the one-pass ncu capture of the level kernels of
+#   python bench.py --steps 1 --warmup 3 --no-cpu-baseline --no-surrogate --no-adaptive
+#       --no-e2e --no-streamed --split-fraction 0.08
+# (mean of its 4 launches of 879 samples).  Reported only while the kernel
 # sources hash to the value recorded with the capture.
 LEVEL_KERNEL_TRAFFIC = {"kernel": "level_kernel n=256 C=4 R=2 cluster=8 coupled=True",
-                        "bytes_per_launch": 2.126e6, "sources_sha256_16": "2b6964eac8425ad6"}
+                        "bytes_per_launch": 2.176e6, "sources_sha256_16": "ba5b7f6722ac88bd"}
 KERNEL_SOURCES = ("dk_kernels.cu", "dk_device.cuh", "dk_kernels.h")
 
 
