@@ -55,6 +55,11 @@ SM_MAX_MHZ = 2070.0
 # sources hash to the value recorded with the capture.
 LEVEL_KERNEL_TRAFFIC = {"kernel": "level_kernel n=256 C=4 R=2 cluster=8 coupled=True",
                         "bytes_per_launch": 2.176e6, "sources_sha256_16": "ba5b7f6722ac88bd"}
+# Thread instructions per fine cell-step of the dominant kernel, from the ncu
+# --set full capture of the 256^2 coupled level kernel (smsp__inst_executed x
+# 32 / fine cell-steps); valid under the same source hash.  The kernel is
+# bound by instruction issue (4 warp instructions per clock per SM).
+LEVEL_KERNEL_INSTR_PER_CELL_STEP = 59.0
 KERNEL_SOURCES = ("dk_kernels.cu", "dk_device.cuh", "dk_kernels.h")
 
 
@@ -381,12 +386,20 @@ def run_ours(args, wl, rank, world, local_rank):
     traffic = None
     if kname == LEVEL_KERNEL_TRAFFIC["kernel"] and kernel_sources_hash() == LEVEL_KERNEL_TRAFFIC["sources_sha256_16"]:
         traffic = LEVEL_KERNEL_TRAFFIC["bytes_per_launch"]
+    issue = None
+    if traffic is not None:   # same sources as the capture that counted the instructions
+        warp_inst = reg_dom * fine[dom] * LEVEL_KERNEL_INSTR_PER_CELL_STEP / 32.0 * args.steps / (level_ms[dom] * 1e-3)
+        issue = {"instructions_per_fine_cell_step": LEVEL_KERNEL_INSTR_PER_CELL_STEP,
+                 "achieved_warp_inst_per_s": warp_inst, "peak_all_sms": 4 * SMS * SM_MAX_MHZ * 1e6,
+                 "frac_all_sms": warp_inst / (4 * SMS * SM_MAX_MHZ * 1e6),
+                 "note": "instruction-issue roofline: the binding limit; the clusters of 8 hold 120 of 152 SMs"}
     roofline = {"bound": "alu", "pipe": "XU (MUFU)",
                 "kernel": kname,
                 "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gop/s", "frac": achieved / peak,
                 "traffic": traffic, "traffic_unit": "DRAM bytes per launch (ncu, one launch per step)",
                 "ops_per_fine_cell_step": XU_OPS_FINE,
                 "samples_per_launch": reg_dom,
+                "issue": issue,
                 "cell_steps_per_s": reg_dom * (fine[dom] + coarse[dom]) * args.steps / (level_ms[dom] * 1e-3),
                 "level_ms_per_step": [x / args.steps for x in level_ms],
                 "note": "levels run concurrently in one CUDA graph; each level's time is its own stream's span"}
