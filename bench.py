@@ -99,7 +99,7 @@ def closed_form_EP_cos1(n, tau, M):
 def streamed_stencil(stream):
     """One wave of samples in flight of the 512^2 level of the low-density
     workload on the streamed-state kernels (CUDA events on the launching
-    stream; tile variant picked by the autotuner)."""
+    stream; fine-step variant picked by the autotuner)."""
     import torch
     from paper_2311_08872_gb300 import mlmc_dk, workloads
     wl = workloads.get("lowdens32_512")

@@ -302,7 +302,8 @@ int mlmc_dk_estimate(mlmc_dk_ctx* ctx, double eps, int32_t relative, uint64_t se
  * All variants compute the same fixed-point paths bit for bit (hence equal
  * masses); the observables differ only by the order of their FP32 partial
  * sums.  Variants differ in how many cells a lane owns and how many SMs share
- * a sample; on streamed levels, in the fine-step tile (tile_rows x 64 cells). */
+ * a sample; on streamed levels, in the resident CTAs per SM of the fine-step
+ * kernel (4, or 5 with at most 48 registers per thread). */
 int mlmc_dk_set_variant(mlmc_dk_ctx* ctx, int32_t level, int32_t coupled, int32_t variant);
 
 /* Autotuner: for every level and kernel with more than one variant, time each

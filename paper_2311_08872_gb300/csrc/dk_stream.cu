@@ -17,9 +17,10 @@
 // coarse transfers from qc and zt (tile and halo) and updates qc.  Kernel
 // boundaries order all reads and writes: no kernel waits on another.
 //
-// Fine-step CTAs: 16 x FR/2 threads on an FR x 64 tile (FR = 32 or 64, picked
-// by the autotuner), each thread a 2 x 4 block of fine cells (two coarse
-// cells).  The coarse step and the observables use 32 x 32 tiles.
+// Fine-step CTAs: 16 x 16 threads on a 32 x 64 tile, each thread a 2 x 4 block
+// of fine cells (two coarse cells); two variants, 4 or 5 resident CTAs per SM
+// (the second capped at 48 registers per thread), picked by the autotuner.
+// The coarse step and the observables use 32 x 32 tiles.
 #include <cstdint>
 
 #include "dk_device.cuh"
@@ -32,14 +33,15 @@ namespace {
 constexpr int kTile = 32;            // fine cells per tile side
 constexpr int kTc = kTile / 2;       // coarse cells per tile side (= threads per side)
 constexpr int kThreads = kTc * kTc;  // 256
-// fine-step tiles: FR x kFC fine cells (FR = 32 or 64, the two tile variants)
-// with a one-cell halo in shared memory, row lr = r - R0 + 1 (0 .. FR+1),
-// column lc = c - C0 + 4 (3 .. kFC+4), so that each thread's own four cells
-// sit on a 16-byte boundary
+// fine-step tiles: FR x kFC fine cells with a one-cell halo in shared memory,
+// row lr = r - R0 + 1 (0 .. FR+1), column lc = c - C0 + 4 (3 .. kFC+4), so
+// that each thread's own four cells sit on a 16-byte boundary
 constexpr int kFC = 64;
 constexpr int kFW = kFC + 8;
+constexpr int kFR = 32;
 constexpr int kStreamVariants = 2;
-__host__ __device__ constexpr int fine_rows(int variant) { return variant == 0 ? 32 : 64; }
+// minimum resident CTAs per SM the compiler is asked for, per variant
+__host__ __device__ constexpr int fine_min_blocks(int variant) { return variant == 0 ? 1 : 5; }
 __host__ __device__ constexpr int fine_threads(int fr) { return 8 * fr; }
 __host__ __device__ constexpr int fine_smem(int fr) { return 3 * (fr + 2) * kFW * (int)sizeof(int32_t); }
 
@@ -93,8 +95,8 @@ __global__ void __launch_bounds__(kThreads) stream_init_kernel(const SArgs a) {
 // Fine step m: noise of step m on the tile and its halo, then q^{m+1}.
 // CTA: 16 x FR/2 threads on an FR x 64 tile; thread (tx, ty) owns the 2 x 4
 // fine block at (R0 + 2 ty, C0 + 4 tx) = 2 coarse cells.
-template <int FR>
-__global__ void __launch_bounds__(fine_threads(FR)) stream_fine_kernel(const SArgs a, int m) {
+template <int FR, int MINB>
+__global__ void __launch_bounds__(fine_threads(FR), MINB) stream_fine_kernel(const SArgs a, int m) {
     constexpr int kHaloPairs = 64 + 2 * FR;   // 2 x 32 pairs in the halo rows, one per row in the halo columns
     const int s = blockIdx.z;
     if (s >= a.count) return;
@@ -351,24 +353,25 @@ size_t stream_bytes(int n, int S) {
 
 int stream_variant_count() { return kStreamVariants; }
 
-template <int FR>
+template <int MINB>
 static cudaError_t fine_attr() {
-    return cudaFuncSetAttribute(stream_fine_kernel<FR>, cudaFuncAttributeMaxDynamicSharedMemorySize, fine_smem(FR));
+    return cudaFuncSetAttribute(stream_fine_kernel<kFR, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                fine_smem(kFR));
 }
 
 cudaError_t stream_variant_info(int n, int variant, VariantInfo* out) {
     if (variant < 0 || variant >= kStreamVariants) return cudaErrorInvalidValue;
-    const int fr = fine_rows(variant);
-    cudaError_t e = variant == 0 ? fine_attr<32>() : fine_attr<64>();
+    const int fr = kFR;
+    cudaError_t e = variant == 0 ? fine_attr<1>() : fine_attr<5>();
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
         (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
         return e;
-    e = variant == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stream_fine_kernel<32>, fine_threads(32),
-                                                                     fine_smem(32))
-                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stream_fine_kernel<64>, fine_threads(64),
-                                                                     fine_smem(64));
+    e = variant == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stream_fine_kernel<kFR, 1>,
+                                                                     fine_threads(kFR), fine_smem(kFR))
+                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stream_fine_kernel<kFR, 5>,
+                                                                     fine_threads(kFR), fine_smem(kFR));
     if (e != cudaSuccess) return e;
     *out = VariantInfo{};
     out->supported = (n % kFC == 0 && n % fr == 0 && per_sm > 0) ? 1 : 0;
@@ -419,11 +422,11 @@ cudaError_t stream_run(const KArgs& k, SArgs a, int S, int variant, cudaStream_t
     // waves of S samples, accumulate per slot, then the caller reduces.
     const int n = a.n;
     if (variant < 0 || variant >= kStreamVariants) return cudaErrorInvalidValue;
-    const int fr = fine_rows(variant);
+    const int fr = kFR;
     if (n % kFC != 0 || n % fr != 0 || (a.coupled && (a.nc % kTile != 0 || a.M % 4 != 0))) return cudaErrorInvalidValue;
     const int tiles = (n / kTile) * (n / kTile);
     const int ctiles = a.coupled ? (a.nc / kTile) * (a.nc / kTile) : 0;
-    cudaError_t e = variant == 0 ? fine_attr<32>() : fine_attr<64>();
+    cudaError_t e = variant == 0 ? fine_attr<1>() : fine_attr<5>();
     if (e != cudaSuccess) return e;
     zero_kernel<<<64, 256, 0, st>>>(k.partials, (size_t)k.slot_stride * S);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -434,9 +437,9 @@ cudaError_t stream_run(const KArgs& k, SArgs a, int S, int variant, cudaStream_t
         stream_init_kernel<<<grid, kThreads, 0, st>>>(a);
         for (int m = 0; m < a.M; ++m) {
             if (variant == 0)
-                stream_fine_kernel<32><<<fgrid, fine_threads(32), fine_smem(32), st>>>(a, m);
+                stream_fine_kernel<kFR, 1><<<fgrid, fine_threads(kFR), fine_smem(kFR), st>>>(a, m);
             else
-                stream_fine_kernel<64><<<fgrid, fine_threads(64), fine_smem(64), st>>>(a, m);
+                stream_fine_kernel<kFR, 5><<<fgrid, fine_threads(kFR), fine_smem(kFR), st>>>(a, m);
             if (a.coupled && (m & 3) == 3) stream_coarse_kernel<<<cgrid, kThreads, 0, st>>>(a, m >> 2);
         }
         stream_observe_kernel<<<grid, kThreads, 0, st>>>(a);
