@@ -18,8 +18,8 @@
 // boundaries order all reads and writes: no kernel waits on another.
 //
 // Fine-step CTAs: 16 x 16 threads on a 32 x 64 tile, each thread a 2 x 4 block
-// of fine cells (two coarse cells); two variants, 4 or 5 resident CTAs per SM
-// (the second capped at 48 registers per thread), picked by the autotuner.
+// of fine cells (two coarse cells); two builds, for 4 or 5 resident CTAs per
+// SM (at most 64 or 48 registers per thread), picked by the autotuner.
 // The coarse step and the observables use 32 x 32 tiles.
 #include <cstdint>
 
@@ -41,7 +41,7 @@ constexpr int kFW = kFC + 8;
 constexpr int kFR = 32;
 constexpr int kStreamVariants = 2;
 // minimum resident CTAs per SM the compiler is asked for, per variant
-__host__ __device__ constexpr int fine_min_blocks(int variant) { return variant == 0 ? 1 : 5; }
+__host__ __device__ constexpr int fine_min_blocks(int variant) { return variant == 0 ? 4 : 5; }
 __host__ __device__ constexpr int fine_threads(int fr) { return 8 * fr; }
 __host__ __device__ constexpr int fine_smem(int fr) { return 3 * (fr + 2) * kFW * (int)sizeof(int32_t); }
 
@@ -362,13 +362,13 @@ static cudaError_t fine_attr() {
 cudaError_t stream_variant_info(int n, int variant, VariantInfo* out) {
     if (variant < 0 || variant >= kStreamVariants) return cudaErrorInvalidValue;
     const int fr = kFR;
-    cudaError_t e = variant == 0 ? fine_attr<1>() : fine_attr<5>();
+    cudaError_t e = variant == 0 ? fine_attr<4>() : fine_attr<5>();
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
         (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
         return e;
-    e = variant == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stream_fine_kernel<kFR, 1>,
+    e = variant == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stream_fine_kernel<kFR, 4>,
                                                                      fine_threads(kFR), fine_smem(kFR))
                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stream_fine_kernel<kFR, 5>,
                                                                      fine_threads(kFR), fine_smem(kFR));
@@ -426,7 +426,7 @@ cudaError_t stream_run(const KArgs& k, SArgs a, int S, int variant, cudaStream_t
     if (n % kFC != 0 || n % fr != 0 || (a.coupled && (a.nc % kTile != 0 || a.M % 4 != 0))) return cudaErrorInvalidValue;
     const int tiles = (n / kTile) * (n / kTile);
     const int ctiles = a.coupled ? (a.nc / kTile) * (a.nc / kTile) : 0;
-    cudaError_t e = variant == 0 ? fine_attr<1>() : fine_attr<5>();
+    cudaError_t e = variant == 0 ? fine_attr<4>() : fine_attr<5>();
     if (e != cudaSuccess) return e;
     zero_kernel<<<64, 256, 0, st>>>(k.partials, (size_t)k.slot_stride * S);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -437,7 +437,7 @@ cudaError_t stream_run(const KArgs& k, SArgs a, int S, int variant, cudaStream_t
         stream_init_kernel<<<grid, kThreads, 0, st>>>(a);
         for (int m = 0; m < a.M; ++m) {
             if (variant == 0)
-                stream_fine_kernel<kFR, 1><<<fgrid, fine_threads(kFR), fine_smem(kFR), st>>>(a, m);
+                stream_fine_kernel<kFR, 4><<<fgrid, fine_threads(kFR), fine_smem(kFR), st>>>(a, m);
             else
                 stream_fine_kernel<kFR, 5><<<fgrid, fine_threads(kFR), fine_smem(kFR), st>>>(a, m);
             if (a.coupled && (m & 3) == 3) stream_coarse_kernel<<<cgrid, kThreads, 0, st>>>(a, m >> 2);
