@@ -11,8 +11,9 @@ TEST INFRASTRUCTURE ONLY (same rules as the rest of ``oracle/``).
   the noise), with g_j the per-step factor of the noise-free scheme on mode j
   (the discrete heat symbol of Section 7.2's operators).  With i.i.d. N(0,1)
   normals and orthonormal modes they are independent N(0, sum_i g_j^(2i)).
-* ``mlp_*``: a plain FP64 4-layer ReLU perceptron 64-256-256-256-1 (forward,
-  backward, mean-squared-error loss) for checking the GPU kernels.
+* ``mlp_*``: a plain FP64 4-layer ReLU perceptron 64-256-256-256-K, one
+  output per test function (forward, backward, squared-error loss summed over
+  the outputs) for checking the GPU kernels.
 """
 from __future__ import annotations
 
@@ -77,15 +78,22 @@ def features(Zs: List[np.ndarray], E: np.ndarray, g: np.ndarray) -> np.ndarray:
 LAYERS = (64, 256, 256, 256, 1)
 
 
-def mlp_param_count() -> int:
-    return sum(LAYERS[i] * LAYERS[i + 1] + LAYERS[i + 1] for i in range(len(LAYERS) - 1))
+def layers(outputs: int = 1):
+    """Widths of the 4-layer perceptron with `outputs` outputs (one per test function)."""
+    return LAYERS[:-1] + (outputs,)
 
 
-def mlp_unpack(theta: np.ndarray):
+def mlp_param_count(outputs: int = 1) -> int:
+    w = layers(outputs)
+    return sum(w[i] * w[i + 1] + w[i + 1] for i in range(len(w) - 1))
+
+
+def mlp_unpack(theta: np.ndarray, outputs: int = 1):
     """Flat parameter vector -> [(W [out, in], b [out])], layer by layer (W then b)."""
+    w = layers(outputs)
     out, off = [], 0
-    for i in range(len(LAYERS) - 1):
-        a, b = LAYERS[i], LAYERS[i + 1]
+    for i in range(len(w) - 1):
+        a, b = w[i], w[i + 1]
         W = theta[off: off + a * b].reshape(b, a)
         off += a * b
         bias = theta[off: off + b]
@@ -94,27 +102,33 @@ def mlp_unpack(theta: np.ndarray):
     return out
 
 
-def mlp_forward(theta: np.ndarray, X: np.ndarray):
+def mlp_forward(theta: np.ndarray, X: np.ndarray, outputs: int = 1):
+    """Outputs y of shape (B,) for one output, (B, outputs) otherwise, and the activations."""
     acts = [X]
     h = X
-    layers = mlp_unpack(theta)
-    for i, (W, b) in enumerate(layers):
+    ls = mlp_unpack(theta, outputs)
+    for i, (W, b) in enumerate(ls):
         z = h @ W.T + b
-        h = np.maximum(z, 0.0) if i < len(layers) - 1 else z
+        h = np.maximum(z, 0.0) if i < len(ls) - 1 else z
         acts.append(h)
-    return h[:, 0], acts
+    return (h[:, 0] if outputs == 1 else h), acts
 
 
 def mlp_loss_grad(theta: np.ndarray, X: np.ndarray, T: np.ndarray):
-    """Mean squared error and its gradient (flat, same layout as theta)."""
-    y, acts = mlp_forward(theta, X)
+    """Squared error summed over the outputs, averaged over the batch (the mean
+    squared error for one output), and its gradient (flat, layout of theta).
+    T: (B,) for one output, (B, outputs) otherwise."""
+    T2 = T[:, None] if T.ndim == 1 else T
+    outputs = T2.shape[1]
+    y, acts = mlp_forward(theta, X, outputs)
+    y2 = y[:, None] if outputs == 1 else y
     B = X.shape[0]
-    loss = float(np.mean((y - T) ** 2))
-    d = (2.0 / B) * (y - T)[:, None]
-    layers = mlp_unpack(theta)
+    loss = float(np.sum((y2 - T2) ** 2) / B)
+    d = (2.0 / B) * (y2 - T2)
+    ls = mlp_unpack(theta, outputs)
     grads = []
-    for i in range(len(layers) - 1, -1, -1):
-        W, b = layers[i]
+    for i in range(len(ls) - 1, -1, -1):
+        W, b = ls[i]
         h_in = acts[i]
         gW = d.T @ h_in
         gb = d.sum(axis=0)

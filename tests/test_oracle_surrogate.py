@@ -48,13 +48,14 @@ def test_features_have_the_exact_gaussian_law():
     assert abs(flat.var() - 1.0) < 5 * math.sqrt(2.0 / flat.size)
 
 
-def test_mlp_gradient_matches_finite_differences():
+@pytest.mark.parametrize("outputs", [1, 4])
+def test_mlp_gradient_matches_finite_differences(outputs):
     rng = np.random.default_rng(0)
-    P = sg.mlp_param_count()
-    assert P == 148481
+    P = sg.mlp_param_count(outputs)
+    assert P == 148224 + 257 * outputs     # 64*256+256 + 2*(256*256+256) + (256+1)*K
     theta = rng.normal(0, 0.08, size=P)
     X = rng.normal(size=(16, 64))
-    T = rng.normal(size=16)
+    T = rng.normal(size=16) if outputs == 1 else rng.normal(size=(16, outputs))
     loss, grad = sg.mlp_loss_grad(theta, X, T)
     idx = rng.choice(P, size=60, replace=False)
     for i in idx:
