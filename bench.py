@@ -450,8 +450,8 @@ def run_ours(args, wl, rank, world, local_rank):
         torch.cuda.synchronize()
         train_s = time.perf_counter() - t
         n_s = 200000
-        s_sur = ctx.run_surrogate(-1, n_s, seed0 + 5)
-        s_cor = ctx.run_surrogate(0, n_s, seed0 + 6)
+        s_sur = ctx.run_surrogate(-1, n_s, seed0 + 5)[0]
+        s_cor = ctx.run_surrogate(0, n_s, seed0 + 6)[0]
         var = lambda q: max(0.0, (q.dp2 - q.dp1 ** 2 / q.n) / (q.n - 1))
         t_l = [c / rate for c in C]        # seconds per sample of levels 0..L at the batch's rate
         terms = [math.sqrt(var(s_sur) * s_sur.kernel_s / n_s), math.sqrt(var(s_cor) * s_cor.kernel_s / n_s)]

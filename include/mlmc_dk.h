@@ -319,41 +319,48 @@ int mlmc_dk_tune(mlmc_dk_ctx* ctx, int32_t repeats, double* seconds);
  * |k|^2), weighted by the noise-free scheme's per-step factor g_j on each mode
  * carried to T: F_(j,r) = sum_m g_j^(M-1-m) <Z^m_(.,r), e_j>, standardised by
  * their exact standard deviation (they are i.i.d. N(0, sum_i g_j^(2i))).  A
- * 64-256-256-256-1 ReLU perceptron (BF16 tensor-core GEMMs, FP32
- * accumulation and master weights) maps them to That ~ sqrt(N) (Y_0 - Ybar_0);
- * S = That^2 stands in for P_0.  The estimate telescopes
+ * 64-256-256-256-K ReLU perceptron (K = n_obs outputs; BF16 tensor-core
+ * GEMMs, FP32 accumulation and master weights) maps them to
+ * That_k ~ sqrt(N) (Y_0k - Ybar_0k); S_jl = That_j That_l stands in for the
+ * quantity P_0,jl (j = l without `products`).  The estimate telescopes
  *     E[P_L] = E[S] + E[P_0 - S] + sum_{l>=1} E[P_l - P_{l-1}],
  * where the level below 0 draws its standardised features directly as
  * standard normals (stream 2, level tag 0) and the correction level evaluates
  * S on the features of the very noise that drives its level-0 path; the sum is
- * unbiased for any network.  Requires one observable without products and a
- * level-0 grid of 8^2..32^2.  Parameters: flat FP32 vector of 148481 values,
- * per layer W [out][in] row-major then b [out]. */
+ * unbiased for any network.  Requires a level-0 grid of 8^2..32^2.
+ * Parameters: flat FP32 vector of 148224 + 257 K values
+ * (mlmc_dk_surrogate_info), per layer W [out][in] row-major then b [out]. */
 int mlmc_dk_surrogate_init(mlmc_dk_ctx* ctx, uint64_t seed);   /* He-uniform weights, zero biases */
 int mlmc_dk_surrogate_params(mlmc_dk_ctx* ctx, float* theta_out, const float* theta_in);  /* get and/or set */
+/* Number of network parameters and outputs (K = n_obs) of an initialised learned level. */
+int mlmc_dk_surrogate_info(const mlmc_dk_ctx* ctx, int32_t* n_params, int32_t* n_outputs);
 /* Standardised features (host float[n][64], n <= 65536) of samples first..
  * of level 0 in stream `stream_tag` (direct = 0), or the direct draws of the
  * level below 0 (direct = 1). */
 int mlmc_dk_surrogate_features(mlmc_dk_ctx* ctx, int32_t direct, int32_t stream_tag, int64_t first, int64_t n,
                                uint64_t seed, float* X_host);
+/* Network outputs y_host[n][K] of the feature rows X_host[n][64] (n <= 65536). */
 int mlmc_dk_surrogate_forward(mlmc_dk_ctx* ctx, const float* X_host, int64_t n, float* y_host);
-/* Mean squared error of the network on (X, T) (B <= 4096 rows) and its
- * gradient (host float[148481], same layout as the parameters). */
+/* Squared error of the network on (X, T) (T [B][K], B <= 4096 rows), summed
+ * over the outputs and averaged over the rows, and its gradient (host float
+ * [n_params], same layout as the parameters). */
 int mlmc_dk_surrogate_loss_grad(mlmc_dk_ctx* ctx, const float* X_host, const float* T_host, int32_t B, double* loss,
                                 float* grad_host);
 /* Train on n_pairs level-0 paths of the training stream (3): targets
- * sqrt(N)(Y_0 - Ybar_0), Adam (beta 0.9, 0.999), cosine-decayed step size,
+ * sqrt(N)(Y_0k - Ybar_0k), Adam (beta 0.9, 0.999), cosine-decayed step size,
  * minibatches of `batch` (a multiple of 64, <= 4096), the last 1/16 held out.
- * Outputs the last batch's and the held-out mean squared errors. */
+ * Outputs the last batch's and the held-out errors (the loss above). */
 int mlmc_dk_surrogate_train(mlmc_dk_ctx* ctx, int64_t n_pairs, int32_t epochs, int32_t batch, double lr, uint64_t seed,
                             double* train_mse, double* val_mse, double* seconds);
 /* n samples of the level below 0 (part = -1: dP = S) or of the correction
- * level (part = 0: dP = P_0 - S, P_f = P_0, P_c = S), added into sums[0]
- * (consecutive sample ids per part). */
+ * level (part = 0: dP = P_0 - S, P_f = P_0, P_c = S), added into
+ * sums[0 .. n_quant-1], one per quantity (consecutive sample ids per part). */
 int mlmc_dk_run_surrogate(mlmc_dk_ctx* ctx, int32_t part, int64_t n_samples, uint64_t seed, mlmc_dk_level_sums* sums);
 /* Algorithm 1 over {level below 0, correction level, levels 1..L}, costs =
- * measured device seconds per sample; result arrays index 0 = correction
- * level, l = level l; the level below 0's sums go to *surrogate_level. */
+ * measured device seconds per sample, allocation by the first quantity;
+ * result arrays index 0 = correction level, l = level l; estimates[q] per
+ * quantity; the level below 0's sums of the first quantity go to
+ * *surrogate_level. */
 int mlmc_dk_estimate_surrogate(mlmc_dk_ctx* ctx, double eps, int32_t relative, uint64_t seed, mlmc_dk_result* out,
                                mlmc_dk_level_sums* surrogate_level);
 

@@ -139,18 +139,22 @@ struct GemmArgs {
 cudaError_t launch_features(const FeatArgs& a, int max_ctas, cudaStream_t st);
 cudaError_t launch_direct_features(const FeatArgs& a, cudaStream_t st);
 cudaError_t launch_gemm(const GemmArgs& g, cudaStream_t st);
-cudaError_t launch_out_forward(const __nv_bfloat16* H, const float* w, const float* b, int B, int K, float* y,
+// Output layer with KO outputs (one per test function): y [B][KO]; weights
+// w4 [KO][K], biases b4 [KO].
+cudaError_t launch_out_forward(const __nv_bfloat16* H, const float* w, const float* b, int B, int K, int KO, float* y,
                                cudaStream_t st);
 cudaError_t launch_out_backward(const float* y, const float* t, const __nv_bfloat16* H, const float* w, int B, int K,
-                                float* dy, __nv_bfloat16* dH, float* dw, float* db, cudaStream_t st);
+                                int KO, float* dy, __nv_bfloat16* dH, float* dw, float* db, cudaStream_t st);
 cudaError_t launch_colsum(const __nv_bfloat16* Xb, const float* Xf, int B, int N, float* out, cudaStream_t st);
 cudaError_t launch_adam(float* theta, const float* grad, float* m1, float* m2, int P, float lr, float b1, float b2,
                         float eps, float c1, float c2, const int* bf_index, __nv_bfloat16* theta_bf, cudaStream_t st);
-cudaError_t launch_gather(const __nv_bfloat16* X, const float* T, const int* idx, int B, __nv_bfloat16* Xb, float* Tb,
-                          cudaStream_t st);
-cudaError_t launch_mse(const float* y, const float* t, int B, double* out, cudaStream_t st);
+cudaError_t launch_gather(const __nv_bfloat16* X, const float* T, const int* idx, int B, int KO, __nv_bfloat16* Xb,
+                          float* Tb, cudaStream_t st);
+// sum of squared differences of n values, divided by B
+cudaError_t launch_mse(const float* y, const float* t, int n, int B, double* out, cudaStream_t st);
 cudaError_t launch_surrogate_moments(const float* that, const double* d0, int d0_stride, int part, double N,
-                                     long long count, int stride, int blocks, double* partials, cudaStream_t st);
+                                     long long count, int stride, int KO, int products, int blocks, double* partials,
+                                     cudaStream_t st);
 
 // Device address and size (doubles) of the statically allocated scratch used
 // by mlmc_dk_run_level_static; the first call on a device looks the address up

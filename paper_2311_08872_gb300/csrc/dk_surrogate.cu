@@ -199,28 +199,35 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(const GemmArgs g) {
 }
 
 // -------------------------------------------------------- small MLP kernels
-// Output layer forward: y[b] = H3[b] . w4 + b4 (one warp per row).
-__global__ void out_forward_kernel(const __nv_bfloat16* H, const float* w, const float* b, int B, int K, float* y) {
+// Output layer forward: y[b][o] = H3[b] . w4[o] + b4[o], o < KO (one warp per row).
+__global__ void out_forward_kernel(const __nv_bfloat16* H, const float* w, const float* b, int B, int K, int KO,
+                                   float* y) {
     const int row = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (row >= B) return;
-    float s = 0.f;
-    for (int k = lane; k < K; k += 32) s = fmaf(__bfloat162float(H[(size_t)row * K + k]), w[k], s);
+    for (int o = 0; o < KO; ++o) {
+        float s = 0.f;
+        for (int k = lane; k < K; k += 32) s = fmaf(__bfloat162float(H[(size_t)row * K + k]), w[(size_t)o * K + k], s);
 #pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) s += __shfl_xor_sync(kFullMask, s, off);
-    if (lane == 0) y[row] = s + b[0];
+        for (int off = 16; off >= 1; off >>= 1) s += __shfl_xor_sync(kFullMask, s, off);
+        if (lane == 0) y[(size_t)row * KO + o] = s + b[o];
+    }
 }
 
-// dy = 2 (y - t) / B; dH[b][k] = dy[b] w4[k] (H[b][k] > 0) as BF16.
+// dy[b][o] = 2 (y - t) / B; dH[b][k] = (sum_o dy[b][o] w4[o][k]) (H[b][k] > 0) as BF16.
 __global__ void out_backward_kernel(const float* y, const float* t, const __nv_bfloat16* H, const float* w, int B,
-                                    int K, float* dy, __nv_bfloat16* dH) {
+                                    int K, int KO, float* dy, __nv_bfloat16* dH) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= (long long)B * K) return;
     const int b = static_cast<int>(i / K), k = static_cast<int>(i % K);
-    const float d = 2.f * (y[b] - t[b]) / static_cast<float>(B);
-    if (k == 0) dy[b] = d;
-    const float v = __bfloat162float(H[i]) > 0.f ? d * w[k] : 0.f;
-    dH[i] = __float2bfloat16_rn(v);
+    float v = 0.f;
+    for (int o = 0; o < KO; ++o) {
+        const size_t bo = (size_t)b * KO + o;
+        const float d = 2.f * (y[bo] - t[bo]) / static_cast<float>(B);
+        if (k == 0) dy[bo] = d;
+        v = fmaf(d, w[(size_t)o * K + k], v);
+    }
+    dH[i] = __float2bfloat16_rn(__bfloat162float(H[i]) > 0.f ? v : 0.f);
 }
 
 // Column sums: out[n] = sum_b X[b][n] (X BF16 or FP32), fixed order per column.
@@ -232,18 +239,20 @@ __global__ void colsum_kernel(const __nv_bfloat16* Xb, const float* Xf, int B, i
     out[n] = s;
 }
 
-// dW4[k] = sum_b dy[b] H3[b][k]; db4 = sum_b dy[b].
-__global__ void out_weight_grad_kernel(const float* dy, const __nv_bfloat16* H, int B, int K, float* dw, float* db) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < K) {
+// dW4[o][k] = sum_b dy[b][o] H3[b][k]; db4[o] = sum_b dy[b][o].
+__global__ void out_weight_grad_kernel(const float* dy, const __nv_bfloat16* H, int B, int K, int KO, float* dw,
+                                       float* db) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < K * KO) {
+        const int o = j / K, k = j % K;
         float s = 0.f;
-        for (int b = 0; b < B; ++b) s = fmaf(dy[b], __bfloat162float(H[(size_t)b * K + k]), s);
-        dw[k] = s;
-    }
-    if (k == K) {
+        for (int b = 0; b < B; ++b) s = fmaf(dy[(size_t)b * KO + o], __bfloat162float(H[(size_t)b * K + k]), s);
+        dw[j] = s;
+    } else if (j < K * KO + KO) {
+        const int o = j - K * KO;
         float s = 0.f;
-        for (int b = 0; b < B; ++b) s += dy[b];
-        db[0] = s;
+        for (int b = 0; b < B; ++b) s += dy[(size_t)b * KO + o];
+        db[o] = s;
     }
 }
 
@@ -264,21 +273,22 @@ __global__ void adam_kernel(float* theta, const float* grad, float* m1, float* m
     if (j >= 0) theta_bf[j] = __float2bfloat16_rn(w);
 }
 
-__global__ void gather_kernel(const __nv_bfloat16* X, const float* T, const int* idx, int B, __nv_bfloat16* Xb,
-                              float* Tb) {
+__global__ void gather_kernel(const __nv_bfloat16* X, const float* T, const int* idx, int B, int KO,
+                              __nv_bfloat16* Xb, float* Tb) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= (long long)B * kFeat) return;
     const int b = static_cast<int>(i / kFeat), j = static_cast<int>(i % kFeat);
     const int src = idx[b];
     Xb[i] = X[(size_t)src * kFeat + j];
-    if (j == 0) Tb[b] = T[src];
+    if (j < KO) Tb[(size_t)b * KO + j] = T[(size_t)src * KO + j];
 }
 
-// Mean squared error of a batch, FP64 accumulation, one block.
-__global__ void mse_kernel(const float* y, const float* t, int B, double* out) {
+// Squared error of a batch summed over its n values (rows x outputs) and
+// divided by the rows B, FP64 accumulation, one block.
+__global__ void mse_kernel(const float* y, const float* t, int n, int B, double* out) {
     __shared__ double sh[256];
     double s = 0.0;
-    for (int i = threadIdx.x; i < B; i += 256) {
+    for (int i = threadIdx.x; i < n; i += 256) {
         const double d = static_cast<double>(y[i]) - t[i];
         s += d * d;
     }
@@ -292,42 +302,60 @@ __global__ void mse_kernel(const float* y, const float* t, int B, double* out) {
 }
 
 // Per-sample quantities of a surrogate batch into per-block FP64 partials
-// (entry-major [stride][blocks]) in the moment layout of the level kernels.
-// part = -1: dP = S = That^2 (level below 0); part = 0: dP = P_0 - S with
-// P_0 = N D0^2 (correction level).  That = network output (sqrt(N)(Y - Ybar)).
+// (entry-major [stride][blocks]) in the moment layout of the level kernels,
+// quantity by quantity: q = (j, l), j <= l when `products` (else l = j).
+// That_k = network output k (sqrt(N)(Y_k - Ybar_k)); S_jl = That_j That_l.
+// part = -1: dP = S (level below 0); part = 0: dP = P_0 - S with
+// P_0 = N D_j D_l, D the level-0 sample's fluctuations (correction level).
 __global__ void __launch_bounds__(256) surrogate_moments_kernel(const float* that, const double* d0, int d0_stride,
                                                                 int part, double N, long long count, int stride,
-                                                                double* partials) {
-    double v[14];
-#pragma unroll
-    for (int i = 0; i < 14; ++i) v[i] = 0.0;
-    for (long long i = blockIdx.x * 256LL + threadIdx.x; i < count; i += 256LL * gridDim.x) {
-        const double S = static_cast<double>(that[i]) * that[i];
-        const double dd = part == 0 ? d0[i * d0_stride] : 0.0;
-        const double pf = part == 0 ? N * dd * dd : S;
-        const double pc = part == 0 ? S : 0.0;
-        const double dp = pf - pc, dp2 = dp * dp;
-        v[0] += 1.0;
-        v[2] += dp; v[3] += dp2; v[4] += dp2 * dp; v[5] += dp2 * dp2;
-        v[6] += pf; v[7] += pf * pf; v[8] += pc; v[9] += pc * pc;
-        const double yf = part == 0 ? dd : that[i] / sqrt(N);
-        const double yc = part == 0 ? that[i] / sqrt(N) : 0.0;
-        v[10] += yf; v[11] += yf * yf; v[12] += yc; v[13] += yc * yc;
-    }
-    __shared__ double sh[8][14];
-#pragma unroll
-    for (int i = 0; i < 14; ++i)
-#pragma unroll
-        for (int off = 16; off >= 1; off >>= 1) v[i] += __shfl_xor_sync(kFullMask, v[i], off);
+                                                                int KO, int products, double* partials) {
+    __shared__ double sh[8][12];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (lane == 0)
+    const double rsN = 1.0 / sqrt(N);
+    int q = 0;
+    for (int j = 0; j < KO; ++j) {
+        const int lend = products ? KO : j + 1;
+        for (int l = j; l < lend; ++l, ++q) {
+            double v[12];
 #pragma unroll
-        for (int i = 0; i < 14; ++i) sh[w][i] = v[i];
-    __syncthreads();
-    if (threadIdx.x < 14 && threadIdx.x < stride) {
-        double t = 0.0;
-        for (int ww = 0; ww < 8; ++ww) t += sh[ww][threadIdx.x];
-        partials[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = t;
+            for (int e = 0; e < 12; ++e) v[e] = 0.0;
+            for (long long i = blockIdx.x * 256LL + threadIdx.x; i < count; i += 256LL * gridDim.x) {
+                const double tj = that[i * KO + j], tl = that[i * KO + l];
+                const double S = tj * tl;
+                const double dj = part == 0 ? d0[i * d0_stride + j] : 0.0;
+                const double dl = part == 0 ? d0[i * d0_stride + l] : 0.0;
+                const double pf = part == 0 ? N * dj * dl : S;
+                const double pc = part == 0 ? S : 0.0;
+                const double dp = pf - pc, dp2 = dp * dp;
+                v[0] += dp; v[1] += dp2; v[2] += dp2 * dp; v[3] += dp2 * dp2;
+                v[4] += pf; v[5] += pf * pf; v[6] += pc; v[7] += pc * pc;
+                const double yf = part == 0 ? dj : tj * rsN;
+                const double yc = part == 0 ? tj * rsN : 0.0;
+                v[8] += yf; v[9] += yf * yf; v[10] += yc; v[11] += yc * yc;
+            }
+#pragma unroll
+            for (int e = 0; e < 12; ++e)
+#pragma unroll
+                for (int off = 16; off >= 1; off >>= 1) v[e] += __shfl_xor_sync(kFullMask, v[e], off);
+            if (lane == 0)
+#pragma unroll
+                for (int e = 0; e < 12; ++e) sh[w][e] = v[e];
+            __syncthreads();
+            if (threadIdx.x < 12 && 2 + 12 * q + (int)threadIdx.x < stride) {
+                double t = 0.0;
+                for (int ww = 0; ww < 8; ++ww) t += sh[ww][threadIdx.x];
+                partials[(size_t)(2 + 12 * q + threadIdx.x) * gridDim.x + blockIdx.x] = t;
+            }
+            __syncthreads();
+        }
+    }
+    if (threadIdx.x == 0) {
+        // entry 0: samples of this block; entry 1: mass error (none here)
+        long long c = 0;
+        for (long long i = blockIdx.x * 256LL; i < count; i += 256LL * gridDim.x) c += min(256LL, count - i);
+        partials[blockIdx.x] = (double)c;
+        partials[(size_t)gridDim.x + blockIdx.x] = 0.0;
     }
 }
 
@@ -353,16 +381,16 @@ cudaError_t launch_gemm(const GemmArgs& g, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_out_forward(const __nv_bfloat16* H, const float* w, const float* b, int B, int K, float* y,
+cudaError_t launch_out_forward(const __nv_bfloat16* H, const float* w, const float* b, int B, int K, int KO, float* y,
                                cudaStream_t st) {
-    out_forward_kernel<<<(B + 7) / 8, 256, 0, st>>>(H, w, b, B, K, y);
+    out_forward_kernel<<<(B + 7) / 8, 256, 0, st>>>(H, w, b, B, K, KO, y);
     return cudaGetLastError();
 }
 
 cudaError_t launch_out_backward(const float* y, const float* t, const __nv_bfloat16* H, const float* w, int B, int K,
-                                float* dy, __nv_bfloat16* dH, float* dw, float* db, cudaStream_t st) {
-    out_backward_kernel<<<(unsigned)(((long long)B * K + 255) / 256), 256, 0, st>>>(y, t, H, w, B, K, dy, dH);
-    out_weight_grad_kernel<<<(K + 1 + 127) / 128, 128, 0, st>>>(dy, H, B, K, dw, db);
+                                int KO, float* dy, __nv_bfloat16* dH, float* dw, float* db, cudaStream_t st) {
+    out_backward_kernel<<<(unsigned)(((long long)B * K + 255) / 256), 256, 0, st>>>(y, t, H, w, B, K, KO, dy, dH);
+    out_weight_grad_kernel<<<(K * KO + KO + 127) / 128, 128, 0, st>>>(dy, H, B, K, KO, dw, db);
     return cudaGetLastError();
 }
 
@@ -378,20 +406,22 @@ cudaError_t launch_adam(float* theta, const float* grad, float* m1, float* m2, i
     return cudaGetLastError();
 }
 
-cudaError_t launch_gather(const __nv_bfloat16* X, const float* T, const int* idx, int B, __nv_bfloat16* Xb, float* Tb,
-                          cudaStream_t st) {
-    gather_kernel<<<(unsigned)(((long long)B * kFeat + 255) / 256), 256, 0, st>>>(X, T, idx, B, Xb, Tb);
+cudaError_t launch_gather(const __nv_bfloat16* X, const float* T, const int* idx, int B, int KO, __nv_bfloat16* Xb,
+                          float* Tb, cudaStream_t st) {
+    gather_kernel<<<(unsigned)(((long long)B * kFeat + 255) / 256), 256, 0, st>>>(X, T, idx, B, KO, Xb, Tb);
     return cudaGetLastError();
 }
 
-cudaError_t launch_mse(const float* y, const float* t, int B, double* out, cudaStream_t st) {
-    mse_kernel<<<1, 256, 0, st>>>(y, t, B, out);
+cudaError_t launch_mse(const float* y, const float* t, int n, int B, double* out, cudaStream_t st) {
+    mse_kernel<<<1, 256, 0, st>>>(y, t, n, B, out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_surrogate_moments(const float* that, const double* d0, int d0_stride, int part, double N,
-                                     long long count, int stride, int blocks, double* partials, cudaStream_t st) {
-    surrogate_moments_kernel<<<blocks, 256, 0, st>>>(that, d0, d0_stride, part, N, count, stride, partials);
+                                     long long count, int stride, int KO, int products, int blocks, double* partials,
+                                     cudaStream_t st) {
+    surrogate_moments_kernel<<<blocks, 256, 0, st>>>(that, d0, d0_stride, part, N, count, stride, KO, products,
+                                                      partials);
     return cudaGetLastError();
 }
 

@@ -94,6 +94,10 @@ struct mlmc_dk_ctx {
 // BF16 copies of the weight matrices, Adam moments) and chunk buffers.
 struct Surrogate {
     int n = 0, M = 0;
+    int K = 1;                         // network outputs: one per test function
+    int products = 0;                  // quantities S_jl = That_j That_l for all j <= l
+    int P = 0;                         // parameters (148224 + 257 K)
+    int sampw = 4;                     // doubles per level-0 per-sample output (2 K + 2)
     int chunk = 65536;                 // samples per inference chunk
     int batch_cap = 0;                 // largest training batch
     float *d_E = nullptr, *d_g = nullptr, *d_inv_sigma = nullptr;
@@ -1178,10 +1182,13 @@ int mlmc_dk_load_state(mlmc_dk_ctx* ctx, const void* buf, size_t len) {
 // ===================================================== learned level below 0
 namespace {
 
-constexpr int kP = 148481;   // 64*256+256 + 2*(256*256+256) + 256+1
+// parameter layout (layer by layer, W [out][in] then b): 64*256+256 + 2*(256*256+256) + K*(256+1)
 constexpr int kOffW1 = 0, kOffB1 = 16384, kOffW2 = 16640, kOffB2 = 82176, kOffW3 = 82432, kOffB3 = 147968,
-              kOffW4 = 148224, kOffB4 = 148480;
-constexpr int kBfW1 = 0, kBfW2 = 16384, kBfW3 = 81920, kBfW4 = 147456, kBfTotal = 147712;
+              kOffW4 = 148224;
+constexpr int kBfW1 = 0, kBfW2 = 16384, kBfW3 = 81920, kBfW4 = 147456;
+constexpr int param_count(int K) { return kOffW4 + (dk::kHidden + 1) * K; }
+constexpr int off_b4(int K) { return kOffW4 + dk::kHidden * K; }
+constexpr int bf_total(int K) { return kBfW4 + dk::kHidden * K; }
 constexpr int kMomentBlocks = 128;
 
 void free_surrogate(Surrogate* s) {
@@ -1253,15 +1260,16 @@ cudaError_t mlp_forward(Surrogate* s, const __nv_bfloat16* X, int n, float* y, c
     g = gemm(n, dk::kHidden, dk::kHidden, s->d_H2, dk::kHidden, 1, s->d_wbf + kBfW3, 1, dk::kHidden);
     g.Cb = s->d_H3; g.ldcb = dk::kHidden; g.bias = s->d_theta + kOffB3; g.relu = 1;
     if ((e = dk::launch_gemm(g, st)) != cudaSuccess) return e;
-    return dk::launch_out_forward(s->d_H3, s->d_theta + kOffW4, s->d_theta + kOffB4, n, dk::kHidden, y, st);
+    return dk::launch_out_forward(s->d_H3, s->d_theta + kOffW4, s->d_theta + off_b4(s->K), n, dk::kHidden, s->K, y,
+                                  st);
 }
 
 // Mean-squared-error gradient of a batch (after mlp_forward on it) into d_grad.
 cudaError_t mlp_backward(Surrogate* s, const __nv_bfloat16* X, const float* T, int B, cudaStream_t st) {
     cudaError_t e;
     float* G = s->d_grad;
-    if ((e = dk::launch_out_backward(s->d_y, T, s->d_H3, s->d_theta + kOffW4, B, dk::kHidden, s->d_dy, s->d_dH3,
-                                     G + kOffW4, G + kOffB4, st)) != cudaSuccess)
+    if ((e = dk::launch_out_backward(s->d_y, T, s->d_H3, s->d_theta + kOffW4, B, dk::kHidden, s->K, s->d_dy, s->d_dH3,
+                                     G + kOffW4, G + off_b4(s->K), st)) != cudaSuccess)
         return e;
     struct Layer { const __nv_bfloat16* dH; const __nv_bfloat16* Hin; int K; float* gW; float* gb;
                    const __nv_bfloat16* W; __nv_bfloat16* dHin; };
@@ -1286,11 +1294,12 @@ cudaError_t mlp_backward(Surrogate* s, const __nv_bfloat16* X, const float* T, i
 }
 
 cudaError_t upload_params(Surrogate* s, const float* theta_host, cudaStream_t st) {
-    cudaError_t e = cudaMemcpyAsync(s->d_theta, theta_host, sizeof(float) * kP, cudaMemcpyHostToDevice, st);
+    const int P = s->P, kOffB4 = off_b4(s->K), kBfTotal = bf_total(s->K);
+    cudaError_t e = cudaMemcpyAsync(s->d_theta, theta_host, sizeof(float) * P, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return e;
     std::vector<__nv_bfloat16> wb(kBfTotal);
-    std::vector<int> idx(kP, -1);
-    for (int i = 0; i < kP; ++i) {
+    std::vector<int> idx(P, -1);
+    for (int i = 0; i < P; ++i) {
         int j = -1;
         if (i < kOffB1) j = kBfW1 + i;
         else if (i >= kOffW2 && i < kOffB2) j = kBfW2 + (i - kOffW2);
@@ -1302,7 +1311,7 @@ cudaError_t upload_params(Surrogate* s, const float* theta_host, cudaStream_t st
     if ((e = cudaMemcpyAsync(s->d_wbf, wb.data(), sizeof(__nv_bfloat16) * kBfTotal, cudaMemcpyHostToDevice, st)) !=
         cudaSuccess)
         return e;
-    if ((e = cudaMemcpyAsync(s->d_bfidx, idx.data(), sizeof(int) * kP, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    if ((e = cudaMemcpyAsync(s->d_bfidx, idx.data(), sizeof(int) * P, cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return e;
     return cudaStreamSynchronize(st);
 }
@@ -1329,8 +1338,6 @@ extern "C" {
 
 int mlmc_dk_surrogate_init(mlmc_dk_ctx* ctx, uint64_t seed) {
     if (!ctx) return fail(nullptr, MLMC_DK_ERR_INVALID, "null context");
-    if (ctx->n_obs != 1 || ctx->products)
-        return fail(ctx, MLMC_DK_ERR_INVALID, "surrogate: one observable, no products");
     const LevelTab& l0 = ctx->lv[0];
     if (l0.n < 8 || l0.n > 32 || l0.streamed)
         return fail(ctx, MLMC_DK_ERR_UNSUPPORTED, "surrogate: level-0 grid must be 8^2..32^2");
@@ -1338,7 +1345,12 @@ int mlmc_dk_surrogate_init(mlmc_dk_ctx* ctx, uint64_t seed) {
     Surrogate* s = ctx->sur = new Surrogate();
     s->n = l0.n;
     s->M = l0.M;
+    s->K = ctx->n_obs;
+    s->products = ctx->products;
+    s->P = param_count(s->K);
+    s->sampw = 2 * ctx->n_obs + 2;
     s->batch_cap = 4096;
+    const int kP = s->P, kBfTotal = bf_total(s->K), K = s->K;
     std::vector<float> E, g, isig;
     build_modes(l0.n, l0.tau / (l0.h * l0.h), l0.M, E, g, isig);
     const size_t ch = (size_t)s->chunk;
@@ -1362,10 +1374,10 @@ int mlmc_dk_surrogate_init(mlmc_dk_ctx* ctx, uint64_t seed) {
     alloc((void**)&s->d_dH1, sizeof(__nv_bfloat16) * s->batch_cap * dk::kHidden);
     alloc((void**)&s->d_dH2, sizeof(__nv_bfloat16) * s->batch_cap * dk::kHidden);
     alloc((void**)&s->d_dH3, sizeof(__nv_bfloat16) * s->batch_cap * dk::kHidden);
-    alloc((void**)&s->d_y, sizeof(float) * ch);
-    alloc((void**)&s->d_dy, sizeof(float) * s->batch_cap);
-    alloc((void**)&s->d_T, sizeof(float) * ch);
-    alloc((void**)&s->d_samp, sizeof(double) * ch * 4);
+    alloc((void**)&s->d_y, sizeof(float) * ch * K);
+    alloc((void**)&s->d_dy, sizeof(float) * s->batch_cap * K);
+    alloc((void**)&s->d_T, sizeof(float) * ch * K);
+    alloc((void**)&s->d_samp, sizeof(double) * ch * s->sampw);
     alloc((void**)&s->d_part, sizeof(double) * ctx->stride * kMomentBlocks);
     alloc((void**)&s->d_loss, sizeof(double));
     if (e == cudaSuccess) e = cudaMemcpy(s->d_E, E.data(), sizeof(float) * E.size(), cudaMemcpyHostToDevice);
@@ -1388,7 +1400,7 @@ int mlmc_dk_surrogate_init(mlmc_dk_ctx* ctx, uint64_t seed) {
     };
     const int fan[4] = {dk::kFeat, dk::kHidden, dk::kHidden, dk::kHidden};
     const int offW[4] = {kOffW1, kOffW2, kOffW3, kOffW4};
-    const int cnt[4] = {dk::kFeat * dk::kHidden, dk::kHidden * dk::kHidden, dk::kHidden * dk::kHidden, dk::kHidden};
+    const int cnt[4] = {dk::kFeat * dk::kHidden, dk::kHidden * dk::kHidden, dk::kHidden * dk::kHidden, dk::kHidden * K};
     for (int l = 0; l < 4; ++l) {
         const double lim = std::sqrt(6.0 / fan[l]);
         for (int i = 0; i < cnt[l]; ++i) theta[offW[l] + i] = (float)((2.0 * uni() - 1.0) * lim * (l == 3 ? 0.1 : 1.0));
@@ -1405,8 +1417,15 @@ int mlmc_dk_surrogate_params(mlmc_dk_ctx* ctx, float* theta_out, const float* th
         ctx->sur->adam_t = 0;
     }
     if (theta_out &&
-        (e = cudaMemcpy(theta_out, ctx->sur->d_theta, sizeof(float) * kP, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        (e = cudaMemcpy(theta_out, ctx->sur->d_theta, sizeof(float) * ctx->sur->P, cudaMemcpyDeviceToHost)) != cudaSuccess)
         return sur_fail(ctx, e, "get params");
+    return MLMC_DK_OK;
+}
+
+int mlmc_dk_surrogate_info(const mlmc_dk_ctx* ctx, int32_t* n_params, int32_t* n_outputs) {
+    if (!ctx || !ctx->sur) return fail(const_cast<mlmc_dk_ctx*>(ctx), MLMC_DK_ERR_INVALID, "surrogate not initialised");
+    if (n_params) *n_params = ctx->sur->P;
+    if (n_outputs) *n_outputs = ctx->sur->K;
     return MLMC_DK_OK;
 }
 
@@ -1432,7 +1451,8 @@ int mlmc_dk_surrogate_forward(mlmc_dk_ctx* ctx, const float* X_host, int64_t n, 
     for (size_t i = 0; i < xb.size(); ++i) xb[i] = __float2bfloat16_rn(X_host[i]);
     cudaError_t e = cudaMemcpy(s->d_X, xb.data(), sizeof(__nv_bfloat16) * xb.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = mlp_forward(s, s->d_X, (int)n, s->d_y, ctx->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(y_host, s->d_y, sizeof(float) * n, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(y_host, s->d_y, sizeof(float) * n * s->K, cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     return e == cudaSuccess ? MLMC_DK_OK : sur_fail(ctx, e, "surrogate forward");
 }
@@ -1445,13 +1465,13 @@ int mlmc_dk_surrogate_loss_grad(mlmc_dk_ctx* ctx, const float* X_host, const flo
     std::vector<__nv_bfloat16> xb((size_t)B * dk::kFeat);
     for (size_t i = 0; i < xb.size(); ++i) xb[i] = __float2bfloat16_rn(X_host[i]);
     cudaError_t e = cudaMemcpy(s->d_X, xb.data(), sizeof(__nv_bfloat16) * xb.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(s->d_T, T_host, sizeof(float) * B, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(s->d_T, T_host, sizeof(float) * B * s->K, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = mlp_forward(s, s->d_X, B, s->d_y, ctx->stream);
-    if (e == cudaSuccess) e = dk::launch_mse(s->d_y, s->d_T, B, s->d_loss, ctx->stream);
+    if (e == cudaSuccess) e = dk::launch_mse(s->d_y, s->d_T, B * s->K, B, s->d_loss, ctx->stream);
     if (e == cudaSuccess) e = mlp_backward(s, s->d_X, s->d_T, B, ctx->stream);
     if (e == cudaSuccess && loss) e = cudaMemcpyAsync(loss, s->d_loss, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess && grad_host)
-        e = cudaMemcpyAsync(grad_host, s->d_grad, sizeof(float) * kP, cudaMemcpyDeviceToHost, ctx->stream);
+        e = cudaMemcpyAsync(grad_host, s->d_grad, sizeof(float) * s->P, cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     return e == cudaSuccess ? MLMC_DK_OK : sur_fail(ctx, e, "surrogate loss/grad");
 }
@@ -1465,13 +1485,14 @@ int mlmc_dk_surrogate_train(mlmc_dk_ctx* ctx, int64_t n_pairs, int32_t epochs, i
     Surrogate* s = ctx->sur;
     cudaStream_t st = ctx->stream;
     cudaError_t e = cudaSuccess;
+    const int K = s->K, W = s->sampw, kP = s->P;
     if (s->n_train != n_pairs) {
         cudaFree(s->d_trainX);
         cudaFree(s->d_trainT);
         cudaFree(s->d_idx);
         s->d_trainX = nullptr; s->d_trainT = nullptr; s->d_idx = nullptr;
         if ((e = cudaMalloc(&s->d_trainX, sizeof(__nv_bfloat16) * n_pairs * dk::kFeat)) != cudaSuccess ||
-            (e = cudaMalloc(&s->d_trainT, sizeof(float) * n_pairs)) != cudaSuccess ||
+            (e = cudaMalloc(&s->d_trainT, sizeof(float) * n_pairs * K)) != cudaSuccess ||
             (e = cudaMalloc(&s->d_idx, sizeof(int) * n_pairs)) != cudaSuccess)
             return sur_fail(ctx, e, "training buffers");
         s->n_train = n_pairs;
@@ -1486,14 +1507,17 @@ int mlmc_dk_surrogate_train(mlmc_dk_ctx* ctx, int64_t n_pairs, int32_t epochs, i
         if (rc != MLMC_DK_OK) return rc;
         dk::FeatArgs a = feat_args(ctx, 1, 3, done, n, seed, s->d_trainX + done * dk::kFeat, nullptr);
         if ((e = dk::launch_features(a, 152 * 8, st)) != cudaSuccess) return sur_fail(ctx, e, "features");
-        hs.resize((size_t)n * 4);
-        if ((e = cudaMemcpyAsync(hs.data(), s->d_samp, sizeof(double) * n * 4, cudaMemcpyDeviceToHost, st)) !=
+        hs.resize((size_t)n * W);
+        if ((e = cudaMemcpyAsync(hs.data(), s->d_samp, sizeof(double) * n * W, cudaMemcpyDeviceToHost, st)) !=
                 cudaSuccess ||
             (e = cudaStreamSynchronize(st)) != cudaSuccess)
             return sur_fail(ctx, e, "training targets");
-        ht.resize(n);
-        for (int64_t i = 0; i < n; ++i) ht[i] = (float)(sqrtN * hs[(size_t)i * 4]);   // sqrt(N) (Y_0 - Ybar_0)
-        if ((e = cudaMemcpy(s->d_trainT + done, ht.data(), sizeof(float) * n, cudaMemcpyHostToDevice)) != cudaSuccess)
+        ht.resize((size_t)n * K);
+        for (int64_t i = 0; i < n; ++i)
+            for (int k = 0; k < K; ++k)
+                ht[(size_t)i * K + k] = (float)(sqrtN * hs[(size_t)i * W + k]);   // sqrt(N) (Y_0k - Ybar_0k)
+        if ((e = cudaMemcpy(s->d_trainT + done * K, ht.data(), sizeof(float) * n * K, cudaMemcpyHostToDevice)) !=
+            cudaSuccess)
             return sur_fail(ctx, e, "training targets");
     }
     // last 1/16 held out for validation
@@ -1516,7 +1540,8 @@ int mlmc_dk_surrogate_train(mlmc_dk_ctx* ctx, int64_t n_pairs, int32_t epochs, i
         // cosine-decayed step size over the epochs
         const double lr_ep = lr * 0.5 * (1.0 + std::cos(M_PI * ep / (double)epochs));
         for (int64_t b0 = 0; b0 < n_fit; b0 += batch) {
-            if ((e = dk::launch_gather(s->d_trainX, s->d_trainT, s->d_idx + b0, batch, s->d_X, s->d_T, st)) != cudaSuccess ||
+            if ((e = dk::launch_gather(s->d_trainX, s->d_trainT, s->d_idx + b0, batch, K, s->d_X, s->d_T, st)) !=
+                    cudaSuccess ||
                 (e = mlp_forward(s, s->d_X, batch, s->d_y, st)) != cudaSuccess ||
                 (e = mlp_backward(s, s->d_X, s->d_T, batch, st)) != cudaSuccess)
                 return sur_fail(ctx, e, "training step");
@@ -1528,7 +1553,7 @@ int mlmc_dk_surrogate_train(mlmc_dk_ctx* ctx, int64_t n_pairs, int32_t epochs, i
         }
         if (ep == epochs - 1 && train_mse) {
             // mean-squared error of the last batch's predictions (before its update)
-            if ((e = dk::launch_mse(s->d_y, s->d_T, batch, s->d_loss, st)) != cudaSuccess ||
+            if ((e = dk::launch_mse(s->d_y, s->d_T, batch * K, batch, s->d_loss, st)) != cudaSuccess ||
                 (e = cudaMemcpyAsync(&last_loss, s->d_loss, sizeof(double), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
                 (e = cudaStreamSynchronize(st)) != cudaSuccess)
                 return sur_fail(ctx, e, "train loss");
@@ -1542,7 +1567,7 @@ int mlmc_dk_surrogate_train(mlmc_dk_ctx* ctx, int64_t n_pairs, int32_t epochs, i
             const int64_t n = std::min<int64_t>(s->chunk, n_pairs - v0);
             double l = 0.0;
             if ((e = mlp_forward(s, s->d_trainX + v0 * dk::kFeat, (int)n, s->d_y, st)) != cudaSuccess ||
-                (e = dk::launch_mse(s->d_y, s->d_trainT + v0, (int)n, s->d_loss, st)) != cudaSuccess ||
+                (e = dk::launch_mse(s->d_y, s->d_trainT + v0 * K, (int)n * K, (int)n, s->d_loss, st)) != cudaSuccess ||
                 (e = cudaMemcpyAsync(&l, s->d_loss, sizeof(double), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
                 (e = cudaStreamSynchronize(st)) != cudaSuccess)
                 return sur_fail(ctx, e, "validation");
@@ -1579,8 +1604,8 @@ int mlmc_dk_run_surrogate(mlmc_dk_ctx* ctx, int32_t part, int64_t n_samples, uin
             if ((e = dk::launch_features(a, 152 * 8, st)) != cudaSuccess) return sur_fail(ctx, e, "features");
         }
         if ((e = mlp_forward(s, s->d_X, (int)n, s->d_y, st)) != cudaSuccess ||
-            (e = dk::launch_surrogate_moments(s->d_y, s->d_samp, 4, part, ctx->N, n, ctx->stride, kMomentBlocks,
-                                              s->d_part, st)) != cudaSuccess ||
+            (e = dk::launch_surrogate_moments(s->d_y, s->d_samp, s->sampw, part, ctx->N, n, ctx->stride, s->K,
+                                              s->products, kMomentBlocks, s->d_part, st)) != cudaSuccess ||
             (e = dk::launch_reduce(s->d_part, kMomentBlocks, ctx->stride, ctx->d_sums, st)) != cudaSuccess ||
             (e = cudaEventRecord(ctx->ev1, st)) != cudaSuccess ||
             (e = cudaMemcpyAsync(ctx->h_sums, ctx->d_sums, sizeof(double) * ctx->stride, cudaMemcpyDeviceToHost, st)) !=
@@ -1604,8 +1629,9 @@ int mlmc_dk_estimate_surrogate(mlmc_dk_ctx* ctx, double eps, int32_t relative, u
     const auto t0 = std::chrono::steady_clock::now();
     *out = mlmc_dk_result{};
     // virtual levels: 0 = level below 0 (S), 1 = correction (P_0 - S), 1 + l = level l >= 1
-    const int VL = ctx->L_max + 2;
-    std::vector<mlmc_dk_level_sums> sums(VL);
+    const int VL = ctx->L_max + 2, Q = ctx->n_quant;
+    std::vector<mlmc_dk_level_sums> all((size_t)VL * Q);   // [virtual level][quantity]
+    auto sums = [&](int v) -> mlmc_dk_level_sums& { return all[(size_t)v * Q]; };   // the first quantity
     std::vector<int64_t> target(VL, 0);
     std::fill(ctx->next_id[0].begin(), ctx->next_id[0].end(), 0);
     ctx->sur->next_id[0] = ctx->sur->next_id[1] = 0;
@@ -1614,12 +1640,12 @@ int mlmc_dk_estimate_surrogate(mlmc_dk_ctx* ctx, double eps, int32_t relative, u
     double eps_abs = relative ? -1.0 : eps;
     int status = MLMC_DK_OK, converged = 0;
     auto run = [&](int v, int64_t n) -> int {
-        if (v <= 1) return mlmc_dk_run_surrogate(ctx, v == 0 ? -1 : 0, n, seed, &sums[v]);
-        return mlmc_dk_run_level(ctx, v - 1, n, seed, &sums[v]);
+        if (v <= 1) return mlmc_dk_run_surrogate(ctx, v == 0 ? -1 : 0, n, seed, &sums(v));
+        return mlmc_dk_run_level(ctx, v - 1, n, seed, &sums(v));
     };
     for (int iter = 0; iter < 1000; ++iter) {
         for (int v = 0; v <= L + 1; ++v) {
-            const int64_t need = target[v] - sums[v].n;
+            const int64_t need = target[v] - sums(v).n;
             if (need > 0) {
                 const int rc = run(v, need);
                 if (rc != MLMC_DK_OK) return rc;
@@ -1627,10 +1653,10 @@ int mlmc_dk_estimate_surrogate(mlmc_dk_ctx* ctx, double eps, int32_t relative, u
         }
         std::vector<double> E(L + 2), V(L + 2), C(L + 2);
         for (int v = 0; v <= L + 1; ++v) {
-            const double m = (double)sums[v].n;
-            E[v] = sums[v].dp1 / m;
-            V[v] = std::max(0.0, (sums[v].dp2 - sums[v].dp1 * sums[v].dp1 / m) / (m - 1.0));
-            C[v] = std::max(sums[v].kernel_s / m, 1e-12);   // measured device seconds per sample
+            const double m = (double)sums(v).n;
+            E[v] = sums(v).dp1 / m;
+            V[v] = std::max(0.0, (sums(v).dp2 - sums(v).dp1 * sums(v).dp1 / m) / (m - 1.0));
+            C[v] = std::max(sums(v).kernel_s / m, 1e-12);   // measured device seconds per sample
         }
         if (eps_abs < 0) {
             double mu = 0;
@@ -1644,7 +1670,7 @@ int mlmc_dk_estimate_surrogate(mlmc_dk_ctx* ctx, double eps, int32_t relative, u
         for (int v = 0; v <= L + 1; ++v) {
             const double opt = std::ceil(2.0 / (eps_abs * eps_abs) * std::sqrt(V[v] / C[v]) * total);
             target[v] = std::max(target[v], (int64_t)std::min(opt, 9.0e18));
-            if ((double)(target[v] - sums[v].n) > 0.01 * (double)sums[v].n) more = true;
+            if ((double)(target[v] - sums(v).n) > 0.01 * (double)sums(v).n) more = true;
         }
         if (more) continue;
         // stopping test on the level differences of the plain hierarchy (level 0 = S + (P_0 - S))
@@ -1664,7 +1690,7 @@ int mlmc_dk_estimate_surrogate(mlmc_dk_ctx* ctx, double eps, int32_t relative, u
     out->eps_abs = eps_abs;
     double est = 0.0;
     for (int v = 0; v <= L + 1; ++v) {
-        const mlmc_dk_level_sums& q = sums[v];
+        const mlmc_dk_level_sums& q = sums(v);
         const double m = (double)q.n;
         const double Vv = std::max(0.0, (q.dp2 - q.dp1 * q.dp1 / m) / (m - 1.0));
         est += q.dp1 / m;
@@ -1684,8 +1710,12 @@ int mlmc_dk_estimate_surrogate(mlmc_dk_ctx* ctx, double eps, int32_t relative, u
         out->d2h_bytes += q.d2h_bytes;
     }
     out->estimate = est;
-    out->estimates[0] = est;
-    if (sur_out) *sur_out = sums[0];
+    for (int q = 0; q < Q && q < MLMC_DK_MAX_QUANT; ++q) {
+        double e = 0.0;
+        for (int v = 0; v <= L + 1; ++v) e += all[(size_t)v * Q + q].dp1 / (double)all[(size_t)v * Q + q].n;
+        out->estimates[q] = e;
+    }
+    if (sur_out) *sur_out = sums(0);
     out->wall_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return status;
 }

@@ -293,14 +293,20 @@ class Context:
         return [[sums[l * self.n_quant + q] for q in range(self.n_quant)] for l in range(self.L_max + 1)]
 
     # ---- learned level below level 0
-    N_PARAMS = 148481
+    N_PARAMS = 148481            # parameters of the one-output network (148224 + 257 K in general)
 
     def surrogate_init(self, seed: int = 0):
         _check(lib().mlmc_dk_surrogate_init(self._ctx, seed), self._ctx)
 
+    def surrogate_info(self):
+        """(parameters, outputs) of the initialised network."""
+        p, k = ctypes.c_int32(0), ctypes.c_int32(0)
+        _check(lib().mlmc_dk_surrogate_info(self._ctx, ctypes.byref(p), ctypes.byref(k)), self._ctx)
+        return p.value, k.value
+
     def surrogate_params(self, theta=None) -> np.ndarray:
         fp = ctypes.POINTER(ctypes.c_float)
-        out = np.empty(self.N_PARAMS, dtype=np.float32)
+        out = np.empty(self.surrogate_info()[0], dtype=np.float32)
         tin = None if theta is None else np.ascontiguousarray(theta, dtype=np.float32)
         _check(lib().mlmc_dk_surrogate_params(self._ctx, out.ctypes.data_as(fp),
                                               None if tin is None else tin.ctypes.data_as(fp)), self._ctx)
@@ -316,16 +322,20 @@ class Context:
     def surrogate_forward(self, X) -> np.ndarray:
         fp = ctypes.POINTER(ctypes.c_float)
         X = np.ascontiguousarray(X, dtype=np.float32)
-        y = np.empty(X.shape[0], dtype=np.float32)
+        K = self.surrogate_info()[1]
+        y = np.empty((X.shape[0], K), dtype=np.float32)
         _check(lib().mlmc_dk_surrogate_forward(self._ctx, X.ctypes.data_as(fp), X.shape[0], y.ctypes.data_as(fp)),
                self._ctx)
-        return y
+        return y[:, 0] if K == 1 else y
 
     def surrogate_loss_grad(self, X, T):
         fp = ctypes.POINTER(ctypes.c_float)
         X = np.ascontiguousarray(X, dtype=np.float32)
         T = np.ascontiguousarray(T, dtype=np.float32)
-        g = np.empty(self.N_PARAMS, dtype=np.float32)
+        P, K = self.surrogate_info()
+        if T.size != X.shape[0] * K:
+            raise ValueError(f"targets must have {K} value(s) per row")
+        g = np.empty(P, dtype=np.float32)
         loss = ctypes.c_double(0.0)
         _check(lib().mlmc_dk_surrogate_loss_grad(self._ctx, X.ctypes.data_as(fp), T.ctypes.data_as(fp), X.shape[0],
                                                  ctypes.byref(loss), g.ctypes.data_as(fp)), self._ctx)
@@ -338,9 +348,11 @@ class Context:
         return {"train_mse": a.value, "val_mse": b.value, "seconds": c.value}
 
     def run_surrogate(self, part: int, n: int, seed: int, sums=None):
+        """Sums of n samples of the level below 0 (part -1) or of the correction
+        level (part 0), one LevelSums per quantity."""
         if sums is None:
-            sums = LevelSums()
-        _check(lib().mlmc_dk_run_surrogate(self._ctx, part, n, seed, ctypes.byref(sums)), self._ctx)
+            sums = (LevelSums * self.n_quant)()
+        _check(lib().mlmc_dk_run_surrogate(self._ctx, part, n, seed, sums), self._ctx)
         return sums
 
     def estimate_surrogate(self, eps: float, relative: bool, seed: int):
