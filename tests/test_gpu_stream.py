@@ -80,6 +80,27 @@ def test_streamed_512_matches_oracle(dk):
         assert np.all(np.abs(y - yo) <= 1e-5 * np.maximum(np.abs(yo), rms)), (key, y - yo, rms)
 
 
+def test_streamed_1024_four_modes_match_oracle(dk):
+    """The largest grid (1024^2 fine, 512^2 coarse) of the four-mode workload
+    over a short horizon (8 and 2 steps), four observables: sample by sample
+    against the FP64 oracle."""
+    wl = W.get("large32_1024").with_(n0=512, L_max=1, T=7.6e-7)
+    with dk.Context.from_workload(wl) as ctx:
+        info = ctx.level_info(1)
+        assert info.n == 1024 and info.streamed == 1 and info.M == 8
+        _, samp = _samples(ctx, dk, 1, 0, 5, 2, 33)
+    lv = oracle.level_table(wl.length, wl.n0, wl.L_max, wl.T, wl.mu)
+    ol = oracle.level_inputs(wl.length, lv, wl.N, wl.rho0_all(), wl.phi_all(), 1, True)
+    ref = oracle.run_samples(ol, 33, range(5, 7), True)
+    K = 4
+    for k in range(K):
+        for col, key, yb in ((k, "Y_f", info.ybar_f[k]), (K + k, "Y_c", info.ybar_c[k])):
+            y = samp[:, col] + yb
+            yo = ref[key][:, k]
+            rms = np.sqrt(np.mean((yo - yb) ** 2))
+            assert np.all(np.abs(y - yo) <= 1e-5 * np.maximum(np.abs(yo), rms)), (k, key, y - yo, rms)
+
+
 @pytest.mark.parametrize("name,level,count", [("lowdens32_512", 4, 9), ("large32_1024", 5, 2)])
 def test_full_size_streamed_levels_conserve_mass(dk, name, level, count):
     wl = W.get(name)
