@@ -10,8 +10,11 @@ diagonal quantity when there are several), the eps-optimal allocation of
 Eq. (opt_M_ell), M_l = ceil(2 eps^-2 sqrt(V_l / t_l) sum_k sqrt(V_k t_k)),
 taken as the maximum over quantities, costs sum_l M_l t_l; plain MC needs
 ceil(2 Var[P_L] / eps^2) finest-level samples (the extrapolation the paper
-uses for its MC times, Section 7.3).  Both figures are extrapolated from
-measured rates and pilot variances, and printed as one JSON line.
+uses for its MC times, Section 7.3).  With --surrogate the learned level
+below 0 is trained (2^18 level-0 paths, 8 epochs) and level 0 is replaced by
+the pair {level below 0, correction level}, each with its own pilot variance
+and device time per sample.  All figures are extrapolated from measured
+rates and pilot variances, and printed as one JSON line.
 """
 from __future__ import annotations
 
@@ -41,6 +44,7 @@ def main() -> None:
     ap.add_argument("--seconds", type=float, default=1.5, help="device time per pilot batch")
     ap.add_argument("--max-pilot", type=int, default=100000)
     ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--surrogate", action="store_true", help="also the cost with the learned level below 0")
     args = ap.parse_args()
 
     import torch
@@ -68,6 +72,18 @@ def main() -> None:
             rows.append({"level": l, "n": info.n, "fine_steps": info.M, "pilot": n, "s_per_sample": t,
                          "cell_steps_per_s": info.cost / t, "E": [x[0] for x in q], "V": [x[1] for x in q],
                          "EPf": [x[2] for x in q], "VPf": [x[3] for x in q]})
+        sur = None
+        if args.surrogate:
+            ctx.surrogate_init(args.seed + 3)
+            tr = ctx.surrogate_train(1 << 18, epochs=8, batch=1024, lr=1e-3, seed=args.seed + 4)
+            sur = {"train_s": tr["seconds"], "val_mse": tr["val_mse"], "parts": []}
+            for part in (-1, 0):
+                n = 200000
+                sm = ctx.run_surrogate(part, n, args.seed + 7 + part)
+                t = sm[0].kernel_s / n
+                q = [_moments(sm[k]) for k in range(nq)]
+                sur["parts"].append({"part": part, "pilot": n, "s_per_sample": t, "E": [x[0] for x in q],
+                                     "V": [x[1] for x in q]})
         L = wl.L_max
         info = ctx.level_info(L)
         n_mc = max(2, int(min(args.max_pilot, args.seconds * rows[-1]["cell_steps_per_s"] / info.cost_mc)))
@@ -85,10 +101,22 @@ def main() -> None:
             M[l] = max(M[l], m)
     t_mlmc = sum(m * r["s_per_sample"] for m, r in zip(M, rows))
     m_mc = max(math.ceil(2.0 * v / eps ** 2) for v in var_pl)
+    if sur is not None:
+        # levels {below 0, correction, 1..L} in place of {0, 1..L}
+        vl = sur["parts"] + rows[1:]
+        Ms = [0] * len(vl)
+        for k in range(nq):
+            s = sum(math.sqrt(r["V"][k] * r["s_per_sample"]) for r in vl)
+            for i, r in enumerate(vl):
+                m = math.ceil(2.0 / eps ** 2 * math.sqrt(r["V"][k] / r["s_per_sample"]) * s) if r["V"][k] > 0 else 0
+                Ms[i] = max(Ms[i], m)
+        sur["M_opt"] = Ms
+        sur["mlmc_s"] = sum(m * r["s_per_sample"] for m, r in zip(Ms, vl))
+        sur["mlmc_s_incl_training"] = sur["mlmc_s"] + sur["train_s"]
     print(json.dumps({"workload": wl.name, "eps_rel": eps_rel, "eps_abs": eps, "estimate": est, "levels": rows,
                       "M_opt": M, "mlmc_s": t_mlmc, "mc_samples": m_mc, "mc_s_per_sample": t_mc,
                       "mc_s": m_mc * t_mc, "mlmc_speedup_vs_mc": m_mc * t_mc / t_mlmc if t_mlmc > 0 else None,
-                      "extrapolated": True}))
+                      "surrogate": sur, "extrapolated": True}))
 
 
 if __name__ == "__main__":

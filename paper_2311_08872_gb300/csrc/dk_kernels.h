@@ -87,6 +87,7 @@ struct SArgs {
     double* tile_part;           // [S][tiles][2 kMaxObs + 2] per-tile observables
     const int32_t* q0f; const int32_t* qbf; const float* phif;
     const int32_t* q0c; const int32_t* qbc; const float* phic;
+    const double* phif64; const double* phic64;   // FP64 test functions (observables)
     int32_t Af, Ac;
     float gf, gc;
     uint32_t key0, key1, tag;

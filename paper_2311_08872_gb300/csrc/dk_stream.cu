@@ -252,7 +252,11 @@ __global__ void __launch_bounds__(kThreads) stream_observe_kernel(const SArgs a)
 #pragma unroll
     for (int i = 0; i < 2 * kMaxObs + 2; ++i) v[i] = 0.0;
     long long mf = 0, mc = 0;
-    float sf[kMaxObs] = {0.f, 0.f, 0.f, 0.f}, sc[kMaxObs] = {0.f, 0.f, 0.f, 0.f};
+    // FP64 products and sums against FP64 test functions (the integer
+    // fluctuations are exact in FP64): the projection of a rough fluctuation on
+    // a smooth phi is small, and FP32 rounding of phi or of the partial sums,
+    // uncorrelated with the noise, would reach 1e-5 of it on fine grids
+    double sf[kMaxObs] = {0.0, 0.0, 0.0, 0.0}, sc[kMaxObs] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
@@ -261,13 +265,14 @@ __global__ void __launch_bounds__(kThreads) stream_observe_kernel(const SArgs a)
             const int32_t qv = q[x];
             mf += qv;
             for (int k = 0; k < a.n_obs; ++k)
-                sf[k] = fmaf(__int2float_rn(qv - a.qbf[x]), a.phif[(size_t)k * n * n + x], sf[k]);
+                sf[k] = fma(static_cast<double>(qv - a.qbf[x]), a.phif64[(size_t)k * n * n + x], sf[k]);
         }
     if (a.coupled) {
         const size_t xc = (size_t)I * nc + J;
         const int32_t qv = a.qc[(a.M >> 2) & 1][(size_t)s * nc * nc + xc];
         mc = qv;
-        for (int k = 0; k < a.n_obs; ++k) sc[k] = __int2float_rn(qv - a.qbc[xc]) * a.phic[(size_t)k * nc * nc + xc];
+        for (int k = 0; k < a.n_obs; ++k)
+            sc[k] = static_cast<double>(qv - a.qbc[xc]) * a.phic64[(size_t)k * nc * nc + xc];
     }
 #pragma unroll
     for (int k = 0; k < kMaxObs; ++k) {

@@ -35,6 +35,7 @@ struct LevelTab {
     int32_t* d_q0 = nullptr;
     int32_t* d_qbar = nullptr;
     float* d_phi = nullptr;
+    double* d_phi64 = nullptr;             // the same test functions in FP64 (observables of the streamed path)
     std::vector<dk::VariantInfo> vis[2];   // kernel variants: [0] fine path only, [1] coupled pair
     int streamed = 0;                      // no register variant: state streamed through global memory
     int inflight = 0;                      // samples in flight on the streamed path (buffers sized for this)
@@ -267,6 +268,8 @@ int launch_streamed(mlmc_dk_ctx* c, int level, int stream_tag, int64_t first, in
     a.n_obs = c->n_obs;
     a.q0f = k.q0f; a.qbf = k.qbf; a.phif = k.phif;
     a.q0c = k.q0c; a.qbc = k.qbc; a.phic = k.phic;
+    a.phif64 = t.d_phi64;
+    a.phic64 = coupled ? c->lv[level - 1].d_phi64 : nullptr;
     a.Af = k.Af; a.Ac = k.Ac; a.gf = k.gf; a.gc = k.gc;
     a.key0 = k.key0; a.key1 = k.key1; a.tag = k.tag;
     a.err = c->d_err;
@@ -369,6 +372,7 @@ void release(mlmc_dk_ctx* c) {
         cudaFree(l.d_q0);
         cudaFree(l.d_qbar);
         cudaFree(l.d_phi);
+        cudaFree(l.d_phi64);
         cudaFree(l.d_stream);
         cudaFree(l.d_spart);
     }
@@ -546,6 +550,22 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
         }
         cudaFreeHost(stage);
         c->h2d_bytes += (int64_t)bytes;
+        {
+            // FP64 test functions for the streamed kernels' observables: there the
+            // fluctuation is projected on phi cell by cell at up to 1024^2, where FP32
+            // phi (relative rounding 2^-25 per value, uncorrelated with the noise)
+            // would reach 1e-5 of the projection
+            std::vector<double> ph64(cells * c->n_obs);
+            for (int k = 0; k < c->n_obs; ++k)
+                std::memcpy(ph64.data() + (size_t)k * cells, cfg->phi[(size_t)l * c->n_obs + k], sizeof(double) * cells);
+            if ((e = cudaMalloc(&t.d_phi64, sizeof(double) * ph64.size())) != cudaSuccess ||
+                (e = cudaMemcpy(t.d_phi64, ph64.data(), sizeof(double) * ph64.size(), cudaMemcpyHostToDevice)) !=
+                    cudaSuccess) {
+                mlmc_dk_free(c);
+                return cuda_fail(nullptr, e, "FP64 test functions");
+            }
+            c->h2d_bytes += (int64_t)(sizeof(double) * ph64.size());
+        }
         const bool force_stream = cfg->stream_from_n > 0 && t.n >= cfg->stream_from_n && t.n % 64 == 0;
         const int nv = force_stream ? 0 : dk::variant_count(t.n);
         if (nv == 0) {
