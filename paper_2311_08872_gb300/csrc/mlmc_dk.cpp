@@ -512,6 +512,13 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
         t.mass0 = mass;
         mean_field(t.n, t.h, t.tau, t.M, rho0, rbar.data());
         for (size_t i = 0; i < cells; ++i) qb[i] = (int32_t)std::llrint(std::ldexp(rbar[i], S));
+        // The quantised initial state q0 2^-S differs from rho0 by e0 (at most half
+        // a quantum per cell); the scheme is linear apart from sqrt([rho]^+), so e0
+        // reaches T as the noise-free evolution of e0 (exact, FP64 by FFT) and is
+        // removed from the observables with the mean-field offset below.
+        std::vector<double> e0(cells), e0T(cells);
+        for (size_t i = 0; i < cells; ++i) e0[i] = std::ldexp((double)q0[i], -S) - rho0[i];
+        mean_field(t.n, t.h, t.tau, t.M, e0.data(), e0T.data());
         std::vector<float> phif(cells * c->n_obs);
         for (int k = 0; k < c->n_obs; ++k) {
             const double* ph = cfg->phi[(size_t)l * c->n_obs + k];
@@ -519,7 +526,7 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
             double yb = 0, dl = 0;
             for (size_t i = 0; i < cells; ++i) {
                 yb += rbar[i] * ph[i];
-                dl += (std::ldexp((double)qb[i], -S) - rbar[i]) * ph[i];
+                dl += (std::ldexp((double)qb[i], -S) - rbar[i] - e0T[i]) * ph[i];
                 phif[(size_t)k * cells + i] = (float)ph[i];
             }
             t.ybar[k] = t.h * t.h * yb;
