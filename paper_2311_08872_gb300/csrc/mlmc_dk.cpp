@@ -911,7 +911,7 @@ int mlmc_dk_tune_batch(mlmc_dk_ctx* ctx, const int64_t* counts, int32_t repeats,
         if (ctx->lv[l].split_ok && counts[l] > 1) lvl = l;
     double best_f = 0.0;
     if (lvl >= 0) {
-        static const double kFractions[] = {0.0, 0.04, 0.08, 0.12, 0.16};
+        static const double kFractions[] = {0.0, 0.04, 0.06, 0.08, 0.10, 0.12, 0.16};
         double best_ms = 1e300;
         cudaError_t e;
         for (double f : kFractions) {
