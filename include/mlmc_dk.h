@@ -248,10 +248,12 @@ int mlmc_dk_set_batch_split(mlmc_dk_ctx* ctx, int32_t level, double fraction);
 
 /* Autotuner of the batch split: on the finest split-capable level with
  * counts[l] > 1, times the whole batch `counts` (sample ids from 0, results
- * discarded; CUDA events on the context's stream, `repeats` timed runs after a
- * warm-up per candidate) for fractions 0, 0.04 .. 0.12 in steps of 0.02, and 0.16, and keeps the
- * fastest (a larger share only when it is at least 1% faster).  *fraction and
- * *seconds (optional) receive the choice and the tuning time. */
+ * discarded; CUDA events on the context's stream; one untimed warm-up run,
+ * then `repeats` timed runs per candidate) for fractions 0, 0.04, 0.06, 0.08,
+ * 0.10, 0.12 and keeps the fastest (a larger share only when it is at least
+ * 1% faster).  Tune on the batch that will run: the best share depends on its
+ * size.  *fraction and *seconds (optional) receive the choice and the tuning
+ * time. */
 int mlmc_dk_tune_batch(mlmc_dk_ctx* ctx, const int64_t* counts, int32_t repeats, double* fraction, double* seconds);
 
 /* Host form of the multi-level batch: ids start at the largest next_sample

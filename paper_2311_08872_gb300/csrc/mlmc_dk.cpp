@@ -911,22 +911,33 @@ int mlmc_dk_tune_batch(mlmc_dk_ctx* ctx, const int64_t* counts, int32_t repeats,
         if (ctx->lv[l].split_ok && counts[l] > 1) lvl = l;
     double best_f = 0.0;
     if (lvl >= 0) {
-        static const double kFractions[] = {0.0, 0.04, 0.06, 0.08, 0.10, 0.12, 0.16};
+        static const double kFractions[] = {0.0, 0.04, 0.06, 0.08, 0.10, 0.12};
         double best_ms = 1e300;
         cudaError_t e;
+        auto time_batch = [&](double* ms) -> int {
+            if ((e = cudaEventRecord(ctx->ev0, ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "tune_batch");
+            int rc = mlmc_dk_run_batch_dev(ctx, counts, 0, 0x7475, ctx->d_bsums, ctx->stream);
+            if (rc != MLMC_DK_OK) return rc;
+            if ((e = cudaEventRecord(ctx->ev1, ctx->stream)) != cudaSuccess ||
+                (e = cudaEventSynchronize(ctx->ev1)) != cudaSuccess)
+                return cuda_fail(ctx, e, "tune_batch");
+            float t = 0.f;
+            cudaEventElapsedTime(&t, ctx->ev0, ctx->ev1);
+            *ms = t;
+            return MLMC_DK_OK;
+        };
+        // one untimed run warms the graph and the streamed path up
+        ctx->lv[lvl].split_frac = kFractions[1];
+        double warm = 0.0;
+        int rc = time_batch(&warm);
+        if (rc != MLMC_DK_OK) return rc;
         for (double f : kFractions) {
             ctx->lv[lvl].split_frac = f;
             double ms_min = 1e300;
-            for (int r = 0; r < repeats + 1; ++r) {
-                if ((e = cudaEventRecord(ctx->ev0, ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "tune_batch");
-                int rc = mlmc_dk_run_batch_dev(ctx, counts, 0, 0x7475, ctx->d_bsums, ctx->stream);
-                if (rc != MLMC_DK_OK) return rc;
-                if ((e = cudaEventRecord(ctx->ev1, ctx->stream)) != cudaSuccess ||
-                    (e = cudaEventSynchronize(ctx->ev1)) != cudaSuccess)
-                    return cuda_fail(ctx, e, "tune_batch");
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
-                if (r > 0 || repeats == 0) ms_min = std::min(ms_min, (double)ms);   // the first run warms up
+            for (int r = 0; r < repeats; ++r) {
+                double ms = 0.0;
+                if ((rc = time_batch(&ms)) != MLMC_DK_OK) return rc;
+                ms_min = std::min(ms_min, ms);
             }
             if (ms_min < 0.99 * best_ms) {   // a larger share only if clearly faster
                 best_ms = ms_min;

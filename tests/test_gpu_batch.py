@@ -102,5 +102,5 @@ def test_batch_split_runs_the_same_samples(dk):
             np.testing.assert_array_equal(g[:4], r[:4])
             _close(g[4], r[4])
         f, secs = ctx.tune_batch(counts, 1)
-        assert f in (0.0, 0.04, 0.06, 0.08, 0.10, 0.12, 0.16) and secs > 0
+        assert f in (0.0, 0.04, 0.06, 0.08, 0.10, 0.12) and secs > 0
         assert ctx.level_info(4).split_fraction == f
