@@ -290,7 +290,9 @@ int mlmc_dk_run_level_static(const mlmc_dk_ctx* ctx, int32_t level, int32_t stre
                              unsigned int* err_dev, void* cuda_stream);
 
 /* Algorithm 1 (Section 7.1): start at L = L_start with `pilot` samples on
- * levels 0..L; repeat {run the missing samples, re-estimate V_l, set targets by
+ * levels 0..L; repeat {run the missing samples (all levels of a round at once
+ * through the multi-level batch, ids continuing each level's range from 0),
+ * re-estimate V_l, set targets by
  * Eq. (opt_M_ell), once no level needs samples apply Eq.
  * (convergence_criterion) with alpha = 2 and add a level if it fails}.  The
  * first quantity drives the allocation; eps is absolute, or relative to the

@@ -790,15 +790,15 @@ int mlmc_dk_run_level_static(const mlmc_dk_ctx* ctx, int32_t level, int32_t stre
     return MLMC_DK_OK;
 }
 
-int mlmc_dk_run_batch_dev(mlmc_dk_ctx* ctx, const int64_t* counts, int64_t first_sample, uint64_t seed,
-                          double* sums_dev, void* cuda_stream) {
-    if (!ctx) return fail(nullptr, MLMC_DK_ERR_INVALID, "null context");
-    if (!counts || !sums_dev || ((uintptr_t)sums_dev & 7) || first_sample < 0)
-        return fail(ctx, MLMC_DK_ERR_INVALID, "run_batch_dev: bad arguments");
+}  // extern "C"
+
+namespace {
+
+// The multi-level batch with sample ids firsts[l].. on level l (the public
+// entry points check the arguments).
+int batch_dev(mlmc_dk_ctx* ctx, const int64_t* counts, const int64_t* firsts, uint64_t seed, double* sums_dev,
+              cudaStream_t st) {
     const int nl = ctx->L_max + 1;
-    for (int l = 0; l < nl; ++l)
-        if (counts[l] < 0) return fail(ctx, MLMC_DK_ERR_INVALID, "run_batch_dev: negative count");
-    cudaStream_t st = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : ctx->stream;
     cudaError_t e;
     // split: the last n_split[l] ids of a split level run streamed beside the graph
     std::vector<int64_t> n_split(nl, 0), n_reg(counts, counts + nl);
@@ -825,7 +825,7 @@ int mlmc_dk_run_batch_dev(mlmc_dk_ctx* ctx, const int64_t* counts, int64_t first
         // external records become event-record nodes of the graph (timing)
         if ((e = cudaEventRecordWithFlags(ctx->ev_lb[l], ctx->lstream[l], cudaEventRecordExternal)) != cudaSuccess)
             break;
-        rc = launch_batch_into(ctx, l, 0, first_sample, n_reg[l], seed, out, nullptr, ctx->lstream[l],
+        rc = launch_batch_into(ctx, l, 0, firsts[l], n_reg[l], seed, out, nullptr, ctx->lstream[l],
                                ctx->d_lpart[l], ctx->lpart_cap[l], ctx->lprio[l]);
         if (rc != MLMC_DK_OK) break;
         if ((e = cudaEventRecordWithFlags(ctx->ev_le[l], ctx->lstream[l], cudaEventRecordExternal)) != cudaSuccess)
@@ -869,7 +869,7 @@ int mlmc_dk_run_batch_dev(mlmc_dk_ctx* ctx, const int64_t* counts, int64_t first
     if (any_split) {
         for (int l = nl - 1; l >= 0; --l) {
             if (n_split[l] == 0) continue;
-            rc = launch_streamed(ctx, l, 0, first_sample + n_reg[l], n_split[l], seed,
+            rc = launch_streamed(ctx, l, 0, firsts[l] + n_reg[l], n_split[l], seed,
                                  ctx->d_ssums + (size_t)l * ctx->stride, nullptr, ctx->sstream, 0, 0);
             if (rc != MLMC_DK_OK) return rc;
         }
@@ -885,11 +885,28 @@ int mlmc_dk_run_batch_dev(mlmc_dk_ctx* ctx, const int64_t* counts, int64_t first
     for (int l = nl - 1; l >= 0; --l) {
         if (!ctx->lv[l].streamed) continue;
         if ((e = cudaEventRecord(ctx->ev_lb[l], st)) != cudaSuccess) return cuda_fail(ctx, e, "cudaEventRecord");
-        rc = launch_streamed(ctx, l, 0, first_sample, counts[l], seed, sums_dev + (size_t)l * ctx->stride, nullptr, st);
+        rc = launch_streamed(ctx, l, 0, firsts[l], counts[l], seed, sums_dev + (size_t)l * ctx->stride, nullptr, st);
         if (rc != MLMC_DK_OK) return rc;
         if ((e = cudaEventRecord(ctx->ev_le[l], st)) != cudaSuccess) return cuda_fail(ctx, e, "cudaEventRecord");
     }
     return MLMC_DK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mlmc_dk_run_batch_dev(mlmc_dk_ctx* ctx, const int64_t* counts, int64_t first_sample, uint64_t seed,
+                          double* sums_dev, void* cuda_stream) {
+    if (!ctx) return fail(nullptr, MLMC_DK_ERR_INVALID, "null context");
+    if (!counts || !sums_dev || ((uintptr_t)sums_dev & 7) || first_sample < 0)
+        return fail(ctx, MLMC_DK_ERR_INVALID, "run_batch_dev: bad arguments");
+    const int nl = ctx->L_max + 1;
+    for (int l = 0; l < nl; ++l)
+        if (counts[l] < 0) return fail(ctx, MLMC_DK_ERR_INVALID, "run_batch_dev: negative count");
+    cudaStream_t st = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : ctx->stream;
+    std::vector<int64_t> firsts(nl, first_sample);
+    return batch_dev(ctx, counts, firsts.data(), seed, sums_dev, st);
 }
 
 int mlmc_dk_set_batch_split(mlmc_dk_ctx* ctx, int32_t level, double fraction) {
@@ -1087,6 +1104,47 @@ int mlmc_dk_plan(int32_t L, const int64_t* n, const double* s1, const double* s2
     return MLMC_DK_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// One round of Algorithm 1: need[l] samples with ids firsts[l].. on every level
+// through the batch graph, accumulated into sums[l][quantity] with each level's
+// own device span; next_sample follows.
+int run_round(mlmc_dk_ctx* ctx, const int64_t* need, const int64_t* firsts, uint64_t seed,
+              std::vector<std::vector<mlmc_dk_level_sums>>& sums) {
+    const int nl = ctx->L_max + 1;
+    const auto t0 = std::chrono::steady_clock::now();
+    int rc = batch_dev(ctx, need, firsts, seed, ctx->d_bsums, ctx->stream);
+    if (rc != MLMC_DK_OK) return rc;
+    cudaError_t e = cudaMemcpyAsync(ctx->h_bsums, ctx->d_bsums, sizeof(double) * ctx->stride * nl,
+                                    cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "Algorithm 1 round");
+    if ((rc = check_device_error(ctx)) != MLMC_DK_OK) return rc;
+    const double wall = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    int active = 0;
+    for (int l = 0; l < nl; ++l) active += need[l] > 0;
+    for (int l = 0; l < nl; ++l) {
+        if (need[l] == 0) continue;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ctx->ev_lb[l], ctx->ev_le[l]) != cudaSuccess) {
+            cudaGetLastError();
+            ms = 0.f;
+        }
+        const LevelTab& f = ctx->lv[l];
+        double cost = (double)f.n * f.n * f.M;
+        if (l > 0) cost += (double)ctx->lv[l - 1].n * ctx->lv[l - 1].n * ctx->lv[l - 1].M;
+        accumulate(ctx, ctx->h_bsums + (size_t)l * ctx->stride, sums[l].data(), cost, wall / active, 1e-3 * ms, 2);
+        ctx->next_id[0][l] = firsts[l] + need[l];
+    }
+    return MLMC_DK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 int mlmc_dk_estimate(mlmc_dk_ctx* ctx, double eps, int32_t relative, uint64_t seed, mlmc_dk_result* out) {
     if (!ctx || !out || !(eps > 0)) return fail(ctx, MLMC_DK_ERR_INVALID, "estimate: bad arguments");
     const auto t0 = std::chrono::steady_clock::now();
@@ -1106,10 +1164,18 @@ int mlmc_dk_estimate(mlmc_dk_ctx* ctx, double eps, int32_t relative, uint64_t se
         cost[l] = li.cost;
     }
     for (int iter = 0; iter < 1000; ++iter) {
-        for (int l = 0; l <= L; ++l) {
-            const int64_t need = target[l] - sums[l][0].n;
-            if (need > 0) {
-                const int rc = mlmc_dk_run_level(ctx, l, need, seed, sums[l].data());
+        {
+            // the round's missing samples of every level at once: the levels run
+            // concurrently in the batch graph, ids continuing each level's range
+            std::vector<int64_t> need(ctx->L_max + 1, 0), firsts(ctx->L_max + 1, 0);
+            bool any = false;
+            for (int l = 0; l <= L; ++l) {
+                firsts[l] = sums[l][0].n;
+                need[l] = std::max<int64_t>(0, target[l] - sums[l][0].n);
+                any = any || need[l] > 0;
+            }
+            if (any) {
+                const int rc = run_round(ctx, need.data(), firsts.data(), seed, sums);
                 if (rc != MLMC_DK_OK) return rc;
             }
         }
