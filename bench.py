@@ -263,6 +263,7 @@ def oracle_rate(wl, alloc, budget_s, cores=None):
               f"levels {[l for l in range(len(alloc)) if l not in t]} extrapolated by cell-steps from level {top}")
     return {"value": sample_steps / cpu_time, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": sample, "cell_steps_per_s": cell_steps / cpu_time,
+            "cell_steps_per_s_per_core": cell_steps / cpu_time / cores,
             "batch_cpu_s": cpu_time, "wall_s": wall}
 
 
