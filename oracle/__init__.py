@@ -8,7 +8,8 @@ arrays.
 
 Contents, each following the paper (Cornalba & Fischer, arXiv 2311.08872):
   * ``liboracle_dk.so`` (dk_oracle.c): Philox4x32-10, Box--Muller normals, one
-    step of Eq. (FullyDiscreteDK) with b0=0, b1=1 (Section 7.2), the
+    step of Eq. (FullyDiscreteDK) with b0=0, b1=1 (Section 7.2) and with
+    general weights b0 + b1 = 1 (theta-scheme, exact periodic solve), the
     Right-Most NN coupled pair of Section 3.2, the discrete mean field.
   * ``level_table``: the CFL-linked level hierarchy of Eq. (cfl_preserved)
     with h_{l-1} = 2 h_l, tau_{l-1} = 4 tau_l (Section 7.2).
@@ -50,6 +51,7 @@ class _OracleLevelC(ctypes.Structure):
         ("n_obs", ctypes.c_int),
         ("phi_f", _dp),
         ("phi_c", _dp),
+        ("b0", ctypes.c_double),
     ]
 
 
@@ -75,6 +77,11 @@ def lib():
         L.oracle_sample_given.restype = ctypes.c_int
         L.oracle_mean_field.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
                                         _dp, _dp]
+        L.oracle_theta_step.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_double, _dp, _dp, _dp]
+        L.oracle_helmholtz_solve.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp]
+        L.oracle_mean_field_theta.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
+                                              ctypes.c_double, _dp, _dp]
         _LIB = L
     return _LIB
 
@@ -113,11 +120,33 @@ def dk_step(n: int, h: float, tau: float, inv_sqrt_N: float, rho: np.ndarray,
     return out
 
 
-def mean_field(n: int, h: float, tau: float, M: int, rho0: np.ndarray) -> np.ndarray:
-    """The discrete mean field rho-bar: the noise-free scheme iterated M times."""
+def theta_step(n: int, h: float, tau: float, inv_sqrt_N: float, b0: float, rho: np.ndarray,
+               dbeta: Optional[np.ndarray]) -> np.ndarray:
+    """One step of Eq. (FullyDiscreteDK) with weights (b0, 1 - b0)."""
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    out = np.empty_like(rho)
+    db = None if dbeta is None else np.ascontiguousarray(dbeta, dtype=np.float64)
+    lib().oracle_theta_step(n, h, tau, inv_sqrt_N, b0, _ptr(rho), _ptr(db), _ptr(out))
+    return out
+
+
+def helmholtz_solve(n: int, c: float, rhs: np.ndarray) -> np.ndarray:
+    """(I + c L)^{-1} rhs on the periodic grid, L = -h^2 Delta_h (5-point)."""
+    rhs = np.ascontiguousarray(rhs, dtype=np.float64)
+    out = np.empty_like(rhs)
+    lib().oracle_helmholtz_solve(n, c, _ptr(rhs), _ptr(out))
+    return out
+
+
+def mean_field(n: int, h: float, tau: float, M: int, rho0: np.ndarray, b0: float = 0.0) -> np.ndarray:
+    """The discrete mean field rho-bar: the noise-free scheme iterated M times
+    (weights (b0, 1 - b0) of Eq. FullyDiscreteDK)."""
     rho0 = np.ascontiguousarray(rho0, dtype=np.float64)
     out = np.empty_like(rho0)
-    lib().oracle_mean_field(n, h, tau, M, _ptr(rho0), _ptr(out))
+    if b0 == 0.0:
+        lib().oracle_mean_field(n, h, tau, M, _ptr(rho0), _ptr(out))
+    else:
+        lib().oracle_mean_field_theta(n, h, tau, M, b0, _ptr(rho0), _ptr(out))
     return out
 
 
@@ -154,9 +183,11 @@ class OracleLevel:
     """Inputs of one level for the C oracle (arrays kept alive here)."""
 
     def __init__(self, lv: Level, N: float, rho0_f: np.ndarray, phi_f: Sequence[np.ndarray],
-                 rho0_c: Optional[np.ndarray] = None, phi_c: Optional[Sequence[np.ndarray]] = None):
+                 rho0_c: Optional[np.ndarray] = None, phi_c: Optional[Sequence[np.ndarray]] = None,
+                 b0: float = 0.0):
         self.lv = lv
         self.N = N
+        self.b0 = float(b0)
         self.n_obs = len(phi_f)
         self.rho0_f = np.ascontiguousarray(rho0_f, dtype=np.float64).reshape(-1)
         self.phi_f = np.ascontiguousarray(np.stack(phi_f), dtype=np.float64)
@@ -165,7 +196,7 @@ class OracleLevel:
         self.c = _OracleLevelC(lv.n, lv.h, lv.tau, lv.M, lv.level,
                                0.0 if not N else 1.0 / math.sqrt(N),
                                _ptr(self.rho0_f), _ptr(self.rho0_c), self.n_obs,
-                               _ptr(self.phi_f), _ptr(self.phi_c))
+                               _ptr(self.phi_f), _ptr(self.phi_c), self.b0)
 
     def sample(self, seed: int, sample: int, coupled: bool, stream: int = 0, fields: bool = False):
         n = self.lv.n
@@ -229,16 +260,16 @@ class OracleLevel:
 
 
 def level_inputs(length: float, levels: List[Level], N: float, rho0: List[np.ndarray],
-                 phi: List[List[np.ndarray]], level: int, coupled: bool) -> OracleLevel:
+                 phi: List[List[np.ndarray]], level: int, coupled: bool, b0: float = 0.0) -> OracleLevel:
     lv = levels[level]
     if coupled and level > 0:
-        return OracleLevel(lv, N, rho0[level], phi[level], rho0[level - 1], phi[level - 1])
-    return OracleLevel(lv, N, rho0[level], phi[level])
+        return OracleLevel(lv, N, rho0[level], phi[level], rho0[level - 1], phi[level - 1], b0=b0)
+    return OracleLevel(lv, N, rho0[level], phi[level], b0=b0)
 
 
 def _run_chunk(args):
-    (lv, N, rho0_f, phi_f, rho0_c, phi_c, seed, ids, coupled, stream) = args
-    ol = OracleLevel(lv, N, rho0_f, phi_f, rho0_c, phi_c)
+    (lv, N, rho0_f, phi_f, rho0_c, phi_c, seed, ids, coupled, stream, b0) = args
+    ol = OracleLevel(lv, N, rho0_f, phi_f, rho0_c, phi_c, b0=b0)
     res = [ol.sample(seed, int(i), coupled, stream) for i in ids]
     return res
 
@@ -256,7 +287,7 @@ def run_samples(ol: OracleLevel, seed: int, ids: Sequence[int], coupled: bool, s
         import multiprocessing as mp
         chunks = [ids[i::processes] for i in range(processes)]
         args = [(ol.lv, ol.N, ol.rho0_f, list(ol.phi_f), ol.rho0_c,
-                 None if ol.phi_c is None else list(ol.phi_c), seed, c, coupled, stream)
+                 None if ol.phi_c is None else list(ol.phi_c), seed, c, coupled, stream, ol.b0)
                 for c in chunks if c]
         with mp.get_context("spawn").Pool(len(args)) as pool:
             parts = pool.map(_run_chunk, args)
@@ -315,14 +346,17 @@ def mlmc_estimator(sums_dp: Sequence[float], counts: Sequence[int]) -> float:
 
 
 # ----------------------------------------------------------- closed forms
-def heat_symbol(k: Sequence[int], n: int, mu: float) -> float:
+def heat_symbol(k: Sequence[int], n: int, mu: float, b0: float = 0.0) -> float:
     """Per-step factor of the noise-free scheme on the discrete Fourier mode
-    exp(2 pi i k.x / L): 1 - 2 (tau/h^2) (sin^2(pi k1/n) + sin^2(pi k2/n)),
-    from Delta_h of Section 7.2 acting on the mode."""
-    return 1.0 - 2.0 * mu * (math.sin(math.pi * k[0] / n) ** 2 + math.sin(math.pi * k[1] / n) ** 2)
+    exp(2 pi i k.x / L): with lam = 2 (tau/h^2) (sin^2(pi k1/n) + sin^2(pi k2/n))
+    (tau/2 Delta_h of Section 7.2 acting on the mode is -lam), the weights
+    (b0, b1 = 1 - b0) of Eq. (FullyDiscreteDK) give (1 - b1 lam) / (1 + b0 lam):
+    the symbol of A_h in Appendix C (Lemma Discrete_Energy_Est)."""
+    lam = 2.0 * mu * (math.sin(math.pi * k[0] / n) ** 2 + math.sin(math.pi * k[1] / n) ** 2)
+    return (1.0 - (1.0 - b0) * lam) / (1.0 + b0 * lam)
 
 
-def closed_form_EP_cos1(length: float, n: int, tau: float, M: int, mass: float = 1.0) -> float:
+def closed_form_EP_cos1(length: float, n: int, tau: float, M: int, mass: float = 1.0, b0: float = 0.0) -> float:
     """E[P] for phi = cos(2 pi x1 / L) while rho stays positive, when the mean
     field minus its average is orthogonal to sin^2(2 pi x1 / L) at every step
     (e.g. rho0 = mass/L^2 (1 + a sin sin)).
@@ -332,8 +366,15 @@ def closed_form_EP_cos1(length: float, n: int, tau: float, M: int, mass: float =
     N^-1 tau ([rho^m]^+, |nabla^c_h phi^{m+1}|^2)_h.  For this phi,
     |nabla^c_h phi^{m+1}|^2 = g^{2(M-m-1)} sin^2(2 pi x1/L) (sin(2 pi h/L)/h)^2,
     so E[P] = mass (tau/2)(sin(2 pi h/L)/h)^2 (1 - g^{2M}) / (1 - g^2) with
-    g = 1 - 2 (tau/h^2) sin^2(pi/n)."""
+    g = 1 - 2 (tau/h^2) sin^2(pi/n).
+
+    With b0 > 0 the noise of a step reaches rho through
+    H = (I - b0 tau/2 Delta_h)^{-1}, so the increment pairs it with
+    H phi^{m+1} = w phi^{m+1}, w = 1 / (1 + b0 lam), lam = 2 (tau/h^2) sin^2(pi/n),
+    and g is the symbol (1 - b1 lam) / (1 + b0 lam): E[P] gains the factor w^2."""
     h = length / n
-    g = heat_symbol((1, 0), n, tau / (h * h))
+    mu = tau / (h * h)
+    g = heat_symbol((1, 0), n, mu, b0)
+    w = 1.0 / (1.0 + b0 * 2.0 * mu * math.sin(math.pi / n) ** 2)
     s = math.sin(2.0 * math.pi * h / length) / h
-    return mass * 0.5 * tau * s * s * (1.0 - g ** (2 * M)) / (1.0 - g * g)
+    return mass * 0.5 * tau * s * s * w * w * (1.0 - g ** (2 * M)) / (1.0 - g * g)

@@ -75,8 +75,10 @@ void oracle_normals(uint64_t seed, int level, int stream, uint64_t sample, int64
 /* -------------------------------------------------------------------- step */
 static inline int wrap(int i, int n) { return (i % n + n) % n; }
 
-void oracle_dk_step(int n, double h, double tau, double inv_sqrt_N,
-                    const double* rho, const double* dbeta, double* out)
+/* rho + w tau/2 Delta_h rho + inv_sqrt_N div_h(F): the explicit right-hand
+ * side of Eq. (FullyDiscreteDK) with diffusion weight w (w = b1). */
+static void explicit_part(int n, double h, double tau, double w, double inv_sqrt_N,
+                          const double* rho, const double* dbeta, double* out)
 {
     const int d = 2;
     const double h_pow = pow(h, -0.5 * d);   /* h^{-d/2}: grid white-noise basis scale */
@@ -97,7 +99,7 @@ void oracle_dk_step(int n, double h, double tau, double inv_sqrt_N,
             int left = i1 * n + wrap(i2 - 1, n), right = i1 * n + wrap(i2 + 1, n);
             /* Delta_h a(x) = (-4 a(x) + sum_{y~x} a(y)) / h^2 */
             double lap = (-4.0 * rho[x] + rho[up] + rho[down] + rho[left] + rho[right]) / (h * h);
-            double value = rho[x] + tau * 0.5 * lap;
+            double value = rho[x] + w * tau * 0.5 * lap;
             if (F) {
                 /* nabla_h . b(x) = sum_r ([b]_r(x + h f_r) - [b]_r(x - h f_r)) / (2h) */
                 double div = (F[2 * down + 0] - F[2 * up + 0]) / (2.0 * h) +
@@ -108,6 +110,102 @@ void oracle_dk_step(int n, double h, double tau, double inv_sqrt_N,
         }
     }
     free(F);
+}
+
+void oracle_dk_step(int n, double h, double tau, double inv_sqrt_N,
+                    const double* rho, const double* dbeta, double* out)
+{
+    explicit_part(n, h, tau, 1.0, inv_sqrt_N, rho, dbeta, out);
+}
+
+/* Separable discrete Fourier transform of an n x n array held as (re, im):
+ * a(k) = sum_x a(x) exp(sign 2 pi i k.x / n), along i2 for every row and then
+ * along i1 for every column; cs/sn hold cos/sin(2 pi j / n). */
+static void dft2(int n, int sign, const double* cs, const double* sn, double* re, double* im)
+{
+    double* tr = (double*)malloc(sizeof(double) * (size_t)n);
+    double* ti = (double*)malloc(sizeof(double) * (size_t)n);
+    for (int axis = 0; axis < 2; ++axis) {
+        for (int line = 0; line < n; ++line) {
+            /* element j of this line sits at base + j * step */
+            const int base = axis == 0 ? line * n : line, step = axis == 0 ? 1 : n;
+            for (int k = 0; k < n; ++k) {
+                double sr = 0.0, si = 0.0;
+                for (int j = 0; j < n; ++j) {
+                    const int t = (int)(((int64_t)k * j) % n);
+                    const double c = cs[t], s = sign * sn[t];
+                    const double ar = re[base + j * step], ai = im[base + j * step];
+                    sr += ar * c - ai * s;
+                    si += ar * s + ai * c;
+                }
+                tr[k] = sr;
+                ti[k] = si;
+            }
+            for (int k = 0; k < n; ++k) {
+                re[base + k * step] = tr[k];
+                im[base + k * step] = ti[k];
+            }
+        }
+    }
+    free(tr);
+    free(ti);
+}
+
+void oracle_helmholtz_solve(int n, double c, const double* rhs, double* out)
+{
+    /* Every mode exp(2 pi i k.x / n) is an eigenvector of L with eigenvalue
+     * 4 (sin^2(pi k1/n) + sin^2(pi k2/n)): transform, divide, transform back. */
+    const size_t cells = (size_t)n * n;
+    double* re = (double*)malloc(sizeof(double) * cells);
+    double* im = (double*)calloc(cells, sizeof(double));
+    double* cs = (double*)malloc(sizeof(double) * (size_t)n);
+    double* sn = (double*)malloc(sizeof(double) * (size_t)n);
+    for (int j = 0; j < n; ++j) {
+        cs[j] = cos(2.0 * M_PI * j / n);
+        sn[j] = sin(2.0 * M_PI * j / n);
+    }
+    memcpy(re, rhs, sizeof(double) * cells);
+    dft2(n, -1, cs, sn, re, im);
+    for (int k1 = 0; k1 < n; ++k1)
+        for (int k2 = 0; k2 < n; ++k2) {
+            const double s1 = sin(M_PI * k1 / n), s2 = sin(M_PI * k2 / n);
+            const double lam = 4.0 * (s1 * s1 + s2 * s2);
+            re[k1 * n + k2] /= 1.0 + c * lam;
+            im[k1 * n + k2] /= 1.0 + c * lam;
+        }
+    dft2(n, +1, cs, sn, re, im);
+    for (size_t x = 0; x < cells; ++x) out[x] = re[x] / (double)cells;
+    free(re); free(im); free(cs); free(sn);
+}
+
+void oracle_theta_step(int n, double h, double tau, double inv_sqrt_N, double b0,
+                       const double* rho, const double* dbeta, double* out)
+{
+    const double b1 = 1.0 - b0;
+    if (b0 == 0.0) {
+        explicit_part(n, h, tau, 1.0, inv_sqrt_N, rho, dbeta, out);
+        return;
+    }
+    double* rhs = (double*)malloc(sizeof(double) * (size_t)n * n);
+    explicit_part(n, h, tau, b1, inv_sqrt_N, rho, dbeta, rhs);
+    /* I - b0 tau/2 Delta_h = I + c L with c = b0 tau / (2 h^2) */
+    oracle_helmholtz_solve(n, b0 * tau / (2.0 * h * h), rhs, out);
+    free(rhs);
+}
+
+void oracle_mean_field_theta(int n, double h, double tau, int64_t M, double b0, const double* rho0,
+                             double* out)
+{
+    double* a = (double*)malloc(sizeof(double) * (size_t)n * n);
+    double* b = (double*)malloc(sizeof(double) * (size_t)n * n);
+    memcpy(a, rho0, sizeof(double) * (size_t)n * n);
+    for (int64_t m = 0; m < M; ++m) {
+        oracle_theta_step(n, h, tau, 0.0, b0, a, NULL, b);
+        double* t = a; a = b; b = t;
+    }
+    memcpy(out, a, sizeof(double) * (size_t)n * n);
+    free(a);
+    free(b);
 }
 
 void oracle_mean_field(int n, double h, double tau, int64_t M, const double* rho0, double* out)
@@ -198,11 +296,11 @@ static int sample_impl(const oracle_level* lv, uint64_t seed, int stream, uint64
                     dbeta_c[2 * y + 1] += block_weight * dbeta_f[2 * z + 1];
                 }
         }
-        oracle_dk_step(n, lv->h, lv->tau, lv->inv_sqrt_N, rho_f, dbeta_f, tmp_f);
+        oracle_theta_step(n, lv->h, lv->tau, lv->inv_sqrt_N, lv->b0, rho_f, dbeta_f, tmp_f);
         double* t = rho_f; rho_f = tmp_f; tmp_f = t;
         if (amp > 0.0) perturb_edges(n, amp, &pstate, rho_f);
         if (coupled && (m % 4) == 3) {
-            oracle_dk_step(nc, 2.0 * lv->h, 4.0 * lv->tau, lv->inv_sqrt_N, rho_c, dbeta_c, tmp_c);
+            oracle_theta_step(nc, 2.0 * lv->h, 4.0 * lv->tau, lv->inv_sqrt_N, lv->b0, rho_c, dbeta_c, tmp_c);
             double* tc = rho_c; rho_c = tmp_c; tmp_c = tc;
             memset(dbeta_c, 0, sizeof(double) * cc * 2);
             if (amp > 0.0) perturb_edges(nc, amp, &pstate, rho_c);

@@ -9,6 +9,8 @@
  * paper (Cornalba & Fischer, "Multilevel Monte Carlo methods for the
  * Dean--Kawasaki equation from Fluctuating Hydrodynamics"):
  *   - Definition 2.1, Eq. (FullyDiscreteDK) with b0 = 0, b1 = 1 (Section 7.2),
+ *     and with general weights b0 + b1 = 1 (the theta-scheme: an implicit
+ *     diffusion half, Definition 2.1 and Appendix C, Lemma Discrete_Energy_Est),
  *   - the operators Delta_h and nabla_h. of Section 7.2,
  *   - the Right-Most Nearest-Neighbour coupling of Section 3.2,
  *   - the observable P_l of Eq. (eqn_MLMCLevels) with psi(x) = x^2.
@@ -50,6 +52,18 @@ void oracle_normals(uint64_t seed, int level, int stream, uint64_t sample, int64
 void oracle_dk_step(int n, double h, double tau, double inv_sqrt_N,
                     const double* rho, const double* dbeta, double* out);
 
+/* One step of Eq. (FullyDiscreteDK) with weights b0 >= 0, b1 = 1 - b0:
+ *   (I - b0 tau/2 Delta_h) out = (I + b1 tau/2 Delta_h) rho + inv_sqrt_N * div_h( F ),
+ * F as in oracle_dk_step (the noise is explicit: it uses rho).  The linear
+ * system is periodic and solved exactly by discrete Fourier diagonalisation
+ * (oracle_helmholtz_solve).  b0 = 0 gives oracle_dk_step. */
+void oracle_theta_step(int n, double h, double tau, double inv_sqrt_N, double b0,
+                       const double* rho, const double* dbeta, double* out);
+
+/* out = (I + c L)^{-1} rhs on the periodic n x n grid, where
+ * L a(x) = 4 a(x) - sum_{y~x} a(y) = -h^2 Delta_h a (c >= 0). */
+void oracle_helmholtz_solve(int n, double c, const double* rhs, double* out);
+
 typedef struct {
     int n;               /* fine cells per axis (even) */
     double h;            /* fine mesh size */
@@ -62,10 +76,12 @@ typedef struct {
     int n_obs;
     const double* phi_f; /* [n_obs][n*n] */
     const double* phi_c; /* [n_obs][(n/2)^2] */
+    double b0;           /* implicit weight of Eq. (FullyDiscreteDK) (0: explicit Euler--Maruyama) */
 } oracle_level;
 
 /* One sample of level `lv`: fine path, and if `coupled` the NN-coupled coarse
- * path (mesh 2h, step 4 tau, increments summed over 2x2 cells and 4 steps).
+ * path (mesh 2h, step 4 tau, increments summed over 2x2 cells and 4 steps);
+ * both paths step with oracle_theta_step and the level's b0.
  * Outputs Y_f[k] = (rho_f^M, phi_f[k])_h, Y_c[k] likewise on the coarse grid,
  * masses (rho, 1)_h, and optionally the final fields.  Returns 0 on success. */
 int oracle_sample(const oracle_level* lv, uint64_t seed, int stream, uint64_t sample,
@@ -96,6 +112,10 @@ int oracle_sample_perturbed(const oracle_level* lv, uint64_t seed, int stream, u
 /* Noise-free scheme (the discrete mean field rho-bar of Eq. (eqn_MLMCLevels))
  * iterated M times from rho0. */
 void oracle_mean_field(int n, double h, double tau, int64_t M, const double* rho0, double* out);
+
+/* Same for the weights (b0, 1 - b0): oracle_theta_step without noise, M times. */
+void oracle_mean_field_theta(int n, double h, double tau, int64_t M, double b0, const double* rho0,
+                             double* out);
 
 #ifdef __cplusplus
 }
