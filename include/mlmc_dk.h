@@ -90,7 +90,8 @@ typedef struct {
     int32_t n0;             /* level-0 cells per axis: a power of two in [4, 1024] */
     int32_t L_max;          /* finest level index, n0 << L_max <= 1024 */
     double T;               /* final time */
-    double cfl_mu;          /* nominal tau/h^2 (<= 1/2): M_0 = ceil(T/(mu h0^2)), tau_0 = T/M_0 */
+    double cfl_mu;          /* nominal tau/h^2 (<= 1/2 for the explicit scheme): M_0 = ceil(T/(mu h0^2)),
+                               tau_0 = T/M_0 */
     int32_t M0;             /* > 0: use this M_0 instead (tau_0 = T/M_0) */
     double N;               /* particle number; 0 switches the noise off */
     const double* const* rho0; /* [L_max+1] host arrays: rho0[l] = I_{h_l} rho-bar_0, n_l^2 values */
@@ -102,6 +103,15 @@ typedef struct {
     void* cuda_stream;      /* cudaStream_t for all device work, or NULL (legacy default stream) */
     int32_t stream_from_n;  /* 0: stream the state only where no register kernel exists (n >= 512);
                                k > 0: also for every level with n >= k (n a multiple of 64) */
+    double theta_b0;        /* implicit weight b0 in [0, 1] of Eq. (FullyDiscreteDK), b1 = 1 - b0
+                               (Definition 2.1): (I - b0 tau/2 Delta_h) rho^m = (I + b1 tau/2 Delta_h)
+                               rho^(m-1) + noise.  0: explicit Euler--Maruyama (Section 7.2).  b0 > 0
+                               runs every level on the theta-scheme kernel (n0 2^L_max <= 64, no
+                               stream_from_n); cfl_mu may then exceed 1/2 up to the scheme's
+                               stability bound 1 / (2 (b1 - b0)) (none for b0 >= 1/2), with
+                               b0 cfl_mu <= 10 */
+    int32_t theta_kernel;   /* 1: run b0 = 0 on the theta-scheme kernel too (the same integer
+                               arithmetic as the explicit kernels); 0: default */
 } mlmc_dk_config;
 
 /* Per-level description returned by mlmc_dk_level_info. */
@@ -127,6 +137,9 @@ typedef struct {
                                shared with the streamed kernels (mlmc_dk_set_batch_split) */
     double split_fraction;  /* share of this level's batch samples run on the streamed kernels */
     int64_t batch_streamed; /* samples of the last multi-level batch that ran on the streamed kernels */
+    int32_t theta;          /* 1: the level runs on the theta-scheme kernel */
+    double theta_b0;        /* its implicit weight b0 */
+    int32_t cheb_steps;     /* Chebyshev steps per implicit solve (0: none) */
 } mlmc_dk_level_desc;
 
 /* Host-side moment sums of one quantity on one level (accumulated into). */

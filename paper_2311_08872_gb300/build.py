@@ -1,7 +1,7 @@
 """Build ``libmlmc_dk.so`` in-tree with nvcc for sm_103a.
 
-Two translation units (the CUDA kernels and the host runtime) compile in
-parallel and link into one shared library with the CUDA runtime linked
+The translation units (the CUDA kernel files and the host runtime) compile
+in parallel and link into one shared library with the CUDA runtime linked
 statically, so the library only needs the driver at run time.
 """
 from __future__ import annotations
@@ -19,7 +19,7 @@ LIB = os.path.join(PKG, "libmlmc_dk.so")
 BUILD_DIR = os.path.join(ROOT, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["dk_kernels.cu", "dk_stream.cu", "dk_surrogate.cu", "mlmc_dk.cpp"]
+SOURCES = ["dk_kernels.cu", "dk_stream.cu", "dk_surrogate.cu", "dk_theta.cu", "mlmc_dk.cpp"]
 HEADERS = ["dk_kernels.h", "dk_device.cuh"]
 
 

@@ -110,6 +110,25 @@ void stream_carve(SArgs* a, void* buf, int n, int S);
 // k.samples; the caller reduces the S slots.
 cudaError_t stream_run(const KArgs& k, SArgs a, int S, int variant, cudaStream_t stream);
 
+// ---- theta-scheme (implicit diffusion weight b0 > 0), grids up to 64 x 64
+constexpr int kMaxCheb = 64;   // largest number of Chebyshev steps per solve
+struct TArgs {
+    int K;                     // Chebyshev steps per solve (0: the explicit step)
+    float alpha;               // b0 tau / (2 h^2), the same on every level
+    float inv_theta;           // 1 / (1 + 4 alpha): first step of the iteration
+    float c1[kMaxCheb];        // direction recurrence d <- c1[k] d + c2[k] r
+    float c2[kMaxCheb];
+    long long Af64, Ac64;      // round(tau / (2 h^2) 2^32) of the fine / coarse grid (64-bit: tau/h^2 may exceed 1)
+    const double* phif64;      // FP64 test functions [n_obs][n^2] / [n_obs][(n/2)^2]
+    const double* phic64;
+};
+bool theta_supported(int n);
+cudaError_t theta_variant_info(int n, bool coupled, int slot_stride, VariantInfo* out);
+// Launch one batch of the theta-scheme kernel on n_ctas CTAs; partials must hold
+// n_ctas * slots_per_cta * slot_stride doubles.
+cudaError_t launch_theta(int n, bool coupled, const KArgs& a, const TArgs& t, int n_ctas, cudaStream_t stream,
+                         int priority = 0);
+
 // ---- learned level below level 0
 constexpr int kModes = 32;     // real orthonormal modes
 constexpr int kFeat = 64;      // features = modes x 2 noise components

@@ -1,0 +1,423 @@
+// Theta-scheme sample kernel for sm_103a: Eq. (FullyDiscreteDK) with an
+// implicit diffusion weight b0 > 0 (b1 = 1 - b0; Definition 2.1, the operator
+// A_h of Appendix C), for the NN-coupled pair of Section 3.2 on grids up to
+// 64 x 64.
+//
+// Step.  Subtracting (I - b0 tau/2 Delta_h) rho^(m-1) from both sides of the
+// scheme gives the increment
+//     rho^m - rho^(m-1) = H (tau/2 Delta_h rho^(m-1) + xi^(m-1)),
+//     H = (I - b0 tau/2 Delta_h)^(-1) = (I + alpha L)^(-1),  alpha = b0 tau/(2 h^2),
+// with L a = 4 a(x) - sum of the four neighbours (= -h^2 Delta_h) and xi the
+// explicit noise divergence.  The bracket is the backward difference of a
+// face flux F_r (diffusion flux across the face x -> x + e_r plus the two noise
+// transfers G_r(x) + G_r(x + e_r) of the central difference), and H commutes
+// with every periodic difference operator, so the increment is the backward
+// difference of H F_r = F_r + u_r with (I + alpha L) u_r = -alpha L F_r.
+// F_r is exact in 32/64-bit fixed point as in the explicit kernels; only the
+// correction u_r is computed in FP32, by K steps of Chebyshev iteration on the
+// spectrum [1, 1 + 8 alpha] of I + alpha L (K fixed on the host from the
+// Chebyshev error bound), and rounded once.  Adding the integer face fluxes
+// keeps sum_x q invariant bit for bit, as in the explicit kernels.  K = 0
+// (b0 = 0) is exactly the explicit step.
+//
+// Work decomposition.  One CTA holds SPB samples; each sample uses (n/2)^2
+// threads, thread t owning coarse cell t and the 2 x 2 block of fine cells to
+// its right-most side (the coupling block of Section 3.2), so the coupled
+// coarse increment is summed in the thread's registers.  The state and the
+// stencil operands live in shared memory (the solve needs every neighbour at
+// every Chebyshev step); one barrier per Chebyshev step.
+#include "dk_device.cuh"
+#include "dk_kernels.h"
+
+namespace dk {
+namespace {
+
+constexpr unsigned kFullMask = 0xffffffffu;
+constexpr int kRed = 2 * kMaxObs + 2;   // reduced values per sample
+
+template <int N_>
+struct TShape {
+    static constexpr int N = N_, NC = N / 2;
+    static constexpr int TPS = NC * NC;                    // threads per sample
+    static constexpr int THREADS = TPS >= 128 ? TPS : 128;
+    static constexpr int SPB = THREADS / TPS;              // samples per CTA
+    // per sample: fine state, four float planes, coarse state
+    static constexpr size_t SAMPLE_BYTES = sizeof(int32_t) * (N * N * 5 + NC * NC);
+    static size_t smem(int slot_stride) {
+        return SAMPLE_BYTES * SPB + sizeof(double) * ((THREADS + 31) / 32) * kRed +
+               sizeof(double) * SPB * slot_stride;
+    }
+};
+
+__device__ __forceinline__ int32_t edge_flux64(long long A, int32_t d) {
+    return static_cast<int32_t>((A * static_cast<long long>(d) + 0x80000000LL) >> 32);
+}
+
+__device__ __forceinline__ float as_f(int32_t v) { return __int_as_float(v); }
+__device__ __forceinline__ int32_t as_i(float v) { return __float_as_int(v); }
+
+// One step of the theta-scheme on an NN x NN periodic grid for the NCELL cells
+// (row[i], col[i]) of this thread.  On entry sq holds the state of every cell
+// and P0 / P2 the noise transfers G_1 / G_2 of every cell (as integers),
+// published by a barrier.  On exit q and sq hold the new state, published by a
+// barrier.  P0..P3 are NN x NN scratch planes.
+template <int NN, int NCELL>
+__device__ __forceinline__ void theta_step(int32_t (&q)[NCELL], const int (&row)[NCELL], const int (&col)[NCELL],
+                                           int32_t* sq, float* P0, float* P1, float* P2, float* P3, long long A,
+                                           const TArgs& t, unsigned& bad) {
+    int idx[NCELL], dn[NCELL], rt[NCELL], up[NCELL], lf[NCELL];
+#pragma unroll
+    for (int i = 0; i < NCELL; ++i) {
+        idx[i] = row[i] * NN + col[i];
+        dn[i] = ((row[i] + 1) % NN) * NN + col[i];
+        up[i] = ((row[i] + NN - 1) % NN) * NN + col[i];
+        rt[i] = row[i] * NN + (col[i] + 1) % NN;
+        lf[i] = row[i] * NN + (col[i] + NN - 1) % NN;
+    }
+    // face fluxes across x -> x + e_1 (down) and x -> x + e_2 (right), exact
+    long long F1[NCELL], F2[NCELL];
+#pragma unroll
+    for (int i = 0; i < NCELL; ++i) {
+        const int32_t g1 = as_i(P0[idx[i]]), g2 = as_i(P2[idx[i]]);
+        F1[i] = (long long)edge_flux64(A, sq[dn[i]] - q[i]) + g1 + as_i(P0[dn[i]]);
+        F2[i] = (long long)edge_flux64(A, sq[rt[i]] - q[i]) + g2 + as_i(P2[rt[i]]);
+    }
+    float u1[NCELL], u2[NCELL];
+#pragma unroll
+    for (int i = 0; i < NCELL; ++i) u1[i] = u2[i] = 0.f;
+    float* out1 = P1;   // plane that receives the corrected fluxes
+    float* out2 = P3;
+    if (t.K > 0) {
+        // right-hand side -alpha L F and the first Chebyshev direction (the
+        // barrier after the F planes also orders every read of the G planes
+        // before the direction overwrites them)
+#pragma unroll
+        for (int i = 0; i < NCELL; ++i) {
+            P1[idx[i]] = static_cast<float>(F1[i]);
+            P3[idx[i]] = static_cast<float>(F2[i]);
+        }
+        __syncthreads();
+        float r1[NCELL], r2[NCELL], d1[NCELL], d2[NCELL];
+#pragma unroll
+        for (int i = 0; i < NCELL; ++i) {
+            const float f1 = P1[idx[i]], f2 = P3[idx[i]];
+            const float l1 = 4.f * f1 - P1[up[i]] - P1[dn[i]] - P1[lf[i]] - P1[rt[i]];
+            const float l2 = 4.f * f2 - P3[up[i]] - P3[dn[i]] - P3[lf[i]] - P3[rt[i]];
+            r1[i] = -t.alpha * l1;
+            r2[i] = -t.alpha * l2;
+            d1[i] = r1[i] * t.inv_theta;
+            d2[i] = r2[i] * t.inv_theta;
+            P0[idx[i]] = d1[i];
+            P2[idx[i]] = d2[i];
+        }
+        __syncthreads();
+        float *c1p = P0, *c2p = P2, *n1p = P1, *n2p = P3;   // current / next direction planes
+        const float diag = 1.f + 4.f * t.alpha;
+        for (int k = 0; k < t.K; ++k) {
+#pragma unroll
+            for (int i = 0; i < NCELL; ++i) {
+                const float a1 = diag * d1[i] - t.alpha * (c1p[up[i]] + c1p[dn[i]] + c1p[lf[i]] + c1p[rt[i]]);
+                const float a2 = diag * d2[i] - t.alpha * (c2p[up[i]] + c2p[dn[i]] + c2p[lf[i]] + c2p[rt[i]]);
+                u1[i] += d1[i];
+                u2[i] += d2[i];
+                r1[i] -= a1;
+                r2[i] -= a2;
+            }
+            if (k + 1 < t.K) {
+                const float ca = t.c1[k], cb = t.c2[k];
+#pragma unroll
+                for (int i = 0; i < NCELL; ++i) {
+                    d1[i] = ca * d1[i] + cb * r1[i];
+                    d2[i] = ca * d2[i] + cb * r2[i];
+                    n1p[idx[i]] = d1[i];
+                    n2p[idx[i]] = d2[i];
+                }
+                __syncthreads();
+                float* s1 = c1p; c1p = n1p; n1p = s1;
+                float* s2 = c2p; c2p = n2p; n2p = s2;
+            }
+        }
+        // the planes not read by the last Chebyshev step take the result
+        out1 = n1p;
+        out2 = n2p;
+    }
+    long long H1[NCELL], H2[NCELL];
+#pragma unroll
+    for (int i = 0; i < NCELL; ++i) {
+        H1[i] = F1[i] + __float2ll_rn(u1[i]);
+        H2[i] = F2[i] + __float2ll_rn(u2[i]);
+        bad |= (H1[i] != (long long)(int32_t)H1[i]) | (H2[i] != (long long)(int32_t)H2[i]);
+        out1[idx[i]] = as_f(static_cast<int32_t>(H1[i]));
+        out2[idx[i]] = as_f(static_cast<int32_t>(H2[i]));
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < NCELL; ++i) {
+        const long long v = (long long)q[i] + (H1[i] - as_i(out1[up[i]])) + (H2[i] - as_i(out2[lf[i]]));
+        bad |= (unsigned)((v >= (1LL << 30)) | (v <= -(1LL << 30)));
+        q[i] = static_cast<int32_t>(v);
+        sq[idx[i]] = q[i];
+    }
+    __syncthreads();
+}
+
+template <int N, bool CPL>
+__global__ void __launch_bounds__(TShape<N>::THREADS) theta_kernel(const KArgs a, const TArgs t) {
+    using S = TShape<N>;
+    constexpr int NC = S::NC, TPS = S::TPS, SPB = S::SPB, THREADS = S::THREADS;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int tid = threadIdx.x;
+    const int sl = tid / TPS, lt = tid % TPS;   // sample slot in the CTA, thread within the sample
+    unsigned char* base = smem_raw + S::SAMPLE_BYTES * sl;
+    int32_t* sq = reinterpret_cast<int32_t*>(base);
+    float* P0 = reinterpret_cast<float*>(sq + N * N);
+    float* P1 = P0 + N * N;
+    float* P2 = P1 + N * N;
+    float* P3 = P2 + N * N;
+    int32_t* sqc = reinterpret_cast<int32_t*>(P3 + N * N);
+    double* red = reinterpret_cast<double*>(smem_raw + S::SAMPLE_BYTES * SPB);
+    double* acc = red + ((THREADS + 31) / 32) * kRed;
+    for (int i = tid; i < SPB * a.slot_stride; i += THREADS) acc[i] = 0.0;
+
+    const int I1 = lt / NC, I2 = lt % NC;   // coarse cell; fine block rows 2 I1 + v1, cols 2 I2 + v2
+    const int frow[4] = {2 * I1, 2 * I1, 2 * I1 + 1, 2 * I1 + 1};
+    const int fcol[4] = {2 * I2, 2 * I2 + 1, 2 * I2, 2 * I2 + 1};
+    const int crow[1] = {I1}, ccol[1] = {I2};
+    const uint32_t p_top = static_cast<uint32_t>((frow[0] * N + fcol[0]) >> 1);
+    const uint32_t p_bot = static_cast<uint32_t>((frow[2] * N + fcol[2]) >> 1);
+
+    const long long n_slots = (long long)gridDim.x * SPB;
+    const long long slot = (long long)blockIdx.x * SPB + sl;
+    const long long cta_slot0 = (long long)blockIdx.x * SPB;
+    const long long iters = a.count > cta_slot0 ? (a.count - cta_slot0 + n_slots - 1) / n_slots : 0;
+    unsigned bad = 0;
+    __syncthreads();
+
+    for (long long it = 0; it < iters; ++it) {
+        const long long idx = slot + it * n_slots;
+        const bool active = idx < a.count;
+        const long long sid = a.first + (active ? idx : 0);
+        const uint32_t c2 = static_cast<uint32_t>(sid);
+        const uint32_t c3 = a.tag | ((static_cast<uint32_t>(static_cast<unsigned long long>(sid) >> 32) & 0xffffu) << 16);
+
+        int32_t q[4], qc[1] = {0};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            q[i] = a.q0f[frow[i] * N + fcol[i]];
+            sq[frow[i] * N + fcol[i]] = q[i];
+        }
+        float zt0 = 0.f, zt1 = 0.f;
+        if constexpr (CPL) {
+            qc[0] = a.q0c[lt];
+            sqc[lt] = qc[0];
+        }
+        __syncthreads();
+
+        for (int m = 0; m < a.M; ++m) {
+            // ---- noise of the fine block: Philox4x32-10 per horizontal cell pair, Box--Muller
+            int32_t G1[4], G2[4];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint4 x = philox10(make_uint4(h ? p_bot : p_top, static_cast<uint32_t>(m), c2, c3), a.key0, a.key1);
+                float ra, ca, sa, rb, cb, sb;
+                box_muller_polar(x.x, x.y, ra, ca, sa);
+                box_muller_polar(x.z, x.w, rb, cb, sb);
+                const float ta = noise_amp(q[2 * h], a.gf) * ra;
+                const float tb = noise_amp(q[2 * h + 1], a.gf) * rb;
+                G1[2 * h] = __float2int_rn(ta * ca);
+                G2[2 * h] = __float2int_rn(ta * sa);
+                G1[2 * h + 1] = __float2int_rn(tb * cb);
+                G2[2 * h + 1] = __float2int_rn(tb * sb);
+                if constexpr (CPL) {
+                    zt0 = fmaf(rb, cb, fmaf(ra, ca, zt0));
+                    zt1 = fmaf(rb, sb, fmaf(ra, sa, zt1));
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                P0[frow[i] * N + fcol[i]] = as_f(G1[i]);
+                P2[frow[i] * N + fcol[i]] = as_f(G2[i]);
+            }
+            __syncthreads();
+            theta_step<N, 4>(q, frow, fcol, sq, P0, P1, P2, P3, t.Af64, t, bad);
+
+            if constexpr (CPL) {
+                if ((m & 3) == 3) {
+                    // coupled coarse step: 1/4 of the 16 summed fine normals
+                    const float s = noise_amp(qc[0], a.gc);
+                    P0[lt] = as_f(__float2int_rn(s * zt0));
+                    P2[lt] = as_f(__float2int_rn(s * zt1));
+                    zt0 = zt1 = 0.f;
+                    __syncthreads();
+                    theta_step<NC, 1>(qc, crow, ccol, sqc, P0, P1, P2, P3, t.Ac64, t, bad);
+                }
+            }
+        }
+
+        // ---- observables: fluctuation sums against the fixed-point mean field (FP64), mass
+        double v[kRed];
+        {
+            long long mf = 0;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) mf += q[i];
+            v[2 * kMaxObs] = static_cast<double>(mf);
+            v[2 * kMaxObs + 1] = CPL ? static_cast<double>(qc[0]) : 0.0;
+#pragma unroll
+            for (int k = 0; k < kMaxObs; ++k) {
+                double sf = 0.0, sc = 0.0;
+                if (k < a.n_obs) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int x = frow[i] * N + fcol[i];
+                        sf += static_cast<double>(q[i] - a.qbf[x]) * t.phif64[(size_t)k * N * N + x];
+                    }
+                    if constexpr (CPL) sc = static_cast<double>(qc[0] - a.qbc[lt]) * t.phic64[(size_t)k * NC * NC + lt];
+                }
+                v[k] = sf;
+                v[kMaxObs + k] = sc;
+            }
+        }
+        bool leader;
+        if constexpr (TPS < 32) {
+#pragma unroll
+            for (int off = TPS / 2; off >= 1; off >>= 1)
+#pragma unroll
+                for (int i = 0; i < kRed; ++i) v[i] += __shfl_xor_sync(kFullMask, v[i], off, TPS);
+            leader = lt == 0;
+        } else {
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1)
+#pragma unroll
+                for (int i = 0; i < kRed; ++i) v[i] += __shfl_xor_sync(kFullMask, v[i], off);
+            if ((tid & 31) == 0)
+#pragma unroll
+                for (int i = 0; i < kRed; ++i) red[(tid >> 5) * kRed + i] = v[i];
+            __syncthreads();
+            leader = lt == 0;
+            if (leader) {
+                for (int w = 1; w < TPS / 32; ++w)
+#pragma unroll
+                    for (int i = 0; i < kRed; ++i) v[i] += red[((tid >> 5) + w) * kRed + i];
+            }
+        }
+
+        // ---- FP64 quantities and moment sums (one thread per sample)
+        if (leader && active) {
+            double Df[kMaxObs], Dc[kMaxObs];
+#pragma unroll
+            for (int k = 0; k < kMaxObs; ++k) {
+                Df[k] = a.dscale_f * v[k] + a.delta_f[k];
+                Dc[k] = CPL ? a.dscale_c * v[kMaxObs + k] + a.delta_c[k] : 0.0;
+            }
+            double* A = acc + sl * a.slot_stride;
+            A[0] += 1.0;
+            double merr = fabs(v[2 * kMaxObs] - static_cast<double>(a.mass0_f)) * a.dscale_f;
+            if (CPL) merr = fmax(merr, fabs(v[2 * kMaxObs + 1] - static_cast<double>(a.mass0_c)) * a.dscale_c);
+            A[1] = fmax(A[1], merr);
+            int qi = 0;
+            for (int j = 0; j < a.n_obs; ++j) {
+                const int kend = a.products ? a.n_obs : j + 1;
+                for (int k = j; k < kend; ++k, ++qi) {
+                    const double pf = a.N * Df[j] * Df[k];
+                    const double pc = CPL ? a.N * Dc[j] * Dc[k] : 0.0;
+                    const double dp = pf - pc, dp2 = dp * dp;
+                    double* B = A + 2 + kNSum * qi;
+                    B[0] += dp; B[1] += dp2; B[2] += dp2 * dp; B[3] += dp2 * dp2;
+                    B[4] += pf; B[5] += pf * pf; B[6] += pc; B[7] += pc * pc;
+                    B[8] += Df[j]; B[9] += Df[j] * Df[j]; B[10] += Dc[j]; B[11] += Dc[j] * Dc[j];
+                }
+            }
+            if (a.samples) {
+                double* o = a.samples + idx * (2 * a.n_obs + 2);
+                for (int k = 0; k < a.n_obs; ++k) {
+                    o[k] = Df[k];
+                    o[a.n_obs + k] = Dc[k];
+                }
+                o[2 * a.n_obs] = v[2 * kMaxObs] * a.dscale_f;
+                o[2 * a.n_obs + 1] = CPL ? v[2 * kMaxObs + 1] * a.dscale_c : 0.0;
+            }
+        }
+        __syncthreads();   // the reduction scratch and the state planes are reused by the next sample
+    }
+    if (bad) atomicOr(a.err, kErrRange);
+
+    // ---- per-slot partial sums to global scratch, entry-major [stride][n_slots]
+    __syncthreads();
+    for (int i = tid; i < SPB * a.slot_stride; i += THREADS) {
+        const int s = i / a.slot_stride, e = i % a.slot_stride;
+        a.partials[(size_t)e * n_slots + cta_slot0 + s] = acc[i];
+    }
+}
+
+template <int N, bool CPL>
+cudaError_t prepare(int slot_stride, VariantInfo* out) {
+    using S = TShape<N>;
+    const size_t smem = S::smem(slot_stride);
+    cudaError_t e = cudaFuncSetAttribute(theta_kernel<N, CPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, dev = 0, sms = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, theta_kernel<N, CPL>, S::THREADS, smem)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    *out = VariantInfo{};
+    out->supported = per_sm > 0;
+    out->threads = S::THREADS;
+    out->cluster = 1;
+    out->slots_per_cta = S::SPB;
+    out->smem = smem;
+    out->max_ctas = per_sm * sms;
+    return cudaSuccess;
+}
+
+template <int N, bool CPL>
+cudaError_t launch_n(const KArgs& a, const TArgs& t, int n_ctas, cudaStream_t st, int priority) {
+    using S = TShape<N>;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(n_ctas);
+    cfg.blockDim = dim3(S::THREADS);
+    cfg.dynamicSmemBytes = S::smem(a.slot_stride);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    int na = 0;
+    if (priority != 0) {
+        attr[na].id = cudaLaunchAttributePriority;
+        attr[na].val.priority = priority;
+        ++na;
+    }
+    cfg.attrs = attr;
+    cfg.numAttrs = na;
+    return cudaLaunchKernelEx(&cfg, theta_kernel<N, CPL>, a, t);
+}
+
+}  // namespace
+
+bool theta_supported(int n) { return n == 4 || n == 8 || n == 16 || n == 32 || n == 64; }
+
+cudaError_t theta_variant_info(int n, bool coupled, int slot_stride, VariantInfo* out) {
+    *out = VariantInfo{};
+    switch (n) {
+        case 4: return coupled ? prepare<4, true>(slot_stride, out) : prepare<4, false>(slot_stride, out);
+        case 8: return coupled ? prepare<8, true>(slot_stride, out) : prepare<8, false>(slot_stride, out);
+        case 16: return coupled ? prepare<16, true>(slot_stride, out) : prepare<16, false>(slot_stride, out);
+        case 32: return coupled ? prepare<32, true>(slot_stride, out) : prepare<32, false>(slot_stride, out);
+        case 64: return coupled ? prepare<64, true>(slot_stride, out) : prepare<64, false>(slot_stride, out);
+        default: return cudaSuccess;   // supported = 0
+    }
+}
+
+cudaError_t launch_theta(int n, bool coupled, const KArgs& a, const TArgs& t, int n_ctas, cudaStream_t st,
+                         int priority) {
+    if (t.K < 0 || t.K > kMaxCheb) return cudaErrorInvalidValue;
+    switch (n) {
+        case 4: return coupled ? launch_n<4, true>(a, t, n_ctas, st, priority) : launch_n<4, false>(a, t, n_ctas, st, priority);
+        case 8: return coupled ? launch_n<8, true>(a, t, n_ctas, st, priority) : launch_n<8, false>(a, t, n_ctas, st, priority);
+        case 16: return coupled ? launch_n<16, true>(a, t, n_ctas, st, priority) : launch_n<16, false>(a, t, n_ctas, st, priority);
+        case 32: return coupled ? launch_n<32, true>(a, t, n_ctas, st, priority) : launch_n<32, false>(a, t, n_ctas, st, priority);
+        case 64: return coupled ? launch_n<64, true>(a, t, n_ctas, st, priority) : launch_n<64, false>(a, t, n_ctas, st, priority);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace dk

@@ -26,7 +26,8 @@ struct LevelTab {
     int n = 0, M = 0;
     double h = 0, tau = 0;
     int S = 24;              // fixed-point fraction bits: rho = q 2^-S
-    int32_t A = 0;           // round(tau / (2 h^2) 2^32)
+    int32_t A = 0;           // round(tau / (2 h^2) 2^32) (explicit kernels: tau/h^2 <= 1/2)
+    long long A64 = 0;       // the same in 64 bits (theta-scheme kernel, where tau/h^2 may exceed 1)
     float g = 0.f;           // N^-1/2 sqrt(tau) / (2 h^2) 2^(S/2)
     double dscale = 0;       // h^2 2^-S
     long long mass0 = 0;     // sum of q0
@@ -58,6 +59,9 @@ struct LevelTab {
 struct mlmc_dk_ctx {
     double length = 1, T = 0, N = 0;
     int L_max = 0, n_obs = 1, products = 0, n_quant = 1, stride = 0, pilot = 256, L_start = 2;
+    double b0 = 0;              // implicit weight of Eq. (FullyDiscreteDK)
+    int theta = 0;              // every level runs on the theta-scheme kernel
+    dk::TArgs targs{};          // its Chebyshev schedule (per-level fields filled at launch)
     std::vector<LevelTab> lv;
     cudaStream_t stream = nullptr;
     double* d_partials = nullptr;
@@ -165,10 +169,12 @@ void fft2(std::vector<std::complex<double>>& a, int n, int sign) {
     for (int c = 0; c < n; ++c) fft1(a.data() + c, n, n, sign);
 }
 
-// Noise-free scheme rho <- rho + tau/2 Delta_h rho iterated M times: every
-// discrete Fourier mode k is multiplied by 1 - 2 (tau/h^2)(sin^2(pi k1/n) +
-// sin^2(pi k2/n)) per step, the symbol of Delta_h (Section 7.2).
-void mean_field(int n, double h, double tau, long long M, const double* rho0, double* out) {
+// Noise-free scheme iterated M times: with lam = 2 (tau/h^2)(sin^2(pi k1/n) +
+// sin^2(pi k2/n)) (tau/2 Delta_h of Section 7.2 acts on discrete Fourier mode
+// k as -lam), the weights (b0, b1 = 1 - b0) of Eq. (FullyDiscreteDK) multiply
+// the mode by (1 - b1 lam) / (1 + b0 lam) per step (1 - lam for the explicit
+// scheme).
+void mean_field(int n, double h, double tau, long long M, const double* rho0, double* out, double b0 = 0.0) {
     std::vector<std::complex<double>> a((size_t)n * n);
     for (size_t i = 0; i < a.size(); ++i) a[i] = rho0[i];
     fft2(a, n, -1);
@@ -180,7 +186,8 @@ void mean_field(int n, double h, double tau, long long M, const double* rho0, do
     }
     for (int k1 = 0; k1 < n; ++k1)
         for (int k2 = 0; k2 < n; ++k2) {
-            const double g = 1.0 - 2.0 * mu * (s2[k1] + s2[k2]);
+            const double lam = 2.0 * mu * (s2[k1] + s2[k2]);
+            const double g = b0 == 0.0 ? 1.0 - lam : (1.0 - (1.0 - b0) * lam) / (1.0 + b0 * lam);
             a[(size_t)k1 * n + k2] *= std::pow(g, (double)M);
         }
     fft2(a, n, +1);
@@ -280,6 +287,22 @@ int launch_streamed(mlmc_dk_ctx* c, int level, int stream_tag, int64_t first, in
     return MLMC_DK_OK;
 }
 
+// The level's sample kernel: the theta-scheme kernel on a theta context, the
+// register-resident kernel variant in use otherwise.
+cudaError_t launch_main(const mlmc_dk_ctx* c, int level, bool coupled, const dk::KArgs& a, int n_ctas,
+                        cudaStream_t st, int priority) {
+    const LevelTab& t = c->lv[level];
+    if (c->theta) {
+        dk::TArgs ta = c->targs;
+        ta.Af64 = t.A64;
+        ta.Ac64 = coupled ? c->lv[level - 1].A64 : 0;
+        ta.phif64 = t.d_phi64;
+        ta.phic64 = coupled ? c->lv[level - 1].d_phi64 : nullptr;
+        return dk::launch_theta(t.n, coupled, a, ta, n_ctas, st, priority);
+    }
+    return dk::launch_level(t.n, coupled, t.sel[coupled ? 1 : 0], a, n_ctas, st, priority);
+}
+
 int launch_batch_into(mlmc_dk_ctx* c, int level, int stream_tag, int64_t first, int64_t count, uint64_t seed,
                       double* sums_dev, double* samples_dev, cudaStream_t st, double* partials, size_t cap,
                       int priority) {
@@ -303,8 +326,7 @@ int launch_batch_into(mlmc_dk_ctx* c, int level, int stream_tag, int64_t first, 
     if ((size_t)n_slots * c->stride > cap) return fail(c, MLMC_DK_ERR_INVALID, "scratch too small");
     dk::KArgs a = make_args(c, level, stream_tag, coupled, first, count, seed, samples_dev);
     a.partials = partials;
-    if ((e = dk::launch_level(c->lv[level].n, coupled, c->lv[level].sel[coupled ? 1 : 0], a, n_ctas, st,
-                              priority)) != cudaSuccess)
+    if ((e = launch_main(c, level, coupled, a, n_ctas, st, priority)) != cudaSuccess)
         return cuda_fail(c, e, "level kernel launch");
     if ((e = dk::launch_reduce(partials, n_slots, c->stride, sums_dev, st)) != cudaSuccess)
         return cuda_fail(c, e, "reduce kernel launch");
@@ -440,9 +462,43 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
         M0 = (long long)std::ceil(x - 1e-9 * x);
     }
     const double tau0 = cfg->T / (double)M0;
-    if (tau0 / (h0 * h0) > 0.5 + 1e-12)
+    const double b0 = cfg->theta_b0, b1 = 1.0 - cfg->theta_b0;
+    if (!(b0 >= 0.0 && b0 <= 1.0)) return fail(nullptr, MLMC_DK_ERR_INVALID, "theta_b0 must lie in [0, 1]");
+    const bool theta = b0 > 0.0 || cfg->theta_kernel != 0;
+    if (b0 == 0.0 && tau0 / (h0 * h0) > 0.5 + 1e-12)
         return fail(nullptr, MLMC_DK_ERR_INVALID,
                     "tau/h^2 > 1/2: the noise-free scheme violates the discrete maximum principle");
+    // the checkerboard mode (lam = 4 tau/h^2) has factor (1 - b1 lam)/(1 + b0 lam) >= -1 iff
+    // (b1 - b0) 2 tau/h^2 <= 1 (Assumption ass_stability)
+    if (b0 > 0.0 && b1 > b0 && (b1 - b0) * 2.0 * tau0 / (h0 * h0) > 1.0 + 1e-12)
+        return fail(nullptr, MLMC_DK_ERR_INVALID, "tau/h^2 above the theta-scheme's stability bound 1/(2 (b1 - b0))");
+    dk::TArgs targs{};
+    if (theta) {
+        if ((cfg->n0 << cfg->L_max) > 64 || cfg->stream_from_n != 0)
+            return fail(nullptr, MLMC_DK_ERR_UNSUPPORTED, "theta-scheme kernel: grids up to 64^2, no streamed levels");
+        // Chebyshev iteration on the spectrum [1, 1 + 8 alpha] of I + alpha L: after K
+        // steps the error is at most 1 / T_K(sigma) of the initial one,
+        // sigma = (1 + 4 alpha) / (4 alpha); K is the first with that below 2^-27
+        const double alpha = b0 * tau0 / (2.0 * h0 * h0);
+        targs.alpha = (float)alpha;
+        targs.inv_theta = (float)(1.0 / (1.0 + 4.0 * alpha));
+        targs.K = 0;
+        if (alpha > 0.0) {
+            const double sigma = (1.0 + 4.0 * alpha) / (4.0 * alpha), delta = 4.0 * alpha;
+            int K = 1;
+            while (K <= dk::kMaxCheb && std::cosh(K * std::acosh(sigma)) < std::ldexp(1.0, 27)) ++K;
+            if (K > dk::kMaxCheb)
+                return fail(nullptr, MLMC_DK_ERR_UNSUPPORTED, "b0 tau/h^2 too large for the solve's step budget");
+            targs.K = K;
+            double rho = 1.0 / sigma;
+            for (int k = 0; k < K; ++k) {
+                const double next = 1.0 / (2.0 * sigma - rho);
+                targs.c1[k] = (float)(next * rho);
+                targs.c2[k] = (float)(2.0 * next / delta);
+                rho = next;
+            }
+        }
+    }
     if (M0 * (1LL << (2 * cfg->L_max)) > (1LL << 30)) return fail(nullptr, MLMC_DK_ERR_INVALID, "too many time steps");
 
     int ndev = 0;
@@ -461,6 +517,9 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
     c->stride = 2 + dk::kNSum * c->n_quant;
     c->pilot = cfg->pilot > 1 ? cfg->pilot : 256;
     c->L_start = std::min(cfg->L_start > 0 ? cfg->L_start : 2, cfg->L_max);
+    c->b0 = b0;
+    c->theta = theta ? 1 : 0;
+    c->targs = targs;
     c->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
     c->lv.resize(cfg->L_max + 1);
     c->next_id[0].assign(cfg->L_max + 1, 0);
@@ -498,7 +557,8 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
             return fail(nullptr, MLMC_DK_ERR_INVALID, "|rho0| too large for the fixed-point range");
         }
         t.S = S;
-        t.A = (int32_t)std::llround(t.tau / (2.0 * t.h * t.h) * 4294967296.0);
+        t.A64 = std::llround(t.tau / (2.0 * t.h * t.h) * 4294967296.0);
+        t.A = t.A64 < (1LL << 31) ? (int32_t)t.A64 : 0;
         t.g = (float)(c_noise * std::pow(2.0, 0.5 * S));
         t.dscale = t.h * t.h * std::ldexp(1.0, -S);
 
@@ -510,7 +570,7 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
             mass += q0[i];
         }
         t.mass0 = mass;
-        mean_field(t.n, t.h, t.tau, t.M, rho0, rbar.data());
+        mean_field(t.n, t.h, t.tau, t.M, rho0, rbar.data(), b0);
         for (size_t i = 0; i < cells; ++i) qb[i] = (int32_t)std::llrint(std::ldexp(rbar[i], S));
         // The quantised initial state q0 2^-S differs from rho0 by e0 (at most half
         // a quantum per cell); the scheme is linear apart from sqrt([rho]^+), so e0
@@ -518,7 +578,7 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
         // removed from the observables with the mean-field offset below.
         std::vector<double> e0(cells), e0T(cells);
         for (size_t i = 0; i < cells; ++i) e0[i] = std::ldexp((double)q0[i], -S) - rho0[i];
-        mean_field(t.n, t.h, t.tau, t.M, e0.data(), e0T.data());
+        mean_field(t.n, t.h, t.tau, t.M, e0.data(), e0T.data(), b0);
         std::vector<float> phif(cells * c->n_obs);
         for (int k = 0; k < c->n_obs; ++k) {
             const double* ph = cfg->phi[(size_t)l * c->n_obs + k];
@@ -572,6 +632,24 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
                 return cuda_fail(nullptr, e, "FP64 test functions");
             }
             c->h2d_bytes += (int64_t)(sizeof(double) * ph64.size());
+        }
+        if (theta) {
+            // one kernel shape per grid size: the theta-scheme kernel
+            for (int mode = 0; mode < 2; ++mode) {
+                if (mode == 1 && l == 0) continue;
+                dk::VariantInfo vi{};
+                if ((e = dk::theta_variant_info(t.n, mode == 1, c->stride, &vi)) != cudaSuccess) {
+                    mlmc_dk_free(c);
+                    return cuda_fail(nullptr, e, "theta kernel setup");
+                }
+                if (!vi.supported) {
+                    mlmc_dk_free(c);
+                    return fail(nullptr, MLMC_DK_ERR_UNSUPPORTED, "no theta-scheme kernel for this grid");
+                }
+                t.vis[mode].push_back(vi);
+                partials_need = std::max(partials_need, (size_t)vi.max_ctas * vi.slots_per_cta * c->stride);
+            }
+            continue;
         }
         const bool force_stream = cfg->stream_from_n > 0 && t.n >= cfg->stream_from_n && t.n % 64 == 0;
         const int nv = force_stream ? 0 : dk::variant_count(t.n);
@@ -721,6 +799,9 @@ int mlmc_dk_level_info(const mlmc_dk_ctx* ctx, int32_t level, mlmc_dk_level_desc
     out->split_capable = t.split_ok;
     out->split_fraction = t.split_frac;
     out->batch_streamed = t.batch_streamed;
+    out->theta = ctx->theta;
+    out->theta_b0 = ctx->b0;
+    out->cheb_steps = ctx->theta ? ctx->targs.K : 0;
     return MLMC_DK_OK;
 }
 
@@ -782,8 +863,7 @@ int mlmc_dk_run_level_static(const mlmc_dk_ctx* ctx, int32_t level, int32_t stre
     dk::KArgs a = make_args(c, level, stream_tag, coupled, first_sample, n_samples, seed, samples_dev);
     a.partials = scratch;        // fully overwritten by the level kernel: nothing to clear
     a.err = err_dev ? err_dev : reinterpret_cast<unsigned*>(scratch + (capacity - 1));
-    if ((e = dk::launch_level(ctx->lv[level].n, coupled, ctx->lv[level].sel[coupled ? 1 : 0], a, n_ctas, st)) !=
-        cudaSuccess)
+    if ((e = launch_main(ctx, level, coupled, a, n_ctas, st, 0)) != cudaSuccess)
         return cuda_fail(c, e, "level kernel launch");
     if ((e = dk::launch_reduce(scratch, n_slots, ctx->stride, sums_dev, st)) != cudaSuccess)
         return cuda_fail(c, e, "reduce kernel launch");
@@ -1443,6 +1523,8 @@ extern "C" {
 int mlmc_dk_surrogate_init(mlmc_dk_ctx* ctx, uint64_t seed) {
     if (!ctx) return fail(nullptr, MLMC_DK_ERR_INVALID, "null context");
     const LevelTab& l0 = ctx->lv[0];
+    if (ctx->theta)
+        return fail(ctx, MLMC_DK_ERR_UNSUPPORTED, "surrogate: explicit scheme only (its features use the explicit symbol)");
     if (l0.n < 8 || l0.n > 32 || l0.streamed)
         return fail(ctx, MLMC_DK_ERR_UNSUPPORTED, "surrogate: level-0 grid must be 8^2..32^2");
     free_surrogate(ctx->sur);

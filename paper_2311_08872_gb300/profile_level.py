@@ -53,6 +53,7 @@ def main() -> None:
     avg = sum(ms) / len(ms)
     print(json.dumps({"workload": wl.name, "level": args.level, "n": info.n, "fine_steps": info.M,
                       "streamed": bool(info.streamed), "coupled": tag == 0 and args.level > 0,
+                      "theta_b0": info.theta_b0 if info.theta else 0.0, "cheb_steps": info.cheb_steps,
                       "samples": args.samples, "ms_per_launch": avg,
                       "cell_steps_per_s": args.samples * cost / (avg * 1e-3)}))
 

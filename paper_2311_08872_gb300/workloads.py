@@ -26,6 +26,11 @@ Workloads:
   * ``paper_reg`` / ``paper_irreg`` -- the paper's Section 7 setting on
                         (0, 2pi)^2 with levels 4^2..128^2 (h_l = 2pi 2^-(2+l),
                         tau_l = 1e-3 4^(5-l), T = 1.024, phi = sin x + sin y).
+  * ``theta16_64``   -- Crank--Nicolson weights b0 = b1 = 1/2 of Eq.
+                        (FullyDiscreteDK) at tau/h^2 = 1 (twice the explicit
+                        limit), levels 16^2..64^2, T=0.02, N=1e5.
+  * ``implicit16_64``-- implicit Euler weights b0 = 1, b1 = 0 at tau/h^2 = 2,
+                        same grids.
 """
 from __future__ import annotations
 
@@ -148,6 +153,7 @@ class Workload:
     alloc: Optional[Tuple[int, ...]] = None   # fixed per-level sample counts of one benchmark step
     alloc_scale: int = 1            # the eps-optimal allocation is about alloc * alloc_scale
     offset: float = 0.0             # grid points at (i + offset) h: 0 right-most, 1/2 symmetric coupling
+    b0: float = 0.0                 # implicit weight of the time step (b1 = 1 - b0); 0 explicit Euler--Maruyama
     note: str = ""
 
     def n(self, level: int) -> int:
@@ -202,6 +208,12 @@ WORKLOADS: Dict[str, Workload] = {
     "paper_irreg": Workload("paper_irreg", TWO_PI, 4, 5, 1.024, 1.024 / (TWO_PI / 4) ** 2, 2e9,
                             "paper_irreg", [Observable("sin+sin")], seed=6, M0=1,
                             note="Section 7 setting, irregular initial datum"),
+    "theta16_64": Workload("theta16_64", 1.0, 16, 2, 0.02, 1.0, 1e5, "sinsin", [COS1],
+                           seed=7, eps_rel=1e-2, b0=0.5,
+                           note="Crank-Nicolson weights at tau/h^2 = 1, levels 16^2..64^2"),
+    "implicit16_64": Workload("implicit16_64", 1.0, 16, 2, 0.02, 2.0, 1e5, "sinsin", [COS1],
+                              seed=8, eps_rel=1e-2, b0=1.0,
+                              note="implicit Euler weights at tau/h^2 = 2, levels 16^2..64^2"),
 }
 
 

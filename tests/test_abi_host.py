@@ -93,3 +93,26 @@ def test_init_without_gpu_fails_loudly(dk):
     with pytest.raises(dk.MLMCError) as e:
         dk.Context(1.0, 4, 0, 0.01, 0.1, 100.0, one, [[np.ones((4, 4))]])
     assert e.value.code == dk.ERR_CUDA
+
+
+def test_theta_scheme_config_checks(dk):
+    """Weights of Eq. (FullyDiscreteDK): b0 in [0, 1]; with b1 > b0 the step
+    ratio is bounded by 1 / (2 (b1 - b0)); the theta kernel covers grids up to
+    64^2 and a bounded number of solve steps."""
+    one = [np.ones((4, 4))]
+    phi = [[np.ones((4, 4))]]
+    cases = [(dict(theta_b0=1.5), 0.1, 4, dk.ERR_INVALID),
+             (dict(theta_b0=0.25), 1.2, 4, dk.ERR_INVALID),
+             (dict(theta_b0=1.0), 25.0, 4, dk.ERR_UNSUPPORTED),
+             (dict(theta_b0=0.5), 3.0, 128, dk.ERR_UNSUPPORTED)]
+    for kw, mu, n0, code in cases:
+        r = [np.ones((n0, n0))]
+        with pytest.raises(dk.MLMCError) as e:
+            dk.Context(1.0, n0, 0, 1.0, mu, 100.0, r, [[np.ones((n0, n0))]], **kw)
+        assert e.value.code == code, (kw, mu, n0)
+    import torch
+    if not torch.cuda.is_available():
+        # a valid theta configuration passes the checks and fails only for want of a GPU
+        with pytest.raises(dk.MLMCError) as e:
+            dk.Context(1.0, 4, 0, 1.0, 0.9, 100.0, one, phi, theta_b0=0.25)
+        assert e.value.code == dk.ERR_CUDA
