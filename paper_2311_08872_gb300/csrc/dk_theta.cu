@@ -23,9 +23,14 @@
 // Work decomposition.  One CTA holds SPB samples; each sample uses (n/2)^2
 // threads, thread t owning coarse cell t and the 2 x 2 block of fine cells to
 // its right-most side (the coupling block of Section 3.2), so the coupled
-// coarse increment is summed in the thread's registers.  The state and the
-// stencil operands live in shared memory (the solve needs every neighbour at
-// every Chebyshev step); one barrier per Chebyshev step.
+// coarse increment is summed in the thread's registers.  The fine state and
+// every Chebyshev operand stay in registers: a coarse row of blocks is a
+// segment of n/2 consecutive lanes, so left / right neighbours come by warp
+// shuffles (the segment wrap is the periodic wrap) and only the top and
+// bottom rows of each block pass through shared memory for the blocks above
+// and below (contiguous 8- and 16-byte accesses), one barrier per Chebyshev
+// step.  The coarse step (1/16 of the work) keeps its state and operands in
+// shared memory.
 #include "dk_device.cuh"
 #include "dk_kernels.h"
 
@@ -41,8 +46,8 @@ struct TShape {
     static constexpr int TPS = NC * NC;                    // threads per sample
     static constexpr int THREADS = TPS >= 128 ? TPS : 128;
     static constexpr int SPB = THREADS / TPS;              // samples per CTA
-    // per sample: fine state, four float planes, coarse state
-    static constexpr size_t SAMPLE_BYTES = sizeof(int32_t) * (N * N * 5 + NC * NC);
+    // per sample: four planes of n^2 words, coarse state
+    static constexpr size_t SAMPLE_BYTES = sizeof(int32_t) * (N * N * 4 + NC * NC);
     static size_t smem(int slot_stride) {
         return SAMPLE_BYTES * SPB + sizeof(double) * ((THREADS + 31) / 32) * kRed +
                sizeof(double) * SPB * slot_stride;
@@ -161,6 +166,157 @@ __device__ __forceinline__ void theta_step(int32_t (&q)[NCELL], const int (&row)
     __syncthreads();
 }
 
+// Left / right neighbour values along a coarse row of W blocks (W lanes).
+template <int W, class T>
+__device__ __forceinline__ T from_left(T v, int l) {
+    return __shfl_sync(kFullMask, v, (l + W - 1) % W, W);
+}
+template <int W, class T>
+__device__ __forceinline__ T from_right(T v, int l) {
+    return __shfl_sync(kFullMask, v, (l + 1) % W, W);
+}
+
+// A plane of a block field: the top rows of all blocks, then the bottom rows
+// ([NC^2] float2 each, block index I1 NC + I2).
+template <int NC>
+struct Plane {
+    float2* top;
+    float2* bot;
+    __device__ __forceinline__ explicit Plane(float* base) : top(reinterpret_cast<float2*>(base)), bot(top + NC * NC) {}
+    __device__ __forceinline__ void put(int qi, const float (&v)[4]) const {
+        top[qi] = make_float2(v[0], v[1]);
+        bot[qi] = make_float2(v[2], v[3]);
+    }
+};
+
+// Sum of the four periodic neighbours of each cell of the 2 x 2 block v
+// (cells: 0 top-left, 1 top-right, 2 bottom-left, 3 bottom-right), the rows
+// above / below from the blocks qa / qb of plane P, the columns by shuffles.
+template <int NC>
+__device__ __forceinline__ void neighbour_sum(const float (&v)[4], const Plane<NC>& P, int qa, int qb, int l,
+                                              float (&s)[4]) {
+    const float2 ab = P.bot[qa], bl = P.top[qb];
+    const float l0 = from_left<NC>(v[1], l), l2 = from_left<NC>(v[3], l);
+    const float r1 = from_right<NC>(v[0], l), r3 = from_right<NC>(v[2], l);
+    s[0] = (ab.x + v[2]) + (l0 + v[1]);
+    s[1] = (ab.y + v[3]) + (v[0] + r1);
+    s[2] = (v[0] + bl.x) + (l2 + v[3]);
+    s[3] = (v[1] + bl.y) + (v[2] + r3);
+}
+
+// One fine theta step for this thread's 2 x 2 block (coarse cell (I1, I2),
+// lane l = I2 of its row segment); B[0..3] are four n^2-word planes.  Enters
+// and leaves with the planes free (a barrier at the end).
+template <int N>
+__device__ __forceinline__ void theta_fine_step(int32_t (&q)[4], const int32_t (&G1)[4], const int32_t (&G2)[4],
+                                                int I1, int I2, float* const (&B)[4], long long A, const TArgs& t,
+                                                unsigned& bad) {
+    constexpr int NC = N / 2;
+    const int qi = I1 * NC + I2;
+    const int qa = ((I1 + NC - 1) % NC) * NC + I2;   // block above
+    const int qb = ((I1 + 1) % NC) * NC + I2;        // block below
+    const int l = I2;
+    // ---- exact face fluxes: the row below from the block below, the column right by shuffles
+    int4* Q = reinterpret_cast<int4*>(B[0]);
+    Q[qi] = make_int4(q[0], q[1], G1[0], G1[1]);
+    __syncthreads();
+    const int4 bq = Q[qb];
+    const int32_t qr1 = from_right<NC>(q[0], l), qr3 = from_right<NC>(q[2], l);
+    const int32_t gr1 = from_right<NC>(G2[0], l), gr3 = from_right<NC>(G2[2], l);
+    const int32_t qdn[4] = {q[2], q[3], bq.x, bq.y}, gdn[4] = {G1[2], G1[3], bq.z, bq.w};
+    const int32_t qrt[4] = {q[1], qr1, q[3], qr3}, grt[4] = {G2[1], gr1, G2[3], gr3};
+    int32_t F1[4], F2[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const long long f1 = (long long)edge_flux64(A, qdn[c] - q[c]) + G1[c] + gdn[c];
+        const long long f2 = (long long)edge_flux64(A, qrt[c] - q[c]) + G2[c] + grt[c];
+        bad |= (unsigned)((f1 != (long long)(int32_t)f1) | (f2 != (long long)(int32_t)f2));
+        F1[c] = static_cast<int32_t>(f1);
+        F2[c] = static_cast<int32_t>(f2);
+    }
+    float u1[4] = {0.f, 0.f, 0.f, 0.f}, u2[4] = {0.f, 0.f, 0.f, 0.f};
+    float* hplane = B[1];   // plane that carries the corrected fluxes of the bottom rows
+    if (t.K > 0) {
+        // ---- right-hand side -alpha L F and the first Chebyshev direction
+        float f1[4], f2[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            f1[c] = static_cast<float>(F1[c]);
+            f2[c] = static_cast<float>(F2[c]);
+        }
+        const Plane<NC> PF1(B[1]), PF2(B[2]);
+        PF1.put(qi, f1);
+        PF2.put(qi, f2);
+        __syncthreads();   // also orders every read of B[0] before it is reused below
+        float s1[4], s2[4], r1[4], r2[4], d1[4], d2[4];
+        neighbour_sum<NC>(f1, PF1, qa, qb, l, s1);
+        neighbour_sum<NC>(f2, PF2, qa, qb, l, s2);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            r1[c] = -t.alpha * (4.f * f1[c] - s1[c]);
+            r2[c] = -t.alpha * (4.f * f2[c] - s2[c]);
+            d1[c] = r1[c] * t.inv_theta;
+            d2[c] = r2[c] * t.inv_theta;
+        }
+        float* cur1 = B[3];
+        float* cur2 = B[0];
+        float* nxt1 = B[1];
+        float* nxt2 = B[2];
+        Plane<NC>(cur1).put(qi, d1);
+        Plane<NC>(cur2).put(qi, d2);
+        __syncthreads();
+        const float diag = 1.f + 4.f * t.alpha;
+        for (int k = 0; k < t.K; ++k) {
+            neighbour_sum<NC>(d1, Plane<NC>(cur1), qa, qb, l, s1);
+            neighbour_sum<NC>(d2, Plane<NC>(cur2), qa, qb, l, s2);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                u1[c] += d1[c];
+                u2[c] += d2[c];
+                r1[c] -= diag * d1[c] - t.alpha * s1[c];
+                r2[c] -= diag * d2[c] - t.alpha * s2[c];
+            }
+            if (k + 1 < t.K) {
+                const float ca = t.c1[k], cb = t.c2[k];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    d1[c] = ca * d1[c] + cb * r1[c];
+                    d2[c] = ca * d2[c] + cb * r2[c];
+                }
+                Plane<NC>(nxt1).put(qi, d1);
+                Plane<NC>(nxt2).put(qi, d2);
+                __syncthreads();
+                float* x = cur1; cur1 = nxt1; nxt1 = x;
+                x = cur2; cur2 = nxt2; nxt2 = x;
+            }
+        }
+        hplane = nxt1;   // not read by the last Chebyshev step
+    }
+    // ---- corrected fluxes, rounded once; the update adds integer face fluxes
+    int32_t H1[4], H2[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const long long h1 = (long long)F1[c] + __float2ll_rn(u1[c]);
+        const long long h2 = (long long)F2[c] + __float2ll_rn(u2[c]);
+        bad |= (unsigned)((h1 != (long long)(int32_t)h1) | (h2 != (long long)(int32_t)h2));
+        H1[c] = static_cast<int32_t>(h1);
+        H2[c] = static_cast<int32_t>(h2);
+    }
+    int2* Hb = reinterpret_cast<int2*>(hplane);
+    Hb[qi] = make_int2(H1[2], H1[3]);
+    __syncthreads();
+    const int2 ha = Hb[qa];
+    const int32_t hl0 = from_left<NC>(H2[1], l), hl2 = from_left<NC>(H2[3], l);
+    const int32_t h1up[4] = {ha.x, ha.y, H1[0], H1[1]}, h2lf[4] = {hl0, H2[0], hl2, H2[2]};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const long long v = (long long)q[c] + ((long long)H1[c] - h1up[c]) + ((long long)H2[c] - h2lf[c]);
+        bad |= (unsigned)((v >= (1LL << 30)) | (v <= -(1LL << 30)));
+        q[c] = static_cast<int32_t>(v);
+    }
+    __syncthreads();
+}
+
 template <int N, bool CPL>
 __global__ void __launch_bounds__(TShape<N>::THREADS) theta_kernel(const KArgs a, const TArgs t) {
     using S = TShape<N>;
@@ -169,8 +325,7 @@ __global__ void __launch_bounds__(TShape<N>::THREADS) theta_kernel(const KArgs a
     const int tid = threadIdx.x;
     const int sl = tid / TPS, lt = tid % TPS;   // sample slot in the CTA, thread within the sample
     unsigned char* base = smem_raw + S::SAMPLE_BYTES * sl;
-    int32_t* sq = reinterpret_cast<int32_t*>(base);
-    float* P0 = reinterpret_cast<float*>(sq + N * N);
+    float* P0 = reinterpret_cast<float*>(base);
     float* P1 = P0 + N * N;
     float* P2 = P1 + N * N;
     float* P3 = P2 + N * N;
@@ -178,13 +333,14 @@ __global__ void __launch_bounds__(TShape<N>::THREADS) theta_kernel(const KArgs a
     double* red = reinterpret_cast<double*>(smem_raw + S::SAMPLE_BYTES * SPB);
     double* acc = red + ((THREADS + 31) / 32) * kRed;
     for (int i = tid; i < SPB * a.slot_stride; i += THREADS) acc[i] = 0.0;
+    float* const planes[4] = {P0, P1, P2, P3};
 
     const int I1 = lt / NC, I2 = lt % NC;   // coarse cell; fine block rows 2 I1 + v1, cols 2 I2 + v2
-    const int frow[4] = {2 * I1, 2 * I1, 2 * I1 + 1, 2 * I1 + 1};
-    const int fcol[4] = {2 * I2, 2 * I2 + 1, 2 * I2, 2 * I2 + 1};
     const int crow[1] = {I1}, ccol[1] = {I2};
-    const uint32_t p_top = static_cast<uint32_t>((frow[0] * N + fcol[0]) >> 1);
-    const uint32_t p_bot = static_cast<uint32_t>((frow[2] * N + fcol[2]) >> 1);
+    const int f00 = (2 * I1) * N + 2 * I2;  // fine index of the block's top-left cell
+    const int fidx[4] = {f00, f00 + 1, f00 + N, f00 + N + 1};
+    const uint32_t p_top = static_cast<uint32_t>(f00 >> 1);
+    const uint32_t p_bot = static_cast<uint32_t>((f00 + N) >> 1);
 
     const long long n_slots = (long long)gridDim.x * SPB;
     const long long slot = (long long)blockIdx.x * SPB + sl;
@@ -202,10 +358,7 @@ __global__ void __launch_bounds__(TShape<N>::THREADS) theta_kernel(const KArgs a
 
         int32_t q[4], qc[1] = {0};
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            q[i] = a.q0f[frow[i] * N + fcol[i]];
-            sq[frow[i] * N + fcol[i]] = q[i];
-        }
+        for (int i = 0; i < 4; ++i) q[i] = a.q0f[fidx[i]];
         float zt0 = 0.f, zt1 = 0.f;
         if constexpr (CPL) {
             qc[0] = a.q0c[lt];
@@ -233,13 +386,7 @@ __global__ void __launch_bounds__(TShape<N>::THREADS) theta_kernel(const KArgs a
                     zt1 = fmaf(rb, sb, fmaf(ra, sa, zt1));
                 }
             }
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                P0[frow[i] * N + fcol[i]] = as_f(G1[i]);
-                P2[frow[i] * N + fcol[i]] = as_f(G2[i]);
-            }
-            __syncthreads();
-            theta_step<N, 4>(q, frow, fcol, sq, P0, P1, P2, P3, t.Af64, t, bad);
+            theta_fine_step<N>(q, G1, G2, I1, I2, planes, t.Af64, t, bad);
 
             if constexpr (CPL) {
                 if ((m & 3) == 3) {
@@ -267,10 +414,8 @@ __global__ void __launch_bounds__(TShape<N>::THREADS) theta_kernel(const KArgs a
                 double sf = 0.0, sc = 0.0;
                 if (k < a.n_obs) {
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const int x = frow[i] * N + fcol[i];
-                        sf += static_cast<double>(q[i] - a.qbf[x]) * t.phif64[(size_t)k * N * N + x];
-                    }
+                    for (int i = 0; i < 4; ++i)
+                        sf += static_cast<double>(q[i] - a.qbf[fidx[i]]) * t.phif64[(size_t)k * N * N + fidx[i]];
                     if constexpr (CPL) sc = static_cast<double>(qc[0] - a.qbc[lt]) * t.phic64[(size_t)k * NC * NC + lt];
                 }
                 v[k] = sf;
