@@ -63,10 +63,20 @@ LEVEL_KERNEL_INSTR_PER_CELL_STEP = 59.0
 KERNEL_SOURCES = ("dk_kernels.cu", "dk_device.cuh")   # the level kernel and its device functions
 
 
-def kernel_sources_hash() -> str:
+# Theta-scheme kernel (implicit diffusion weight b0 > 0): thread instructions
+# per fine cell-step (coupled, coarse work included) of the 64^2 coupled
+# launch at b0 = 1/2, tau/h^2 = 0.85 (14 Chebyshev steps per solve), from its
+# ncu --set full capture (smsp__inst_executed x 32 / fine cell-steps); valid
+# under the recorded hash of its sources.  Bound by instruction issue.
+THETA_KERNEL_INSTR = {"kernel": "theta_kernel n=64 coupled=True b0=0.5 chebyshev_steps=14",
+                      "instructions_per_fine_cell_step": 580.6, "sources_sha256_16": "5f4fec27e80df0df"}
+THETA_SOURCES = ("dk_theta.cu", "dk_device.cuh")
+
+
+def kernel_sources_hash(files=KERNEL_SOURCES) -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in files:
         with open(os.path.join(ROOT, "paper_2311_08872_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -127,6 +137,41 @@ def streamed_stencil(stream):
             "bound": "alu (instruction issue): the working set stays in L2, DRAM traffic is the cold start only"}
 
 
+def theta_scheme(stream):
+    """The theta-scheme kernel on the finest level of the Crank--Nicolson
+    workload (64^2 coupled with 32^2, b0 = 1/2, tau/h^2 = 0.85): 32 waves of one
+    sample per SM, CUDA events on the launching stream, against the
+    instruction-issue roofline."""
+    import torch
+    from paper_2311_08872_gb300 import mlmc_dk, workloads
+    wl = workloads.get("theta16_64")
+    level = wl.L_max
+    count = 32 * SMS
+    with mlmc_dk.Context.from_workload(wl, stream=stream.cuda_stream) as c:
+        info = c.level_info(level)
+        sums = torch.zeros(mlmc_dk.sums_len(c.n_quant), dtype=torch.float64, device="cuda")
+        c.run_level_dev(level, 0, 0, count, 11, sums.data_ptr(), 0, stream.cuda_stream)      # warm-up
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        c.run_level_dev(level, 0, count, count, 11, sums.data_ptr(), 0, stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) * 1e-3
+    fine = count * info.n ** 2 * info.M
+    out = {"workload": wl.name, "level": level, "n": info.n, "fine_steps": info.M, "b0": info.theta_b0,
+           "tau_over_h2": info.tau / info.h ** 2, "chebyshev_steps": info.cheb_steps, "samples": count, "s": sec,
+           "cell_steps_per_s": count * info.cost / sec, "fine_cell_steps_per_s": fine / sec,
+           "coupled_sample_steps_per_s": count * info.M / sec, "bound": "alu (instruction issue)"}
+    if kernel_sources_hash(THETA_SOURCES) == THETA_KERNEL_INSTR["sources_sha256_16"]:
+        ipc = THETA_KERNEL_INSTR["instructions_per_fine_cell_step"]
+        warp_inst = fine * ipc / 32.0 / sec
+        peak = 4.0 * SMS * SM_MAX_MHZ * 1e6
+        out["issue"] = {"instructions_per_fine_cell_step": ipc, "achieved_warp_inst_per_s": warp_inst,
+                        "peak_warp_inst_per_s": peak, "frac": warp_inst / peak}
+    return out
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -137,6 +182,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-streamed", action="store_true", help="skip the streamed-state stencil timing")
+    ap.add_argument("--no-theta", action="store_true", help="skip the theta-scheme kernel timing")
     ap.add_argument("--split-fraction", type=float, default=None,
                     help="fixed batch split of the finest cluster level (default: autotuned)")
     ap.add_argument("--no-adaptive", action="store_true", help="skip the Algorithm 1 / plain MC timing")
@@ -467,6 +513,9 @@ def run_ours(args, wl, rank, world, local_rank):
     streamed = None
     if not args.no_streamed:
         streamed = streamed_stencil(stream)
+    theta = None
+    if not args.no_theta:
+        theta = theta_scheme(stream)
 
     e2e = None
     if not args.no_e2e:
@@ -541,6 +590,7 @@ def run_ours(args, wl, rank, world, local_rank):
                                              "level N h^2 = %.2g particles per cell, so it is a lower bound and "
                                              "the gap is the positive-part effect" % (wl.N * (wl.length / fin.n) ** 2)}
     line["streamed_stencil"] = streamed
+    line["theta_scheme"] = theta
     if surrogate:
         line["surrogate"] = surrogate
         line["mlmc_surrogate_s_to_eps"] = surrogate["mlmc_s_to_eps_incl_training"]
