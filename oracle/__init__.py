@@ -52,6 +52,7 @@ class _OracleLevelC(ctypes.Structure):
         ("phi_f", _dp),
         ("phi_c", _dp),
         ("b0", ctypes.c_double),
+        ("coupling", ctypes.c_int),
     ]
 
 
@@ -80,6 +81,7 @@ def lib():
         L.oracle_theta_step.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                         ctypes.c_double, _dp, _dp, _dp]
         L.oracle_helmholtz_solve.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp]
+        L.oracle_fourier_restrict.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp]
         L.oracle_mean_field_theta.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
                                               ctypes.c_double, _dp, _dp]
         _LIB = L
@@ -138,6 +140,15 @@ def helmholtz_solve(n: int, c: float, rhs: np.ndarray) -> np.ndarray:
     return out
 
 
+def fourier_restrict(n: int, nc: int, fine: np.ndarray) -> np.ndarray:
+    """The coarse field of the Fourier coupling (Section 3.1) carrying the modes
+    of the fine field that the nc x nc grid resolves (see oracle_fourier_restrict)."""
+    fine = np.ascontiguousarray(fine, dtype=np.float64).reshape(n, n)
+    out = np.empty((nc, nc))
+    lib().oracle_fourier_restrict(n, nc, _ptr(fine), _ptr(out))
+    return out
+
+
 def mean_field(n: int, h: float, tau: float, M: int, rho0: np.ndarray, b0: float = 0.0) -> np.ndarray:
     """The discrete mean field rho-bar: the noise-free scheme iterated M times
     (weights (b0, 1 - b0) of Eq. FullyDiscreteDK)."""
@@ -165,9 +176,10 @@ class Level:
     M: int
 
 
-def level_table(length: float, n0: int, L_max: int, T: float, mu: float, M0: int = 0) -> List[Level]:
-    """Levels with tau_l / h_l^2 fixed (Eq. cfl_preserved), h_{l-1} = 2 h_l and
-    tau_{l-1} = 4 tau_l (Section 7.2).  T / tau_0 must be an integer; where the
+def level_table(length: float, n0: int, L_max: int, T: float, mu: float, M0: int = 0, ratio: int = 2) -> List[Level]:
+    """Levels with tau_l / h_l^2 fixed (Eq. cfl_preserved), h_{l-1} = r h_l and
+    tau_{l-1} = r^2 tau_l: r = 2 for the NN coupling (Section 7.2), r = 3 for
+    the Fourier coupling (Section 3.1).  T / tau_0 must be an integer; where the
     nominal mu does not give one, M_0 = ceil(T / (mu h_0^2)) and tau_0 = T / M_0,
     so the effective ratio is at most mu and the same on every level."""
     h0 = length / n0
@@ -175,7 +187,8 @@ def level_table(length: float, n0: int, L_max: int, T: float, mu: float, M0: int
         x = T / (mu * h0 * h0)
         M0 = int(math.ceil(x - 1e-9 * x))
     tau0 = T / M0
-    return [Level(l, n0 << l, h0 / (1 << l), tau0 / (4 ** l), M0 * (4 ** l)) for l in range(L_max + 1)]
+    k = ratio * ratio
+    return [Level(l, n0 * ratio ** l, h0 / ratio ** l, tau0 / (k ** l), M0 * (k ** l)) for l in range(L_max + 1)]
 
 
 # ---------------------------------------------------------------- samples
@@ -184,10 +197,11 @@ class OracleLevel:
 
     def __init__(self, lv: Level, N: float, rho0_f: np.ndarray, phi_f: Sequence[np.ndarray],
                  rho0_c: Optional[np.ndarray] = None, phi_c: Optional[Sequence[np.ndarray]] = None,
-                 b0: float = 0.0):
+                 b0: float = 0.0, coupling: int = 0):
         self.lv = lv
         self.N = N
         self.b0 = float(b0)
+        self.coupling = int(coupling)
         self.n_obs = len(phi_f)
         self.rho0_f = np.ascontiguousarray(rho0_f, dtype=np.float64).reshape(-1)
         self.phi_f = np.ascontiguousarray(np.stack(phi_f), dtype=np.float64)
@@ -196,7 +210,7 @@ class OracleLevel:
         self.c = _OracleLevelC(lv.n, lv.h, lv.tau, lv.M, lv.level,
                                0.0 if not N else 1.0 / math.sqrt(N),
                                _ptr(self.rho0_f), _ptr(self.rho0_c), self.n_obs,
-                               _ptr(self.phi_f), _ptr(self.phi_c), self.b0)
+                               _ptr(self.phi_f), _ptr(self.phi_c), self.b0, self.coupling)
 
     def sample(self, seed: int, sample: int, coupled: bool, stream: int = 0, fields: bool = False):
         n = self.lv.n
@@ -205,7 +219,8 @@ class OracleLevel:
         mf = ctypes.c_double(0.0)
         mc = ctypes.c_double(0.0)
         rf = np.empty(n * n) if fields else None
-        rc = np.empty((n // 2) ** 2) if (fields and coupled) else None
+        nc = n // (3 if self.coupling == 1 else 2)
+        rc = np.empty(nc * nc) if (fields and coupled) else None
         rc_ = lib().oracle_sample(ctypes.byref(self.c), seed, stream, sample, int(coupled),
                                   _ptr(Yf), _ptr(Yc), ctypes.byref(mf), ctypes.byref(mc),
                                   _ptr(rf), _ptr(rc))
@@ -216,7 +231,7 @@ class OracleLevel:
         if fields:
             out["rho_f"] = rf.reshape(n, n)
             if coupled:
-                out["rho_c"] = rc.reshape(n // 2, n // 2)
+                out["rho_c"] = rc.reshape(nc, nc)
         return out
 
 
@@ -232,7 +247,8 @@ class OracleLevel:
         mf = ctypes.c_double(0.0)
         mc = ctypes.c_double(0.0)
         rf = np.empty(n * n) if fields else None
-        rc = np.empty((n // 2) ** 2) if (fields and coupled) else None
+        nc = n // (3 if self.coupling == 1 else 2)
+        rc = np.empty(nc * nc) if (fields and coupled) else None
         rc_ = lib().oracle_sample_given(ctypes.byref(self.c), _ptr(Z), int(coupled), _ptr(Yf), _ptr(Yc),
                                         ctypes.byref(mf), ctypes.byref(mc), _ptr(rf), _ptr(rc))
         if rc_ != 0:
@@ -241,7 +257,7 @@ class OracleLevel:
         if fields:
             out["rho_f"] = rf.reshape(n, n)
             if coupled:
-                out["rho_c"] = rc.reshape(n // 2, n // 2)
+                out["rho_c"] = rc.reshape(nc, nc)
         return out
 
     def sample_perturbed(self, seed: int, sample: int, coupled: bool, amp: float, perturb_seed: int,
@@ -260,16 +276,17 @@ class OracleLevel:
 
 
 def level_inputs(length: float, levels: List[Level], N: float, rho0: List[np.ndarray],
-                 phi: List[List[np.ndarray]], level: int, coupled: bool, b0: float = 0.0) -> OracleLevel:
+                 phi: List[List[np.ndarray]], level: int, coupled: bool, b0: float = 0.0,
+                 coupling: int = 0) -> OracleLevel:
     lv = levels[level]
     if coupled and level > 0:
-        return OracleLevel(lv, N, rho0[level], phi[level], rho0[level - 1], phi[level - 1], b0=b0)
-    return OracleLevel(lv, N, rho0[level], phi[level], b0=b0)
+        return OracleLevel(lv, N, rho0[level], phi[level], rho0[level - 1], phi[level - 1], b0=b0, coupling=coupling)
+    return OracleLevel(lv, N, rho0[level], phi[level], b0=b0, coupling=coupling)
 
 
 def _run_chunk(args):
-    (lv, N, rho0_f, phi_f, rho0_c, phi_c, seed, ids, coupled, stream, b0) = args
-    ol = OracleLevel(lv, N, rho0_f, phi_f, rho0_c, phi_c, b0=b0)
+    (lv, N, rho0_f, phi_f, rho0_c, phi_c, seed, ids, coupled, stream, b0, coupling) = args
+    ol = OracleLevel(lv, N, rho0_f, phi_f, rho0_c, phi_c, b0=b0, coupling=coupling)
     res = [ol.sample(seed, int(i), coupled, stream) for i in ids]
     return res
 
@@ -287,7 +304,7 @@ def run_samples(ol: OracleLevel, seed: int, ids: Sequence[int], coupled: bool, s
         import multiprocessing as mp
         chunks = [ids[i::processes] for i in range(processes)]
         args = [(ol.lv, ol.N, ol.rho0_f, list(ol.phi_f), ol.rho0_c,
-                 None if ol.phi_c is None else list(ol.phi_c), seed, c, coupled, stream, ol.b0)
+                 None if ol.phi_c is None else list(ol.phi_c), seed, c, coupled, stream, ol.b0, ol.coupling)
                 for c in chunks if c]
         with mp.get_context("spawn").Pool(len(args)) as pool:
             parts = pool.map(_run_chunk, args)

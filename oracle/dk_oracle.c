@@ -255,27 +255,96 @@ static void perturb_edges(int n, double amp, uint64_t* state, double* rho)
         }
 }
 
+void oracle_fourier_restrict(int n, int nc, const double* fine, double* coarse)
+{
+    /* unitary DFT of the fine field on the kept modes (separable sums: along
+     * x2 for every row, then along x1), weights, inverse DFT on the coarse grid */
+    const int K = nc / 2;
+    const int J = 2 * K + 1;   /* modes -K..K per axis */
+    double* cs = (double*)malloc(sizeof(double) * (size_t)n);
+    double* sn = (double*)malloc(sizeof(double) * (size_t)n);
+    for (int j = 0; j < n; ++j) {
+        cs[j] = cos(2.0 * M_PI * j / n);
+        sn[j] = sin(2.0 * M_PI * j / n);
+    }
+    /* row transforms: t(x1, xi2) = sum_x2 f(x1, x2) exp(-2 pi i xi2 x2 / n) */
+    double* tre = (double*)malloc(sizeof(double) * (size_t)n * J);
+    double* tim = (double*)malloc(sizeof(double) * (size_t)n * J);
+    for (int x1 = 0; x1 < n; ++x1)
+        for (int b = 0; b < J; ++b) {
+            double sr = 0.0, si = 0.0;
+            for (int x2 = 0; x2 < n; ++x2) {
+                const int t = (int)((((int64_t)(b - K) * x2) % n + n) % n);
+                sr += fine[x1 * n + x2] * cs[t];
+                si -= fine[x1 * n + x2] * sn[t];
+            }
+            tre[x1 * J + b] = sr;
+            tim[x1 * J + b] = si;
+        }
+    /* column transforms and weights: c(xi1, xi2) */
+    double* cre = (double*)malloc(sizeof(double) * (size_t)J * J);
+    double* cim = (double*)malloc(sizeof(double) * (size_t)J * J);
+    for (int a = 0; a < J; ++a)
+        for (int b = 0; b < J; ++b) {
+            double sr = 0.0, si = 0.0;
+            for (int x1 = 0; x1 < n; ++x1) {
+                const int t = (int)((((int64_t)(a - K) * x1) % n + n) % n);
+                /* (tre + i tim) (cos - i sin) */
+                sr += tre[x1 * J + b] * cs[t] + tim[x1 * J + b] * sn[t];
+                si += tim[x1 * J + b] * cs[t] - tre[x1 * J + b] * sn[t];
+            }
+            const double w = ((a == 0 || a == J - 1) ? M_SQRT1_2 : 1.0) * ((b == 0 || b == J - 1) ? M_SQRT1_2 : 1.0);
+            cre[a * J + b] = w * sr / n;
+            cim[a * J + b] = w * si / n;
+        }
+    /* inverse on the coarse grid, real part: g(y) = nc^-1 sum c(xi) exp(2 pi i xi.y / nc) */
+    double* ccs = (double*)malloc(sizeof(double) * (size_t)nc);
+    double* csn = (double*)malloc(sizeof(double) * (size_t)nc);
+    for (int j = 0; j < nc; ++j) {
+        ccs[j] = cos(2.0 * M_PI * j / nc);
+        csn[j] = sin(2.0 * M_PI * j / nc);
+    }
+    for (int y1 = 0; y1 < nc; ++y1)
+        for (int y2 = 0; y2 < nc; ++y2) {
+            double g = 0.0;
+            for (int a = 0; a < J; ++a)
+                for (int b = 0; b < J; ++b) {
+                    const int t = (int)((((int64_t)(a - K) * y1 + (int64_t)(b - K) * y2) % nc + nc) % nc);
+                    g += cre[a * J + b] * ccs[t] - cim[a * J + b] * csn[t];
+                }
+            coarse[y1 * nc + y2] = g / nc;
+        }
+    free(cs); free(sn); free(ccs); free(csn); free(tre); free(tim); free(cre); free(cim);
+}
+
 static int sample_impl(const oracle_level* lv, uint64_t seed, int stream, uint64_t sample,
                        int coupled, double amp, uint64_t perturb_seed, const double* given,
                        double* Y_f, double* Y_c, double* mass_f, double* mass_c,
                        double* rho_f_out, double* rho_c_out)
 {
     uint64_t pstate = perturb_seed;
-    const int n = lv->n, nc = n / 2;
+    const int fourier = lv->coupling == 1;
+    const int ratio = fourier ? 3 : 2, kappa = ratio * ratio;   /* h and tau ratios (Eq. cfl_preserved) */
+    const int n = lv->n, nc = n / ratio;
     if (n < 2 || (n & 1)) return -1;
-    if (coupled && (lv->M % 4) != 0) return -2;
+    if (coupled && ((lv->M % kappa) != 0 || n % ratio != 0 || (nc & 1))) return -2;
     const size_t cf = (size_t)n * n, cc = (size_t)nc * nc;
     double* rho_f = (double*)malloc(sizeof(double) * cf);
     double* tmp_f = (double*)malloc(sizeof(double) * cf);
     double* Z = (double*)malloc(sizeof(double) * cf * 2);
     double* dbeta_f = (double*)malloc(sizeof(double) * cf * 2);
-    double* rho_c = NULL, *tmp_c = NULL, *dbeta_c = NULL;
+    double* rho_c = NULL, *tmp_c = NULL, *dbeta_c = NULL, *sum_f = NULL, *comp_f = NULL, *comp_c = NULL;
     memcpy(rho_f, lv->rho0_f, sizeof(double) * cf);
     if (coupled) {
         rho_c = (double*)malloc(sizeof(double) * cc);
         tmp_c = (double*)malloc(sizeof(double) * cc);
         dbeta_c = (double*)calloc(cc * 2, sizeof(double));
         memcpy(rho_c, lv->rho0_c, sizeof(double) * cc);
+        if (fourier) {
+            sum_f = (double*)calloc(cf * 2, sizeof(double));
+            comp_f = (double*)malloc(sizeof(double) * cf);
+            comp_c = (double*)malloc(sizeof(double) * cc);
+        }
     }
     const double sqrt_tau = sqrt(lv->tau);
     const double block_weight = pow(2.0, -0.5 * 2);   /* 2^{-d/2} of the NN coupling */
@@ -285,7 +354,11 @@ static int sample_impl(const oracle_level* lv, uint64_t seed, int stream, uint64
         else
             oracle_normals(seed, lv->level, stream, sample, m, n, Z);
         for (size_t i = 0; i < cf * 2; ++i) dbeta_f[i] = sqrt_tau * Z[i];
-        if (coupled) {
+        if (coupled && fourier) {
+            /* Fourier coupling: the coarse increment over one coarse step carries the
+             * modes of the sum of the kappa_t = 9 fine increments inside it */
+            for (size_t i = 0; i < cf * 2; ++i) sum_f[i] += dbeta_f[i];
+        } else if (coupled) {
             /* beta-tilde_(y,r) = 2^{-d/2} sum_{z in B->(y)} beta_(z,r), B->(y) = {y + h v}:
              * fine cells (2 I1 + v1, 2 I2 + v2).  The coarse increment over one coarse
              * step is the sum of the kappa_t = 4 fine increments inside it. */
@@ -299,8 +372,16 @@ static int sample_impl(const oracle_level* lv, uint64_t seed, int stream, uint64
         oracle_theta_step(n, lv->h, lv->tau, lv->inv_sqrt_N, lv->b0, rho_f, dbeta_f, tmp_f);
         double* t = rho_f; rho_f = tmp_f; tmp_f = t;
         if (amp > 0.0) perturb_edges(n, amp, &pstate, rho_f);
-        if (coupled && (m % 4) == 3) {
-            oracle_theta_step(nc, 2.0 * lv->h, 4.0 * lv->tau, lv->inv_sqrt_N, lv->b0, rho_c, dbeta_c, tmp_c);
+        if (coupled && (m % kappa) == kappa - 1) {
+            if (fourier) {
+                for (int r = 0; r < 2; ++r) {
+                    for (size_t i = 0; i < cf; ++i) comp_f[i] = sum_f[2 * i + r];
+                    oracle_fourier_restrict(n, nc, comp_f, comp_c);
+                    for (size_t i = 0; i < cc; ++i) dbeta_c[2 * i + r] = comp_c[i];
+                }
+                memset(sum_f, 0, sizeof(double) * cf * 2);
+            }
+            oracle_theta_step(nc, ratio * lv->h, kappa * lv->tau, lv->inv_sqrt_N, lv->b0, rho_c, dbeta_c, tmp_c);
             double* tc = rho_c; rho_c = tmp_c; tmp_c = tc;
             memset(dbeta_c, 0, sizeof(double) * cc * 2);
             if (amp > 0.0) perturb_edges(nc, amp, &pstate, rho_c);
@@ -313,13 +394,14 @@ static int sample_impl(const oracle_level* lv, uint64_t seed, int stream, uint64
     if (rho_f_out) memcpy(rho_f_out, rho_f, sizeof(double) * cf);
     if (coupled) {
         for (int k = 0; k < lv->n_obs; ++k)
-            Y_c[k] = inner_h(nc, 2.0 * lv->h, rho_c, lv->phi_c + (size_t)k * cc);
-        if (mass_c) *mass_c = inner_h(nc, 2.0 * lv->h, rho_c, ones);
+            Y_c[k] = inner_h(nc, ratio * lv->h, rho_c, lv->phi_c + (size_t)k * cc);
+        if (mass_c) *mass_c = inner_h(nc, ratio * lv->h, rho_c, ones);
         if (rho_c_out) memcpy(rho_c_out, rho_c, sizeof(double) * cc);
     }
     free(ones);
     free(rho_f); free(tmp_f); free(Z); free(dbeta_f);
     free(rho_c); free(tmp_c); free(dbeta_c);
+    free(sum_f); free(comp_f); free(comp_c);
     return 0;
 }
 

@@ -12,7 +12,8 @@
  *     and with general weights b0 + b1 = 1 (the theta-scheme: an implicit
  *     diffusion half, Definition 2.1 and Appendix C, Lemma Discrete_Energy_Est),
  *   - the operators Delta_h and nabla_h. of Section 7.2,
- *   - the Right-Most Nearest-Neighbour coupling of Section 3.2,
+ *   - the Right-Most Nearest-Neighbour coupling of Section 3.2 and the Fourier
+ *     coupling of Section 3.1 (h_{l-1} = 3 h_l, tau_{l-1} = 9 tau_l),
  *   - the observable P_l of Eq. (eqn_MLMCLevels) with psi(x) = x^2.
  *
  * Conventions (readings where the paper is silent; same reading as the CUDA
@@ -77,10 +78,24 @@ typedef struct {
     const double* phi_f; /* [n_obs][n*n] */
     const double* phi_c; /* [n_obs][(n/2)^2] */
     double b0;           /* implicit weight of Eq. (FullyDiscreteDK) (0: explicit Euler--Maruyama) */
+    int coupling;        /* 0: Right-Most NN (coarse mesh 2h, step 4 tau); 1: Fourier (3h, 9 tau) */
 } oracle_level;
 
-/* One sample of level `lv`: fine path, and if `coupled` the NN-coupled coarse
- * path (mesh 2h, step 4 tau, increments summed over 2x2 cells and 4 steps);
+/* Fourier coupling of Section 3.1: the coarse-grid field carrying the fine
+ * field's Fourier modes that the coarse grid (nc = n/3 points, nc even)
+ * resolves.  With the unitary discrete Fourier coefficients
+ * c(xi) = n^-1 sum_x f(x) exp(-2 pi i xi.x/n) of the fine field f,
+ *   g(y) = nc^-1 sum_{xi in J^2} w(xi_1) w(xi_2) c(xi) exp(2 pi i xi.y/nc),
+ * J = {-nc/2, ..., nc/2}, w = 1 except w(+-nc/2) = 2^-1/2 (the two fine modes
+ * that alias to the coarse Nyquist mode share it), so that g is real and, for
+ * a white f, white with the same variance (Remark distribution_W_ell).
+ * Coarse point y is the fine point 3y. */
+void oracle_fourier_restrict(int n, int nc, const double* fine, double* coarse);
+
+/* One sample of level `lv`: fine path, and if `coupled` the coupled coarse
+ * path: NN (mesh 2h, step 4 tau, increments summed over 2x2 cells and 4
+ * steps) or Fourier (mesh 3h, step 9 tau, oracle_fourier_restrict of the sum
+ * of the 9 fine increments);
  * both paths step with oracle_theta_step and the level's b0.
  * Outputs Y_f[k] = (rho_f^M, phi_f[k])_h, Y_c[k] likewise on the coarse grid,
  * masses (rho, 1)_h, and optionally the final fields.  Returns 0 on success. */
