@@ -112,6 +112,13 @@ typedef struct {
                                b0 cfl_mu <= 10 */
     int32_t theta_kernel;   /* 1: run b0 = 0 on the theta-scheme kernel too (the same integer
                                arithmetic as the explicit kernels); 0: default */
+    int32_t coupling;       /* 0: Right-Most Nearest-Neighbour coupling (Section 3.2), h_{l-1} = 2 h_l,
+                               tau_{l-1} = 4 tau_l; 1: Fourier coupling (Section 3.1), h_{l-1} = 3 h_l,
+                               tau_{l-1} = 9 tau_l: the coarse noise of a coarse step carries every
+                               Fourier mode of the summed fine noise that the coarse grid resolves (the
+                               coarse Nyquist mode takes its two fine aliases with weight 2^-1/2 each).
+                               Fourier: n0 = 6, L_max <= 2 (grids 6^2, 18^2, 54^2), explicit scheme,
+                               level n_l = n0 3^l, M_l = M_0 9^l; rho0 / phi arrays on those grids */
 } mlmc_dk_config;
 
 /* Per-level description returned by mlmc_dk_level_info. */
@@ -140,6 +147,7 @@ typedef struct {
     int32_t theta;          /* 1: the level runs on the theta-scheme kernel */
     double theta_b0;        /* its implicit weight b0 */
     int32_t cheb_steps;     /* Chebyshev steps per implicit solve (0: none) */
+    int32_t coupling;       /* 0: NN, 1: Fourier (as configured) */
 } mlmc_dk_level_desc;
 
 /* Host-side moment sums of one quantity on one level (accumulated into). */

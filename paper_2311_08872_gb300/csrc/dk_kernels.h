@@ -129,6 +129,18 @@ cudaError_t theta_variant_info(int n, bool coupled, int slot_stride, VariantInfo
 cudaError_t launch_theta(int n, bool coupled, const KArgs& a, const TArgs& t, int n_ctas, cudaStream_t stream,
                          int priority = 0);
 
+// ---- Fourier coupling (Section 3.1): grids 6, 18, 54 (h ratio 3, tau ratio 9)
+struct FArgs {
+    const float* P1;           // [n/3][n] restriction of the fine normals to the coarse grid (coupled only)
+    const double* phif64;      // FP64 test functions [n_obs][n^2] / [n_obs][(n/3)^2]
+    const double* phic64;
+};
+bool fourier_supported(int n);
+cudaError_t fourier_variant_info(int n, bool coupled, int slot_stride, VariantInfo* out);
+// One CTA per sample slot; partials must hold n_ctas * slot_stride doubles.
+cudaError_t launch_fourier(int n, bool coupled, const KArgs& a, const FArgs& f, int n_ctas, cudaStream_t stream,
+                           int priority = 0);
+
 // ---- learned level below level 0
 constexpr int kModes = 32;     // real orthonormal modes
 constexpr int kFeat = 64;      // features = modes x 2 noise components

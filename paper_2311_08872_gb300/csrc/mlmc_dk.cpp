@@ -37,6 +37,7 @@ struct LevelTab {
     int32_t* d_qbar = nullptr;
     float* d_phi = nullptr;
     double* d_phi64 = nullptr;             // the same test functions in FP64 (observables of the streamed path)
+    float* d_P1 = nullptr;                 // Fourier coupling: restriction of this level's normals to level l-1
     std::vector<dk::VariantInfo> vis[2];   // kernel variants: [0] fine path only, [1] coupled pair
     int streamed = 0;                      // no register variant: state streamed through global memory
     int inflight = 0;                      // samples in flight on the streamed path (buffers sized for this)
@@ -61,6 +62,7 @@ struct mlmc_dk_ctx {
     int L_max = 0, n_obs = 1, products = 0, n_quant = 1, stride = 0, pilot = 256, L_start = 2;
     double b0 = 0;              // implicit weight of Eq. (FullyDiscreteDK)
     int theta = 0;              // every level runs on the theta-scheme kernel
+    int coupling = 0;           // 0: Right-Most NN (h ratio 2); 1: Fourier (h ratio 3, Section 3.1)
     dk::TArgs targs{};          // its Chebyshev schedule (per-level fields filled at launch)
     std::vector<LevelTab> lv;
     cudaStream_t stream = nullptr;
@@ -195,6 +197,29 @@ void mean_field(int n, double h, double tau, long long M, const double* rho0, do
     for (size_t i = 0; i < a.size(); ++i) out[i] = a[i].real() * inv;
 }
 
+// The same for any even n (grids of the Fourier coupling are not powers of
+// two): the noise-free step applied M times in FP64 (5-point stencil; the
+// implicit half, if any, by the Fourier symbol).
+void mean_field_any(int n, double h, double tau, long long M, const double* rho0, double* out, double b0 = 0.0) {
+    if (is_pow2(n)) {
+        mean_field(n, h, tau, M, rho0, out, b0);
+        return;
+    }
+    std::vector<double> a(rho0, rho0 + (size_t)n * n), b((size_t)n * n);
+    const double w = tau / (2.0 * h * h);
+    for (long long m = 0; m < M; ++m) {
+        for (int i1 = 0; i1 < n; ++i1)
+            for (int i2 = 0; i2 < n; ++i2) {
+                const double c = a[(size_t)i1 * n + i2];
+                const double s = a[(size_t)((i1 + 1) % n) * n + i2] + a[(size_t)((i1 + n - 1) % n) * n + i2] +
+                                 a[(size_t)i1 * n + (i2 + 1) % n] + a[(size_t)i1 * n + (i2 + n - 1) % n];
+                b[(size_t)i1 * n + i2] = c + w * (s - 4.0 * c);
+            }
+        a.swap(b);
+    }
+    std::copy(a.begin(), a.end(), out);
+}
+
 int quantities(int n_obs, int products) { return products ? n_obs * (n_obs + 1) / 2 : n_obs; }
 
 // Fill the kernel arguments of one batch.
@@ -230,7 +255,9 @@ dk::KArgs make_args(mlmc_dk_ctx* c, int level, int stream_tag, bool coupled, int
         a.qbc = g.d_qbar;
         a.phic = g.d_phi;
         a.Ac = g.A;
-        a.gc = 0.25f * g.g;   // coupled coarse normal = 1/4 x (sum of 16 fine normals)
+        // coupled coarse normal: NN 1/4 x (sum of 16 fine normals); Fourier 1/3 x (restriction
+        // of the sum of 9 fine normal fields, each restricted field white with unit variance)
+        a.gc = c->coupling == 1 ? g.g / 3.0f : 0.25f * g.g;
         a.dscale_c = g.dscale;
         a.mass0_c = g.mass0;
         for (int k = 0; k < dk::kMaxObs; ++k) a.delta_c[k] = g.delta[k];
@@ -292,6 +319,13 @@ int launch_streamed(mlmc_dk_ctx* c, int level, int stream_tag, int64_t first, in
 cudaError_t launch_main(const mlmc_dk_ctx* c, int level, bool coupled, const dk::KArgs& a, int n_ctas,
                         cudaStream_t st, int priority) {
     const LevelTab& t = c->lv[level];
+    if (c->coupling == 1) {
+        dk::FArgs fa{};
+        fa.P1 = coupled ? t.d_P1 : nullptr;
+        fa.phif64 = t.d_phi64;
+        fa.phic64 = coupled ? c->lv[level - 1].d_phi64 : nullptr;
+        return dk::launch_fourier(t.n, coupled, a, fa, n_ctas, st, priority);
+    }
     if (c->theta) {
         dk::TArgs ta = c->targs;
         ta.Af64 = t.A64;
@@ -395,6 +429,7 @@ void release(mlmc_dk_ctx* c) {
         cudaFree(l.d_qbar);
         cudaFree(l.d_phi);
         cudaFree(l.d_phi64);
+        cudaFree(l.d_P1);
         cudaFree(l.d_stream);
         cudaFree(l.d_spart);
     }
@@ -447,9 +482,21 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
     if (!out) return fail(nullptr, MLMC_DK_ERR_INVALID, "null output pointer");
     *out = nullptr;
     if (!cfg) return fail(nullptr, MLMC_DK_ERR_INVALID, "null config");
-    if (!is_pow2(cfg->n0) || cfg->n0 < 4 || cfg->L_max < 0 || cfg->L_max >= MLMC_DK_MAX_LEVELS ||
-        ((long long)cfg->n0 << cfg->L_max) > 1024)
+    const bool fourier = cfg->coupling == 1;
+    if (cfg->coupling != 0 && !fourier) return fail(nullptr, MLMC_DK_ERR_INVALID, "coupling must be 0 (NN) or 1 (Fourier)");
+    const int ratio = fourier ? 3 : 2;   // h_{l-1} = ratio h_l, tau_{l-1} = ratio^2 tau_l (Eq. cfl_preserved)
+    if (cfg->L_max < 0 || cfg->L_max >= MLMC_DK_MAX_LEVELS)
+        return fail(nullptr, MLMC_DK_ERR_INVALID, "L_max out of range");
+    if (!fourier && (!is_pow2(cfg->n0) || cfg->n0 < 4 || ((long long)cfg->n0 << cfg->L_max) > 1024))
         return fail(nullptr, MLMC_DK_ERR_INVALID, "n0 must be a power of two >= 4 with n0 2^L_max <= 1024");
+    if (fourier) {
+        long long nl = cfg->n0;
+        for (int l = 1; l <= cfg->L_max; ++l) nl *= 3;
+        if (cfg->n0 != 6 || nl > 54)
+            return fail(nullptr, MLMC_DK_ERR_UNSUPPORTED, "Fourier coupling: levels 6^2, 18^2, 54^2 (n0 = 6, L_max <= 2)");
+        if (cfg->theta_b0 != 0.0 || cfg->theta_kernel || cfg->stream_from_n != 0)
+            return fail(nullptr, MLMC_DK_ERR_UNSUPPORTED, "Fourier coupling: explicit scheme, no streamed levels");
+    }
     if (!(cfg->length > 0) || !(cfg->T > 0) || !(cfg->N >= 0))
         return fail(nullptr, MLMC_DK_ERR_INVALID, "length, T must be > 0 and N >= 0");
     if (cfg->n_obs < 1 || cfg->n_obs > MLMC_DK_MAX_OBS || !cfg->rho0 || !cfg->phi)
@@ -499,7 +546,11 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
             }
         }
     }
-    if (M0 * (1LL << (2 * cfg->L_max)) > (1LL << 30)) return fail(nullptr, MLMC_DK_ERR_INVALID, "too many time steps");
+    {
+        long long Mmax = M0;
+        for (int l = 1; l <= cfg->L_max; ++l) Mmax *= ratio * ratio;
+        if (Mmax > (1LL << 30)) return fail(nullptr, MLMC_DK_ERR_INVALID, "too many time steps");
+    }
 
     int ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
@@ -519,6 +570,7 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
     c->L_start = std::min(cfg->L_start > 0 ? cfg->L_start : 2, cfg->L_max);
     c->b0 = b0;
     c->theta = theta ? 1 : 0;
+    c->coupling = fourier ? 1 : 0;
     c->targs = targs;
     c->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
     c->lv.resize(cfg->L_max + 1);
@@ -528,10 +580,10 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
     size_t partials_need = 0;
     for (int l = 0; l <= cfg->L_max; ++l) {
         LevelTab& t = c->lv[l];
-        t.n = cfg->n0 << l;
-        t.h = h0 / (double)(1 << l);
-        t.tau = tau0 / std::pow(4.0, l);
-        t.M = (int)(M0 << (2 * l));
+        t.n = cfg->n0 * (int)std::lround(std::pow((double)ratio, l));
+        t.h = h0 / std::pow((double)ratio, l);
+        t.tau = tau0 / std::pow((double)(ratio * ratio), l);
+        t.M = (int)(M0 * std::llround(std::pow((double)(ratio * ratio), l)));
         const size_t cells = (size_t)t.n * t.n;
         const double* rho0 = cfg->rho0[l];
         if (!rho0) { mlmc_dk_free(c); return fail(nullptr, MLMC_DK_ERR_INVALID, "null rho0 level array"); }
@@ -570,7 +622,7 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
             mass += q0[i];
         }
         t.mass0 = mass;
-        mean_field(t.n, t.h, t.tau, t.M, rho0, rbar.data(), b0);
+        mean_field_any(t.n, t.h, t.tau, t.M, rho0, rbar.data(), b0);
         for (size_t i = 0; i < cells; ++i) qb[i] = (int32_t)std::llrint(std::ldexp(rbar[i], S));
         // The quantised initial state q0 2^-S differs from rho0 by e0 (at most half
         // a quantum per cell); the scheme is linear apart from sqrt([rho]^+), so e0
@@ -578,7 +630,7 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
         // removed from the observables with the mean-field offset below.
         std::vector<double> e0(cells), e0T(cells);
         for (size_t i = 0; i < cells; ++i) e0[i] = std::ldexp((double)q0[i], -S) - rho0[i];
-        mean_field(t.n, t.h, t.tau, t.M, e0.data(), e0T.data(), b0);
+        mean_field_any(t.n, t.h, t.tau, t.M, e0.data(), e0T.data(), b0);
         std::vector<float> phif(cells * c->n_obs);
         for (int k = 0; k < c->n_obs; ++k) {
             const double* ph = cfg->phi[(size_t)l * c->n_obs + k];
@@ -632,6 +684,44 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
                 return cuda_fail(nullptr, e, "FP64 test functions");
             }
             c->h2d_bytes += (int64_t)(sizeof(double) * ph64.size());
+        }
+        if (fourier) {
+            // one kernel shape per grid size: the Fourier-coupled kernel, and the
+            // restriction of this level's normals to the coarse grid
+            if (l > 0) {
+                const int n = t.n, nc = t.n / 3, K = nc / 2;
+                std::vector<float> P1((size_t)nc * n);
+                for (int y = 0; y < nc; ++y)
+                    for (int x = 0; x < n; ++x) {
+                        double v = 0.0;
+                        for (int xi = -K; xi <= K; ++xi) {
+                            const double w = (xi == K || xi == -K) ? M_SQRT1_2 : 1.0;
+                            v += w * std::cos(2.0 * M_PI * xi * ((double)y / nc - (double)x / n));
+                        }
+                        P1[(size_t)y * n + x] = (float)(v / std::sqrt((double)n * nc));
+                    }
+                if ((e = cudaMalloc(&t.d_P1, sizeof(float) * P1.size())) != cudaSuccess ||
+                    (e = cudaMemcpy(t.d_P1, P1.data(), sizeof(float) * P1.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
+                    mlmc_dk_free(c);
+                    return cuda_fail(nullptr, e, "Fourier restriction");
+                }
+                c->h2d_bytes += (int64_t)(sizeof(float) * P1.size());
+            }
+            for (int mode = 0; mode < 2; ++mode) {
+                if (mode == 1 && l == 0) continue;
+                dk::VariantInfo vi{};
+                if ((e = dk::fourier_variant_info(t.n, mode == 1, c->stride, &vi)) != cudaSuccess) {
+                    mlmc_dk_free(c);
+                    return cuda_fail(nullptr, e, "Fourier kernel setup");
+                }
+                if (!vi.supported) {
+                    mlmc_dk_free(c);
+                    return fail(nullptr, MLMC_DK_ERR_UNSUPPORTED, "no Fourier-coupled kernel for this grid");
+                }
+                t.vis[mode].push_back(vi);
+                partials_need = std::max(partials_need, (size_t)vi.max_ctas * vi.slots_per_cta * c->stride);
+            }
+            continue;
         }
         if (theta) {
             // one kernel shape per grid size: the theta-scheme kernel
@@ -802,6 +892,7 @@ int mlmc_dk_level_info(const mlmc_dk_ctx* ctx, int32_t level, mlmc_dk_level_desc
     out->theta = ctx->theta;
     out->theta_b0 = ctx->b0;
     out->cheb_steps = ctx->theta ? ctx->targs.K : 0;
+    out->coupling = ctx->coupling;
     return MLMC_DK_OK;
 }
 
@@ -1158,8 +1249,15 @@ int mlmc_dk_tune(mlmc_dk_ctx* ctx, int32_t repeats, double* seconds) {
     return MLMC_DK_OK;
 }
 
-int mlmc_dk_plan(int32_t L, const int64_t* n, const double* s1, const double* s2, const double* cost, double eps,
-                 int64_t* target, int32_t* converged) {
+}  // extern "C"
+
+namespace {
+// Eq. (opt_M_ell) and Eq. (convergence_criterion) with the levels' mesh ratio
+// r (the printed criterion has r = 2, the NN coupling's; the Fourier
+// coupling's levels refine by r = 3): stop if
+// max_t r^(-t alpha) |E_{L-t}| / (r^alpha - 1) < eps / sqrt 2.
+int plan_ratio(int32_t L, const int64_t* n, const double* s1, const double* s2, const double* cost, double eps,
+               int64_t* target, int32_t* converged, double ratio) {
     if (L < 0 || L >= MLMC_DK_MAX_LEVELS || !n || !s1 || !s2 || !cost || !target || !converged || !(eps > 0))
         return fail(nullptr, MLMC_DK_ERR_INVALID, "plan: bad arguments");
     double V[MLMC_DK_MAX_LEVELS], E[MLMC_DK_MAX_LEVELS];
@@ -1179,9 +1277,17 @@ int mlmc_dk_plan(int32_t L, const int64_t* n, const double* s1, const double* s2
     // Eq. (convergence_criterion), alpha = 2, P_{-1} = 0
     const double alpha = 2.0;
     double worst = 0;
-    for (int t = 0; t <= 2 && L - t >= 0; ++t) worst = std::max(worst, std::pow(2.0, -t * alpha) * std::fabs(E[L - t]));
-    *converged = worst / (std::pow(2.0, alpha) - 1.0) < eps / std::sqrt(2.0) ? 1 : 0;
+    for (int t = 0; t <= 2 && L - t >= 0; ++t) worst = std::max(worst, std::pow(ratio, -t * alpha) * std::fabs(E[L - t]));
+    *converged = worst / (std::pow(ratio, alpha) - 1.0) < eps / std::sqrt(2.0) ? 1 : 0;
     return MLMC_DK_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int mlmc_dk_plan(int32_t L, const int64_t* n, const double* s1, const double* s2, const double* cost, double eps,
+                 int64_t* target, int32_t* converged) {
+    return plan_ratio(L, n, s1, s2, cost, eps, target, converged, 2.0);
 }
 
 }  // extern "C"
@@ -1274,7 +1380,7 @@ int mlmc_dk_estimate(mlmc_dk_ctx* ctx, double eps, int32_t relative, uint64_t se
         }
         int64_t tgt[MLMC_DK_MAX_LEVELS];
         int32_t conv = 0;
-        int rc = mlmc_dk_plan(L, n, s1, s2, cost.data(), eps_abs, tgt, &conv);
+        int rc = plan_ratio(L, n, s1, s2, cost.data(), eps_abs, tgt, &conv, ctx->coupling == 1 ? 3.0 : 2.0);
         if (rc != MLMC_DK_OK) return fail(ctx, rc, g_init_error);
         bool more = false;
         for (int l = 0; l <= L; ++l) {

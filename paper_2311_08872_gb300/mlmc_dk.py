@@ -45,6 +45,7 @@ class Config(ctypes.Structure):
         ("stream_from_n", ctypes.c_int32),
         ("theta_b0", ctypes.c_double),
         ("theta_kernel", ctypes.c_int32),
+        ("coupling", ctypes.c_int32),
     ]
 
 
@@ -60,6 +61,7 @@ class LevelDesc(ctypes.Structure):
         ("streamed", ctypes.c_int32), ("in_flight", ctypes.c_int32), ("tile_rows", ctypes.c_int32),
         ("split_capable", ctypes.c_int32), ("split_fraction", ctypes.c_double), ("batch_streamed", ctypes.c_int64),
         ("theta", ctypes.c_int32), ("theta_b0", ctypes.c_double), ("cheb_steps", ctypes.c_int32),
+        ("coupling", ctypes.c_int32),
     ]
 
 
@@ -196,7 +198,7 @@ class Context:
     def __init__(self, length: float, n0: int, L_max: int, T: float, mu: float, N: float,
                  rho0: List[np.ndarray], phi: List[List[np.ndarray]], products: bool = False,
                  M0: int = 0, pilot: int = 0, L_start: int = 0, stream: Optional[int] = None,
-                 stream_from_n: int = 0, theta_b0: float = 0.0, theta_kernel: bool = False):
+                 stream_from_n: int = 0, theta_b0: float = 0.0, theta_kernel: bool = False, coupling: int = 0):
         self._ctx = None
         self._rho0 = [_f64(r).reshape(-1) for r in rho0]
         self.n_obs = len(phi[0])
@@ -205,7 +207,7 @@ class Context:
         phi_ptrs = (_dp * len(self._phi))(*[p.ctypes.data_as(_dp) for p in self._phi])
         self.cfg = Config(length, n0, L_max, T, mu, M0, N, rho_ptrs, self.n_obs, phi_ptrs,
                           int(products), pilot, L_start, stream, stream_from_n, float(theta_b0),
-                          int(theta_kernel))
+                          int(theta_kernel), int(coupling))
         h = ctypes.c_void_p()
         _check(lib().mlmc_dk_init(ctypes.byref(self.cfg), ctypes.byref(h)))
         self._ctx = h
@@ -215,6 +217,7 @@ class Context:
     @classmethod
     def from_workload(cls, wl, **kw) -> "Context":
         kw.setdefault("theta_b0", getattr(wl, "b0", 0.0))
+        kw.setdefault("coupling", getattr(wl, "coupling", 0))
         return cls(wl.length, wl.n0, wl.L_max, wl.T, wl.mu, wl.N, wl.rho0_all(), wl.phi_all(),
                    products=wl.products, M0=wl.M0, **kw)
 

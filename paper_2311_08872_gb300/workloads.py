@@ -31,6 +31,8 @@ Workloads:
                         limit), levels 16^2..64^2, T=0.02, N=1e5.
   * ``implicit16_64``-- implicit Euler weights b0 = 1, b1 = 0 at tau/h^2 = 2,
                         same grids.
+  * ``fourier6_54``  -- Fourier coupling (Section 3.1), levels 6^2, 18^2, 54^2
+                        (h ratio 3, tau ratio 9), T=0.02, N=1e5.
 """
 from __future__ import annotations
 
@@ -154,10 +156,15 @@ class Workload:
     alloc_scale: int = 1            # the eps-optimal allocation is about alloc * alloc_scale
     offset: float = 0.0             # grid points at (i + offset) h: 0 right-most, 1/2 symmetric coupling
     b0: float = 0.0                 # implicit weight of the time step (b1 = 1 - b0); 0 explicit Euler--Maruyama
+    coupling: int = 0               # 0 Right-Most NN (h ratio 2), 1 Fourier (h ratio 3)
     note: str = ""
 
+    @property
+    def ratio(self) -> int:
+        return 3 if self.coupling == 1 else 2
+
     def n(self, level: int) -> int:
-        return self.n0 << level
+        return self.n0 * self.ratio ** level
 
     def rho0(self, level: int) -> np.ndarray:
         n = self.n(level)
@@ -214,6 +221,9 @@ WORKLOADS: Dict[str, Workload] = {
     "implicit16_64": Workload("implicit16_64", 1.0, 16, 2, 0.02, 2.0, 1e5, "sinsin", [COS1],
                               seed=8, eps_rel=1e-2, b0=1.0,
                               note="implicit Euler weights at tau/h^2 = 2, levels 16^2..64^2"),
+    "fourier6_54": Workload("fourier6_54", 1.0, 6, 2, 0.02, 0.1, 1e5, "sinsin", [COS1],
+                            seed=9, eps_rel=1e-2, coupling=1,
+                            note="Fourier coupling, levels 6^2, 18^2, 54^2"),
 }
 
 

@@ -1,0 +1,109 @@
+"""GPU parity of the Fourier-coupled kernel (Section 3.1: h ratio 3, tau
+ratio 9, the coarse noise carrying every resolved Fourier mode of the fine
+noise) against the FP64 oracle, through the C-ABI; and the coupling's
+properties on the GPU: the coarse member's law equals a stand-alone coarse
+path's (Remark distribution_W_ell), Var[P_l - P_{l-1}] falls faster than the
+NN coupling's rate (Proposition PropBoundVarLevels: beta = 4 against 2), and
+Algorithm 1 runs on the ratio-3 hierarchy.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2311_08872_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def dk():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2311_08872_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2311_08872_gb300 import mlmc_dk
+    return mlmc_dk
+
+
+def _gpu(ctx, dk, level, tag, first, count, seed):
+    import torch
+    sums = torch.zeros(dk.sums_len(ctx.n_quant), dtype=torch.float64, device="cuda")
+    samp = torch.zeros(max(count, 1), dk.sample_stride(ctx.n_obs), dtype=torch.float64, device="cuda")
+    ctx.run_level_dev(level, tag, first, count, seed, sums.data_ptr(), samp.data_ptr(),
+                      torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    return sums.cpu().numpy(), samp.cpu().numpy()[:count]
+
+
+def _levels(wl):
+    return oracle.level_table(wl.length, wl.n0, wl.L_max, wl.T, wl.mu, wl.M0, ratio=3)
+
+
+def _ybar(wl, levels, l):
+    lv = levels[l]
+    return np.array([oracle.inner_h(oracle.mean_field(lv.n, lv.h, lv.tau, lv.M, wl.rho0(l)), p, lv.h)
+                     for p in wl.phi(l)])
+
+
+@pytest.mark.parametrize("level,tag,count", [(0, 0, 32), (1, 0, 24), (2, 0, 8), (2, 1, 6)])
+def test_fourier_kernel_matches_oracle(dk, level, tag, count):
+    wl = W.get("fourier6_54")
+    seed, first = 41 + level, 3
+    levels = _levels(wl)
+    with dk.Context.from_workload(wl) as ctx:
+        info = ctx.level_info(level)
+        assert info.coupling == 1 and info.n == levels[level].n and info.M == levels[level].M
+        sums, samp = _gpu(ctx, dk, level, tag, first, count, seed)
+    coupled = tag == 0 and level > 0
+    ol = oracle.level_inputs(wl.length, levels, wl.N, wl.rho0_all(), wl.phi_all(), level, coupled, coupling=1)
+    r = oracle.run_samples(ol, seed, range(first, first + count), coupled, stream=tag)
+    ybf = _ybar(wl, levels, level)
+    np.testing.assert_allclose(np.array(info.ybar_f[:1]), ybf, rtol=1e-9, atol=1e-12)
+    worst = 0.0
+    pairs = [(samp[:, 0] + ybf[0], r["Y_f"][:, 0], ybf[0])]
+    if coupled:
+        ybc = _ybar(wl, levels, level - 1)
+        np.testing.assert_allclose(np.array(info.ybar_c[:1]), ybc, rtol=1e-9, atol=1e-12)
+        pairs.append((samp[:, 1] + ybc[0], r["Y_c"][:, 0], ybc[0]))
+    for y, yo, yb in pairs:
+        scale = np.sqrt(np.mean((yo - yb) ** 2))
+        w = float(np.max(np.abs(y - yo) / (TOL * np.maximum(np.abs(yo), scale))))
+        assert w <= 1.0, f"level {level} tag {tag}: worst error / bound = {w:.3g}"
+        worst = max(worst, w)
+    assert int(sums[0]) == count and sums[1] == 0.0
+    print(f"fourier6_54 level {level} tag {tag}: worst/bound {worst:.3g}")
+
+
+def test_coarse_member_law_and_variance_decay(dk):
+    """E[P_c] of level-l pairs equals E[P_f] of stand-alone level-(l-1) paths,
+    and V_l decays like h^beta with beta well above the NN coupling's 2 at
+    high density (the paper predicts 4 for the Fourier coupling)."""
+    wl = W.get("fourier6_54").with_(N=1e9)
+    with dk.Context.from_workload(wl) as ctx:
+        s1 = ctx.run_level(1, 200000, 7)[0]
+        s2 = ctx.run_level(2, 20000, 8)[0]
+        a0 = ctx.run_level(0, 200000, 9, mc=True)[0]
+        a1 = ctx.run_level(1, 20000, 10, mc=True)[0]
+    var = lambda s: (s.dp2 - s.dp1 ** 2 / s.n) / (s.n - 1)
+    for pair, alone in ((s1, a0), (s2, a1)):
+        mc, ma = pair.pc1 / pair.n, alone.pf1 / alone.n
+        vc = (pair.pc2 - pair.pc1 ** 2 / pair.n) / (pair.n - 1)
+        va = (alone.pf2 - alone.pf1 ** 2 / alone.n) / (alone.n - 1)
+        assert abs(mc - ma) < 4.0 * math.sqrt(vc / pair.n + va / alone.n), (mc, ma)
+    v1, v2 = var(s1), var(s2)
+    beta = math.log(v1 / v2) / math.log(3.0)
+    print(f"Fourier coupling at N = 1e9: V_1 = {v1:.3e}, V_2 = {v2:.3e}, beta = {beta:.2f}")
+    assert beta > 2.5
+
+
+def test_algorithm1_on_fourier_levels(dk):
+    wl = W.get("fourier6_54")
+    with dk.Context.from_workload(wl) as ctx:
+        r = ctx.estimate(2e-2, True, 5)
+        assert r.L >= 1 and all(r.M[l] > 0 for l in range(r.L + 1))
+        assert math.isfinite(r.estimate) and r.estimate > 0
