@@ -45,6 +45,8 @@ def main() -> None:
     ap.add_argument("--max-pilot", type=int, default=100000)
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--surrogate", action="store_true", help="also the cost with the learned level below 0")
+    ap.add_argument("--L-max", type=int, default=None, help="finest level (default: the workload's)")
+    ap.add_argument("--N", type=float, default=None, help="particle number (default: the workload's)")
     args = ap.parse_args()
 
     import torch
@@ -53,6 +55,10 @@ def main() -> None:
 
     build.build()
     wl = workloads.get(args.workload)
+    if args.L_max is not None:
+        wl = wl.with_(L_max=args.L_max)
+    if args.N is not None:
+        wl = wl.with_(N=args.N)
     eps_rel = args.eps_rel if args.eps_rel is not None else (wl.eps_rel or 1e-2)
     st = torch.cuda.current_stream()
     rows = []
@@ -113,7 +119,7 @@ def main() -> None:
         sur["M_opt"] = Ms
         sur["mlmc_s"] = sum(m * r["s_per_sample"] for m, r in zip(Ms, vl))
         sur["mlmc_s_incl_training"] = sur["mlmc_s"] + sur["train_s"]
-    print(json.dumps({"workload": wl.name, "eps_rel": eps_rel, "eps_abs": eps, "estimate": est, "levels": rows,
+    print(json.dumps({"workload": wl.name, "L_max": wl.L_max, "N": wl.N, "eps_rel": eps_rel, "eps_abs": eps, "estimate": est, "levels": rows,
                       "M_opt": M, "mlmc_s": t_mlmc, "mc_samples": m_mc, "mc_s_per_sample": t_mc,
                       "mc_s": m_mc * t_mc, "mlmc_speedup_vs_mc": m_mc * t_mc / t_mlmc if t_mlmc > 0 else None,
                       "surrogate": sur, "extrapolated": True}))
