@@ -172,6 +172,30 @@ def theta_scheme(stream):
     return out
 
 
+def fourier_coupling(stream):
+    """The Fourier-coupled kernel on the finest level of fourier6_54 (54^2
+    coupled with 18^2, ratio 3): 32 waves of one sample per SM, CUDA events."""
+    import torch
+    from paper_2311_08872_gb300 import mlmc_dk, workloads
+    wl = workloads.get("fourier6_54")
+    level = wl.L_max
+    count = 32 * SMS
+    with mlmc_dk.Context.from_workload(wl, stream=stream.cuda_stream) as c:
+        info = c.level_info(level)
+        sums = torch.zeros(mlmc_dk.sums_len(c.n_quant), dtype=torch.float64, device="cuda")
+        c.run_level_dev(level, 0, 0, count, 13, sums.data_ptr(), 0, stream.cuda_stream)      # warm-up
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        c.run_level_dev(level, 0, count, count, 13, sums.data_ptr(), 0, stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) * 1e-3
+    return {"workload": wl.name, "level": level, "n": info.n, "coarse_n": info.n // 3, "fine_steps": info.M,
+            "samples": count, "s": sec, "cell_steps_per_s": count * info.cost / sec,
+            "coupled_sample_steps_per_s": count * info.M / sec}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -183,6 +207,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-streamed", action="store_true", help="skip the streamed-state stencil timing")
     ap.add_argument("--no-theta", action="store_true", help="skip the theta-scheme kernel timing")
+    ap.add_argument("--no-fourier", action="store_true", help="skip the Fourier-coupled kernel timing")
     ap.add_argument("--split-fraction", type=float, default=None,
                     help="fixed batch split of the finest cluster level (default: autotuned)")
     ap.add_argument("--no-adaptive", action="store_true", help="skip the Algorithm 1 / plain MC timing")
@@ -516,6 +541,9 @@ def run_ours(args, wl, rank, world, local_rank):
     theta = None
     if not args.no_theta:
         theta = theta_scheme(stream)
+    fourier = None
+    if not args.no_fourier:
+        fourier = fourier_coupling(stream)
 
     e2e = None
     if not args.no_e2e:
@@ -591,6 +619,7 @@ def run_ours(args, wl, rank, world, local_rank):
                                              "the gap is the positive-part effect" % (wl.N * (wl.length / fin.n) ** 2)}
     line["streamed_stencil"] = streamed
     line["theta_scheme"] = theta
+    line["fourier_coupling"] = fourier
     if surrogate:
         line["surrogate"] = surrogate
         line["mlmc_surrogate_s_to_eps"] = surrogate["mlmc_s_to_eps_incl_training"]
