@@ -34,22 +34,6 @@ __device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
     return c;
 }
 
-// The same ten rounds with the round keys precomputed: rk[2r], rk[2r+1] are
-// the two key words after r Weyl increments, read from the kernel's parameter
-// space (a __grid_constant__ argument), so no round spends instructions or
-// registers on the key schedule.
-__device__ __forceinline__ uint4 philox10_rk(uint4 c, const uint32_t* __restrict__ rk) {
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const unsigned long long p0 = static_cast<unsigned long long>(c.x) * kPhiloxM0;
-        const unsigned long long p1 = static_cast<unsigned long long>(c.z) * kPhiloxM1;
-        const uint32_t hi0 = static_cast<uint32_t>(p0 >> 32), lo0 = static_cast<uint32_t>(p0);
-        const uint32_t hi1 = static_cast<uint32_t>(p1 >> 32), lo1 = static_cast<uint32_t>(p1);
-        c = make_uint4(hi1 ^ c.y ^ rk[2 * r], lo1, hi0 ^ c.w ^ rk[2 * r + 1], lo0);
-    }
-    return c;
-}
-
 __device__ __forceinline__ float sqrt_approx(float x) {
     float y;
     asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));

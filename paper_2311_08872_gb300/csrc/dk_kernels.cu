@@ -230,7 +230,7 @@ __device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster
 __device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory"); }
 
 template <class S>
-__global__ void __launch_bounds__(S::THREADS) level_kernel(const __grid_constant__ KArgs a) {
+__global__ void __launch_bounds__(S::THREADS) level_kernel(const KArgs a) {
     constexpr int NF = S::NF, NC = S::NC, FR = S::FR, FC = S::FC, R = S::R, C = S::C;
     constexpr int LPB = S::LPB, LPS = S::LPS, CL = S::CL, BPC = S::BPC;
     constexpr bool CPL = S::COUPLED;
@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(S::THREADS) level_kernel(const __grid_constant
 #pragma unroll
                 for (int pc = 0; pc < C; ++pc) {
                     const uint32_t p = static_cast<uint32_t>(((row0 + r) * NF + col0 + 2 * pc) >> 1);
-                    const uint4 x = philox10_rk(make_uint4(p, static_cast<uint32_t>(m), c2, c3), a.rk);
+                    const uint4 x = philox10(make_uint4(p, static_cast<uint32_t>(m), c2, c3), a.key0, a.key1);
                     // normals (ra ca, ra sa) and (rb cb, rb sb); the amplitude scales the radius
                     float ra, ca, sa, rb, cb, sb;
                     box_muller_polar(x.x, x.y, ra, ca, sa);

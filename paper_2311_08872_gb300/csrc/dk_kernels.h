@@ -32,7 +32,6 @@ struct KArgs {
     int32_t Af, Ac;         // diffusion multipliers round(tau/(2h^2) 2^32)
     float gf, gc;           // noise multipliers (gc includes the 1/4 of the coupled sum)
     uint32_t key0, key1;    // seed words
-    uint32_t rk[20];        // Philox round keys: rk[2r] = key0 + r W0, rk[2r+1] = key1 + r W1 (mod 2^32)
     uint32_t tag;           // (level + 1) | stream << 8
     int32_t slot_stride;    // 2 + kNSum * n_quant doubles
     double N;
@@ -92,7 +91,6 @@ struct SArgs {
     int32_t Af, Ac;
     float gf, gc;
     uint32_t key0, key1, tag;
-    uint32_t rk[20];             // Philox round keys (as in KArgs)
     unsigned int* err;
 };
 

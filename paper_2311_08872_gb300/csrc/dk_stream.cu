@@ -57,7 +57,7 @@ struct PairNoise {
 
 __device__ __forceinline__ PairNoise pair_noise(const SArgs& a, uint32_t p, int m, uint32_t c2, uint32_t c3,
                                                 int32_t qa, int32_t qb, float& z1, float& z2) {
-    const uint4 x = philox10_rk(make_uint4(p, static_cast<uint32_t>(m), c2, c3), a.rk);
+    const uint4 x = philox10(make_uint4(p, static_cast<uint32_t>(m), c2, c3), a.key0, a.key1);
     float ra, ca, sa, rb, cb, sb;
     box_muller_polar(x.x, x.y, ra, ca, sa);
     box_muller_polar(x.z, x.w, rb, cb, sb);
@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(kThreads) stream_init_kernel(const SArgs a) {
 // CTA: 16 x FR/2 threads on an FR x 64 tile; thread (tx, ty) owns the 2 x 4
 // fine block at (R0 + 2 ty, C0 + 4 tx) = 2 coarse cells.
 template <int FR, int MINB>
-__global__ void __launch_bounds__(fine_threads(FR), MINB) stream_fine_kernel(const __grid_constant__ SArgs a, int m) {
+__global__ void __launch_bounds__(fine_threads(FR), MINB) stream_fine_kernel(const SArgs a, int m) {
     constexpr int kHaloPairs = 64 + 2 * FR;   // 2 x 32 pairs in the halo rows, one per row in the halo columns
     const int s = blockIdx.z;
     if (s >= a.count) return;

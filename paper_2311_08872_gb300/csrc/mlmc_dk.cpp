@@ -243,10 +243,6 @@ dk::KArgs make_args(mlmc_dk_ctx* c, int level, int stream_tag, bool coupled, int
     a.gf = f.g;
     a.key0 = (uint32_t)(seed & 0xffffffffu);
     a.key1 = (uint32_t)(seed >> 32);
-    for (int r = 0; r < 10; ++r) {   // Philox4x32-10 key schedule (Weyl constants of Salmon et al.)
-        a.rk[2 * r] = a.key0 + (uint32_t)r * 0x9E3779B9u;
-        a.rk[2 * r + 1] = a.key1 + (uint32_t)r * 0xBB67AE85u;
-    }
     a.tag = ((uint32_t)(level + 1) & 0xffu) | (((uint32_t)stream_tag & 0xffu) << 8);
     a.slot_stride = c->stride;
     a.N = c->N;
@@ -310,7 +306,6 @@ int launch_streamed(mlmc_dk_ctx* c, int level, int stream_tag, int64_t first, in
     a.phic64 = coupled ? c->lv[level - 1].d_phi64 : nullptr;
     a.Af = k.Af; a.Ac = k.Ac; a.gf = k.gf; a.gc = k.gc;
     a.key0 = k.key0; a.key1 = k.key1; a.tag = k.tag;
-    for (int r = 0; r < 20; ++r) a.rk[r] = k.rk[r];
     a.err = c->d_err;
     const int S = t.inflight_v[variant];
     if ((e = dk::stream_run(k, a, S, variant, st)) != cudaSuccess) return cuda_fail(c, e, "streamed level");
