@@ -22,9 +22,13 @@
 // noise transfers G = rint(c 2^S sqrt(rho^+) Z) and diffusion fluxes, every
 // edge flux computed identically by both of its cells, so the mass is exact.
 //
-// Work decomposition.  One CTA per sample, state and operands in shared
-// memory, loops over cells / cell pairs with the CTA's stride (the grid sizes
-// 6, 18, 54 are not powers of two), three barriers per fine step.
+// Work decomposition.  One CTA per sample.  A thread holds a segment of 6
+// consecutive fine cells of one row (3 Philox cell pairs) in registers, with
+// its row's periodic neighbours fixed once, so a fine step needs no index
+// arithmetic; the state and transfers are published in shared memory for the
+// rows above and below and the segment ends.  The coarse grid and the
+// restriction loop over cells with the CTA's stride.  Two barriers per fine
+// step (three at a coarse step).
 #include "dk_device.cuh"
 #include "dk_kernels.h"
 
@@ -37,7 +41,12 @@ constexpr int kRedF = 2 * kMaxObs + 2;
 template <int N_>
 struct FShape {
     static constexpr int N = N_, NC = N / 3;
-    static constexpr int THREADS = N >= 54 ? 512 : (N >= 18 ? 128 : 32);
+    static constexpr int SEG = 6;                       // fine cells per thread: one row segment (3 Philox pairs)
+    static constexpr int SEGS = N / SEG;                // segments per row
+    static constexpr int FT = N * SEGS;                 // threads that hold fine cells
+    static constexpr int THREADS = FT > 256 ? 512 : (FT > 32 ? 64 : 32);
+    static_assert(N % SEG == 0 && FT <= THREADS, "fine row segments must cover the grid");
+    static constexpr int MINB = THREADS >= 512 ? 2 : 1;   // two samples per SM at 54^2 (64 registers)
     static constexpr int WARPS = THREADS / 32;
     // words: q (2 buffers), G1, G2, summed normals (2), coarse q (2 buffers),
     // coarse G1, G2, the row-restricted sums T (N x NC x 2), P1 (NC x N)
@@ -68,7 +77,7 @@ __device__ __forceinline__ void explicit_update(const int32_t* q, const int32_t*
 }
 
 template <int N, bool CPL>
-__global__ void __launch_bounds__(FShape<N>::THREADS) fourier_kernel(const KArgs a, const FArgs f) {
+__global__ void __launch_bounds__(FShape<N>::THREADS, FShape<N>::MINB) fourier_kernel(const KArgs a, const FArgs f) {
     using S = FShape<N>;
     constexpr int NC = S::NC, THREADS = S::THREADS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -90,6 +99,16 @@ __global__ void __launch_bounds__(FShape<N>::THREADS) fourier_kernel(const KArgs
     if constexpr (CPL)
         for (int i = tid; i < NC * N; i += THREADS) P1[i] = f.P1[i];
 
+    constexpr int SEG = S::SEG, SEGS = S::SEGS;
+    const bool fine_thread = tid < S::FT;
+    const int frow = fine_thread ? tid / SEGS : 0;
+    const int fc0 = fine_thread ? (tid % SEGS) * SEG : 0;
+    const int fx0 = frow * N + fc0;                                  // first cell of the segment
+    const int upo = frow == 0 ? N * (N - 1) : -N;                    // offsets to the rows above / below
+    const int dno = frow == N - 1 ? -N * (N - 1) : N;
+    const int lfx = fc0 == 0 ? fx0 + N - 1 : fx0 - 1;                // left of the first cell
+    const int rtx = fc0 + SEG == N ? fx0 + SEG - N : fx0 + SEG;      // right of the last cell
+
     unsigned bad = 0;
     const long long slot = blockIdx.x, n_slots = gridDim.x;
     const long long iters = a.count > slot ? (a.count - slot + n_slots - 1) / n_slots : 0;
@@ -101,7 +120,14 @@ __global__ void __launch_bounds__(FShape<N>::THREADS) fourier_kernel(const KArgs
         const uint32_t c2 = static_cast<uint32_t>(sid);
         const uint32_t c3 = a.tag | ((static_cast<uint32_t>(static_cast<unsigned long long>(sid) >> 32) & 0xffffu) << 16);
         int cur = 0, ccur = 0;
-        for (int x = tid; x < N * N; x += THREADS) qA[x] = a.q0f[x];
+        int32_t qr[SEG];
+        if (fine_thread) {
+#pragma unroll
+            for (int j = 0; j < SEG; ++j) {
+                qr[j] = a.q0f[fx0 + j];
+                qA[fx0 + j] = qr[j];
+            }
+        }
         if constexpr (CPL)
             for (int y = tid; y < NC * NC; y += THREADS) qcA[y] = a.q0c[y];
         __syncthreads();
@@ -109,31 +135,62 @@ __global__ void __launch_bounds__(FShape<N>::THREADS) fourier_kernel(const KArgs
         for (int m = 0; m < a.M; ++m) {
             const int32_t* q = cur ? qB : qA;
             const bool first_of_coarse = CPL && (m % 9) == 0;
-            // ---- noise: Philox4x32-10 per horizontal cell pair, Box--Muller, transfers
-            for (int p = tid; p < N * N / 2; p += THREADS) {
-                const uint4 x = philox10(make_uint4(static_cast<uint32_t>(p), static_cast<uint32_t>(m), c2, c3),
-                                         a.key0, a.key1);
-                float ra, ca, sa, rb, cb, sb;
-                box_muller_polar(x.x, x.y, ra, ca, sa);
-                box_muller_polar(x.z, x.w, rb, cb, sb);
-                const float ta = noise_amp(q[2 * p], a.gf) * ra;
-                const float tb = noise_amp(q[2 * p + 1], a.gf) * rb;
-                G1[2 * p] = __float2int_rn(ta * ca);
-                G2[2 * p] = __float2int_rn(ta * sa);
-                G1[2 * p + 1] = __float2int_rn(tb * cb);
-                G2[2 * p + 1] = __float2int_rn(tb * sb);
-                if constexpr (CPL) {
-                    float4 z = first_of_coarse ? make_float4(0.f, 0.f, 0.f, 0.f)
-                                               : reinterpret_cast<float4*>(Zs)[p];
-                    z.x += ra * ca;
-                    z.y += ra * sa;
-                    z.z += rb * cb;
-                    z.w += rb * sb;
-                    reinterpret_cast<float4*>(Zs)[p] = z;
+            // ---- noise of the segment: Philox4x32-10 per horizontal cell pair, Box--Muller, transfers
+            int32_t g1[SEG], g2[SEG];
+            if (fine_thread) {
+#pragma unroll
+                for (int j = 0; j < SEG / 2; ++j) {
+                    const int p = (fx0 >> 1) + j;
+                    const uint4 x = philox10(make_uint4(static_cast<uint32_t>(p), static_cast<uint32_t>(m), c2, c3),
+                                             a.key0, a.key1);
+                    float ra, ca, sa, rb, cb, sb;
+                    box_muller_polar(x.x, x.y, ra, ca, sa);
+                    box_muller_polar(x.z, x.w, rb, cb, sb);
+                    const float ta = noise_amp(qr[2 * j], a.gf) * ra;
+                    const float tb = noise_amp(qr[2 * j + 1], a.gf) * rb;
+                    g1[2 * j] = __float2int_rn(ta * ca);
+                    g2[2 * j] = __float2int_rn(ta * sa);
+                    g1[2 * j + 1] = __float2int_rn(tb * cb);
+                    g2[2 * j + 1] = __float2int_rn(tb * sb);
+                    reinterpret_cast<int2*>(G1)[p] = make_int2(g1[2 * j], g1[2 * j + 1]);
+                    reinterpret_cast<int2*>(G2)[p] = make_int2(g2[2 * j], g2[2 * j + 1]);
+                    if constexpr (CPL) {
+                        float4 z = first_of_coarse ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                                   : reinterpret_cast<float4*>(Zs)[p];
+                        z.x += ra * ca;
+                        z.y += ra * sa;
+                        z.z += rb * cb;
+                        z.w += rb * sb;
+                        reinterpret_cast<float4*>(Zs)[p] = z;
+                    }
                 }
             }
             __syncthreads();
-            explicit_update<N, THREADS>(q, G1, G2, cur ? qA : qB, a.Af, bad);
+            // ---- explicit step of the segment in flux form (every edge flux computed
+            // from the same two states by both of its cells)
+            if (fine_thread) {
+                int32_t* qn = cur ? qA : qB;
+                int32_t nq[SEG];
+#pragma unroll
+                for (int j = 0; j < SEG; ++j) {
+                    const int x = fx0 + j;
+                    const int32_t c = qr[j];
+                    const int32_t up = q[x + upo], dn = q[x + dno];
+                    const int32_t lf = j == 0 ? q[lfx] : qr[j - 1];
+                    const int32_t rt = j == SEG - 1 ? q[rtx] : qr[j + 1];
+                    const int32_t g2l = j == 0 ? G2[lfx] : g2[j - 1];
+                    const int32_t g2r = j == SEG - 1 ? G2[rtx] : g2[j + 1];
+                    nq[j] = c + (edge_flux(a.Af, dn - c) - edge_flux(a.Af, c - up)) +
+                            (edge_flux(a.Af, rt - c) - edge_flux(a.Af, c - lf)) + (G1[x + dno] - G1[x + upo]) +
+                            (g2r - g2l);
+                    bad |= (static_cast<uint32_t>(nq[j]) + 0x40000000u) >> 31;
+                }
+#pragma unroll
+                for (int j = 0; j < SEG; ++j) {
+                    qr[j] = nq[j];
+                    qn[fx0 + j] = nq[j];
+                }
+            }
             cur ^= 1;
             if constexpr (CPL) {
                 if ((m % 9) == 8) {
