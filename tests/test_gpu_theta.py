@@ -140,3 +140,20 @@ def test_algorithm1_runs_on_theta_levels(dk):
         info = ctx.level_info(2)
         cf = oracle.closed_form_EP_cos1(1.0, info.n, info.tau, info.M, b0=wl.b0)
         assert abs(r.estimate - cf) < 0.1 * cf
+
+
+@pytest.mark.parametrize("level,count", [(0, 37), (1, 29), (2, 13)])
+def test_small_grids_and_ragged_counts(dk, level, count):
+    """Grids 4^2, 8^2, 16^2 (several samples per CTA, sub-warp reductions) with
+    sample counts that leave the last CTA partly idle."""
+    wl = W.get("theta16_64").with_(name="theta4_16", n0=4, L_max=2)
+    seed, first = 61 + level, 2
+    with dk.Context.from_workload(wl) as ctx:
+        info = ctx.level_info(level)
+        assert info.theta == 1 and info.n == 4 << level
+        sums, samp = _gpu(ctx, dk, level, 0, first, count, seed)
+    r, ybf, ybc = _oracle(wl, level, 0, first, count, seed)
+    _parity(samp[:, :1] + ybf[None, :], r["Y_f"], ybf, f"theta 4..16 level {level} fine")
+    if ybc is not None:
+        _parity(samp[:, 1:2] + ybc[None, :], r["Y_c"], ybc, f"theta 4..16 level {level} coarse")
+    assert int(sums[0]) == count and sums[1] == 0.0
