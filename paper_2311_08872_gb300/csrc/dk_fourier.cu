@@ -170,25 +170,35 @@ __global__ void __launch_bounds__(FShape<N>::THREADS, FShape<N>::MINB) fourier_k
             // from the same two states by both of its cells)
             if (fine_thread) {
                 int32_t* qn = cur ? qA : qB;
+                // the rows above and below, 8-byte loads (segments start at even cells)
+                int32_t qu[SEG], qd[SEG], gu[SEG], gd[SEG];
+#pragma unroll
+                for (int j = 0; j < SEG; j += 2) {
+                    const int2 a0 = *reinterpret_cast<const int2*>(q + fx0 + upo + j);
+                    const int2 a1 = *reinterpret_cast<const int2*>(q + fx0 + dno + j);
+                    const int2 b0 = *reinterpret_cast<const int2*>(G1 + fx0 + upo + j);
+                    const int2 b1 = *reinterpret_cast<const int2*>(G1 + fx0 + dno + j);
+                    qu[j] = a0.x; qu[j + 1] = a0.y; qd[j] = a1.x; qd[j + 1] = a1.y;
+                    gu[j] = b0.x; gu[j + 1] = b0.y; gd[j] = b1.x; gd[j + 1] = b1.y;
+                }
+                const int32_t qlf = q[lfx], qrt = q[rtx], g2lf = G2[lfx], g2rt = G2[rtx];
                 int32_t nq[SEG];
 #pragma unroll
                 for (int j = 0; j < SEG; ++j) {
-                    const int x = fx0 + j;
                     const int32_t c = qr[j];
-                    const int32_t up = q[x + upo], dn = q[x + dno];
-                    const int32_t lf = j == 0 ? q[lfx] : qr[j - 1];
-                    const int32_t rt = j == SEG - 1 ? q[rtx] : qr[j + 1];
-                    const int32_t g2l = j == 0 ? G2[lfx] : g2[j - 1];
-                    const int32_t g2r = j == SEG - 1 ? G2[rtx] : g2[j + 1];
-                    nq[j] = c + (edge_flux(a.Af, dn - c) - edge_flux(a.Af, c - up)) +
-                            (edge_flux(a.Af, rt - c) - edge_flux(a.Af, c - lf)) + (G1[x + dno] - G1[x + upo]) +
-                            (g2r - g2l);
+                    const int32_t lf = j == 0 ? qlf : qr[j - 1];
+                    const int32_t rt = j == SEG - 1 ? qrt : qr[j + 1];
+                    const int32_t g2l = j == 0 ? g2lf : g2[j - 1];
+                    const int32_t g2r = j == SEG - 1 ? g2rt : g2[j + 1];
+                    nq[j] = c + (edge_flux(a.Af, qd[j] - c) - edge_flux(a.Af, c - qu[j])) +
+                            (edge_flux(a.Af, rt - c) - edge_flux(a.Af, c - lf)) + (gd[j] - gu[j]) + (g2r - g2l);
                     bad |= (static_cast<uint32_t>(nq[j]) + 0x40000000u) >> 31;
                 }
 #pragma unroll
-                for (int j = 0; j < SEG; ++j) {
+                for (int j = 0; j < SEG; j += 2) {
                     qr[j] = nq[j];
-                    qn[fx0 + j] = nq[j];
+                    qr[j + 1] = nq[j + 1];
+                    *reinterpret_cast<int2*>(qn + fx0 + j) = make_int2(nq[j], nq[j + 1]);
                 }
             }
             cur ^= 1;
