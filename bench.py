@@ -71,6 +71,12 @@ KERNEL_SOURCES = ("dk_kernels.cu", "dk_device.cuh")   # the level kernel and its
 THETA_KERNEL_INSTR = {"kernel": "theta_kernel n=64 coupled=True b0=0.5 chebyshev_steps=14",
                       "instructions_per_fine_cell_step": 580.6, "sources_sha256_16": "5f4fec27e80df0df"}
 THETA_SOURCES = ("dk_theta.cu", "dk_device.cuh")
+# Fourier-coupled kernel: thread instructions per cell-step (fine and coarse
+# cell-steps) of the 54^2 coupled launch, from its ncu --set full capture;
+# valid under the recorded hash of its sources.
+FOURIER_KERNEL_INSTR = {"kernel": "fourier_kernel n=54 coupled=True",
+                        "instructions_per_cell_step": 94.6, "sources_sha256_16": "3014eb041e0601d7"}
+FOURIER_SOURCES = ("dk_fourier.cu", "dk_device.cuh")
 
 
 def kernel_sources_hash(files=KERNEL_SOURCES) -> str:
@@ -191,9 +197,17 @@ def fourier_coupling(stream):
         e1.record(stream)
         torch.cuda.synchronize()
         sec = e0.elapsed_time(e1) * 1e-3
-    return {"workload": wl.name, "level": level, "n": info.n, "coarse_n": info.n // 3, "fine_steps": info.M,
-            "samples": count, "s": sec, "cell_steps_per_s": count * info.cost / sec,
-            "coupled_sample_steps_per_s": count * info.M / sec}
+    out = {"workload": wl.name, "level": level, "n": info.n, "coarse_n": info.n // 3, "fine_steps": info.M,
+           "samples": count, "s": sec, "cell_steps_per_s": count * info.cost / sec,
+           "coupled_sample_steps_per_s": count * info.M / sec,
+           "bound": "alu (instruction issue; shared-memory queue stalls lead)"}
+    if kernel_sources_hash(FOURIER_SOURCES) == FOURIER_KERNEL_INSTR["sources_sha256_16"]:
+        ipc = FOURIER_KERNEL_INSTR["instructions_per_cell_step"]
+        warp_inst = count * info.cost * ipc / 32.0 / sec
+        peak = 4.0 * SMS * SM_MAX_MHZ * 1e6
+        out["issue"] = {"instructions_per_cell_step": ipc, "achieved_warp_inst_per_s": warp_inst,
+                        "peak_warp_inst_per_s": peak, "frac": warp_inst / peak}
+    return out
 
 
 def parse():
