@@ -107,3 +107,10 @@ def test_algorithm1_on_fourier_levels(dk):
         r = ctx.estimate(2e-2, True, 5)
         assert r.L >= 1 and all(r.M[l] > 0 for l in range(r.L + 1))
         assert math.isfinite(r.estimate) and r.estimate > 0
+
+
+def test_empty_batch_gives_zero_sums(dk):
+    wl = W.get("fourier6_54")
+    with dk.Context.from_workload(wl) as ctx:
+        sums, _ = _gpu(ctx, dk, 2, 0, 0, 0, 1)
+    assert not sums.any()

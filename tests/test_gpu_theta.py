@@ -157,3 +157,10 @@ def test_small_grids_and_ragged_counts(dk, level, count):
     if ybc is not None:
         _parity(samp[:, 1:2] + ybc[None, :], r["Y_c"], ybc, f"theta 4..16 level {level} coarse")
     assert int(sums[0]) == count and sums[1] == 0.0
+
+
+def test_empty_batch_gives_zero_sums(dk):
+    wl = W.get("theta16_64")
+    with dk.Context.from_workload(wl) as ctx:
+        sums, _ = _gpu(ctx, dk, 2, 0, 0, 0, 1)
+    assert not sums.any()
