@@ -401,6 +401,20 @@ int mlmc_dk_plan(int32_t L, const int64_t* n, const double* s1, const double* s2
  * diagonalisation in FP64.  out may alias rho0. */
 int mlmc_dk_mean_field_host(int32_t n, double h, double tau, int64_t M, const double* rho0, double* out);
 
+/* Host-only Chebyshev schedule of the theta-scheme's implicit solve
+ * (I + alpha L) u = b, L = -h^2 Delta_h, alpha = b0 tau / (2 h^2): *K steps
+ * (the first with 1/T_K((1+4 alpha)/(4 alpha)) <= 2^-27; 0 for alpha = 0) and the
+ * direction recurrence d <- c1[k] d + c2[k] r (c1, c2: caller arrays of 64
+ * floats) of Chebyshev acceleration, started with u = 0, r = b,
+ * d = r / (1 + 4 alpha).  MLMC_DK_ERR_UNSUPPORTED if K would exceed 64. */
+int mlmc_dk_chebyshev_schedule_host(double alpha, int32_t* K, float* c1, float* c2);
+
+/* Host-only restriction matrix of the Fourier coupling (Section 3.1) along one
+ * axis: P1 [n/3][n] (caller array, row-major) with the coarse normal field of
+ * a coarse step P1 S P1^T / 3 for S the sum of its 9 fine normal fields; n a
+ * multiple of 6. */
+int mlmc_dk_fourier_restriction_host(int32_t n, float* P1);
+
 /* Checkpoint: the per-level next sample ids (coupled and MC).  With
  * buf == NULL, *len receives the size needed.  Results stay a pure function
  * of (seed, level, stream, sample id), so a restored context continues the

@@ -220,6 +220,47 @@ void mean_field_any(int n, double h, double tau, long long M, const double* rho0
     std::copy(a.begin(), a.end(), out);
 }
 
+// Chebyshev iteration on the spectrum [1, 1 + 8 alpha] of I + alpha L (the
+// theta-scheme's implicit operator): after K steps the error is at most
+// 1 / T_K(sigma) of the initial one, sigma = (1 + 4 alpha) / (4 alpha); K is the
+// first with that below 2^-27, and the direction recurrence d <- c1[k] d +
+// c2[k] r follows Chebyshev acceleration (Saad, Iterative Methods for Sparse
+// Linear Systems, Algorithm 12.1).  Returns false if K would exceed kMaxCheb.
+bool chebyshev_schedule(double alpha, int* K_out, float* c1, float* c2) {
+    *K_out = 0;
+    if (!(alpha > 0.0)) return true;
+    const double sigma = (1.0 + 4.0 * alpha) / (4.0 * alpha), delta = 4.0 * alpha;
+    int K = 1;
+    while (K <= dk::kMaxCheb && std::cosh(K * std::acosh(sigma)) < std::ldexp(1.0, 27)) ++K;
+    if (K > dk::kMaxCheb) return false;
+    double rho = 1.0 / sigma;
+    for (int k = 0; k < K; ++k) {
+        const double next = 1.0 / (2.0 * sigma - rho);
+        c1[k] = (float)(next * rho);
+        c2[k] = (float)(2.0 * next / delta);
+        rho = next;
+    }
+    *K_out = K;
+    return true;
+}
+
+// Restriction of the Fourier coupling (Section 3.1) along one axis, an
+// (n/3) x n matrix: P1[y][x] = (n nc)^-1/2 sum_{xi=-nc/2..nc/2} w(xi)
+// cos(2 pi xi (y/nc - x/n)), w = 2^-1/2 at xi = +-nc/2 (the two fine aliases of
+// the coarse Nyquist mode) and 1 otherwise; coarse point y is fine point 3y.
+void fourier_restriction(int n, float* P1) {
+    const int nc = n / 3, K = nc / 2;
+    for (int y = 0; y < nc; ++y)
+        for (int x = 0; x < n; ++x) {
+            double v = 0.0;
+            for (int xi = -K; xi <= K; ++xi) {
+                const double w = (xi == K || xi == -K) ? M_SQRT1_2 : 1.0;
+                v += w * std::cos(2.0 * M_PI * xi * ((double)y / nc - (double)x / n));
+            }
+            P1[(size_t)y * n + x] = (float)(v / std::sqrt((double)n * nc));
+        }
+}
+
 int quantities(int n_obs, int products) { return products ? n_obs * (n_obs + 1) / 2 : n_obs; }
 
 // Fill the kernel arguments of one batch.
@@ -470,6 +511,20 @@ const char* mlmc_dk_last_error(const mlmc_dk_ctx* ctx) {
 
 int32_t mlmc_dk_num_quantities(const mlmc_dk_ctx* ctx) { return ctx ? ctx->n_quant : 0; }
 
+int mlmc_dk_chebyshev_schedule_host(double alpha, int32_t* K, float* c1, float* c2) {
+    if (!K || !c1 || !c2 || !(alpha >= 0.0)) return fail(nullptr, MLMC_DK_ERR_INVALID, "chebyshev_schedule: bad arguments");
+    int k = 0;
+    if (!chebyshev_schedule(alpha, &k, c1, c2)) return fail(nullptr, MLMC_DK_ERR_UNSUPPORTED, "alpha too large");
+    *K = k;
+    return MLMC_DK_OK;
+}
+
+int mlmc_dk_fourier_restriction_host(int32_t n, float* P1) {
+    if (!P1 || n < 6 || n % 6 != 0) return fail(nullptr, MLMC_DK_ERR_INVALID, "fourier_restriction: n must be a multiple of 6");
+    fourier_restriction(n, P1);
+    return MLMC_DK_OK;
+}
+
 int mlmc_dk_mean_field_host(int32_t n, double h, double tau, int64_t M, const double* rho0, double* out) {
     if (!is_pow2(n) || n < 2 || h <= 0 || tau < 0 || M < 0 || !rho0 || !out)
         return fail(nullptr, MLMC_DK_ERR_INVALID, "mean_field_host: bad arguments");
@@ -523,28 +578,11 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
     if (theta) {
         if ((cfg->n0 << cfg->L_max) > 64 || cfg->stream_from_n != 0)
             return fail(nullptr, MLMC_DK_ERR_UNSUPPORTED, "theta-scheme kernel: grids up to 64^2, no streamed levels");
-        // Chebyshev iteration on the spectrum [1, 1 + 8 alpha] of I + alpha L: after K
-        // steps the error is at most 1 / T_K(sigma) of the initial one,
-        // sigma = (1 + 4 alpha) / (4 alpha); K is the first with that below 2^-27
         const double alpha = b0 * tau0 / (2.0 * h0 * h0);
         targs.alpha = (float)alpha;
         targs.inv_theta = (float)(1.0 / (1.0 + 4.0 * alpha));
-        targs.K = 0;
-        if (alpha > 0.0) {
-            const double sigma = (1.0 + 4.0 * alpha) / (4.0 * alpha), delta = 4.0 * alpha;
-            int K = 1;
-            while (K <= dk::kMaxCheb && std::cosh(K * std::acosh(sigma)) < std::ldexp(1.0, 27)) ++K;
-            if (K > dk::kMaxCheb)
-                return fail(nullptr, MLMC_DK_ERR_UNSUPPORTED, "b0 tau/h^2 too large for the solve's step budget");
-            targs.K = K;
-            double rho = 1.0 / sigma;
-            for (int k = 0; k < K; ++k) {
-                const double next = 1.0 / (2.0 * sigma - rho);
-                targs.c1[k] = (float)(next * rho);
-                targs.c2[k] = (float)(2.0 * next / delta);
-                rho = next;
-            }
-        }
+        if (!chebyshev_schedule(alpha, &targs.K, targs.c1, targs.c2))
+            return fail(nullptr, MLMC_DK_ERR_UNSUPPORTED, "b0 tau/h^2 too large for the solve's step budget");
     }
     {
         long long Mmax = M0;
@@ -689,17 +727,8 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
             // one kernel shape per grid size: the Fourier-coupled kernel, and the
             // restriction of this level's normals to the coarse grid
             if (l > 0) {
-                const int n = t.n, nc = t.n / 3, K = nc / 2;
-                std::vector<float> P1((size_t)nc * n);
-                for (int y = 0; y < nc; ++y)
-                    for (int x = 0; x < n; ++x) {
-                        double v = 0.0;
-                        for (int xi = -K; xi <= K; ++xi) {
-                            const double w = (xi == K || xi == -K) ? M_SQRT1_2 : 1.0;
-                            v += w * std::cos(2.0 * M_PI * xi * ((double)y / nc - (double)x / n));
-                        }
-                        P1[(size_t)y * n + x] = (float)(v / std::sqrt((double)n * nc));
-                    }
+                std::vector<float> P1((size_t)(t.n / 3) * t.n);
+                fourier_restriction(t.n, P1.data());
                 if ((e = cudaMalloc(&t.d_P1, sizeof(float) * P1.size())) != cudaSuccess ||
                     (e = cudaMemcpy(t.d_P1, P1.data(), sizeof(float) * P1.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
                     mlmc_dk_free(c);

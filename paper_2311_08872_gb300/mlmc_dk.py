@@ -114,6 +114,9 @@ def lib() -> ctypes.CDLL:
                                    ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]
         L.mlmc_dk_mean_field_host.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
                                               _dp, _dp]
+        _fp = ctypes.POINTER(ctypes.c_float)
+        L.mlmc_dk_chebyshev_schedule_host.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_int32), _fp, _fp]
+        L.mlmc_dk_fourier_restriction_host.argtypes = [ctypes.c_int32, _fp]
         L.mlmc_dk_save_state.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_size_t)]
         L.mlmc_dk_load_state.argtypes = [vp, vp, ctypes.c_size_t]
         L.mlmc_dk_num_quantities.argtypes = [vp]
@@ -169,6 +172,22 @@ def mean_field_host(n: int, h: float, tau: float, M: int, rho0: np.ndarray) -> n
     out = np.empty_like(r)
     _check(lib().mlmc_dk_mean_field_host(n, h, tau, M, r.ctypes.data_as(_dp), out.ctypes.data_as(_dp)))
     return out.reshape(n, n)
+
+
+def chebyshev_schedule(alpha: float):
+    """(K, c1[:K], c2[:K]) of the theta-scheme's implicit solve (host logic)."""
+    K = ctypes.c_int32(0)
+    c1 = (ctypes.c_float * 64)()
+    c2 = (ctypes.c_float * 64)()
+    _check(lib().mlmc_dk_chebyshev_schedule_host(alpha, ctypes.byref(K), c1, c2))
+    return K.value, np.array(c1[:K.value], dtype=np.float32), np.array(c2[:K.value], dtype=np.float32)
+
+
+def fourier_restriction(n: int) -> np.ndarray:
+    """The Fourier coupling's restriction matrix P1 [n/3][n] (host logic)."""
+    P1 = np.zeros((n // 3, n), dtype=np.float32)
+    _check(lib().mlmc_dk_fourier_restriction_host(n, P1.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+    return P1
 
 
 def noise_dev(seed: int, level: int, stream_tag: int, sample: int, m: int, n: int,

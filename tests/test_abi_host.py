@@ -116,3 +116,40 @@ def test_theta_scheme_config_checks(dk):
         with pytest.raises(dk.MLMCError) as e:
             dk.Context(1.0, 4, 0, 1.0, 0.9, 100.0, one, phi, theta_b0=0.25)
         assert e.value.code == dk.ERR_CUDA
+
+
+@pytest.mark.parametrize("alpha", [0.01, 0.21, 0.85, 2.0])
+def test_chebyshev_schedule_solves_the_implicit_system(dk, alpha):
+    """The kernel's iteration (u = 0, r = b, d = r/(1+4 alpha); u += d, r -= A d,
+    d = c1 d + c2 r) with the host's schedule, run in FP64, against the
+    oracle's exact Fourier solve of (I + alpha L) u = b."""
+    K, c1, c2 = dk.chebyshev_schedule(alpha)
+    assert 1 <= K <= 64
+    n = 16
+    rng = np.random.default_rng(5)
+    b = rng.standard_normal((n, n))
+    L = lambda a: 4 * a - np.roll(a, 1, 0) - np.roll(a, -1, 0) - np.roll(a, 1, 1) - np.roll(a, -1, 1)
+    u = np.zeros_like(b)
+    r = b.copy()
+    d = r / (1 + 4 * alpha)
+    for k in range(K):
+        ad = d + alpha * L(d)
+        u += d
+        r -= ad
+        if k + 1 < K:
+            d = float(c1[k]) * d + float(c2[k]) * r
+    exact = oracle.helmholtz_solve(n, alpha, b)
+    # 2^-27 bound of the polynomial, plus the FP32 rounding of the coefficients
+    assert np.linalg.norm(u - exact) <= 1e-6 * np.linalg.norm(exact)
+    assert dk.chebyshev_schedule(0.0)[0] == 0
+
+
+@pytest.mark.parametrize("n", [18, 54])
+def test_fourier_restriction_matrix_is_the_oracles(dk, n):
+    """P1 S P1^T from the host's matrix equals the oracle's restriction (its own
+    DFT sums) to FP32 accuracy, and P1 has orthonormal rows."""
+    P1 = dk.fourier_restriction(n).astype(np.float64)
+    nc = n // 3
+    np.testing.assert_allclose(P1 @ P1.T, np.eye(nc), rtol=0, atol=2e-6)
+    S = np.random.default_rng(n).standard_normal((n, n))
+    np.testing.assert_allclose(P1 @ S @ P1.T, oracle.fourier_restrict(n, nc, S), rtol=0, atol=2e-5)
