@@ -114,3 +114,22 @@ def test_empty_batch_gives_zero_sums(dk):
     with dk.Context.from_workload(wl) as ctx:
         sums, _ = _gpu(ctx, dk, 2, 0, 0, 0, 1)
     assert not sums.any()
+
+
+def test_four_observables_with_products(dk):
+    four = W.get("large32_1024").observables
+    wl = W.get("fourier6_54").with_(name="fourier6_54_four", observables=four, products=True)
+    level, count, seed, first = 1, 12, 73, 0
+    levels = _levels(wl)
+    with dk.Context.from_workload(wl) as ctx:
+        assert ctx.n_quant == 10
+        sums, samp = _gpu(ctx, dk, level, 0, first, count, seed)
+    ol = oracle.level_inputs(wl.length, levels, wl.N, wl.rho0_all(), wl.phi_all(), level, True, coupling=1)
+    r = oracle.run_samples(ol, seed, range(first, first + count), True)
+    for cols, key, l in ((slice(0, 4), "Y_f", level), (slice(4, 8), "Y_c", level - 1)):
+        yb = _ybar(wl, levels, l)
+        yo = r[key]
+        scale = np.sqrt(np.mean((yo - yb[None, :]) ** 2, axis=0))
+        err = np.abs(samp[:, cols] + yb[None, :] - yo) / (TOL * np.maximum(np.abs(yo), scale[None, :]))
+        assert float(err.max()) <= 1.0, (key, float(err.max()))
+    assert int(sums[0]) == count and sums[1] == 0.0

@@ -164,3 +164,18 @@ def test_empty_batch_gives_zero_sums(dk):
     with dk.Context.from_workload(wl) as ctx:
         sums, _ = _gpu(ctx, dk, 2, 0, 0, 0, 1)
     assert not sums.any()
+
+
+def test_four_observables_with_products(dk):
+    """Four test functions and all their products on the theta kernel: every
+    observable per sample against the oracle, ten quantities summed."""
+    four = W.get("large32_1024").observables
+    wl = W.get("theta16_64").with_(name="theta16_64_four", observables=four, products=True)
+    level, count, seed, first = 1, 12, 71, 0
+    with dk.Context.from_workload(wl) as ctx:
+        assert ctx.n_quant == 10
+        sums, samp = _gpu(ctx, dk, level, 0, first, count, seed)
+    r, ybf, ybc = _oracle(wl, level, 0, first, count, seed)
+    _parity(samp[:, 0:4] + ybf[None, :], r["Y_f"], ybf, "theta four observables fine")
+    _parity(samp[:, 4:8] + ybc[None, :], r["Y_c"], ybc, "theta four observables coarse")
+    assert int(sums[0]) == count and sums[1] == 0.0
