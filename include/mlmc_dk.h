@@ -396,6 +396,13 @@ int mlmc_dk_estimate_surrogate(mlmc_dk_ctx* ctx, double eps, int32_t relative, u
 int mlmc_dk_plan(int32_t L, const int64_t* n, const double* s1, const double* s2,
                  const double* cost, double eps, int64_t* target, int32_t* converged);
 
+/* The same for a level hierarchy with mesh ratio `ratio` (> 1): the stopping
+ * test max_t ratio^(-t alpha) |E_{L-t}| / (ratio^alpha - 1) < eps / sqrt 2 (the
+ * printed test has ratio 2; the Fourier coupling's levels refine by 3).
+ * mlmc_dk_estimate uses the context's ratio. */
+int mlmc_dk_plan_ratio(int32_t L, const int64_t* n, const double* s1, const double* s2, const double* cost,
+                       double eps, double ratio, int64_t* target, int32_t* converged);
+
 /* Host-only discrete mean field: the noise-free scheme with mesh h and step
  * tau iterated M times from rho0 (n x n, n a power of two), by FFT
  * diagonalisation in FP64.  out may alias rho0. */

@@ -344,17 +344,18 @@ def mlmc_optimal_samples(V: Sequence[float], C: Sequence[float], eps: float) -> 
     return [int(math.ceil(2.0 / (eps * eps) * math.sqrt(v / c) * total)) for v, c in zip(V, C)]
 
 
-def mlmc_converged(E: Sequence[float], eps: float, alpha: float = 2.0) -> bool:
+def mlmc_converged(E: Sequence[float], eps: float, alpha: float = 2.0, ratio: float = 2.0) -> bool:
     """Eq. (convergence_criterion): stop on level L if
     max_{t in {0,1,2}} 2^{-t alpha} |E[P_{L-t} - P_{L-t-1}]| / (2^alpha - 1) < eps / sqrt 2,
-    with P_{-1} = 0 (levels below 0 are skipped)."""
+    with P_{-1} = 0 (levels below 0 are skipped).  The 2 is the mesh ratio of
+    the NN hierarchy; `ratio` = 3 for the Fourier coupling's levels."""
     L = len(E) - 1
     worst = 0.0
     for t in range(3):
         if L - t < 0:
             break
-        worst = max(worst, 2.0 ** (-t * alpha) * abs(E[L - t]))
-    return worst / (2.0 ** alpha - 1.0) < eps / math.sqrt(2.0)
+        worst = max(worst, ratio ** (-t * alpha) * abs(E[L - t]))
+    return worst / (ratio ** alpha - 1.0) < eps / math.sqrt(2.0)
 
 
 def mlmc_estimator(sums_dp: Sequence[float], counts: Sequence[int]) -> float:

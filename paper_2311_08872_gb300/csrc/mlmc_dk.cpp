@@ -1319,6 +1319,12 @@ int mlmc_dk_plan(int32_t L, const int64_t* n, const double* s1, const double* s2
     return plan_ratio(L, n, s1, s2, cost, eps, target, converged, 2.0);
 }
 
+int mlmc_dk_plan_ratio(int32_t L, const int64_t* n, const double* s1, const double* s2, const double* cost,
+                       double eps, double ratio, int64_t* target, int32_t* converged) {
+    if (!(ratio > 1.0)) return fail(nullptr, MLMC_DK_ERR_INVALID, "plan: ratio must exceed 1");
+    return plan_ratio(L, n, s1, s2, cost, eps, target, converged, ratio);
+}
+
 }  // extern "C"
 
 namespace {

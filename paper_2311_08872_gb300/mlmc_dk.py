@@ -114,6 +114,8 @@ def lib() -> ctypes.CDLL:
                                    ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]
         L.mlmc_dk_mean_field_host.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
                                               _dp, _dp]
+        L.mlmc_dk_plan_ratio.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_int64), _dp, _dp, _dp, ctypes.c_double,
+                                         ctypes.c_double, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]
         _fp = ctypes.POINTER(ctypes.c_float)
         L.mlmc_dk_chebyshev_schedule_host.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_int32), _fp, _fp]
         L.mlmc_dk_fourier_restriction_host.argtypes = [ctypes.c_int32, _fp]
@@ -197,8 +199,10 @@ def noise_dev(seed: int, level: int, stream_tag: int, sample: int, m: int, n: in
                                    ctypes.c_void_p(raw_ptr or None), ctypes.c_void_p(stream or None)))
 
 
-def plan(n: Sequence[int], s1: Sequence[float], s2: Sequence[float], cost: Sequence[float], eps: float):
-    """Algorithm 1's host step: targets by Eq. (opt_M_ell), stopping test."""
+def plan(n: Sequence[int], s1: Sequence[float], s2: Sequence[float], cost: Sequence[float], eps: float,
+         ratio: float = 2.0):
+    """Algorithm 1's host step: targets by Eq. (opt_M_ell), stopping test of
+    Eq. (convergence_criterion) for levels refining by `ratio`."""
     L = len(n) - 1
     n_ = (ctypes.c_int64 * (L + 1))(*n)
     a = (ctypes.c_double * (L + 1))(*s1)
@@ -206,7 +210,10 @@ def plan(n: Sequence[int], s1: Sequence[float], s2: Sequence[float], cost: Seque
     c = (ctypes.c_double * (L + 1))(*cost)
     t = (ctypes.c_int64 * (L + 1))()
     conv = ctypes.c_int32(0)
-    _check(lib().mlmc_dk_plan(L, n_, a, b, c, eps, t, ctypes.byref(conv)))
+    if ratio == 2.0:
+        _check(lib().mlmc_dk_plan(L, n_, a, b, c, eps, t, ctypes.byref(conv)))
+    else:
+        _check(lib().mlmc_dk_plan_ratio(L, n_, a, b, c, eps, ratio, t, ctypes.byref(conv)))
     return list(t), bool(conv.value)
 
 

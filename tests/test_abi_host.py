@@ -153,3 +153,27 @@ def test_fourier_restriction_matrix_is_the_oracles(dk, n):
     np.testing.assert_allclose(P1 @ P1.T, np.eye(nc), rtol=0, atol=2e-6)
     S = np.random.default_rng(n).standard_normal((n, n))
     np.testing.assert_allclose(P1 @ S @ P1.T, oracle.fourier_restrict(n, nc, S), rtol=0, atol=2e-5)
+
+
+def test_plan_with_mesh_ratio_three(dk):
+    """Eq. (convergence_criterion) on a ratio-3 hierarchy (Fourier coupling)
+    against the oracle's test with the same ratio; the allocation does not
+    depend on the ratio."""
+    rng = np.random.default_rng(11)
+    differs = 0
+    for trial in range(300):
+        L = int(rng.integers(0, 5))
+        n = [int(rng.integers(2, 10 ** 5)) for _ in range(L + 1)]
+        E = [float(rng.normal(0, 10.0 ** -rng.uniform(1, 4))) for _ in range(L + 1)]
+        V = [float(10.0 ** -rng.uniform(1, 8)) for _ in range(L + 1)]
+        s1 = [e * m for e, m in zip(E, n)]
+        s2 = [(v * (m - 1) + e * e * m) for e, v, m in zip(E, V, n)]
+        cost = [float(9.0 ** l * 1e3) for l in range(L + 1)]
+        eps = float(10.0 ** -rng.uniform(1, 4))
+        t3, c3 = dk.plan(n, s1, s2, cost, eps, ratio=3.0)
+        t2, c2 = dk.plan(n, s1, s2, cost, eps)
+        assert t3 == t2
+        Eh = [a / m for a, m in zip(s1, n)]
+        assert c3 == oracle.mlmc_converged(Eh, eps, ratio=3.0)
+        differs += c3 != c2
+    assert differs > 0      # the ratio changes some decisions
