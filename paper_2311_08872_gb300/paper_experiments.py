@@ -19,8 +19,9 @@ estimate, both costs and their ratio.
 Type 2: for each finest level L = 1..L_max, MLMC with the geometric
 progression M_(l-1) = 4 M_l and a plain-MC estimator on level L of the same
 cost; the ratio of their variances is the variance reduction factor of
-Proposition PropVarFactor, printed beside h_min^-2 |log2 h_min|^-1 scaled to
-agree at L = 1.
+Proposition PropVarFactor, printed beside h_min^-beta |log2 h_min|^-1 scaled to
+agree at L = 1 (beta = 2 for the NN coupling, 4 for the Fourier coupling:
+`paper_reg_fourier`, the regular setting on 6^2, 18^2, 54^2).
 
 Each row is printed as it completes, then one JSON line with all rows.  Times
 are device times of the level kernels (CUDA events) on the GPU this runs on.
@@ -103,10 +104,11 @@ def type2(ctx, L_max, M_finest, seed, length, times):
         m_mc = secs / times[L]["t_mc"]
         var_mc = times[L]["var_P"] / m_mc
         h_min = length / ctx.level_info(L).n
+        beta = 4 if ctx.level_info(L).coupling == 1 else 2
         rows.append({"L": L, "h_min": h_min, "M": M, "V": V, "mlmc_s": secs, "var_mlmc": var_mlmc,
                      "mc_samples_same_cost": m_mc, "var_P_L": times[L]["var_P"], "var_mc": var_mc,
                      "variance_reduction": var_mc / var_mlmc if var_mlmc > 0 else None,
-                     "predicted_shape": h_min ** -2 / abs(math.log2(h_min))})
+                     "predicted_shape": h_min ** -beta / abs(math.log2(h_min))})
         print(json.dumps({"row": rows[-1]}), flush=True)
     base = rows[0]["variance_reduction"] / rows[0]["predicted_shape"] if rows and rows[0]["variance_reduction"] else None
     for r in rows:
@@ -116,7 +118,7 @@ def type2(ctx, L_max, M_finest, seed, length, times):
 
 def main() -> None:
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="paper_reg", choices=["paper_reg", "paper_irreg"])
+    ap.add_argument("--workload", default="paper_reg", choices=["paper_reg", "paper_irreg", "paper_reg_fourier"])
     ap.add_argument("--N", type=float, default=2e5)
     ap.add_argument("--type", type=int, default=1, choices=[1, 2])
     ap.add_argument("--eps", type=str, default=None, help="comma-separated absolute accuracies (default: the paper's)")
