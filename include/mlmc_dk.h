@@ -352,7 +352,10 @@ int mlmc_dk_tune(mlmc_dk_ctx* ctx, int32_t repeats, double* seconds);
  * where the level below 0 draws its standardised features directly as
  * standard normals (stream 2, level tag 0) and the correction level evaluates
  * S on the features of the very noise that drives its level-0 path; the sum is
- * unbiased for any network.  Requires a level-0 grid of 8^2..32^2.
+ * unbiased for any network.  Requires a level-0 grid of 8^2..32^2 (so not the
+ * Fourier coupling's 6^2).  With the theta-scheme g_j is its factor
+ * (1 - b1 lam_j)/(1 + b0 lam_j); the constant factor 1/(1 + b0 lam_j) through
+ * which each step's noise reaches the mode cancels in the standardisation.
  * Parameters: flat FP32 vector of 148224 + 257 K values
  * (mlmc_dk_surrogate_info), per layer W [out][in] row-major then b [out]. */
 int mlmc_dk_surrogate_init(mlmc_dk_ctx* ctx, uint64_t seed);   /* He-uniform weights, zero biases */

@@ -48,10 +48,14 @@ def modes(n: int, count: int = 32) -> np.ndarray:
     return np.array(out[:count])
 
 
-def heat_factors(n: int, mu: float, count: int = 32) -> np.ndarray:
+def heat_factors(n: int, mu: float, count: int = 32, b0: float = 0.0) -> np.ndarray:
+    """Per-step factor of each mode under the noise-free scheme: with
+    lam = 2 mu (sin^2(pi k1/n) + sin^2(pi k2/n)), (1 - b1 lam)/(1 + b0 lam) for
+    the weights (b0, b1 = 1 - b0) of Eq. (FullyDiscreteDK) (1 - lam explicit)."""
     g = []
     for k1, k2 in mode_vectors(n, count):
-        gk = 1.0 - 2.0 * mu * (math.sin(math.pi * k1 / n) ** 2 + math.sin(math.pi * k2 / n) ** 2)
+        lam = 2.0 * mu * (math.sin(math.pi * k1 / n) ** 2 + math.sin(math.pi * k2 / n) ** 2)
+        gk = (1.0 - (1.0 - b0) * lam) / (1.0 + b0 * lam)
         g += [gk, gk]
     return np.array(g[:count])
 

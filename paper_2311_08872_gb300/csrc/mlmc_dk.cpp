@@ -1531,7 +1531,12 @@ void free_surrogate(Surrogate* s) {
 // The 32 lowest real orthonormal modes of the n x n grid: wave vectors with
 // k1 > 0, or k1 = 0 and k2 > 0 (Nyquist lines excluded), ordered by |k|^2
 // then (k1, k2); a cosine and a sine mode each, scaled to unit plain-sum norm.
-void build_modes(int n, double mu, int M, std::vector<float>& E, std::vector<float>& g, std::vector<float>& isig) {
+// With the theta-scheme's weights (b0, 1 - b0) the per-step factor of mode k is
+// (1 - b1 lam)/(1 + b0 lam), and the noise of every step reaches the mode
+// through the implicit operator with the constant factor 1/(1 + b0 lam), which
+// the standardisation by the feature's exact deviation removes.
+void build_modes(int n, double mu, int M, std::vector<float>& E, std::vector<float>& g, std::vector<float>& isig,
+                 double b0) {
     std::vector<std::pair<int, int>> ks;
     for (int k1 = 0; k1 <= n / 2; ++k1)
         for (int k2 = -n / 2 + 1; k2 <= n / 2; ++k2) {
@@ -1548,7 +1553,8 @@ void build_modes(int n, double mu, int M, std::vector<float>& E, std::vector<flo
     const double scale = std::sqrt(2.0 / ((double)n * n));
     for (int j = 0; j < dk::kModes / 2; ++j) {
         const int k1 = ks[j].first, k2 = ks[j].second;
-        const double gk = 1.0 - 2.0 * mu * (std::pow(std::sin(M_PI * k1 / n), 2) + std::pow(std::sin(M_PI * k2 / n), 2));
+        const double lam = 2.0 * mu * (std::pow(std::sin(M_PI * k1 / n), 2) + std::pow(std::sin(M_PI * k2 / n), 2));
+        const double gk = (1.0 - (1.0 - b0) * lam) / (1.0 + b0 * lam);
         double var = 0.0, p = 1.0;
         for (int i = 0; i < M; ++i, p *= gk * gk) var += p;
         for (int cs = 0; cs < 2; ++cs) {
@@ -1664,8 +1670,6 @@ extern "C" {
 int mlmc_dk_surrogate_init(mlmc_dk_ctx* ctx, uint64_t seed) {
     if (!ctx) return fail(nullptr, MLMC_DK_ERR_INVALID, "null context");
     const LevelTab& l0 = ctx->lv[0];
-    if (ctx->theta)
-        return fail(ctx, MLMC_DK_ERR_UNSUPPORTED, "surrogate: explicit scheme only (its features use the explicit symbol)");
     if (l0.n < 8 || l0.n > 32 || l0.streamed)
         return fail(ctx, MLMC_DK_ERR_UNSUPPORTED, "surrogate: level-0 grid must be 8^2..32^2");
     free_surrogate(ctx->sur);
@@ -1679,7 +1683,7 @@ int mlmc_dk_surrogate_init(mlmc_dk_ctx* ctx, uint64_t seed) {
     s->batch_cap = 4096;
     const int kP = s->P, kBfTotal = bf_total(s->K), K = s->K;
     std::vector<float> E, g, isig;
-    build_modes(l0.n, l0.tau / (l0.h * l0.h), l0.M, E, g, isig);
+    build_modes(l0.n, l0.tau / (l0.h * l0.h), l0.M, E, g, isig, ctx->b0);
     const size_t ch = (size_t)s->chunk;
     cudaError_t e;
     auto alloc = [&](void** p, size_t bytes) { return e == cudaSuccess ? (e = cudaMalloc(p, bytes)) : e; };

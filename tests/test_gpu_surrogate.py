@@ -191,3 +191,28 @@ def test_four_output_level_is_unbiased_for_every_quantity(dk, trained):
             assert abs(est - ref) < 3.5 * se, (q, est, ref, se)
             if trained and q in (0, 4, 7, 9):   # diagonal quantities (j, j)
                 assert var(b) < var(c), (q, var(b), var(c))
+
+
+def test_theta_scheme_features_and_unbiasedness(dk):
+    """The learned level on Crank--Nicolson levels: features with the theta
+    factor (1 - b1 lam)/(1 + b0 lam) against the oracle, and the learned level
+    plus its correction unbiased against plain level 0 (random network)."""
+    wl = W.get("theta16_64").with_(L_max=1)
+    n_s = 40000
+    with dk.Context.from_workload(wl) as ctx:
+        ctx.surrogate_init(3)
+        info = ctx.level_info(0)
+        X = ctx.surrogate_features(5, 4, seed=9, stream_tag=3)
+        s_sur = ctx.run_surrogate(-1, n_s, seed=13)[0]
+        s_cor = ctx.run_surrogate(0, n_s, seed=14)[0]
+        s_p0 = ctx.run_level(0, n_s, seed=15)[0]
+    n, M = info.n, info.M
+    E, g = sg.modes(n), sg.heat_factors(n, info.tau / info.h ** 2, b0=wl.b0)
+    sig = sg.feature_sigma(g, M)
+    for i in range(4):
+        Zs = [oracle.normals(9, 0, 3, 5 + i, m, n) for m in range(M)]
+        np.testing.assert_allclose(X[i], sg.features(Zs, E, g) / sig, atol=2e-5, rtol=0)
+    var = lambda q: (q.dp2 - q.dp1 ** 2 / q.n) / (q.n - 1)
+    est = s_sur.dp1 / n_s + s_cor.dp1 / n_s
+    se = math.sqrt(var(s_sur) / n_s + var(s_cor) / n_s + var(s_p0) / n_s)
+    assert abs(est - s_p0.dp1 / n_s) < 3.5 * se
