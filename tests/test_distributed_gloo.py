@@ -59,7 +59,7 @@ def _oracle_sampler(wl):
     """run_level(level, first, count) -> sums in the device layout, from the
     FP64 oracle (stands in for the GPU path of each rank)."""
     import oracle
-    levels = oracle.level_table(wl.length, wl.n0, wl.L_max, wl.T, wl.mu, wl.M0)
+    levels = oracle.level_table(wl.length, wl.n0, wl.L_max, wl.T, wl.mu, wl.M0, ratio=wl.ratio)
     rho0, phi = wl.rho0_all(), wl.phi_all()
     ybar = [oracle.inner_h(oracle.mean_field(l.n, l.h, l.tau, l.M, rho0[l.level]), phi[l.level][0], l.h)
             for l in levels]
@@ -67,7 +67,7 @@ def _oracle_sampler(wl):
             for l in range(len(levels))]
 
     def run_level(l, first, count):
-        ol = oracle.level_inputs(wl.length, levels, wl.N, rho0, phi, l, l > 0)
+        ol = oracle.level_inputs(wl.length, levels, wl.N, rho0, phi, l, l > 0, coupling=wl.coupling)
         r = oracle.run_samples(ol, wl.seed, range(first, first + count), l > 0)
         df = r["Y_f"][:, 0] - ybar[l]
         dc = r["Y_c"][:, 0] - ybar[l - 1] if l else np.zeros(count)
@@ -79,12 +79,19 @@ def _oracle_sampler(wl):
     return run_level, cost
 
 
-def _small_workload():
+def _small_workload(fourier=False):
     from paper_2311_08872_gb300 import workloads as W
+    if fourier:
+        return W.get("fourier6_54").with_(L_max=1)
     return W.get("mlmc16_256").with_(n0=8, L_max=3, T=0.005, N=1e5)
 
 
-def _estimate_worker(rank, world, port, out):
+def _plan(wl):
+    from paper_2311_08872_gb300 import mlmc_dk
+    return lambda n, s1, s2, cost, eps: mlmc_dk.plan(n, s1, s2, cost, eps, ratio=float(wl.ratio))
+
+
+def _estimate_worker(rank, world, port, out, fourier=False):
     import torch.distributed as dist
     from paper_2311_08872_gb300 import distributed as D
     from paper_2311_08872_gb300 import mlmc_dk
@@ -93,30 +100,31 @@ def _estimate_worker(rank, world, port, out):
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
-        wl = _small_workload()
+        wl = _small_workload(fourier)
         run_level, cost = _oracle_sampler(wl)
-        r = D.estimate(run_level, wl.L_max, 0.03, cost, mlmc_dk.plan, 14, pilot=64, world=world, rank=rank,
+        r = D.estimate(run_level, wl.L_max, 0.03, cost, _plan(wl), 14, pilot=64, world=world, rank=rank,
                        reduce=D.allreduce_sums)
         out.put((rank, r["estimate"], r["variance"], r["L"], r["M"], r["converged"]))
     finally:
         dist.destroy_process_group()
 
 
-def test_algorithm1_across_two_gloo_ranks_matches_one_rank():
+@pytest.mark.parametrize("fourier", [False, True])
+def test_algorithm1_across_two_gloo_ranks_matches_one_rank(fourier):
     """Two ranks share every round's new sample ids and all-reduce the level
-    sums; they take the same decisions as one rank running all the ids."""
+    sums; they take the same decisions as one rank running all the ids (NN
+    hierarchy, and the Fourier coupling's ratio-3 hierarchy)."""
     import multiprocessing as mp
     from paper_2311_08872_gb300 import distributed as D
-    from paper_2311_08872_gb300 import mlmc_dk
 
-    wl = _small_workload()
+    wl = _small_workload(fourier)
     run_level, cost = _oracle_sampler(wl)
-    ref = D.estimate(run_level, wl.L_max, 0.03, cost, mlmc_dk.plan, 14, pilot=64)
+    ref = D.estimate(run_level, wl.L_max, 0.03, cost, _plan(wl), 14, pilot=64)
     assert ref["converged"] or ref["L"] == wl.L_max
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_estimate_worker, args=(r, 2, port, q)) for r in range(2)]
+    procs = [ctx.Process(target=_estimate_worker, args=(r, 2, port, q, fourier)) for r in range(2)]
     for p in procs:
         p.start()
     res = [q.get(timeout=600) for _ in range(2)]
