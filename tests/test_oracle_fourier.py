@@ -8,8 +8,9 @@ against those of the fine field (shared modes equal, the Nyquist alias pair
 combined), the restriction as a matrix (rows orthonormal, so white noise stays
 white with the same variance: Remark distribution_W_ell), resolved smooth
 modes carried unchanged, a dense restatement of a whole coupled pair on a
-6 x 6 / 2 x 2 grid built from numpy's complex exponentials, and the law of the
-coarse member against stand-alone coarse paths on seeded samples.
+6 x 6 / 2 x 2 grid built from numpy's complex exponentials, the law of the
+coarse member against stand-alone coarse paths on seeded samples, and
+E[Y] = Ybar on both members at low density.
 """
 import math
 
@@ -148,3 +149,18 @@ def test_coarse_member_has_law_of_standalone_coarse_path():
     assert abs(pc.mean() - pa.mean()) < 3.5 * se
     # variances of P within sampling error (ratio of variances, F-distribution spread ~ 2/sqrt(n))
     assert abs(pc.var() / pa.var() - 1.0) < 0.2
+
+
+def test_mean_of_Y_is_the_mean_field_on_both_members():
+    """E[Y_f] = Ybar_l and E[Y_c] = Ybar_{l-1} for Fourier-coupled pairs at low
+    density (the restricted noise has zero mean)."""
+    N = 50.0
+    levels = oracle.level_table(1.0, 6, 1, 0.02, 0.1, ratio=3)
+    g = lambda n: 0.05 + np.exp(-((_grid(n)[0] - 0.5) ** 2 + (_grid(n)[1] - 0.5) ** 2) / 0.05)
+    phi = lambda n: np.cos(2 * math.pi * _grid(n)[0])
+    ol = oracle.OracleLevel(levels[1], N, g(18), [phi(18)], g(6), [phi(6)], coupling=1)
+    r = oracle.run_samples(ol, 6, range(2000), True)
+    for key, lv in (("Y_f", levels[1]), ("Y_c", levels[0])):
+        ybar = oracle.inner_h(oracle.mean_field(lv.n, lv.h, lv.tau, lv.M, g(lv.n)), phi(lv.n), lv.h)
+        y = r[key][:, 0]
+        assert abs(y.mean() - ybar) < 3.5 * y.std(ddof=1) / math.sqrt(y.size), key

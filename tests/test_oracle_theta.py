@@ -8,8 +8,8 @@ code path: the linear system itself applied with shifted arrays (residual),
 a dense LU solve on 8 x 8 grids (one step and a whole coupled pair), the
 special case b0 = 0 (the explicit oracle), the mode symbol
 (1 - b1 lam)/(1 + b0 lam), the stability threshold it implies, exact mass
-conservation, and the martingale closed form of E[P] (with the factor the
-solve puts on the noise) on seeded samples.
+conservation, the martingale closed form of E[P] (with the factor the
+solve puts on the noise) on seeded samples, and E[Y] = Ybar at low density.
 """
 import math
 
@@ -186,3 +186,17 @@ def test_mean_of_P_matches_martingale_closed_form(b0, mu):
     expect = oracle.closed_form_EP_cos1(1.0, n, lv.tau, lv.M, b0=b0)
     assert abs(P.mean() - expect) < 3.5 * se
     assert se / expect < 0.05
+
+
+def test_mean_of_Y_is_the_theta_mean_field_at_low_density():
+    """E[Y] = Ybar for the theta-scheme too (linear scheme, zero-mean noise),
+    even where [rho]^+ truncates."""
+    N, n = 30.0, 8
+    lv = oracle.level_table(1.0, n, 0, 0.02, 1.5)[0]
+    x1, x2 = _grid(n)
+    rho0 = 0.02 + np.exp(-((x1 - 0.5) ** 2 + (x2 - 0.5) ** 2) / 0.02)
+    phi = np.cos(2 * math.pi * x1)
+    ol = oracle.OracleLevel(lv, N, rho0, [phi], b0=0.5)
+    y = oracle.run_samples(ol, seed=3, ids=range(3000), coupled=False, stream=1)["Y_f"][:, 0]
+    ybar = oracle.inner_h(oracle.mean_field(n, lv.h, lv.tau, lv.M, rho0, b0=0.5), phi, lv.h)
+    assert abs(y.mean() - ybar) < 3.5 * y.std(ddof=1) / math.sqrt(y.size)
