@@ -407,9 +407,16 @@ int mlmc_dk_plan_ratio(int32_t L, const int64_t* n, const double* s1, const doub
                        double eps, double ratio, int64_t* target, int32_t* converged);
 
 /* Host-only discrete mean field: the noise-free scheme with mesh h and step
- * tau iterated M times from rho0 (n x n, n a power of two), by FFT
- * diagonalisation in FP64.  out may alias rho0. */
+ * tau iterated M times from rho0 (n x n, n even), in FP64: by FFT
+ * diagonalisation when n is a power of two, by M direct stencil steps
+ * otherwise (the Fourier coupling's grids).  out may alias rho0. */
 int mlmc_dk_mean_field_host(int32_t n, double h, double tau, int64_t M, const double* rho0, double* out);
+
+/* The same for the theta-scheme's weights (b0, 1 - b0) of Eq. (FullyDiscreteDK):
+ * every discrete Fourier mode is multiplied by (1 - b1 lam)/(1 + b0 lam) per
+ * step (n a power of two). */
+int mlmc_dk_mean_field_theta_host(int32_t n, double h, double tau, int64_t M, double b0, const double* rho0,
+                                  double* out);
 
 /* Host-only Chebyshev schedule of the theta-scheme's implicit solve
  * (I + alpha L) u = b, L = -h^2 Delta_h, alpha = b0 tau / (2 h^2): *K steps

@@ -526,10 +526,19 @@ int mlmc_dk_fourier_restriction_host(int32_t n, float* P1) {
 }
 
 int mlmc_dk_mean_field_host(int32_t n, double h, double tau, int64_t M, const double* rho0, double* out) {
-    if (!is_pow2(n) || n < 2 || h <= 0 || tau < 0 || M < 0 || !rho0 || !out)
+    if (n < 2 || (n & 1) || h <= 0 || tau < 0 || M < 0 || !rho0 || !out)
         return fail(nullptr, MLMC_DK_ERR_INVALID, "mean_field_host: bad arguments");
     std::vector<double> tmp(rho0, rho0 + (size_t)n * n);
-    mean_field(n, h, tau, M, tmp.data(), out);
+    mean_field_any(n, h, tau, M, tmp.data(), out);
+    return MLMC_DK_OK;
+}
+
+int mlmc_dk_mean_field_theta_host(int32_t n, double h, double tau, int64_t M, double b0, const double* rho0,
+                                  double* out) {
+    if (!is_pow2(n) || n < 2 || h <= 0 || tau < 0 || M < 0 || !(b0 >= 0.0 && b0 <= 1.0) || !rho0 || !out)
+        return fail(nullptr, MLMC_DK_ERR_INVALID, "mean_field_theta_host: bad arguments");
+    std::vector<double> tmp(rho0, rho0 + (size_t)n * n);
+    mean_field(n, h, tau, M, tmp.data(), out, b0);
     return MLMC_DK_OK;
 }
 

@@ -114,6 +114,8 @@ def lib() -> ctypes.CDLL:
                                    ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]
         L.mlmc_dk_mean_field_host.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
                                               _dp, _dp]
+        L.mlmc_dk_mean_field_theta_host.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                                    ctypes.c_int64, ctypes.c_double, _dp, _dp]
         L.mlmc_dk_plan_ratio.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_int64), _dp, _dp, _dp, ctypes.c_double,
                                          ctypes.c_double, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]
         _fp = ctypes.POINTER(ctypes.c_float)
@@ -169,10 +171,13 @@ def _f64(a) -> np.ndarray:
 
 
 # ------------------------------------------------------------ host helpers
-def mean_field_host(n: int, h: float, tau: float, M: int, rho0: np.ndarray) -> np.ndarray:
+def mean_field_host(n: int, h: float, tau: float, M: int, rho0: np.ndarray, b0: float = 0.0) -> np.ndarray:
     r = _f64(rho0).reshape(-1)
     out = np.empty_like(r)
-    _check(lib().mlmc_dk_mean_field_host(n, h, tau, M, r.ctypes.data_as(_dp), out.ctypes.data_as(_dp)))
+    if b0 == 0.0:
+        _check(lib().mlmc_dk_mean_field_host(n, h, tau, M, r.ctypes.data_as(_dp), out.ctypes.data_as(_dp)))
+    else:
+        _check(lib().mlmc_dk_mean_field_theta_host(n, h, tau, M, b0, r.ctypes.data_as(_dp), out.ctypes.data_as(_dp)))
     return out.reshape(n, n)
 
 

@@ -177,3 +177,29 @@ def test_plan_with_mesh_ratio_three(dk):
         assert c3 == oracle.mlmc_converged(Eh, eps, ratio=3.0)
         differs += c3 != c2
     assert differs > 0      # the ratio changes some decisions
+
+
+@pytest.mark.parametrize("n,M", [(6, 8), (18, 72), (54, 648)])
+def test_host_mean_field_on_fourier_grids(dk, n, M):
+    """The mean field the context uses on the Fourier coupling's grids (not
+    powers of two: direct stencil steps) against the oracle's iteration."""
+    h = 1.0 / n
+    x = np.arange(n) * h
+    x1, x2 = np.meshgrid(x, x, indexing="ij")
+    rho0 = 1.0 + 0.5 * np.sin(2 * math.pi * x1) * np.sin(2 * math.pi * x2) + 0.1 * np.cos(4 * math.pi * x1)
+    tau = 0.09 * h * h
+    np.testing.assert_allclose(dk.mean_field_host(n, h, tau, M, rho0), oracle.mean_field(n, h, tau, M, rho0),
+                               rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("b0,mu,M", [(0.5, 0.85, 96), (1.0, 1.7, 48), (0.25, 0.9, 30)])
+def test_host_theta_mean_field_matches_oracle(dk, b0, mu, M):
+    """The theta-scheme mean field of the context (Fourier symbol) against the
+    oracle's iterated exact solves."""
+    n = 32
+    h = 1.0 / n
+    x = np.arange(n) * h
+    x1, x2 = np.meshgrid(x, x, indexing="ij")
+    rho0 = 0.02 + 0.98 * np.exp(-((x1 - 0.5) ** 2 + (x2 - 0.4) ** 2) / 0.02)
+    np.testing.assert_allclose(dk.mean_field_host(n, h, mu * h * h, M, rho0, b0=b0),
+                               oracle.mean_field(n, h, mu * h * h, M, rho0, b0=b0), rtol=0, atol=1e-12)
