@@ -75,7 +75,7 @@ THETA_SOURCES = ("dk_theta.cu", "dk_device.cuh")
 # cell-steps) of the 54^2 coupled launch, from its ncu --set full capture;
 # valid under the recorded hash of its sources.
 FOURIER_KERNEL_INSTR = {"kernel": "fourier_kernel n=54 coupled=True",
-                        "instructions_per_cell_step": 94.6, "sources_sha256_16": "3014eb041e0601d7"}
+                        "instructions_per_cell_step": 94.6, "sources_sha256_16": "5eb2d85d130ecf3e"}
 FOURIER_SOURCES = ("dk_fourier.cu", "dk_device.cuh")
 
 

@@ -28,7 +28,7 @@
 // arithmetic; the state and transfers are published in shared memory for the
 // rows above and below and the segment ends.  The coarse grid and the
 // restriction loop over cells with the CTA's stride.  Two barriers per fine
-// step (three at a coarse step).
+// step, two more at a coarse step.
 #include "dk_device.cuh"
 #include "dk_kernels.h"
 
