@@ -203,3 +203,26 @@ def test_host_theta_mean_field_matches_oracle(dk, b0, mu, M):
     rho0 = 0.02 + 0.98 * np.exp(-((x1 - 0.5) ** 2 + (x2 - 0.4) ** 2) / 0.02)
     np.testing.assert_allclose(dk.mean_field_host(n, h, mu * h * h, M, rho0, b0=b0),
                                oracle.mean_field(n, h, mu * h * h, M, rho0, b0=b0), rtol=0, atol=1e-12)
+
+
+def test_fourier_coupling_config_checks(dk):
+    """The Fourier hierarchy's configuration checks run before any GPU call:
+    an unknown coupling, grids other than 6^2/18^2/54^2, and the Fourier
+    coupling with the theta-scheme are refused."""
+    def ctx(n0, L_max, **kw):
+        n = [n0 * 3 ** l for l in range(L_max + 1)]
+        return dk.Context(1.0, n0, L_max, 0.02, 0.1, 1e5, [np.ones((m, m)) for m in n],
+                          [[np.ones((m, m))] for m in n], **kw)
+    cases = [(dict(coupling=2), 6, 1, dk.ERR_INVALID),
+             (dict(coupling=1), 12, 1, dk.ERR_UNSUPPORTED),
+             (dict(coupling=1), 6, 3, dk.ERR_UNSUPPORTED),
+             (dict(coupling=1, theta_b0=0.5), 6, 1, dk.ERR_UNSUPPORTED)]
+    for kw, n0, L, code in cases:
+        with pytest.raises(dk.MLMCError) as e:
+            ctx(n0, L, **kw)
+        assert e.value.code == code, (kw, n0, L)
+    import torch
+    if not torch.cuda.is_available():
+        with pytest.raises(dk.MLMCError) as e:
+            ctx(6, 2, coupling=1)
+        assert e.value.code == dk.ERR_CUDA
