@@ -73,6 +73,7 @@ def lib():
                                               ctypes.c_uint64, ctypes.c_int, ctypes.c_double, ctypes.c_uint64,
                                               _dp, _dp, _dp, _dp]
         L.oracle_sample_perturbed.restype = ctypes.c_int
+        L.oracle_perturb_field.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_uint64, _dp, _dp]
         L.oracle_sample_given.argtypes = [ctypes.POINTER(_OracleLevelC), _dp, ctypes.c_int,
                                           _dp, _dp, _dp, _dp, _dp, _dp]
         L.oracle_sample_given.restype = ctypes.c_int
@@ -273,6 +274,15 @@ class OracleLevel:
         if rc_ != 0:
             raise ValueError(f"oracle_sample_perturbed failed ({rc_})")
         return dict(Y_f=Yf, Y_c=Yc if coupled else None, mass_f=mf.value, mass_c=mc.value if coupled else None)
+
+
+def perturb_field(n: int, amp: float, perturb_seed: int, rho: np.ndarray):
+    """The perturbation oracle_sample_perturbed applies after a step, on a copy
+    of the n x n field rho: returns (perturbed field, transfers [n, n, 2])."""
+    out = np.ascontiguousarray(rho, dtype=np.float64).reshape(n, n).copy()
+    tr = np.empty((n, n, 2))
+    lib().oracle_perturb_field(n, amp, perturb_seed, _ptr(out), _ptr(tr))
+    return out, tr
 
 
 def level_inputs(length: float, levels: List[Level], N: float, rho0: List[np.ndarray],

@@ -241,7 +241,9 @@ static uint64_t splitmix64(uint64_t* state)
     return z ^ (z >> 31);
 }
 
-static void perturb_edges(int n, double amp, uint64_t* state, double* rho)
+/* Edge (x, x + h e_r) moves e_r(x), uniform in [-amp/2, amp/2), from cell
+ * x + h e_r to cell x; transfers (optional, [n*n][2]) receives e_1, e_2. */
+static void perturb_edges(int n, double amp, uint64_t* state, double* rho, double* transfers)
 {
     for (int i1 = 0; i1 < n; ++i1)
         for (int i2 = 0; i2 < n; ++i2) {
@@ -252,7 +254,17 @@ static void perturb_edges(int n, double amp, uint64_t* state, double* rho)
             rho[x] += e1 + e2;
             rho[down] -= e1;
             rho[right] -= e2;
+            if (transfers) {
+                transfers[2 * x + 0] = e1;
+                transfers[2 * x + 1] = e2;
+            }
         }
+}
+
+void oracle_perturb_field(int n, double amp, uint64_t perturb_seed, double* rho, double* transfers)
+{
+    uint64_t state = perturb_seed;
+    perturb_edges(n, amp, &state, rho, transfers);
 }
 
 void oracle_fourier_restrict(int n, int nc, const double* fine, double* coarse)
@@ -371,7 +383,7 @@ static int sample_impl(const oracle_level* lv, uint64_t seed, int stream, uint64
         }
         oracle_theta_step(n, lv->h, lv->tau, lv->inv_sqrt_N, lv->b0, rho_f, dbeta_f, tmp_f);
         double* t = rho_f; rho_f = tmp_f; tmp_f = t;
-        if (amp > 0.0) perturb_edges(n, amp, &pstate, rho_f);
+        if (amp > 0.0) perturb_edges(n, amp, &pstate, rho_f, NULL);
         if (coupled && (m % kappa) == kappa - 1) {
             if (fourier) {
                 for (int r = 0; r < 2; ++r) {
@@ -384,7 +396,7 @@ static int sample_impl(const oracle_level* lv, uint64_t seed, int stream, uint64
             oracle_theta_step(nc, ratio * lv->h, kappa * lv->tau, lv->inv_sqrt_N, lv->b0, rho_c, dbeta_c, tmp_c);
             double* tc = rho_c; rho_c = tmp_c; tmp_c = tc;
             memset(dbeta_c, 0, sizeof(double) * cc * 2);
-            if (amp > 0.0) perturb_edges(nc, amp, &pstate, rho_c);
+            if (amp > 0.0) perturb_edges(nc, amp, &pstate, rho_c, NULL);
         }
     }
     double* ones = (double*)malloc(sizeof(double) * cf);

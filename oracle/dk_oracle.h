@@ -124,6 +124,13 @@ int oracle_sample_perturbed(const oracle_level* lv, uint64_t seed, int stream, u
                             int coupled, double amp, uint64_t perturb_seed,
                             double* Y_f, double* Y_c, double* mass_f, double* mass_c);
 
+/* One application of those perturbations to an n x n field rho (in place),
+ * the splitmix64 stream started at perturb_seed: edge (x, x + h e_r) moves
+ * e_r(x), uniform in [-amp/2, amp/2), from cell x + h e_r to cell x
+ * (transfers: NULL or [n*n][2] receiving e_1(x), e_2(x)).  Exposed so that
+ * tests can pin the perturbation's law and its conservation of mass. */
+void oracle_perturb_field(int n, double amp, uint64_t perturb_seed, double* rho, double* transfers);
+
 /* Noise-free scheme (the discrete mean field rho-bar of Eq. (eqn_MLMCLevels))
  * iterated M times from rho0. */
 void oracle_mean_field(int n, double h, double tau, int64_t M, const double* rho0, double* out);

@@ -199,7 +199,7 @@ def test_low_density_gaussian_ill_conditioned_level(dk):
     a rounding-sized perturbation already moves the oracle's own Y by ~1e-6, so
     the per-sample bar is the oracle's measured sensitivity."""
     wl = W.get("lowdens32_512")
-    check_level(dk, wl, 2, 0, 0, 1, seed=2, conditioned=True)
+    check_level(dk, wl, 2, 0, 0, 4, seed=2, processes=4, conditioned=True)
 
 
 def test_four_observables_with_products(dk):

@@ -94,7 +94,7 @@ def test_symmetric_and_right_most_couplings_are_unbiased(dk):
     print("V_l (levels 1..3), right-most:", out["mlmc16_256"], "symmetric:", out["mlmc16_256_sym"])
 
 
-def _oracle_mlmc(wl, eps_rel, seed, pilot, L_start):
+def _oracle_mlmc(wl, eps_rel, seed, pilot, L_start, processes=1):
     """Algorithm 1 with oracle samples, same decisions as the library's driver."""
     levels = oracle.level_table(wl.length, wl.n0, wl.L_max, wl.T, wl.mu, wl.M0)
     rho0, phi = wl.rho0_all(), wl.phi_all()
@@ -107,7 +107,7 @@ def _oracle_mlmc(wl, eps_rel, seed, pilot, L_start):
     def run(l, count):
         ol = oracle.level_inputs(wl.length, levels, wl.N, rho0, phi, l, l > 0)
         first = dps[l].size
-        r = oracle.run_samples(ol, seed, range(first, first + count), l > 0)
+        r = oracle.run_samples(ol, seed, range(first, first + count), l > 0, processes=processes)
         pf = wl.N * (r["Y_f"][:, 0] - ybar[l]) ** 2
         pc = wl.N * (r["Y_c"][:, 0] - ybar[l - 1]) ** 2 if l else 0.0
         dps[l] = np.concatenate([dps[l], pf - pc])
@@ -152,6 +152,59 @@ def test_estimate_matches_oracle_driven_algorithm(dk):
     if gM == counts:   # identical allocation -> identical samples -> per-sample tolerance
         assert abs(r.estimate - est) <= 1e-4 * abs(est)
     assert r.variance <= (r.eps_abs ** 2) / 2 * 1.05
+
+
+def test_estimate_matches_oracle_on_benchmark_shaped_hierarchy(dk):
+    """Algorithm 1 (Section 7.1) through mlmc_dk_estimate on the benchmark
+    workload's first three levels (16^2, 32^2, 64^2; T = 0.02, N = 1e5) at
+    eps = 2e-2 relative, beside the same algorithm driven by FP64 oracle
+    samples with the same seed and sample ids: the two estimates agree within
+    3 combined standard errors, and, since identical allocations give identical
+    samples, to the per-sample tolerance when the allocations coincide."""
+    wl = W.get("mlmc16_256").with_(L_max=2)
+    pilot = 256
+    with dk.Context.from_workload(wl, pilot=pilot, L_start=2) as ctx:
+        r = ctx.estimate(2e-2, relative=True, seed=23)
+    est, var, counts = _oracle_mlmc(wl, 2e-2, 23, pilot, 2, processes=8)
+    gM = [r.M[l] for l in range(r.L + 1)]
+    se = math.sqrt(r.variance + var)
+    print("GPU", r.estimate, gM, "oracle", est, counts, "combined SE", se)
+    assert abs(r.estimate - est) < 3.0 * se
+    assert r.variance <= (r.eps_abs ** 2) / 2 * 1.05
+    if gM == counts:
+        assert abs(r.estimate - est) <= 1e-4 * abs(est)
+
+
+def test_fixed_allocation_estimate_matches_oracle(dk):
+    """The MLMC estimate of Eq. (MLMCEstimator) from one multi-level batch with
+    fixed per-level counts (the benchmark step's form), against the oracle on
+    the same seed and sample ids: per level the sums of dP agree to the
+    per-sample tolerance, so the estimates do, unconditionally."""
+    wl = W.get("mlmc16_256").with_(L_max=2)
+    counts = [1500, 256, 64]
+    with dk.Context.from_workload(wl) as ctx:
+        res = ctx.run_batch(counts, seed=29)
+    levels = oracle.level_table(wl.length, wl.n0, wl.L_max, wl.T, wl.mu, wl.M0)
+    rho0, phi = wl.rho0_all(), wl.phi_all()
+    ybar = [oracle.inner_h(oracle.mean_field(v.n, v.h, v.tau, v.M, rho0[v.level]), phi[v.level][0], v.h)
+            for v in levels]
+    est_o, est_g, var_g = 0.0, 0.0, 0.0
+    for l, m in enumerate(counts):
+        ol = oracle.level_inputs(wl.length, levels, wl.N, rho0, phi, l, l > 0)
+        o = oracle.run_samples(ol, 29, range(m), l > 0, processes=8)
+        pf = wl.N * (o["Y_f"][:, 0] - ybar[l]) ** 2
+        pc = wl.N * (o["Y_c"][:, 0] - ybar[l - 1]) ** 2 if l else 0.0
+        dp = pf - pc
+        s = res[l][0]
+        assert s.n == m and s.max_mass_err == 0.0
+        # per level: the mean of dP to 1e-4 of the RMS of P_f (per-sample error ~1e-5)
+        rms = math.sqrt(np.mean(pf * pf))
+        assert abs(s.dp1 / m - dp.mean()) <= 1e-4 * rms, (l, s.dp1 / m, dp.mean())
+        est_o += dp.mean()
+        est_g += s.dp1 / m
+        var_g += (s.dp2 - s.dp1 ** 2 / m) / (m - 1) / m
+    assert abs(est_g - est_o) <= 1e-4 * abs(est_o)
+    assert abs(est_g - est_o) < 3.0 * math.sqrt(var_g)
 
 
 def test_estimate_on_benchmark_workload(dk):

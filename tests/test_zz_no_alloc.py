@@ -48,6 +48,10 @@ def _run(ctx, dk, static, level, tag, first, count, seed):
     ("mlmc16_256", 2, [(2, 0, 10, 700, 5), (1, 0, 0, 5000, 6), (2, 1, 3, 300, 7)]),
     # 4^2 grids keep 32 samples per CTA: the static array limits the grid (fewer slots)
     ("paper_reg", 1, [(0, 0, 0, 300000, 8), (1, 0, 0, 50000, 9)]),
+    # the same entry point on a theta-scheme context (Crank--Nicolson weights) ...
+    ("theta16_64", 2, [(2, 0, 0, 600, 10), (1, 0, 4, 900, 11)]),
+    # ... and on the Fourier coupling's ratio-3 hierarchy
+    ("fourier6_54", 2, [(2, 0, 0, 400, 12), (1, 0, 2, 700, 13)]),
 ])
 def test_static_scratch_matches_context_scratch(dk, name, L_max, calls):
     wl = W.get(name).with_(L_max=L_max)
