@@ -119,6 +119,17 @@ typedef struct {
                                coarse Nyquist mode takes its two fine aliases with weight 2^-1/2 each).
                                Fourier: n0 = 6, L_max <= 2 (grids 6^2, 18^2, 54^2), explicit scheme,
                                level n_l = n0 3^l, M_l = M_0 9^l; rho0 / phi arrays on those grids */
+    int32_t state_repr;     /* representation of the fixed-point state (Eq. FullyDiscreteDK is linear apart
+                               from sqrt([rho]^+), so both give the same scheme):
+                               1: absolute, q = rho 2^S_l;
+                               2: fluctuation about the noise-free path, q = (rho - rho-bar^m) 2^S_l, with
+                                  rho-bar^m (m = 0..M_l - 1) kept in a per-level FP32 table on the device and the
+                                  transfers G = rint(c 2^S sqrt([rho-bar^m + q 2^-S]^+) Z); S_l then only has to
+                                  cover 12 standard deviations of the per-cell fluctuation, i.e. many more
+                                  fraction bits at large N.  Explicit NN hierarchies with N > 0 and grids up to
+                                  128^2 (register kernels), tables <= 512 MB; else MLMC_DK_ERR_UNSUPPORTED;
+                               0: automatic -- fluctuation where it is supported and gains at least 3 bits on
+                                  every level, absolute otherwise */
 } mlmc_dk_config;
 
 /* Per-level description returned by mlmc_dk_level_info. */
@@ -148,6 +159,7 @@ typedef struct {
     double theta_b0;        /* its implicit weight b0 */
     int32_t cheb_steps;     /* Chebyshev steps per implicit solve (0: none) */
     int32_t coupling;       /* 0: NN, 1: Fourier (as configured) */
+    int32_t fluct;          /* 1: fluctuation state (frac_bits is then the fluctuation's S_l) */
 } mlmc_dk_level_desc;
 
 /* Host-side moment sums of one quantity on one level (accumulated into). */

@@ -65,6 +65,12 @@ __device__ __forceinline__ float noise_amp(int32_t q, float g) {
     return g * sqrt_approx(__int2float_rn(max(q, 0)));
 }
 
+// The same for a fluctuation state dq = (rho - rho-bar) 2^S: the transfer is
+// g sqrt([rho-bar + dq 2^-S]^+) z with g = c 2^S, rho-bar the noise-free path.
+__device__ __forceinline__ float noise_amp_fluct(int32_t dq, float rbar, float inv_scale, float g) {
+    return g * sqrt_approx(fmaxf(fmaf(__int2float_rn(dq), inv_scale, rbar), 0.f));
+}
+
 // Diffusion flux across one edge: round(a * (q_far - q_near)) with a given as
 // A = round(a 2^32); computed identically by both cells of the edge.
 __device__ __forceinline__ int32_t edge_flux(int32_t A, int32_t d) {

@@ -47,10 +47,13 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kRedW = 2 * kMaxObs + 2;     // reduced values per sample
 constexpr int kMaxStride = 2 + kNSum * 10;  // largest slot stride (4 obs with products)
 
-template <int NF_, int C_, int R_, int CL_, bool COUPLED_>
+template <int NF_, int C_, int R_, int CL_, bool COUPLED_, bool FLUCT_ = false>
 struct Shape {
     static constexpr int NF = NF_, C = C_, R = R_, CL = CL_;
     static constexpr bool COUPLED = COUPLED_;
+    // fluctuation state: q holds (rho - rho-bar^m) 2^S, rho-bar^m read from a
+    // per-step mean-field table (see KArgs::rbf)
+    static constexpr bool FLUCT = FLUCT_;
     static constexpr int NC = NF / 2;
     static constexpr int FR = 2 * R, FC = 2 * C;
     static constexpr int LPB = NC / C;            // lanes per band
@@ -308,6 +311,13 @@ __global__ void __launch_bounds__(S::THREADS) level_kernel(const KArgs a) {
         }
 
         for (int m = 0; m < a.M; ++m) {
+            // fluctuation state: the noise-free path rho-bar^m of this lane's cells
+            float rb[S::FLUCT ? FR : 1][S::FLUCT ? FC : 1];
+            if constexpr (S::FLUCT) {
+#pragma unroll
+                for (int r = 0; r < FR; ++r)
+                    load_row_f<FC>(rb[r], a.rbf + (size_t)m * NF * NF + (size_t)(row0 + r) * NF + col0);
+            }
             // ---- noise: Philox4x32-10 per horizontal cell pair, Box--Muller, transfers
             int32_t G1[FR][FC], G2[FR][FC];
 #pragma unroll
@@ -317,18 +327,24 @@ __global__ void __launch_bounds__(S::THREADS) level_kernel(const KArgs a) {
                     const uint32_t p = static_cast<uint32_t>(((row0 + r) * NF + col0 + 2 * pc) >> 1);
                     const uint4 x = philox10(make_uint4(p, static_cast<uint32_t>(m), c2, c3), a.key0, a.key1);
                     // normals (ra ca, ra sa) and (rb cb, rb sb); the amplitude scales the radius
-                    float ra, ca, sa, rb, cb, sb;
+                    float ra, ca, sa, rb_, cb, sb;
                     box_muller_polar(x.x, x.y, ra, ca, sa);
-                    box_muller_polar(x.z, x.w, rb, cb, sb);
-                    const float ta = noise_amp(q[r][2 * pc], a.gf) * ra;
-                    const float tb = noise_amp(q[r][2 * pc + 1], a.gf) * rb;
+                    box_muller_polar(x.z, x.w, rb_, cb, sb);
+                    float ta, tb;
+                    if constexpr (S::FLUCT) {
+                        ta = noise_amp_fluct(q[r][2 * pc], rb[r][2 * pc], a.isf, a.gf) * ra;
+                        tb = noise_amp_fluct(q[r][2 * pc + 1], rb[r][2 * pc + 1], a.isf, a.gf) * rb_;
+                    } else {
+                        ta = noise_amp(q[r][2 * pc], a.gf) * ra;
+                        tb = noise_amp(q[r][2 * pc + 1], a.gf) * rb_;
+                    }
                     G1[r][2 * pc] = __float2int_rn(ta * ca);
                     G2[r][2 * pc] = __float2int_rn(ta * sa);
                     G1[r][2 * pc + 1] = __float2int_rn(tb * cb);
                     G2[r][2 * pc + 1] = __float2int_rn(tb * sb);
                     if constexpr (CPL) {
-                        zt[r >> 1][pc][0] = fmaf(rb, cb, fmaf(ra, ca, zt[r >> 1][pc][0]));
-                        zt[r >> 1][pc][1] = fmaf(rb, sb, fmaf(ra, sa, zt[r >> 1][pc][1]));
+                        zt[r >> 1][pc][0] = fmaf(rb_, cb, fmaf(ra, ca, zt[r >> 1][pc][0]));
+                        zt[r >> 1][pc][1] = fmaf(rb_, sb, fmaf(ra, sa, zt[r >> 1][pc][1]));
                     }
                 }
             }
@@ -336,11 +352,19 @@ __global__ void __launch_bounds__(S::THREADS) level_kernel(const KArgs a) {
             int32_t Gc1[R][C], Gc2[R][C];
             if constexpr (CPL) {
                 if (cstep) {
+                    float rbc[S::FLUCT ? R : 1][S::FLUCT ? C : 1];
+                    if constexpr (S::FLUCT) {
+#pragma unroll
+                        for (int i = 0; i < R; ++i)
+                            load_row_f<C>(rbc[i], a.rbc + (size_t)(m >> 2) * NC * NC + (size_t)(crow0 + i) * NC + ccol0);
+                    }
 #pragma unroll
                     for (int i = 0; i < R; ++i)
 #pragma unroll
                         for (int j = 0; j < C; ++j) {
-                            const float s = noise_amp(qc[i][j], a.gc);
+                            float s;
+                            if constexpr (S::FLUCT) s = noise_amp_fluct(qc[i][j], rbc[i][j], a.isc, a.gc);
+                            else s = noise_amp(qc[i][j], a.gc);
                             Gc1[i][j] = __float2int_rn(s * zt[i][j][0]);
                             Gc2[i][j] = __float2int_rn(s * zt[i][j][1]);
                             zt[i][j][0] = zt[i][j][1] = 0.f;
@@ -579,8 +603,8 @@ __global__ void __launch_bounds__(S::THREADS) level_kernel(const KArgs a) {
                     o[k] = Df[k];
                     o[a.n_obs + k] = Dc[k];
                 }
-                o[2 * a.n_obs] = v[2 * kMaxObs] * a.dscale_f;
-                o[2 * a.n_obs + 1] = CPL ? v[2 * kMaxObs + 1] * a.dscale_c : 0.0;
+                o[2 * a.n_obs] = v[2 * kMaxObs] * a.dscale_f + a.mass_off_f;
+                o[2 * a.n_obs + 1] = CPL ? v[2 * kMaxObs + 1] * a.dscale_c + a.mass_off_c : 0.0;
             }
         }
     }
@@ -785,40 +809,56 @@ struct VariantEntry {
     cudaError_t (*launch)(bool coupled, const KArgs& a, int n_ctas, cudaStream_t st, int priority);
 };
 
-template <int NF, int C, int R, int CL>
+template <int NF, int C, int R, int CL, bool FL>
 cudaError_t variant_info_fn(bool coupled, int stride, VariantInfo* vi) {
-    return coupled ? Kern<Shape<NF, C, R, CL, true>>::info(stride, vi)
-                   : Kern<Shape<NF, C, R, CL, false>>::info(stride, vi);
+    return coupled ? Kern<Shape<NF, C, R, CL, true, FL>>::info(stride, vi)
+                   : Kern<Shape<NF, C, R, CL, false, FL>>::info(stride, vi);
 }
 
-template <int NF, int C, int R, int CL>
+template <int NF, int C, int R, int CL, bool FL>
 cudaError_t variant_launch_fn(bool coupled, const KArgs& a, int n_ctas, cudaStream_t st, int priority) {
-    return coupled ? Kern<Shape<NF, C, R, CL, true>>::launch(a, n_ctas, st, priority)
-                   : Kern<Shape<NF, C, R, CL, false>>::launch(a, n_ctas, st, priority);
+    return coupled ? Kern<Shape<NF, C, R, CL, true, FL>>::launch(a, n_ctas, st, priority)
+                   : Kern<Shape<NF, C, R, CL, false, FL>>::launch(a, n_ctas, st, priority);
 }
 
-#define DK_ENTRY(NF, C, R, CL) {NF, C, R, CL, variant_info_fn<NF, C, R, CL>, variant_launch_fn<NF, C, R, CL>},
+#define DK_ENTRY(NF, C, R, CL) \
+    {NF, C, R, CL, variant_info_fn<NF, C, R, CL, false>, variant_launch_fn<NF, C, R, CL, false>},
 const VariantEntry kVariants[] = {DK_VARIANTS(DK_ENTRY)};
 #undef DK_ENTRY
-constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+// Fluctuation-state builds: one lane-block shape per grid size up to 128^2
+// (the grids of the high-particle-number hierarchies that need them).
+#define DK_FLUCT_VARIANTS(X) \
+    X(4, 1, 1, 1)            \
+    X(8, 1, 1, 1)            \
+    X(16, 1, 2, 1)           \
+    X(32, 2, 2, 1)           \
+    X(64, 2, 2, 1)           \
+    X(128, 2, 2, 2)
+#define DK_ENTRY(NF, C, R, CL) \
+    {NF, C, R, CL, variant_info_fn<NF, C, R, CL, true>, variant_launch_fn<NF, C, R, CL, true>},
+const VariantEntry kFluctVariants[] = {DK_FLUCT_VARIANTS(DK_ENTRY)};
+#undef DK_ENTRY
 
-const VariantEntry* find_variant(int n, int idx) {
+const VariantEntry* find_variant(int n, int idx, bool fluct) {
+    const VariantEntry* tab = fluct ? kFluctVariants : kVariants;
+    const int count = fluct ? (int)(sizeof(kFluctVariants) / sizeof(kFluctVariants[0]))
+                            : (int)(sizeof(kVariants) / sizeof(kVariants[0]));
     int k = 0;
-    for (int i = 0; i < kNumVariants; ++i)
-        if (kVariants[i].n == n && k++ == idx) return &kVariants[i];
+    for (int i = 0; i < count; ++i)
+        if (tab[i].n == n && k++ == idx) return &tab[i];
     return nullptr;
 }
 }  // namespace
 
-int variant_count(int n) {
+int variant_count(int n, bool fluct) {
     int k = 0;
-    for (int i = 0; i < kNumVariants; ++i) k += kVariants[i].n == n;
+    while (find_variant(n, k, fluct)) ++k;
     return k;
 }
 
-cudaError_t variant_info(int n, bool coupled, int stride, int idx, VariantInfo* out) {
+cudaError_t variant_info(int n, bool coupled, int stride, int idx, VariantInfo* out, bool fluct) {
     *out = VariantInfo{};
-    const VariantEntry* v = find_variant(n, idx);
+    const VariantEntry* v = find_variant(n, idx, fluct);
     if (!v) return cudaSuccess;   // supported = 0
     cudaError_t e = v->info(coupled, stride, out);
     out->C = v->C;
@@ -826,8 +866,9 @@ cudaError_t variant_info(int n, bool coupled, int stride, int idx, VariantInfo* 
     return e;
 }
 
-cudaError_t launch_level(int n, bool coupled, int idx, const KArgs& a, int n_ctas, cudaStream_t st, int priority) {
-    const VariantEntry* v = find_variant(n, idx);
+cudaError_t launch_level(int n, bool coupled, int idx, const KArgs& a, int n_ctas, cudaStream_t st, int priority,
+                         bool fluct) {
+    const VariantEntry* v = find_variant(n, idx, fluct);
     if (!v) return cudaErrorInvalidValue;
     return v->launch(coupled, a, n_ctas, st, priority);
 }

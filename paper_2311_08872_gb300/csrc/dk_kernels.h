@@ -39,6 +39,11 @@ struct KArgs {
     double delta_f[kMaxObs], delta_c[kMaxObs];  // (2^-S qbar - rho-bar^T, phi)_h
     double mscale_f, mscale_c;        // h^2 2^-S for the mass
     long long mass0_f, mass0_c;       // sum of the initial fixed-point states
+    // fluctuation state (kernels built with it only): q = (rho - rho-bar^m) 2^S
+    const float* rbf;                 // fine noise-free path rho-bar^m, [M][n^2] (m = 0 .. M-1)
+    const float* rbc;                 // coarse noise-free path, [M/4][(n/2)^2]
+    float isf, isc;                   // 2^-S of the fine / coarse level
+    double mass_off_f, mass_off_c;    // (rho-bar, 1)_h added to the reported masses (0 for absolute states)
 };
 
 enum : unsigned int { kErrRange = 1u };
@@ -55,19 +60,20 @@ struct VariantInfo {
     int tile_rows;          // streamed kernels: fine rows per CTA tile (0 for the register kernels)
 };
 
-// Number of kernel variants (lane-block shapes / cluster sizes) for fine size n.
-int variant_count(int n);
+// Number of kernel variants (lane-block shapes / cluster sizes) for fine size n;
+// `fluct`: the builds for a fluctuation state (KArgs::rbf).
+int variant_count(int n, bool fluct = false);
 
 // Query (and prepare: attributes, occupancy) variant `idx` for fine size n;
 // supported = 0 when it does not exist.
-cudaError_t variant_info(int n, bool coupled, int slot_stride, int idx, VariantInfo* out);
+cudaError_t variant_info(int n, bool coupled, int slot_stride, int idx, VariantInfo* out, bool fluct = false);
 
 // Launch one batch with variant `idx` on n_ctas CTAs; partials must hold
 // (n_ctas / cluster) * slots_per_cta * slot_stride doubles.
 // `priority` (0: none) is passed as the launch's scheduling priority (lower
 // numbers are more urgent, as for streams).
 cudaError_t launch_level(int n, bool coupled, int idx, const KArgs& a, int n_ctas, cudaStream_t stream,
-                         int priority = 0);
+                         int priority = 0, bool fluct = false);
 
 // Deterministic fixed-order reduction of the per-slot partials into
 // out[slot_stride]: entry 1 is a max, all others sums.

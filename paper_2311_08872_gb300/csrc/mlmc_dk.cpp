@@ -48,6 +48,8 @@ struct LevelTab {
     void* d_stream = nullptr;              // their state
     double* d_spart = nullptr;             // their per-slot partial sums [stride][S]
     int sel[2] = {0, 0};                   // variant in use for each mode
+    float* d_rbar = nullptr;               // fluctuation state: noise-free path rho-bar^m, [M][n^2] FP32
+    double mass_bar = 0.0;                 // fluctuation state: (rho-bar, 1)_h, added to reported masses
     const dk::VariantInfo& vi(bool coupled) const {
         static const dk::VariantInfo none{};
         const auto& v = vis[coupled ? 1 : 0];
@@ -63,6 +65,7 @@ struct mlmc_dk_ctx {
     double b0 = 0;              // implicit weight of Eq. (FullyDiscreteDK)
     int theta = 0;              // every level runs on the theta-scheme kernel
     int coupling = 0;           // 0: Right-Most NN (h ratio 2); 1: Fourier (h ratio 3, Section 3.1)
+    int fluct = 0;              // 1: states are fluctuations about the noise-free path (see mlmc_dk_init)
     dk::TArgs targs{};          // its Chebyshev schedule (per-level fields filled at launch)
     std::vector<LevelTab> lv;
     cudaStream_t stream = nullptr;
@@ -290,6 +293,11 @@ dk::KArgs make_args(mlmc_dk_ctx* c, int level, int stream_tag, bool coupled, int
     a.dscale_f = f.dscale;
     a.mass0_f = f.mass0;
     for (int k = 0; k < dk::kMaxObs; ++k) a.delta_f[k] = f.delta[k];
+    if (c->fluct) {
+        a.rbf = f.d_rbar;
+        a.isf = (float)std::ldexp(1.0, -f.S);
+        a.mass_off_f = f.mass_bar;
+    }
     if (coupled) {
         const LevelTab& g = c->lv[level - 1];
         a.q0c = g.d_q0;
@@ -302,6 +310,11 @@ dk::KArgs make_args(mlmc_dk_ctx* c, int level, int stream_tag, bool coupled, int
         a.dscale_c = g.dscale;
         a.mass0_c = g.mass0;
         for (int k = 0; k < dk::kMaxObs; ++k) a.delta_c[k] = g.delta[k];
+        if (c->fluct) {
+            a.rbc = g.d_rbar;
+            a.isc = (float)std::ldexp(1.0, -g.S);
+            a.mass_off_c = g.mass_bar;
+        }
     }
     return a;
 }
@@ -375,7 +388,7 @@ cudaError_t launch_main(const mlmc_dk_ctx* c, int level, bool coupled, const dk:
         ta.phic64 = coupled ? c->lv[level - 1].d_phi64 : nullptr;
         return dk::launch_theta(t.n, coupled, a, ta, n_ctas, st, priority);
     }
-    return dk::launch_level(t.n, coupled, t.sel[coupled ? 1 : 0], a, n_ctas, st, priority);
+    return dk::launch_level(t.n, coupled, t.sel[coupled ? 1 : 0], a, n_ctas, st, priority, c->fluct != 0);
 }
 
 int launch_batch_into(mlmc_dk_ctx* c, int level, int stream_tag, int64_t first, int64_t count, uint64_t seed,
@@ -473,6 +486,7 @@ void release(mlmc_dk_ctx* c) {
         cudaFree(l.d_P1);
         cudaFree(l.d_stream);
         cudaFree(l.d_spart);
+        cudaFree(l.d_rbar);
     }
     cudaFree(c->d_partials);
     cudaFree(c->d_sums);
@@ -624,6 +638,63 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
     c->next_id[0].assign(cfg->L_max + 1, 0);
     c->next_id[1].assign(cfg->L_max + 1, 0);
 
+    // Fixed-point scales of every level and the choice of state.  An absolute
+    // state q = rho 2^S needs 2^S (twice the initial range plus 12 standard
+    // deviations of the per-cell fluctuation sqrt(rho/(N h^2))) below 2^29, so
+    // |q| stays under the 2^30 range check with a factor 2 to spare.  A
+    // fluctuation state q = (rho - rho-bar^m) 2^S, rho-bar the noise-free path
+    // (the scheme is linear apart from sqrt([rho]^+), so q obeys the same
+    // integer flux form and the noise alone moves it), needs only the 12
+    // deviations: at large N (the paper's N = 2e9) that is many more bits, i.e.
+    // finer resolution of every transfer and flux.
+    std::vector<int> S_abs(cfg->L_max + 1), S_fl(cfg->L_max + 1);
+    bool fl_ok = !fourier && !theta && cfg->N > 0 && cfg->stream_from_n == 0;
+    double table_bytes = 0.0;
+    int min_gain = 1 << 20;
+    for (int l = 0; l <= cfg->L_max; ++l) {
+        const int n = cfg->n0 * (int)std::lround(std::pow((double)ratio, l));
+        const double h = h0 / std::pow((double)ratio, l), tau = tau0 / std::pow((double)(ratio * ratio), l);
+        const long long M = M0 * std::llround(std::pow((double)(ratio * ratio), l));
+        const size_t cells = (size_t)n * n;
+        const double* rho0 = cfg->rho0[l];
+        if (!rho0) { mlmc_dk_free(c); return fail(nullptr, MLMC_DK_ERR_INVALID, "null rho0 level array"); }
+        double rmax = 0;
+        for (size_t i = 0; i < cells; ++i) {
+            if (!std::isfinite(rho0[i])) { mlmc_dk_free(c); return fail(nullptr, MLMC_DK_ERR_INVALID, "non-finite rho0"); }
+            rmax = std::max(rmax, std::fabs(rho0[i]));
+        }
+        const double noise_sd = cfg->N > 0 ? std::sqrt(std::max(rmax, 1e-3) / (cfg->N * h * h)) : 0.0;
+        const double c_noise = cfg->N > 0 ? std::sqrt(tau) / (std::sqrt(cfg->N) * 2.0 * h * h) : 0.0;
+        int S = 29 - (int)std::ceil(std::log2(std::max(2.0 * rmax + 12.0 * noise_sd, 1e-6)));
+        S = std::max(16, std::min(40, S));
+        // keep the noise multiplier g = c 2^(S/2) small enough that |G| stays far below 2^31
+        while (S > 16 && c_noise * std::pow(2.0, 0.5 * S) > 2048.0) --S;
+        if (rmax * std::ldexp(1.0, S) >= std::ldexp(1.0, 30)) {
+            mlmc_dk_free(c);
+            return fail(nullptr, MLMC_DK_ERR_INVALID, "|rho0| too large for the fixed-point range");
+        }
+        S_abs[l] = S;
+        int F = 29 - (int)std::ceil(std::log2(std::max(12.0 * noise_sd, 1e-12)));
+        F = std::max(16, std::min(40, F));
+        // fluctuation transfers G = c 2^F sqrt(rho) z: |G| far below 2^31
+        while (F > 16 && c_noise * std::ldexp(1.0, F) * std::sqrt(std::max(rmax, 1e-3)) > std::ldexp(1.0, 27)) --F;
+        S_fl[l] = F;
+        min_gain = std::min(min_gain, F - S);
+        table_bytes += 4.0 * (double)cells * (double)M;
+        if (dk::variant_count(n, true) == 0) fl_ok = false;
+    }
+    fl_ok = fl_ok && table_bytes <= 512.0 * (1 << 20);
+    if (cfg->state_repr == 2 && !fl_ok) {
+        mlmc_dk_free(c);
+        return fail(nullptr, MLMC_DK_ERR_UNSUPPORTED,
+                    "fluctuation state: explicit NN hierarchy with N > 0, grids up to 128^2, mean-field tables <= 512 MB");
+    }
+    if (cfg->state_repr < 0 || cfg->state_repr > 2) {
+        mlmc_dk_free(c);
+        return fail(nullptr, MLMC_DK_ERR_INVALID, "state_repr must be 0 (automatic), 1 (absolute) or 2 (fluctuation)");
+    }
+    c->fluct = (cfg->state_repr == 2 || (cfg->state_repr == 0 && fl_ok && min_gain >= 3)) ? 1 : 0;
+
     size_t partials_need = 0;
     for (int l = 0; l <= cfg->L_max; ++l) {
         LevelTab& t = c->lv[l];
@@ -633,51 +704,63 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
         t.M = (int)(M0 * std::llround(std::pow((double)(ratio * ratio), l)));
         const size_t cells = (size_t)t.n * t.n;
         const double* rho0 = cfg->rho0[l];
-        if (!rho0) { mlmc_dk_free(c); return fail(nullptr, MLMC_DK_ERR_INVALID, "null rho0 level array"); }
-        double rmax = 0;
-        for (size_t i = 0; i < cells; ++i) {
-            if (!std::isfinite(rho0[i])) { mlmc_dk_free(c); return fail(nullptr, MLMC_DK_ERR_INVALID, "non-finite rho0"); }
-            rmax = std::max(rmax, std::fabs(rho0[i]));
-        }
-        // Fixed-point scale: the largest S with 2^S times (twice the initial range
-        // plus 12 standard deviations of the per-cell fluctuation sqrt(rho/(N h^2)))
-        // below 2^29, so |q| stays under the 2^30 range check with a factor 2 to
-        // spare; a larger S resolves the noise transfers and diffusion fluxes
-        // more finely.
-        const double noise_sd = cfg->N > 0 ? std::sqrt(std::max(rmax, 1e-3) / (cfg->N * t.h * t.h)) : 0.0;
-        const double range = std::max(2.0 * rmax + 12.0 * noise_sd, 1e-6);
-        int S = 29 - (int)std::ceil(std::log2(range));
-        S = std::max(16, std::min(40, S));
         const double c_noise = cfg->N > 0 ? std::sqrt(t.tau) / (std::sqrt(cfg->N) * 2.0 * t.h * t.h) : 0.0;
-        // keep the noise multiplier g = c 2^(S/2) small enough that |G| stays far below 2^31
-        while (S > 16 && c_noise * std::pow(2.0, 0.5 * S) > 2048.0) --S;
-        if (rmax * std::ldexp(1.0, S) >= std::ldexp(1.0, 30)) {
-            mlmc_dk_free(c);
-            return fail(nullptr, MLMC_DK_ERR_INVALID, "|rho0| too large for the fixed-point range");
-        }
+        const int S = c->fluct ? S_fl[l] : S_abs[l];
         t.S = S;
         t.A64 = std::llround(t.tau / (2.0 * t.h * t.h) * 4294967296.0);
         t.A = t.A64 < (1LL << 31) ? (int32_t)t.A64 : 0;
-        t.g = (float)(c_noise * std::pow(2.0, 0.5 * S));
+        // absolute state: G = rint(c 2^S sqrt(q 2^-S) z) = rint(c 2^(S/2) sqrt(q) z);
+        // fluctuation state: G = rint(c 2^S sqrt(rho-bar + q 2^-S) z)
+        t.g = (float)(c_noise * (c->fluct ? std::ldexp(1.0, S) : std::pow(2.0, 0.5 * S)));
         t.dscale = t.h * t.h * std::ldexp(1.0, -S);
 
         std::vector<int32_t> q0(cells), qb(cells);
         std::vector<double> rbar(cells);
         long long mass = 0;
+        double mass_bar = 0.0;
         for (size_t i = 0; i < cells; ++i) {
-            q0[i] = (int32_t)std::llrint(std::ldexp(rho0[i], S));
+            q0[i] = c->fluct ? 0 : (int32_t)std::llrint(std::ldexp(rho0[i], S));
             mass += q0[i];
+            mass_bar += rho0[i];
         }
         t.mass0 = mass;
+        t.mass_bar = c->fluct ? t.h * t.h * mass_bar : 0.0;
         mean_field_any(t.n, t.h, t.tau, t.M, rho0, rbar.data(), b0);
-        for (size_t i = 0; i < cells; ++i) qb[i] = (int32_t)std::llrint(std::ldexp(rbar[i], S));
+        for (size_t i = 0; i < cells; ++i) qb[i] = c->fluct ? 0 : (int32_t)std::llrint(std::ldexp(rbar[i], S));
+        if (c->fluct) {
+            // the noise-free path rho-bar^m, m = 0 .. M-1, by the explicit step in
+            // FP64, stored in FP32 for the transfers' amplitudes
+            std::vector<float> tab(cells * (size_t)t.M);
+            std::vector<double> cur(rho0, rho0 + cells), nxt(cells);
+            const double a = t.tau / (2.0 * t.h * t.h);
+            const int n = t.n;
+            for (int m = 0; m < t.M; ++m) {
+                for (size_t i = 0; i < cells; ++i) tab[(size_t)m * cells + i] = (float)cur[i];
+                for (int i1 = 0; i1 < n; ++i1)
+                    for (int i2 = 0; i2 < n; ++i2) {
+                        const double x = cur[(size_t)i1 * n + i2];
+                        const double nb = cur[(size_t)((i1 + 1) % n) * n + i2] + cur[(size_t)((i1 + n - 1) % n) * n + i2] +
+                                          cur[(size_t)i1 * n + (i2 + 1) % n] + cur[(size_t)i1 * n + (i2 + n - 1) % n];
+                        nxt[(size_t)i1 * n + i2] = x + a * (nb - 4.0 * x);
+                    }
+                cur.swap(nxt);
+            }
+            if ((e = cudaMalloc(&t.d_rbar, sizeof(float) * tab.size())) != cudaSuccess ||
+                (e = cudaMemcpy(t.d_rbar, tab.data(), sizeof(float) * tab.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
+                mlmc_dk_free(c);
+                return cuda_fail(nullptr, e, "noise-free path tables");
+            }
+            c->h2d_bytes += (int64_t)(sizeof(float) * tab.size());
+        }
         // The quantised initial state q0 2^-S differs from rho0 by e0 (at most half
         // a quantum per cell); the scheme is linear apart from sqrt([rho]^+), so e0
         // reaches T as the noise-free evolution of e0 (exact, FP64 by FFT) and is
         // removed from the observables with the mean-field offset below.
-        std::vector<double> e0(cells), e0T(cells);
-        for (size_t i = 0; i < cells; ++i) e0[i] = std::ldexp((double)q0[i], -S) - rho0[i];
-        mean_field_any(t.n, t.h, t.tau, t.M, e0.data(), e0T.data(), b0);
+        std::vector<double> e0(cells, 0.0), e0T(cells, 0.0);
+        if (!c->fluct) {
+            for (size_t i = 0; i < cells; ++i) e0[i] = std::ldexp((double)q0[i], -S) - rho0[i];
+            mean_field_any(t.n, t.h, t.tau, t.M, e0.data(), e0T.data(), b0);
+        }
         std::vector<float> phif(cells * c->n_obs);
         for (int k = 0; k < c->n_obs; ++k) {
             const double* ph = cfg->phi[(size_t)l * c->n_obs + k];
@@ -685,7 +768,7 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
             double yb = 0, dl = 0;
             for (size_t i = 0; i < cells; ++i) {
                 yb += rbar[i] * ph[i];
-                dl += (std::ldexp((double)qb[i], -S) - rbar[i] - e0T[i]) * ph[i];
+                if (!c->fluct) dl += (std::ldexp((double)qb[i], -S) - rbar[i] - e0T[i]) * ph[i];
                 phif[(size_t)k * cells + i] = (float)ph[i];
             }
             t.ybar[k] = t.h * t.h * yb;
@@ -780,7 +863,7 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
             continue;
         }
         const bool force_stream = cfg->stream_from_n > 0 && t.n >= cfg->stream_from_n && t.n % 64 == 0;
-        const int nv = force_stream ? 0 : dk::variant_count(t.n);
+        const int nv = force_stream ? 0 : dk::variant_count(t.n, c->fluct != 0);
         if (nv == 0) {
             // no register-resident variant: stream the state through global memory,
             // samples in flight within a 96 MB working set (L2-resident)
@@ -814,7 +897,7 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
             if (mode == 1 && l == 0) continue;
             for (int v = 0; v < nv; ++v) {
                 dk::VariantInfo vi{};
-                if ((e = dk::variant_info(t.n, mode == 1, c->stride, v, &vi)) != cudaSuccess) {
+                if ((e = dk::variant_info(t.n, mode == 1, c->stride, v, &vi, c->fluct != 0)) != cudaSuccess) {
                     mlmc_dk_free(c);
                     return cuda_fail(nullptr, e, "kernel variant setup");
                 }
@@ -823,7 +906,7 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
                     partials_need = std::max(partials_need, (size_t)(vi.max_ctas / vi.cluster) * vi.slots_per_cta * c->stride);
             }
         }
-        if (!t.streamed && t.n >= 256 && t.n % 64 == 0) {
+        if (!t.streamed && !c->fluct && t.n >= 256 && t.n % 64 == 0) {
             // register level with 8-SM clusters: streamed buffers for a batch split
             t.inflight_v[0] = dk::stream_inflight(t.n, (size_t)96 << 20, 0);
             t.inflight = t.inflight_v[0];
@@ -931,6 +1014,7 @@ int mlmc_dk_level_info(const mlmc_dk_ctx* ctx, int32_t level, mlmc_dk_level_desc
     out->theta_b0 = ctx->b0;
     out->cheb_steps = ctx->theta ? ctx->targs.K : 0;
     out->coupling = ctx->coupling;
+    out->fluct = ctx->fluct;
     return MLMC_DK_OK;
 }
 

@@ -46,6 +46,7 @@ class Config(ctypes.Structure):
         ("theta_b0", ctypes.c_double),
         ("theta_kernel", ctypes.c_int32),
         ("coupling", ctypes.c_int32),
+        ("state_repr", ctypes.c_int32),
     ]
 
 
@@ -61,7 +62,7 @@ class LevelDesc(ctypes.Structure):
         ("streamed", ctypes.c_int32), ("in_flight", ctypes.c_int32), ("tile_rows", ctypes.c_int32),
         ("split_capable", ctypes.c_int32), ("split_fraction", ctypes.c_double), ("batch_streamed", ctypes.c_int64),
         ("theta", ctypes.c_int32), ("theta_b0", ctypes.c_double), ("cheb_steps", ctypes.c_int32),
-        ("coupling", ctypes.c_int32),
+        ("coupling", ctypes.c_int32), ("fluct", ctypes.c_int32),
     ]
 
 
@@ -229,7 +230,8 @@ class Context:
     def __init__(self, length: float, n0: int, L_max: int, T: float, mu: float, N: float,
                  rho0: List[np.ndarray], phi: List[List[np.ndarray]], products: bool = False,
                  M0: int = 0, pilot: int = 0, L_start: int = 0, stream: Optional[int] = None,
-                 stream_from_n: int = 0, theta_b0: float = 0.0, theta_kernel: bool = False, coupling: int = 0):
+                 stream_from_n: int = 0, theta_b0: float = 0.0, theta_kernel: bool = False, coupling: int = 0,
+                 state_repr: int = 0):
         self._ctx = None
         self._rho0 = [_f64(r).reshape(-1) for r in rho0]
         self.n_obs = len(phi[0])
@@ -238,7 +240,7 @@ class Context:
         phi_ptrs = (_dp * len(self._phi))(*[p.ctypes.data_as(_dp) for p in self._phi])
         self.cfg = Config(length, n0, L_max, T, mu, M0, N, rho_ptrs, self.n_obs, phi_ptrs,
                           int(products), pilot, L_start, stream, stream_from_n, float(theta_b0),
-                          int(theta_kernel), int(coupling))
+                          int(theta_kernel), int(coupling), int(state_repr))
         h = ctypes.c_void_p()
         _check(lib().mlmc_dk_init(ctypes.byref(self.cfg), ctypes.byref(h)))
         self._ctx = h

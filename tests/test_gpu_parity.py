@@ -97,8 +97,8 @@ def conditioning(wl, level, stream_tag, first, count, seed, amp, repeats=3):
     return rms(df), (rms(dc) if coupled else None)
 
 
-def check_level(dk, wl, level, stream_tag, first, count, seed, processes=1, conditioned=False):
-    ctx = dk.Context.from_workload(wl)
+def check_level(dk, wl, level, stream_tag, first, count, seed, processes=1, conditioned=False, **ctx_kw):
+    ctx = dk.Context.from_workload(wl, **ctx_kw)
     try:
         info = ctx.level_info(level)
         sums, samp = gpu_samples(ctx, dk, level, stream_tag, first, count, seed)
@@ -185,6 +185,39 @@ def test_tiny_grids_paper_setting(dk):
     check_level(dk, wl, 0, 0, 0, 64, seed=5)
     check_level(dk, wl, 1, 0, 0, 64, seed=5)
     check_level(dk, wl, 2, 0, 0, 32, seed=5)
+
+
+@pytest.mark.parametrize("name", ["paper_reg", "paper_irreg"])
+def test_paper_setting_main_particle_number(dk, name):
+    """The paper's Section 7.2 setting at its main particle number N = 2e9
+    (Table tab_9_s): the fluctuation Y - Ybar is ~N^-1/2 small, and the state
+    held as its fluctuation about the noise-free path (chosen automatically)
+    meets the unrelaxed per-sample bar on levels 2..5 (16^2 .. 128^2)."""
+    wl = W.get(name)
+    ctx = dk.Context.from_workload(wl)
+    try:
+        assert all(ctx.level_info(l).fluct == 1 for l in range(wl.L_max + 1))
+    finally:
+        ctx.close()
+    worst = 0.0
+    for level in (2, 3, 4, 5):
+        worst = max(worst, check_level(dk, wl, level, 0, 0, 8, seed=wl.seed, processes=8))
+    print(name, "N = 2e9 worst error / bound", worst)
+
+
+def test_fluctuation_and_absolute_states_agree(dk):
+    """Both representations run the same scheme: at a particle number where
+    either resolves the fluctuation, both meet the per-sample bar against the
+    oracle on the same samples (and the automatic choice is the absolute one)."""
+    wl = W.get("paper_reg").with_(N=2e6, L_max=3)
+    for repr_ in (1, 2):
+        check_level(dk, wl, 3, 0, 0, 16, seed=3, processes=4, state_repr=repr_)
+        check_level(dk, wl, 2, 1, 5, 16, seed=3, state_repr=repr_)
+    with dk.Context.from_workload(W.get("mlmc16_256")) as ctx:
+        assert ctx.level_info(0).fluct == 0
+    with pytest.raises(dk.MLMCError) as e:
+        dk.Context.from_workload(W.get("mlmc16_256"), state_repr=2)
+    assert e.value.code == dk.ERR_UNSUPPORTED
 
 
 def test_low_density_gaussian(dk):
