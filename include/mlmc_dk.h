@@ -78,6 +78,7 @@ extern "C" {
 #define MLMC_DK_ERR_RANGE (-3)       /* |rho| reached 2^(30-S_l): the level's fixed-point range */
 #define MLMC_DK_ERR_UNSUPPORTED (-4) /* grid size without a kernel variant */
 #define MLMC_DK_ERR_STATE (-5)       /* checkpoint buffer does not match */
+#define MLMC_DK_ERR_TIMEOUT (-6)     /* a band kernel's bounded wait for a neighbouring CTA gave up */
 
 #define MLMC_DK_MAX_LEVELS 16
 #define MLMC_DK_MAX_OBS 4
@@ -160,6 +161,10 @@ typedef struct {
     int32_t cheb_steps;     /* Chebyshev steps per implicit solve (0: none) */
     int32_t coupling;       /* 0: NN, 1: Fourier (as configured) */
     int32_t fluct;          /* 1: fluctuation state (frac_bits is then the fluctuation's S_l) */
+    int32_t band;           /* 1: the level's kernel in use spreads each sample over `bands` CTAs (full-width
+                               bands of coarse rows in registers, band edges exchanged through global memory;
+                               in_flight samples per launch) */
+    int32_t bands;
 } mlmc_dk_level_desc;
 
 /* Host-side moment sums of one quantity on one level (accumulated into). */

@@ -46,7 +46,7 @@ struct KArgs {
     double mass_off_f, mass_off_c;    // (rho-bar, 1)_h added to the reported masses (0 for absolute states)
 };
 
-enum : unsigned int { kErrRange = 1u };
+enum : unsigned int { kErrRange = 1u, kErrTimeout = 2u };
 
 // Static facts about the kernel variant used for a grid size.
 struct VariantInfo {
@@ -58,6 +58,8 @@ struct VariantInfo {
     int max_ctas;           // resident CTAs on the whole GPU
     int C, R;               // lane block: C x R coarse cells (2R x 2C fine)
     int tile_rows;          // streamed kernels: fine rows per CTA tile (0 for the register kernels)
+    int band;               // 1: the band kernel (a sample over several CTAs, cooperative launch)
+    int bands;              // band kernel: bands (CTAs) per sample
 };
 
 // Number of kernel variants (lane-block shapes / cluster sizes) for fine size n;
@@ -115,6 +117,37 @@ void stream_carve(SArgs* a, void* buf, int n, int S);
 // to k.partials ([k.slot_stride][S], zeroed here), per-sample outputs to
 // k.samples; the caller reduces the S slots.
 cudaError_t stream_run(const KArgs& k, SArgs a, int S, int variant, cudaStream_t stream);
+
+// ---- band kernels (grids 128 .. 1024): a sample over several CTAs, each a
+// full-width band of coarse rows held in registers; band edges through global
+// memory with per-step counters; cooperative launch
+struct BArgs {
+    int n, coupled;
+    int nb, bmax, S;             // bands per sample, coarse rows of the tallest band, samples in flight
+    int steps;                   // fine steps (the level's M, fewer only to time variants)
+    int count;                   // samples in this wave (<= S)
+    long long sid0;              // sample id of the wave's first sample
+    unsigned* flags;             // [S][nb][2]: published top / bottom edges (zeroed before every wave)
+    int2* edge;                  // [S][nb][2 side][2 parity][n]: (q, G1) of the top / bottom fine row
+    int2* cedge;                 // [S][nb][2 side][n/2]: (qc, Gc1) of the top / bottom coarse row
+    double* band_part;           // [S][nb][2 kMaxObs + 2]: per-band observable partials
+    const double* phif64;        // FP64 test functions [n_obs][n^2] / [n_obs][(n/2)^2]
+    const double* phic64;
+};
+struct BandPlan {
+    int supported;
+    int nb, bmax, S, threads;
+    size_t smem;
+};
+bool band_supported(int n);
+// Launch shape of the band kernel for n x n on this device (see dk_band.cu).
+cudaError_t band_plan(int n, bool coupled, BandPlan* out);
+// Device bytes of the exchange buffers for `p`, and their layout.
+size_t band_bytes(int n, const BandPlan& p);
+void band_carve(BArgs* b, void* buf, int n, const BandPlan& p);
+// Run k.count samples (ids k.first..) in waves of p.S: per-slot moment sums go
+// to k.partials ([k.slot_stride][p.S], zeroed here); the caller reduces the slots.
+cudaError_t band_run(const KArgs& k, BArgs b, const BandPlan& p, cudaStream_t stream);
 
 // ---- theta-scheme (implicit diffusion weight b0 > 0), grids up to 64 x 64
 constexpr int kMaxCheb = 64;   // largest number of Chebyshev steps per solve

@@ -48,6 +48,9 @@ struct LevelTab {
     void* d_stream = nullptr;              // their state
     double* d_spart = nullptr;             // their per-slot partial sums [stride][S]
     int sel[2] = {0, 0};                   // variant in use for each mode
+    dk::BandPlan bplan[2] = {};            // band kernel launch shape per mode (fine only, coupled)
+    void* d_band = nullptr;                // its exchange buffers
+    double* d_bpart = nullptr;             // its per-slot partial sums [stride][S]
     float* d_rbar = nullptr;               // fluctuation state: noise-free path rho-bar^m, [M][n^2] FP32
     double mass_bar = 0.0;                 // fluctuation state: (rho-bar, 1)_h, added to reported masses
     const dk::VariantInfo& vi(bool coupled) const {
@@ -368,6 +371,34 @@ int launch_streamed(mlmc_dk_ctx* c, int level, int stream_tag, int64_t first, in
     return MLMC_DK_OK;
 }
 
+// Band-kernel level: each sample over t.bplan[mode].nb CTAs; `steps` > 0
+// truncates every sample to that many fine steps (used only to time variants).
+int launch_band(mlmc_dk_ctx* c, int level, int stream_tag, int64_t first, int64_t count, uint64_t seed,
+                double* sums_dev, double* samples_dev, cudaStream_t st, int steps = 0) {
+    const bool coupled = (stream_tag == 0) && level > 0;
+    LevelTab& t = c->lv[level];
+    const dk::BandPlan& p = t.bplan[coupled ? 1 : 0];
+    cudaError_t e;
+    if (count == 0) {
+        e = cudaMemsetAsync(sums_dev, 0, sizeof(double) * c->stride, st);
+        return e == cudaSuccess ? MLMC_DK_OK : cuda_fail(c, e, "cudaMemsetAsync");
+    }
+    if (!p.supported || !t.d_band) return fail(c, MLMC_DK_ERR_UNSUPPORTED, "no band kernel for this level");
+    dk::KArgs k = make_args(c, level, stream_tag, coupled, first, count, seed, samples_dev);
+    k.partials = t.d_bpart;
+    dk::BArgs b{};
+    dk::band_carve(&b, t.d_band, t.n, p);
+    b.n = t.n;
+    b.coupled = coupled ? 1 : 0;
+    b.steps = steps > 0 ? std::min(steps, t.M) : t.M;
+    b.phif64 = t.d_phi64;
+    b.phic64 = coupled ? c->lv[level - 1].d_phi64 : nullptr;
+    if ((e = dk::band_run(k, b, p, st)) != cudaSuccess) return cuda_fail(c, e, "band kernel");
+    if ((e = dk::launch_reduce(t.d_bpart, p.S, c->stride, sums_dev, st)) != cudaSuccess)
+        return cuda_fail(c, e, "reduce kernel launch");
+    return MLMC_DK_OK;
+}
+
 // The level's sample kernel: the theta-scheme kernel on a theta context, the
 // register-resident kernel variant in use otherwise.
 cudaError_t launch_main(const mlmc_dk_ctx* c, int level, bool coupled, const dk::KArgs& a, int n_ctas,
@@ -394,9 +425,11 @@ cudaError_t launch_main(const mlmc_dk_ctx* c, int level, bool coupled, const dk:
 int launch_batch_into(mlmc_dk_ctx* c, int level, int stream_tag, int64_t first, int64_t count, uint64_t seed,
                       double* sums_dev, double* samples_dev, cudaStream_t st, double* partials, size_t cap,
                       int priority) {
+    const bool coupled = (stream_tag == 0) && level > 0;
+    if (c->lv[level].vi(coupled).band)
+        return launch_band(c, level, stream_tag, first, count, seed, sums_dev, samples_dev, st);
     if (c->lv[level].streamed)
         return launch_streamed(c, level, stream_tag, first, count, seed, sums_dev, samples_dev, st);
-    const bool coupled = (stream_tag == 0) && level > 0;
     const dk::VariantInfo& vi = c->lv[level].vi(coupled);
     if (!vi.supported)
         return fail(c, MLMC_DK_ERR_UNSUPPORTED, "no kernel variant for n = " + std::to_string(c->lv[level].n));
@@ -425,6 +458,10 @@ int check_device_error(mlmc_dk_ctx* c) {
     cudaError_t e = cudaMemcpyAsync(c->h_err, c->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "device error word");
+    if (*c->h_err & dk::kErrTimeout) {
+        cudaMemsetAsync(c->d_err, 0, sizeof(unsigned), c->stream);
+        return fail(c, MLMC_DK_ERR_TIMEOUT, "a band kernel's bounded wait for a neighbouring CTA gave up");
+    }
     if (*c->h_err & dk::kErrRange) {
         cudaMemsetAsync(c->d_err, 0, sizeof(unsigned), c->stream);
         return fail(c, MLMC_DK_ERR_RANGE, "fixed-point range exceeded (|rho| too large for this level's scale)");
@@ -487,6 +524,8 @@ void release(mlmc_dk_ctx* c) {
         cudaFree(l.d_stream);
         cudaFree(l.d_spart);
         cudaFree(l.d_rbar);
+        cudaFree(l.d_band);
+        cudaFree(l.d_bpart);
     }
     cudaFree(c->d_partials);
     cudaFree(c->d_sums);
@@ -906,6 +945,48 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
                     partials_need = std::max(partials_need, (size_t)(vi.max_ctas / vi.cluster) * vi.slots_per_cta * c->stride);
             }
         }
+        if (!c->fluct && !force_stream && dk::band_supported(t.n)) {
+            // band kernel: a sample over several CTAs; the default on streamed
+            // levels, a tuner candidate on register levels
+            size_t bytes = 0;
+            int S_max = 0;
+            bool ok = true;
+            for (int mode = 0; mode < 2; ++mode) {
+                if (mode == 1 && l == 0) continue;
+                if ((e = dk::band_plan(t.n, mode == 1, &t.bplan[mode])) != cudaSuccess) {
+                    mlmc_dk_free(c);
+                    return cuda_fail(nullptr, e, "band kernel setup");
+                }
+                ok = ok && t.bplan[mode].supported;
+                if (!t.bplan[mode].supported) continue;
+                bytes = std::max(bytes, dk::band_bytes(t.n, t.bplan[mode]));
+                S_max = std::max(S_max, t.bplan[mode].S);
+            }
+            if (ok) {
+                if ((e = cudaMalloc(&t.d_band, bytes)) != cudaSuccess ||
+                    (e = cudaMalloc(&t.d_bpart, sizeof(double) * c->stride * S_max)) != cudaSuccess) {
+                    mlmc_dk_free(c);
+                    return cuda_fail(nullptr, e, "band kernel buffers");
+                }
+                for (int mode = 0; mode < 2; ++mode) {
+                    if (mode == 1 && l == 0) continue;
+                    const dk::BandPlan& p = t.bplan[mode];
+                    dk::VariantInfo vi{};
+                    vi.supported = 1;
+                    vi.band = 1;
+                    vi.bands = p.nb;
+                    vi.threads = p.threads;
+                    vi.cluster = 1;
+                    vi.slots_per_cta = 0;
+                    vi.smem = p.smem;
+                    vi.max_ctas = p.S * p.nb;
+                    vi.C = 2;
+                    vi.R = 1;
+                    t.vis[mode].push_back(vi);
+                    if (t.streamed) t.sel[mode] = (int)t.vis[mode].size() - 1;
+                }
+            }
+        }
         if (!t.streamed && !c->fluct && t.n >= 256 && t.n % 64 == 0) {
             // register level with 8-SM clusters: streamed buffers for a batch split
             t.inflight_v[0] = dk::stream_inflight(t.n, (size_t)96 << 20, 0);
@@ -1015,6 +1096,9 @@ int mlmc_dk_level_info(const mlmc_dk_ctx* ctx, int32_t level, mlmc_dk_level_desc
     out->cheb_steps = ctx->theta ? ctx->targs.K : 0;
     out->coupling = ctx->coupling;
     out->fluct = ctx->fluct;
+    out->band = vs.band;
+    out->bands = vs.bands;
+    if (vs.band) out->in_flight = t.bplan[level > 0 ? 1 : 0].S;
     return MLMC_DK_OK;
 }
 
@@ -1048,7 +1132,7 @@ int mlmc_dk_run_level_static(const mlmc_dk_ctx* ctx, int32_t level, int32_t stre
         return fail(c, MLMC_DK_ERR_INVALID, "run_level_static: bad arguments");
     const bool coupled = (stream_tag == 0) && level > 0;
     const dk::VariantInfo& vi = ctx->lv[level].vi(coupled);
-    if (!vi.supported || ctx->lv[level].streamed)
+    if (!vi.supported || ctx->lv[level].streamed || vi.band)
         return fail(c, MLMC_DK_ERR_UNSUPPORTED, "no register-resident kernel for n = " + std::to_string(ctx->lv[level].n));
     cudaStream_t st = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : ctx->stream;
     cudaError_t e;
@@ -1096,10 +1180,13 @@ int batch_dev(mlmc_dk_ctx* ctx, const int64_t* counts, const int64_t* firsts, ui
     // split: the last n_split[l] ids of a split level run streamed beside the graph
     std::vector<int64_t> n_split(nl, 0), n_reg(counts, counts + nl);
     bool any_split = false;
+    // levels whose kernel runs many launches (streamed state) or a cooperative
+    // grid (band kernel) run beside the graph, not inside it
+    auto outside = [&](int l) { return ctx->lv[l].streamed || ctx->lv[l].vi(l > 0).band; };
     for (int l = 0; l < nl; ++l) {
         LevelTab& t = ctx->lv[l];
         t.batch_streamed = 0;
-        if (t.split_ok && t.split_frac > 0 && l > 0 && counts[l] > 1) {
+        if (t.split_ok && t.split_frac > 0 && l > 0 && counts[l] > 1 && !outside(l)) {
             n_split[l] = std::min<int64_t>(counts[l] - 1, (int64_t)std::floor(t.split_frac * (double)counts[l]));
             n_reg[l] = counts[l] - n_split[l];
             t.batch_streamed = n_split[l];
@@ -1112,7 +1199,7 @@ int batch_dev(mlmc_dk_ctx* ctx, const int64_t* counts, const int64_t* firsts, ui
     e = cudaEventRecord(ctx->ev_fork, ctx->cap_stream);
     // finest level first: its clusters are placed before the coarser levels fill the remaining SMs
     for (int l = nl - 1; l >= 0 && e == cudaSuccess && rc == MLMC_DK_OK; --l) {
-        if (ctx->lv[l].streamed) continue;   // thousands of launches: run after the graph
+        if (outside(l)) continue;
         double* out = sums_dev + (size_t)l * ctx->stride;
         if ((e = cudaStreamWaitEvent(ctx->lstream[l], ctx->ev_fork, 0)) != cudaSuccess) break;
         // external records become event-record nodes of the graph (timing)
@@ -1158,7 +1245,30 @@ int batch_dev(mlmc_dk_ctx* ctx, const int64_t* counts, const int64_t* firsts, ui
             (e = cudaStreamWaitEvent(ctx->sstream, ctx->ev_sfork, 0)) != cudaSuccess)
             return cuda_fail(ctx, e, "batch split fork");
     }
+    // band-kernel levels first, each on its level's stream: their cooperative
+    // grids are placed before the graph's kernels fill the remaining SMs
+    bool any_band = false;
+    for (int l = nl - 1; l >= 0; --l) {
+        if (!outside(l) || ctx->lv[l].streamed) continue;
+        if (!any_band) {
+            if ((e = cudaEventRecord(ctx->ev_fork, st)) != cudaSuccess) return cuda_fail(ctx, e, "band fork");
+            any_band = true;
+        }
+        if ((e = cudaStreamWaitEvent(ctx->lstream[l], ctx->ev_fork, 0)) != cudaSuccess ||
+            (e = cudaEventRecord(ctx->ev_lb[l], ctx->lstream[l])) != cudaSuccess)
+            return cuda_fail(ctx, e, "band fork");
+        rc = launch_batch_into(ctx, l, 0, firsts[l], counts[l], seed, sums_dev + (size_t)l * ctx->stride, nullptr,
+                               ctx->lstream[l], nullptr, 0, 0);
+        if (rc != MLMC_DK_OK) return rc;
+        if ((e = cudaEventRecord(ctx->ev_le[l], ctx->lstream[l])) != cudaSuccess ||
+            (e = cudaEventRecord(ctx->ev_join[l], ctx->lstream[l])) != cudaSuccess)
+            return cuda_fail(ctx, e, "band join");
+    }
     if ((e = cudaGraphLaunch(ctx->gexec, st)) != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphLaunch");
+    for (int l = nl - 1; l >= 0 && any_band; --l) {
+        if (!outside(l) || ctx->lv[l].streamed) continue;
+        if ((e = cudaStreamWaitEvent(st, ctx->ev_join[l], 0)) != cudaSuccess) return cuda_fail(ctx, e, "band join");
+    }
     if (any_split) {
         for (int l = nl - 1; l >= 0; --l) {
             if (n_split[l] == 0) continue;
@@ -1176,7 +1286,7 @@ int batch_dev(mlmc_dk_ctx* ctx, const int64_t* counts, const int64_t* firsts, ui
                 return cuda_fail(ctx, e, "batch split merge");
     }
     for (int l = nl - 1; l >= 0; --l) {
-        if (!ctx->lv[l].streamed) continue;
+        if (!ctx->lv[l].streamed || ctx->lv[l].vi(l > 0).band) continue;
         if ((e = cudaEventRecord(ctx->ev_lb[l], st)) != cudaSuccess) return cuda_fail(ctx, e, "cudaEventRecord");
         rc = launch_streamed(ctx, l, 0, firsts[l], counts[l], seed, sums_dev + (size_t)l * ctx->stride, nullptr, st);
         if (rc != MLMC_DK_OK) return rc;
@@ -1338,16 +1448,28 @@ int mlmc_dk_tune(mlmc_dk_ctx* ctx, int32_t repeats, double* seconds) {
                 const dk::VariantInfo& vi = t.vis[mode][v];
                 if (!vi.supported) continue;
                 t.sel[mode] = v;
-                // two full waves of resident sample slots; streamed levels: one wave
-                // of samples in flight over a short horizon
-                const int64_t count = t.streamed ? t.inflight_v[v] : 2LL * (vi.max_ctas / vi.cluster) * vi.slots_per_cta;
+                // register kernels: two full waves of resident sample slots; streamed
+                // and band kernels: one wave of samples in flight over a shorter
+                // horizon; compared per sample and fine step
+                int steps = t.M;
+                int64_t count;
+                if (vi.band) {
+                    count = t.bplan[mode].S;
+                    steps = std::min(t.M, 1024);
+                } else if (t.streamed) {
+                    count = t.inflight_v[v];
+                    steps = std::min(t.M, 64);
+                } else {
+                    count = 2LL * (vi.max_ctas / vi.cluster) * vi.slots_per_cta;
+                }
                 double ms_min = 1e300;
                 for (int r = 0; r < repeats + 1; ++r) {
                     if ((e = cudaEventRecord(ctx->ev0, ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "tune");
                     const int tag = mode == 1 ? 0 : 1;
-                    int rc = t.streamed ? launch_streamed(ctx, l, tag, 0, count, 0x7475, ctx->d_sums, nullptr, ctx->stream,
-                                                          std::min(t.M, 64))
-                                        : launch_batch(ctx, l, tag, 0, count, 0x7475, ctx->d_sums, nullptr, ctx->stream);
+                    int rc = vi.band ? launch_band(ctx, l, tag, 0, count, 0x7475, ctx->d_sums, nullptr, ctx->stream, steps)
+                             : t.streamed ? launch_streamed(ctx, l, tag, 0, count, 0x7475, ctx->d_sums, nullptr, ctx->stream,
+                                                            steps)
+                                          : launch_batch(ctx, l, tag, 0, count, 0x7475, ctx->d_sums, nullptr, ctx->stream);
                     if (rc != MLMC_DK_OK) return rc;
                     if ((e = cudaEventRecord(ctx->ev1, ctx->stream)) != cudaSuccess ||
                         (e = cudaEventSynchronize(ctx->ev1)) != cudaSuccess)
@@ -1356,7 +1478,7 @@ int mlmc_dk_tune(mlmc_dk_ctx* ctx, int32_t repeats, double* seconds) {
                     cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
                     if (r > 0) ms_min = std::min(ms_min, (double)ms);   // the first run warms up
                 }
-                const double per_sample = ms_min / (double)count;
+                const double per_sample = ms_min / ((double)count * (double)steps);
                 if (per_sample < best) {
                     best = per_sample;
                     best_v = v;

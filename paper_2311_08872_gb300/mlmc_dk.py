@@ -21,7 +21,7 @@ MAX_QUANT = 10
 NSUM = 12
 
 OK, NOT_CONVERGED = 0, 1
-ERR_INVALID, ERR_CUDA, ERR_RANGE, ERR_UNSUPPORTED, ERR_STATE = -1, -2, -3, -4, -5
+ERR_INVALID, ERR_CUDA, ERR_RANGE, ERR_UNSUPPORTED, ERR_STATE, ERR_TIMEOUT = -1, -2, -3, -4, -5, -6
 
 _dp = ctypes.POINTER(ctypes.c_double)
 
@@ -62,7 +62,8 @@ class LevelDesc(ctypes.Structure):
         ("streamed", ctypes.c_int32), ("in_flight", ctypes.c_int32), ("tile_rows", ctypes.c_int32),
         ("split_capable", ctypes.c_int32), ("split_fraction", ctypes.c_double), ("batch_streamed", ctypes.c_int64),
         ("theta", ctypes.c_int32), ("theta_b0", ctypes.c_double), ("cheb_steps", ctypes.c_int32),
-        ("coupling", ctypes.c_int32), ("fluct", ctypes.c_int32),
+        ("coupling", ctypes.c_int32), ("fluct", ctypes.c_int32), ("band", ctypes.c_int32),
+        ("bands", ctypes.c_int32),
     ]
 
 

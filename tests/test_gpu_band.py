@@ -1,0 +1,132 @@
+"""Band kernels: a sample of a large grid spread over several CTAs (full-width
+bands of coarse rows held in registers, band edges exchanged through global
+memory with per-step counters, cooperative launch).
+
+* On 128^2 and 256^2 levels they reproduce the register kernels and on 512^2
+  and 1024^2 levels the streamed-state kernels: identical fixed-point paths
+  (equal masses), observables equal up to summation order.
+* Several waves of samples in flight, ragged last waves, the plain-MC stream.
+* Oracle parity at 512^2 and 1024^2 runs through them (tests/test_gpu_stream.py:
+  the band kernel is the default on those levels).
+"""
+import numpy as np
+import pytest
+
+from paper_2311_08872_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dk():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2311_08872_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2311_08872_gb300 import mlmc_dk
+    return mlmc_dk
+
+
+def _samples(ctx, dk, level, tag, first, count, seed):
+    import torch
+    sums = torch.zeros(dk.sums_len(ctx.n_quant), dtype=torch.float64, device="cuda")
+    samp = torch.zeros(count, dk.sample_stride(ctx.n_obs), dtype=torch.float64, device="cuda")
+    ctx.run_level_dev(level, tag, first, count, seed, sums.data_ptr(), samp.data_ptr(),
+                      torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    return sums.cpu().numpy(), samp.cpu().numpy()
+
+
+def _band_variant(ctx, level, coupled):
+    """Index of the band kernel among the level's variants (the last entry)."""
+    ctx.set_variant(level, coupled, ctx.level_info(level).n_variants - 1)
+    d = ctx.level_info(level)
+    assert d.band == 1 and d.bands >= 2 and d.in_flight >= 1
+    return d
+
+
+def _compare(a, b, K, tol):
+    assert np.array_equal(a[:, 2 * K:], b[:, 2 * K:])            # masses: same integer paths
+    scale = np.sqrt(np.mean(a[:, :2 * K] ** 2, axis=0)) + 1e-300
+    err = np.abs(a[:, :2 * K] - b[:, :2 * K]) / scale
+    assert np.all(err <= tol), float(err.max())
+
+
+@pytest.mark.parametrize("level,count", [(3, 40), (4, 23)])
+def test_band_equals_register_kernels(dk, level, count):
+    """128^2 / 256^2 (with 64^2 / 128^2 coarse): more samples than one wave
+    in flight on 128^2, a ragged count on both."""
+    wl = W.get("mlmc16_256").with_(L_max=level, T=0.002)
+    with dk.Context.from_workload(wl) as reg, dk.Context.from_workload(wl) as bnd:
+        for tag in (0, 1):
+            coupled = tag == 0
+            d = _band_variant(bnd, level, coupled)
+            s_r, a = _samples(reg, dk, level, tag, 3, count, 11)
+            s_b, b = _samples(bnd, dk, level, tag, 3, count, 11)
+            _compare(a, b, reg.n_obs, 1e-6)
+            assert s_b[0] == count and s_b[1] == 0.0
+            print(level, tag, "bands", d.bands, "in flight", d.in_flight)
+
+
+def test_band_many_waves(dk):
+    """More than two waves of 256^2 samples in flight, the last one ragged."""
+    wl = W.get("mlmc16_256").with_(L_max=4, T=2.5e-4)
+    with dk.Context.from_workload(wl) as reg, dk.Context.from_workload(wl) as bnd:
+        d = _band_variant(bnd, 4, True)
+        count = 2 * d.in_flight + 5
+        _, a = _samples(reg, dk, 4, 0, 100, count, 7)
+        s, b = _samples(bnd, dk, 4, 0, 100, count, 7)
+        _compare(a, b, reg.n_obs, 1e-6)
+        assert s[0] == count
+
+
+@pytest.mark.parametrize("name,kw,level,count", [
+    ("lowdens32_512", dict(n0=256, L_max=1, T=4.0e-6), 1, 6),
+    ("large32_1024", dict(n0=512, L_max=1, T=1.52e-6), 1, 3),
+])
+def test_band_equals_streamed_kernels(dk, name, kw, level, count):
+    wl = W.get(name).with_(**kw)
+    with dk.Context.from_workload(wl) as ctx:
+        for tag in (0, 1):
+            coupled = tag == 0
+            d = ctx.level_info(level)
+            assert d.streamed == 1 and d.n_variants == 3
+            _band_variant(ctx, level, coupled)
+            _, b = _samples(ctx, dk, level, tag, 2, count, 5)
+            ctx.set_variant(level, coupled, 0)
+            _, a = _samples(ctx, dk, level, tag, 2, count, 5)
+            _compare(a, b, ctx.n_obs, 1e-9)
+
+
+def test_band_is_default_on_large_levels_and_tuned(dk):
+    wl = W.get("large32_1024")
+    with dk.Context.from_workload(wl) as ctx:
+        for level in (4, 5):
+            d = ctx.level_info(level)
+            assert d.band == 1 and d.streamed == 1
+        secs = ctx.tune(1)
+        assert secs > 0
+        print("variants after tuning", ctx.variants())
+
+
+def test_batch_with_band_level(dk):
+    """A multi-level batch whose finest level runs on the band kernel (beside
+    the graph of the register levels): the same sums as per-level launches."""
+    import torch
+    wl = W.get("mlmc16_256").with_(T=0.004)
+    st = torch.cuda.current_stream().cuda_stream
+    counts = [3000, 400, 60, 30, 25]
+    with dk.Context.from_workload(wl) as ctx:
+        _band_variant(ctx, 4, True)
+        S = dk.sums_len(ctx.n_quant)
+        batch = torch.full((5, S), float("nan"), dtype=torch.float64, device="cuda")
+        ctx.run_batch_dev(counts, 4, 12, batch.data_ptr(), st)
+        torch.cuda.synchronize()
+        ms = ctx.batch_level_ms()
+        assert ms[4] > 0 and ctx.level_info(4).batch_streamed == 0
+        for l, m in enumerate(counts):
+            ref = torch.zeros(S, dtype=torch.float64, device="cuda")
+            ctx.run_level_dev(l, 0, 4, m, 12, ref.data_ptr(), 0, st)
+            torch.cuda.synchronize()
+            np.testing.assert_allclose(batch[l].cpu().numpy(), ref.cpu().numpy(), rtol=1e-12, atol=0)
