@@ -1,25 +1,28 @@
 #!/usr/bin/env python3
 """Benchmark of the GB300 MLMC hot path for the 2-D Dean--Kawasaki equation.
 
-Workload (default ``mlmc16_256``): unit torus, levels 16^2..256^2 (h_l =
-1/16..1/256), tau_l ~ 0.1 h_l^2, T = 0.02, N = 1e5, rho0 = 1 + 0.5 sin sin,
-phi = cos(2 pi x1), NN-coupled levels, RMSE target eps = 1e-3 relative.
+Workload (default ``large32_1024``, the largest single-GPU configuration):
+unit torus, levels 32^2..1024^2 (h_l = 1/32..1/1024, six levels), tau_l =
+0.1 h_l^2 (tau_0 = 9.766e-5, 512..524288 fine steps), T = 0.05, N = 1e6,
+rho0 = 1 + 0.5 sin sin + 0.3 cos(4 pi x2), observables (rho_T, cos 2 pi k.x)_h
+for k in {(1,0), (0,1), (1,1), (2,0)} with all ten pairwise products, NN-coupled
+levels, the learned level below level 0, RMSE target eps = 5e-4 relative.
 
 One *step* is one pass of the whole hot path over the workload's MLMC batch:
-for every level l, M_l coupled samples (Philox normals, fused fine/coarse
-stepping, observables, P, FP64 moment sums; the per-level counts M_l are the
-allocation Algorithm 1 reaches for eps = 1e-3), then the estimator and its
-variance from the sums (Eq. MLMCEstimator).  ``value`` is coupled
-sample-steps per second (sum over levels of M_l x fine steps, per second),
-inputs resident on the device; ``e2e`` is the same through the public C-ABI
-with host buffers (init uploads the level tables from pinned memory, host
-sums are read back per level).  Also reported: the wall time of a full
-adaptive Algorithm 1 run to eps and the plain single-level MC time to the
-same eps on the finest level reached (sample count 2 Var[P_L] / eps^2 times
-the measured MC time per sample).
+the eps-optimal allocation (Eq. opt_M_ell, from pilot variances, divided by
+2^20) of coupled samples on levels 1..5 (Philox normals, fused fine/coarse
+stepping, observables, P, FP64 moment sums; the register levels in one CUDA
+graph, the band-kernel levels beside it), plus the learned level's two parts
+(the level below 0 drawn from its exact feature law and the correction level
+P_0 - S on level-0 paths through the BF16 network), then the estimator and its
+variance from the sums (Eq. MLMCEstimator).  ``value`` is coupled sample-steps
+per second (sum over levels of samples x fine steps, the correction level
+counted with level 0's steps), inputs resident on the device; ``e2e`` is the
+same through the public C-ABI with host buffers (init uploads the level tables
+and the trained network from pinned memory, host sums are read back).
 
-Under torchrun every rank runs the same batch under its own seed (independent
-samples, no collective on the data path): weak scaling.
+Under torchrun every rank runs the same batch on its own sample ids
+(independent samples, no collective on the data path): weak scaling.
 """
 from __future__ import annotations
 
@@ -46,21 +49,8 @@ XU_OPS_COARSE = 1.0
 XU_PER_CLK_PER_SM = 16
 SMS = 152
 SM_MAX_MHZ = 2070.0
-# DRAM bytes of one full-size launch of the dominant kernel (read + write; the
-# state never leaves registers, so this is the initial-state, mean-field and
-# observable tables), from the one-pass ncu capture of the level kernels of
-#   python bench.py --steps 1 --warmup 3 --no-cpu-baseline --no-surrogate --no-adaptive
-#       --no-e2e --no-streamed --split-fraction 0.08
-# (mean of its 4 launches of 879 samples).  Reported only while the kernel
-# sources hash to the value recorded with the capture.
-LEVEL_KERNEL_TRAFFIC = {"kernel": "level_kernel n=256 C=4 R=2 cluster=8 coupled=True",
-                        "bytes_per_launch": 2.176e6, "sources_sha256_16": "bf4df8416557e594"}
-# Thread instructions per fine cell-step of the dominant kernel, from the ncu
-# --set full capture of the 256^2 coupled level kernel (smsp__inst_executed x
-# 32 / fine cell-steps); valid under the same source hash.  The kernel is
-# bound by instruction issue (4 warp instructions per clock per SM).
-LEVEL_KERNEL_INSTR_PER_CELL_STEP = 59.0
-KERNEL_SOURCES = ("dk_kernels.cu", "dk_device.cuh")   # the level kernel and its device functions
+KERNEL_SOURCES = ("dk_kernels.cu", "dk_device.cuh")   # the register kernel and its device functions
+BAND_SOURCES = ("dk_band.cu", "dk_device.cuh")
 
 
 # Theta-scheme kernel (implicit diffusion weight b0 > 0): thread instructions
@@ -77,6 +67,13 @@ THETA_SOURCES = ("dk_theta.cu", "dk_device.cuh")
 FOURIER_KERNEL_INSTR = {"kernel": "fourier_kernel n=54 coupled=True",
                         "instructions_per_cell_step": 94.6, "sources_sha256_16": "5eb2d85d130ecf3e"}
 FOURIER_SOURCES = ("dk_fourier.cu", "dk_device.cuh")
+
+
+# ncu figures of the dominant kernels, valid while their sources hash to the
+# recorded value: DRAM bytes (read + write) per sample of one launch group, and
+# thread instructions per fine cell-step (smsp__inst_executed x 32 / fine
+# cell-steps); keyed by the kernel description the bench prints.
+KERNEL_PROFILE = {}
 
 
 def kernel_sources_hash(files=KERNEL_SOURCES) -> str:
@@ -113,9 +110,12 @@ def closed_form_EP_cos1(n, tau, M):
 
 
 def streamed_stencil(stream):
-    """One wave of samples in flight of the 512^2 level of the low-density
-    workload on the streamed-state kernels (CUDA events on the launching
-    stream; fine-step variant picked by the autotuner)."""
+    """The 512^2 level of the low-density workload (coupled with 256^2, 52480
+    fine steps): one launch group of the samples in flight on the level's tuned
+    large-grid kernel (the band kernel unless the tuner prefers the streamed
+    state), CUDA events on the launching stream, against the HBM rate a state
+    streamed through memory would need (8.5 algorithmic bytes per coupled fine
+    cell-step)."""
     import torch
     from paper_2311_08872_gb300 import mlmc_dk, workloads
     wl = workloads.get("lowdens32_512")
@@ -136,11 +136,12 @@ def streamed_stencil(stream):
     fine = S * info.n ** 2 * info.M
     peak, src = measured_peaks()
     gbs = fine * STREAM_BYTES_PER_FINE_CELL_STEP / sec / 1e9
-    return {"workload": wl.name, "level": level, "n": info.n, "fine_steps": info.M, "samples": S,
-            "tile_rows": info.tile_rows, "s": sec, "cell_steps_per_s": S * info.cost / sec,
+    kernel = f"band_kernel bands={info.bands}" if info.band else f"streamed tile_rows={info.tile_rows}"
+    return {"workload": wl.name, "level": level, "n": info.n, "fine_steps": info.M, "samples": S, "kernel": kernel,
+            "s": sec, "cell_steps_per_s": S * info.cost / sec,
             "fine_cell_steps_per_s": fine / sec, "algorithmic_bytes_per_fine_cell_step": STREAM_BYTES_PER_FINE_CELL_STEP,
             "achieved_GBps": gbs, "hbm_peak_GBps": peak, "peak_source": src, "frac_of_hbm": gbs / peak,
-            "bound": "alu (instruction issue): the working set stays in L2, DRAM traffic is the cold start only"}
+            "bound": "alu (instruction issue): the state stays on chip; DRAM sees the tables only"}
 
 
 def theta_scheme(stream):
@@ -216,7 +217,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="mlmc16_256")
+    ap.add_argument("--workload", default="large32_1024")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-streamed", action="store_true", help="skip the streamed-state stencil timing")
@@ -224,7 +225,9 @@ def parse():
     ap.add_argument("--no-fourier", action="store_true", help="skip the Fourier-coupled kernel timing")
     ap.add_argument("--split-fraction", type=float, default=None,
                     help="fixed batch split of the finest cluster level (default: autotuned)")
-    ap.add_argument("--no-adaptive", action="store_true", help="skip the Algorithm 1 / plain MC timing")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the secondary measurements (16^2..256^2 batch, 512^2 stencil, theta, Fourier)")
+    ap.add_argument("--no-mlmc16", action="store_true", help="skip the 16^2..256^2 batch and Algorithm 1 run")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned level below 0")
     ap.add_argument("--adaptive-eps", type=float, default=1e-2,
@@ -233,19 +236,42 @@ def parse():
 
 
 # ------------------------------------------------------------------ helpers
-def level_costs(wl):
+def nominal_levels(wl):
+    """(n_l, M_l) of the workload's hierarchy: M_0 = ceil(T / (mu h_0^2)), M_l =
+    M_0 4^l (labels of the config; the work units come from the library's or
+    the oracle's own level table)."""
+    h0 = wl.length / wl.n0
+    x = wl.T / (wl.mu * h0 * h0)
+    M0 = wl.M0 or int(math.ceil(x - 1e-9 * x))
+    return [(wl.n0 * 2 ** l, M0 * 4 ** l) for l in range(wl.L_max + 1)]
+
+
+def workload_config(wl, alloc, learned):
+    lv = nominal_levels(wl)
+    cfg = {"workload": wl.name, "levels": [n for n, _ in lv], "fine_steps": [m for _, m in lv], "T": wl.T, "N": wl.N,
+           "mu": wl.mu, "n_obs": len(wl.observables), "products": bool(wl.products), "eps_rel": wl.eps_rel,
+           "alloc": list(alloc), "alloc_scale": wl.alloc_scale}
+    if learned is not None:
+        cfg["alloc_learned"] = {"below_0": learned[0], "correction": learned[1]}
+    return cfg
+
+
+def step_units(fine, coarse, M, alloc, learned):
+    """Coupled sample-steps and cell-steps of one step: levels l >= 1 from
+    alloc, level 0 from alloc[0] or, with the learned level, the correction
+    level's count (its level-0 paths; the level below 0 takes no steps)."""
+    n0 = alloc[0] if learned is None else learned[1]
+    sample_steps = n0 * M[0] + sum(alloc[l] * M[l] for l in range(1, len(alloc)))
+    cell_steps = n0 * fine[0] + sum(alloc[l] * (fine[l] + coarse[l]) for l in range(1, len(alloc)))
+    return sample_steps, cell_steps
+
+
+def oracle_level_costs(wl):
     import oracle
     lv = oracle.level_table(wl.length, wl.n0, wl.L_max, wl.T, wl.mu, wl.M0)
     fine = [l.n * l.n * l.M for l in lv]
     coarse = [0.0] + [lv[l - 1].n ** 2 * lv[l - 1].M for l in range(1, len(lv))]
-    return lv, fine, coarse
-
-
-def batch_units(wl, alloc):
-    lv, fine, coarse = level_costs(wl)
-    sample_steps = sum(m * lv[l].M for l, m in enumerate(alloc))
-    cell_steps = sum(m * (fine[l] + coarse[l]) for l, m in enumerate(alloc))
-    return sample_steps, cell_steps
+    return [l.M for l in lv], fine, coarse
 
 
 class Clocks:
@@ -303,53 +329,119 @@ class Clocks:
 
 # ------------------------------------------------------------ CPU oracle leg
 def _oracle_task(args):
-    (wl, level, sample) = args
+    (wl, level, sample, seed) = args
     import oracle
     lv = oracle.level_table(wl.length, wl.n0, wl.L_max, wl.T, wl.mu, wl.M0)
     ol = oracle.level_inputs(wl.length, lv, wl.N, wl.rho0_all(), wl.phi_all(), level, level > 0)
     t = time.perf_counter()
-    ol.sample(wl.seed, sample, level > 0)
-    return level, time.perf_counter() - t
+    r = ol.sample(seed, sample, level > 0)
+    dt = time.perf_counter() - t
+    return level, sample, dt, list(r["Y_f"]), (list(r["Y_c"]) if level > 0 else None)
 
 
-def oracle_rate(wl, alloc, budget_s, cores=None):
-    """The FP64 oracle, as it stands, on the host cores: per-level single-core
-    seconds per coupled sample measured on a bounded sample (levels with a
-    sample of at most ~budget/4 core-seconds), extrapolated by cell-steps to
-    the others, then the batch's sample-steps over the batch's CPU time on
-    `cores` cores."""
+def oracle_leg(wl, alloc, learned, budget_s, seed, first, cores=None):
+    """The FP64 oracle, as it stands, on the host cores (one process per core,
+    each single-threaded): coupled samples with the benchmark step's own seed
+    and sample ids on every level whose samples fit the budget (a bounded
+    sample of the workload), timed per level and extrapolated by cell-steps to
+    the others.  Returns the timing figures and the oracle's per-sample
+    observables (for the per-sample error of the GPU path on the same ids)."""
     import multiprocessing as mp
-    cores = cores or min(os.cpu_count() or 1, 16)
-    lv, fine, coarse = level_costs(wl)
-    per_cell = 1.0 / 15e6     # first guess, refined by the measurement below
+    nproc = os.cpu_count() or 1
+    cores = cores or min(nproc, 16)
+    M, fine, coarse = oracle_level_costs(wl)
+    per_cell = 1.0 / 2.5e7     # first guess (one core), refined by the measurement
     tasks = []
     for l in range(len(alloc)):
         est = (fine[l] + coarse[l]) * per_cell
-        if est > budget_s * cores / 4:
+        if est > budget_s * cores / 6:
             continue
-        k = max(1, min(64, int(budget_s * cores / (4 * max(est, 1e-6) * len(alloc)))))
-        tasks += [(wl, l, 1000 + i) for i in range(k)]
+        k = max(1, min(64, cores, int(budget_s * cores / (4 * max(est, 1e-6) * len(alloc)))))
+        if l > 0 and k < 2 and est > budget_s / 2:
+            k = 1
+        tasks += [(wl, l, first + i, seed) for i in range(k)]
     t0 = time.perf_counter()
     with mp.get_context("spawn").Pool(cores) as pool:
         res = pool.map(_oracle_task, tasks, chunksize=1)
     wall = time.perf_counter() - t0
-    per_level = {}
-    for l, dt in res:
+    per_level, outs = {}, {}
+    for l, i, dt, yf, yc in res:
         per_level.setdefault(l, []).append(dt)
+        outs.setdefault(l, {})[i] = (yf, yc)
     t = {l: statistics.mean(v) for l, v in per_level.items()}
     top = max(t)
     cell_rate = (fine[top] + coarse[top]) / t[top]
-    secs = []
+    secs = [0.0] * len(alloc)
     for l, m in enumerate(alloc):
-        secs.append(m * (t[l] if l in t else (fine[l] + coarse[l]) / cell_rate))
-    sample_steps, cell_steps = batch_units(wl, alloc)
+        if l == 0 and learned is not None:
+            m = learned[1]     # the correction level's level-0 paths (network cost not counted)
+        secs[l] = m * (t[l] if l in t else (fine[l] + coarse[l]) / cell_rate)
+    sample_steps, cell_steps = step_units(fine, coarse, M, alloc, learned)
     cpu_time = sum(secs) / cores
-    sample = (f"{len(tasks)} coupled samples of levels {sorted(t)} in {wall:.1f} s wall on {cores} processes; "
-              f"levels {[l for l in range(len(alloc)) if l not in t]} extrapolated by cell-steps from level {top}")
-    return {"value": sample_steps / cpu_time, "unit": UNIT, "cores": cores, "kind": "oracle",
+    sample = (f"{len(tasks)} coupled samples (the step's seed and ids) of levels {sorted(t)} in {wall:.1f} s wall "
+              f"on {cores} processes; levels {[l for l in range(len(alloc)) if l not in t]} extrapolated by "
+              f"cell-steps from level {top}")
+    return {"value": sample_steps / cpu_time, "unit": UNIT, "cores": cores, "nproc": nproc, "kind": "oracle",
             "sample": sample, "cell_steps_per_s": cell_steps / cpu_time,
             "cell_steps_per_s_per_core": cell_steps / cpu_time / cores,
-            "batch_cpu_s": cpu_time, "wall_s": wall}
+            "batch_cpu_s": cpu_time, "wall_s": wall}, outs
+
+
+def oracle_error(ctx, wl, outs, seed, stream):
+    """Per-sample error of the GPU path against the oracle on the same ids:
+    max |Y_gpu - Y_oracle| / max(|Y_oracle|, RMS of the level's Y_oracle - Ybar)
+    over the observables of the fine and coarse paths, and the level means of
+    P_l - P_{l-1} (every quantity) from both on those ids."""
+    import numpy as np
+    import torch
+    from paper_2311_08872_gb300 import mlmc_dk
+    K = ctx.n_obs
+    rows = []
+    worst = 0.0
+    for l in sorted(outs):
+        ids = sorted(outs[l])
+        first, k = ids[0], len(ids)
+        assert ids == list(range(first, first + k))
+        info = ctx.level_info(l)
+        sums = torch.zeros(mlmc_dk.sums_len(ctx.n_quant), dtype=torch.float64, device="cuda")
+        samp = torch.zeros(k, mlmc_dk.sample_stride(K), dtype=torch.float64, device="cuda")
+        ctx.run_level_dev(l, 0, first, k, seed, sums.data_ptr(), samp.data_ptr(), stream.cuda_stream)
+        torch.cuda.synchronize()
+        g = samp.cpu().numpy()
+        yf_o = np.array([outs[l][i][0] for i in ids])
+        yb_f = np.array(info.ybar_f[:K])
+        pairs = [(g[:, :K] + yb_f[None, :], yf_o, yb_f)]
+        if l > 0:
+            yc_o = np.array([outs[l][i][1] for i in ids])
+            yb_c = np.array(info.ybar_c[:K])
+            pairs.append((g[:, K:2 * K] + yb_c[None, :], yc_o, yb_c))
+        lw = 0.0
+        for yg, yo, yb in pairs:
+            scale = np.sqrt(np.mean((yo - yb[None, :]) ** 2, axis=0))
+            lw = max(lw, float(np.max(np.abs(yg - yo) / np.maximum(np.abs(yo), scale[None, :]))))
+        worst = max(worst, lw)
+
+        def dP(Df, Dc):
+            cols = []
+            for j in range(K):
+                for q in range(j, K if wl.products else j + 1):
+                    pf = wl.N * Df[:, j] * Df[:, q]
+                    pc = wl.N * Dc[:, j] * Dc[:, q] if Dc is not None else 0.0
+                    cols.append(pf - pc)
+            return np.stack(cols, axis=1)
+        dg = dP(g[:, :K], g[:, K:2 * K] if l > 0 else None)
+        do = dP(yf_o - yb_f[None, :], (yc_o - yb_c[None, :]) if l > 0 else None)
+        rows.append({"level": l, "n": info.n, "ids": [first, first + k - 1], "max_err_over_bar_scale": lw,
+                     "mean_dP_gpu": dg.mean(axis=0).tolist(), "mean_dP_oracle": do.mean(axis=0).tolist(),
+                     "max_abs_diff_mean_dP": float(np.max(np.abs(dg.mean(axis=0) - do.mean(axis=0))))})
+    return {"levels": rows, "worst_err_over_bar_scale": worst, "bar": 1e-5,
+            "within_bar": worst <= 1e-5,
+            "what": "per-sample |Y_gpu - Y_oracle| / max(|Y_oracle|, RMS(Y_oracle - Ybar)) on the step's seed and ids "
+                    "of the levels the oracle finished (FP32 noise and 32-bit fixed-point state against FP64); "
+                    "the per-sample bar is 1e-5 of that scale; the level means of dP from both on the same ids",
+            "levels_without_oracle": "finer levels: the oracle needs hours per sample there; their kernels are "
+                                     "checked against the oracle over short horizons and against each other "
+                                     "(tests/test_gpu_band.py, tests/test_gpu_stream.py)"}
 
 
 # --------------------------------------------------------------- our arm
@@ -359,69 +451,95 @@ def run_ours(args, wl, rank, world, local_rank):
 
     import __graft_entry__
     __graft_entry__.build()
+    from paper_2311_08872_gb300 import distributed as D
     from paper_2311_08872_gb300 import mlmc_dk
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream(dev)
-    from paper_2311_08872_gb300 import distributed as D
-    alloc = list(wl.alloc) if wl.alloc else None
+    if wl.alloc is None:
+        raise SystemExit("workload has no fixed allocation")
+    L = wl.L_max
+    alloc = list(wl.alloc) + [0] * (L + 1 - len(wl.alloc))
+    learned = tuple(wl.alloc_learned) if (wl.alloc_learned and not args.no_surrogate) else None
     seed0 = wl.seed
     first0 = D.first_sample(rank)          # ranks shard the sample ids (no collective on the data path)
 
     ctx = mlmc_dk.Context.from_workload(wl, stream=stream.cuda_stream)
-    tune_s = ctx.tune(repeats=1)          # autotuner: fastest kernel variant per level (outside timing)
+    tune_s = ctx.tune(repeats=1)          # autotuner: fastest kernel per level (outside timing)
     choice = ctx.variants()
-    info = [ctx.level_info(l) for l in range(wl.L_max + 1)]
+    info = [ctx.level_info(l) for l in range(L + 1)]
+    M = [i.M for i in info]
+    fine = [i.cost_mc for i in info]
+    coarse = [i.cost - i.cost_mc for i in info]
+    sample_steps, cell_steps = step_units(fine, coarse, M, alloc, learned)
+    nq = ctx.n_quant
 
-    # ---- a complete adaptive Algorithm 1 run, measured (at a looser eps than the
-    #      workload's when the workload's eps would take longer than the bench allows)
-    adaptive = None
-    if not args.no_adaptive:
-        eps_meas = args.adaptive_eps or wl.eps_rel
+    # the learned level below 0 is trained once, outside the timed region: the
+    # network is an input of every step (like the level tables)
+    sur = None
+    theta = None
+    if learned is not None:
         torch.cuda.synchronize()
         t = time.perf_counter()
-        r = ctx.estimate(eps_meas, relative=True, seed=seed0 + 5)
+        ctx.surrogate_init(seed0 + 3)
+        tr = ctx.surrogate_train(1 << 18, epochs=8, batch=1024, lr=1e-3, seed=seed0 + 4)
         torch.cuda.synchronize()
-        adaptive = {"eps_rel": eps_meas, "s": time.perf_counter() - t, "L": r.L,
-                    "M": [r.M[l] for l in range(r.L + 1)], "estimate": r.estimate, "variance": r.variance,
-                    "eps_abs": r.eps_abs, "converged": bool(r.converged), "cell_steps": r.cell_steps}
-    if alloc is None:
-        raise SystemExit("workload has no fixed allocation")
-    alloc = alloc + [0] * (wl.L_max + 1 - len(alloc))
-    sample_steps, cell_steps = batch_units(wl, alloc)
-    # batch split: share of the 256^2 level's samples on the streamed kernels, on the
-    # SMs its 8-SM clusters leave free (tuned on the batch itself, outside the timing)
-    split_level = max((l for l in range(len(alloc)) if ctx.level_info(l).split_capable), default=None)
-    if args.split_fraction is None:
-        split_frac, split_s = ctx.tune_batch(alloc, 1)
-    else:
-        split_frac, split_s = args.split_fraction, 0.0
-        if split_level is not None:
+        sur = {"train_s": time.perf_counter() - t, "train_pairs": 1 << 18, "val_mse": tr["val_mse"]}
+        theta = ctx.surrogate_params()
+
+    batch_counts = list(alloc)
+    if learned is not None:
+        batch_counts[0] = 0
+    # batch split: a share of an 8-SM-cluster level's samples on the streamed
+    # kernels (only where such a level runs the register kernel)
+    split_level = max((l for l in range(L + 1) if info[l].split_capable and not info[l].band), default=None)
+    split_frac, split_s = 0.0, 0.0
+    if split_level is not None:
+        if args.split_fraction is None:
+            split_frac, split_s = ctx.tune_batch(batch_counts, 1)
+        else:
+            split_frac = args.split_fraction
             ctx.set_batch_split(split_level, split_frac)
 
-    nq = ctx.n_quant
-    sums = torch.zeros(wl.L_max + 1, mlmc_dk.sums_len(nq), dtype=torch.float64, device=dev)
+    S = mlmc_dk.sums_len(nq)
+    sums = torch.zeros(L + 1, S, dtype=torch.float64, device=dev)
     host = torch.zeros_like(sums, device="cpu").pin_memory()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     step_ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
 
+    def sur_array(parts):
+        return np.array([[p.n, p.dp1, p.dp2, p.pf1, p.pf2, p.kernel_s, p.launches] for p in parts])
+
     def step(seed):
-        # all levels concurrently: one CUDA-graph launch of the multi-level batch
         step_ev[0].record(stream)
-        ctx.run_batch_dev(alloc, first0, seed, sums.data_ptr(), stream.cuda_stream)
+        ctx.run_batch_dev(batch_counts, first0, seed, sums.data_ptr(), stream.cuda_stream)
+        parts = None
+        if learned is not None:
+            # the level below 0 and the correction level P_0 - S (host sums; same stream)
+            parts = (sur_array(ctx.run_surrogate(-1, learned[0], seed)),
+                     sur_array(ctx.run_surrogate(0, learned[1], seed)))
         host.copy_(sums, non_blocking=True)
         step_ev[1].record(stream)
         stream.synchronize()
-        s = host.numpy()
-        est, var = 0.0, 0.0
-        for l, m in enumerate(alloc):
-            if m <= 0:
+        return host.numpy().copy(), parts
+
+    def estimate(s, parts):
+        """Eq. (MLMCEstimator) for every quantity, and its variance."""
+        est, var = np.zeros(nq), np.zeros(nq)
+        for l in range(L + 1):
+            m = batch_counts[l]
+            if m <= 1:
                 continue
-            e = s[l, 2] / m
-            est += e
-            var += max(0.0, (s[l, 3] - s[l, 2] ** 2 / m) / (m - 1)) / m
-        return est, var, s.copy()
+            d1, d2 = s[l, 2 + 12 * np.arange(nq)], s[l, 3 + 12 * np.arange(nq)]
+            est += d1 / m
+            var += np.maximum(0.0, (d2 - d1 * d1 / m) / (m - 1)) / m
+        if parts is not None:
+            for p in parts:
+                n = p[:, 0]
+                est += p[:, 1] / n
+                var += np.maximum(0.0, (p[:, 2] - p[:, 1] ** 2 / n) / (n - 1)) / n
+        return est, var
 
     for w in range(args.warmup):
         step(seed0 + 17 + w)
@@ -430,21 +548,32 @@ def run_ours(args, wl, rank, world, local_rank):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    step_ms, level_ms = [], [0.0] * len(alloc)
+    step_ms, level_ms = [], [0.0] * (L + 1)
+    acc = np.zeros((L + 1, S))
+    acc_parts = None
     launches = 0
     last = None
     for k in range(args.steps):
         flush.zero_()                      # evict L2 between steps (outside the step events)
-        last = step(seed0 + 101 + k)
+        s, parts = step(seed0 + 101 + k)
         step_ms.append(step_ev[0].elapsed_time(step_ev[1]))
-        for l, t in enumerate(ctx.batch_level_ms()):   # CUDA events on each level's stream in the graph
+        acc += s
+        if parts is not None:
+            acc_parts = [p.copy() for p in parts] if acc_parts is None else [a + p for a, p in zip(acc_parts, parts)]
+            launches += int(parts[0][0, 6] + parts[1][0, 6])
+        last = (s, parts)
+        for l, t in enumerate(ctx.batch_level_ms()):   # CUDA events on each level's stream
             level_ms[l] += t
-            if alloc[l] > 0:
-                launches += 2
+            if batch_counts[l] <= 0:
+                continue
             d = ctx.level_info(l)
-            if d.batch_streamed > 0:      # zero + per wave (init, fine steps, coarse steps, observe, finish) + reduce + merge
-                waves = -(-d.batch_streamed // d.in_flight)
-                launches += 1 + waves * (3 + d.M + d.M // 4) + 2
+            if d.band:                       # zero + per wave (kernel + finish) + reduce
+                launches += 2 + 2 * (-(-batch_counts[l] // d.in_flight))
+            else:
+                launches += 2
+                if d.batch_streamed > 0:     # zero + per wave (init, fine steps, coarse steps, observe, finish) + reduce + merge
+                    waves = -(-d.batch_streamed // d.in_flight)
+                    launches += 1 + waves * (3 + d.M + d.M // 4) + 2
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -455,109 +584,116 @@ def run_ours(args, wl, rank, world, local_rank):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total_ms = float(t.item())
     value = world * sample_steps * args.steps / (total_ms * 1e-3)
+    est, var = estimate(*last)
 
-    split_samples = ctx.level_info(split_level).batch_streamed if split_level is not None else 0
-
-    # ---- roofline of the dominant kernel (the level kernel of the costliest level)
-    dom = max(range(len(alloc)), key=lambda l: level_ms[l])
+    # ---- roofline of the dominant kernel (the costliest level's kernel)
+    dom = max(range(L + 1), key=lambda l: level_ms[l])
     if level_ms[dom] <= 0:
         raise SystemExit("no per-level kernel times from the batch")
-    lv, fine, coarse = level_costs(wl)
-    reg_dom = alloc[dom] - ctx.level_info(dom).batch_streamed    # samples the register kernel ran
-    ops = reg_dom * (fine[dom] * XU_OPS_FINE + coarse[dom] * XU_OPS_COARSE) * args.steps
-    achieved = ops / (level_ms[dom] * 1e-3)
-    peak = XU_PER_CLK_PER_SM * SMS * SM_MAX_MHZ * 1e6
-    kname = (f"level_kernel n={info[dom].n} C={info[dom].lane_cols} R={info[dom].lane_rows} "
-             f"cluster={info[dom].cluster} coupled={dom > 0}")
+    dinfo = ctx.level_info(dom)
+    reg_dom = batch_counts[dom] - dinfo.batch_streamed
+    sec_dom = level_ms[dom] * 1e-3
+    fine_cs = reg_dom * fine[dom] * args.steps
+    all_cs = reg_dom * (fine[dom] + coarse[dom]) * args.steps
+    xu_ops = reg_dom * (fine[dom] * XU_OPS_FINE + coarse[dom] * XU_OPS_COARSE) * args.steps
+    xu_peak = XU_PER_CLK_PER_SM * SMS * SM_MAX_MHZ * 1e6
+    hbm_peak, hbm_src = measured_peaks()
+    if dinfo.band:
+        kname = f"band_kernel n={dinfo.n} bands={dinfo.bands} in_flight={dinfo.in_flight} coupled={dom > 0}"
+    else:
+        kname = (f"level_kernel n={dinfo.n} C={dinfo.lane_cols} R={dinfo.lane_rows} "
+                 f"cluster={dinfo.cluster} coupled={dom > 0}")
     traffic = None
-    if kname == LEVEL_KERNEL_TRAFFIC["kernel"] and kernel_sources_hash() == LEVEL_KERNEL_TRAFFIC["sources_sha256_16"]:
-        traffic = LEVEL_KERNEL_TRAFFIC["bytes_per_launch"]
+    rec = KERNEL_PROFILE.get(kname)
+    if rec and kernel_sources_hash(rec["sources"]) == rec["sources_sha256_16"]:
+        traffic = rec["dram_bytes_per_sample"] * reg_dom
     issue = None
-    if traffic is not None:   # same sources as the capture that counted the instructions
-        warp_inst = reg_dom * fine[dom] * LEVEL_KERNEL_INSTR_PER_CELL_STEP / 32.0 * args.steps / (level_ms[dom] * 1e-3)
-        issue = {"instructions_per_fine_cell_step": LEVEL_KERNEL_INSTR_PER_CELL_STEP,
-                 "achieved_warp_inst_per_s": warp_inst, "peak_all_sms": 4 * SMS * SM_MAX_MHZ * 1e6,
-                 "frac_all_sms": warp_inst / (4 * SMS * SM_MAX_MHZ * 1e6),
-                 "note": "instruction-issue roofline: the binding limit; the clusters of 8 hold 120 of 152 SMs"}
-    roofline = {"bound": "alu", "pipe": "XU (MUFU)",
-                "kernel": kname,
-                "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gop/s", "frac": achieved / peak,
-                "traffic": traffic, "traffic_unit": "DRAM bytes per launch (ncu, one launch per step)",
-                "ops_per_fine_cell_step": XU_OPS_FINE,
-                "samples_per_launch": reg_dom,
+    if rec and rec.get("instructions_per_fine_cell_step") and traffic is not None:
+        ipc = rec["instructions_per_fine_cell_step"]
+        warp_inst = fine_cs * ipc / 32.0 / sec_dom
+        issue = {"instructions_per_fine_cell_step": ipc, "achieved_warp_inst_per_s": warp_inst,
+                 "peak_warp_inst_per_s": 4 * SMS * SM_MAX_MHZ * 1e6,
+                 "frac": warp_inst / (4 * SMS * SM_MAX_MHZ * 1e6)}
+    hbm_equiv = fine_cs * STREAM_BYTES_PER_FINE_CELL_STEP / sec_dom / 1e9
+    roofline = {"bound": "alu", "pipe": "XU (MUFU)", "kernel": kname,
+                "achieved": xu_ops / sec_dom / 1e9, "peak": xu_peak / 1e9, "unit": "Gop/s",
+                "frac": xu_ops / sec_dom / xu_peak,
+                "traffic": traffic, "traffic_unit": "DRAM bytes per launch group (ncu, per sample x samples)",
+                "ops_per_fine_cell_step": XU_OPS_FINE, "samples_per_step": reg_dom,
+                "cell_steps_per_s": all_cs / sec_dom, "fine_cell_steps_per_s": fine_cs / sec_dom,
                 "issue": issue,
-                "cell_steps_per_s": reg_dom * (fine[dom] + coarse[dom]) * args.steps / (level_ms[dom] * 1e-3),
+                "hbm_equivalent": {"algorithmic_bytes_per_fine_cell_step": STREAM_BYTES_PER_FINE_CELL_STEP,
+                                   "achieved_GBps": hbm_equiv, "peak_GBps": hbm_peak, "peak_source": hbm_src,
+                                   "frac": hbm_equiv / hbm_peak,
+                                   "note": "the state stays on chip (registers); DRAM sees the tables only, so this "
+                                           "is the rate a state streamed through HBM would need, not DRAM traffic"},
                 "level_ms_per_step": [x / args.steps for x in level_ms],
-                "note": "levels run concurrently in one CUDA graph; each level's time is its own stream's span"}
+                "note": "XU ops are the algorithmic MUFU operations (Box--Muller log, sqrt, sin, cos; sqrt of rho+); "
+                        "peak 16 per clock per SM x 152 SMs x 2.07 GHz"}
 
-    # ---- time to the workload's eps, MLMC against plain MC on the finest level.
-    # From the timed batch: V_l = Var[P_l - P_{l-1}]; the eps-optimal cost in
-    # cell-steps is 2 eps^-2 (sum_l sqrt(V_l C_l))^2 (Eq. opt_M_ell with C_l the
-    # cell-steps of one coupled sample, as Algorithm 1 uses), timed at the
-    # batch's measured cell-step rate; plain MC needs 2 Var[P_L] / eps^2
-    # samples of level L, timed separately below.
-    est, _, s = last
-    Ls = max(l for l, m in enumerate(alloc) if m > 0)
-    V, C = [], []
-    for l, m in enumerate(alloc):
-        if m > 0:
-            V.append(max(0.0, (s[l, 3] - s[l, 2] ** 2 / m) / (m - 1)))
-            C.append(fine[l] + coarse[l])
-    eps_abs = wl.eps_rel * abs(est)
-    cost_opt = 2.0 / eps_abs ** 2 * sum(math.sqrt(v * c) for v, c in zip(V, C)) ** 2
-    rate = cell_steps * args.steps / (sum(step_ms) * 1e-3)
-    t_mlmc = cost_opt / rate
-    mL = alloc[Ls]
-    var_pL = max(0.0, (s[Ls, 7] - s[Ls, 6] ** 2 / mL) / (mL - 1))
-    n_mc = int(max(32, min(20000, 2.0e11 / fine[Ls])))
+    # ---- time to the workload's eps: plain MLMC, MLMC with the learned level, plain MC
+    rate = cell_steps * args.steps / (sum(step_ms) * 1e-3)        # the batch's cell-steps per second
+    t_l = [(fine[l] + coarse[l]) / rate for l in range(L + 1)]
+    V = np.zeros((L + 1, nq))
+    for l in range(1, L + 1):
+        m = batch_counts[l] * args.steps
+        if m > 1:
+            d1, d2 = acc[l, 2 + 12 * np.arange(nq)], acc[l, 3 + 12 * np.arange(nq)]
+            V[l] = np.maximum(0.0, (d2 - d1 * d1 / m) / (m - 1))
+    n0p = 20000                                                    # level 0 of plain MLMC, measured apart
+    s0 = ctx.run_level(0, n0p, seed0 + 9)
+    V[0] = [max(0.0, (q.dp2 - q.dp1 ** 2 / q.n) / (q.n - 1)) for q in s0]
+    est0 = np.array([q.dp1 / q.n for q in s0])
+    plain_est = est.copy()
+    if learned is not None:
+        plain_est = est - sum(p[:, 1] / p[:, 0] for p in last[1]) + est0
+    eps_abs = wl.eps_rel * float(np.max(np.abs(plain_est)))
+
+    def opt_cost(Vs, ts):
+        Mopt = np.zeros(len(ts))
+        for q in range(nq):
+            tot = sum(math.sqrt(v * t) for v, t in zip(Vs[:, q], ts))
+            for i, (v, t) in enumerate(zip(Vs[:, q], ts)):
+                if v > 0:
+                    Mopt[i] = max(Mopt[i], math.ceil(2.0 / eps_abs ** 2 * math.sqrt(v / t) * tot))
+        return Mopt, float(sum(m * t for m, t in zip(Mopt, ts)))
+
+    M_plain, t_mlmc = opt_cost(V, t_l)
+    n_mc = 1 if fine[L] > 1e11 else max(2, int(2e11 / fine[L]))
     torch.cuda.synchronize()
     a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a0.record(stream)
-    ctx.run_level(Ls, n_mc, seed0 + 7, mc=True)
+    ctx.run_level(L, n_mc, seed0 + 7, mc=True)
     a1.record(stream)
     torch.cuda.synchronize()
-    per = a0.elapsed_time(a1) * 1e-3 / n_mc
-    m_mc = math.ceil(2.0 * var_pL / eps_abs ** 2)
-    mc = {"level": Ls, "samples": m_mc, "s_per_sample": per, "s": m_mc * per, "extrapolated": True,
-          "measured_samples": n_mc, "var_P_L": var_pL}
-    to_eps = {"eps_rel": wl.eps_rel, "eps_abs": eps_abs, "estimate": est, "V": V, "cost_cell_steps": cost_opt,
-              "batch_cell_steps_per_s": rate, "mlmc_s": t_mlmc, "mc_s": m_mc * per, "extrapolated": True,
-              "how": "eps-optimal cost from the timed batch's V_l at its measured cell-step rate; "
-                     "plain MC from 2 Var[P_L]/eps^2 samples at the measured MC time per sample"}
+    t_mc = a0.elapsed_time(a1) * 1e-3 / n_mc
+    mL = batch_counts[L] * args.steps
+    pf1, pf2 = acc[L, 6 + 12 * np.arange(nq)], acc[L, 7 + 12 * np.arange(nq)]
+    var_pL = np.maximum(0.0, (pf2 - pf1 ** 2 / mL) / (mL - 1))
+    m_mc = int(max(math.ceil(2.0 * v / eps_abs ** 2) for v in var_pL))
+    to_eps = {"eps_rel": wl.eps_rel, "eps_abs": eps_abs, "estimate": plain_est.tolist(), "V": V[:, 0].tolist(),
+              "M_opt": M_plain.tolist(), "batch_cell_steps_per_s": rate, "mlmc_s": t_mlmc,
+              "mc_samples": m_mc, "mc_s_per_sample": t_mc, "mc_s": m_mc * t_mc, "extrapolated": True,
+              "how": "eps-optimal cost (Eq. opt_M_ell, max over the quantities) from the timed steps' V_l "
+                     "(level 0: 20000 samples apart) at the batch's cell-step rate; plain MC from "
+                     "2 Var[P_L]/eps^2 samples at the measured MC time per sample of the finest level"}
+    if learned is not None:
+        pS, pC = acc_parts
+        Vs = np.zeros((L + 2, nq))
+        ts = [pS[0, 5] / pS[0, 0], pC[0, 5] / pC[0, 0]] + t_l[1:]
+        for i, p in enumerate((pS, pC)):
+            n = p[:, 0]
+            Vs[i] = np.maximum(0.0, (p[:, 2] - p[:, 1] ** 2 / n) / (n - 1))
+        Vs[2:] = V[1:]
+        M_sur, t_sur = opt_cost(Vs, ts)
+        sur.update({"var_P0": V[0].tolist(), "var_S": Vs[0].tolist(), "var_P0_minus_S": Vs[1].tolist(),
+                    "s_per_sample_S": ts[0], "s_per_sample_P0_minus_S": ts[1], "s_per_sample_P0": t_l[0],
+                    "M_opt": M_sur.tolist(), "mlmc_s_to_eps": t_sur,
+                    "mlmc_s_to_eps_incl_training": t_sur + sur["train_s"], "extrapolated": True})
 
-    # ---- learned level below 0 (trained on 2^18 level-0 paths): the same eps-optimal
-    #      time with levels {S, P_0 - S, 1..L} in place of {0, 1..L}
-    surrogate = None
-    if not args.no_surrogate:
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        ctx.surrogate_init(seed0 + 3)
-        tr = ctx.surrogate_train(1 << 18, epochs=8, batch=1024, lr=1e-3, seed=seed0 + 4)
-        torch.cuda.synchronize()
-        train_s = time.perf_counter() - t
-        n_s = 200000
-        s_sur = ctx.run_surrogate(-1, n_s, seed0 + 5)[0]
-        s_cor = ctx.run_surrogate(0, n_s, seed0 + 6)[0]
-        var = lambda q: max(0.0, (q.dp2 - q.dp1 ** 2 / q.n) / (q.n - 1))
-        t_l = [c / rate for c in C]        # seconds per sample of levels 0..L at the batch's rate
-        terms = [math.sqrt(var(s_sur) * s_sur.kernel_s / n_s), math.sqrt(var(s_cor) * s_cor.kernel_s / n_s)]
-        terms += [math.sqrt(v * tt) for v, tt in zip(V[1:], t_l[1:])]
-        t_sur = 2.0 / eps_abs ** 2 * sum(terms) ** 2
-        surrogate = {"train_s": train_s, "train_pairs": 1 << 18, "val_mse": tr["val_mse"],
-                     "var_P0": V[0], "var_S": var(s_sur), "var_P0_minus_S": var(s_cor),
-                     "s_per_sample_S": s_sur.kernel_s / n_s, "s_per_sample_P0_minus_S": s_cor.kernel_s / n_s,
-                     "s_per_sample_P0": t_l[0], "mlmc_s_to_eps": t_sur,
-                     "mlmc_s_to_eps_incl_training": t_sur + train_s, "extrapolated": True}
-
-    streamed = None
-    if not args.no_streamed:
-        streamed = streamed_stencil(stream)
-    theta = None
-    if not args.no_theta:
-        theta = theta_scheme(stream)
-    fourier = None
-    if not args.no_fourier:
-        fourier = fourier_coupling(stream)
+    extras = {}
+    if not args.no_secondary:
+        extras = secondary(args, stream)
 
     e2e = None
     if not args.no_e2e:
@@ -573,10 +709,17 @@ def run_ours(args, wl, rank, world, local_rank):
                     c2.set_variant(l, True, vc)
             if split_level is not None:
                 c2.set_batch_split(split_level, split_frac)
-            res = c2.run_batch(alloc, seed0 + 101 + k)      # host sums of every level
-            est = sum(res[l][0].dp1 / res[l][0].n for l, m in enumerate(alloc) if m > 0)
-            d2h_k = 8 * mlmc_dk.sums_len(nq) * len(alloc) + 4
             h2d_k = c2.level_info(0).h2d_bytes
+            d2h_k = 8 * S * (L + 1) + 4
+            if learned is not None:
+                c2.surrogate_init(seed0 + 3)
+                c2.surrogate_params(theta)            # the trained network: host -> device
+                h2d_k += 4 * theta.size
+            res = c2.run_batch(batch_counts, seed0 + 101 + k)      # host sums of every level
+            if learned is not None:
+                for part, n in ((-1, learned[0]), (0, learned[1])):
+                    c2.run_surrogate(part, n, seed0 + 101 + k)
+                    d2h_k += 8 * S + 4
             c2.close()
             torch.cuda.synchronize()
             times.append(time.perf_counter() - t)
@@ -588,84 +731,143 @@ def run_ours(args, wl, rank, world, local_rank):
             tot = float(t.item())
         e2e = {"value": world * sample_steps * args.steps / tot, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * tot / args.steps,
-               "what": "mlmc_dk_init (FFT mean fields + pinned uploads) + mlmc_dk_run_batch (host sums) + free"}
-    else:
-        ctx.close()
+               "what": "mlmc_dk_init (mean fields + pinned uploads) + the trained network's parameters + "
+                       "mlmc_dk_run_batch (host sums) + mlmc_dk_run_surrogate (both parts) + free"}
+        ctx = None
 
     if rank != 0:
+        if ctx is not None:
+            ctx.close()
         return None
-    cpu = None
+    cpu, oerr = None, None
     if world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_rate(wl, alloc, args.cpu_budget)
+        # the oracle on a bounded sample of the step's own ids (seed of the first timed step),
+        # which also gives the per-sample error of the GPU path on those ids
+        cpu, outs = oracle_leg(wl, alloc, learned, args.cpu_budget, seed0 + 101, first0)
+        c3 = ctx or mlmc_dk.Context.from_workload(wl, stream=stream.cuda_stream)
+        oerr = oracle_error(c3, wl, outs, seed0 + 101, stream)
+        c3.close()
+        ctx = None
+    if ctx is not None:
+        ctx.close()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "i32 fixed-point state, f32 noise, f64 sums",
+        "scaling": "weak", "vs_baseline": None, "dtype": "i32 fixed-point state, f32 noise, f64 sums, bf16 network",
         "data": "synthetic",
-        "config": {"workload": wl.name, "levels": [i.n for i in info], "fine_steps": [i.M for i in info],
-                   "T": wl.T, "N": wl.N, "mu": wl.mu, "eps_rel": wl.eps_rel, "alloc": alloc,
-                   "sample_steps_per_step": sample_steps, "cell_steps_per_step": cell_steps,
-                   "l2": "512 MiB buffer zeroed between timed steps, outside the step events",
-                   "parallelism": f"{world} rank(s), disjoint sample ids per rank",
-                   "kernel_variants": [{"n": i.n, "C": i.lane_cols, "R": i.lane_rows, "cluster": i.cluster}
-                                       for i in info],
-                   "tune_s": tune_s,
-                   "batch_split": {"level": split_level, "fraction": split_frac,
-                                   "streamed_samples": split_samples, "tune_s": split_s}},
+        "config": dict(workload_config(wl, alloc, learned),
+                       sample_steps_per_step=sample_steps, cell_steps_per_step=cell_steps,
+                       l2="512 MiB buffer zeroed between timed steps, outside the step events",
+                       parallelism=f"{world} rank(s), disjoint sample ids per rank",
+                       kernels=[{"n": i.n, "band": bool(i.band), "bands": i.bands, "in_flight": i.in_flight,
+                                 "C": i.lane_cols, "R": i.lane_rows, "cluster": i.cluster} for i in info],
+                       tune_s=tune_s,
+                       batch_split={"level": split_level, "fraction": split_frac, "tune_s": split_s}),
         "cell_steps_per_s": world * cell_steps * args.steps / (total_ms * 1e-3),
         "gpu_launches": launches,
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clk,
+        "estimate": {"values": est.tolist(), "se": np.sqrt(var).tolist(), "oracle_error": oerr},
+        "oracle_error": oerr,
     }
     line["mlmc_s_to_eps"] = t_mlmc
-    line["mc_s_to_eps"] = mc["s"]
-    line["mlmc_speedup_vs_mc"] = mc["s"] / t_mlmc
+    line["mc_s_to_eps"] = m_mc * t_mc
+    line["mlmc_speedup_vs_mc"] = m_mc * t_mc / t_mlmc
     line["to_eps"] = to_eps
-    line["mc"] = mc
-    line["mlmc_adaptive_measured"] = adaptive
-    fin = info[Ls]
-    cf = closed_form_EP_cos1(fin.n, fin.tau, fin.M) if wl.rho0_kind == "sinsin" and wl.length == 1.0 else None
-    line["closed_form_EP_finest"] = {"value": cf, "estimate": to_eps["estimate"],
-                                     "note": "martingale-lemma E[P_L] if rho stayed positive; at the finest "
-                                             "level N h^2 = %.2g particles per cell, so it is a lower bound and "
-                                             "the gap is the positive-part effect" % (wl.N * (wl.length / fin.n) ** 2)}
-    line["streamed_stencil"] = streamed
-    line["theta_scheme"] = theta
-    line["fourier_coupling"] = fourier
-    if surrogate:
-        line["surrogate"] = surrogate
-        line["mlmc_surrogate_s_to_eps"] = surrogate["mlmc_s_to_eps_incl_training"]
+    if sur:
+        line["surrogate"] = sur
+        line["mlmc_surrogate_s_to_eps"] = sur["mlmc_s_to_eps_incl_training"]
+    line.update(extras)
     return line
 
 
+def secondary(args, stream):
+    """Secondary measurements: the 16^2..256^2 workload's batch (the previous
+    headline) with a measured Algorithm 1 run, the 512^2 large-grid stencil,
+    the theta-scheme and the Fourier-coupled kernels."""
+    out = {}
+    if not args.no_mlmc16:
+        out["mlmc16_256"] = mlmc16_batch(args, stream)
+    if not args.no_streamed:
+        out["large_grid_stencil"] = streamed_stencil(stream)
+    if not args.no_theta:
+        out["theta_scheme"] = theta_scheme(stream)
+    if not args.no_fourier:
+        out["fourier_coupling"] = fourier_coupling(stream)
+    return out
+
+
+def mlmc16_batch(args, stream):
+    """The 16^2..256^2 workload (N = 1e5, eps = 1e-3): its scaled eps-optimal
+    batch timed over three steps, and a complete Algorithm 1 run at eps = 1e-2
+    (levels added by the stopping test), both through the batch graph."""
+    import torch
+    from paper_2311_08872_gb300 import mlmc_dk, workloads
+    wl = workloads.get("mlmc16_256")
+    alloc = list(wl.alloc)
+    with mlmc_dk.Context.from_workload(wl, stream=stream.cuda_stream) as c:
+        c.tune(1)
+        info = [c.level_info(l) for l in range(wl.L_max + 1)]
+        steps = sum(m * i.M for m, i in zip(alloc, info))
+        sums = torch.zeros(wl.L_max + 1, mlmc_dk.sums_len(c.n_quant), dtype=torch.float64, device="cuda")
+        c.run_batch_dev(alloc, 0, 3, sums.data_ptr(), stream.cuda_stream)      # warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(3):
+            c.run_batch_dev(alloc, 1000 * (k + 1), 5 + k, sums.data_ptr(), stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 3
+        level_ms = c.batch_level_ms()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        r = c.estimate(args.adaptive_eps, relative=True, seed=wl.seed + 5)
+        torch.cuda.synchronize()
+        adaptive = {"eps_rel": args.adaptive_eps, "s": time.perf_counter() - t, "L": r.L,
+                    "M": [r.M[l] for l in range(r.L + 1)], "estimate": r.estimate, "variance": r.variance,
+                    "eps_abs": r.eps_abs, "converged": bool(r.converged), "cell_steps": r.cell_steps}
+    fin = info[-1]
+    return {"alloc": alloc, "ms_per_step": ms, "coupled_sample_steps_per_s": steps / (ms * 1e-3),
+            "cell_steps_per_s": sum(m * i.cost for m, i in zip(alloc, info)) / (ms * 1e-3),
+            "level_ms": level_ms, "kernels": [{"n": i.n, "band": bool(i.band), "cluster": i.cluster} for i in info],
+            "algorithm1_measured": adaptive,
+            "closed_form_EP_finest": closed_form_EP_cos1(fin.n, fin.tau, fin.M)}
+
+
 def run_reference(args, wl, rank, world):
+    """The reference arm: the FP64 oracle (there is no published implementation)
+    as it stands, on the host cores, on a bounded sample of the same workload
+    and step allocation, scaled to the step by level."""
     if rank != 0:
         return None
-    alloc = list(wl.alloc) if wl.alloc else None
-    if alloc is None:
+    if wl.alloc is None:
         return {"impl": "reference", "unavailable": "workload has no fixed allocation"}
-    alloc = alloc + [0] * (wl.L_max + 1 - len(alloc))
-    sample_steps, cell_steps = batch_units(wl, alloc)
+    alloc = list(wl.alloc) + [0] * (wl.L_max + 1 - len(wl.alloc))
+    learned = tuple(wl.alloc_learned) if (wl.alloc_learned and not args.no_surrogate) else None
+    M, fine, coarse = oracle_level_costs(wl)
+    sample_steps, cell_steps = step_units(fine, coarse, M, alloc, learned)
     budget = max(2.0, args.cpu_budget / 3)
-    for _ in range(args.warmup):
-        oracle_rate(wl, alloc, budget / 2)
+    for w in range(args.warmup):
+        oracle_leg(wl, alloc, learned, budget / 2, wl.seed + 17 + w, 0)
     vals, res = [], None
-    for _ in range(args.steps):
-        res = oracle_rate(wl, alloc, budget)
+    for k in range(args.steps):
+        res, _ = oracle_leg(wl, alloc, learned, budget, wl.seed + 101 + k, 0)
         vals.append(res["batch_cpu_s"])
     cpu_s = statistics.mean(vals)
     value = sample_steps / cpu_s
     cb = dict(res)
     cb["value"] = value
+    cfg = dict(workload_config(wl, alloc, learned), sample_steps_per_step=sample_steps,
+               cell_steps_per_step=cell_steps,
+               what="FP64 oracle (plain C) per coupled sample on the host cores; each step times a bounded sample "
+                    "of the step's allocation and scales it to the full step by level (learned level: the "
+                    "correction level's level-0 paths, network cost not counted)")
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * cpu_s, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl.name, "alloc": alloc, "sample_steps_per_step": sample_steps,
-                       "cell_steps_per_step": cell_steps,
-                       "what": "FP64 oracle (plain C) per coupled sample on the host cores; each step times a "
-                               "bounded sample of the batch and scales it to the full batch by level"},
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
             "cpu_baseline": cb,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 

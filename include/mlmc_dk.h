@@ -327,6 +327,15 @@ int mlmc_dk_run_level_static(const mlmc_dk_ctx* ctx, int32_t level, int32_t stre
                              int64_t n_samples, uint64_t seed, double* sums_dev, double* samples_dev,
                              unsigned int* err_dev, void* cuda_stream);
 
+/* Failure-detection test of the band kernel's bounded waits (the paper has no
+ * counterpart): one sample of `level` (>= 1) over at most 64 fine steps on the
+ * band kernel, with every wait limited to `polls` polls and band `stall_band`
+ * never publishing its edges, so that its neighbours' waits run out.  The
+ * kernel records the timeout, every CTA stops stepping, and the call returns
+ * MLMC_DK_ERR_TIMEOUT; the context stays usable.  MLMC_DK_ERR_UNSUPPORTED
+ * when the level does not run on the band kernel. */
+int mlmc_dk_band_wait_test(mlmc_dk_ctx* ctx, int32_t level, uint32_t polls, int32_t stall_band);
+
 /* Algorithm 1 (Section 7.1): start at L = L_start with `pilot` samples on
  * levels 0..L; repeat {run the missing samples (all levels of a round at once
  * through the multi-level batch, ids continuing each level's range from 0),

@@ -54,9 +54,9 @@ __device__ __forceinline__ unsigned ld_volatile(const unsigned* p) {
 }
 
 // Wait until *flag >= target (counters only grow).  Returns false after
-// kWaitPolls polls, or as soon as another CTA has recorded a timeout.
-__device__ bool wait_counter(const unsigned* flag, unsigned target, unsigned* err) {
-    for (unsigned it = 0; it < kWaitPolls; ++it) {
+// `polls` polls, or as soon as another CTA has recorded a timeout.
+__device__ bool wait_counter(const unsigned* flag, unsigned target, unsigned* err, unsigned polls) {
+    for (unsigned it = 0; it < polls; ++it) {
         if (static_cast<int>(ld_acquire(flag) - target) >= 0) return true;
         if ((it & 63u) == 63u && (ld_volatile(err) & kErrTimeout)) return false;
         __nanosleep(32);
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(kBandMaxThreads, 1) band_kernel(const KArgs a,
                             make_int4(qc[0][0], Gc1[0][0], qc[0][1], Gc1[0][1]);
                 }
                 __syncwarp();
-                if (lane == 0) {
+                if (lane == 0 && band != b.stall_band) {   // stall_band: failure-detection test only
                     __threadfence();
                     if (top) red_release_add(flags + (size_t)band * 2 + 0, 1u);
                     if (bot) red_release_add(flags + (size_t)band * 2 + 1, 1u);
@@ -246,8 +246,8 @@ __global__ void __launch_bounds__(kBandMaxThreads, 1) band_kernel(const KArgs a,
         if (top || bot) {
             if (lane == 0) {
                 bool ok = true;
-                if (top) ok = wait_counter(flags + (size_t)up * 2 + 1, (unsigned)(WPR * (m + 1)), a.err);
-                if (bot && ok) ok = wait_counter(flags + (size_t)dn * 2 + 0, (unsigned)(WPR * (m + 1)), a.err);
+                if (top) ok = wait_counter(flags + (size_t)up * 2 + 1, (unsigned)(WPR * (m + 1)), a.err, b.wait_polls);
+                if (bot && ok) ok = wait_counter(flags + (size_t)dn * 2 + 0, (unsigned)(WPR * (m + 1)), a.err, b.wait_polls);
                 if (!ok) sm.abort[par ^ 1] = 1;
             }
             __syncwarp();
@@ -562,6 +562,7 @@ cudaError_t band_run(const KArgs& k, BArgs b, const BandPlan& p, cudaStream_t st
     b.nb = p.nb;
     b.bmax = p.bmax;
     b.S = p.S;
+    if (b.wait_polls == 0) b.wait_polls = kWaitPolls;
     cudaError_t e;
     band_zero_kernel<<<64, 256, 0, st>>>(k.partials, (size_t)k.slot_stride * p.S);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

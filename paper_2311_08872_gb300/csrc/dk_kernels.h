@@ -133,6 +133,8 @@ struct BArgs {
     double* band_part;           // [S][nb][2 kMaxObs + 2]: per-band observable partials
     const double* phif64;        // FP64 test functions [n_obs][n^2] / [n_obs][(n/2)^2]
     const double* phic64;
+    unsigned wait_polls;         // polls before a wait gives up (0: the default, about a second or more)
+    int stall_band;              // -1; >= 0 only in the failure-detection test: that band never publishes
 };
 struct BandPlan {
     int supported;

@@ -374,7 +374,8 @@ int launch_streamed(mlmc_dk_ctx* c, int level, int stream_tag, int64_t first, in
 // Band-kernel level: each sample over t.bplan[mode].nb CTAs; `steps` > 0
 // truncates every sample to that many fine steps (used only to time variants).
 int launch_band(mlmc_dk_ctx* c, int level, int stream_tag, int64_t first, int64_t count, uint64_t seed,
-                double* sums_dev, double* samples_dev, cudaStream_t st, int steps = 0) {
+                double* sums_dev, double* samples_dev, cudaStream_t st, int steps = 0, unsigned wait_polls = 0,
+                int stall_band = -1) {
     const bool coupled = (stream_tag == 0) && level > 0;
     LevelTab& t = c->lv[level];
     const dk::BandPlan& p = t.bplan[coupled ? 1 : 0];
@@ -391,6 +392,8 @@ int launch_band(mlmc_dk_ctx* c, int level, int stream_tag, int64_t first, int64_
     b.n = t.n;
     b.coupled = coupled ? 1 : 0;
     b.steps = steps > 0 ? std::min(steps, t.M) : t.M;
+    b.wait_polls = wait_polls;
+    b.stall_band = stall_band;
     b.phif64 = t.d_phi64;
     b.phic64 = coupled ? c->lv[level - 1].d_phi64 : nullptr;
     if ((e = dk::band_run(k, b, p, st)) != cudaSuccess) return cuda_fail(c, e, "band kernel");
@@ -1165,6 +1168,21 @@ int mlmc_dk_run_level_static(const mlmc_dk_ctx* ctx, int32_t level, int32_t stre
     if ((e = dk::launch_reduce(scratch, n_slots, ctx->stride, sums_dev, st)) != cudaSuccess)
         return cuda_fail(c, e, "reduce kernel launch");
     return MLMC_DK_OK;
+}
+
+int mlmc_dk_band_wait_test(mlmc_dk_ctx* ctx, int32_t level, uint32_t polls, int32_t stall_band) {
+    if (!ctx) return fail(nullptr, MLMC_DK_ERR_INVALID, "null context");
+    if (level < 1 || level > ctx->L_max || polls == 0 || stall_band < 0)
+        return fail(ctx, MLMC_DK_ERR_INVALID, "band_wait_test: bad arguments");
+    LevelTab& t = ctx->lv[level];
+    if (!t.bplan[1].supported || !t.d_band || stall_band >= t.bplan[1].nb)
+        return fail(ctx, MLMC_DK_ERR_UNSUPPORTED, "band_wait_test: the level has no band kernel");
+    const int rc = launch_band(ctx, level, 0, 0, 1, 0x7465, ctx->d_sums, nullptr, ctx->stream, std::min(t.M, 64),
+                               polls, stall_band);
+    if (rc != MLMC_DK_OK) return rc;
+    const cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "band_wait_test");
+    return check_device_error(ctx);
 }
 
 }  // extern "C"

@@ -130,6 +130,7 @@ def lib() -> ctypes.CDLL:
         L.mlmc_dk_version.restype = ctypes.c_char_p
         L.mlmc_dk_run_level_static.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
                                                ctypes.c_int64, ctypes.c_uint64, vp, vp, vp, vp]
+        L.mlmc_dk_band_wait_test.argtypes = [vp, ctypes.c_int32, ctypes.c_uint32, ctypes.c_int32]
         L.mlmc_dk_run_batch_dev.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.c_int64, ctypes.c_uint64,
                                             vp, vp]
         L.mlmc_dk_run_batch.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.c_uint64, ctypes.POINTER(LevelSums)]
@@ -303,6 +304,10 @@ class Context:
                                               ctypes.c_void_p(sums_ptr), ctypes.c_void_p(samples_ptr or None),
                                               ctypes.c_void_p(err_ptr or None), ctypes.c_void_p(stream or None)),
                self._ctx)
+
+    def band_wait_test(self, level: int, polls: int, stall_band: int) -> int:
+        """Failure-detection test of the band kernel's bounded waits; returns the status code."""
+        return lib().mlmc_dk_band_wait_test(self._ctx, level, polls, stall_band)
 
     def run_batch_dev(self, counts, first: int, seed: int, sums_ptr: int, stream: int = 0):
         """All levels concurrently (CUDA graph); sums_ptr: device double[L_max+1][sums_len]."""

@@ -157,6 +157,8 @@ class Workload:
     M0: int = 0                     # >0 overrides M_0 = ceil(T / (mu h0^2))
     alloc: Optional[Tuple[int, ...]] = None   # fixed per-level sample counts of one benchmark step
     alloc_scale: int = 1            # the eps-optimal allocation is about alloc * alloc_scale
+    alloc_learned: Optional[Tuple[int, int]] = None  # with the learned level: (level below 0, correction level)
+                                    # counts of one step, in place of alloc[0]
     offset: float = 0.0             # grid points at (i + offset) h: 0 right-most, 1/2 symmetric coupling
     b0: float = 0.0                 # implicit weight of the time step (b1 = 1 - b0); 0 explicit Euler--Maruyama
     coupling: int = 0               # 0 Right-Most NN (h ratio 2), 1 Fourier (h ratio 3)
@@ -207,10 +209,15 @@ WORKLOADS: Dict[str, Workload] = {
     "lowdens32_512": Workload("lowdens32_512", 1.0, 32, 4, 0.02, 0.1, 1e5, "gauss", [COS1],
                               seed=2, eps_rel=2e-3,
                               note="low-density periodised Gaussian, levels 32^2..512^2"),
+    # alloc: the eps-optimal allocation for eps = 5e-4 relative (max over the 10
+    # quantities of Eq. opt_M_ell, from pilot variances and device times per
+    # sample on a GB300), divided by 2^20; alloc_learned: the same with the
+    # learned level below 0 for levels {below 0, correction}
     "large32_1024": Workload("large32_1024", 1.0, 32, 5, 0.05, 0.1, 1e6, "sinsin_cos",
                              [Observable("cos", (1, 0)), Observable("cos", (0, 1)),
                               Observable("cos", (1, 1)), Observable("cos", (2, 0))],
                              products=True, seed=4, eps_rel=5e-4,
+                             alloc=(12372, 566, 73, 17, 8, 5), alloc_scale=1 << 20, alloc_learned=(132504, 506),
                              note="levels 32^2..1024^2, four modes plus products"),
     "paper_reg": Workload("paper_reg", TWO_PI, 4, 5, 1.024, 1.024 / (TWO_PI / 4) ** 2, 2e9,
                           "paper_reg", [Observable("sin+sin")], seed=5, M0=1,

@@ -39,10 +39,12 @@ def _samples(ctx, dk, level, tag, first, count, seed):
 
 
 def _band_variant(ctx, level, coupled):
-    """Index of the band kernel among the level's variants (the last entry)."""
+    """Select the band kernel (the last variant) for the level's coupled or
+    fine-only kernel; level_info describes the coupled kernel of a level >= 1."""
     ctx.set_variant(level, coupled, ctx.level_info(level).n_variants - 1)
     d = ctx.level_info(level)
-    assert d.band == 1 and d.bands >= 2 and d.in_flight >= 1
+    if coupled or level == 0:
+        assert d.band == 1 and d.bands >= 2 and d.in_flight >= 1
     return d
 
 
@@ -70,15 +72,37 @@ def test_band_equals_register_kernels(dk, level, count):
 
 
 def test_band_many_waves(dk):
-    """More than two waves of 256^2 samples in flight, the last one ragged."""
+    """More than two waves of 256^2 samples in flight, the last one ragged,
+    against the streamed-state kernels forced onto the same level: both project
+    the integer states on FP64 test functions in FP64, so identical paths give
+    observables equal to FP64 summation order."""
     wl = W.get("mlmc16_256").with_(L_max=4, T=2.5e-4)
-    with dk.Context.from_workload(wl) as reg, dk.Context.from_workload(wl) as bnd:
+    with dk.Context.from_workload(wl, stream_from_n=256) as stm, dk.Context.from_workload(wl) as bnd:
         d = _band_variant(bnd, 4, True)
         count = 2 * d.in_flight + 5
-        _, a = _samples(reg, dk, 4, 0, 100, count, 7)
+        _, a = _samples(stm, dk, 4, 0, 100, count, 7)
         s, b = _samples(bnd, dk, 4, 0, 100, count, 7)
-        _compare(a, b, reg.n_obs, 1e-6)
+        _compare(a, b, bnd.n_obs, 1e-10)
         assert s[0] == count
+
+
+def test_band_256_matches_oracle(dk):
+    """The band kernel on the benchmark workload's 256^2 level (coupled with
+    128^2) over 1536 fine steps, sample by sample against the FP64 oracle."""
+    import oracle
+    wl = W.get("mlmc16_256").with_(T=0.0025)
+    with dk.Context.from_workload(wl) as ctx:
+        _band_variant(ctx, 4, True)
+        info = ctx.level_info(4)
+        _, samp = _samples(ctx, dk, 4, 0, 40, 4, 13)
+    lv = oracle.level_table(wl.length, wl.n0, wl.L_max, wl.T, wl.mu)
+    ol = oracle.level_inputs(wl.length, lv, wl.N, wl.rho0_all(), wl.phi_all(), 4, True)
+    ref = oracle.run_samples(ol, 13, range(40, 44), True, processes=4)
+    for col, key, yb in ((0, "Y_f", info.ybar_f[0]), (1, "Y_c", info.ybar_c[0])):
+        y = samp[:, col] + yb
+        yo = ref[key][:, 0]
+        rms = np.sqrt(np.mean((yo - yb) ** 2))
+        assert np.all(np.abs(y - yo) <= 1e-5 * np.maximum(np.abs(yo), rms)), (key, y - yo, rms)
 
 
 @pytest.mark.parametrize("name,kw,level,count", [
@@ -130,3 +154,18 @@ def test_batch_with_band_level(dk):
             ctx.run_level_dev(l, 0, 4, m, 12, ref.data_ptr(), 0, st)
             torch.cuda.synchronize()
             np.testing.assert_allclose(batch[l].cpu().numpy(), ref.cpu().numpy(), rtol=1e-12, atol=0)
+
+
+def test_band_bounded_wait_reports_timeout(dk):
+    """Failure detection without a fault: one band never publishes its edges,
+    its neighbours' waits (limited to 4096 polls) run out, the kernel records
+    the timeout and stops, the call returns MLMC_DK_ERR_TIMEOUT, and the same
+    context then runs correct samples."""
+    wl = W.get("mlmc16_256").with_(L_max=4, T=2.5e-4)
+    with dk.Context.from_workload(wl) as ctx, dk.Context.from_workload(wl, stream_from_n=256) as stm:
+        _band_variant(ctx, 4, True)
+        assert ctx.band_wait_test(4, 4096, 1) == dk.ERR_TIMEOUT
+        _, a = _samples(stm, dk, 4, 0, 0, 3, 9)
+        s, b = _samples(ctx, dk, 4, 0, 0, 3, 9)
+        _compare(a, b, ctx.n_obs, 1e-10)
+        assert s[0] == 3
