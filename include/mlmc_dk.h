@@ -348,6 +348,36 @@ int mlmc_dk_band_wait_test(mlmc_dk_ctx* ctx, int32_t level, uint32_t polls, int3
 int mlmc_dk_estimate(mlmc_dk_ctx* ctx, double eps, int32_t relative, uint64_t seed,
                      mlmc_dk_result* out);
 
+/* Algorithm 1 over several processes, host-only (no context, no GPU needed).
+ * The same algorithm as mlmc_dk_estimate (which runs it on one process with
+ * the multi-level batch): start at L = L_start with `pilot` (>= 2) samples on
+ * levels 0..L; every round, the missing samples of level l, ids
+ * next_l .. target_l - 1, are cut into `world` contiguous pieces and piece
+ * `rank` is run here by
+ *     run_round(user, L, first, count, sums):
+ *         count[l] samples of level l with ids first[l].. (0 <= l <= L_max;
+ *         count 0 for levels to skip); write their sums into sums
+ *         [(L_max + 1) * (2 + 12 n_quant)] in the layout of
+ *         mlmc_dk_run_level_dev (zeros for skipped levels; the buffer arrives
+ *         zeroed); return 0, or nonzero to stop with MLMC_DK_ERR_INVALID;
+ * then, with world > 1,
+ *     reduce(user, sums, L_max + 1, 2 + 12 n_quant):
+ *         combine the round's sums over all processes in place (sum; entry 1
+ *         of each level, the mass error, by max); return 0 on success.
+ * Every process then takes the same decisions (Eq. opt_M_ell with the
+ * costs cost[l] of one sample of level l, Eq. convergence_criterion with
+ * alpha = 2 and mesh ratio `ratio`), so the result does not depend on the
+ * number of processes up to FP64 summation order.  eps is absolute, or
+ * relative to the pilot estimate when `relative` is nonzero.  Fills
+ * estimate(s), variance, eps_abs, L, converged, M, E, V, C, cell_steps,
+ * var_pf and wall_s of *out.  Returns MLMC_DK_OK, MLMC_DK_NOT_CONVERGED
+ * (L_max reached) or MLMC_DK_ERR_INVALID. */
+typedef int (*mlmc_dk_round_fn)(void* user, int32_t L, const int64_t* first, const int64_t* count, double* sums);
+typedef int (*mlmc_dk_reduce_fn)(void* user, double* sums, int64_t n_levels, int64_t stride);
+int mlmc_dk_algorithm1(int32_t L_max, int32_t L_start, int64_t pilot, int32_t n_quant, const double* cost,
+                       double ratio, double eps, int32_t relative, int32_t rank, int32_t world,
+                       mlmc_dk_round_fn run_round, mlmc_dk_reduce_fn reduce, void* user, mlmc_dk_result* out);
+
 /* Choose kernel variant `variant` (0 .. n_variants-1, see mlmc_dk_level_info)
  * for level `level`'s coupled (coupled = 1, level >= 1) or fine-only kernel.
  * All variants compute the same fixed-point paths bit for bit (hence equal

@@ -138,12 +138,14 @@ struct BArgs {
 };
 struct BandPlan {
     int supported;
+    int fc;                      // fine columns per thread (4: 4 x 4 blocks, 8: 4 x 8 blocks)
     int nb, bmax, S, threads;
     size_t smem;
 };
-bool band_supported(int n);
-// Launch shape of the band kernel for n x n on this device (see dk_band.cu).
-cudaError_t band_plan(int n, bool coupled, BandPlan* out);
+bool band_supported(int n, int fc);
+// Launch shape of the band kernel build with 4 x fc thread blocks for n x n on
+// this device (see dk_band.cu); supported = 0 where that build does not exist.
+cudaError_t band_plan(int n, bool coupled, int fc, BandPlan* out);
 // Device bytes of the exchange buffers for `p`, and their layout.
 size_t band_bytes(int n, const BandPlan& p);
 void band_carve(BArgs* b, void* buf, int n, const BandPlan& p);

@@ -10,6 +10,7 @@
 #include <numeric>
 #include <random>
 #include <cstring>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -48,7 +49,7 @@ struct LevelTab {
     void* d_stream = nullptr;              // their state
     double* d_spart = nullptr;             // their per-slot partial sums [stride][S]
     int sel[2] = {0, 0};                   // variant in use for each mode
-    dk::BandPlan bplan[2] = {};            // band kernel launch shape per mode (fine only, coupled)
+    dk::BandPlan bplan[2][2] = {};         // band kernel launch shapes [mode: fine only, coupled][build: 4, 8 columns]
     void* d_band = nullptr;                // its exchange buffers
     double* d_bpart = nullptr;             // its per-slot partial sums [stride][S]
     float* d_rbar = nullptr;               // fluctuation state: noise-free path rho-bar^m, [M][n^2] FP32
@@ -378,7 +379,8 @@ int launch_band(mlmc_dk_ctx* c, int level, int stream_tag, int64_t first, int64_
                 int stall_band = -1) {
     const bool coupled = (stream_tag == 0) && level > 0;
     LevelTab& t = c->lv[level];
-    const dk::BandPlan& p = t.bplan[coupled ? 1 : 0];
+    const int fc = t.vi(coupled).band ? t.vi(coupled).band : (t.bplan[coupled ? 1 : 0][0].supported ? 4 : 8);
+    const dk::BandPlan& p = t.bplan[coupled ? 1 : 0][fc == 4 ? 0 : 1];
     cudaError_t e;
     if (count == 0) {
         e = cudaMemsetAsync(sums_dev, 0, sizeof(double) * c->stride, st);
@@ -948,24 +950,24 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
                     partials_need = std::max(partials_need, (size_t)(vi.max_ctas / vi.cluster) * vi.slots_per_cta * c->stride);
             }
         }
-        if (!c->fluct && !force_stream && dk::band_supported(t.n)) {
-            // band kernel: a sample over several CTAs; the default on streamed
-            // levels, a tuner candidate on register levels
+        if (!c->fluct && !force_stream && (dk::band_supported(t.n, 4) || dk::band_supported(t.n, 8))) {
+            // band kernels (4 x 4 and 4 x 8 thread blocks): a sample over several
+            // CTAs; the default on streamed levels, tuner candidates elsewhere
             size_t bytes = 0;
             int S_max = 0;
-            bool ok = true;
             for (int mode = 0; mode < 2; ++mode) {
                 if (mode == 1 && l == 0) continue;
-                if ((e = dk::band_plan(t.n, mode == 1, &t.bplan[mode])) != cudaSuccess) {
-                    mlmc_dk_free(c);
-                    return cuda_fail(nullptr, e, "band kernel setup");
+                for (int k = 0; k < 2; ++k) {
+                    if ((e = dk::band_plan(t.n, mode == 1, k == 0 ? 4 : 8, &t.bplan[mode][k])) != cudaSuccess) {
+                        mlmc_dk_free(c);
+                        return cuda_fail(nullptr, e, "band kernel setup");
+                    }
+                    if (!t.bplan[mode][k].supported) continue;
+                    bytes = std::max(bytes, dk::band_bytes(t.n, t.bplan[mode][k]));
+                    S_max = std::max(S_max, t.bplan[mode][k].S);
                 }
-                ok = ok && t.bplan[mode].supported;
-                if (!t.bplan[mode].supported) continue;
-                bytes = std::max(bytes, dk::band_bytes(t.n, t.bplan[mode]));
-                S_max = std::max(S_max, t.bplan[mode].S);
             }
-            if (ok) {
+            if (bytes > 0) {
                 if ((e = cudaMalloc(&t.d_band, bytes)) != cudaSuccess ||
                     (e = cudaMalloc(&t.d_bpart, sizeof(double) * c->stride * S_max)) != cudaSuccess) {
                     mlmc_dk_free(c);
@@ -973,20 +975,27 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
                 }
                 for (int mode = 0; mode < 2; ++mode) {
                     if (mode == 1 && l == 0) continue;
-                    const dk::BandPlan& p = t.bplan[mode];
-                    dk::VariantInfo vi{};
-                    vi.supported = 1;
-                    vi.band = 1;
-                    vi.bands = p.nb;
-                    vi.threads = p.threads;
-                    vi.cluster = 1;
-                    vi.slots_per_cta = 0;
-                    vi.smem = p.smem;
-                    vi.max_ctas = p.S * p.nb;
-                    vi.C = 2;
-                    vi.R = 1;
-                    t.vis[mode].push_back(vi);
-                    if (t.streamed) t.sel[mode] = (int)t.vis[mode].size() - 1;
+                    for (int k = 1; k >= 0; --k) {   // 4 x 8 blocks first: the default on streamed levels
+                        const dk::BandPlan& p = t.bplan[mode][k];
+                        if (!p.supported) continue;
+                        dk::VariantInfo vi{};
+                        vi.supported = 1;
+                        vi.band = p.fc;
+                        vi.bands = p.nb;
+                        vi.threads = p.threads;
+                        vi.cluster = 1;
+                        vi.slots_per_cta = 0;
+                        vi.smem = p.smem;
+                        vi.max_ctas = p.S * p.nb;
+                        vi.C = p.fc / 2;
+                        vi.R = 2;
+                        t.vis[mode].push_back(vi);
+                    }
+                    if (t.streamed) {
+                        // the first band variant after the streamed ones
+                        for (int v = 0; v < (int)t.vis[mode].size(); ++v)
+                            if (t.vis[mode][v].band) { t.sel[mode] = v; break; }
+                    }
                 }
             }
         }
@@ -1099,9 +1108,9 @@ int mlmc_dk_level_info(const mlmc_dk_ctx* ctx, int32_t level, mlmc_dk_level_desc
     out->cheb_steps = ctx->theta ? ctx->targs.K : 0;
     out->coupling = ctx->coupling;
     out->fluct = ctx->fluct;
-    out->band = vs.band;
+    out->band = vs.band ? 1 : 0;
     out->bands = vs.bands;
-    if (vs.band) out->in_flight = t.bplan[level > 0 ? 1 : 0].S;
+    if (vs.band) out->in_flight = t.bplan[level > 0 ? 1 : 0][vs.band == 4 ? 0 : 1].S;
     return MLMC_DK_OK;
 }
 
@@ -1175,8 +1184,9 @@ int mlmc_dk_band_wait_test(mlmc_dk_ctx* ctx, int32_t level, uint32_t polls, int3
     if (level < 1 || level > ctx->L_max || polls == 0 || stall_band < 0)
         return fail(ctx, MLMC_DK_ERR_INVALID, "band_wait_test: bad arguments");
     LevelTab& t = ctx->lv[level];
-    if (!t.bplan[1].supported || !t.d_band || stall_band >= t.bplan[1].nb)
-        return fail(ctx, MLMC_DK_ERR_UNSUPPORTED, "band_wait_test: the level has no band kernel");
+    const dk::VariantInfo& vi = t.vi(true);
+    if (!vi.band || !t.d_band || stall_band >= t.bplan[1][vi.band == 4 ? 0 : 1].nb)
+        return fail(ctx, MLMC_DK_ERR_UNSUPPORTED, "band_wait_test: the level's coupled kernel is not a band kernel");
     const int rc = launch_band(ctx, level, 0, 0, 1, 0x7465, ctx->d_sums, nullptr, ctx->stream, std::min(t.M, 64),
                                polls, stall_band);
     if (rc != MLMC_DK_OK) return rc;
@@ -1266,8 +1276,9 @@ int batch_dev(mlmc_dk_ctx* ctx, const int64_t* counts, const int64_t* firsts, ui
     // band-kernel levels first, each on its level's stream: their cooperative
     // grids are placed before the graph's kernels fill the remaining SMs
     bool any_band = false;
+    auto band_level = [&](int l) { return ctx->lv[l].vi(l > 0).band != 0; };
     for (int l = nl - 1; l >= 0; --l) {
-        if (!outside(l) || ctx->lv[l].streamed) continue;
+        if (!band_level(l)) continue;
         if (!any_band) {
             if ((e = cudaEventRecord(ctx->ev_fork, st)) != cudaSuccess) return cuda_fail(ctx, e, "band fork");
             any_band = true;
@@ -1284,7 +1295,7 @@ int batch_dev(mlmc_dk_ctx* ctx, const int64_t* counts, const int64_t* firsts, ui
     }
     if ((e = cudaGraphLaunch(ctx->gexec, st)) != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphLaunch");
     for (int l = nl - 1; l >= 0 && any_band; --l) {
-        if (!outside(l) || ctx->lv[l].streamed) continue;
+        if (!band_level(l)) continue;
         if ((e = cudaStreamWaitEvent(st, ctx->ev_join[l], 0)) != cudaSuccess) return cuda_fail(ctx, e, "band join");
     }
     if (any_split) {
@@ -1472,7 +1483,7 @@ int mlmc_dk_tune(mlmc_dk_ctx* ctx, int32_t repeats, double* seconds) {
                 int steps = t.M;
                 int64_t count;
                 if (vi.band) {
-                    count = t.bplan[mode].S;
+                    count = t.bplan[mode][vi.band == 4 ? 0 : 1].S;
                     steps = std::min(t.M, 1024);
                 } else if (t.streamed) {
                     count = t.inflight_v[v];
@@ -1562,94 +1573,80 @@ int mlmc_dk_plan_ratio(int32_t L, const int64_t* n, const double* s1, const doub
 
 namespace {
 
-// One round of Algorithm 1: need[l] samples with ids firsts[l].. on every level
-// through the batch graph, accumulated into sums[l][quantity] with each level's
-// own device span; next_sample follows.
-int run_round(mlmc_dk_ctx* ctx, const int64_t* need, const int64_t* firsts, uint64_t seed,
-              std::vector<std::vector<mlmc_dk_level_sums>>& sums) {
-    const int nl = ctx->L_max + 1;
-    const auto t0 = std::chrono::steady_clock::now();
-    int rc = batch_dev(ctx, need, firsts, seed, ctx->d_bsums, ctx->stream);
-    if (rc != MLMC_DK_OK) return rc;
-    cudaError_t e = cudaMemcpyAsync(ctx->h_bsums, ctx->d_bsums, sizeof(double) * ctx->stride * nl,
-                                    cudaMemcpyDeviceToHost, ctx->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "Algorithm 1 round");
-    if ((rc = check_device_error(ctx)) != MLMC_DK_OK) return rc;
-    const double wall = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    int active = 0;
-    for (int l = 0; l < nl; ++l) active += need[l] > 0;
-    for (int l = 0; l < nl; ++l) {
-        if (need[l] == 0) continue;
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, ctx->ev_lb[l], ctx->ev_le[l]) != cudaSuccess) {
-            cudaGetLastError();
-            ms = 0.f;
-        }
-        const LevelTab& f = ctx->lv[l];
-        double cost = (double)f.n * f.n * f.M;
-        if (l > 0) cost += (double)ctx->lv[l - 1].n * ctx->lv[l - 1].n * ctx->lv[l - 1].M;
-        accumulate(ctx, ctx->h_bsums + (size_t)l * ctx->stride, sums[l].data(), cost, wall / active, 1e-3 * ms, 2);
-        ctx->next_id[0][l] = firsts[l] + need[l];
-    }
-    return MLMC_DK_OK;
-}
+using RoundFn = std::function<int(int32_t L, const int64_t* first, const int64_t* count, double* sums)>;
+using ReduceFn = std::function<int(double* sums, int64_t n_levels, int64_t stride)>;
 
-}  // namespace
-
-extern "C" {
-
-int mlmc_dk_estimate(mlmc_dk_ctx* ctx, double eps, int32_t relative, uint64_t seed, mlmc_dk_result* out) {
-    if (!ctx || !out || !(eps > 0)) return fail(ctx, MLMC_DK_ERR_INVALID, "estimate: bad arguments");
-    const auto t0 = std::chrono::steady_clock::now();
-    *out = mlmc_dk_result{};
-    const int Q = ctx->n_quant;
-    std::vector<std::vector<mlmc_dk_level_sums>> sums(ctx->L_max + 1, std::vector<mlmc_dk_level_sums>(Q));
-    std::vector<int64_t> target(ctx->L_max + 1, 0);
-    std::fill(ctx->next_id[0].begin(), ctx->next_id[0].end(), 0);
-    int L = ctx->L_start;
-    for (int l = 0; l <= L; ++l) target[l] = ctx->pilot;
+// Algorithm 1 (Section 7.1), the one implementation behind mlmc_dk_estimate
+// (one process, the multi-level batch on the GPU) and mlmc_dk_algorithm1 (any
+// sampler, several processes): start at L = L_start with `pilot` samples on
+// levels 0..L; repeat {run the missing samples of every level -- each level's
+// new ids cut into `world` contiguous pieces, piece `rank` run here, the
+// round's sums combined over the processes by `reduce` --, set targets by
+// Eq. (opt_M_ell), once no level needs more than 1% more samples apply Eq.
+// (convergence_criterion) with alpha = 2 and the hierarchy's mesh ratio, and
+// add a level if it fails}.  The first quantity drives the allocation; eps is
+// absolute, or relative to the pilot estimate.  Sums use the device layout
+// [level][2 + 12 n_quant] (entry 0 count, entry 1 max mass error).
+int algorithm1_core(int32_t L_max, int32_t L_start, int64_t pilot, int32_t n_quant, const double* cost, double ratio,
+                    double eps, int32_t relative, int32_t rank, int32_t world, const RoundFn& run,
+                    const ReduceFn& reduce, mlmc_dk_result* out, std::vector<double>* totals, std::string* err) {
+    const int nl = L_max + 1;
+    const int64_t stride = 2 + (int64_t)dk::kNSum * n_quant;
+    std::vector<double> tot((size_t)nl * stride, 0.0), rnd((size_t)nl * stride);
+    std::vector<int64_t> target(nl, 0), next(nl, 0), first(nl, 0), count(nl, 0), need(nl, 0);
+    int L = std::min(L_start, L_max);
+    for (int l = 0; l <= L; ++l) target[l] = pilot;
     double eps_abs = relative ? -1.0 : eps;
     int status = MLMC_DK_OK, converged = 0;
-    std::vector<double> cost(ctx->L_max + 1);
-    for (int l = 0; l <= ctx->L_max; ++l) {
-        mlmc_dk_level_desc li;
-        mlmc_dk_level_info(ctx, l, &li);
-        cost[l] = li.cost;
-    }
     for (int iter = 0; iter < 1000; ++iter) {
-        {
-            // the round's missing samples of every level at once: the levels run
-            // concurrently in the batch graph, ids continuing each level's range
-            std::vector<int64_t> need(ctx->L_max + 1, 0), firsts(ctx->L_max + 1, 0);
-            bool any = false;
-            for (int l = 0; l <= L; ++l) {
-                firsts[l] = sums[l][0].n;
-                need[l] = std::max<int64_t>(0, target[l] - sums[l][0].n);
-                any = any || need[l] > 0;
+        bool any = false;
+        for (int l = 0; l < nl; ++l) {
+            need[l] = l <= L ? std::max<int64_t>(0, target[l] - next[l]) : 0;
+            const int64_t base = need[l] / world, extra = need[l] % world;
+            count[l] = base + (rank < extra ? 1 : 0);
+            first[l] = next[l] + rank * base + std::min<int64_t>(rank, extra);
+            any = any || need[l] > 0;
+        }
+        if (any) {
+            std::fill(rnd.begin(), rnd.end(), 0.0);
+            int rc = run(L, first.data(), count.data(), rnd.data());
+            if (rc != MLMC_DK_OK) return rc;
+            if (world > 1 && reduce && (rc = reduce(rnd.data(), nl, stride)) != MLMC_DK_OK) {
+                *err = "Algorithm 1: the reduction over processes failed";
+                return rc;
             }
-            if (any) {
-                const int rc = run_round(ctx, need.data(), firsts.data(), seed, sums);
-                if (rc != MLMC_DK_OK) return rc;
+            for (int l = 0; l < nl; ++l) {
+                for (int64_t e = 0; e < stride; ++e) {
+                    double& t = tot[(size_t)l * stride + e];
+                    const double r = rnd[(size_t)l * stride + e];
+                    t = e == 1 ? std::max(t, r) : t + r;
+                }
+                next[l] += need[l];
             }
         }
         int64_t n[MLMC_DK_MAX_LEVELS];
         double s1[MLMC_DK_MAX_LEVELS], s2[MLMC_DK_MAX_LEVELS];
         for (int l = 0; l <= L; ++l) {
-            n[l] = sums[l][0].n;
-            s1[l] = sums[l][0].dp1;
-            s2[l] = sums[l][0].dp2;
+            n[l] = (int64_t)std::llround(tot[(size_t)l * stride]);
+            s1[l] = tot[(size_t)l * stride + 2];
+            s2[l] = tot[(size_t)l * stride + 3];
         }
         if (eps_abs < 0) {
             double mu = 0;
             for (int l = 0; l <= L; ++l) mu += s1[l] / (double)n[l];
             eps_abs = eps * std::fabs(mu);
-            if (!(eps_abs > 0)) return fail(ctx, MLMC_DK_ERR_INVALID, "relative eps with a zero pilot estimate");
+            if (!(eps_abs > 0)) {
+                *err = "relative eps with a zero pilot estimate";
+                return MLMC_DK_ERR_INVALID;
+            }
         }
         int64_t tgt[MLMC_DK_MAX_LEVELS];
         int32_t conv = 0;
-        int rc = plan_ratio(L, n, s1, s2, cost.data(), eps_abs, tgt, &conv, ctx->coupling == 1 ? 3.0 : 2.0);
-        if (rc != MLMC_DK_OK) return fail(ctx, rc, g_init_error);
+        const int rc = plan_ratio(L, n, s1, s2, cost, eps_abs, tgt, &conv, ratio);
+        if (rc != MLMC_DK_OK) {
+            *err = g_init_error;
+            return rc;
+        }
         bool more = false;
         for (int l = 0; l <= L; ++l) {
             target[l] = std::max(target[l], tgt[l]);
@@ -1657,34 +1654,113 @@ int mlmc_dk_estimate(mlmc_dk_ctx* ctx, double eps, int32_t relative, uint64_t se
         }
         if (more) continue;
         if (conv) { converged = 1; break; }
-        if (L == ctx->L_max) { status = MLMC_DK_NOT_CONVERGED; break; }
+        if (L == L_max) { status = MLMC_DK_NOT_CONVERGED; break; }
         ++L;
-        target[L] = ctx->pilot;
+        target[L] = pilot;
     }
     out->L = L;
     out->converged = converged;
     out->eps_abs = eps_abs;
-    for (int q = 0; q < Q && q < MLMC_DK_MAX_QUANT; ++q) {
+    for (int q = 0; q < n_quant && q < MLMC_DK_MAX_QUANT; ++q) {
         double est = 0;
-        for (int l = 0; l <= L; ++l) est += sums[l][q].dp1 / (double)sums[l][q].n;
+        for (int l = 0; l <= L; ++l) est += tot[(size_t)l * stride + 2 + dk::kNSum * q] / tot[(size_t)l * stride];
         out->estimates[q] = est;
     }
     out->estimate = out->estimates[0];
+    out->variance = 0.0;
     for (int l = 0; l <= L; ++l) {
-        const mlmc_dk_level_sums& s = sums[l][0];
-        const double m = (double)s.n;
-        out->M[l] = s.n;
-        out->E[l] = s.dp1 / m;
-        out->V[l] = std::max(0.0, (s.dp2 - s.dp1 * s.dp1 / m) / (m - 1.0));
+        const double* t = tot.data() + (size_t)l * stride;
+        const double m = t[0];
+        out->M[l] = (int64_t)std::llround(m);
+        out->E[l] = t[2] / m;
+        out->V[l] = std::max(0.0, (t[3] - t[2] * t[2] / m) / (m - 1.0));
         out->C[l] = cost[l];
         out->variance += out->V[l] / m;
-        out->sample_steps += m * ctx->lv[l].M;
         out->cell_steps += m * cost[l];
-        out->kernel_s[l] = s.kernel_s;
-        out->var_pf[l] = std::max(0.0, (s.pf2 - s.pf1 * s.pf1 / m) / (m - 1.0));
-        out->launches += s.launches;
-        out->d2h_bytes += s.d2h_bytes;
+        out->var_pf[l] = std::max(0.0, (t[7] - t[6] * t[6] / m) / (m - 1.0));
     }
+    if (totals) totals->swap(tot);
+    return status;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mlmc_dk_algorithm1(int32_t L_max, int32_t L_start, int64_t pilot, int32_t n_quant, const double* cost,
+                       double ratio, double eps, int32_t relative, int32_t rank, int32_t world,
+                       mlmc_dk_round_fn run_round, mlmc_dk_reduce_fn reduce, void* user, mlmc_dk_result* out) {
+    if (L_max < 0 || L_max >= MLMC_DK_MAX_LEVELS || L_start < 0 || pilot < 2 || n_quant < 1 ||
+        n_quant > MLMC_DK_MAX_QUANT || !cost || !(ratio > 1.0) || !(eps > 0) || world < 1 || rank < 0 ||
+        rank >= world || !run_round || !out || (world > 1 && !reduce))
+        return fail(nullptr, MLMC_DK_ERR_INVALID, "algorithm1: bad arguments");
+    *out = mlmc_dk_result{};
+    const auto t0 = std::chrono::steady_clock::now();
+    std::string err;
+    const RoundFn run = [&](int32_t L, const int64_t* first, const int64_t* count, double* sums) {
+        const int rc = run_round(user, L, first, count, sums);
+        if (rc != 0) err = "Algorithm 1: the round callback failed";
+        return rc == 0 ? MLMC_DK_OK : MLMC_DK_ERR_INVALID;
+    };
+    const ReduceFn red = [&](double* sums, int64_t nl, int64_t stride) {
+        return reduce(user, sums, nl, stride) == 0 ? MLMC_DK_OK : MLMC_DK_ERR_INVALID;
+    };
+    const int rc = algorithm1_core(L_max, L_start, pilot, n_quant, cost, ratio, eps, relative, rank, world, run, red,
+                                   out, nullptr, &err);
+    if (rc < 0) return fail(nullptr, rc, err);
+    out->wall_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return rc;
+}
+
+int mlmc_dk_estimate(mlmc_dk_ctx* ctx, double eps, int32_t relative, uint64_t seed, mlmc_dk_result* out) {
+    if (!ctx || !out || !(eps > 0)) return fail(ctx, MLMC_DK_ERR_INVALID, "estimate: bad arguments");
+    const auto t0 = std::chrono::steady_clock::now();
+    *out = mlmc_dk_result{};
+    const int nl = ctx->L_max + 1;
+    std::fill(ctx->next_id[0].begin(), ctx->next_id[0].end(), 0);
+    std::vector<double> cost(nl), kernel_s(nl, 0.0);
+    for (int l = 0; l < nl; ++l) {
+        mlmc_dk_level_desc li;
+        mlmc_dk_level_info(ctx, l, &li);
+        cost[l] = li.cost;
+    }
+    int64_t launches = 0, d2h = 0;
+    // one round: the missing samples of every level at once through the
+    // multi-level batch (the levels run concurrently), ids continuing each
+    // level's range
+    const RoundFn run = [&](int32_t, const int64_t* first, const int64_t* count, double* sums) {
+        int rc = batch_dev(ctx, count, first, seed, ctx->d_bsums, ctx->stream);
+        if (rc != MLMC_DK_OK) return rc;
+        cudaError_t e = cudaMemcpyAsync(sums, ctx->d_bsums, sizeof(double) * ctx->stride * nl,
+                                        cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "Algorithm 1 round");
+        if ((rc = check_device_error(ctx)) != MLMC_DK_OK) return rc;
+        for (int l = 0; l < nl; ++l) {
+            if (count[l] == 0) continue;
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, ctx->ev_lb[l], ctx->ev_le[l]) != cudaSuccess) {
+                cudaGetLastError();
+                ms = 0.f;
+            }
+            kernel_s[l] += 1e-3 * ms;
+            launches += 2;
+            d2h += (int64_t)(sizeof(double) * ctx->stride + sizeof(unsigned));
+            ctx->next_id[0][l] = first[l] + count[l];
+        }
+        return MLMC_DK_OK;
+    };
+    std::string err;
+    const int status = algorithm1_core(ctx->L_max, ctx->L_start, ctx->pilot, ctx->n_quant, cost.data(),
+                                       ctx->coupling == 1 ? 3.0 : 2.0, eps, relative, 0, 1, run, nullptr, out,
+                                       nullptr, &err);
+    if (status < 0) return err.empty() ? status : fail(ctx, status, err);
+    for (int l = 0; l <= out->L; ++l) {
+        out->sample_steps += (double)out->M[l] * ctx->lv[l].M;
+        out->kernel_s[l] = kernel_s[l];
+    }
+    out->launches = launches;
+    out->d2h_bytes = d2h;
     out->wall_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return status;
 }

@@ -54,72 +54,33 @@ def merge_sums(a: np.ndarray, b: np.ndarray) -> np.ndarray:
     return out
 
 
-def estimate(run_level, L_max: int, eps: float, cost, plan, width: int, *, relative: bool = True,
-             pilot: int = 256, L_start: int = 2, world: int = 1, rank: int = 0, reduce=None,
-             max_iter: int = 1000):
-    """Algorithm 1 (Section 7.1) with the samples of every round shared by the ranks.
+def estimate(run_level, L_max: int, eps: float, cost, width: int, *, ratio: float = 2.0, relative: bool = True,
+             pilot: int = 256, L_start: int = 2, world: int = 1, rank: int = 0, reduce=None):
+    """Algorithm 1 (Section 7.1) with the samples of every round shared by the
+    ranks: the library's mlmc_dk_algorithm1 drives it (targets, stopping test
+    and estimator are computed there, identically on every rank).
 
     run_level(level, first_id, count) -> this rank's sums of `count` coupled
     samples with ids first_id.. (float64 [width], the device sums layout,
-    width = 2 + 12 n_quant); cost[l]: cost of one sample of level l;
-    plan(n, s1, s2, cost, eps_abs) -> (targets, converged): the host step of
-    Eq. (opt_M_ell) and Eq. (convergence_criterion) (mlmc_dk.plan);
-    reduce(local) -> global sums over ranks (allreduce_sums; unused on one
-    rank).  Each round the missing samples of level l, ids next[l] ..
-    target[l]-1, are cut into `world` contiguous pieces and piece `rank` runs
-    here; the union over ranks is the id range a single rank would run, so
+    width = 2 + 12 n_quant); cost[l]: cost of one sample of level l; ratio:
+    the hierarchy's mesh ratio (2 NN, 3 Fourier); reduce(local) -> global sums
+    over ranks (allreduce_sums; required when world > 1).  The union over the
+    ranks of each round's pieces is the id range a single rank would run, so
     decisions and estimate do not depend on the number of ranks (up to FP64
-    summation order).  The first quantity drives the allocation; eps is
-    relative to the pilot estimate when `relative` (frozen after the pilot).
-    Returns the estimate, its variance, L, samples per level, eps_abs,
-    convergence and the per-level global sums.
-    """
-    if pilot <= 0:
-        raise ValueError("pilot must be positive")
-    L = min(L_start, L_max)
-    sums = np.zeros((L_max + 1, width))
-    nxt = [0] * (L_max + 1)
-    target = [pilot if l <= L else 0 for l in range(L_max + 1)]
-    eps_abs = None if relative else eps
-    converged = False
-    for _ in range(max_iter):
-        rnd = np.zeros((L_max + 1, width))
-        for l in range(L + 1):
-            need = target[l] - nxt[l]
-            if need <= 0:
-                continue
-            base, extra = divmod(need, world)
-            cnt = base + (1 if rank < extra else 0)
-            if cnt > 0:
-                rnd[l] = run_level(l, nxt[l] + rank * base + min(rank, extra), cnt)
-            nxt[l] += need
-        if reduce is not None and world > 1:
-            rnd = reduce(rnd)
-        sums = merge_sums(sums, rnd)
-        n = [int(round(sums[l, 0])) for l in range(L + 1)]
-        s1 = [float(sums[l, 2]) for l in range(L + 1)]
-        s2 = [float(sums[l, 3]) for l in range(L + 1)]
-        if eps_abs is None:
-            eps_abs = eps * abs(sum(a / b for a, b in zip(s1, n)))
-            if not eps_abs > 0:
-                raise ValueError("relative eps with a zero pilot estimate")
-        tgt, conv = plan(n, s1, s2, list(cost[:L + 1]), eps_abs)
-        more = False
-        for l in range(L + 1):
-            target[l] = max(target[l], int(tgt[l]))
-            if target[l] - n[l] > 0.01 * n[l]:
-                more = True
-        if more:
-            continue
-        if conv:
-            converged = True
-            break
-        if L == L_max:
-            break
-        L += 1
-        target[L] = pilot
-    n = sums[:L + 1, 0]
-    est = float(np.sum(sums[:L + 1, 2] / n))
-    var = float(np.sum((sums[:L + 1, 3] - sums[:L + 1, 2] ** 2 / n) / (n - 1) / n))
-    return {"estimate": est, "variance": var, "L": L, "M": [int(x) for x in n], "eps_abs": eps_abs,
-            "converged": converged, "sums": sums[:L + 1]}
+    summation order).  Returns the estimate, its variance, L, samples per
+    level, eps_abs and convergence."""
+    from . import mlmc_dk
+
+    n_quant = (width - 2) // mlmc_dk.NSUM
+
+    def run_round(L, first, count):
+        out = np.zeros((L_max + 1, width))
+        for l in range(L_max + 1):
+            if count[l] > 0:
+                out[l] = run_level(l, first[l], count[l])
+        return out
+
+    r = mlmc_dk.algorithm1(run_round, reduce, L_max, n_quant, cost, eps, ratio=ratio, relative=relative,
+                           pilot=pilot, L_start=L_start, rank=rank, world=world)
+    return {"estimate": r.estimate, "variance": r.variance, "L": r.L, "M": [int(r.M[l]) for l in range(r.L + 1)],
+            "eps_abs": r.eps_abs, "converged": bool(r.converged)}

@@ -90,6 +90,12 @@ class Result(ctypes.Structure):
     ]
 
 
+# callbacks of mlmc_dk_algorithm1
+ROUND_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
+                            ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double))
+REDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int64,
+                             ctypes.c_int64)
+
 _LIB = None
 
 
@@ -130,6 +136,9 @@ def lib() -> ctypes.CDLL:
         L.mlmc_dk_version.restype = ctypes.c_char_p
         L.mlmc_dk_run_level_static.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
                                                ctypes.c_int64, ctypes.c_uint64, vp, vp, vp, vp]
+        L.mlmc_dk_algorithm1.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, _dp,
+                                         ctypes.c_double, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_int32, ROUND_FN, REDUCE_FN, vp, ctypes.POINTER(Result)]
         L.mlmc_dk_band_wait_test.argtypes = [vp, ctypes.c_int32, ctypes.c_uint32, ctypes.c_int32]
         L.mlmc_dk_run_batch_dev.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.c_int64, ctypes.c_uint64,
                                             vp, vp]
@@ -205,6 +214,49 @@ def noise_dev(seed: int, level: int, stream_tag: int, sample: int, m: int, n: in
     """Normals / raw Philox words of one fine step into device memory."""
     _check(lib().mlmc_dk_noise_dev(seed, level, stream_tag, sample, m, n, ctypes.c_void_p(z_ptr or None),
                                    ctypes.c_void_p(raw_ptr or None), ctypes.c_void_p(stream or None)))
+
+
+def algorithm1(run_round, reduce, L_max: int, n_quant: int, cost: Sequence[float], eps: float, *,
+               ratio: float = 2.0, relative: bool = True, pilot: int = 256, L_start: int = 2, rank: int = 0,
+               world: int = 1) -> Result:
+    """mlmc_dk_algorithm1: Algorithm 1 (Section 7.1) in the library with this
+    process's share of every round run by run_round(L, first, count) -> numpy
+    sums [(L_max + 1), 2 + 12 n_quant] and the round's sums combined over the
+    processes by reduce(sums) -> sums (used when world > 1)."""
+    stride = 2 + NSUM * n_quant
+    nl = L_max + 1
+    errors = []
+
+    def _round(_user, L, first, count, sums):
+        try:
+            f = [first[l] for l in range(nl)]
+            c = [count[l] for l in range(nl)]
+            out = np.asarray(run_round(int(L), f, c), dtype=np.float64).reshape(nl, stride)
+            ctypes.memmove(sums, out.ctypes.data, out.nbytes)
+            return 0
+        except Exception as e:           # reported after the call
+            errors.append(e)
+            return 1
+
+    def _reduce(_user, sums, n_levels, width):
+        try:
+            arr = np.ctypeslib.as_array(sums, shape=(int(n_levels) * int(width),)).copy()
+            red = np.asarray(reduce(arr.reshape(int(n_levels), int(width))), dtype=np.float64)
+            ctypes.memmove(sums, red.ctypes.data, red.nbytes)
+            return 0
+        except Exception as e:
+            errors.append(e)
+            return 1
+
+    rf, df = ROUND_FN(_round), REDUCE_FN(_reduce)
+    c = (ctypes.c_double * nl)(*[float(x) for x in cost])
+    r = Result()
+    rc = lib().mlmc_dk_algorithm1(L_max, L_start, pilot, n_quant, c, ratio, eps, int(relative), rank, world, rf, df,
+                                  None, ctypes.byref(r))
+    if errors:
+        raise errors[0]
+    _check(rc, None, allow=(OK, NOT_CONVERGED))
+    return r
 
 
 def plan(n: Sequence[int], s1: Sequence[float], s2: Sequence[float], cost: Sequence[float], eps: float,

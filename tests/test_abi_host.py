@@ -226,3 +226,81 @@ def test_fourier_coupling_config_checks(dk):
         with pytest.raises(dk.MLMCError) as e:
             ctx(6, 2, coupling=1)
         assert e.value.code == dk.ERR_CUDA
+
+
+def _oracle_round(wl):
+    """Round sampler from the FP64 oracle: sums in the device layout."""
+    levels = oracle.level_table(wl.length, wl.n0, wl.L_max, wl.T, wl.mu, wl.M0)
+    rho0, phi = wl.rho0_all(), wl.phi_all()
+    ybar = [oracle.inner_h(oracle.mean_field(l.n, l.h, l.tau, l.M, rho0[l.level]), phi[l.level][0], l.h)
+            for l in levels]
+
+    def dP(l, first, count):
+        ol = oracle.level_inputs(wl.length, levels, wl.N, rho0, phi, l, l > 0)
+        r = oracle.run_samples(ol, wl.seed, range(first, first + count), l > 0)
+        pf = oracle.observable_P(wl.N, r["Y_f"][:, :1], [ybar[l]])[:, 0]
+        pc = oracle.observable_P(wl.N, r["Y_c"][:, :1], [ybar[l - 1]])[:, 0] if l else np.zeros(count)
+        return pf, pc
+
+    cost = [levels[l].n ** 2 * levels[l].M + (levels[l - 1].n ** 2 * levels[l - 1].M if l else 0)
+            for l in range(len(levels))]
+    return dP, cost
+
+
+def test_algorithm1_in_the_library_matches_the_oracles_statement(dk):
+    """mlmc_dk_algorithm1 (the library's Algorithm 1, Section 7.1) with oracle
+    samples, against Algorithm 1 written out with the oracle's Eq. (opt_M_ell),
+    Eq. (convergence_criterion) and Eq. (MLMCEstimator) on the same samples:
+    the same levels, sample counts and estimate."""
+    from paper_2311_08872_gb300 import workloads as W
+    wl = W.get("mlmc16_256").with_(n0=8, L_max=3, T=0.005, N=1e5)
+    dP, cost = _oracle_round(wl)
+    cache = {}
+
+    def samples(l, first, count):
+        pf, pc = dP(l, first, count)
+        for i in range(count):
+            cache[(l, first + i)] = (pf[i], pc[i])
+        return pf, pc
+
+    def run_round(L, first, count):
+        out = np.zeros((wl.L_max + 1, 14))
+        for l in range(wl.L_max + 1):
+            if count[l] > 0:
+                pf, pc = samples(l, first[l], count[l])
+                d = pf - pc
+                out[l, :10] = [count[l], 0.0, d.sum(), (d ** 2).sum(), (d ** 3).sum(), (d ** 4).sum(),
+                               pf.sum(), (pf ** 2).sum(), pc.sum(), (pc ** 2).sum()]
+        return out
+
+    r = dk.algorithm1(run_round, None, wl.L_max, 1, cost, 0.03, pilot=64, L_start=2)
+    # the same algorithm from the oracle's formulas, on the cached samples
+    L, target, n = 2, [64, 64, 64, 0], [0, 0, 0, 0]
+    eps_abs = None
+    while True:
+        for l in range(L + 1):
+            n[l] = max(n[l], target[l])
+        d = [np.array([cache[(l, i)][0] - cache[(l, i)][1] for i in range(n[l])]) for l in range(L + 1)]
+        E = [x.mean() for x in d]
+        V = [x.var(ddof=1) for x in d]
+        if eps_abs is None:
+            eps_abs = 0.03 * abs(sum(E))
+        opt = oracle.mlmc_optimal_samples(V, cost[:L + 1], eps_abs)
+        more = False
+        for l in range(L + 1):
+            target[l] = max(target[l], opt[l], n[l])
+            if target[l] - n[l] > 0.01 * n[l]:
+                more = True
+        if more:
+            if any((l, target[l] - 1) not in cache for l in range(L + 1)):
+                break        # the library stopped earlier than this statement would: fails below
+            continue
+        if oracle.mlmc_converged(E, eps_abs) or L == wl.L_max:
+            break
+        L += 1
+        target[L] = 64
+    assert r.L == L
+    assert [r.M[l] for l in range(L + 1)] == n[:L + 1]
+    est = oracle.mlmc_estimator([x.sum() for x in d], [x.size for x in d])
+    assert r.estimate == pytest.approx(est, rel=1e-12)
+    assert r.eps_abs == pytest.approx(eps_abs, rel=1e-12)

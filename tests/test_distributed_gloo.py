@@ -86,11 +86,6 @@ def _small_workload(fourier=False):
     return W.get("mlmc16_256").with_(n0=8, L_max=3, T=0.005, N=1e5)
 
 
-def _plan(wl):
-    from paper_2311_08872_gb300 import mlmc_dk
-    return lambda n, s1, s2, cost, eps: mlmc_dk.plan(n, s1, s2, cost, eps, ratio=float(wl.ratio))
-
-
 def _estimate_worker(rank, world, port, out, fourier=False):
     import torch.distributed as dist
     from paper_2311_08872_gb300 import distributed as D
@@ -102,8 +97,8 @@ def _estimate_worker(rank, world, port, out, fourier=False):
     try:
         wl = _small_workload(fourier)
         run_level, cost = _oracle_sampler(wl)
-        r = D.estimate(run_level, wl.L_max, 0.03, cost, _plan(wl), 14, pilot=64, world=world, rank=rank,
-                       reduce=D.allreduce_sums)
+        r = D.estimate(run_level, wl.L_max, 0.03, cost, 14, ratio=float(wl.ratio), pilot=64, world=world,
+                       rank=rank, reduce=D.allreduce_sums)
         out.put((rank, r["estimate"], r["variance"], r["L"], r["M"], r["converged"]))
     finally:
         dist.destroy_process_group()
@@ -119,7 +114,7 @@ def test_algorithm1_across_two_gloo_ranks_matches_one_rank(fourier):
 
     wl = _small_workload(fourier)
     run_level, cost = _oracle_sampler(wl)
-    ref = D.estimate(run_level, wl.L_max, 0.03, cost, _plan(wl), 14, pilot=64)
+    ref = D.estimate(run_level, wl.L_max, 0.03, cost, 14, ratio=float(wl.ratio), pilot=64)
     assert ref["converged"] or ref["L"] == wl.L_max
     ctx = mp.get_context("spawn")
     q = ctx.Queue()

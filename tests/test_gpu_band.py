@@ -38,10 +38,18 @@ def _samples(ctx, dk, level, tag, first, count, seed):
     return sums.cpu().numpy(), samp.cpu().numpy()
 
 
-def _band_variant(ctx, level, coupled):
-    """Select the band kernel (the last variant) for the level's coupled or
-    fine-only kernel; level_info describes the coupled kernel of a level >= 1."""
-    ctx.set_variant(level, coupled, ctx.level_info(level).n_variants - 1)
+def _band_variants(ctx, level):
+    """Indices of the band-kernel builds among the level's variants (the last
+    ones: 4 x 8 thread blocks where the grid allows them, then 4 x 4)."""
+    n = ctx.level_info(level).n_variants
+    return [v for v in range(n) if v >= n - (2 if ctx.level_info(level).n >= 256 else 1)]
+
+
+def _band_variant(ctx, level, coupled, v=None):
+    """Select a band-kernel build (default: the last variant) for the level's
+    coupled or fine-only kernel; level_info describes the coupled kernel of a
+    level >= 1."""
+    ctx.set_variant(level, coupled, ctx.level_info(level).n_variants - 1 if v is None else v)
     d = ctx.level_info(level)
     if coupled or level == 0:
         assert d.band == 1 and d.bands >= 2 and d.in_flight >= 1
@@ -61,14 +69,15 @@ def test_band_equals_register_kernels(dk, level, count):
     in flight on 128^2, a ragged count on both."""
     wl = W.get("mlmc16_256").with_(L_max=level, T=0.002)
     with dk.Context.from_workload(wl) as reg, dk.Context.from_workload(wl) as bnd:
-        for tag in (0, 1):
-            coupled = tag == 0
-            d = _band_variant(bnd, level, coupled)
-            s_r, a = _samples(reg, dk, level, tag, 3, count, 11)
-            s_b, b = _samples(bnd, dk, level, tag, 3, count, 11)
-            _compare(a, b, reg.n_obs, 1e-6)
-            assert s_b[0] == count and s_b[1] == 0.0
-            print(level, tag, "bands", d.bands, "in flight", d.in_flight)
+        for v in _band_variants(bnd, level):
+            for tag in (0, 1):
+                coupled = tag == 0
+                d = _band_variant(bnd, level, coupled, v)
+                s_r, a = _samples(reg, dk, level, tag, 3, count, 11)
+                s_b, b = _samples(bnd, dk, level, tag, 3, count, 11)
+                _compare(a, b, reg.n_obs, 1e-6)
+                assert s_b[0] == count and s_b[1] == 0.0
+                print(level, v, tag, "bands", d.bands, "in flight", d.in_flight)
 
 
 def test_band_many_waves(dk):
@@ -78,12 +87,13 @@ def test_band_many_waves(dk):
     observables equal to FP64 summation order."""
     wl = W.get("mlmc16_256").with_(L_max=4, T=2.5e-4)
     with dk.Context.from_workload(wl, stream_from_n=256) as stm, dk.Context.from_workload(wl) as bnd:
-        d = _band_variant(bnd, 4, True)
-        count = 2 * d.in_flight + 5
-        _, a = _samples(stm, dk, 4, 0, 100, count, 7)
-        s, b = _samples(bnd, dk, 4, 0, 100, count, 7)
-        _compare(a, b, bnd.n_obs, 1e-10)
-        assert s[0] == count
+        for v in _band_variants(bnd, 4):
+            d = _band_variant(bnd, 4, True, v)
+            count = 2 * d.in_flight + 5
+            _, a = _samples(stm, dk, 4, 0, 100, count, 7)
+            s, b = _samples(bnd, dk, 4, 0, 100, count, 7)
+            _compare(a, b, bnd.n_obs, 1e-10)
+            assert s[0] == count
 
 
 def test_band_256_matches_oracle(dk):
@@ -112,15 +122,16 @@ def test_band_256_matches_oracle(dk):
 def test_band_equals_streamed_kernels(dk, name, kw, level, count):
     wl = W.get(name).with_(**kw)
     with dk.Context.from_workload(wl) as ctx:
+        d = ctx.level_info(level)
+        assert d.streamed == 1 and d.n_variants == 4 and d.band == 1      # the band kernel is the default
         for tag in (0, 1):
             coupled = tag == 0
-            d = ctx.level_info(level)
-            assert d.streamed == 1 and d.n_variants == 3
-            _band_variant(ctx, level, coupled)
-            _, b = _samples(ctx, dk, level, tag, 2, count, 5)
             ctx.set_variant(level, coupled, 0)
             _, a = _samples(ctx, dk, level, tag, 2, count, 5)
-            _compare(a, b, ctx.n_obs, 1e-9)
+            for v in _band_variants(ctx, level):
+                _band_variant(ctx, level, coupled, v)
+                _, b = _samples(ctx, dk, level, tag, 2, count, 5)
+                _compare(a, b, ctx.n_obs, 1e-9)
 
 
 def test_band_is_default_on_large_levels_and_tuned(dk):
