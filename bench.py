@@ -600,6 +600,9 @@ def run_ours(args, wl, rank, world, local_rank):
     hbm_peak, hbm_src = measured_peaks()
     if dinfo.band:
         kname = f"band_kernel n={dinfo.n} bands={dinfo.bands} in_flight={dinfo.in_flight} coupled={dom > 0}"
+    elif dinfo.streamed:
+        kname = (f"stream_fine_kernel n={dinfo.n} tile_rows={dinfo.tile_rows} in_flight={dinfo.in_flight} "
+                 f"coupled={dom > 0}")
     else:
         kname = (f"level_kernel n={dinfo.n} C={dinfo.lane_cols} R={dinfo.lane_rows} "
                  f"cluster={dinfo.cluster} coupled={dom > 0}")
@@ -659,7 +662,11 @@ def run_ours(args, wl, rank, world, local_rank):
         return Mopt, float(sum(m * t for m, t in zip(Mopt, ts)))
 
     M_plain, t_mlmc = opt_cost(V, t_l)
-    n_mc = 1 if fine[L] > 1e11 else max(2, int(2e11 / fine[L]))
+    # plain MC on the finest level: at least one full wave of samples in flight
+    d_L = ctx.level_info(L)
+    n_mc = max(2, int(2e11 / fine[L]), d_L.in_flight if (d_L.streamed or d_L.band) else 0)
+    if fine[L] > 1e11:
+        n_mc = max(1, d_L.in_flight)
     torch.cuda.synchronize()
     a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a0.record(stream)

@@ -120,6 +120,9 @@ struct Surrogate {
     int* d_bfidx = nullptr;            // parameter -> BF16 index (-1 for biases)
     __nv_bfloat16 *d_X = nullptr, *d_H1 = nullptr, *d_H2 = nullptr, *d_H3 = nullptr;
     __nv_bfloat16 *d_dH1 = nullptr, *d_dH2 = nullptr, *d_dH3 = nullptr;
+    // K-major operands of the backward GEMMs: dH^T, Hin^T [256][batch], W^T [256][256]
+    __nv_bfloat16 *d_tA = nullptr, *d_tB = nullptr, *d_wt = nullptr;
+    unsigned* err = nullptr;           // the context's device error word (bounded waits of the GEMM)
     float *d_y = nullptr, *d_dy = nullptr, *d_T = nullptr, *d_Xf = nullptr;
     double* d_samp = nullptr;          // level-0 per-sample outputs of a chunk
     double* d_D0 = nullptr;
@@ -952,7 +955,7 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
         }
         if (!c->fluct && !force_stream && (dk::band_supported(t.n, 4) || dk::band_supported(t.n, 8))) {
             // band kernels (4 x 4 and 4 x 8 thread blocks): a sample over several
-            // CTAs; the default on streamed levels, tuner candidates elsewhere
+            // CTAs; candidates for the tuner (the first variant stays the default)
             size_t bytes = 0;
             int S_max = 0;
             for (int mode = 0; mode < 2; ++mode) {
@@ -975,7 +978,7 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
                 }
                 for (int mode = 0; mode < 2; ++mode) {
                     if (mode == 1 && l == 0) continue;
-                    for (int k = 1; k >= 0; --k) {   // 4 x 8 blocks first: the default on streamed levels
+                    for (int k = 1; k >= 0; --k) {   // 4 x 8 blocks, then 4 x 4
                         const dk::BandPlan& p = t.bplan[mode][k];
                         if (!p.supported) continue;
                         dk::VariantInfo vi{};
@@ -991,11 +994,7 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
                         vi.R = 2;
                         t.vis[mode].push_back(vi);
                     }
-                    if (t.streamed) {
-                        // the first band variant after the streamed ones
-                        for (int v = 0; v < (int)t.vis[mode].size(); ++v)
-                            if (t.vis[mode][v].band) { t.sel[mode] = v; break; }
-                    }
+
                 }
             }
         }
@@ -1484,10 +1483,10 @@ int mlmc_dk_tune(mlmc_dk_ctx* ctx, int32_t repeats, double* seconds) {
                 int64_t count;
                 if (vi.band) {
                     count = t.bplan[mode][vi.band == 4 ? 0 : 1].S;
-                    steps = std::min(t.M, 1024);
+                    steps = std::min(t.M, 512);
                 } else if (t.streamed) {
                     count = t.inflight_v[v];
-                    steps = std::min(t.M, 64);
+                    steps = std::min(t.M, 512);
                 } else {
                     count = 2LL * (vi.max_ctas / vi.cluster) * vi.slots_per_cta;
                 }
@@ -1832,7 +1831,7 @@ void free_surrogate(Surrogate* s) {
                     (void*)s->d_H1, (void*)s->d_H2, (void*)s->d_H3, (void*)s->d_dH1, (void*)s->d_dH2,
                     (void*)s->d_dH3, (void*)s->d_y, (void*)s->d_dy, (void*)s->d_T, (void*)s->d_Xf,
                     (void*)s->d_samp, (void*)s->d_D0, (void*)s->d_part, (void*)s->d_loss, (void*)s->d_trainX,
-                    (void*)s->d_trainT, (void*)s->d_idx})
+                    (void*)s->d_trainT, (void*)s->d_idx, (void*)s->d_tA, (void*)s->d_tB, (void*)s->d_wt})
         cudaFree(p);
     delete s;
 }
@@ -1889,17 +1888,19 @@ dk::GemmArgs gemm(int M, int N, int K, const __nv_bfloat16* A, long long sam, lo
 }
 
 // Network forward on n standardised feature rows X (n <= chunk): y = That.
+// The dense layers run on the tensor cores (tcgen05): H = relu(X W^T + b),
+// X [n][in] and W [out][in] both K-major.
 cudaError_t mlp_forward(Surrogate* s, const __nv_bfloat16* X, int n, float* y, cudaStream_t st) {
     cudaError_t e;
     dk::GemmArgs g = gemm(n, dk::kHidden, dk::kFeat, X, dk::kFeat, 1, s->d_wbf + kBfW1, 1, dk::kFeat);
     g.Cb = s->d_H1; g.ldcb = dk::kHidden; g.bias = s->d_theta + kOffB1; g.relu = 1;
-    if ((e = dk::launch_gemm(g, st)) != cudaSuccess) return e;
+    if ((e = dk::launch_gemm_tc(g, s->err, st)) != cudaSuccess) return e;
     g = gemm(n, dk::kHidden, dk::kHidden, s->d_H1, dk::kHidden, 1, s->d_wbf + kBfW2, 1, dk::kHidden);
     g.Cb = s->d_H2; g.ldcb = dk::kHidden; g.bias = s->d_theta + kOffB2; g.relu = 1;
-    if ((e = dk::launch_gemm(g, st)) != cudaSuccess) return e;
+    if ((e = dk::launch_gemm_tc(g, s->err, st)) != cudaSuccess) return e;
     g = gemm(n, dk::kHidden, dk::kHidden, s->d_H2, dk::kHidden, 1, s->d_wbf + kBfW3, 1, dk::kHidden);
     g.Cb = s->d_H3; g.ldcb = dk::kHidden; g.bias = s->d_theta + kOffB3; g.relu = 1;
-    if ((e = dk::launch_gemm(g, st)) != cudaSuccess) return e;
+    if ((e = dk::launch_gemm_tc(g, s->err, st)) != cudaSuccess) return e;
     return dk::launch_out_forward(s->d_H3, s->d_theta + kOffW4, s->d_theta + off_b4(s->K), n, dk::kHidden, s->K, y,
                                   st);
 }
@@ -1918,16 +1919,25 @@ cudaError_t mlp_backward(Surrogate* s, const __nv_bfloat16* X, const float* T, i
         {s->d_dH2, s->d_H1, dk::kHidden, G + kOffW2, G + kOffB2, s->d_wbf + kBfW2, s->d_dH1},
         {s->d_dH1, X, dk::kFeat, G + kOffW1, G + kOffB1, nullptr, nullptr}};
     for (const Layer& L : layers) {
-        // dW = dH^T Hin  (256 x K, summed over the batch)
-        dk::GemmArgs g = gemm(dk::kHidden, L.K, B, L.dH, 1, dk::kHidden, L.Hin, L.K, 1);
+        // dW = dH^T Hin (256 x K, summed over the batch) as a K-major product on
+        // the tensor cores: A = dH^T [256][B], B operand = Hin^T [K][B]
+        // rows of the transposed operands padded to 8 elements (16 bytes, the TMA
+        // stride unit); the padding lies beyond K = B and is never read
+        const int ldt = (B + 7) & ~7;
+        if ((e = dk::launch_transpose_bf16(L.dH, B, dk::kHidden, s->d_tA, ldt, st)) != cudaSuccess ||
+            (e = dk::launch_transpose_bf16(L.Hin, B, L.K, s->d_tB, ldt, st)) != cudaSuccess)
+            return e;
+        dk::GemmArgs g = gemm(dk::kHidden, L.K, B, s->d_tA, ldt, 1, s->d_tB, 1, ldt);
         g.C = L.gW; g.ldc = L.K;
-        if ((e = dk::launch_gemm(g, st)) != cudaSuccess) return e;
+        if ((e = dk::launch_gemm_tc(g, s->err, st)) != cudaSuccess) return e;
         if ((e = dk::launch_colsum(L.dH, nullptr, B, dk::kHidden, L.gb, st)) != cudaSuccess) return e;
         if (L.W) {
-            // dHin = (dH W) * (Hin > 0)
-            g = gemm(B, dk::kHidden, dk::kHidden, L.dH, dk::kHidden, 1, L.W, dk::kHidden, 1);
+            // dHin = (dH W) * (Hin > 0): A = dH [B][256], B operand = W^T [in][out]
+            if ((e = dk::launch_transpose_bf16(L.W, dk::kHidden, dk::kHidden, s->d_wt, dk::kHidden, st)) != cudaSuccess)
+                return e;
+            g = gemm(B, dk::kHidden, dk::kHidden, L.dH, dk::kHidden, 1, s->d_wt, 1, dk::kHidden);
             g.Cb = L.dHin; g.ldcb = dk::kHidden; g.mask = L.Hin; g.ldm = dk::kHidden;
-            if ((e = dk::launch_gemm(g, st)) != cudaSuccess) return e;
+            if ((e = dk::launch_gemm_tc(g, s->err, st)) != cudaSuccess) return e;
         }
     }
     return cudaSuccess;
@@ -2014,6 +2024,10 @@ int mlmc_dk_surrogate_init(mlmc_dk_ctx* ctx, uint64_t seed) {
     alloc((void**)&s->d_dH1, sizeof(__nv_bfloat16) * s->batch_cap * dk::kHidden);
     alloc((void**)&s->d_dH2, sizeof(__nv_bfloat16) * s->batch_cap * dk::kHidden);
     alloc((void**)&s->d_dH3, sizeof(__nv_bfloat16) * s->batch_cap * dk::kHidden);
+    alloc((void**)&s->d_tA, sizeof(__nv_bfloat16) * (s->batch_cap + 8) * dk::kHidden);
+    alloc((void**)&s->d_tB, sizeof(__nv_bfloat16) * (s->batch_cap + 8) * dk::kHidden);
+    alloc((void**)&s->d_wt, sizeof(__nv_bfloat16) * dk::kHidden * dk::kHidden);
+    s->err = ctx->d_err;
     alloc((void**)&s->d_y, sizeof(float) * ch * K);
     alloc((void**)&s->d_dy, sizeof(float) * s->batch_cap * K);
     alloc((void**)&s->d_T, sizeof(float) * ch * K);
