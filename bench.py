@@ -225,6 +225,10 @@ def parse():
     ap.add_argument("--no-fourier", action="store_true", help="skip the Fourier-coupled kernel timing")
     ap.add_argument("--split-fraction", type=float, default=None,
                     help="fixed batch split of the finest cluster level (default: autotuned)")
+    ap.add_argument("--profile-level", default=None, metavar="WORKLOAD:LEVEL:SAMPLES[:T[:VARIANT]]",
+                    help="run one level batch twice (a small case for a profiler), print its timing and exit")
+    ap.add_argument("--profile-gemm", type=int, default=0, metavar="ROWS",
+                    help="run the learned level's network forward on ROWS rows twice (tensor-core GEMMs) and exit")
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the secondary measurements (16^2..256^2 batch, 512^2 stencil, theta, Fourier)")
     ap.add_argument("--no-mlmc16", action="store_true", help="skip the 16^2..256^2 batch and Algorithm 1 run")
@@ -879,8 +883,68 @@ def run_reference(args, wl, rank, world):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def profile_level(spec):
+    """One level batch, run twice (warm-up, then timed with CUDA events): the
+    small, repeatable case behind the kernel profiles."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2311_08872_gb300 import mlmc_dk, workloads
+    parts = spec.split(":")
+    wl = workloads.get(parts[0])
+    level, count = int(parts[1]), int(parts[2])
+    if len(parts) > 3 and parts[3]:
+        wl = wl.with_(T=float(parts[3]))
+    st = torch.cuda.current_stream()
+    with mlmc_dk.Context.from_workload(wl, stream=st.cuda_stream) as ctx:
+        if len(parts) > 4:
+            ctx.set_variant(level, level > 0, int(parts[4]))
+        info = ctx.level_info(level)
+        sums = torch.zeros(mlmc_dk.sums_len(ctx.n_quant), dtype=torch.float64, device="cuda")
+        ctx.run_level_dev(level, 0, 0, count, wl.seed, sums.data_ptr(), 0, st.cuda_stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        ctx.run_level_dev(level, 0, count, count, wl.seed, sums.data_ptr(), 0, st.cuda_stream)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+    print(json.dumps({"workload": wl.name, "level": level, "n": info.n, "fine_steps": info.M, "samples": count,
+                      "streamed": bool(info.streamed), "band": bool(info.band), "variant": info.variant_coupled,
+                      "in_flight": info.in_flight, "ms": ms, "cell_steps_per_s": count * info.cost / (ms * 1e-3),
+                      "fine_cell_steps_per_s": count * info.cost_mc / (ms * 1e-3)}))
+
+
+def profile_gemm(rows):
+    """The learned level's network forward (three 256-wide dense layers on the
+    tensor cores, then the output layer) on `rows` random feature rows, run
+    twice; the second run is timed with CUDA events."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2311_08872_gb300 import mlmc_dk, workloads
+    wl = workloads.get("mlmc16_256").with_(L_max=1)
+    X = np.random.default_rng(1).normal(size=(rows, 64)).astype(np.float32)
+    with mlmc_dk.Context.from_workload(wl) as ctx:
+        ctx.surrogate_init(1)
+        ctx.surrogate_forward(X)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        ctx.surrogate_forward(X)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t
+    flops = 2.0 * rows * (64 * 256 + 2 * 256 * 256)
+    print(json.dumps({"rows": rows, "gemm_flops": flops, "forward_s_incl_copies": sec}))
+
+
 def main():
     args = parse()
+    if args.profile_level:
+        profile_level(args.profile_level)
+        return
+    if args.profile_gemm:
+        profile_gemm(args.profile_gemm)
+        return
     from paper_2311_08872_gb300 import workloads
     wl = workloads.get(args.workload)
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -213,10 +213,9 @@ struct GemmArgs {
 
 cudaError_t launch_features(const FeatArgs& a, int max_ctas, cudaStream_t st);
 cudaError_t launch_direct_features(const FeatArgs& a, cudaStream_t st);
-cudaError_t launch_gemm(const GemmArgs& g, cudaStream_t st);
-// The same on the 5th-generation tensor cores (dk_umma.cu): A [M][K] and B
-// given as [N][K], both K-major (sak == sbk == 1), N <= 256; bounded waits
-// record kErrTimeout in *err.
+// C = A B on the 5th-generation tensor cores (dk_umma.cu): A [M][K] and B
+// given as [N][K], both K-major (sak == sbk == 1), N <= 256; epilogue as in
+// GemmArgs; bounded waits record kErrTimeout in *err.
 cudaError_t launch_gemm_tc(const GemmArgs& g, unsigned* err, cudaStream_t st);
 // out[c][r] = in[r][c] for an R x C BF16 matrix, output rows ldo >= R apart.
 cudaError_t launch_transpose_bf16(const __nv_bfloat16* in, int R, int C, __nv_bfloat16* out, int ldo,

@@ -1,7 +1,7 @@
 // Learned level below level 0 (not in the paper): feature projection of the
 // level-0 noise, a direct sampler of the features' exact law, and the
-// kernels that train and run a 64-256-256-256-1 ReLU perceptron on BF16
-// tensor cores with FP32 accumulation and FP32 master weights.
+// kernels that train and run a 64-256-256-256-1 ReLU perceptron with BF16
+// tensor-core GEMMs (dk_umma.cu), FP32 accumulation and FP32 master weights.
 //
 // Features.  With e_j the 32 lowest real orthonormal grid modes (cosine and
 // sine per wave vector k, ordered by |k|^2) and g_j the per-step factor of the
@@ -108,95 +108,9 @@ __global__ void direct_feature_kernel(const FeatArgs a) {
 }
 
 // ------------------------------------------------------------- BF16 GEMM
-// C[M x N] = A[M x K] B[K x N] with arbitrary element strides, on tensor cores
-// (mma.sync m16n8k16, BF16 inputs, FP32 accumulation).  CTA tile 64 x 64 x 32,
-// 4 warps of 32 x 32.  Tiles are staged in shared memory as A[m][k] and B[n][k]
-// (k contiguous, padded rows).  Epilogue: + bias[n], ReLU, * (mask[m][n] > 0),
-// FP32 and/or BF16 output.
-namespace {
-constexpr int BM = 64, BN = 64, BK = 32, PAD = 8;
-
-__device__ __forceinline__ uint32_t ld_pair(const __nv_bfloat16* p) {
-    return *reinterpret_cast<const uint32_t*>(p);
-}
-
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-}  // namespace
-
-__global__ void __launch_bounds__(128) gemm_bf16_kernel(const GemmArgs g) {
-    __shared__ __align__(16) __nv_bfloat16 sA[BM][BK + PAD];
-    __shared__ __align__(16) __nv_bfloat16 sB[BN][BK + PAD];
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-    const int gid = lane >> 2, tig = lane & 3;
-    float acc[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
-    const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
-    for (int k0 = 0; k0 < g.K; k0 += BK) {
-        for (int i = tid; i < BM * BK; i += 128) {
-            const int r = i / BK, c = i % BK;
-            const int m = m0 + r, k = k0 + c;
-            sA[r][c] = (m < g.M && k < g.K) ? g.A[m * g.sam + k * g.sak] : zero;
-        }
-        for (int i = tid; i < BN * BK; i += 128) {
-            const int r = i / BK, c = i % BK;
-            const int n = n0 + r, k = k0 + c;
-            sB[r][c] = (n < g.N && k < g.K) ? g.B[k * g.sbk + n * g.sbn] : zero;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < BK; kk += 16) {
-            uint32_t af[2][4], bf[4][2];
-#pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                const int r = wm + 16 * i + gid;
-                af[i][0] = ld_pair(&sA[r][kk + 2 * tig]);
-                af[i][1] = ld_pair(&sA[r + 8][kk + 2 * tig]);
-                af[i][2] = ld_pair(&sA[r][kk + 8 + 2 * tig]);
-                af[i][3] = ld_pair(&sA[r + 8][kk + 8 + 2 * tig]);
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int c = wn + 8 * j + gid;
-                bf[j][0] = ld_pair(&sB[c][kk + 2 * tig]);
-                bf[j][1] = ld_pair(&sB[c][kk + 8 + 2 * tig]);
-            }
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bf[j]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int m = m0 + wm + 16 * i + gid + (r >= 2 ? 8 : 0);
-                const int n = n0 + wn + 8 * j + 2 * tig + (r & 1);
-                if (m >= g.M || n >= g.N) continue;
-                float v = acc[i][j][r];
-                if (g.bias) v += g.bias[n];
-                if (g.relu) v = fmaxf(v, 0.f);
-                if (g.mask && !(__bfloat162float(g.mask[m * g.ldm + n]) > 0.f)) v = 0.f;
-                if (g.C) g.C[m * g.ldc + n] = v;
-                if (g.Cb) g.Cb[m * g.ldcb + n] = __float2bfloat16_rn(v);
-            }
-}
+// The dense layers' GEMMs run on the 5th-generation tensor cores (tcgen05,
+// dk_umma.cu); this file holds the output layer (K outputs, too narrow for a
+// tensor-core tile), the feature kernels, Adam and the moment kernels.
 
 // -------------------------------------------------------- small MLP kernels
 // Output layer forward: y[b][o] = H3[b] . w4[o] + b4[o], o < KO (one warp per row).
@@ -372,12 +286,6 @@ cudaError_t launch_features(const FeatArgs& a, int max_ctas, cudaStream_t st) {
 cudaError_t launch_direct_features(const FeatArgs& a, cudaStream_t st) {
     const long long threads = a.count * (kFeat / 4);
     direct_feature_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(a);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_gemm(const GemmArgs& g, cudaStream_t st) {
-    const dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM);
-    gemm_bf16_kernel<<<grid, 128, 0, st>>>(g);
     return cudaGetLastError();
 }
 
