@@ -234,6 +234,12 @@ def parse():
     ap.add_argument("--no-mlmc16", action="store_true", help="skip the 16^2..256^2 batch and Algorithm 1 run")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned level below 0")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the default kernel variants and no batch split (profiling runs: timings taken "
+                         "under a profiler would mislead the tuner)")
+    ap.add_argument("--t-scale", type=float, default=1.0,
+                    help="divide the workload's T by this (profiling runs: the same levels and launch mix "
+                         "with fewer steps; the line then describes that shorter workload)")
     ap.add_argument("--adaptive-eps", type=float, default=1e-2,
                     help="relative eps of the fully measured Algorithm 1 run (0: the workload's)")
     return ap.parse_args()
@@ -391,6 +397,51 @@ def oracle_leg(wl, alloc, learned, budget_s, seed, first, cores=None):
             "batch_cpu_s": cpu_time, "wall_s": wall}, outs
 
 
+def level_launches(d, count, coupled):
+    """Kernel launches of one level's share of a batch, from its kernel's description."""
+    if d.band:                                   # zero + per wave (kernel + finish) + reduce
+        return 2 + 2 * (-(-count // d.in_flight))
+    if d.streamed:                               # zero + per wave (init, steps, observe, finish) + reduce
+        steps = 1 if d.persistent else d.M + (d.M // 4 if coupled else 0)
+        return 2 + (-(-count // d.in_flight)) * (3 + steps)
+    n = 2                                        # level kernel + reduce
+    if d.batch_streamed > 0:                     # the split share: one launch per step, then the merge
+        n += 2 + (-(-d.batch_streamed // d.in_flight)) * (3 + d.M + d.M // 4) + 1
+    return n
+
+
+def oracle_samples(wl, counts, seed, cores=None):
+    """The FP64 oracle's observables for ids 0..counts[l]-1 of each level
+    (coupled), one process per core: {level: {id: (Y_f, Y_c)}}."""
+    import multiprocessing as mp
+    cores = cores or min(os.cpu_count() or 1, 16)
+    tasks = [(wl, l, i, seed) for l, k in enumerate(counts) for i in range(k)]
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_task, tasks, chunksize=1)
+    outs = {}
+    for l, i, _, yf, yc in res:
+        outs.setdefault(l, {})[i] = (yf, yc)
+    return outs
+
+
+def network_error(ctx, theta, outputs, rows, seed):
+    """The learned level's network (BF16 operands, FP32 accumulation, tensor
+    cores) against the same network in FP64 on the level's own feature rows:
+    max and RMS of |y_gpu - y_fp64| over RMS(y_fp64)."""
+    import numpy as np
+    from oracle import surrogate as sg
+    X = ctx.surrogate_features(0, rows, seed, direct=True)
+    y = ctx.surrogate_forward(X).astype(np.float64).reshape(rows, -1)
+    yo, _ = sg.mlp_forward(theta.astype(np.float64), X.astype(np.float64), outputs)
+    yo = yo.reshape(rows, -1)
+    scale = np.sqrt(np.mean(yo ** 2, axis=0))
+    d = np.abs(y - yo) / scale[None, :]
+    return {"rows": rows, "max_err_over_rms": float(d.max()), "rms_err_over_rms": float(np.sqrt(np.mean(d ** 2))),
+            "what": "network outputs on directly drawn level -1 feature rows against the FP64 network with the "
+                    "same parameters; the BF16 rounding of the operands sets this error, and the correction "
+                    "level E[P_0 - S] removes its effect on the estimate (the estimator stays unbiased)"}
+
+
 def oracle_error(ctx, wl, outs, seed, stream):
     """Per-sample error of the GPU path against the oracle on the same ids:
     max |Y_gpu - Y_oracle| / max(|Y_oracle|, RMS of the level's Y_oracle - Ybar)
@@ -470,7 +521,7 @@ def run_ours(args, wl, rank, world, local_rank):
     first0 = D.first_sample(rank)          # ranks shard the sample ids (no collective on the data path)
 
     ctx = mlmc_dk.Context.from_workload(wl, stream=stream.cuda_stream)
-    tune_s = ctx.tune(repeats=1)          # autotuner: fastest kernel per level (outside timing)
+    tune_s = 0.0 if args.no_tune else ctx.tune(repeats=1)   # autotuner: fastest kernel per level (outside timing)
     choice = ctx.variants()
     info = [ctx.level_info(l) for l in range(L + 1)]
     M = [i.M for i in info]
@@ -501,7 +552,7 @@ def run_ours(args, wl, rank, world, local_rank):
     split_frac, split_s = 0.0, 0.0
     if split_level is not None:
         if args.split_fraction is None:
-            split_frac, split_s = ctx.tune_batch(batch_counts, 1)
+            split_frac, split_s = (0.0, 0.0) if args.no_tune else ctx.tune_batch(batch_counts, 1)
         else:
             split_frac = args.split_fraction
             ctx.set_batch_split(split_level, split_frac)
@@ -568,16 +619,8 @@ def run_ours(args, wl, rank, world, local_rank):
         last = (s, parts)
         for l, t in enumerate(ctx.batch_level_ms()):   # CUDA events on each level's stream
             level_ms[l] += t
-            if batch_counts[l] <= 0:
-                continue
-            d = ctx.level_info(l)
-            if d.band:                       # zero + per wave (kernel + finish) + reduce
-                launches += 2 + 2 * (-(-batch_counts[l] // d.in_flight))
-            else:
-                launches += 2
-                if d.batch_streamed > 0:     # zero + per wave (init, fine steps, coarse steps, observe, finish) + reduce + merge
-                    waves = -(-d.batch_streamed // d.in_flight)
-                    launches += 1 + waves * (3 + d.M + d.M // 4) + 2
+            if batch_counts[l] > 0:
+                launches += level_launches(ctx.level_info(l), batch_counts[l], l > 0)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -757,6 +800,14 @@ def run_ours(args, wl, rank, world, local_rank):
         cpu, outs = oracle_leg(wl, alloc, learned, args.cpu_budget, seed0 + 101, first0)
         c3 = ctx or mlmc_dk.Context.from_workload(wl, stream=stream.cuda_stream)
         oerr = oracle_error(c3, wl, outs, seed0 + 101, stream)
+        summary = {"same_kernels_as": "oracle_error", "worst_err_over_bar_scale": oerr["worst_err_over_bar_scale"],
+                   "within_bar": oerr["within_bar"]}
+        to_eps["oracle_error"] = summary
+        if sur is not None:
+            c3.surrogate_init(seed0 + 3)
+            c3.surrogate_params(theta)
+            sur["oracle_error"] = dict(summary, network=network_error(c3, theta, c3.surrogate_info()[1],
+                                                                      4096, seed0 + 23))
         c3.close()
         ctx = None
     if ctx is not None:
@@ -772,7 +823,7 @@ def run_ours(args, wl, rank, world, local_rank):
                        parallelism=f"{world} rank(s), disjoint sample ids per rank",
                        kernels=[{"n": i.n, "band": bool(i.band), "bands": i.bands, "in_flight": i.in_flight,
                                  "C": i.lane_cols, "R": i.lane_rows, "cluster": i.cluster} for i in info],
-                       tune_s=tune_s,
+                       tune_s=tune_s, tuned=not args.no_tune, t_scale=args.t_scale,
                        batch_split={"level": split_level, "fraction": split_frac, "tune_s": split_s}),
         "cell_steps_per_s": world * cell_steps * args.steps / (total_ms * 1e-3),
         "gpu_launches": launches,
@@ -840,6 +891,11 @@ def mlmc16_batch(args, stream):
         adaptive = {"eps_rel": args.adaptive_eps, "s": time.perf_counter() - t, "L": r.L,
                     "M": [r.M[l] for l in range(r.L + 1)], "estimate": r.estimate, "variance": r.variance,
                     "eps_abs": r.eps_abs, "converged": bool(r.converged), "cell_steps": r.cell_steps}
+        if not args.no_cpu_baseline:
+            # the oracle on the first ids of the run's levels up to 128^2 (same seed)
+            counts = [min(r.M[l], 8 if info[l].n <= 64 else 4) for l in range(min(r.L, 3) + 1)]
+            outs = oracle_samples(wl, counts, wl.seed + 5)
+            adaptive["oracle_error"] = oracle_error(c, wl, outs, wl.seed + 5, stream)
     fin = info[-1]
     return {"alloc": alloc, "ms_per_step": ms, "coupled_sample_steps_per_s": steps / (ms * 1e-3),
             "cell_steps_per_s": sum(m * i.cost for m, i in zip(alloc, info)) / (ms * 1e-3),
@@ -947,6 +1003,8 @@ def main():
         return
     from paper_2311_08872_gb300 import workloads
     wl = workloads.get(args.workload)
+    if args.t_scale != 1.0:
+        wl = wl.with_(T=wl.T / args.t_scale)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -78,7 +78,7 @@ extern "C" {
 #define MLMC_DK_ERR_RANGE (-3)       /* |rho| reached 2^(30-S_l): the level's fixed-point range */
 #define MLMC_DK_ERR_UNSUPPORTED (-4) /* grid size without a kernel variant */
 #define MLMC_DK_ERR_STATE (-5)       /* checkpoint buffer does not match */
-#define MLMC_DK_ERR_TIMEOUT (-6)     /* a band kernel's bounded wait for a neighbouring CTA gave up */
+#define MLMC_DK_ERR_TIMEOUT (-6)     /* a kernel's bounded wait for another CTA's progress gave up (band, persistent streamed and tensor-core GEMM kernels) */
 
 #define MLMC_DK_MAX_LEVELS 16
 #define MLMC_DK_MAX_OBS 4
@@ -165,6 +165,9 @@ typedef struct {
                                bands of coarse rows in registers, band edges exchanged through global memory;
                                in_flight samples per launch) */
     int32_t bands;
+    int32_t persistent;     /* 1: the level's streamed kernel in use runs each wave of in_flight samples as one
+                               launch whose CTAs take (tile, step) items in order from a counter and wait, with
+                               bounded polls, for the items they read from; 0: one launch per step */
 } mlmc_dk_level_desc;
 
 /* Host-side moment sums of one quantity on one level (accumulated into). */
@@ -335,6 +338,15 @@ int mlmc_dk_run_level_static(const mlmc_dk_ctx* ctx, int32_t level, int32_t stre
  * MLMC_DK_ERR_TIMEOUT; the context stays usable.  MLMC_DK_ERR_UNSUPPORTED
  * when the level does not run on the band kernel. */
 int mlmc_dk_band_wait_test(mlmc_dk_ctx* ctx, int32_t level, uint32_t polls, int32_t stall_band);
+
+/* Failure-detection test of the persistent streamed kernel's bounded waits
+ * (the paper has no counterpart): one sample of streamed `level` over at most
+ * 64 fine steps on the persistent streamed kernel, with every wait limited to
+ * `polls` polls and fine tile `stall_tile` never reporting its step 1, so that
+ * the waits for it run out.  The kernel records the timeout, every CTA stops
+ * at its next item, and the call returns MLMC_DK_ERR_TIMEOUT; the context
+ * stays usable.  MLMC_DK_ERR_UNSUPPORTED when the level is not streamed. */
+int mlmc_dk_stream_wait_test(mlmc_dk_ctx* ctx, int32_t level, uint32_t polls, int32_t stall_tile);
 
 /* Algorithm 1 (Section 7.1): start at L = L_start with `pilot` samples on
  * levels 0..L; repeat {run the missing samples (all levels of a round at once

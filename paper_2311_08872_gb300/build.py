@@ -59,7 +59,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if p.returncode:
             raise RuntimeError("nvcc failed: " + " ".join(cmd))
     tmp = LIB + ".tmp"
-    subprocess.run([cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-cudart", "static"], check=True)
+    subprocess.run([cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-cudart", "static", "-lpthread"], check=True)
     os.replace(tmp, LIB)
     return LIB
 

@@ -52,20 +52,6 @@ struct BShape {
     static_assert(WPR >= 1 && NF % (32 * FC) == 0, "a warp covers 32 FC columns of the grid");
 };
 
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
-    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ unsigned ld_volatile(const unsigned* p) {
-    return *reinterpret_cast<const volatile unsigned*>(p);
-}
-
 // Wait until *flag >= target (counters only grow).  Returns false after
 // `polls` polls, or as soon as another CTA has recorded a timeout.
 __device__ bool wait_counter(const unsigned* flag, unsigned target, unsigned* err, unsigned polls) {

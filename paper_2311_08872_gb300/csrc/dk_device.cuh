@@ -60,6 +60,22 @@ __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float& z1, fl
     z2 = r * s;
 }
 
+// Progress counters shared between CTAs of one launch: an acquire load, a
+// release increment (after the CTA's or warp's writes), a volatile read.
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned ld_volatile(const unsigned* p) {
+    return *reinterpret_cast<const volatile unsigned*>(p);
+}
+
 // Noise transfer G = rint(g sqrt(max(q,0)) z) in fixed-point units.
 __device__ __forceinline__ float noise_amp(int32_t q, float g) {
     return g * sqrt_approx(__int2float_rn(max(q, 0)));

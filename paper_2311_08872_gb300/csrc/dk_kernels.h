@@ -58,6 +58,7 @@ struct VariantInfo {
     int max_ctas;           // resident CTAs on the whole GPU
     int C, R;               // lane block: C x R coarse cells (2R x 2C fine)
     int tile_rows;          // streamed kernels: fine rows per CTA tile (0 for the register kernels)
+    int persistent;         // streamed kernels: 1 = one launch per wave (work items from a counter)
     int band;               // 1: the band kernel (a sample over several CTAs, cooperative launch)
     int bands;              // band kernel: bands (CTAs) per sample
 };
@@ -100,6 +101,17 @@ struct SArgs {
     float gf, gc;
     uint32_t key0, key1, tag;
     unsigned int* err;
+    // persistent launch: progress counters (fine steps done per fine tile,
+    // coarse steps done per coarse tile), the item counter, their region,
+    // the poll limit of every wait, and a tile (of sample 0) that never
+    // reports its step 1 (-1: none; failure-detection test only)
+    unsigned int* fdone;
+    unsigned int* cdone;
+    unsigned long long* head;
+    void* counters;
+    size_t counter_bytes;
+    unsigned int wait_polls;
+    int stall_tile;
 };
 
 // Device bytes for `S` samples in flight on an n x n grid, and their layout.

@@ -12,7 +12,8 @@
 //     in TMEM and frees each stage with tcgen05.commit;
 //   * all four warps then read their 32 TMEM lanes (= rows) with tcgen05.ld and
 //     apply the epilogue: + bias[n], ReLU, * (mask[m][n] > 0), FP32 and/or BF16
-//     output.
+//     output, each thread 32 consecutive columns of its row per tcgen05.ld
+//     with 16-byte loads and stores.
 // Every mbarrier wait is bounded: after kMbarPolls polls it records
 // kErrTimeout in the error word and the CTA skips to the epilogue, which still
 // frees its TMEM.
@@ -31,7 +32,7 @@ namespace {
 
 constexpr int kTM = 128;                        // rows of a CTA tile (TMEM lanes)
 constexpr int kTK = 64;                         // K of a stage: 64 BF16 = one 128-byte swizzle row
-constexpr int kStages = 4;
+constexpr int kStages = 2;   // two stages: 99 KB at N = 256, so two CTAs share an SM
 constexpr unsigned kMbarPolls = 1u << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -195,20 +196,76 @@ __global__ void __launch_bounds__(128, 1)
     const int m = m0 + warp * 32 + lane;
     if (ready) {
 #pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 32) {
+        for (int c0 = 0; c0 < BN && c0 < g.N; c0 += 32) {
             uint32_t v[32];
             tmem_ld32(tmem + (static_cast<uint32_t>(warp * 32) << 16) + static_cast<uint32_t>(c0), v);
-            if (m < g.M) {
+            if (m >= g.M) continue;
+            // this thread's 32 consecutive columns of row m: 16-byte loads and
+            // stores where the whole chunk is inside N and the row is aligned
+            const bool full = c0 + 32 <= g.N;
+            float x[32];
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int n = c0 + j;
-                    if (n >= g.N) break;
-                    float x = __uint_as_float(v[j]);
-                    if (g.bias) x += g.bias[n];
-                    if (g.relu) x = fmaxf(x, 0.f);
-                    if (g.mask && !(__bfloat162float(g.mask[(long long)m * g.ldm + n]) > 0.f)) x = 0.f;
-                    if (g.C) g.C[(long long)m * g.ldc + n] = x;
-                    if (g.Cb) g.Cb[(long long)m * g.ldcb + n] = __float2bfloat16_rn(x);
+            for (int j = 0; j < 32; ++j) x[j] = __uint_as_float(v[j]);
+            if (g.bias) {
+                if (full && (reinterpret_cast<uintptr_t>(g.bias + c0) & 15) == 0) {
+#pragma unroll
+                    for (int j = 0; j < 32; j += 4) {
+                        const float4 b = *reinterpret_cast<const float4*>(g.bias + c0 + j);
+                        x[j] += b.x; x[j + 1] += b.y; x[j + 2] += b.z; x[j + 3] += b.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (c0 + j < g.N) x[j] += g.bias[c0 + j];
+                }
+            }
+            if (g.relu)
+#pragma unroll
+                for (int j = 0; j < 32; ++j) x[j] = fmaxf(x[j], 0.f);
+            if (g.mask) {
+                const __nv_bfloat16* mr = g.mask + (long long)m * g.ldm + c0;
+                if (full && (reinterpret_cast<uintptr_t>(mr) & 15) == 0) {
+#pragma unroll
+                    for (int j = 0; j < 32; j += 8) {
+                        const uint4 w = *reinterpret_cast<const uint4*>(mr + j);
+                        const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&w);
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+                            if (!(__bfloat162float(h[i]) > 0.f)) x[j + i] = 0.f;
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (c0 + j < g.N && !(__bfloat162float(mr[j]) > 0.f)) x[j] = 0.f;
+                }
+            }
+            if (g.C) {
+                float* cr = g.C + (long long)m * g.ldc + c0;
+                if (full && (reinterpret_cast<uintptr_t>(cr) & 15) == 0) {
+#pragma unroll
+                    for (int j = 0; j < 32; j += 4)
+                        *reinterpret_cast<float4*>(cr + j) = make_float4(x[j], x[j + 1], x[j + 2], x[j + 3]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (c0 + j < g.N) cr[j] = x[j];
+                }
+            }
+            if (g.Cb) {
+                __nv_bfloat16* br = g.Cb + (long long)m * g.ldcb + c0;
+                if (full && (reinterpret_cast<uintptr_t>(br) & 15) == 0) {
+#pragma unroll
+                    for (int j = 0; j < 32; j += 8) {
+                        uint4 w;
+                        __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&w);
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) h[i] = __floats2bfloat162_rn(x[j + 2 * i], x[j + 2 * i + 1]);
+                        *reinterpret_cast<uint4*>(br + j) = w;
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (c0 + j < g.N) br[j] = __float2bfloat16_rn(x[j]);
                 }
             }
         }

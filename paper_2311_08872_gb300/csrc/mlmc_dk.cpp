@@ -11,7 +11,9 @@
 #include <random>
 #include <cstring>
 #include <functional>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include <cuda_bf16.h>
@@ -141,6 +143,8 @@ namespace {
 void free_surrogate(Surrogate* s);
 
 int fail(mlmc_dk_ctx* ctx, int code, const std::string& msg) {
+    static std::mutex m;   // the batch enqueues streamed levels from several host threads
+    std::lock_guard<std::mutex> lock(m);
     if (ctx) ctx->err = msg; else g_init_error = msg;
     return code;
 }
@@ -343,7 +347,8 @@ int launch_batch(mlmc_dk_ctx* c, int level, int stream_tag, int64_t first, int64
 // `variant` >= 0 picks the fine-step tile (levels that normally run the
 // register kernels); otherwise the level's tuned streamed variant.
 int launch_streamed(mlmc_dk_ctx* c, int level, int stream_tag, int64_t first, int64_t count, uint64_t seed,
-                    double* sums_dev, double* samples_dev, cudaStream_t st, int steps = 0, int variant = -1) {
+                    double* sums_dev, double* samples_dev, cudaStream_t st, int steps = 0, int variant = -1,
+                    unsigned wait_polls = 0, int stall_tile = -1) {
     const bool coupled = (stream_tag == 0) && level > 0;
     LevelTab& t = c->lv[level];
     if (variant < 0) variant = t.sel[coupled ? 1 : 0];
@@ -368,6 +373,8 @@ int launch_streamed(mlmc_dk_ctx* c, int level, int stream_tag, int64_t first, in
     a.Af = k.Af; a.Ac = k.Ac; a.gf = k.gf; a.gc = k.gc;
     a.key0 = k.key0; a.key1 = k.key1; a.tag = k.tag;
     a.err = c->d_err;
+    a.wait_polls = wait_polls;
+    a.stall_tile = stall_tile;
     const int S = t.inflight_v[variant];
     if ((e = dk::stream_run(k, a, S, variant, st)) != cudaSuccess) return cuda_fail(c, e, "streamed level");
     if ((e = dk::launch_reduce(t.d_spart, S, c->stride, sums_dev, st)) != cudaSuccess)
@@ -468,7 +475,7 @@ int check_device_error(mlmc_dk_ctx* c) {
     if (e != cudaSuccess) return cuda_fail(c, e, "device error word");
     if (*c->h_err & dk::kErrTimeout) {
         cudaMemsetAsync(c->d_err, 0, sizeof(unsigned), c->stream);
-        return fail(c, MLMC_DK_ERR_TIMEOUT, "a band kernel's bounded wait for a neighbouring CTA gave up");
+        return fail(c, MLMC_DK_ERR_TIMEOUT, "a bounded wait for another CTA's progress gave up");
     }
     if (*c->h_err & dk::kErrRange) {
         cudaMemsetAsync(c->d_err, 0, sizeof(unsigned), c->stream);
@@ -1109,6 +1116,7 @@ int mlmc_dk_level_info(const mlmc_dk_ctx* ctx, int32_t level, mlmc_dk_level_desc
     out->fluct = ctx->fluct;
     out->band = vs.band ? 1 : 0;
     out->bands = vs.bands;
+    out->persistent = vs.persistent;
     if (vs.band) out->in_flight = t.bplan[level > 0 ? 1 : 0][vs.band == 4 ? 0 : 1].S;
     return MLMC_DK_OK;
 }
@@ -1194,6 +1202,26 @@ int mlmc_dk_band_wait_test(mlmc_dk_ctx* ctx, int32_t level, uint32_t polls, int3
     return check_device_error(ctx);
 }
 
+int mlmc_dk_stream_wait_test(mlmc_dk_ctx* ctx, int32_t level, uint32_t polls, int32_t stall_tile) {
+    if (!ctx) return fail(nullptr, MLMC_DK_ERR_INVALID, "null context");
+    if (level < 0 || level > ctx->L_max || polls == 0 || stall_tile < 0)
+        return fail(ctx, MLMC_DK_ERR_INVALID, "stream_wait_test: bad arguments");
+    LevelTab& t = ctx->lv[level];
+    if (!t.streamed) return fail(ctx, MLMC_DK_ERR_UNSUPPORTED, "stream_wait_test: the level is not streamed");
+    int variant = -1;
+    for (int v = 0; v < (int)t.vis[level > 0 ? 1 : 0].size(); ++v)
+        if (t.vis[level > 0 ? 1 : 0][v].persistent && t.vis[level > 0 ? 1 : 0][v].supported) variant = v;
+    const dk::VariantInfo* vi = variant >= 0 ? &t.vis[level > 0 ? 1 : 0][variant] : nullptr;
+    if (!vi || stall_tile >= (t.n / vi->tile_rows) * (t.n / 64))
+        return fail(ctx, MLMC_DK_ERR_UNSUPPORTED, "stream_wait_test: no persistent streamed kernel or no such tile");
+    const int rc = launch_streamed(ctx, level, 0, 0, 1, 0x7465, ctx->d_sums, nullptr, ctx->stream, std::min(t.M, 64),
+                                   variant, polls, stall_tile);
+    if (rc != MLMC_DK_OK) return rc;
+    const cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "stream_wait_test");
+    return check_device_error(ctx);
+}
+
 }  // extern "C"
 
 namespace {
@@ -1274,14 +1302,13 @@ int batch_dev(mlmc_dk_ctx* ctx, const int64_t* counts, const int64_t* firsts, ui
     }
     // band-kernel levels first, each on its level's stream: their cooperative
     // grids are placed before the graph's kernels fill the remaining SMs
-    bool any_band = false;
+    bool any_band = false, any_outside = false;
     auto band_level = [&](int l) { return ctx->lv[l].vi(l > 0).band != 0; };
+    for (int l = 0; l < nl; ++l) any_outside = any_outside || outside(l);
+    if (any_outside && (e = cudaEventRecord(ctx->ev_fork, st)) != cudaSuccess) return cuda_fail(ctx, e, "level fork");
     for (int l = nl - 1; l >= 0; --l) {
         if (!band_level(l)) continue;
-        if (!any_band) {
-            if ((e = cudaEventRecord(ctx->ev_fork, st)) != cudaSuccess) return cuda_fail(ctx, e, "band fork");
-            any_band = true;
-        }
+        any_band = true;
         if ((e = cudaStreamWaitEvent(ctx->lstream[l], ctx->ev_fork, 0)) != cudaSuccess ||
             (e = cudaEventRecord(ctx->ev_lb[l], ctx->lstream[l])) != cudaSuccess)
             return cuda_fail(ctx, e, "band fork");
@@ -1293,9 +1320,42 @@ int batch_dev(mlmc_dk_ctx* ctx, const int64_t* counts, const int64_t* firsts, ui
             return cuda_fail(ctx, e, "band join");
     }
     if ((e = cudaGraphLaunch(ctx->gexec, st)) != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphLaunch");
-    for (int l = nl - 1; l >= 0 && any_band; --l) {
-        if (!band_level(l)) continue;
-        if ((e = cudaStreamWaitEvent(st, ctx->ev_join[l], 0)) != cudaSuccess) return cuda_fail(ctx, e, "band join");
+    // streamed levels (one launch per step or per wave), each on its level's
+    // stream beside the graph: their short CTAs take the SMs the graph's
+    // persistent grids leave, and the levels fill each other's last waves.
+    // Each level's launches are enqueued by a host thread of its own, since
+    // enqueueing blocks while a stream's launch queue is full.
+    std::vector<char> joined(nl, 0);
+    std::vector<int> lrc(nl, MLMC_DK_OK);
+    std::vector<std::thread> enq;
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(ctx, e, "cudaGetDevice");
+    auto enqueue = [ctx, counts, firsts, seed, sums_dev, dev, &lrc](int l) {
+        cudaError_t ee = cudaSetDevice(dev);
+        if (ee == cudaSuccess) ee = cudaStreamWaitEvent(ctx->lstream[l], ctx->ev_fork, 0);
+        if (ee == cudaSuccess) ee = cudaEventRecord(ctx->ev_lb[l], ctx->lstream[l]);
+        if (ee != cudaSuccess) {
+            lrc[l] = cuda_fail(ctx, ee, "streamed level fork");
+            return;
+        }
+        lrc[l] = launch_streamed(ctx, l, 0, firsts[l], counts[l], seed, sums_dev + (size_t)l * ctx->stride, nullptr,
+                                 ctx->lstream[l]);
+        if (lrc[l] != MLMC_DK_OK) return;
+        if ((ee = cudaEventRecord(ctx->ev_le[l], ctx->lstream[l])) != cudaSuccess ||
+            (ee = cudaEventRecord(ctx->ev_join[l], ctx->lstream[l])) != cudaSuccess)
+            lrc[l] = cuda_fail(ctx, ee, "streamed level join");
+    };
+    for (int l = nl - 1; l >= 0; --l) {
+        if (!ctx->lv[l].streamed || band_level(l)) continue;
+        joined[l] = 1;
+        enq.emplace_back(enqueue, l);
+    }
+    for (auto& th : enq) th.join();
+    for (int l = nl - 1; l >= 0; --l)
+        if (lrc[l] != MLMC_DK_OK) return lrc[l];
+    for (int l = nl - 1; l >= 0; --l) {
+        if (!joined[l] && !(any_band && band_level(l))) continue;
+        if ((e = cudaStreamWaitEvent(st, ctx->ev_join[l], 0)) != cudaSuccess) return cuda_fail(ctx, e, "level join");
     }
     if (any_split) {
         for (int l = nl - 1; l >= 0; --l) {
@@ -1312,13 +1372,6 @@ int batch_dev(mlmc_dk_ctx* ctx, const int64_t* counts, const int64_t* firsts, ui
                                                              ctx->d_ssums + (size_t)l * ctx->stride, ctx->stride,
                                                              st)) != cudaSuccess)
                 return cuda_fail(ctx, e, "batch split merge");
-    }
-    for (int l = nl - 1; l >= 0; --l) {
-        if (!ctx->lv[l].streamed || ctx->lv[l].vi(l > 0).band) continue;
-        if ((e = cudaEventRecord(ctx->ev_lb[l], st)) != cudaSuccess) return cuda_fail(ctx, e, "cudaEventRecord");
-        rc = launch_streamed(ctx, l, 0, firsts[l], counts[l], seed, sums_dev + (size_t)l * ctx->stride, nullptr, st);
-        if (rc != MLMC_DK_OK) return rc;
-        if ((e = cudaEventRecord(ctx->ev_le[l], st)) != cudaSuccess) return cuda_fail(ctx, e, "cudaEventRecord");
     }
     return MLMC_DK_OK;
 }

@@ -63,7 +63,7 @@ class LevelDesc(ctypes.Structure):
         ("split_capable", ctypes.c_int32), ("split_fraction", ctypes.c_double), ("batch_streamed", ctypes.c_int64),
         ("theta", ctypes.c_int32), ("theta_b0", ctypes.c_double), ("cheb_steps", ctypes.c_int32),
         ("coupling", ctypes.c_int32), ("fluct", ctypes.c_int32), ("band", ctypes.c_int32),
-        ("bands", ctypes.c_int32),
+        ("bands", ctypes.c_int32), ("persistent", ctypes.c_int32),
     ]
 
 
@@ -140,6 +140,7 @@ def lib() -> ctypes.CDLL:
                                          ctypes.c_double, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
                                          ctypes.c_int32, ROUND_FN, REDUCE_FN, vp, ctypes.POINTER(Result)]
         L.mlmc_dk_band_wait_test.argtypes = [vp, ctypes.c_int32, ctypes.c_uint32, ctypes.c_int32]
+        L.mlmc_dk_stream_wait_test.argtypes = [vp, ctypes.c_int32, ctypes.c_uint32, ctypes.c_int32]
         L.mlmc_dk_run_batch_dev.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.c_int64, ctypes.c_uint64,
                                             vp, vp]
         L.mlmc_dk_run_batch.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.c_uint64, ctypes.POINTER(LevelSums)]
@@ -360,6 +361,10 @@ class Context:
     def band_wait_test(self, level: int, polls: int, stall_band: int) -> int:
         """Failure-detection test of the band kernel's bounded waits; returns the status code."""
         return lib().mlmc_dk_band_wait_test(self._ctx, level, polls, stall_band)
+
+    def stream_wait_test(self, level: int, polls: int, stall_tile: int) -> int:
+        """Failure-detection test of the persistent streamed kernel's bounded waits; returns the status code."""
+        return lib().mlmc_dk_stream_wait_test(self._ctx, level, polls, stall_tile)
 
     def run_batch_dev(self, counts, first: int, seed: int, sums_ptr: int, stream: int = 0):
         """All levels concurrently (CUDA graph); sums_ptr: device double[L_max+1][sums_len]."""

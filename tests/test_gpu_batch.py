@@ -41,6 +41,35 @@ def test_batch_equals_per_level_launches(dk):
                     assert ms[l] > 0
 
 
+@pytest.mark.parametrize("persistent", [False, True])
+def test_batch_with_streamed_levels_beside_the_graph(dk, persistent):
+    """The four-mode workload's 512^2 and 1024^2 levels run on the streamed
+    kernels on their own streams beside the graph of the register levels
+    (short horizon): the same sums as per-level launches, with one launch per
+    step or the persistent launch on the streamed levels."""
+    import torch
+    wl = W.get("large32_1024").with_(T=1e-6)
+    st = torch.cuda.current_stream().cuda_stream
+    counts = [300, 60, 12, 5, 4, 3]
+    with dk.Context.from_workload(wl) as ctx:
+        if persistent:
+            for l in (4, 5):
+                ctx.set_variant(l, True, 3)
+                assert ctx.level_info(l).persistent == 1
+        assert ctx.level_info(4).streamed == 1 and ctx.level_info(5).streamed == 1
+        S = dk.sums_len(ctx.n_quant)
+        batch = torch.full((6, S), float("nan"), dtype=torch.float64, device="cuda")
+        ctx.run_batch_dev(counts, 9, 21, batch.data_ptr(), st)
+        torch.cuda.synchronize()
+        ms = ctx.batch_level_ms()
+        for l, m in enumerate(counts):
+            ref = torch.zeros(S, dtype=torch.float64, device="cuda")
+            ctx.run_level_dev(l, 0, 9, m, 21, ref.data_ptr(), 0, st)
+            torch.cuda.synchronize()
+            np.testing.assert_allclose(batch[l].cpu().numpy(), ref.cpu().numpy(), rtol=1e-12, atol=0)
+            assert ms[l] > 0
+
+
 def test_host_batch_matches_host_levels(dk):
     wl = W.get("mlmc16_256").with_(L_max=2)
     counts = [2000, 300, 40]

@@ -131,13 +131,14 @@ def test_full_size_1024_noise_off_is_mean_field(dk):
     ("mlmc16_256", dict(L_max=4), 4, 3),
 ])
 def test_streamed_kernel_variants_agree(dk, name, kw, level, count):
-    """The two fine-step variants (4 or 5 resident CTAs per SM) compute the
-    same integer paths and reduce them with the same observation kernel:
-    outputs equal exactly; the tuner keeps one of them."""
+    """The six streamed variants (one launch per step, one persistent launch
+    per wave, or one programmatic dependent launch per step; 4 or 5 resident
+    CTAs per SM) compute the same integer paths and reduce them with the same
+    observation kernel: outputs equal exactly; the tuner keeps one of them."""
     wl = W.get(name).with_(**kw)
     with dk.Context.from_workload(wl, stream_from_n=256) as ctx:
         info = ctx.level_info(level)
-        assert info.streamed == 1 and info.n_variants == 2
+        assert info.streamed == 1 and info.n_variants == 6
         for tag in (0, 1):
             coupled = tag == 0
             outs = []
@@ -145,11 +146,75 @@ def test_streamed_kernel_variants_agree(dk, name, kw, level, count):
                 ctx.set_variant(level, coupled, v)
                 if coupled:   # level_info describes the coupled kernel of a level >= 1
                     d = ctx.level_info(level)
-                    assert d.tile_rows == 32 and d.variant_coupled == v
+                    assert d.tile_rows == 32 and d.variant_coupled == v and d.persistent == (v in (2, 3))
                 outs.append(_samples(ctx, dk, level, tag, 7, count, 4))
-            assert np.array_equal(outs[0][1], outs[1][1])
-            assert np.array_equal(outs[0][0], outs[1][0])
+            for o in outs[1:]:
+                assert np.array_equal(outs[0][1], o[1])
+                assert np.array_equal(outs[0][0], o[0])
         secs = ctx.tune(1)
         assert secs > 0
         d = ctx.level_info(level)
         assert d.tile_rows == 32 and d.in_flight >= 1
+
+
+def _persistent(ctx, level, coupled):
+    """Select the persistent streamed build with 5 CTAs per SM (variant 3)."""
+    ctx.set_variant(level, coupled, 3)
+    d = ctx.level_info(level)
+    if coupled or level == 0:
+        assert d.persistent == 1 and d.streamed == 1
+    return d
+
+
+@pytest.mark.parametrize("name,kw,level", [
+    ("lowdens32_512", dict(n0=256, L_max=1, T=4.0e-6), 1),
+    ("large32_1024", dict(n0=512, L_max=1, T=1.52e-6), 1),
+])
+def test_persistent_waves_equal_per_step_launches(dk, name, kw, level):
+    """Several waves of samples in flight and a ragged last wave through the
+    persistent launch (CTAs take (tile, step) items from a counter and wait
+    for the items they read from) give the same integer paths and the same
+    outputs, bit for bit, as one launch per step; coupled and fine-only."""
+    wl = W.get(name).with_(**kw)
+    with dk.Context.from_workload(wl) as ctx:
+        for tag in (0, 1):
+            coupled = tag == 0
+            d = _persistent(ctx, level, True)
+            count = 2 * d.in_flight + 3
+            _persistent(ctx, level, coupled)
+            s_p, a = _samples(ctx, dk, level, tag, 11, count, 19)
+            ctx.set_variant(level, coupled, 0)
+            s_l, b = _samples(ctx, dk, level, tag, 11, count, 19)
+            assert np.array_equal(a, b)
+            assert s_p[0] == count and s_p[1] == 0.0
+            np.testing.assert_allclose(s_p, s_l, rtol=1e-12, atol=0)
+
+
+def test_persistent_and_pdl_full_size_1024_match_per_step_launches(dk):
+    """The full 1024^2 level of the four-mode workload (524288 fine steps),
+    two samples: the persistent launch and the programmatic dependent launches
+    reproduce one launch per step exactly and conserve mass."""
+    wl = W.get("large32_1024")
+    with dk.Context.from_workload(wl) as ctx:
+        _persistent(ctx, 5, True)
+        s_p, a = _samples(ctx, dk, 5, 0, 0, 2, 5)
+        ctx.set_variant(5, True, 5)
+        s_d, c = _samples(ctx, dk, 5, 0, 0, 2, 5)
+        ctx.set_variant(5, True, 0)
+        _, b = _samples(ctx, dk, 5, 0, 0, 2, 5)
+    assert np.array_equal(a, b) and np.array_equal(c, b)
+    assert s_p[0] == 2 and s_p[1] == 0.0 and s_d[0] == 2 and s_d[1] == 0.0
+
+
+def test_persistent_bounded_wait_reports_timeout(dk):
+    """Failure detection without a fault: one tile never reports its step 1,
+    the waits for it (limited to 4096 polls) run out, the kernel records the
+    timeout and every CTA stops, the call returns MLMC_DK_ERR_TIMEOUT, and
+    the same context then runs correct samples."""
+    wl = W.get("lowdens32_512").with_(n0=256, L_max=1, T=4.0e-6)
+    with dk.Context.from_workload(wl) as ctx, dk.Context.from_workload(wl) as ref:
+        assert ctx.stream_wait_test(1, 4096, 5) == dk.ERR_TIMEOUT
+        _persistent(ctx, 1, True)
+        _, a = _samples(ctx, dk, 1, 0, 0, 3, 9)
+        _, b = _samples(ref, dk, 1, 0, 0, 3, 9)
+    assert np.array_equal(a, b)
