@@ -59,21 +59,30 @@ BAND_SOURCES = ("dk_band.cu", "dk_device.cuh")
 # ncu --set full capture (smsp__inst_executed x 32 / fine cell-steps); valid
 # under the recorded hash of its sources.  Bound by instruction issue.
 THETA_KERNEL_INSTR = {"kernel": "theta_kernel n=64 coupled=True b0=0.5 chebyshev_steps=14",
-                      "instructions_per_fine_cell_step": 580.6, "sources_sha256_16": "5f4fec27e80df0df"}
+                      "instructions_per_fine_cell_step": 580.6, "sources_sha256_16": "e8dc915d7d236c06"}
 THETA_SOURCES = ("dk_theta.cu", "dk_device.cuh")
 # Fourier-coupled kernel: thread instructions per cell-step (fine and coarse
 # cell-steps) of the 54^2 coupled launch, from its ncu --set full capture;
 # valid under the recorded hash of its sources.
 FOURIER_KERNEL_INSTR = {"kernel": "fourier_kernel n=54 coupled=True",
-                        "instructions_per_cell_step": 94.6, "sources_sha256_16": "5eb2d85d130ecf3e"}
+                        "instructions_per_cell_step": 94.6, "sources_sha256_16": "f58083f4e5afc61f"}
 FOURIER_SOURCES = ("dk_fourier.cu", "dk_device.cuh")
 
 
-# ncu figures of the dominant kernels, valid while their sources hash to the
-# recorded value: DRAM bytes (read + write) per sample of one launch group, and
-# thread instructions per fine cell-step (smsp__inst_executed x 32 / fine
-# cell-steps); keyed by the kernel description the bench prints.
-KERNEL_PROFILE = {}
+# ncu figures of the dominant kernels per grid size, valid while their sources
+# hash to the recorded value: DRAM bytes (read + write) per fine cell-step of a
+# warm-cache launch (--cache-control none, so the L2-resident working set stays
+# resident as in the bench) and thread instructions per fine cell-step
+# (smsp__inst_executed x 32 / fine cell-steps); keyed by kernel function.
+KERNEL_PROFILE = {
+    "stream_fine_kernel": {
+        "sources": ("dk_stream.cu", "dk_device.cuh"), "sources_sha256_16": "843f4a742dcf92b2",
+        "per_n": {1024: {"dram_bytes_per_fine_cell_step": 0.94, "instructions_per_fine_cell_step": 86.0},
+                  512: {"dram_bytes_per_fine_cell_step": 0.014, "instructions_per_fine_cell_step": 86.0}},
+        "capture": "ncu --cache-control none, 3 consecutive launches of the 1024^2 (5 samples) and 512^2 "
+                   "(8 samples) fine step (profiles/stream_fine_kernel_1024_pdl_full.md, _512_pdl_full.md)",
+    },
+}
 
 
 def kernel_sources_hash(files=KERNEL_SOURCES) -> str:
@@ -633,53 +642,68 @@ def run_ours(args, wl, rank, world, local_rank):
     value = world * sample_steps * args.steps / (total_ms * 1e-3)
     est, var = estimate(*last)
 
-    # ---- roofline of the dominant kernel (the costliest level's kernel)
+    # ---- roofline of the dominant kernel (the costliest level's kernel); the
+    # streamed levels run concurrently on their own streams from one fork, so
+    # their kernel is measured over all of them and their common span
     dom = max(range(L + 1), key=lambda l: level_ms[l])
     if level_ms[dom] <= 0:
         raise SystemExit("no per-level kernel times from the batch")
     dinfo = ctx.level_info(dom)
-    reg_dom = batch_counts[dom] - dinfo.batch_streamed
-    sec_dom = level_ms[dom] * 1e-3
-    fine_cs = reg_dom * fine[dom] * args.steps
-    all_cs = reg_dom * (fine[dom] + coarse[dom]) * args.steps
-    xu_ops = reg_dom * (fine[dom] * XU_OPS_FINE + coarse[dom] * XU_OPS_COARSE) * args.steps
+    group = [dom]
+    if dinfo.streamed and not dinfo.band:
+        group = [l for l in range(L + 1) if batch_counts[l] > 0 and ctx.level_info(l).streamed
+                 and not ctx.level_info(l).band]
+    ginfo = {l: ctx.level_info(l) for l in group}
+    reg = {l: batch_counts[l] - ginfo[l].batch_streamed for l in group}
+    sec_dom = max(level_ms[l] for l in group) * 1e-3
+    fine_cs = sum(reg[l] * fine[l] for l in group) * args.steps
+    all_cs = sum(reg[l] * (fine[l] + coarse[l]) for l in group) * args.steps
+    xu_ops = sum(reg[l] * (fine[l] * XU_OPS_FINE + coarse[l] * XU_OPS_COARSE) for l in group) * args.steps
     xu_peak = XU_PER_CLK_PER_SM * SMS * SM_MAX_MHZ * 1e6
     hbm_peak, hbm_src = measured_peaks()
     if dinfo.band:
         kname = f"band_kernel n={dinfo.n} bands={dinfo.bands} in_flight={dinfo.in_flight} coupled={dom > 0}"
+        family = "band_kernel"
     elif dinfo.streamed:
-        kname = (f"stream_fine_kernel n={dinfo.n} tile_rows={dinfo.tile_rows} in_flight={dinfo.in_flight} "
-                 f"coupled={dom > 0}")
+        how = "persistent" if dinfo.persistent else ("pdl" if dinfo.pdl else "per-step")
+        family = "stream_persist_kernel" if dinfo.persistent else "stream_fine_kernel"
+        kname = (f"{family} ({how}) n=" + ",".join(str(ginfo[l].n) for l in group) +
+                 " in_flight=" + ",".join(str(ginfo[l].in_flight) for l in group) + " coupled=True")
     else:
+        family = "level_kernel"
         kname = (f"level_kernel n={dinfo.n} C={dinfo.lane_cols} R={dinfo.lane_rows} "
                  f"cluster={dinfo.cluster} coupled={dom > 0}")
-    traffic = None
-    rec = KERNEL_PROFILE.get(kname)
-    if rec and kernel_sources_hash(rec["sources"]) == rec["sources_sha256_16"]:
-        traffic = rec["dram_bytes_per_sample"] * reg_dom
-    issue = None
-    if rec and rec.get("instructions_per_fine_cell_step") and traffic is not None:
-        ipc = rec["instructions_per_fine_cell_step"]
-        warp_inst = fine_cs * ipc / 32.0 / sec_dom
-        issue = {"instructions_per_fine_cell_step": ipc, "achieved_warp_inst_per_s": warp_inst,
+    traffic, issue = None, None
+    rec = KERNEL_PROFILE.get(family)
+    if rec and kernel_sources_hash(rec["sources"]) == rec["sources_sha256_16"] and \
+            all(ginfo[l].n in rec["per_n"] for l in group):
+        per_l = {l: reg[l] * fine[l] * args.steps for l in group}     # fine cell-steps of each level
+        traffic = sum(per_l[l] * rec["per_n"][ginfo[l].n]["dram_bytes_per_fine_cell_step"] for l in group)
+        inst = sum(per_l[l] * rec["per_n"][ginfo[l].n]["instructions_per_fine_cell_step"] for l in group)
+        warp_inst = inst / 32.0 / sec_dom
+        issue = {"instructions_per_fine_cell_step": inst / fine_cs, "achieved_warp_inst_per_s": warp_inst,
                  "peak_warp_inst_per_s": 4 * SMS * SM_MAX_MHZ * 1e6,
                  "frac": warp_inst / (4 * SMS * SM_MAX_MHZ * 1e6)}
     hbm_equiv = fine_cs * STREAM_BYTES_PER_FINE_CELL_STEP / sec_dom / 1e9
-    roofline = {"bound": "alu", "pipe": "XU (MUFU)", "kernel": kname,
+    roofline = {"bound": "alu", "pipe": "XU (MUFU)", "kernel": kname, "levels": group,
                 "achieved": xu_ops / sec_dom / 1e9, "peak": xu_peak / 1e9, "unit": "Gop/s",
                 "frac": xu_ops / sec_dom / xu_peak,
-                "traffic": traffic, "traffic_unit": "DRAM bytes per launch group (ncu, per sample x samples)",
-                "ops_per_fine_cell_step": XU_OPS_FINE, "samples_per_step": reg_dom,
+                "traffic": traffic,
+                "traffic_unit": "DRAM bytes over the timed steps: ncu dram__bytes_read.sum + dram__bytes_write.sum "
+                                "per fine cell-step of a warm-cache launch (small case, same kernel) x fine cell-steps",
+                "ops_per_fine_cell_step": XU_OPS_FINE, "samples_per_step": sum(reg.values()),
                 "cell_steps_per_s": all_cs / sec_dom, "fine_cell_steps_per_s": fine_cs / sec_dom,
                 "issue": issue,
                 "hbm_equivalent": {"algorithmic_bytes_per_fine_cell_step": STREAM_BYTES_PER_FINE_CELL_STEP,
                                    "achieved_GBps": hbm_equiv, "peak_GBps": hbm_peak, "peak_source": hbm_src,
                                    "frac": hbm_equiv / hbm_peak,
-                                   "note": "the state stays on chip (registers); DRAM sees the tables only, so this "
-                                           "is the rate a state streamed through HBM would need, not DRAM traffic"},
+                                   "algorithmic_bytes_over_timed_steps": fine_cs * STREAM_BYTES_PER_FINE_CELL_STEP,
+                                   "note": "the rate a state streamed through HBM would need; the streamed levels' "
+                                           "working set stays in L2, so DRAM traffic (`traffic`) is far below it"},
                 "level_ms_per_step": [x / args.steps for x in level_ms],
                 "note": "XU ops are the algorithmic MUFU operations (Box--Muller log, sqrt, sin, cos; sqrt of rho+); "
-                        "peak 16 per clock per SM x 152 SMs x 2.07 GHz"}
+                        "peak 16 per clock per SM x 152 SMs x 2.07 GHz; time = the span of the levels' kernels "
+                        "(CUDA events on their streams)"}
 
     # ---- time to the workload's eps: plain MLMC, MLMC with the learned level, plain MC
     rate = cell_steps * args.steps / (sum(step_ms) * 1e-3)        # the batch's cell-steps per second

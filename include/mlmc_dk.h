@@ -107,8 +107,8 @@ typedef struct {
     double theta_b0;        /* implicit weight b0 in [0, 1] of Eq. (FullyDiscreteDK), b1 = 1 - b0
                                (Definition 2.1): (I - b0 tau/2 Delta_h) rho^m = (I + b1 tau/2 Delta_h)
                                rho^(m-1) + noise.  0: explicit Euler--Maruyama (Section 7.2).  b0 > 0
-                               runs every level on the theta-scheme kernel (n0 2^L_max <= 64, no
-                               stream_from_n); cfl_mu may then exceed 1/2 up to the scheme's
+                               runs every level on the theta-scheme kernel (n0 2^L_max <= 128, no
+                               stream_from_n; a 128^2 level runs on clusters of 8 CTAs per sample); cfl_mu may then exceed 1/2 up to the scheme's
                                stability bound 1 / (2 (b1 - b0)) (none for b0 >= 1/2), with
                                b0 cfl_mu <= 10 */
     int32_t theta_kernel;   /* 1: run b0 = 0 on the theta-scheme kernel too (the same integer
@@ -168,6 +168,8 @@ typedef struct {
     int32_t persistent;     /* 1: the level's streamed kernel in use runs each wave of in_flight samples as one
                                launch whose CTAs take (tile, step) items in order from a counter and wait, with
                                bounded polls, for the items they read from; 0: one launch per step */
+    int32_t pdl;            /* 1: the level's streamed kernel in use launches each step as a programmatic dependent
+                               launch of the previous one (its Philox words are drawn before it waits for it) */
 } mlmc_dk_level_desc;
 
 /* Host-side moment sums of one quantity on one level (accumulated into). */

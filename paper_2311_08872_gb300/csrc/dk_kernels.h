@@ -59,6 +59,7 @@ struct VariantInfo {
     int C, R;               // lane block: C x R coarse cells (2R x 2C fine)
     int tile_rows;          // streamed kernels: fine rows per CTA tile (0 for the register kernels)
     int persistent;         // streamed kernels: 1 = one launch per wave (work items from a counter)
+    int pdl;                // streamed kernels: 1 = programmatic dependent launches (one per step)
     int band;               // 1: the band kernel (a sample over several CTAs, cooperative launch)
     int bands;              // band kernel: bands (CTAs) per sample
 };
@@ -121,6 +122,7 @@ size_t stream_bytes(int n, int S);
 // flight for an n x n level within `budget` bytes of working set, chosen so
 // that the fine-step CTAs of `variant` fill whole waves of the GPU.
 int stream_variant_count();
+int stream_default_variant();
 cudaError_t stream_variant_info(int n, int variant, VariantInfo* out);
 int stream_inflight(int n, size_t budget, int variant);
 void stream_carve(SArgs* a, void* buf, int n, int S);

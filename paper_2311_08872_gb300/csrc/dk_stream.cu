@@ -15,7 +15,9 @@
 // and writes q^{m+1} and, for coupled samples, the running coarse sums zt.
 // After the fourth fine step of a coarse step, a coarse launch forms the
 // coarse transfers from qc and zt (tile and halo) and updates qc.  Kernel
-// boundaries order all reads and writes: no kernel waits on another.
+// boundaries order all reads and writes; in the default build the fine steps
+// are programmatic dependent launches that draw their noise before waiting
+// for the previous kernel.
 //
 // Fine-step CTAs: 16 x 16 threads on a 32 x 64 tile, each thread a 2 x 4 block
 // of fine cells (two coarse cells); two builds, for 4 or 5 resident CTAs per
@@ -663,6 +665,7 @@ size_t stream_bytes(int n, int S) {
 }
 
 int stream_variant_count() { return kStreamVariants; }
+int stream_default_variant() { return 4; }   // one programmatic dependent launch per step, 4 CTAs per SM
 
 // Variants: 0, 1 one launch per step, 2, 3 the persistent launch, 4, 5 one
 // launch per step as programmatic dependent launches; even: at most 64
@@ -710,6 +713,7 @@ cudaError_t stream_variant_info(int n, int variant, VariantInfo* out) {
     out->R = 1;
     out->tile_rows = fr;
     out->persistent = persistent_variant(variant) ? 1 : 0;
+    out->pdl = pdl_variant(variant) ? 1 : 0;
     return cudaSuccess;
 }
 

@@ -31,6 +31,8 @@
 // and below (contiguous 8- and 16-byte accesses), one barrier per Chebyshev
 // step.  The coarse step (1/16 of the work) keeps its state and operands in
 // shared memory.
+#include <cooperative_groups.h>
+
 #include "dk_device.cuh"
 #include "dk_kernels.h"
 
@@ -494,6 +496,413 @@ __global__ void __launch_bounds__(TShape<N>::THREADS) theta_kernel(const KArgs a
     }
 }
 
+// ---------------------------------------------------------------------------
+// Grids beyond one CTA (128 x 128): a thread-block cluster of CL CTAs per
+// sample, CTA `rank` holding the band of BR = NC/CL block rows (its threads
+// own those rows' 2 x 2 blocks as above).  The block fields live in the band's
+// shared memory with the same layout in every CTA; the rows just above and
+// below the band are read from the neighbouring CTAs' shared memory
+// (distributed shared memory), and every barrier that orders a plane's writes
+// before its reads is a cluster barrier.  The arithmetic is the one-CTA
+// kernel's, so both give the same integer paths.
+// ---------------------------------------------------------------------------
+namespace cg = cooperative_groups;
+
+template <int N, int CL>
+struct CShape {
+    static constexpr int NC = N / 2, BR = NC / CL;          // block rows per CTA
+    static constexpr int THREADS = BR * NC;                 // one thread per block of the band
+    static constexpr int BAND = BR * NC;                    // blocks (= coarse cells) per CTA
+    static_assert(NC % CL == 0 && THREADS <= 1024 && THREADS % 32 == 0 && NC % 32 == 0, "band shape");
+    // four block planes of BAND x 16 bytes (top and bottom rows, or an int4 per block),
+    // the coarse state of the band, reduction scratch
+    static size_t smem(int slot_stride) {
+        return 4 * sizeof(float) * 4 * BAND + sizeof(int32_t) * BAND + sizeof(double) * (THREADS / 32) * kRed +
+               sizeof(double) * kRed + sizeof(double) * slot_stride;
+    }
+};
+
+// Pointer into the shared memory of cluster rank r (this CTA's own when r == rank).
+template <class T>
+__device__ __forceinline__ T* band_at(T* local, int r, int rank) {
+    if (r == rank) return local;
+    return cg::this_cluster().map_shared_rank(local, r);
+}
+
+// Neighbours of block (or coarse cell) (lr, I2) of a band of BR rows x NC:
+// left / right in the same row (periodic), above / below in the row before /
+// after, in the neighbouring CTA for the band's first / last row (periodic
+// over the cluster).
+template <int NC, int BR>
+struct BandNbr {
+    int lq, il, ir, ia, ib, ra, rb, rank;
+    __device__ __forceinline__ BandNbr(int lr, int I2, int rank_, int cl) : rank(rank_) {
+        lq = lr * NC + I2;
+        il = lr * NC + (I2 + NC - 1) % NC;
+        ir = lr * NC + (I2 + 1) % NC;
+        if (lr > 0) { ia = lq - NC; ra = rank; } else { ia = (BR - 1) * NC + I2; ra = (rank + cl - 1) % cl; }
+        if (lr < BR - 1) { ib = lq + NC; rb = rank; } else { ib = I2; rb = (rank + 1) % cl; }
+    }
+    template <class T> __device__ __forceinline__ T above(T* p) const { return band_at(p, ra, rank)[ia]; }
+    template <class T> __device__ __forceinline__ T below(T* p) const { return band_at(p, rb, rank)[ib]; }
+    template <class T> __device__ __forceinline__ T left(const T* p) const { return p[il]; }
+    template <class T> __device__ __forceinline__ T right(const T* p) const { return p[ir]; }
+};
+
+__device__ __forceinline__ void cluster_sync() { cg::this_cluster().sync(); }
+
+// Sum of the four neighbours of each cell of block v = (top-left, top-right,
+// bottom-left, bottom-right), from the blocks above / below / left / right,
+// in the one-CTA kernel's order of additions.
+__device__ __forceinline__ void nsum4(const float (&v)[4], float4 A, float4 Bv, float4 L, float4 R, float (&s)[4]) {
+    s[0] = (A.z + v[2]) + (L.y + v[1]);
+    s[1] = (A.w + v[3]) + (v[0] + R.x);
+    s[2] = (v[0] + Bv.x) + (L.w + v[3]);
+    s[3] = (v[1] + Bv.y) + (v[2] + R.z);
+}
+
+template <int NC, int BR>
+__device__ __forceinline__ void nsum_band(const float (&v)[4], const float4* P, const BandNbr<NC, BR>& nb,
+                                          float (&s)[4]) {
+    nsum4(v, nb.above(P), nb.below(P), nb.left(P), nb.right(P), s);
+}
+
+// theta_fine_step for one block of a band (B: four planes of one 16-byte
+// word per block of the band; all neighbours through shared memory).
+template <int NC, int BR>
+__device__ __forceinline__ void theta_fine_step_cl(int32_t (&q)[4], const int32_t (&G1)[4], const int32_t (&G2)[4],
+                                                   const BandNbr<NC, BR>& nb, float* const (&B)[4], long long A,
+                                                   const TArgs& t, unsigned& bad) {
+    const int lq = nb.lq;
+    // ---- exact face fluxes: the top row of the block below, the left column of the block right
+    int4* Qd = reinterpret_cast<int4*>(B[0]);
+    int4* Qr = reinterpret_cast<int4*>(B[3]);
+    Qd[lq] = make_int4(q[0], q[1], G1[0], G1[1]);
+    Qr[lq] = make_int4(q[0], q[2], G2[0], G2[2]);
+    cluster_sync();
+    const int4 bq = nb.below(Qd), rq = nb.right(Qr);
+    const int32_t qdn[4] = {q[2], q[3], bq.x, bq.y}, gdn[4] = {G1[2], G1[3], bq.z, bq.w};
+    const int32_t qrt[4] = {q[1], rq.x, q[3], rq.y}, grt[4] = {G2[1], rq.z, G2[3], rq.w};
+    int32_t F1[4], F2[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const long long f1 = (long long)edge_flux64(A, qdn[c] - q[c]) + G1[c] + gdn[c];
+        const long long f2 = (long long)edge_flux64(A, qrt[c] - q[c]) + G2[c] + grt[c];
+        bad |= (unsigned)((f1 != (long long)(int32_t)f1) | (f2 != (long long)(int32_t)f2));
+        F1[c] = static_cast<int32_t>(f1);
+        F2[c] = static_cast<int32_t>(f2);
+    }
+    float u1[4] = {0.f, 0.f, 0.f, 0.f}, u2[4] = {0.f, 0.f, 0.f, 0.f};
+    float* hplane = B[1];
+    if (t.K > 0) {
+        float f1[4], f2[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            f1[c] = static_cast<float>(F1[c]);
+            f2[c] = static_cast<float>(F2[c]);
+        }
+        float4* PF1 = reinterpret_cast<float4*>(B[1]);
+        float4* PF2 = reinterpret_cast<float4*>(B[2]);
+        PF1[lq] = make_float4(f1[0], f1[1], f1[2], f1[3]);
+        PF2[lq] = make_float4(f2[0], f2[1], f2[2], f2[3]);
+        cluster_sync();   // also orders every read of B[0], B[3] before they are reused below
+        float s1[4], s2[4], r1[4], r2[4], d1[4], d2[4];
+        nsum_band(f1, PF1, nb, s1);
+        nsum_band(f2, PF2, nb, s2);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            r1[c] = -t.alpha * (4.f * f1[c] - s1[c]);
+            r2[c] = -t.alpha * (4.f * f2[c] - s2[c]);
+            d1[c] = r1[c] * t.inv_theta;
+            d2[c] = r2[c] * t.inv_theta;
+        }
+        float4* cur1 = reinterpret_cast<float4*>(B[3]);
+        float4* cur2 = reinterpret_cast<float4*>(B[0]);
+        float4* nxt1 = reinterpret_cast<float4*>(B[1]);
+        float4* nxt2 = reinterpret_cast<float4*>(B[2]);
+        cur1[lq] = make_float4(d1[0], d1[1], d1[2], d1[3]);
+        cur2[lq] = make_float4(d2[0], d2[1], d2[2], d2[3]);
+        cluster_sync();
+        const float diag = 1.f + 4.f * t.alpha;
+        for (int k = 0; k < t.K; ++k) {
+            nsum_band(d1, cur1, nb, s1);
+            nsum_band(d2, cur2, nb, s2);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                u1[c] += d1[c];
+                u2[c] += d2[c];
+                r1[c] -= diag * d1[c] - t.alpha * s1[c];
+                r2[c] -= diag * d2[c] - t.alpha * s2[c];
+            }
+            if (k + 1 < t.K) {
+                const float ca = t.c1[k], cb = t.c2[k];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    d1[c] = ca * d1[c] + cb * r1[c];
+                    d2[c] = ca * d2[c] + cb * r2[c];
+                }
+                nxt1[lq] = make_float4(d1[0], d1[1], d1[2], d1[3]);
+                nxt2[lq] = make_float4(d2[0], d2[1], d2[2], d2[3]);
+                cluster_sync();
+                float4* x = cur1; cur1 = nxt1; nxt1 = x;
+                x = cur2; cur2 = nxt2; nxt2 = x;
+            }
+        }
+        hplane = reinterpret_cast<float*>(nxt1);   // not read by the last Chebyshev step
+    }
+    int32_t H1[4], H2[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const long long h1 = (long long)F1[c] + __float2ll_rn(u1[c]);
+        const long long h2 = (long long)F2[c] + __float2ll_rn(u2[c]);
+        bad |= (unsigned)((h1 != (long long)(int32_t)h1) | (h2 != (long long)(int32_t)h2));
+        H1[c] = static_cast<int32_t>(h1);
+        H2[c] = static_cast<int32_t>(h2);
+    }
+    int4* Hb = reinterpret_cast<int4*>(hplane);
+    Hb[lq] = make_int4(H1[2], H1[3], H2[1], H2[3]);
+    cluster_sync();
+    const int4 ha = nb.above(Hb), hl = nb.left(Hb);
+    const int32_t h1up[4] = {ha.x, ha.y, H1[0], H1[1]}, h2lf[4] = {hl.z, H2[0], hl.w, H2[2]};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const long long v = (long long)q[c] + ((long long)H1[c] - h1up[c]) + ((long long)H2[c] - h2lf[c]);
+        bad |= (unsigned)((v >= (1LL << 30)) | (v <= -(1LL << 30)));
+        q[c] = static_cast<int32_t>(v);
+    }
+    cluster_sync();
+}
+
+// theta_step<NC, 1> for one coarse cell of a band: sq the band's coarse
+// state, P0 / P2 the coarse transfers G_1 / G_2 (as integers) on entry, P0..P3
+// band planes of one float per cell.  The one-CTA step's arithmetic and order
+// of additions.
+template <int NC, int BR>
+__device__ __forceinline__ void theta_coarse_step_cl(int32_t& q, const BandNbr<NC, BR>& nb, int32_t* sq, float* P0,
+                                                     float* P1, float* P2, float* P3, long long A, const TArgs& t,
+                                                     unsigned& bad) {
+    const int idx = nb.lq;
+    const int32_t g1 = as_i(P0[idx]), g2 = as_i(P2[idx]);
+    const long long F1 = (long long)edge_flux64(A, nb.below(sq) - q) + g1 + as_i(nb.below(P0));
+    const long long F2 = (long long)edge_flux64(A, nb.right(sq) - q) + g2 + as_i(nb.right(P2));
+    float u1 = 0.f, u2 = 0.f;
+    float* out1 = P1;
+    float* out2 = P3;
+    if (t.K > 0) {
+        P1[idx] = static_cast<float>(F1);
+        P3[idx] = static_cast<float>(F2);
+        cluster_sync();
+        const float f1 = P1[idx], f2 = P3[idx];
+        const float l1 = 4.f * f1 - nb.above(P1) - nb.below(P1) - nb.left(P1) - nb.right(P1);
+        const float l2 = 4.f * f2 - nb.above(P3) - nb.below(P3) - nb.left(P3) - nb.right(P3);
+        float r1 = -t.alpha * l1, r2 = -t.alpha * l2;
+        float d1 = r1 * t.inv_theta, d2 = r2 * t.inv_theta;
+        P0[idx] = d1;
+        P2[idx] = d2;
+        cluster_sync();
+        float *c1p = P0, *c2p = P2, *n1p = P1, *n2p = P3;
+        const float diag = 1.f + 4.f * t.alpha;
+        for (int k = 0; k < t.K; ++k) {
+            const float a1 = diag * d1 - t.alpha * (nb.above(c1p) + nb.below(c1p) + nb.left(c1p) + nb.right(c1p));
+            const float a2 = diag * d2 - t.alpha * (nb.above(c2p) + nb.below(c2p) + nb.left(c2p) + nb.right(c2p));
+            u1 += d1;
+            u2 += d2;
+            r1 -= a1;
+            r2 -= a2;
+            if (k + 1 < t.K) {
+                d1 = t.c1[k] * d1 + t.c2[k] * r1;
+                d2 = t.c1[k] * d2 + t.c2[k] * r2;
+                n1p[idx] = d1;
+                n2p[idx] = d2;
+                cluster_sync();
+                float* x = c1p; c1p = n1p; n1p = x;
+                x = c2p; c2p = n2p; n2p = x;
+            }
+        }
+        out1 = n1p;
+        out2 = n2p;
+    }
+    const long long H1 = F1 + __float2ll_rn(u1), H2 = F2 + __float2ll_rn(u2);
+    bad |= (unsigned)((H1 != (long long)(int32_t)H1) | (H2 != (long long)(int32_t)H2));
+    out1[idx] = as_f(static_cast<int32_t>(H1));
+    out2[idx] = as_f(static_cast<int32_t>(H2));
+    cluster_sync();
+    const long long v = (long long)q + (H1 - as_i(nb.above(out1))) + (H2 - as_i(nb.left(out2)));
+    bad |= (unsigned)((v >= (1LL << 30)) | (v <= -(1LL << 30)));
+    q = static_cast<int32_t>(v);
+    sq[idx] = q;
+    cluster_sync();
+}
+
+// The theta-scheme sample kernel for a cluster of CL CTAs per sample (see
+// above); a cluster is one sample slot of a persistent grid of clusters.
+template <int N, int CL, bool CPL>
+__global__ void __launch_bounds__(CShape<N, CL>::THREADS, 1) theta_cluster_kernel(const KArgs a, const TArgs t) {
+    using S = CShape<N, CL>;
+    constexpr int NC = S::NC, BR = S::BR, BAND = S::BAND, THREADS = S::THREADS;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int tid = threadIdx.x;
+    const int rank = static_cast<int>(cg::this_cluster().block_rank());
+    float* P0 = reinterpret_cast<float*>(smem_raw);
+    float* P1 = P0 + 4 * BAND;
+    float* P2 = P1 + 4 * BAND;
+    float* P3 = P2 + 4 * BAND;
+    int32_t* sqc = reinterpret_cast<int32_t*>(P3 + 4 * BAND);
+    double* red = reinterpret_cast<double*>(sqc + BAND);
+    double* tot = red + (THREADS / 32) * kRed;       // this CTA's band total
+    double* acc = tot + kRed;                        // the slot's moment sums (rank 0)
+    for (int i = tid; i < a.slot_stride; i += THREADS) acc[i] = 0.0;
+    float* const planes[4] = {P0, P1, P2, P3};
+
+    const int lr = tid / NC, I2 = tid % NC;           // block row within the band, column
+    const int I1 = rank * BR + lr;                    // coarse cell; fine block rows 2 I1 + v1, cols 2 I2 + v2
+    const BandNbr<NC, BR> nb(lr, I2, rank, CL);
+    const int gc = I1 * NC + I2;                      // global coarse index
+    const int f00 = (2 * I1) * N + 2 * I2;
+    const int fidx[4] = {f00, f00 + 1, f00 + N, f00 + N + 1};
+    const uint32_t p_top = static_cast<uint32_t>(f00 >> 1);
+    const uint32_t p_bot = static_cast<uint32_t>((f00 + N) >> 1);
+
+    const long long n_slots = (long long)gridDim.x / CL;
+    const long long slot = (long long)blockIdx.x / CL;
+    const long long iters = a.count > slot ? (a.count - slot + n_slots - 1) / n_slots : 0;
+    unsigned bad = 0;
+    cluster_sync();
+
+    for (long long it = 0; it < iters; ++it) {
+        const long long idx = slot + it * n_slots;
+        const bool active = idx < a.count;
+        const long long sid = a.first + (active ? idx : 0);
+        const uint32_t c2 = static_cast<uint32_t>(sid);
+        const uint32_t c3 = a.tag | ((static_cast<uint32_t>(static_cast<unsigned long long>(sid) >> 32) & 0xffffu) << 16);
+
+        int32_t q[4], qc = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) q[i] = a.q0f[fidx[i]];
+        float zt0 = 0.f, zt1 = 0.f;
+        if constexpr (CPL) {
+            qc = a.q0c[gc];
+            sqc[nb.lq] = qc;
+        }
+        cluster_sync();
+
+        for (int m = 0; m < a.M; ++m) {
+            int32_t G1[4], G2[4];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint4 x = philox10(make_uint4(h ? p_bot : p_top, static_cast<uint32_t>(m), c2, c3), a.key0, a.key1);
+                float ra, ca, sa, rb, cb, sb;
+                box_muller_polar(x.x, x.y, ra, ca, sa);
+                box_muller_polar(x.z, x.w, rb, cb, sb);
+                const float ta = noise_amp(q[2 * h], a.gf) * ra;
+                const float tb = noise_amp(q[2 * h + 1], a.gf) * rb;
+                G1[2 * h] = __float2int_rn(ta * ca);
+                G2[2 * h] = __float2int_rn(ta * sa);
+                G1[2 * h + 1] = __float2int_rn(tb * cb);
+                G2[2 * h + 1] = __float2int_rn(tb * sb);
+                if constexpr (CPL) {
+                    zt0 = fmaf(rb, cb, fmaf(ra, ca, zt0));
+                    zt1 = fmaf(rb, sb, fmaf(ra, sa, zt1));
+                }
+            }
+            theta_fine_step_cl<NC, BR>(q, G1, G2, nb, planes, t.Af64, t, bad);
+
+            if constexpr (CPL) {
+                if ((m & 3) == 3) {
+                    const float sc = noise_amp(qc, a.gc);
+                    P0[nb.lq] = as_f(__float2int_rn(sc * zt0));
+                    P2[nb.lq] = as_f(__float2int_rn(sc * zt1));
+                    zt0 = zt1 = 0.f;
+                    cluster_sync();
+                    theta_coarse_step_cl<NC, BR>(qc, nb, sqc, P0, P1, P2, P3, t.Ac64, t, bad);
+                }
+            }
+        }
+
+        // ---- observables of the band, then the band totals summed on rank 0 in rank order
+        double v[kRed];
+        {
+            long long mf = 0;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) mf += q[i];
+            v[2 * kMaxObs] = static_cast<double>(mf);
+            v[2 * kMaxObs + 1] = CPL ? static_cast<double>(qc) : 0.0;
+#pragma unroll
+            for (int k = 0; k < kMaxObs; ++k) {
+                double sf = 0.0, sc = 0.0;
+                if (k < a.n_obs) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        sf += static_cast<double>(q[i] - a.qbf[fidx[i]]) * t.phif64[(size_t)k * N * N + fidx[i]];
+                    if constexpr (CPL) sc = static_cast<double>(qc - a.qbc[gc]) * t.phic64[(size_t)k * NC * NC + gc];
+                }
+                v[k] = sf;
+                v[kMaxObs + k] = sc;
+            }
+        }
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1)
+#pragma unroll
+            for (int i = 0; i < kRed; ++i) v[i] += __shfl_xor_sync(kFullMask, v[i], off);
+        if ((tid & 31) == 0)
+#pragma unroll
+            for (int i = 0; i < kRed; ++i) red[(tid >> 5) * kRed + i] = v[i];
+        __syncthreads();
+        if (tid < kRed) {
+            double x = 0.0;
+            for (int w = 0; w < THREADS / 32; ++w) x += red[w * kRed + tid];
+            tot[tid] = x;
+        }
+        cluster_sync();
+        if (rank == 0 && tid == 0 && active) {
+            for (int i = 0; i < kRed; ++i) {
+                double x = 0.0;
+                for (int r = 0; r < CL; ++r) x += band_at(tot, r, 0)[i];
+                v[i] = x;
+            }
+            double Df[kMaxObs], Dc[kMaxObs];
+#pragma unroll
+            for (int k = 0; k < kMaxObs; ++k) {
+                Df[k] = a.dscale_f * v[k] + a.delta_f[k];
+                Dc[k] = CPL ? a.dscale_c * v[kMaxObs + k] + a.delta_c[k] : 0.0;
+            }
+            acc[0] += 1.0;
+            double merr = fabs(v[2 * kMaxObs] - static_cast<double>(a.mass0_f)) * a.dscale_f;
+            if (CPL) merr = fmax(merr, fabs(v[2 * kMaxObs + 1] - static_cast<double>(a.mass0_c)) * a.dscale_c);
+            acc[1] = fmax(acc[1], merr);
+            int qi = 0;
+            for (int j = 0; j < a.n_obs; ++j) {
+                const int kend = a.products ? a.n_obs : j + 1;
+                for (int k = j; k < kend; ++k, ++qi) {
+                    const double pf = a.N * Df[j] * Df[k];
+                    const double pc = CPL ? a.N * Dc[j] * Dc[k] : 0.0;
+                    const double dp = pf - pc, dp2 = dp * dp;
+                    double* B = acc + 2 + kNSum * qi;
+                    B[0] += dp; B[1] += dp2; B[2] += dp2 * dp; B[3] += dp2 * dp2;
+                    B[4] += pf; B[5] += pf * pf; B[6] += pc; B[7] += pc * pc;
+                    B[8] += Df[j]; B[9] += Df[j] * Df[j]; B[10] += Dc[j]; B[11] += Dc[j] * Dc[j];
+                }
+            }
+            if (a.samples) {
+                double* o = a.samples + idx * (2 * a.n_obs + 2);
+                for (int k = 0; k < a.n_obs; ++k) {
+                    o[k] = Df[k];
+                    o[a.n_obs + k] = Dc[k];
+                }
+                o[2 * a.n_obs] = v[2 * kMaxObs] * a.dscale_f;
+                o[2 * a.n_obs + 1] = CPL ? v[2 * kMaxObs + 1] * a.dscale_c : 0.0;
+            }
+        }
+        cluster_sync();   // the band totals and the state planes are reused by the next sample
+    }
+    if (bad) atomicOr(a.err, kErrRange);
+
+    // ---- the slot's partial sums (rank 0), entry-major [stride][n_slots]
+    __syncthreads();
+    if (rank == 0)
+        for (int i = tid; i < a.slot_stride; i += THREADS) a.partials[(size_t)i * n_slots + slot] = acc[i];
+}
+
 template <int N, bool CPL>
 cudaError_t prepare(int slot_stride, VariantInfo* out) {
     using S = TShape<N>;
@@ -536,9 +945,69 @@ cudaError_t launch_n(const KArgs& a, const TArgs& t, int n_ctas, cudaStream_t st
     return cudaLaunchKernelEx(&cfg, theta_kernel<N, CPL>, a, t);
 }
 
+// Grids beyond one CTA: clusters of CL CTAs.
+constexpr int kThetaClusterN = 128, kThetaClusterCL = 8;
+
+template <int N, int CL, bool CPL>
+cudaError_t prepare_cluster(int slot_stride, VariantInfo* out) {
+    using S = CShape<N, CL>;
+    const size_t smem = S::smem(slot_stride);
+    cudaError_t e = cudaFuncSetAttribute(theta_cluster_kernel<N, CL, CPL>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(CL);
+    cfg.blockDim = dim3(S::THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    if ((e = cudaOccupancyMaxActiveClusters(&clusters, theta_cluster_kernel<N, CL, CPL>, &cfg)) != cudaSuccess)
+        return e;
+    *out = VariantInfo{};
+    out->supported = clusters > 0;
+    out->threads = S::THREADS;
+    out->cluster = CL;
+    out->slots_per_cta = 1;   // one sample slot per cluster
+    out->smem = smem;
+    out->max_ctas = clusters * CL;
+    return cudaSuccess;
+}
+
+template <int N, int CL, bool CPL>
+cudaError_t launch_cluster(const KArgs& a, const TArgs& t, int n_ctas, cudaStream_t st, int priority) {
+    using S = CShape<N, CL>;
+    if (n_ctas % CL != 0) return cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(n_ctas);
+    cfg.blockDim = dim3(S::THREADS);
+    cfg.dynamicSmemBytes = S::smem(a.slot_stride);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[2];
+    int na = 0;
+    attr[na].id = cudaLaunchAttributeClusterDimension;
+    attr[na].val.clusterDim.x = CL;
+    attr[na].val.clusterDim.y = 1;
+    attr[na].val.clusterDim.z = 1;
+    ++na;
+    if (priority != 0) {
+        attr[na].id = cudaLaunchAttributePriority;
+        attr[na].val.priority = priority;
+        ++na;
+    }
+    cfg.attrs = attr;
+    cfg.numAttrs = na;
+    return cudaLaunchKernelEx(&cfg, theta_cluster_kernel<N, CL, CPL>, a, t);
+}
+
 }  // namespace
 
-bool theta_supported(int n) { return n == 4 || n == 8 || n == 16 || n == 32 || n == 64; }
+bool theta_supported(int n) { return n == 4 || n == 8 || n == 16 || n == 32 || n == 64 || n == kThetaClusterN; }
 
 cudaError_t theta_variant_info(int n, bool coupled, int slot_stride, VariantInfo* out) {
     *out = VariantInfo{};
@@ -548,6 +1017,9 @@ cudaError_t theta_variant_info(int n, bool coupled, int slot_stride, VariantInfo
         case 16: return coupled ? prepare<16, true>(slot_stride, out) : prepare<16, false>(slot_stride, out);
         case 32: return coupled ? prepare<32, true>(slot_stride, out) : prepare<32, false>(slot_stride, out);
         case 64: return coupled ? prepare<64, true>(slot_stride, out) : prepare<64, false>(slot_stride, out);
+        case kThetaClusterN:
+            return coupled ? prepare_cluster<kThetaClusterN, kThetaClusterCL, true>(slot_stride, out)
+                           : prepare_cluster<kThetaClusterN, kThetaClusterCL, false>(slot_stride, out);
         default: return cudaSuccess;   // supported = 0
     }
 }
@@ -561,6 +1033,9 @@ cudaError_t launch_theta(int n, bool coupled, const KArgs& a, const TArgs& t, in
         case 16: return coupled ? launch_n<16, true>(a, t, n_ctas, st, priority) : launch_n<16, false>(a, t, n_ctas, st, priority);
         case 32: return coupled ? launch_n<32, true>(a, t, n_ctas, st, priority) : launch_n<32, false>(a, t, n_ctas, st, priority);
         case 64: return coupled ? launch_n<64, true>(a, t, n_ctas, st, priority) : launch_n<64, false>(a, t, n_ctas, st, priority);
+        case kThetaClusterN:
+            return coupled ? launch_cluster<kThetaClusterN, kThetaClusterCL, true>(a, t, n_ctas, st, priority)
+                           : launch_cluster<kThetaClusterN, kThetaClusterCL, false>(a, t, n_ctas, st, priority);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -100,6 +100,7 @@ struct mlmc_dk_ctx {
     // beside the graph, on the least urgent stream, on the SMs clusters leave
     cudaStream_t sstream = nullptr;
     cudaEvent_t ev_sfork = nullptr, ev_sjoin = nullptr;
+    cudaEvent_t ev_graph = nullptr;        // the batch graph's completion (streamed levels start after it)
     double* d_ssums = nullptr;        // [L_max+1][stride] sums of the streamed share
     double* d_bsums = nullptr;        // device sums of mlmc_dk_run_batch
     double* h_bsums = nullptr;        // pinned host copy
@@ -559,6 +560,7 @@ void release(mlmc_dk_ctx* c) {
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->ev_sfork) cudaEventDestroy(c->ev_sfork);
     if (c->ev_sjoin) cudaEventDestroy(c->ev_sjoin);
+    if (c->ev_graph) cudaEventDestroy(c->ev_graph);
     if (c->sstream) cudaStreamDestroy(c->sstream);
     cudaFree(c->d_ssums);
     cudaFree(c->d_bsums);
@@ -653,8 +655,8 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
         return fail(nullptr, MLMC_DK_ERR_INVALID, "tau/h^2 above the theta-scheme's stability bound 1/(2 (b1 - b0))");
     dk::TArgs targs{};
     if (theta) {
-        if ((cfg->n0 << cfg->L_max) > 64 || cfg->stream_from_n != 0)
-            return fail(nullptr, MLMC_DK_ERR_UNSUPPORTED, "theta-scheme kernel: grids up to 64^2, no streamed levels");
+        if ((cfg->n0 << cfg->L_max) > 128 || cfg->stream_from_n != 0)
+            return fail(nullptr, MLMC_DK_ERR_UNSUPPORTED, "theta-scheme kernel: grids up to 128^2, no streamed levels");
         const double alpha = b0 * tau0 / (2.0 * h0 * h0);
         targs.alpha = (float)alpha;
         targs.inv_theta = (float)(1.0 / (1.0 + 4.0 * alpha));
@@ -941,6 +943,7 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
                     t.vis[mode].push_back(vi);
                 }
             }
+            t.sel[0] = t.sel[1] = dk::stream_default_variant();
             if ((e = cudaMalloc(&t.d_stream, dk::stream_bytes(t.n, t.inflight))) != cudaSuccess ||
                 (e = cudaMalloc(&t.d_spart, sizeof(double) * c->stride * t.inflight)) != cudaSuccess) {
                 mlmc_dk_free(c);
@@ -1007,8 +1010,9 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
         }
         if (!t.streamed && !c->fluct && t.n >= 256 && t.n % 64 == 0) {
             // register level with 8-SM clusters: streamed buffers for a batch split
-            t.inflight_v[0] = dk::stream_inflight(t.n, (size_t)96 << 20, 0);
-            t.inflight = t.inflight_v[0];
+            const int dv = dk::stream_default_variant();
+            t.inflight_v[dv] = dk::stream_inflight(t.n, (size_t)96 << 20, dv);
+            t.inflight = t.inflight_v[dv];
             if ((e = cudaMalloc(&t.d_stream, dk::stream_bytes(t.n, t.inflight))) != cudaSuccess ||
                 (e = cudaMalloc(&t.d_spart, sizeof(double) * c->stride * t.inflight)) != cudaSuccess) {
                 mlmc_dk_free(c);
@@ -1061,6 +1065,7 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
         (e = cudaStreamCreateWithPriority(&c->sstream, cudaStreamNonBlocking, prio_lo)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&c->ev_sfork, cudaEventDisableTiming)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&c->ev_sjoin, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&c->ev_graph, cudaEventDisableTiming)) != cudaSuccess ||
         (e = cudaMalloc(&c->d_ssums, sizeof(double) * c->stride * nl)) != cudaSuccess ||
         (e = cudaMalloc(&c->d_bsums, sizeof(double) * c->stride * nl)) != cudaSuccess ||
         (e = cudaMallocHost(&c->h_bsums, sizeof(double) * c->stride * nl)) != cudaSuccess) {
@@ -1104,7 +1109,8 @@ int mlmc_dk_level_info(const mlmc_dk_ctx* ctx, int32_t level, mlmc_dk_level_desc
     out->lane_rows = vs.R;
     out->cluster = vs.cluster;
     out->streamed = t.streamed;
-    out->in_flight = t.streamed ? t.inflight_v[t.sel[level > 0 ? 1 : 0]] : (t.split_ok ? t.inflight_v[0] : 0);
+    out->in_flight = t.streamed ? t.inflight_v[t.sel[level > 0 ? 1 : 0]]
+                                : (t.split_ok ? t.inflight_v[dk::stream_default_variant()] : 0);
     out->tile_rows = vs.tile_rows;
     out->split_capable = t.split_ok;
     out->split_fraction = t.split_frac;
@@ -1117,6 +1123,7 @@ int mlmc_dk_level_info(const mlmc_dk_ctx* ctx, int32_t level, mlmc_dk_level_desc
     out->band = vs.band ? 1 : 0;
     out->bands = vs.bands;
     out->persistent = vs.persistent;
+    out->pdl = vs.pdl;
     if (vs.band) out->in_flight = t.bplan[level > 0 ? 1 : 0][vs.band == 4 ? 0 : 1].S;
     return MLMC_DK_OK;
 }
@@ -1321,10 +1328,12 @@ int batch_dev(mlmc_dk_ctx* ctx, const int64_t* counts, const int64_t* firsts, ui
     }
     if ((e = cudaGraphLaunch(ctx->gexec, st)) != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphLaunch");
     // streamed levels (one launch per step or per wave), each on its level's
-    // stream beside the graph: their short CTAs take the SMs the graph's
-    // persistent grids leave, and the levels fill each other's last waves.
-    // Each level's launches are enqueued by a host thread of its own, since
-    // enqueueing blocks while a stream's launch queue is full.
+    // stream, after the graph (whose cluster grids would otherwise wait for
+    // free SMs behind the streamed levels' stream of short CTAs) and beside
+    // each other: the levels fill each other's last waves.  Each level's
+    // launches are enqueued by a host thread of its own, since enqueueing
+    // blocks while a stream's launch queue is full.
+    if ((e = cudaEventRecord(ctx->ev_graph, st)) != cudaSuccess) return cuda_fail(ctx, e, "graph event");
     std::vector<char> joined(nl, 0);
     std::vector<int> lrc(nl, MLMC_DK_OK);
     std::vector<std::thread> enq;
@@ -1332,7 +1341,7 @@ int batch_dev(mlmc_dk_ctx* ctx, const int64_t* counts, const int64_t* firsts, ui
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(ctx, e, "cudaGetDevice");
     auto enqueue = [ctx, counts, firsts, seed, sums_dev, dev, &lrc](int l) {
         cudaError_t ee = cudaSetDevice(dev);
-        if (ee == cudaSuccess) ee = cudaStreamWaitEvent(ctx->lstream[l], ctx->ev_fork, 0);
+        if (ee == cudaSuccess) ee = cudaStreamWaitEvent(ctx->lstream[l], ctx->ev_graph, 0);
         if (ee == cudaSuccess) ee = cudaEventRecord(ctx->ev_lb[l], ctx->lstream[l]);
         if (ee != cudaSuccess) {
             lrc[l] = cuda_fail(ctx, ee, "streamed level fork");
@@ -1361,7 +1370,8 @@ int batch_dev(mlmc_dk_ctx* ctx, const int64_t* counts, const int64_t* firsts, ui
         for (int l = nl - 1; l >= 0; --l) {
             if (n_split[l] == 0) continue;
             rc = launch_streamed(ctx, l, 0, firsts[l] + n_reg[l], n_split[l], seed,
-                                 ctx->d_ssums + (size_t)l * ctx->stride, nullptr, ctx->sstream, 0, 0);
+                                 ctx->d_ssums + (size_t)l * ctx->stride, nullptr, ctx->sstream, 0,
+                                 dk::stream_default_variant());
             if (rc != MLMC_DK_OK) return rc;
         }
         if ((e = cudaEventRecord(ctx->ev_sjoin, ctx->sstream)) != cudaSuccess ||

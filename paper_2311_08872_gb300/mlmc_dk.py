@@ -63,7 +63,7 @@ class LevelDesc(ctypes.Structure):
         ("split_capable", ctypes.c_int32), ("split_fraction", ctypes.c_double), ("batch_streamed", ctypes.c_int64),
         ("theta", ctypes.c_int32), ("theta_b0", ctypes.c_double), ("cheb_steps", ctypes.c_int32),
         ("coupling", ctypes.c_int32), ("fluct", ctypes.c_int32), ("band", ctypes.c_int32),
-        ("bands", ctypes.c_int32), ("persistent", ctypes.c_int32),
+        ("bands", ctypes.c_int32), ("persistent", ctypes.c_int32), ("pdl", ctypes.c_int32),
     ]
 
 

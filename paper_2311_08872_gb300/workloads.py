@@ -29,6 +29,7 @@ Workloads:
   * ``theta16_64``   -- Crank--Nicolson weights b0 = b1 = 1/2 of Eq.
                         (FullyDiscreteDK) at tau/h^2 = 1 (twice the explicit
                         limit), levels 16^2..64^2, T=0.02, N=1e5.
+  * ``theta16_128``  -- the same weights and step ratio on levels 16^2..128^2.
   * ``implicit16_64``-- implicit Euler weights b0 = 1, b1 = 0 at tau/h^2 = 2,
                         same grids.
   * ``fourier6_54``  -- Fourier coupling (Section 3.1), levels 6^2, 18^2, 54^2
@@ -228,6 +229,9 @@ WORKLOADS: Dict[str, Workload] = {
     "theta16_64": Workload("theta16_64", 1.0, 16, 2, 0.02, 1.0, 1e5, "sinsin", [COS1],
                            seed=7, eps_rel=1e-2, b0=0.5,
                            note="Crank-Nicolson weights at tau/h^2 = 1, levels 16^2..64^2"),
+    "theta16_128": Workload("theta16_128", 1.0, 16, 3, 0.02, 1.0, 1e5, "sinsin", [COS1],
+                            seed=7, eps_rel=1e-2, b0=0.5,
+                            note="Crank-Nicolson weights at tau/h^2 = 1, levels 16^2..128^2 (128^2 on 8-CTA clusters)"),
     "implicit16_64": Workload("implicit16_64", 1.0, 16, 2, 0.02, 2.0, 1e5, "sinsin", [COS1],
                               seed=8, eps_rel=1e-2, b0=1.0,
                               note="implicit Euler weights at tau/h^2 = 2, levels 16^2..64^2"),

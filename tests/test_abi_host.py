@@ -98,13 +98,13 @@ def test_init_without_gpu_fails_loudly(dk):
 def test_theta_scheme_config_checks(dk):
     """Weights of Eq. (FullyDiscreteDK): b0 in [0, 1]; with b1 > b0 the step
     ratio is bounded by 1 / (2 (b1 - b0)); the theta kernel covers grids up to
-    64^2 and a bounded number of solve steps."""
+    128^2 and a bounded number of solve steps."""
     one = [np.ones((4, 4))]
     phi = [[np.ones((4, 4))]]
     cases = [(dict(theta_b0=1.5), 0.1, 4, dk.ERR_INVALID),
              (dict(theta_b0=0.25), 1.2, 4, dk.ERR_INVALID),
              (dict(theta_b0=1.0), 25.0, 4, dk.ERR_UNSUPPORTED),
-             (dict(theta_b0=0.5), 3.0, 128, dk.ERR_UNSUPPORTED)]
+             (dict(theta_b0=0.5), 3.0, 256, dk.ERR_UNSUPPORTED)]
     for kw, mu, n0, code in cases:
         r = [np.ones((n0, n0))]
         with pytest.raises(dk.MLMCError) as e:

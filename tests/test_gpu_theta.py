@@ -90,6 +90,59 @@ def test_theta_kernel_matches_oracle(dk, name, level, tag, count):
     print(f"{name} level {level} tag {tag}: worst/bound {w:.3g}, Chebyshev steps {info.cheb_steps}")
 
 
+@pytest.mark.parametrize("name,tag", [("theta16_64", 0), ("theta16_64", 1), ("implicit16_64", 0)])
+def test_theta_cluster_level_128_matches_oracle(dk, name, tag):
+    """The 128^2 level (coupled with 64^2) runs on the cluster kernel: 8 CTAs
+    per sample, each a band of 8 block rows, neighbour rows through
+    distributed shared memory and cluster barriers.  Full horizon (384 fine
+    steps), sample by sample against the oracle's exact Fourier solves."""
+    wl = W.get(name).with_(L_max=3)
+    level, count, seed, first = 3, 4, 41, 2
+    with dk.Context.from_workload(wl) as ctx:
+        info = ctx.level_info(level)
+        assert info.n == 128 and info.theta == 1 and info.cluster == 8 and info.cheb_steps > 0
+        sums, samp = _gpu(ctx, dk, level, tag, first, count, seed)
+    levels = oracle.level_table(wl.length, wl.n0, wl.L_max, wl.T, wl.mu, wl.M0)
+    coupled = tag == 0
+    ol = oracle.level_inputs(wl.length, levels, wl.N, wl.rho0_all(), wl.phi_all(), level, coupled, b0=wl.b0)
+    r = oracle.run_samples(ol, seed, range(first, first + count), coupled, stream=tag, processes=4)
+    K = 1
+    ybf = np.array(info.ybar_f[:K])
+    w = _parity(samp[:, :K] + ybf[None, :], r["Y_f"], ybf, f"{name} level 3 fine")
+    if coupled:
+        ybc = np.array(info.ybar_c[:K])
+        w = max(w, _parity(samp[:, K:2 * K] + ybc[None, :], r["Y_c"], ybc, f"{name} level 3 coarse"))
+    assert int(sums[0]) == count and sums[1] == 0.0
+    print(f"{name} 128^2 tag {tag}: worst/bound {w:.3g}, Chebyshev steps {info.cheb_steps}")
+
+
+def test_theta_cluster_level_many_samples_and_batch(dk):
+    """More samples than resident clusters (several passes of the persistent
+    cluster grid, a ragged last pass): device sums equal the per-sample
+    outputs' sums, and the multi-level batch gives the same sums as per-level
+    launches with the 128^2 level in it."""
+    import torch
+    wl = W.get("theta16_64").with_(L_max=3, T=0.0025)
+    st = torch.cuda.current_stream().cuda_stream
+    with dk.Context.from_workload(wl) as ctx:
+        info = ctx.level_info(3)
+        count = 2 * (info.in_flight or 19) + 3
+        sums, samp = _gpu(ctx, dk, 3, 0, 0, count, 12)
+        assert int(sums[0]) == count
+        dp = wl.N * (samp[:, 0] ** 2 - samp[:, 1] ** 2)
+        np.testing.assert_allclose(sums[2], dp.sum(), rtol=1e-9)
+        S = dk.sums_len(ctx.n_quant)
+        counts = [400, 100, 30, 25]
+        batch = torch.zeros(4, S, dtype=torch.float64, device="cuda")
+        ctx.run_batch_dev(counts, 3, 13, batch.data_ptr(), st)
+        torch.cuda.synchronize()
+        for l, m in enumerate(counts):
+            ref = torch.zeros(S, dtype=torch.float64, device="cuda")
+            ctx.run_level_dev(l, 0, 3, m, 13, ref.data_ptr(), 0, st)
+            torch.cuda.synchronize()
+            np.testing.assert_allclose(batch[l].cpu().numpy(), ref.cpu().numpy(), rtol=1e-12, atol=0)
+
+
 def test_b0_zero_theta_kernel_is_the_explicit_step(dk):
     """The theta kernel with b0 = 0 against the streamed kernels (64^2, the same
     integer arithmetic and FP64 projections) and the register kernels (16^2,
