@@ -549,7 +549,43 @@ struct BandNbr {
     template <class T> __device__ __forceinline__ T right(const T* p) const { return p[ir]; }
 };
 
-__device__ __forceinline__ void cluster_sync() { cg::this_cluster().sync(); }
+// Split cluster barrier of a plane exchange.  After writing its part of a
+// plane a thread arrives (release); a CTA barrier then publishes the plane
+// inside the CTA.  The warps of the band's first and last block row, which
+// read the neighbouring CTAs' rows, wait (acquire) at once; the other warps
+// only read rows of their own CTA and defer the wait until just before they
+// next write a plane that other CTAs read, so the cluster barrier's latency
+// is spent on their arithmetic.  A thread always waits once between two
+// arrivals, so the barrier is never more than one phase ahead of it.
+struct ClPhase {
+    bool edge;
+    bool pend = false;
+    __device__ __forceinline__ explicit ClPhase(bool edge_) : edge(edge_) {}
+    __device__ __forceinline__ static void arrive() {
+        asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+    }
+    __device__ __forceinline__ static void wait() {
+        asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+    }
+    // before writing a plane that other CTAs read (or before a full barrier)
+    __device__ __forceinline__ void settle() {
+        if (pend) {
+            wait();
+            pend = false;
+        }
+    }
+    __device__ __forceinline__ void publish() {
+        arrive();
+        __syncthreads();
+        if (edge) wait();
+        else pend = true;
+    }
+    __device__ __forceinline__ void full() {
+        settle();
+        arrive();
+        wait();
+    }
+};
 
 // Sum of the four neighbours of each cell of block v = (top-left, top-right,
 // bottom-left, bottom-right), from the blocks above / below / left / right,
@@ -568,18 +604,21 @@ __device__ __forceinline__ void nsum_band(const float (&v)[4], const float4* P, 
 }
 
 // theta_fine_step for one block of a band (B: four planes of one 16-byte
-// word per block of the band; all neighbours through shared memory).
+// word per block of the band; all neighbours through shared memory).  Every
+// plane write is preceded by ph.settle() and followed by ph.publish(); the
+// step ends with an arrival whose wait comes before the next plane write.
 template <int NC, int BR>
 __device__ __forceinline__ void theta_fine_step_cl(int32_t (&q)[4], const int32_t (&G1)[4], const int32_t (&G2)[4],
                                                    const BandNbr<NC, BR>& nb, float* const (&B)[4], long long A,
-                                                   const TArgs& t, unsigned& bad) {
+                                                   const TArgs& t, unsigned& bad, ClPhase& ph) {
     const int lq = nb.lq;
     // ---- exact face fluxes: the top row of the block below, the left column of the block right
     int4* Qd = reinterpret_cast<int4*>(B[0]);
     int4* Qr = reinterpret_cast<int4*>(B[3]);
+    ph.settle();
     Qd[lq] = make_int4(q[0], q[1], G1[0], G1[1]);
     Qr[lq] = make_int4(q[0], q[2], G2[0], G2[2]);
-    cluster_sync();
+    ph.publish();
     const int4 bq = nb.below(Qd), rq = nb.right(Qr);
     const int32_t qdn[4] = {q[2], q[3], bq.x, bq.y}, gdn[4] = {G1[2], G1[3], bq.z, bq.w};
     const int32_t qrt[4] = {q[1], rq.x, q[3], rq.y}, grt[4] = {G2[1], rq.z, G2[3], rq.w};
@@ -603,9 +642,10 @@ __device__ __forceinline__ void theta_fine_step_cl(int32_t (&q)[4], const int32_
         }
         float4* PF1 = reinterpret_cast<float4*>(B[1]);
         float4* PF2 = reinterpret_cast<float4*>(B[2]);
+        ph.settle();
         PF1[lq] = make_float4(f1[0], f1[1], f1[2], f1[3]);
         PF2[lq] = make_float4(f2[0], f2[1], f2[2], f2[3]);
-        cluster_sync();   // also orders every read of B[0], B[3] before they are reused below
+        ph.publish();   // its wait also orders every read of B[0], B[3] before they are reused below
         float s1[4], s2[4], r1[4], r2[4], d1[4], d2[4];
         nsum_band(f1, PF1, nb, s1);
         nsum_band(f2, PF2, nb, s2);
@@ -620,9 +660,10 @@ __device__ __forceinline__ void theta_fine_step_cl(int32_t (&q)[4], const int32_
         float4* cur2 = reinterpret_cast<float4*>(B[0]);
         float4* nxt1 = reinterpret_cast<float4*>(B[1]);
         float4* nxt2 = reinterpret_cast<float4*>(B[2]);
+        ph.settle();
         cur1[lq] = make_float4(d1[0], d1[1], d1[2], d1[3]);
         cur2[lq] = make_float4(d2[0], d2[1], d2[2], d2[3]);
-        cluster_sync();
+        ph.publish();
         const float diag = 1.f + 4.f * t.alpha;
         for (int k = 0; k < t.K; ++k) {
             nsum_band(d1, cur1, nb, s1);
@@ -641,9 +682,10 @@ __device__ __forceinline__ void theta_fine_step_cl(int32_t (&q)[4], const int32_
                     d1[c] = ca * d1[c] + cb * r1[c];
                     d2[c] = ca * d2[c] + cb * r2[c];
                 }
+                ph.settle();
                 nxt1[lq] = make_float4(d1[0], d1[1], d1[2], d1[3]);
                 nxt2[lq] = make_float4(d2[0], d2[1], d2[2], d2[3]);
-                cluster_sync();
+                ph.publish();
                 float4* x = cur1; cur1 = nxt1; nxt1 = x;
                 x = cur2; cur2 = nxt2; nxt2 = x;
             }
@@ -660,8 +702,9 @@ __device__ __forceinline__ void theta_fine_step_cl(int32_t (&q)[4], const int32_
         H2[c] = static_cast<int32_t>(h2);
     }
     int4* Hb = reinterpret_cast<int4*>(hplane);
+    ph.settle();
     Hb[lq] = make_int4(H1[2], H1[3], H2[1], H2[3]);
-    cluster_sync();
+    ph.publish();
     const int4 ha = nb.above(Hb), hl = nb.left(Hb);
     const int32_t h1up[4] = {ha.x, ha.y, H1[0], H1[1]}, h2lf[4] = {hl.z, H2[0], hl.w, H2[2]};
 #pragma unroll
@@ -670,17 +713,20 @@ __device__ __forceinline__ void theta_fine_step_cl(int32_t (&q)[4], const int32_
         bad |= (unsigned)((v >= (1LL << 30)) | (v <= -(1LL << 30)));
         q[c] = static_cast<int32_t>(v);
     }
-    cluster_sync();
+    // every thread has read what it needs: arrive, wait before the next plane write
+    ph.settle();
+    ClPhase::arrive();
+    ph.pend = true;
 }
 
 // theta_step<NC, 1> for one coarse cell of a band: sq the band's coarse
-// state, P0 / P2 the coarse transfers G_1 / G_2 (as integers) on entry, P0..P3
-// band planes of one float per cell.  The one-CTA step's arithmetic and order
-// of additions.
+// state, P0 / P2 the coarse transfers G_1 / G_2 (as integers, published by
+// the caller), P0..P3 band planes of one float per cell.  The one-CTA step's
+// arithmetic and order of additions; plane exchanges as in the fine step.
 template <int NC, int BR>
 __device__ __forceinline__ void theta_coarse_step_cl(int32_t& q, const BandNbr<NC, BR>& nb, int32_t* sq, float* P0,
                                                      float* P1, float* P2, float* P3, long long A, const TArgs& t,
-                                                     unsigned& bad) {
+                                                     unsigned& bad, ClPhase& ph) {
     const int idx = nb.lq;
     const int32_t g1 = as_i(P0[idx]), g2 = as_i(P2[idx]);
     const long long F1 = (long long)edge_flux64(A, nb.below(sq) - q) + g1 + as_i(nb.below(P0));
@@ -689,17 +735,19 @@ __device__ __forceinline__ void theta_coarse_step_cl(int32_t& q, const BandNbr<N
     float* out1 = P1;
     float* out2 = P3;
     if (t.K > 0) {
+        ph.settle();
         P1[idx] = static_cast<float>(F1);
         P3[idx] = static_cast<float>(F2);
-        cluster_sync();
+        ph.publish();   // its wait also orders every read of the G planes before they are overwritten
         const float f1 = P1[idx], f2 = P3[idx];
         const float l1 = 4.f * f1 - nb.above(P1) - nb.below(P1) - nb.left(P1) - nb.right(P1);
         const float l2 = 4.f * f2 - nb.above(P3) - nb.below(P3) - nb.left(P3) - nb.right(P3);
         float r1 = -t.alpha * l1, r2 = -t.alpha * l2;
         float d1 = r1 * t.inv_theta, d2 = r2 * t.inv_theta;
+        ph.settle();
         P0[idx] = d1;
         P2[idx] = d2;
-        cluster_sync();
+        ph.publish();
         float *c1p = P0, *c2p = P2, *n1p = P1, *n2p = P3;
         const float diag = 1.f + 4.f * t.alpha;
         for (int k = 0; k < t.K; ++k) {
@@ -712,9 +760,10 @@ __device__ __forceinline__ void theta_coarse_step_cl(int32_t& q, const BandNbr<N
             if (k + 1 < t.K) {
                 d1 = t.c1[k] * d1 + t.c2[k] * r1;
                 d2 = t.c1[k] * d2 + t.c2[k] * r2;
+                ph.settle();
                 n1p[idx] = d1;
                 n2p[idx] = d2;
-                cluster_sync();
+                ph.publish();
                 float* x = c1p; c1p = n1p; n1p = x;
                 x = c2p; c2p = n2p; n2p = x;
             }
@@ -724,14 +773,17 @@ __device__ __forceinline__ void theta_coarse_step_cl(int32_t& q, const BandNbr<N
     }
     const long long H1 = F1 + __float2ll_rn(u1), H2 = F2 + __float2ll_rn(u2);
     bad |= (unsigned)((H1 != (long long)(int32_t)H1) | (H2 != (long long)(int32_t)H2));
+    ph.settle();
     out1[idx] = as_f(static_cast<int32_t>(H1));
     out2[idx] = as_f(static_cast<int32_t>(H2));
-    cluster_sync();
+    ph.publish();
     const long long v = (long long)q + (H1 - as_i(nb.above(out1))) + (H2 - as_i(nb.left(out2)));
     bad |= (unsigned)((v >= (1LL << 30)) | (v <= -(1LL << 30)));
     q = static_cast<int32_t>(v);
+    ph.settle();
     sq[idx] = q;
-    cluster_sync();
+    ClPhase::arrive();
+    ph.pend = true;
 }
 
 // The theta-scheme sample kernel for a cluster of CL CTAs per sample (see
@@ -757,6 +809,7 @@ __global__ void __launch_bounds__(CShape<N, CL>::THREADS, 1) theta_cluster_kerne
     const int lr = tid / NC, I2 = tid % NC;           // block row within the band, column
     const int I1 = rank * BR + lr;                    // coarse cell; fine block rows 2 I1 + v1, cols 2 I2 + v2
     const BandNbr<NC, BR> nb(lr, I2, rank, CL);
+    ClPhase ph(lr == 0 || lr == BR - 1);              // the band's first and last rows read other CTAs
     const int gc = I1 * NC + I2;                      // global coarse index
     const int f00 = (2 * I1) * N + 2 * I2;
     const int fidx[4] = {f00, f00 + 1, f00 + N, f00 + N + 1};
@@ -767,7 +820,7 @@ __global__ void __launch_bounds__(CShape<N, CL>::THREADS, 1) theta_cluster_kerne
     const long long slot = (long long)blockIdx.x / CL;
     const long long iters = a.count > slot ? (a.count - slot + n_slots - 1) / n_slots : 0;
     unsigned bad = 0;
-    cluster_sync();
+    ph.full();
 
     for (long long it = 0; it < iters; ++it) {
         const long long idx = slot + it * n_slots;
@@ -784,7 +837,7 @@ __global__ void __launch_bounds__(CShape<N, CL>::THREADS, 1) theta_cluster_kerne
             qc = a.q0c[gc];
             sqc[nb.lq] = qc;
         }
-        cluster_sync();
+        ph.full();
 
         for (int m = 0; m < a.M; ++m) {
             int32_t G1[4], G2[4];
@@ -805,16 +858,17 @@ __global__ void __launch_bounds__(CShape<N, CL>::THREADS, 1) theta_cluster_kerne
                     zt1 = fmaf(rb, sb, fmaf(ra, sa, zt1));
                 }
             }
-            theta_fine_step_cl<NC, BR>(q, G1, G2, nb, planes, t.Af64, t, bad);
+            theta_fine_step_cl<NC, BR>(q, G1, G2, nb, planes, t.Af64, t, bad, ph);
 
             if constexpr (CPL) {
                 if ((m & 3) == 3) {
                     const float sc = noise_amp(qc, a.gc);
+                    ph.settle();
                     P0[nb.lq] = as_f(__float2int_rn(sc * zt0));
                     P2[nb.lq] = as_f(__float2int_rn(sc * zt1));
                     zt0 = zt1 = 0.f;
-                    cluster_sync();
-                    theta_coarse_step_cl<NC, BR>(qc, nb, sqc, P0, P1, P2, P3, t.Ac64, t, bad);
+                    ph.publish();
+                    theta_coarse_step_cl<NC, BR>(qc, nb, sqc, P0, P1, P2, P3, t.Ac64, t, bad, ph);
                 }
             }
         }
@@ -853,7 +907,7 @@ __global__ void __launch_bounds__(CShape<N, CL>::THREADS, 1) theta_cluster_kerne
             for (int w = 0; w < THREADS / 32; ++w) x += red[w * kRed + tid];
             tot[tid] = x;
         }
-        cluster_sync();
+        ph.full();
         if (rank == 0 && tid == 0 && active) {
             for (int i = 0; i < kRed; ++i) {
                 double x = 0.0;
@@ -893,7 +947,7 @@ __global__ void __launch_bounds__(CShape<N, CL>::THREADS, 1) theta_cluster_kerne
                 o[2 * a.n_obs + 1] = CPL ? v[2 * kMaxObs + 1] * a.dscale_c : 0.0;
             }
         }
-        cluster_sync();   // the band totals and the state planes are reused by the next sample
+        ph.full();   // the band totals and the state planes are reused by the next sample
     }
     if (bad) atomicOr(a.err, kErrRange);
 
