@@ -76,7 +76,7 @@ FOURIER_SOURCES = ("dk_fourier.cu", "dk_device.cuh")
 # (smsp__inst_executed x 32 / fine cell-steps); keyed by kernel function.
 KERNEL_PROFILE = {
     "stream_fine_kernel": {
-        "sources": ("dk_stream.cu", "dk_device.cuh"), "sources_sha256_16": "843f4a742dcf92b2",
+        "sources": ("dk_stream.cu", "dk_device.cuh"), "sources_sha256_16": "4a364a9befb1c264",
         "per_n": {1024: {"dram_bytes_per_fine_cell_step": 0.94, "instructions_per_fine_cell_step": 86.0},
                   512: {"dram_bytes_per_fine_cell_step": 0.014, "instructions_per_fine_cell_step": 86.0}},
         "capture": "ncu --cache-control none, 3 consecutive launches of the 1024^2 (5 samples) and 512^2 "

@@ -59,22 +59,35 @@ __device__ __forceinline__ uint4 pair_words(const SArgs& a, uint32_t p, int m, u
     return philox10(make_uint4(p, static_cast<uint32_t>(m), c2, c3), a.key0, a.key1);
 }
 
-// The same from the pair's Philox words x (drawn earlier by pair_words).
-__device__ __forceinline__ PairNoise pair_noise_w(const SArgs& a, uint4 x, int32_t qa, int32_t qb, float& z1,
-                                                  float& z2) {
+// Box--Muller radii and directions of the pair's two cells.
+struct PairNormals {
     float ra, ca, sa, rb, cb, sb;
-    box_muller_polar(x.x, x.y, ra, ca, sa);
-    box_muller_polar(x.z, x.w, rb, cb, sb);
-    const float ta = noise_amp(qa, a.gf) * ra, tb = noise_amp(qb, a.gf) * rb;
-    z1 = fmaf(rb, cb, fmaf(ra, ca, z1));
-    z2 = fmaf(rb, sb, fmaf(ra, sa, z2));
-    return {__float2int_rn(ta * ca), __float2int_rn(ta * sa), __float2int_rn(tb * cb), __float2int_rn(tb * sb)};
+};
+
+__device__ __forceinline__ PairNormals pair_normals(uint4 x) {
+    PairNormals z;
+    box_muller_polar(x.x, x.y, z.ra, z.ca, z.sa);
+    box_muller_polar(x.z, x.w, z.rb, z.cb, z.sb);
+    return z;
 }
 
-__device__ __forceinline__ PairNoise pair_noise(const SArgs& a, uint32_t p, int m, uint32_t c2, uint32_t c3,
-                                                int32_t qa, int32_t qb, float& z1, float& z2) {
-    return pair_noise_w(a, pair_words(a, p, m, c2, c3), qa, qb, z1, z2);
+// Makes the normals exist at this point of the program (an empty asm
+// statement that reads and writes them): the compiler keeps their arithmetic
+// before a later volatile asm statement such as the grid dependency wait.
+__device__ __forceinline__ void pin(PairNormals& z) {
+    asm volatile("" : "+f"(z.ra), "+f"(z.ca), "+f"(z.sa), "+f"(z.rb), "+f"(z.cb), "+f"(z.sb));
 }
+
+// The transfers from the pair's normals (drawn earlier).
+__device__ __forceinline__ PairNoise pair_noise_n(const SArgs& a, const PairNormals& z, int32_t qa, int32_t qb,
+                                                  float& z1, float& z2) {
+    const float ta = noise_amp(qa, a.gf) * z.ra, tb = noise_amp(qb, a.gf) * z.rb;
+    z1 = fmaf(z.rb, z.cb, fmaf(z.ra, z.ca, z1));
+    z2 = fmaf(z.rb, z.sb, fmaf(z.ra, z.sa, z2));
+    return {__float2int_rn(ta * z.ca), __float2int_rn(ta * z.sa), __float2int_rn(tb * z.cb),
+            __float2int_rn(tb * z.sb)};
+}
+
 
 // Programmatic dependent launch: let the next kernel in the stream start its
 // CTAs once every CTA of this one has started, and wait until the previous
@@ -152,16 +165,22 @@ __device__ __forceinline__ bool fine_tile(const SArgs& a, int s, int R0, int C0,
             hc = wrapi(u / FR ? C0 + kFC : C0 - 2, n);
         }
     };
-    uint4 w[2][2], hw = make_uint4(0, 0, 0, 0);
+    PairNormals w[2][2], hw{};
     if constexpr (PDL) {
         if (t < kHaloPairs) halo_cell();
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
             const uint32_t p = static_cast<uint32_t>(((r0 + i) * n + c0) >> 1);
-            w[i][0] = pair_words(a, p, m, c2, c3);
-            w[i][1] = pair_words(a, p + 1, m, c2, c3);
+            w[i][0] = pair_normals(pair_words(a, p, m, c2, c3));
+            w[i][1] = pair_normals(pair_words(a, p + 1, m, c2, c3));
         }
-        if (t < kHaloPairs) hw = pair_words(a, static_cast<uint32_t>((hr * n + hc) >> 1), m, c2, c3);
+        if (t < kHaloPairs) hw = pair_normals(pair_words(a, static_cast<uint32_t>((hr * n + hc) >> 1), m, c2, c3));
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            pin(w[i][0]);
+            pin(w[i][1]);
+        }
+        pin(hw);
         wait_previous_grid();
     }
 
@@ -185,11 +204,11 @@ __device__ __forceinline__ bool fine_tile(const SArgs& a, int s, int R0, int C0,
         q[i][0] = v.x; q[i][1] = v.y; q[i][2] = v.z; q[i][3] = v.w;
         const uint32_t p = static_cast<uint32_t>(((r0 + i) * n + c0) >> 1);
         if constexpr (!PDL) {
-            w[i][0] = pair_words(a, p, m, c2, c3);
-            w[i][1] = pair_words(a, p + 1, m, c2, c3);
+            w[i][0] = pair_normals(pair_words(a, p, m, c2, c3));
+            w[i][1] = pair_normals(pair_words(a, p + 1, m, c2, c3));
         }
-        const PairNoise g = pair_noise_w(a, w[i][0], v.x, v.y, z[0][0], z[0][1]);
-        const PairNoise h = pair_noise_w(a, w[i][1], v.z, v.w, z[1][0], z[1][1]);
+        const PairNoise g = pair_noise_n(a, w[i][0], v.x, v.y, z[0][0], z[0][1]);
+        const PairNoise h = pair_noise_n(a, w[i][1], v.z, v.w, z[1][0], z[1][1]);
         G1[i][0] = g.g1a; G2[i][0] = g.g2a; G1[i][1] = g.g1b; G2[i][1] = g.g2b;
         G1[i][2] = h.g1a; G2[i][2] = h.g2a; G1[i][3] = h.g1b; G2[i][3] = h.g2b;
         if constexpr (!PERSIST) {
@@ -211,8 +230,8 @@ __device__ __forceinline__ bool fine_tile(const SArgs& a, int s, int R0, int C0,
             const int side = t >> 5, k = t & 31;
             const int r = PDL ? hr : wrapi(side ? R0 + FR : R0 - 1, n), c = PDL ? hc : C0 + 2 * k;
             const int2 v = ldg<PERSIST>(reinterpret_cast<const int2*>(qin + (size_t)r * n + c));
-            const uint4 x = PDL ? hw : pair_words(a, static_cast<uint32_t>((r * n + c) >> 1), m, c2, c3);
-            const PairNoise g = pair_noise_w(a, x, v.x, v.y, d1, d2);
+            const PairNormals x = PDL ? hw : pair_normals(pair_words(a, static_cast<uint32_t>((r * n + c) >> 1), m, c2, c3));
+            const PairNoise g = pair_noise_n(a, x, v.x, v.y, d1, d2);
             const int lr = side ? FR + 1 : 0;
             if constexpr (PERSIST) {
                 hq = &sq[lr][4 + 2 * k];
@@ -228,8 +247,8 @@ __device__ __forceinline__ bool fine_tile(const SArgs& a, int s, int R0, int C0,
             const int u = t - 64, side = u / FR, rr = u % FR;
             const int r = PDL ? hr : R0 + rr, c = PDL ? hc : wrapi(side ? C0 + kFC : C0 - 2, n);
             const int2 v = ldg<PERSIST>(reinterpret_cast<const int2*>(qin + (size_t)r * n + c));
-            const uint4 x = PDL ? hw : pair_words(a, static_cast<uint32_t>((r * n + c) >> 1), m, c2, c3);
-            const PairNoise g = pair_noise_w(a, x, v.x, v.y, d1, d2);
+            const PairNormals x = PDL ? hw : pair_normals(pair_words(a, static_cast<uint32_t>((r * n + c) >> 1), m, c2, c3));
+            const PairNoise g = pair_noise_n(a, x, v.x, v.y, d1, d2);
             if constexpr (PERSIST) {
                 hq = side ? &sq[rr + 1][kFC + 4] : &sq[rr + 1][3];
                 hg = side ? &s2[rr + 1][kFC + 4] : &s2[rr + 1][3];
@@ -348,10 +367,13 @@ __global__ void __launch_bounds__(fine_threads(FR), MINB) stream_fine_kernel(con
     fine_tile<FR, false, PDL>(a, s, blockIdx.y * FR, blockIdx.x * kFC, m, smem_fine, 0);
 }
 
-// One launch per coarse step cn (after fine step 4 cn + 3); launched in
-// stream order, it lets the next fine step's CTAs start early.
+// One launch per coarse step cn (after fine step 4 cn + 3).  It lets the next
+// fine step's CTAs start early; launched as a dependent launch itself (with the
+// dependent fine steps), its CTAs are placed while the fine step's last wave
+// runs and wait there for it to finish.
 __global__ void __launch_bounds__(kThreads) stream_coarse_kernel(const SArgs a, int cn) {
     launch_dependents();
+    wait_previous_grid();
     const int s = blockIdx.y;
     if (s >= a.count) return;
     __shared__ __align__(16) int32_t smem_coarse[(kTile + 2) * (kTile + 2) * 3];
@@ -801,11 +823,16 @@ cudaError_t stream_run(const KArgs& k, SArgs a, int S, int variant, cudaStream_t
             cfg.stream = st;
             cfg.attrs = attr;
             cfg.numAttrs = 1;
+            cudaLaunchConfig_t ccfg = cfg;
+            ccfg.gridDim = cgrid;
+            ccfg.blockDim = dim3(kThreads);
+            ccfg.dynamicSmemBytes = 0;
             for (int m = 0; m < a.M; ++m) {
                 e = variant == 4 ? cudaLaunchKernelEx(&cfg, stream_fine_kernel<kFR, 4, true>, a, m)
                                  : cudaLaunchKernelEx(&cfg, stream_fine_kernel<kFR, 5, true>, a, m);
+                if (e == cudaSuccess && a.coupled && (m & 3) == 3)
+                    e = cudaLaunchKernelEx(&ccfg, stream_coarse_kernel, a, m >> 2);
                 if (e != cudaSuccess) return e;
-                if (a.coupled && (m & 3) == 3) stream_coarse_kernel<<<cgrid, kThreads, 0, st>>>(a, m >> 2);
             }
         } else {
             for (int m = 0; m < a.M; ++m) {
