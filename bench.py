@@ -77,8 +77,8 @@ FOURIER_SOURCES = ("dk_fourier.cu", "dk_device.cuh")
 KERNEL_PROFILE = {
     "stream_fine_kernel": {
         "sources": ("dk_stream.cu", "dk_device.cuh"), "sources_sha256_16": "4a364a9befb1c264",
-        "per_n": {1024: {"dram_bytes_per_fine_cell_step": 0.94, "instructions_per_fine_cell_step": 86.0},
-                  512: {"dram_bytes_per_fine_cell_step": 0.014, "instructions_per_fine_cell_step": 86.0}},
+        "per_n": {1024: {"dram_bytes_per_fine_cell_step": 0.92, "instructions_per_fine_cell_step": 82.8},
+                  512: {"dram_bytes_per_fine_cell_step": 0.016, "instructions_per_fine_cell_step": 82.8}},
         "capture": "ncu --cache-control none, 3 consecutive launches of the 1024^2 (5 samples) and 512^2 "
                    "(8 samples) fine step (profiles/stream_fine_kernel_1024_pdl_full.md, _512_pdl_full.md)",
     },
@@ -101,7 +101,7 @@ STREAM_BYTES_PER_FINE_CELL_STEP = 8.5
 
 
 def measured_peaks():
-    """(HBM GB/s, source) from the measured peaks, else the fallback."""
+    """(HBM GB/s, source) from the measured peaks file, else the fallback."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
             return float(json.load(fh)["hbm_gbs"]), "measured"

@@ -1050,8 +1050,12 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
             for (const auto& vi : t.vis[mode])
                 if (vi.supported) need = std::max(need, (size_t)(vi.max_ctas / vi.cluster) * vi.slots_per_cta * c->stride);
         c->lpart_cap[l] = need;
-        // the finest level gets the most urgent priority, coarser levels fill in
-        c->lprio[l] = std::max(prio_hi, prio_lo - (l * (prio_lo - prio_hi)) / std::max(1, nl - 1));
+        // the finest level gets the most urgent priority, coarser levels fill in;
+        // the streamed levels (which run side by side after the graph) share the
+        // finest one's, so that the block scheduler interleaves their launches
+        int rank_l = l;
+        if (t.streamed) rank_l = nl - 1;
+        c->lprio[l] = std::max(prio_hi, prio_lo - (rank_l * (prio_lo - prio_hi)) / std::max(1, nl - 1));
         if ((e = cudaMalloc(&c->d_lpart[l], sizeof(double) * std::max<size_t>(need, 1))) != cudaSuccess ||
             (e = cudaStreamCreateWithPriority(&c->lstream[l], cudaStreamNonBlocking, c->lprio[l])) != cudaSuccess ||
             (e = cudaEventCreateWithFlags(&c->ev_join[l], cudaEventDisableTiming)) != cudaSuccess ||
