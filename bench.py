@@ -895,6 +895,9 @@ def mlmc16_batch(args, stream):
     alloc = list(wl.alloc)
     with mlmc_dk.Context.from_workload(wl, stream=stream.cuda_stream) as c:
         c.tune(1)
+        # batch split: a share of the 256^2 level's samples on the streamed kernels
+        # beside its 8-CTA clusters (the SMs those cannot use)
+        split_frac, split_s = c.tune_batch(alloc, 1)
         info = [c.level_info(l) for l in range(wl.L_max + 1)]
         steps = sum(m * i.M for m, i in zip(alloc, info))
         sums = torch.zeros(wl.L_max + 1, mlmc_dk.sums_len(c.n_quant), dtype=torch.float64, device="cuda")
@@ -922,6 +925,7 @@ def mlmc16_batch(args, stream):
             adaptive["oracle_error"] = oracle_error(c, wl, outs, wl.seed + 5, stream)
     fin = info[-1]
     return {"alloc": alloc, "ms_per_step": ms, "coupled_sample_steps_per_s": steps / (ms * 1e-3),
+            "batch_split": {"fraction": split_frac, "tune_s": split_s},
             "cell_steps_per_s": sum(m * i.cost for m, i in zip(alloc, info)) / (ms * 1e-3),
             "level_ms": level_ms, "kernels": [{"n": i.n, "band": bool(i.band), "cluster": i.cluster} for i in info],
             "algorithm1_measured": adaptive,
