@@ -508,12 +508,13 @@ __global__ void __launch_bounds__(TShape<N>::THREADS) theta_kernel(const KArgs a
 // ---------------------------------------------------------------------------
 namespace cg = cooperative_groups;
 
-template <int N, int CL>
+template <int N, int CL, int NB>
 struct CShape {
     static constexpr int NC = N / 2, BR = NC / CL;          // block rows per CTA
-    static constexpr int THREADS = BR * NC;                 // one thread per block of the band
+    static constexpr int RT = NC / NB;                      // threads per block row (NB blocks each)
+    static constexpr int THREADS = BR * RT;
     static constexpr int BAND = BR * NC;                    // blocks (= coarse cells) per CTA
-    static_assert(NC % CL == 0 && THREADS <= 1024 && THREADS % 32 == 0 && NC % 32 == 0, "band shape");
+    static_assert(NC % CL == 0 && NC % NB == 0 && THREADS <= 1024 && RT % 32 == 0, "band shape");
     // four block planes of BAND x 16 bytes (top and bottom rows, or an int4 per block),
     // the coarse state of the band, reduction scratch
     static size_t smem(int slot_stride) {
@@ -536,6 +537,7 @@ __device__ __forceinline__ T* band_at(T* local, int r, int rank) {
 template <int NC, int BR>
 struct BandNbr {
     int lq, il, ir, ia, ib, ra, rb, rank;
+    BandNbr() = default;
     __device__ __forceinline__ BandNbr(int lr, int I2, int rank_, int cl) : rank(rank_) {
         lq = lr * NC + I2;
         il = lr * NC + (I2 + NC - 1) % NC;
@@ -603,88 +605,120 @@ __device__ __forceinline__ void nsum_band(const float (&v)[4], const float4* P, 
     nsum4(v, nb.above(P), nb.below(P), nb.left(P), nb.right(P), s);
 }
 
-// theta_fine_step for one block of a band (B: four planes of one 16-byte
-// word per block of the band; all neighbours through shared memory).  Every
-// plane write is preceded by ph.settle() and followed by ph.publish(); the
-// step ends with an arrival whose wait comes before the next plane write.
-template <int NC, int BR>
-__device__ __forceinline__ void theta_fine_step_cl(int32_t (&q)[4], const int32_t (&G1)[4], const int32_t (&G2)[4],
-                                                   const BandNbr<NC, BR>& nb, float* const (&B)[4], long long A,
-                                                   const TArgs& t, unsigned& bad, ClPhase& ph) {
-    const int lq = nb.lq;
+// theta_fine_step for the NB blocks of a thread in a band (B: four planes of
+// one 16-byte word per block of the band; all neighbours through shared
+// memory).  Every plane write is preceded by ph.settle() and followed by
+// ph.publish(); the step ends with an arrival whose wait comes before the
+// next plane write.
+template <int NC, int BR, int NB>
+__device__ __forceinline__ void theta_fine_step_cl(int32_t (&q)[NB][4], const int32_t (&G1)[NB][4],
+                                                   const int32_t (&G2)[NB][4], const BandNbr<NC, BR> (&nb)[NB],
+                                                   float* const (&B)[4], long long A, const TArgs& t, unsigned& bad,
+                                                   ClPhase& ph) {
     // ---- exact face fluxes: the top row of the block below, the left column of the block right
     int4* Qd = reinterpret_cast<int4*>(B[0]);
     int4* Qr = reinterpret_cast<int4*>(B[3]);
     ph.settle();
-    Qd[lq] = make_int4(q[0], q[1], G1[0], G1[1]);
-    Qr[lq] = make_int4(q[0], q[2], G2[0], G2[2]);
-    ph.publish();
-    const int4 bq = nb.below(Qd), rq = nb.right(Qr);
-    const int32_t qdn[4] = {q[2], q[3], bq.x, bq.y}, gdn[4] = {G1[2], G1[3], bq.z, bq.w};
-    const int32_t qrt[4] = {q[1], rq.x, q[3], rq.y}, grt[4] = {G2[1], rq.z, G2[3], rq.w};
-    int32_t F1[4], F2[4];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        const long long f1 = (long long)edge_flux64(A, qdn[c] - q[c]) + G1[c] + gdn[c];
-        const long long f2 = (long long)edge_flux64(A, qrt[c] - q[c]) + G2[c] + grt[c];
-        bad |= (unsigned)((f1 != (long long)(int32_t)f1) | (f2 != (long long)(int32_t)f2));
-        F1[c] = static_cast<int32_t>(f1);
-        F2[c] = static_cast<int32_t>(f2);
+    for (int b = 0; b < NB; ++b) {
+        Qd[nb[b].lq] = make_int4(q[b][0], q[b][1], G1[b][0], G1[b][1]);
+        Qr[nb[b].lq] = make_int4(q[b][0], q[b][2], G2[b][0], G2[b][2]);
     }
-    float u1[4] = {0.f, 0.f, 0.f, 0.f}, u2[4] = {0.f, 0.f, 0.f, 0.f};
-    float* hplane = B[1];
-    if (t.K > 0) {
-        float f1[4], f2[4];
+    ph.publish();
+    int32_t F1[NB][4], F2[NB][4];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        const int4 bq = nb[b].below(Qd), rq = nb[b].right(Qr);
+        const int32_t qdn[4] = {q[b][2], q[b][3], bq.x, bq.y}, gdn[4] = {G1[b][2], G1[b][3], bq.z, bq.w};
+        const int32_t qrt[4] = {q[b][1], rq.x, q[b][3], rq.y}, grt[4] = {G2[b][1], rq.z, G2[b][3], rq.w};
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            f1[c] = static_cast<float>(F1[c]);
-            f2[c] = static_cast<float>(F2[c]);
+            const long long f1 = (long long)edge_flux64(A, qdn[c] - q[b][c]) + G1[b][c] + gdn[c];
+            const long long f2 = (long long)edge_flux64(A, qrt[c] - q[b][c]) + G2[b][c] + grt[c];
+            bad |= (unsigned)((f1 != (long long)(int32_t)f1) | (f2 != (long long)(int32_t)f2));
+            F1[b][c] = static_cast<int32_t>(f1);
+            F2[b][c] = static_cast<int32_t>(f2);
         }
+    }
+    float u1[NB][4], u2[NB][4];
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) u1[b][c] = u2[b][c] = 0.f;
+    float* hplane = B[1];
+    if (t.K > 0) {
+        float f1[NB][4], f2[NB][4];
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                f1[b][c] = static_cast<float>(F1[b][c]);
+                f2[b][c] = static_cast<float>(F2[b][c]);
+            }
         float4* PF1 = reinterpret_cast<float4*>(B[1]);
         float4* PF2 = reinterpret_cast<float4*>(B[2]);
         ph.settle();
-        PF1[lq] = make_float4(f1[0], f1[1], f1[2], f1[3]);
-        PF2[lq] = make_float4(f2[0], f2[1], f2[2], f2[3]);
-        ph.publish();   // its wait also orders every read of B[0], B[3] before they are reused below
-        float s1[4], s2[4], r1[4], r2[4], d1[4], d2[4];
-        nsum_band(f1, PF1, nb, s1);
-        nsum_band(f2, PF2, nb, s2);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            r1[c] = -t.alpha * (4.f * f1[c] - s1[c]);
-            r2[c] = -t.alpha * (4.f * f2[c] - s2[c]);
-            d1[c] = r1[c] * t.inv_theta;
-            d2[c] = r2[c] * t.inv_theta;
+        for (int b = 0; b < NB; ++b) {
+            PF1[nb[b].lq] = make_float4(f1[b][0], f1[b][1], f1[b][2], f1[b][3]);
+            PF2[nb[b].lq] = make_float4(f2[b][0], f2[b][1], f2[b][2], f2[b][3]);
+        }
+        ph.publish();   // its wait also orders every read of B[0], B[3] before they are reused below
+        float r1[NB][4], r2[NB][4], d1[NB][4], d2[NB][4];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            float s1[4], s2[4];
+            nsum_band(f1[b], PF1, nb[b], s1);
+            nsum_band(f2[b], PF2, nb[b], s2);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                r1[b][c] = -t.alpha * (4.f * f1[b][c] - s1[c]);
+                r2[b][c] = -t.alpha * (4.f * f2[b][c] - s2[c]);
+                d1[b][c] = r1[b][c] * t.inv_theta;
+                d2[b][c] = r2[b][c] * t.inv_theta;
+            }
         }
         float4* cur1 = reinterpret_cast<float4*>(B[3]);
         float4* cur2 = reinterpret_cast<float4*>(B[0]);
         float4* nxt1 = reinterpret_cast<float4*>(B[1]);
         float4* nxt2 = reinterpret_cast<float4*>(B[2]);
         ph.settle();
-        cur1[lq] = make_float4(d1[0], d1[1], d1[2], d1[3]);
-        cur2[lq] = make_float4(d2[0], d2[1], d2[2], d2[3]);
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            cur1[nb[b].lq] = make_float4(d1[b][0], d1[b][1], d1[b][2], d1[b][3]);
+            cur2[nb[b].lq] = make_float4(d2[b][0], d2[b][1], d2[b][2], d2[b][3]);
+        }
         ph.publish();
         const float diag = 1.f + 4.f * t.alpha;
         for (int k = 0; k < t.K; ++k) {
-            nsum_band(d1, cur1, nb, s1);
-            nsum_band(d2, cur2, nb, s2);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                u1[c] += d1[c];
-                u2[c] += d2[c];
-                r1[c] -= diag * d1[c] - t.alpha * s1[c];
-                r2[c] -= diag * d2[c] - t.alpha * s2[c];
+            for (int b = 0; b < NB; ++b) {
+                float s1[4], s2[4];
+                nsum_band(d1[b], cur1, nb[b], s1);
+                nsum_band(d2[b], cur2, nb[b], s2);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    u1[b][c] += d1[b][c];
+                    u2[b][c] += d2[b][c];
+                    r1[b][c] -= diag * d1[b][c] - t.alpha * s1[c];
+                    r2[b][c] -= diag * d2[b][c] - t.alpha * s2[c];
+                }
             }
             if (k + 1 < t.K) {
                 const float ca = t.c1[k], cb = t.c2[k];
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    d1[c] = ca * d1[c] + cb * r1[c];
-                    d2[c] = ca * d2[c] + cb * r2[c];
-                }
+                for (int b = 0; b < NB; ++b)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        d1[b][c] = ca * d1[b][c] + cb * r1[b][c];
+                        d2[b][c] = ca * d2[b][c] + cb * r2[b][c];
+                    }
                 ph.settle();
-                nxt1[lq] = make_float4(d1[0], d1[1], d1[2], d1[3]);
-                nxt2[lq] = make_float4(d2[0], d2[1], d2[2], d2[3]);
+#pragma unroll
+                for (int b = 0; b < NB; ++b) {
+                    nxt1[nb[b].lq] = make_float4(d1[b][0], d1[b][1], d1[b][2], d1[b][3]);
+                    nxt2[nb[b].lq] = make_float4(d2[b][0], d2[b][1], d2[b][2], d2[b][3]);
+                }
                 ph.publish();
                 float4* x = cur1; cur1 = nxt1; nxt1 = x;
                 x = cur2; cur2 = nxt2; nxt2 = x;
@@ -692,26 +726,32 @@ __device__ __forceinline__ void theta_fine_step_cl(int32_t (&q)[4], const int32_
         }
         hplane = reinterpret_cast<float*>(nxt1);   // not read by the last Chebyshev step
     }
-    int32_t H1[4], H2[4];
+    int32_t H1[NB][4], H2[NB][4];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        const long long h1 = (long long)F1[c] + __float2ll_rn(u1[c]);
-        const long long h2 = (long long)F2[c] + __float2ll_rn(u2[c]);
-        bad |= (unsigned)((h1 != (long long)(int32_t)h1) | (h2 != (long long)(int32_t)h2));
-        H1[c] = static_cast<int32_t>(h1);
-        H2[c] = static_cast<int32_t>(h2);
-    }
+    for (int b = 0; b < NB; ++b)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const long long h1 = (long long)F1[b][c] + __float2ll_rn(u1[b][c]);
+            const long long h2 = (long long)F2[b][c] + __float2ll_rn(u2[b][c]);
+            bad |= (unsigned)((h1 != (long long)(int32_t)h1) | (h2 != (long long)(int32_t)h2));
+            H1[b][c] = static_cast<int32_t>(h1);
+            H2[b][c] = static_cast<int32_t>(h2);
+        }
     int4* Hb = reinterpret_cast<int4*>(hplane);
     ph.settle();
-    Hb[lq] = make_int4(H1[2], H1[3], H2[1], H2[3]);
-    ph.publish();
-    const int4 ha = nb.above(Hb), hl = nb.left(Hb);
-    const int32_t h1up[4] = {ha.x, ha.y, H1[0], H1[1]}, h2lf[4] = {hl.z, H2[0], hl.w, H2[2]};
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        const long long v = (long long)q[c] + ((long long)H1[c] - h1up[c]) + ((long long)H2[c] - h2lf[c]);
-        bad |= (unsigned)((v >= (1LL << 30)) | (v <= -(1LL << 30)));
-        q[c] = static_cast<int32_t>(v);
+    for (int b = 0; b < NB; ++b) Hb[nb[b].lq] = make_int4(H1[b][2], H1[b][3], H2[b][1], H2[b][3]);
+    ph.publish();
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        const int4 ha = nb[b].above(Hb), hl = nb[b].left(Hb);
+        const int32_t h1up[4] = {ha.x, ha.y, H1[b][0], H1[b][1]}, h2lf[4] = {hl.z, H2[b][0], hl.w, H2[b][2]};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const long long v = (long long)q[b][c] + ((long long)H1[b][c] - h1up[c]) + ((long long)H2[b][c] - h2lf[c]);
+            bad |= (unsigned)((v >= (1LL << 30)) | (v <= -(1LL << 30)));
+            q[b][c] = static_cast<int32_t>(v);
+        }
     }
     // every thread has read what it needs: arrive, wait before the next plane write
     ph.settle();
@@ -719,50 +759,80 @@ __device__ __forceinline__ void theta_fine_step_cl(int32_t (&q)[4], const int32_
     ph.pend = true;
 }
 
-// theta_step<NC, 1> for one coarse cell of a band: sq the band's coarse
-// state, P0 / P2 the coarse transfers G_1 / G_2 (as integers, published by
-// the caller), P0..P3 band planes of one float per cell.  The one-CTA step's
-// arithmetic and order of additions; plane exchanges as in the fine step.
-template <int NC, int BR>
-__device__ __forceinline__ void theta_coarse_step_cl(int32_t& q, const BandNbr<NC, BR>& nb, int32_t* sq, float* P0,
-                                                     float* P1, float* P2, float* P3, long long A, const TArgs& t,
-                                                     unsigned& bad, ClPhase& ph) {
-    const int idx = nb.lq;
-    const int32_t g1 = as_i(P0[idx]), g2 = as_i(P2[idx]);
-    const long long F1 = (long long)edge_flux64(A, nb.below(sq) - q) + g1 + as_i(nb.below(P0));
-    const long long F2 = (long long)edge_flux64(A, nb.right(sq) - q) + g2 + as_i(nb.right(P2));
-    float u1 = 0.f, u2 = 0.f;
+// theta_step<NC, 1> for the NB coarse cells of a thread in a band: sq the
+// band's coarse state, P0 / P2 the coarse transfers G_1 / G_2 (as integers,
+// published by the caller), P0..P3 band planes of one float per cell.  The
+// one-CTA step's arithmetic and order of additions; plane exchanges as in the
+// fine step.
+template <int NC, int BR, int NB>
+__device__ __forceinline__ void theta_coarse_step_cl(int32_t (&q)[NB], const BandNbr<NC, BR> (&nb)[NB], int32_t* sq,
+                                                     float* P0, float* P1, float* P2, float* P3, long long A,
+                                                     const TArgs& t, unsigned& bad, ClPhase& ph) {
+    long long F1[NB], F2[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        const int idx = nb[b].lq;
+        const int32_t g1 = as_i(P0[idx]), g2 = as_i(P2[idx]);
+        F1[b] = (long long)edge_flux64(A, nb[b].below(sq) - q[b]) + g1 + as_i(nb[b].below(P0));
+        F2[b] = (long long)edge_flux64(A, nb[b].right(sq) - q[b]) + g2 + as_i(nb[b].right(P2));
+    }
+    float u1[NB], u2[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) u1[b] = u2[b] = 0.f;
     float* out1 = P1;
     float* out2 = P3;
     if (t.K > 0) {
         ph.settle();
-        P1[idx] = static_cast<float>(F1);
-        P3[idx] = static_cast<float>(F2);
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            P1[nb[b].lq] = static_cast<float>(F1[b]);
+            P3[nb[b].lq] = static_cast<float>(F2[b]);
+        }
         ph.publish();   // its wait also orders every read of the G planes before they are overwritten
-        const float f1 = P1[idx], f2 = P3[idx];
-        const float l1 = 4.f * f1 - nb.above(P1) - nb.below(P1) - nb.left(P1) - nb.right(P1);
-        const float l2 = 4.f * f2 - nb.above(P3) - nb.below(P3) - nb.left(P3) - nb.right(P3);
-        float r1 = -t.alpha * l1, r2 = -t.alpha * l2;
-        float d1 = r1 * t.inv_theta, d2 = r2 * t.inv_theta;
+        float r1[NB], r2[NB], d1[NB], d2[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const BandNbr<NC, BR>& n = nb[b];
+            const float f1 = P1[n.lq], f2 = P3[n.lq];
+            const float l1 = 4.f * f1 - n.above(P1) - n.below(P1) - n.left(P1) - n.right(P1);
+            const float l2 = 4.f * f2 - n.above(P3) - n.below(P3) - n.left(P3) - n.right(P3);
+            r1[b] = -t.alpha * l1;
+            r2[b] = -t.alpha * l2;
+            d1[b] = r1[b] * t.inv_theta;
+            d2[b] = r2[b] * t.inv_theta;
+        }
         ph.settle();
-        P0[idx] = d1;
-        P2[idx] = d2;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            P0[nb[b].lq] = d1[b];
+            P2[nb[b].lq] = d2[b];
+        }
         ph.publish();
         float *c1p = P0, *c2p = P2, *n1p = P1, *n2p = P3;
         const float diag = 1.f + 4.f * t.alpha;
         for (int k = 0; k < t.K; ++k) {
-            const float a1 = diag * d1 - t.alpha * (nb.above(c1p) + nb.below(c1p) + nb.left(c1p) + nb.right(c1p));
-            const float a2 = diag * d2 - t.alpha * (nb.above(c2p) + nb.below(c2p) + nb.left(c2p) + nb.right(c2p));
-            u1 += d1;
-            u2 += d2;
-            r1 -= a1;
-            r2 -= a2;
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                const BandNbr<NC, BR>& n = nb[b];
+                const float a1 = diag * d1[b] - t.alpha * (n.above(c1p) + n.below(c1p) + n.left(c1p) + n.right(c1p));
+                const float a2 = diag * d2[b] - t.alpha * (n.above(c2p) + n.below(c2p) + n.left(c2p) + n.right(c2p));
+                u1[b] += d1[b];
+                u2[b] += d2[b];
+                r1[b] -= a1;
+                r2[b] -= a2;
+            }
             if (k + 1 < t.K) {
-                d1 = t.c1[k] * d1 + t.c2[k] * r1;
-                d2 = t.c1[k] * d2 + t.c2[k] * r2;
+#pragma unroll
+                for (int b = 0; b < NB; ++b) {
+                    d1[b] = t.c1[k] * d1[b] + t.c2[k] * r1[b];
+                    d2[b] = t.c1[k] * d2[b] + t.c2[k] * r2[b];
+                }
                 ph.settle();
-                n1p[idx] = d1;
-                n2p[idx] = d2;
+#pragma unroll
+                for (int b = 0; b < NB; ++b) {
+                    n1p[nb[b].lq] = d1[b];
+                    n2p[nb[b].lq] = d2[b];
+                }
                 ph.publish();
                 float* x = c1p; c1p = n1p; n1p = x;
                 x = c2p; c2p = n2p; n2p = x;
@@ -771,27 +841,40 @@ __device__ __forceinline__ void theta_coarse_step_cl(int32_t& q, const BandNbr<N
         out1 = n1p;
         out2 = n2p;
     }
-    const long long H1 = F1 + __float2ll_rn(u1), H2 = F2 + __float2ll_rn(u2);
-    bad |= (unsigned)((H1 != (long long)(int32_t)H1) | (H2 != (long long)(int32_t)H2));
+    long long H1[NB], H2[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        H1[b] = F1[b] + __float2ll_rn(u1[b]);
+        H2[b] = F2[b] + __float2ll_rn(u2[b]);
+        bad |= (unsigned)((H1[b] != (long long)(int32_t)H1[b]) | (H2[b] != (long long)(int32_t)H2[b]));
+    }
     ph.settle();
-    out1[idx] = as_f(static_cast<int32_t>(H1));
-    out2[idx] = as_f(static_cast<int32_t>(H2));
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        out1[nb[b].lq] = as_f(static_cast<int32_t>(H1[b]));
+        out2[nb[b].lq] = as_f(static_cast<int32_t>(H2[b]));
+    }
     ph.publish();
-    const long long v = (long long)q + (H1 - as_i(nb.above(out1))) + (H2 - as_i(nb.left(out2)));
-    bad |= (unsigned)((v >= (1LL << 30)) | (v <= -(1LL << 30)));
-    q = static_cast<int32_t>(v);
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        const long long v = (long long)q[b] + (H1[b] - as_i(nb[b].above(out1))) + (H2[b] - as_i(nb[b].left(out2)));
+        bad |= (unsigned)((v >= (1LL << 30)) | (v <= -(1LL << 30)));
+        q[b] = static_cast<int32_t>(v);
+    }
     ph.settle();
-    sq[idx] = q;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) sq[nb[b].lq] = q[b];
     ClPhase::arrive();
     ph.pend = true;
 }
 
 // The theta-scheme sample kernel for a cluster of CL CTAs per sample (see
-// above); a cluster is one sample slot of a persistent grid of clusters.
-template <int N, int CL, bool CPL>
-__global__ void __launch_bounds__(CShape<N, CL>::THREADS, 1) theta_cluster_kernel(const KArgs a, const TArgs t) {
-    using S = CShape<N, CL>;
-    constexpr int NC = S::NC, BR = S::BR, BAND = S::BAND, THREADS = S::THREADS;
+// above), NB blocks of a block row per thread; a cluster is one sample
+// slot of a persistent grid of clusters.
+template <int N, int CL, int NB, bool CPL>
+__global__ void __launch_bounds__(CShape<N, CL, NB>::THREADS, 1) theta_cluster_kernel(const KArgs a, const TArgs t) {
+    using S = CShape<N, CL, NB>;
+    constexpr int NC = S::NC, BR = S::BR, BAND = S::BAND, THREADS = S::THREADS, RT = S::RT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int tid = threadIdx.x;
     const int rank = static_cast<int>(cg::this_cluster().block_rank());
@@ -806,15 +889,25 @@ __global__ void __launch_bounds__(CShape<N, CL>::THREADS, 1) theta_cluster_kerne
     for (int i = tid; i < a.slot_stride; i += THREADS) acc[i] = 0.0;
     float* const planes[4] = {P0, P1, P2, P3};
 
-    const int lr = tid / NC, I2 = tid % NC;           // block row within the band, column
-    const int I1 = rank * BR + lr;                    // coarse cell; fine block rows 2 I1 + v1, cols 2 I2 + v2
-    const BandNbr<NC, BR> nb(lr, I2, rank, CL);
+    // block row within the band; the thread's blocks are columns j0, j0 + RT, ...
+    // (consecutive lanes on consecutive blocks: conflict-free 16-byte plane accesses)
+    const int lr = tid / RT, j0 = tid % RT;
+    const int I1 = rank * BR + lr;                    // coarse row; fine block rows 2 I1 + v1, cols 2 I2 + v2
+    BandNbr<NC, BR> nb[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) nb[b] = BandNbr<NC, BR>(lr, j0 + b * RT, rank, CL);
     ClPhase ph(lr == 0 || lr == BR - 1);              // the band's first and last rows read other CTAs
-    const int gc = I1 * NC + I2;                      // global coarse index
-    const int f00 = (2 * I1) * N + 2 * I2;
-    const int fidx[4] = {f00, f00 + 1, f00 + N, f00 + N + 1};
-    const uint32_t p_top = static_cast<uint32_t>(f00 >> 1);
-    const uint32_t p_bot = static_cast<uint32_t>((f00 + N) >> 1);
+    int gc[NB], fidx[NB][4];
+    uint32_t p_top[NB], p_bot[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        const int I2 = j0 + b * RT;
+        gc[b] = I1 * NC + I2;                         // global coarse index
+        const int f00 = (2 * I1) * N + 2 * I2;
+        fidx[b][0] = f00; fidx[b][1] = f00 + 1; fidx[b][2] = f00 + N; fidx[b][3] = f00 + N + 1;
+        p_top[b] = static_cast<uint32_t>(f00 >> 1);
+        p_bot[b] = static_cast<uint32_t>((f00 + N) >> 1);
+    }
 
     const long long n_slots = (long long)gridDim.x / CL;
     const long long slot = (long long)blockIdx.x / CL;
@@ -829,46 +922,57 @@ __global__ void __launch_bounds__(CShape<N, CL>::THREADS, 1) theta_cluster_kerne
         const uint32_t c2 = static_cast<uint32_t>(sid);
         const uint32_t c3 = a.tag | ((static_cast<uint32_t>(static_cast<unsigned long long>(sid) >> 32) & 0xffffu) << 16);
 
-        int32_t q[4], qc = 0;
+        int32_t q[NB][4], qc[NB];
+        float zt0[NB], zt1[NB];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) q[i] = a.q0f[fidx[i]];
-        float zt0 = 0.f, zt1 = 0.f;
-        if constexpr (CPL) {
-            qc = a.q0c[gc];
-            sqc[nb.lq] = qc;
+        for (int b = 0; b < NB; ++b) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) q[b][i] = a.q0f[fidx[b][i]];
+            zt0[b] = zt1[b] = 0.f;
+            qc[b] = 0;
+            if constexpr (CPL) {
+                qc[b] = a.q0c[gc[b]];
+                sqc[nb[b].lq] = qc[b];
+            }
         }
         ph.full();
 
         for (int m = 0; m < a.M; ++m) {
-            int32_t G1[4], G2[4];
+            int32_t G1[NB][4], G2[NB][4];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const uint4 x = philox10(make_uint4(h ? p_bot : p_top, static_cast<uint32_t>(m), c2, c3), a.key0, a.key1);
-                float ra, ca, sa, rb, cb, sb;
-                box_muller_polar(x.x, x.y, ra, ca, sa);
-                box_muller_polar(x.z, x.w, rb, cb, sb);
-                const float ta = noise_amp(q[2 * h], a.gf) * ra;
-                const float tb = noise_amp(q[2 * h + 1], a.gf) * rb;
-                G1[2 * h] = __float2int_rn(ta * ca);
-                G2[2 * h] = __float2int_rn(ta * sa);
-                G1[2 * h + 1] = __float2int_rn(tb * cb);
-                G2[2 * h + 1] = __float2int_rn(tb * sb);
-                if constexpr (CPL) {
-                    zt0 = fmaf(rb, cb, fmaf(ra, ca, zt0));
-                    zt1 = fmaf(rb, sb, fmaf(ra, sa, zt1));
+            for (int b = 0; b < NB; ++b)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint4 x = philox10(make_uint4(h ? p_bot[b] : p_top[b], static_cast<uint32_t>(m), c2, c3),
+                                             a.key0, a.key1);
+                    float ra, ca, sa, rb, cb, sb;
+                    box_muller_polar(x.x, x.y, ra, ca, sa);
+                    box_muller_polar(x.z, x.w, rb, cb, sb);
+                    const float ta = noise_amp(q[b][2 * h], a.gf) * ra;
+                    const float tb = noise_amp(q[b][2 * h + 1], a.gf) * rb;
+                    G1[b][2 * h] = __float2int_rn(ta * ca);
+                    G2[b][2 * h] = __float2int_rn(ta * sa);
+                    G1[b][2 * h + 1] = __float2int_rn(tb * cb);
+                    G2[b][2 * h + 1] = __float2int_rn(tb * sb);
+                    if constexpr (CPL) {
+                        zt0[b] = fmaf(rb, cb, fmaf(ra, ca, zt0[b]));
+                        zt1[b] = fmaf(rb, sb, fmaf(ra, sa, zt1[b]));
+                    }
                 }
-            }
-            theta_fine_step_cl<NC, BR>(q, G1, G2, nb, planes, t.Af64, t, bad, ph);
+            theta_fine_step_cl<NC, BR, NB>(q, G1, G2, nb, planes, t.Af64, t, bad, ph);
 
             if constexpr (CPL) {
                 if ((m & 3) == 3) {
-                    const float sc = noise_amp(qc, a.gc);
                     ph.settle();
-                    P0[nb.lq] = as_f(__float2int_rn(sc * zt0));
-                    P2[nb.lq] = as_f(__float2int_rn(sc * zt1));
-                    zt0 = zt1 = 0.f;
+#pragma unroll
+                    for (int b = 0; b < NB; ++b) {
+                        const float sc = noise_amp(qc[b], a.gc);
+                        P0[nb[b].lq] = as_f(__float2int_rn(sc * zt0[b]));
+                        P2[nb[b].lq] = as_f(__float2int_rn(sc * zt1[b]));
+                        zt0[b] = zt1[b] = 0.f;
+                    }
                     ph.publish();
-                    theta_coarse_step_cl<NC, BR>(qc, nb, sqc, P0, P1, P2, P3, t.Ac64, t, bad, ph);
+                    theta_coarse_step_cl<NC, BR, NB>(qc, nb, sqc, P0, P1, P2, P3, t.Ac64, t, bad, ph);
                 }
             }
         }
@@ -876,19 +980,28 @@ __global__ void __launch_bounds__(CShape<N, CL>::THREADS, 1) theta_cluster_kerne
         // ---- observables of the band, then the band totals summed on rank 0 in rank order
         double v[kRed];
         {
-            long long mf = 0;
+            long long mf = 0, mc = 0;
 #pragma unroll
-            for (int i = 0; i < 4; ++i) mf += q[i];
+            for (int b = 0; b < NB; ++b) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) mf += q[b][i];
+                mc += qc[b];
+            }
             v[2 * kMaxObs] = static_cast<double>(mf);
-            v[2 * kMaxObs + 1] = CPL ? static_cast<double>(qc) : 0.0;
+            v[2 * kMaxObs + 1] = CPL ? static_cast<double>(mc) : 0.0;
 #pragma unroll
             for (int k = 0; k < kMaxObs; ++k) {
                 double sf = 0.0, sc = 0.0;
                 if (k < a.n_obs) {
 #pragma unroll
-                    for (int i = 0; i < 4; ++i)
-                        sf += static_cast<double>(q[i] - a.qbf[fidx[i]]) * t.phif64[(size_t)k * N * N + fidx[i]];
-                    if constexpr (CPL) sc = static_cast<double>(qc - a.qbc[gc]) * t.phic64[(size_t)k * NC * NC + gc];
+                    for (int b = 0; b < NB; ++b) {
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            sf += static_cast<double>(q[b][i] - a.qbf[fidx[b][i]]) *
+                                  t.phif64[(size_t)k * N * N + fidx[b][i]];
+                        if constexpr (CPL)
+                            sc += static_cast<double>(qc[b] - a.qbc[gc[b]]) * t.phic64[(size_t)k * NC * NC + gc[b]];
+                    }
                 }
                 v[k] = sf;
                 v[kMaxObs + k] = sc;
@@ -1000,13 +1113,13 @@ cudaError_t launch_n(const KArgs& a, const TArgs& t, int n_ctas, cudaStream_t st
 }
 
 // Grids beyond one CTA: clusters of CL CTAs.
-constexpr int kThetaClusterN = 128, kThetaClusterCL = 8;
+constexpr int kThetaClusterN = 128, kThetaClusterCL = 4, kThetaClusterNB = 2;
 
-template <int N, int CL, bool CPL>
+template <int N, int CL, int NB, bool CPL>
 cudaError_t prepare_cluster(int slot_stride, VariantInfo* out) {
-    using S = CShape<N, CL>;
+    using S = CShape<N, CL, NB>;
     const size_t smem = S::smem(slot_stride);
-    cudaError_t e = cudaFuncSetAttribute(theta_cluster_kernel<N, CL, CPL>,
+    cudaError_t e = cudaFuncSetAttribute(theta_cluster_kernel<N, CL, NB, CPL>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg{};
@@ -1021,7 +1134,7 @@ cudaError_t prepare_cluster(int slot_stride, VariantInfo* out) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int clusters = 0;
-    if ((e = cudaOccupancyMaxActiveClusters(&clusters, theta_cluster_kernel<N, CL, CPL>, &cfg)) != cudaSuccess)
+    if ((e = cudaOccupancyMaxActiveClusters(&clusters, theta_cluster_kernel<N, CL, NB, CPL>, &cfg)) != cudaSuccess)
         return e;
     *out = VariantInfo{};
     out->supported = clusters > 0;
@@ -1033,9 +1146,9 @@ cudaError_t prepare_cluster(int slot_stride, VariantInfo* out) {
     return cudaSuccess;
 }
 
-template <int N, int CL, bool CPL>
+template <int N, int CL, int NB, bool CPL>
 cudaError_t launch_cluster(const KArgs& a, const TArgs& t, int n_ctas, cudaStream_t st, int priority) {
-    using S = CShape<N, CL>;
+    using S = CShape<N, CL, NB>;
     if (n_ctas % CL != 0) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(n_ctas);
@@ -1056,7 +1169,7 @@ cudaError_t launch_cluster(const KArgs& a, const TArgs& t, int n_ctas, cudaStrea
     }
     cfg.attrs = attr;
     cfg.numAttrs = na;
-    return cudaLaunchKernelEx(&cfg, theta_cluster_kernel<N, CL, CPL>, a, t);
+    return cudaLaunchKernelEx(&cfg, theta_cluster_kernel<N, CL, NB, CPL>, a, t);
 }
 
 }  // namespace
@@ -1072,8 +1185,8 @@ cudaError_t theta_variant_info(int n, bool coupled, int slot_stride, VariantInfo
         case 32: return coupled ? prepare<32, true>(slot_stride, out) : prepare<32, false>(slot_stride, out);
         case 64: return coupled ? prepare<64, true>(slot_stride, out) : prepare<64, false>(slot_stride, out);
         case kThetaClusterN:
-            return coupled ? prepare_cluster<kThetaClusterN, kThetaClusterCL, true>(slot_stride, out)
-                           : prepare_cluster<kThetaClusterN, kThetaClusterCL, false>(slot_stride, out);
+            return coupled ? prepare_cluster<kThetaClusterN, kThetaClusterCL, kThetaClusterNB, true>(slot_stride, out)
+                           : prepare_cluster<kThetaClusterN, kThetaClusterCL, kThetaClusterNB, false>(slot_stride, out);
         default: return cudaSuccess;   // supported = 0
     }
 }
@@ -1088,8 +1201,8 @@ cudaError_t launch_theta(int n, bool coupled, const KArgs& a, const TArgs& t, in
         case 32: return coupled ? launch_n<32, true>(a, t, n_ctas, st, priority) : launch_n<32, false>(a, t, n_ctas, st, priority);
         case 64: return coupled ? launch_n<64, true>(a, t, n_ctas, st, priority) : launch_n<64, false>(a, t, n_ctas, st, priority);
         case kThetaClusterN:
-            return coupled ? launch_cluster<kThetaClusterN, kThetaClusterCL, true>(a, t, n_ctas, st, priority)
-                           : launch_cluster<kThetaClusterN, kThetaClusterCL, false>(a, t, n_ctas, st, priority);
+            return coupled ? launch_cluster<kThetaClusterN, kThetaClusterCL, kThetaClusterNB, true>(a, t, n_ctas, st, priority)
+                           : launch_cluster<kThetaClusterN, kThetaClusterCL, kThetaClusterNB, false>(a, t, n_ctas, st, priority);
         default: return cudaErrorInvalidValue;
     }
 }

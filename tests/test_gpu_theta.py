@@ -92,15 +92,15 @@ def test_theta_kernel_matches_oracle(dk, name, level, tag, count):
 
 @pytest.mark.parametrize("name,tag", [("theta16_64", 0), ("theta16_64", 1), ("implicit16_64", 0)])
 def test_theta_cluster_level_128_matches_oracle(dk, name, tag):
-    """The 128^2 level (coupled with 64^2) runs on the cluster kernel: 8 CTAs
-    per sample, each a band of 8 block rows, neighbour rows through
-    distributed shared memory and cluster barriers.  Full horizon (384 fine
+    """The 128^2 level (coupled with 64^2) runs on the cluster kernel: 4 CTAs
+    per sample, each a band of 16 block rows (two blocks per thread),
+    neighbour rows through distributed shared memory and cluster barriers.  Full horizon (384 fine
     steps), sample by sample against the oracle's exact Fourier solves."""
     wl = W.get(name).with_(L_max=3)
     level, count, seed, first = 3, 4, 41, 2
     with dk.Context.from_workload(wl) as ctx:
         info = ctx.level_info(level)
-        assert info.n == 128 and info.theta == 1 and info.cluster == 8 and info.cheb_steps > 0
+        assert info.n == 128 and info.theta == 1 and info.cluster == 4 and info.cheb_steps > 0
         sums, samp = _gpu(ctx, dk, level, tag, first, count, seed)
     levels = oracle.level_table(wl.length, wl.n0, wl.L_max, wl.T, wl.mu, wl.M0)
     coupled = tag == 0
