@@ -108,7 +108,7 @@ typedef struct {
                                (Definition 2.1): (I - b0 tau/2 Delta_h) rho^m = (I + b1 tau/2 Delta_h)
                                rho^(m-1) + noise.  0: explicit Euler--Maruyama (Section 7.2).  b0 > 0
                                runs every level on the theta-scheme kernel (n0 2^L_max <= 128, no
-                               stream_from_n; a 128^2 level runs on clusters of 8 CTAs per sample); cfl_mu may then exceed 1/2 up to the scheme's
+                               stream_from_n; a 128^2 level runs on clusters of 4 CTAs per sample); cfl_mu may then exceed 1/2 up to the scheme's
                                stability bound 1 / (2 (b1 - b0)) (none for b0 >= 1/2), with
                                b0 cfl_mu <= 10 */
     int32_t theta_kernel;   /* 1: run b0 = 0 on the theta-scheme kernel too (the same integer

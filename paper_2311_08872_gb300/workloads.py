@@ -231,7 +231,7 @@ WORKLOADS: Dict[str, Workload] = {
                            note="Crank-Nicolson weights at tau/h^2 = 1, levels 16^2..64^2"),
     "theta16_128": Workload("theta16_128", 1.0, 16, 3, 0.02, 1.0, 1e5, "sinsin", [COS1],
                             seed=7, eps_rel=1e-2, b0=0.5,
-                            note="Crank-Nicolson weights at tau/h^2 = 1, levels 16^2..128^2 (128^2 on 8-CTA clusters)"),
+                            note="Crank-Nicolson weights at tau/h^2 = 1, levels 16^2..128^2 (128^2 on 4-CTA clusters)"),
     "implicit16_64": Workload("implicit16_64", 1.0, 16, 2, 0.02, 2.0, 1e5, "sinsin", [COS1],
                               seed=8, eps_rel=1e-2, b0=1.0,
                               note="implicit Euler weights at tau/h^2 = 2, levels 16^2..64^2"),

@@ -33,7 +33,7 @@ def test_workload_levels_and_inputs(name):
     if wl.coupling == 1:
         assert wl.n0 == 6 and wl.L_max <= 2
     if wl.b0 > 0:
-        assert wl.n(wl.L_max) <= 128      # the theta kernels: one CTA up to 64^2, 8-CTA clusters at 128^2
+        assert wl.n(wl.L_max) <= 128      # the theta kernels: one CTA up to 64^2, 4-CTA clusters at 128^2
 
 
 def test_cell_centred_workload_is_the_shifted_grid():
