@@ -19,7 +19,7 @@ LIB = os.path.join(PKG, "libmlmc_dk.so")
 BUILD_DIR = os.path.join(ROOT, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["dk_kernels.cu", "dk_band.cu", "dk_stream.cu", "dk_surrogate.cu", "dk_umma.cu", "dk_theta.cu", "dk_fourier.cu", "mlmc_dk.cpp"]
+SOURCES = ["dk_kernels.cu", "dk_band.cu", "dk_stream.cu", "dk_surrogate.cu", "dk_umma.cu", "dk_theta.cu", "dk_fourier.cu", "dk_fourier_cluster.cu", "mlmc_dk.cpp"]
 HEADERS = ["dk_kernels.h", "dk_device.cuh"]
 
 

@@ -197,6 +197,12 @@ cudaError_t fourier_variant_info(int n, bool coupled, int slot_stride, VariantIn
 // One CTA per sample slot; partials must hold n_ctas * slot_stride doubles.
 cudaError_t launch_fourier(int n, bool coupled, const KArgs& a, const FArgs& f, int n_ctas, cudaStream_t stream,
                            int priority = 0);
+// Grids beyond one CTA (162^2, coupled with 54^2): clusters of 6 CTAs, one
+// sample slot per cluster; n_ctas a multiple of 6.
+bool fourier_cluster_supported(int n);
+cudaError_t fourier_cluster_variant_info(int n, bool coupled, int slot_stride, VariantInfo* out);
+cudaError_t launch_fourier_cluster(int n, bool coupled, const KArgs& a, const FArgs& f, int n_ctas,
+                                   cudaStream_t stream, int priority);
 
 // ---- learned level below level 0
 constexpr int kModes = 32;     // real orthonormal modes

@@ -425,6 +425,8 @@ cudaError_t launch_main(const mlmc_dk_ctx* c, int level, bool coupled, const dk:
         fa.P1 = coupled ? t.d_P1 : nullptr;
         fa.phif64 = t.d_phi64;
         fa.phic64 = coupled ? c->lv[level - 1].d_phi64 : nullptr;
+        if (dk::fourier_cluster_supported(t.n))
+            return dk::launch_fourier_cluster(t.n, coupled, a, fa, n_ctas, st, priority);
         return dk::launch_fourier(t.n, coupled, a, fa, n_ctas, st, priority);
     }
     if (c->theta) {
@@ -626,8 +628,9 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
     if (fourier) {
         long long nl = cfg->n0;
         for (int l = 1; l <= cfg->L_max; ++l) nl *= 3;
-        if (cfg->n0 != 6 || nl > 54)
-            return fail(nullptr, MLMC_DK_ERR_UNSUPPORTED, "Fourier coupling: levels 6^2, 18^2, 54^2 (n0 = 6, L_max <= 2)");
+        if (cfg->n0 != 6 || nl > 162)
+            return fail(nullptr, MLMC_DK_ERR_UNSUPPORTED,
+                        "Fourier coupling: levels 6^2, 18^2, 54^2, 162^2 (n0 = 6, L_max <= 3)");
         if (cfg->theta_b0 != 0.0 || cfg->theta_kernel || cfg->stream_from_n != 0)
             return fail(nullptr, MLMC_DK_ERR_UNSUPPORTED, "Fourier coupling: explicit scheme, no streamed levels");
     }
@@ -887,7 +890,9 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
             for (int mode = 0; mode < 2; ++mode) {
                 if (mode == 1 && l == 0) continue;
                 dk::VariantInfo vi{};
-                if ((e = dk::fourier_variant_info(t.n, mode == 1, c->stride, &vi)) != cudaSuccess) {
+                e = dk::fourier_cluster_supported(t.n) ? dk::fourier_cluster_variant_info(t.n, mode == 1, c->stride, &vi)
+                                                       : dk::fourier_variant_info(t.n, mode == 1, c->stride, &vi);
+                if (e != cudaSuccess) {
                     mlmc_dk_free(c);
                     return cuda_fail(nullptr, e, "Fourier kernel setup");
                 }

@@ -34,6 +34,8 @@ Workloads:
                         same grids.
   * ``fourier6_54``  -- Fourier coupling (Section 3.1), levels 6^2, 18^2, 54^2
                         (h ratio 3, tau ratio 9), T=0.02, N=1e5.
+  * ``fourier6_162`` -- the same with a fourth level, 162^2 (a 6-CTA cluster
+                        per sample).
   * ``paper_reg_fourier`` -- the paper's regular setting (Section 7.2) with the
                         Fourier coupling on 6^2, 18^2, 54^2 (same tau/h^2 as the
                         paper's levels).
@@ -238,6 +240,9 @@ WORKLOADS: Dict[str, Workload] = {
     "fourier6_54": Workload("fourier6_54", 1.0, 6, 2, 0.02, 0.1, 1e5, "sinsin", [COS1],
                             seed=9, eps_rel=1e-2, coupling=1,
                             note="Fourier coupling, levels 6^2, 18^2, 54^2"),
+    "fourier6_162": Workload("fourier6_162", 1.0, 6, 3, 0.02, 0.1, 1e5, "sinsin", [COS1],
+                             seed=9, eps_rel=1e-2, coupling=1,
+                             note="Fourier coupling, levels 6^2, 18^2, 54^2, 162^2 (162^2 on 6-CTA clusters)"),
     "paper_reg_fourier": Workload("paper_reg_fourier", TWO_PI, 6, 2, 1.024, 1.024 / (TWO_PI / 4) ** 2, 2e9,
                                   "paper_reg", [Observable("sin+sin")], seed=10, coupling=1,
                                   note="Section 7 setting, regular datum, Fourier coupling on 6^2, 18^2, 54^2"),

@@ -144,7 +144,7 @@ def test_chebyshev_schedule_solves_the_implicit_system(dk, alpha):
     assert dk.chebyshev_schedule(0.0)[0] == 0
 
 
-@pytest.mark.parametrize("n", [18, 54])
+@pytest.mark.parametrize("n", [18, 54, 162])
 def test_fourier_restriction_matrix_is_the_oracles(dk, n):
     """P1 S P1^T from the host's matrix equals the oracle's restriction (its own
     DFT sums) to FP32 accuracy, and P1 has orthonormal rows."""
@@ -207,7 +207,7 @@ def test_host_theta_mean_field_matches_oracle(dk, b0, mu, M):
 
 def test_fourier_coupling_config_checks(dk):
     """The Fourier hierarchy's configuration checks run before any GPU call:
-    an unknown coupling, grids other than 6^2/18^2/54^2, and the Fourier
+    an unknown coupling, grids other than 6^2/18^2/54^2/162^2, and the Fourier
     coupling with the theta-scheme are refused."""
     def ctx(n0, L_max, **kw):
         n = [n0 * 3 ** l for l in range(L_max + 1)]
@@ -215,7 +215,7 @@ def test_fourier_coupling_config_checks(dk):
                           [[np.ones((m, m))] for m in n], **kw)
     cases = [(dict(coupling=2), 6, 1, dk.ERR_INVALID),
              (dict(coupling=1), 12, 1, dk.ERR_UNSUPPORTED),
-             (dict(coupling=1), 6, 3, dk.ERR_UNSUPPORTED),
+             (dict(coupling=1), 6, 4, dk.ERR_UNSUPPORTED),
              (dict(coupling=1, theta_b0=0.5), 6, 1, dk.ERR_UNSUPPORTED)]
     for kw, n0, L, code in cases:
         with pytest.raises(dk.MLMCError) as e:

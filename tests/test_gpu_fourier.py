@@ -133,3 +133,102 @@ def test_four_observables_with_products(dk):
         err = np.abs(samp[:, cols] + yb[None, :] - yo) / (TOL * np.maximum(np.abs(yo), scale[None, :]))
         assert float(err.max()) <= 1.0, (key, float(err.max()))
     assert int(sums[0]) == count and sums[1] == 0.0
+
+
+# ---------------------------------------------------------------- 162^2 on clusters
+def _short162():
+    """The four-level hierarchy over one level-0 step (T = tau_0 = 0.0025,
+    tau/h^2 = 0.09): 729 fine and 81 coarse steps on the 162^2 level, so that
+    the oracle's samples take seconds."""
+    return W.get("fourier6_162").with_(name="fourier6_162_short", T=0.0025, M0=1)
+
+
+def _worst(wl, levels, level, coupled, samp, r):
+    ybf = _ybar(wl, levels, level)
+    pairs = [(samp[:, 0] + ybf[0], r["Y_f"][:, 0], ybf[0])]
+    if coupled:
+        ybc = _ybar(wl, levels, level - 1)
+        pairs.append((samp[:, 1] + ybc[0], r["Y_c"][:, 0], ybc[0]))
+    worst = 0.0
+    for y, yo, yb in pairs:
+        scale = np.sqrt(np.mean((yo - yb) ** 2))
+        worst = max(worst, float(np.max(np.abs(y - yo) / (TOL * np.maximum(np.abs(yo), scale)))))
+    return worst
+
+
+@pytest.mark.parametrize("tag,count", [(0, 6), (1, 4)])
+def test_fourier_cluster_level_162_matches_oracle(dk, tag, count):
+    """The 162^2 level (coupled with 54^2) runs on the cluster kernel: 6 CTAs
+    per sample, the neighbouring rows and the partial restrictions of the
+    coarse noise through distributed shared memory.  Per-sample parity with the
+    oracle for the coupled pair (tag 0) and the fine path alone (tag 1)."""
+    wl = _short162()
+    level, seed, first = 3, 51 + tag, 5
+    levels = _levels(wl)
+    assert levels[level].n == 162 and levels[level].M == 729
+    with dk.Context.from_workload(wl) as ctx:
+        info = ctx.level_info(level)
+        assert info.coupling == 1 and info.n == 162 and info.M == 729 and info.cluster == 6
+        sums, samp = _gpu(ctx, dk, level, tag, first, count, seed)
+    coupled = tag == 0
+    ol = oracle.level_inputs(wl.length, levels, wl.N, wl.rho0_all(), wl.phi_all(), level, coupled, coupling=1)
+    r = oracle.run_samples(ol, seed, range(first, first + count), coupled, stream=tag, processes=count)
+    worst = _worst(wl, levels, level, coupled, samp, r)
+    print(f"fourier6_162 level 3 tag {tag}: worst/bound {worst:.3g}")
+    assert worst <= 1.0
+    # the integer flux form conserves the (quantised) initial mass exactly
+    for col, key, l in ((2, "mass_f", level), (3, "mass_c", level - 1))[:2 if coupled else 1]:
+        m0 = oracle.inner_h(wl.rho0(l), np.ones_like(wl.rho0(l)), levels[l].h)
+        np.testing.assert_allclose(samp[:, col], m0, rtol=1e-7)
+        assert np.ptp(samp[:, col]) == 0.0
+        np.testing.assert_allclose(r[key], m0, rtol=1e-12)
+    assert int(sums[0]) == count and sums[1] == 0.0
+
+
+def test_fourier_cluster_level_many_samples_and_batch(dk):
+    """More samples than resident clusters (several passes of the persistent
+    cluster grid, a ragged last pass): device sums equal the per-sample
+    outputs' sums, and the multi-level batch gives the same sums as per-level
+    launches with the 162^2 level in it."""
+    import torch
+    wl = _short162()
+    st = torch.cuda.current_stream().cuda_stream
+    with dk.Context.from_workload(wl) as ctx:
+        info = ctx.level_info(3)
+        count = 2 * (info.in_flight or 24) + 5
+        sums, samp = _gpu(ctx, dk, 3, 0, 0, count, 14)
+        assert int(sums[0]) == count and sums[1] == 0.0
+        dp = wl.N * (samp[:, 0] ** 2 - samp[:, 1] ** 2)
+        np.testing.assert_allclose(sums[2], dp.sum(), rtol=1e-9)
+        S = dk.sums_len(ctx.n_quant)
+        counts = [400, 100, 30, 20]
+        batch = torch.zeros(4, S, dtype=torch.float64, device="cuda")
+        ctx.run_batch_dev(counts, 3, 15, batch.data_ptr(), st)
+        torch.cuda.synchronize()
+        for l, m in enumerate(counts):
+            ref = torch.zeros(S, dtype=torch.float64, device="cuda")
+            ctx.run_level_dev(l, 0, 3, m, 15, ref.data_ptr(), 0, st)
+            torch.cuda.synchronize()
+            np.testing.assert_allclose(batch[l].cpu().numpy(), ref.cpu().numpy(), rtol=1e-12, atol=0)
+
+
+def test_fourier_162_coarse_member_law_and_variance_decay(dk):
+    """Full horizon (5832 fine steps at 162^2): E[P_c] of level-3 pairs equals
+    E[P_f] of stand-alone 54^2 paths (Remark distribution_W_ell), the mass
+    stays exact, and V_3 / V_2 falls like 3^-beta with beta well above the NN
+    coupling's 2 (the paper predicts 4)."""
+    wl = W.get("fourier6_162").with_(N=1e9)
+    with dk.Context.from_workload(wl) as ctx:
+        s3 = ctx.run_level(3, 1500, 21)[0]
+        s2 = ctx.run_level(2, 20000, 22)[0]
+        a2 = ctx.run_level(2, 20000, 23, mc=True)[0]
+    var = lambda s: (s.dp2 - s.dp1 ** 2 / s.n) / (s.n - 1)
+    mc, ma = s3.pc1 / s3.n, a2.pf1 / a2.n
+    vc = (s3.pc2 - s3.pc1 ** 2 / s3.n) / (s3.n - 1)
+    va = (a2.pf2 - a2.pf1 ** 2 / a2.n) / (a2.n - 1)
+    assert abs(mc - ma) < 4.0 * math.sqrt(vc / s3.n + va / a2.n), (mc, ma)
+    assert s3.max_mass_err < 1e-12
+    v2, v3 = var(s2), var(s3)
+    beta = math.log(v2 / v3) / math.log(3.0)
+    print(f"Fourier coupling at N = 1e9: V_2 = {v2:.3e}, V_3 = {v3:.3e}, beta = {beta:.2f}")
+    assert beta > 2.5

@@ -31,7 +31,7 @@ def test_workload_levels_and_inputs(name):
         for p in wl.phi(l):
             assert p.shape == (lv.n, lv.n) and np.all(np.isfinite(p))
     if wl.coupling == 1:
-        assert wl.n0 == 6 and wl.L_max <= 2
+        assert wl.n0 == 6 and wl.L_max <= 3      # 6^2 .. 162^2
     if wl.b0 > 0:
         assert wl.n(wl.L_max) <= 128      # the theta kernels: one CTA up to 64^2, 4-CTA clusters at 128^2
 
