@@ -67,6 +67,12 @@ THETA_SOURCES = ("dk_theta.cu", "dk_device.cuh")
 FOURIER_KERNEL_INSTR = {"kernel": "fourier_kernel n=54 coupled=True",
                         "instructions_per_cell_step": 94.6, "sources_sha256_16": "f58083f4e5afc61f"}
 FOURIER_SOURCES = ("dk_fourier.cu", "dk_device.cuh")
+# The 162^2 Fourier level on 6-CTA clusters: thread instructions per cell-step
+# (fine and coarse cell-steps) of the coupled launch of 144 samples, from its
+# ncu capture; valid under the recorded hash of its sources.
+FOURIER_CLUSTER_KERNEL_INSTR = {"kernel": "fourier_cluster_kernel n=162 coupled=True",
+                                "instructions_per_cell_step": 106.7, "sources_sha256_16": "9d8da938f719df45"}
+FOURIER_CLUSTER_SOURCES = ("dk_fourier_cluster.cu", "dk_device.cuh")
 
 
 # ncu figures of the dominant kernels per grid size, valid while their sources
@@ -190,7 +196,9 @@ def theta_scheme(stream):
 
 def fourier_coupling(stream):
     """The Fourier-coupled kernel on the finest level of fourier6_54 (54^2
-    coupled with 18^2, ratio 3): 32 waves of one sample per SM, CUDA events."""
+    coupled with 18^2, ratio 3): 32 waves of one sample per SM, CUDA events;
+    and the 162^2 level of fourier6_162 (coupled with 54^2) on its cluster
+    kernel, 144 samples."""
     import torch
     from paper_2311_08872_gb300 import mlmc_dk, workloads
     wl = workloads.get("fourier6_54")
@@ -217,6 +225,31 @@ def fourier_coupling(stream):
         peak = 4.0 * SMS * SM_MAX_MHZ * 1e6
         out["issue"] = {"instructions_per_cell_step": ipc, "achieved_warp_inst_per_s": warp_inst,
                         "peak_warp_inst_per_s": peak, "frac": warp_inst / peak}
+    # the 162^2 level (coupled with 54^2) on 6-CTA clusters, 144 samples in one launch
+    wl = workloads.get("fourier6_162")
+    level, count = wl.L_max, 144
+    with mlmc_dk.Context.from_workload(wl, stream=stream.cuda_stream) as c:
+        info = c.level_info(level)
+        sums = torch.zeros(mlmc_dk.sums_len(c.n_quant), dtype=torch.float64, device="cuda")
+        c.run_level_dev(level, 0, 0, count, 13, sums.data_ptr(), 0, stream.cuda_stream)      # warm-up
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        c.run_level_dev(level, 0, count, count, 13, sums.data_ptr(), 0, stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) * 1e-3
+    cl = {"workload": wl.name, "level": level, "n": info.n, "coarse_n": info.n // 3, "fine_steps": info.M,
+          "cluster": info.cluster, "samples": count, "s": sec, "cell_steps_per_s": count * info.cost / sec,
+          "fine_cell_steps_per_s": count * info.cost_mc / sec, "coupled_sample_steps_per_s": count * info.M / sec,
+          "bound": "alu (instruction issue; shared-memory queue and scoreboard stalls lead)"}
+    if kernel_sources_hash(FOURIER_CLUSTER_SOURCES) == FOURIER_CLUSTER_KERNEL_INSTR["sources_sha256_16"]:
+        ipc = FOURIER_CLUSTER_KERNEL_INSTR["instructions_per_cell_step"]
+        warp_inst = count * info.cost * ipc / 32.0 / sec
+        peak = 4.0 * SMS * SM_MAX_MHZ * 1e6
+        cl["issue"] = {"instructions_per_cell_step": ipc, "achieved_warp_inst_per_s": warp_inst,
+                       "peak_warp_inst_per_s": peak, "frac": warp_inst / peak}
+    out["cluster_162"] = cl
     return out
 
 

@@ -118,7 +118,8 @@ typedef struct {
                                tau_{l-1} = 9 tau_l: the coarse noise of a coarse step carries every
                                Fourier mode of the summed fine noise that the coarse grid resolves (the
                                coarse Nyquist mode takes its two fine aliases with weight 2^-1/2 each).
-                               Fourier: n0 = 6, L_max <= 2 (grids 6^2, 18^2, 54^2), explicit scheme,
+                               Fourier: n0 = 6, L_max <= 3 (grids 6^2, 18^2, 54^2, 162^2; a 162^2
+                               level runs on clusters of 6 CTAs per sample), explicit scheme,
                                level n_l = n0 3^l, M_l = M_0 9^l; rho0 / phi arrays on those grids */
     int32_t state_repr;     /* representation of the fixed-point state (Eq. FullyDiscreteDK is linear apart
                                from sqrt([rho]^+), so both give the same scheme):
