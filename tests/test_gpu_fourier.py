@@ -232,3 +232,21 @@ def test_fourier_162_coarse_member_law_and_variance_decay(dk):
     beta = math.log(v2 / v3) / math.log(3.0)
     print(f"Fourier coupling at N = 1e9: V_2 = {v2:.3e}, V_3 = {v3:.3e}, beta = {beta:.2f}")
     assert beta > 2.5
+
+
+def test_algorithm1_reaches_162_and_matches_closed_form(dk):
+    """Algorithm 1 on the four-level hierarchy (6^2 .. 162^2) at N = 1e9 and
+    eps = 1e-3 relative: the stopping test of Eq. (convergence_criterion) with
+    ratio 3 needs the 162^2 level, the estimator variance meets eps^2 / 2, and
+    the estimate is within 4 standard deviations of the closed form of E[P_3]
+    (the telescoping sum is unbiased for the finest level's expectation, and
+    at N = 1e9 the density stays positive, so the closed form is exact)."""
+    wl = W.get("fourier6_162").with_(N=1e9)
+    with dk.Context.from_workload(wl) as ctx:
+        r = ctx.estimate(1e-3, relative=True, seed=wl.seed)
+        info = ctx.level_info(r.L)
+    print("estimate", r.estimate, "L", r.L, "M", [r.M[l] for l in range(r.L + 1)], "wall", r.wall_s)
+    assert r.L == 3 and r.converged == 1 and info.n == 162
+    assert r.variance <= r.eps_abs ** 2 / 2 * 1.05
+    cf = oracle.closed_form_EP_cos1(1.0, info.n, info.tau, info.M)
+    assert abs(r.estimate - cf) < 4 * math.sqrt(r.variance), (r.estimate, cf, math.sqrt(r.variance))

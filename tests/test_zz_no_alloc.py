@@ -52,6 +52,9 @@ def _run(ctx, dk, static, level, tag, first, count, seed):
     ("theta16_64", 2, [(2, 0, 0, 600, 10), (1, 0, 4, 900, 11)]),
     # ... and on the Fourier coupling's ratio-3 hierarchy
     ("fourier6_54", 2, [(2, 0, 0, 400, 12), (1, 0, 2, 700, 13)]),
+    # the cluster kernels: the 128^2 theta level (4-CTA clusters), the 162^2 Fourier level (6-CTA clusters)
+    ("theta16_128", 3, [(3, 0, 0, 40, 14)]),
+    ("fourier6_162", 3, [(3, 0, 5, 30, 15)]),
 ])
 def test_static_scratch_matches_context_scratch(dk, name, L_max, calls):
     wl = W.get(name).with_(L_max=L_max)
