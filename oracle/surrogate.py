@@ -14,6 +14,11 @@ TEST INFRASTRUCTURE ONLY (same rules as the rest of ``oracle/``).
 * ``mlp_*``: a plain FP64 4-layer ReLU perceptron 64-256-256-256-K, one
   output per test function (forward, backward, squared-error loss summed over
   the outputs) for checking the GPU kernels.
+
+Pins (tests/test_oracle_surrogate.py): the modes' orthonormality, the
+features' exact Gaussian law, the MLP gradient against central finite
+differences.  Parity unpinned: the values of a trained network (the paper
+has no learned level, so nothing fixes them beyond these properties).
 """
 from __future__ import annotations
 
