@@ -25,7 +25,7 @@ def _grid(n, L=1.0):
     return np.meshgrid(x, x, indexing="ij")
 
 
-@pytest.mark.parametrize("n", [6, 18, 54])
+@pytest.mark.parametrize("n", [6, 18, 54, 162])
 def test_shared_modes_are_the_fine_modes(n):
     nc = n // 3
     K = nc // 2
