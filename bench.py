@@ -65,7 +65,7 @@ THETA_SOURCES = ("dk_theta.cu", "dk_device.cuh")
 # cell-steps) of the 54^2 coupled launch, from its ncu --set full capture;
 # valid under the recorded hash of its sources.
 FOURIER_KERNEL_INSTR = {"kernel": "fourier_kernel n=54 coupled=True",
-                        "instructions_per_cell_step": 94.6, "sources_sha256_16": "f58083f4e5afc61f"}
+                        "instructions_per_cell_step": 94.6, "sources_sha256_16": "f3dd0738e5d2295f"}
 FOURIER_SOURCES = ("dk_fourier.cu", "dk_device.cuh")
 # The 162^2 Fourier level on 6-CTA clusters: thread instructions per cell-step
 # (fine and coarse cell-steps) of the coupled launch of 144 samples, from its

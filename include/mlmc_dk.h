@@ -128,8 +128,9 @@ typedef struct {
                                   rho-bar^m (m = 0..M_l - 1) kept in a per-level FP32 table on the device and the
                                   transfers G = rint(c 2^S sqrt([rho-bar^m + q 2^-S]^+) Z); S_l then only has to
                                   cover 12 standard deviations of the per-cell fluctuation, i.e. many more
-                                  fraction bits at large N.  Explicit NN hierarchies with N > 0 and grids up to
-                                  128^2 (register kernels), tables <= 512 MB; else MLMC_DK_ERR_UNSUPPORTED;
+                                  fraction bits at large N.  Explicit hierarchies with N > 0: NN with grids up
+                                  to 128^2 (register kernels), Fourier with grids up to 54^2 (one CTA per
+                                  sample); tables <= 512 MB; else MLMC_DK_ERR_UNSUPPORTED;
                                0: automatic -- fluctuation where it is supported and gains at least 3 bits on
                                   every level, absolute otherwise */
 } mlmc_dk_config;

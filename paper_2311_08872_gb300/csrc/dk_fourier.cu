@@ -21,6 +21,9 @@
 // Arithmetic as in the explicit kernels: int32 fixed-point state, integer
 // noise transfers G = rint(c 2^S sqrt(rho^+) Z) and diffusion fluxes, every
 // edge flux computed identically by both of its cells, so the mass is exact.
+// With the fluctuation state (FL) the state is q = (rho - rho-bar^m) 2^S
+// about the noise-free path and the amplitudes read rho-bar^m from the
+// per-step tables (fine: step m; coarse: coarse step m / 9).
 //
 // Work decomposition.  One CTA per sample.  A thread holds a segment of 6
 // consecutive fine cells of one row (3 Philox cell pairs) in registers, with
@@ -76,7 +79,7 @@ __device__ __forceinline__ void explicit_update(const int32_t* q, const int32_t*
     }
 }
 
-template <int N, bool CPL>
+template <int N, bool CPL, bool FL>
 __global__ void __launch_bounds__(FShape<N>::THREADS, FShape<N>::MINB) fourier_kernel(const KArgs a, const FArgs f) {
     using S = FShape<N>;
     constexpr int NC = S::NC, THREADS = S::THREADS;
@@ -146,8 +149,15 @@ __global__ void __launch_bounds__(FShape<N>::THREADS, FShape<N>::MINB) fourier_k
                     float ra, ca, sa, rb, cb, sb;
                     box_muller_polar(x.x, x.y, ra, ca, sa);
                     box_muller_polar(x.z, x.w, rb, cb, sb);
-                    const float ta = noise_amp(qr[2 * j], a.gf) * ra;
-                    const float tb = noise_amp(qr[2 * j + 1], a.gf) * rb;
+                    float ta, tb;
+                    if constexpr (FL) {
+                        const float2 rbar = reinterpret_cast<const float2*>(a.rbf + (size_t)m * N * N)[p];
+                        ta = noise_amp_fluct(qr[2 * j], rbar.x, a.isf, a.gf) * ra;
+                        tb = noise_amp_fluct(qr[2 * j + 1], rbar.y, a.isf, a.gf) * rb;
+                    } else {
+                        ta = noise_amp(qr[2 * j], a.gf) * ra;
+                        tb = noise_amp(qr[2 * j + 1], a.gf) * rb;
+                    }
                     g1[2 * j] = __float2int_rn(ta * ca);
                     g2[2 * j] = __float2int_rn(ta * sa);
                     g1[2 * j + 1] = __float2int_rn(tb * cb);
@@ -221,7 +231,9 @@ __global__ void __launch_bounds__(FShape<N>::THREADS, FShape<N>::MINB) fourier_k
                             s1 = fmaf(w, Tm[x1 * NC + y2], s1);
                             s2 = fmaf(w, Tm[N * NC + x1 * NC + y2], s2);
                         }
-                        const float amp = noise_amp(qc[o], a.gc);   // gc includes the 1/3 of the 9-step sum
+                        // gc includes the 1/3 of the 9-step sum
+                        const float amp = FL ? noise_amp_fluct(qc[o], a.rbc[(size_t)(m / 9) * NC * NC + o], a.isc, a.gc)
+                                             : noise_amp(qc[o], a.gc);
                         Gc1[o] = __float2int_rn(amp * s1);
                         Gc2[o] = __float2int_rn(amp * s2);
                     }
@@ -292,8 +304,8 @@ __global__ void __launch_bounds__(FShape<N>::THREADS, FShape<N>::MINB) fourier_k
                     o[k] = Df[k];
                     o[a.n_obs + k] = Dc[k];
                 }
-                o[2 * a.n_obs] = v[2 * kMaxObs] * a.dscale_f;
-                o[2 * a.n_obs + 1] = CPL ? v[2 * kMaxObs + 1] * a.dscale_c : 0.0;
+                o[2 * a.n_obs] = v[2 * kMaxObs] * a.dscale_f + a.mass_off_f;
+                o[2 * a.n_obs + 1] = CPL ? v[2 * kMaxObs + 1] * a.dscale_c + a.mass_off_c : 0.0;
             }
         }
         __syncthreads();
@@ -303,14 +315,14 @@ __global__ void __launch_bounds__(FShape<N>::THREADS, FShape<N>::MINB) fourier_k
     for (int i = tid; i < a.slot_stride; i += THREADS) a.partials[(size_t)i * n_slots + slot] = acc[i];
 }
 
-template <int N, bool CPL>
+template <int N, bool CPL, bool FL>
 cudaError_t fprepare(int slot_stride, VariantInfo* out) {
     using S = FShape<N>;
     const size_t smem = S::smem(slot_stride);
-    cudaError_t e = cudaFuncSetAttribute(fourier_kernel<N, CPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(fourier_kernel<N, CPL, FL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0, dev = 0, sms = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fourier_kernel<N, CPL>, S::THREADS, smem)) !=
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fourier_kernel<N, CPL, FL>, S::THREADS, smem)) !=
         cudaSuccess)
         return e;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -325,7 +337,7 @@ cudaError_t fprepare(int slot_stride, VariantInfo* out) {
     return cudaSuccess;
 }
 
-template <int N, bool CPL>
+template <int N, bool CPL, bool FL>
 cudaError_t flaunch(const KArgs& a, const FArgs& f, int n_ctas, cudaStream_t st, int priority) {
     using S = FShape<N>;
     cudaLaunchConfig_t cfg{};
@@ -342,31 +354,46 @@ cudaError_t flaunch(const KArgs& a, const FArgs& f, int n_ctas, cudaStream_t st,
     }
     cfg.attrs = attr;
     cfg.numAttrs = na;
-    return cudaLaunchKernelEx(&cfg, fourier_kernel<N, CPL>, a, f);
+    return cudaLaunchKernelEx(&cfg, fourier_kernel<N, CPL, FL>, a, f);
+}
+
+template <bool FL>
+cudaError_t fourier_info_fl(int n, bool coupled, int slot_stride, VariantInfo* out) {
+    switch (n) {
+        case 6: return coupled ? cudaSuccess : fprepare<6, false, FL>(slot_stride, out);   // level 0 only
+        case 18: return coupled ? fprepare<18, true, FL>(slot_stride, out) : fprepare<18, false, FL>(slot_stride, out);
+        case 54: return coupled ? fprepare<54, true, FL>(slot_stride, out) : fprepare<54, false, FL>(slot_stride, out);
+        default: return cudaSuccess;
+    }
+}
+
+template <bool FL>
+cudaError_t launch_fourier_fl(int n, bool coupled, const KArgs& a, const FArgs& f, int n_ctas, cudaStream_t st,
+                              int priority) {
+    switch (n) {
+        case 6: return coupled ? cudaErrorInvalidValue : flaunch<6, false, FL>(a, f, n_ctas, st, priority);
+        case 18: return coupled ? flaunch<18, true, FL>(a, f, n_ctas, st, priority)
+                                : flaunch<18, false, FL>(a, f, n_ctas, st, priority);
+        case 54: return coupled ? flaunch<54, true, FL>(a, f, n_ctas, st, priority)
+                                : flaunch<54, false, FL>(a, f, n_ctas, st, priority);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace
 
 bool fourier_supported(int n) { return n == 6 || n == 18 || n == 54; }
 
-cudaError_t fourier_variant_info(int n, bool coupled, int slot_stride, VariantInfo* out) {
+cudaError_t fourier_variant_info(int n, bool coupled, int slot_stride, VariantInfo* out, bool fluct) {
     *out = VariantInfo{};
-    switch (n) {
-        case 6: return coupled ? cudaSuccess : fprepare<6, false>(slot_stride, out);   // level 0 only
-        case 18: return coupled ? fprepare<18, true>(slot_stride, out) : fprepare<18, false>(slot_stride, out);
-        case 54: return coupled ? fprepare<54, true>(slot_stride, out) : fprepare<54, false>(slot_stride, out);
-        default: return cudaSuccess;
-    }
+    return fluct ? fourier_info_fl<true>(n, coupled, slot_stride, out) : fourier_info_fl<false>(n, coupled, slot_stride, out);
 }
 
 cudaError_t launch_fourier(int n, bool coupled, const KArgs& a, const FArgs& f, int n_ctas, cudaStream_t st,
-                           int priority) {
-    switch (n) {
-        case 6: return coupled ? cudaErrorInvalidValue : flaunch<6, false>(a, f, n_ctas, st, priority);
-        case 18: return coupled ? flaunch<18, true>(a, f, n_ctas, st, priority) : flaunch<18, false>(a, f, n_ctas, st, priority);
-        case 54: return coupled ? flaunch<54, true>(a, f, n_ctas, st, priority) : flaunch<54, false>(a, f, n_ctas, st, priority);
-        default: return cudaErrorInvalidValue;
-    }
+                           int priority, bool fluct) {
+    if (fluct && (!a.rbf || (coupled && !a.rbc))) return cudaErrorInvalidValue;
+    return fluct ? launch_fourier_fl<true>(n, coupled, a, f, n_ctas, st, priority)
+                 : launch_fourier_fl<false>(n, coupled, a, f, n_ctas, st, priority);
 }
 
 }  // namespace dk

@@ -193,10 +193,11 @@ struct FArgs {
     const double* phic64;
 };
 bool fourier_supported(int n);
-cudaError_t fourier_variant_info(int n, bool coupled, int slot_stride, VariantInfo* out);
+// fluct: the fluctuation-state build (KArgs::rbf / rbc tables required)
+cudaError_t fourier_variant_info(int n, bool coupled, int slot_stride, VariantInfo* out, bool fluct = false);
 // One CTA per sample slot; partials must hold n_ctas * slot_stride doubles.
 cudaError_t launch_fourier(int n, bool coupled, const KArgs& a, const FArgs& f, int n_ctas, cudaStream_t stream,
-                           int priority = 0);
+                           int priority = 0, bool fluct = false);
 // Grids beyond one CTA (162^2, coupled with 54^2): clusters of 6 CTAs, one
 // sample slot per cluster; n_ctas a multiple of 6.
 bool fourier_cluster_supported(int n);

@@ -427,7 +427,7 @@ cudaError_t launch_main(const mlmc_dk_ctx* c, int level, bool coupled, const dk:
         fa.phic64 = coupled ? c->lv[level - 1].d_phi64 : nullptr;
         if (dk::fourier_cluster_supported(t.n))
             return dk::launch_fourier_cluster(t.n, coupled, a, fa, n_ctas, st, priority);
-        return dk::launch_fourier(t.n, coupled, a, fa, n_ctas, st, priority);
+        return dk::launch_fourier(t.n, coupled, a, fa, n_ctas, st, priority, c->fluct != 0);
     }
     if (c->theta) {
         dk::TArgs ta = c->targs;
@@ -707,7 +707,7 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
     // deviations: at large N (the paper's N = 2e9) that is many more bits, i.e.
     // finer resolution of every transfer and flux.
     std::vector<int> S_abs(cfg->L_max + 1), S_fl(cfg->L_max + 1);
-    bool fl_ok = !fourier && !theta && cfg->N > 0 && cfg->stream_from_n == 0;
+    bool fl_ok = !theta && cfg->N > 0 && cfg->stream_from_n == 0;
     double table_bytes = 0.0;
     int min_gain = 1 << 20;
     for (int l = 0; l <= cfg->L_max; ++l) {
@@ -740,13 +740,16 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
         S_fl[l] = F;
         min_gain = std::min(min_gain, F - S);
         table_bytes += 4.0 * (double)cells * (double)M;
-        if (dk::variant_count(n, true) == 0) fl_ok = false;
+        // kernels built with the fluctuation state: the register kernels (NN) and
+        // the one-CTA Fourier kernel
+        if (fourier ? !dk::fourier_supported(n) : dk::variant_count(n, true) == 0) fl_ok = false;
     }
     fl_ok = fl_ok && table_bytes <= 512.0 * (1 << 20);
     if (cfg->state_repr == 2 && !fl_ok) {
         mlmc_dk_free(c);
         return fail(nullptr, MLMC_DK_ERR_UNSUPPORTED,
-                    "fluctuation state: explicit NN hierarchy with N > 0, grids up to 128^2, mean-field tables <= 512 MB");
+                    "fluctuation state: explicit scheme with N > 0, grids up to 128^2 (NN) or 54^2 (Fourier), "
+                    "mean-field tables <= 512 MB");
     }
     if (cfg->state_repr < 0 || cfg->state_repr > 2) {
         mlmc_dk_free(c);
@@ -891,7 +894,8 @@ int mlmc_dk_init(const mlmc_dk_config* cfg, mlmc_dk_ctx** out) {
                 if (mode == 1 && l == 0) continue;
                 dk::VariantInfo vi{};
                 e = dk::fourier_cluster_supported(t.n) ? dk::fourier_cluster_variant_info(t.n, mode == 1, c->stride, &vi)
-                                                       : dk::fourier_variant_info(t.n, mode == 1, c->stride, &vi);
+                                                       : dk::fourier_variant_info(t.n, mode == 1, c->stride, &vi,
+                                                                                  c->fluct != 0);
                 if (e != cudaSuccess) {
                     mlmc_dk_free(c);
                     return cuda_fail(nullptr, e, "Fourier kernel setup");

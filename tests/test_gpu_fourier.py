@@ -250,3 +250,50 @@ def test_algorithm1_reaches_162_and_matches_closed_form(dk):
     assert r.variance <= r.eps_abs ** 2 / 2 * 1.05
     cf = oracle.closed_form_EP_cos1(1.0, info.n, info.tau, info.M)
     assert abs(r.estimate - cf) < 4 * math.sqrt(r.variance), (r.estimate, cf, math.sqrt(r.variance))
+
+
+# ---------------------------------------------------------------- fluctuation state
+@pytest.mark.parametrize("level,tag,count", [(1, 0, 12), (2, 0, 8), (2, 1, 6)])
+def test_paper_setting_fourier_main_particle_number(dk, level, tag, count):
+    """The paper's regular setting (Section 7.2) with the Fourier coupling at
+    its main particle number N = 2e9: the state is held as its fluctuation
+    about the noise-free path (chosen automatically), meets the unrelaxed
+    per-sample bar, and the reported masses are the mean field's."""
+    wl = W.get("paper_reg_fourier")
+    levels = _levels(wl)
+    seed, first = wl.seed, 3
+    with dk.Context.from_workload(wl) as ctx:
+        assert all(ctx.level_info(l).fluct == 1 for l in range(wl.L_max + 1))
+        sums, samp = _gpu(ctx, dk, level, tag, first, count, seed)
+    coupled = tag == 0
+    ol = oracle.level_inputs(wl.length, levels, wl.N, wl.rho0_all(), wl.phi_all(), level, coupled, coupling=1)
+    r = oracle.run_samples(ol, seed, range(first, first + count), coupled, stream=tag, processes=4)
+    worst = _worst(wl, levels, level, coupled, samp, r)
+    print(f"paper_reg_fourier N = 2e9 level {level} tag {tag}: worst/bound {worst:.3g}")
+    assert worst <= 1.0
+    np.testing.assert_allclose(samp[:, 2], r["mass_f"], rtol=1e-12)
+    if coupled:
+        np.testing.assert_allclose(samp[:, 3], r["mass_c"], rtol=1e-12)
+    assert int(sums[0]) == count and sums[1] == 0.0
+
+
+def test_fluctuation_state_on_request_at_low_particle_number(dk):
+    """The fluctuation state asked for explicitly where the automatic choice is
+    the absolute one (N = 1e5): the same scheme, so the same per-sample bar
+    against the oracle; the 162^2 level has no such build and is refused."""
+    wl = W.get("fourier6_54")
+    levels = _levels(wl)
+    level, seed, first, count = 2, 61, 0, 8
+    with dk.Context.from_workload(wl) as ctx:
+        assert ctx.level_info(level).fluct == 0
+    with dk.Context.from_workload(wl, state_repr=2) as ctx:
+        assert ctx.level_info(level).fluct == 1
+        sums, samp = _gpu(ctx, dk, level, 0, first, count, seed)
+    ol = oracle.level_inputs(wl.length, levels, wl.N, wl.rho0_all(), wl.phi_all(), level, True, coupling=1)
+    r = oracle.run_samples(ol, seed, range(first, first + count), True, processes=4)
+    worst = _worst(wl, levels, level, True, samp, r)
+    print(f"fourier6_54 fluctuation state at N = 1e5: worst/bound {worst:.3g}")
+    assert worst <= 1.0 and sums[1] == 0.0
+    with pytest.raises(dk.MLMCError) as e:
+        dk.Context.from_workload(W.get("fourier6_162"), state_repr=2)
+    assert e.value.code == dk.ERR_UNSUPPORTED
